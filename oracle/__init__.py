@@ -1,0 +1,231 @@
+"""ORACLE — test infrastructure only.
+
+Plain FP64 CPU implementation of the ideal-MHD finite-volume step (paper §2),
+loaded through ctypes.  Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline leg may import this package; the product path never does.
+
+State dictionaries use the external layout of the C library (no ghosts, x
+fastest): keys rho, mx, my, mz, E and b0, b1, b2, where b0/b1/b2 are the face
+fields Bx [nz][ny][nx+1], By [nz][ny+1][nx], Bz [nz+1][ny][nx] in 3D, and in
+2D Bx [ny][nx+1], By [ny+1][nx] and the cell-centred Bz [ny][nx].
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RECON = {"plm": 0, "wenoz": 1, "ppm": 2}
+RIEMANN = {"hll": 0, "hlld": 1}
+BC = {"periodic": 0, "outflow": 1}
+KEYS = ("rho", "mx", "my", "mz", "E", "b0", "b1", "b2")
+PHASES = ("ghost", "c2p", "recon", "riemann", "fluxdiff", "emf", "ct", "rk", "cfl")
+OPS = ("add", "mul", "div", "sqrt")
+
+
+class OrcConfig(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x0", ctypes.c_double * 3), ("x1", ctypes.c_double * 3), ("gamma", ctypes.c_double),
+                ("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("rk", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        so = _build.build()
+        L = ctypes.CDLL(so)
+        P = ctypes.c_void_p
+        D = ctypes.c_double
+        DP = ctypes.POINTER(ctypes.c_double)
+        L.orc_create.restype = P
+        L.orc_create.argtypes = [ctypes.POINTER(OrcConfig)]
+        L.orc_destroy.argtypes = [P]
+        L.orc_set_state.argtypes = [P, ctypes.POINTER(DP)]
+        L.orc_get_state.argtypes = [P, ctypes.POINTER(DP)]
+        L.orc_cfl_dt.restype = D
+        L.orc_cfl_dt.argtypes = [P]
+        L.orc_step.argtypes = [P, D]
+        L.orc_time.restype = D
+        L.orc_time.argtypes = [P]
+        L.orc_fallbacks.restype = ctypes.c_longlong
+        L.orc_fallbacks.argtypes = [P]
+        L.orc_status.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_get_emf.argtypes = [P, ctypes.c_int, DP]
+        L.orc_stage_increment.argtypes = [P, D, ctypes.POINTER(DP)]
+        L.orc_riemann.argtypes = [ctypes.c_int, DP, DP, D, D, DP, DP]
+        L.orc_side_flux.argtypes = [DP, D, D, DP, DP]
+        L.orc_recon.argtypes = [ctypes.c_int, DP, DP, DP]
+        L.orc_c2p.argtypes = [DP, D, DP]
+        L.orc_fast_speed.restype = D
+        L.orc_fast_speed.argtypes = [D, D, D, D, D]
+        L.orc_count_flops.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
+                                      ctypes.POINTER(ctypes.c_ulonglong)]
+        _lib = L
+    return _lib
+
+
+def make_config(cfg):
+    """cfg: dict with ndim, n (tuple), x0, x1, gamma, recon, riemann, rk, cfl, bc (6 names)."""
+    c = OrcConfig()
+    n = list(cfg["n"]) + [1] * (3 - len(cfg["n"]))
+    c.ndim = cfg["ndim"]
+    c.nx, c.ny, c.nz = n[0], n[1], n[2] if cfg["ndim"] == 3 else 1
+    x0 = list(cfg["x0"]) + [0.0] * (3 - len(cfg["x0"]))
+    x1 = list(cfg["x1"]) + [1.0] * (3 - len(cfg["x1"]))
+    for d in range(3):
+        c.x0[d] = x0[d]
+        c.x1[d] = x1[d]
+    c.gamma = cfg["gamma"]
+    c.recon = RECON[cfg["recon"]]
+    c.riemann = RIEMANN[cfg["riemann"]]
+    c.rk = cfg["rk"]
+    c.cfl = cfg["cfl"]
+    for s in range(6):
+        c.bc[s] = BC[cfg["bc"][s]]
+    return c
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ptrs(arrays):
+    arr = (ctypes.POINTER(ctypes.c_double) * 8)()
+    for q, a in enumerate(arrays):
+        arr[q] = _dp(a)
+    return arr
+
+
+def state_shapes(cfg):
+    nd = cfg["ndim"]
+    nx, ny = cfg["n"][0], cfg["n"][1]
+    nz = cfg["n"][2] if nd == 3 else 1
+    cell = (nz, ny, nx)
+    if nd == 3:
+        faces = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)]
+    else:
+        faces = [(1, ny, nx + 1), (1, ny + 1, nx), (1, ny, nx)]
+    return [cell] * 5 + faces
+
+
+class OracleSim:
+    """One grid advanced by the oracle scheme."""
+
+    def __init__(self, cfg, state=None):
+        self.cfg = dict(cfg)
+        self._c = make_config(cfg)
+        self.h = lib().orc_create(ctypes.byref(self._c))
+        if not self.h:
+            raise ValueError("oracle rejected the configuration")
+        self.shapes = state_shapes(cfg)
+        if state is not None:
+            self.set_state(state)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_destroy(self.h)
+            self.h = None
+
+    def set_state(self, state):
+        arrs = [np.ascontiguousarray(np.asarray(state[k], dtype=np.float64).reshape(s))
+                for k, s in zip(KEYS, self.shapes)]
+        lib().orc_set_state(self.h, _ptrs(arrs))
+
+    def get_state(self):
+        arrs = [np.zeros(s) for s in self.shapes]
+        lib().orc_get_state(self.h, _ptrs(arrs))
+        return dict(zip(KEYS, arrs))
+
+    def cfl_dt(self):
+        return lib().orc_cfl_dt(self.h)
+
+    def step(self, dt):
+        rc = lib().orc_step(self.h, float(dt))
+        if rc != 0:
+            raise FloatingPointError("oracle met a non-positive density or pressure")
+
+    def advance(self, nsteps, record_dt=False):
+        dts = []
+        for _ in range(nsteps):
+            dt = self.cfl_dt()
+            self.step(dt)
+            dts.append(dt)
+        return dts if record_dt else None
+
+    @property
+    def time(self):
+        return lib().orc_time(self.h)
+
+    @property
+    def fallbacks(self):
+        return lib().orc_fallbacks(self.h)
+
+    def emf(self, comp):
+        nd = self.cfg["ndim"]
+        n = list(self.cfg["n"]) + [1]
+        nx, ny, nz = n[0], n[1], (n[2] if nd == 3 else 1)
+        ext = {0: (nz + 1, ny + 1, nx), 1: (nz + 1, ny, nx + 1), 2: (nz, ny + 1, nx + 1)}[comp]
+        out = np.zeros(ext)
+        if lib().orc_get_emf(self.h, comp, _dp(out)) != 0:
+            raise ValueError("no such edge field")
+        return out
+
+    def stage_increment(self, dt):
+        arrs = [np.zeros(s) for s in self.shapes]
+        lib().orc_stage_increment(self.h, float(dt), _ptrs(arrs))
+        return dict(zip(KEYS, arrs))
+
+
+def riemann(solver, wl, wr, bn, gamma):
+    """Riemann flux (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and UCT ingredients (a+, a-, d, uL, uR)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    F = np.zeros(7)
+    ing = np.zeros(5)
+    lib().orc_riemann(RIEMANN[solver], _dp(wl), _dp(wr), float(bn), float(gamma), _dp(F), _dp(ing))
+    return F, ing
+
+
+def side_flux(w, bn, gamma):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    F = np.zeros(7)
+    U = np.zeros(7)
+    lib().orc_side_flux(_dp(w), float(bn), float(gamma), _dp(F), _dp(U))
+    return F, U
+
+
+def recon(method, s5):
+    s5 = np.ascontiguousarray(s5, dtype=np.float64)
+    p = ctypes.c_double()
+    m = ctypes.c_double()
+    lib().orc_recon(RECON[method], _dp(s5), ctypes.byref(p), ctypes.byref(m))
+    return p.value, m.value
+
+
+def c2p(u8, gamma):
+    u8 = np.ascontiguousarray(u8, dtype=np.float64)
+    V = np.zeros(8)
+    lib().orc_c2p(_dp(u8), float(gamma), _dp(V))
+    return V
+
+
+def fast_speed(rho, p, B2, bn, gamma):
+    return lib().orc_fast_speed(rho, p, B2, bn, gamma)
+
+
+def count_flops(cfg, state, nsteps, dt):
+    """Counted-scalar run: dict phase -> dict op -> count (one CFL + nsteps steps)."""
+    c = make_config(cfg)
+    shapes = state_shapes(cfg)
+    arrs = [np.ascontiguousarray(np.asarray(state[k], dtype=np.float64).reshape(s)) for k, s in zip(KEYS, shapes)]
+    out = (ctypes.c_ulonglong * (len(PHASES) * len(OPS)))()
+    lib().orc_count_flops(ctypes.byref(c), _ptrs(arrs), int(nsteps), float(dt), out)
+    res = {}
+    for i, ph in enumerate(PHASES):
+        res[ph] = {op: int(out[i * len(OPS) + j]) for j, op in enumerate(OPS)}
+    return res

@@ -1,0 +1,172 @@
+// ORACLE — test infrastructure only.  C entry points over the templated
+// oracle scheme (mhd_oracle.hpp), loaded by the tests through ctypes.
+//
+// External state layout (no ghosts), x fastest:
+//   cell arrays rho, mx, my, mz, E (and the 2D cell Bz): [nz][ny][nx]
+//   face Bx: [nz][ny][nx+1], By: [nz][ny+1][nx], Bz (3D): [nz+1][ny][nx]
+// On a periodic axis the last face duplicates the first: it is ignored on
+// input and written as a copy of the first on output.
+#include <cstring>
+#include <memory>
+
+#include "mhd_oracle.hpp"
+
+using namespace orc;
+
+namespace {
+
+template <class R> struct Ext {
+  // extents of slot q in the external layout
+  static void extents(const Sim<R>& s, int q, int e[3]) {
+    e[0] = s.n[0]; e[1] = s.n[1]; e[2] = s.n[2];
+    for (int d = 0; d < s.ndim; d++)
+      if (s.is_face(q, d)) e[d] += 1;
+  }
+};
+
+template <class R> void load(Sim<R>& s, const double* const* src) {
+  for (int q = 0; q < NQ; q++) {
+    int e[3];
+    Ext<R>::extents(s, q, e);
+    const double* p = src[q];
+    for (int k = 0; k < e[2]; k++)
+      for (int j = 0; j < e[1]; j++)
+        for (int i = 0; i < e[0]; i++) s.U0[q](i, j, k) = R(*p++);
+  }
+}
+template <class R> void store(Sim<R>& s, double* const* dst) {
+  s.fill_ghosts(s.U0);
+  for (int q = 0; q < NQ; q++) {
+    int e[3];
+    Ext<R>::extents(s, q, e);
+    double* p = dst[q];
+    for (int k = 0; k < e[2]; k++)
+      for (int j = 0; j < e[1]; j++)
+        for (int i = 0; i < e[0]; i++) *p++ = value(s.U0[q](i, j, k));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+struct OrcConfig {
+  int ndim, nx, ny, nz;
+  double x0[3], x1[3];
+  double gamma;
+  int recon, riemann, rk;
+  double cfl;
+  int bc[6];
+};
+
+static Config to_cfg(const OrcConfig* c) {
+  Config o{};
+  o.ndim = c->ndim; o.nx = c->nx; o.ny = c->ny; o.nz = c->nz;
+  for (int d = 0; d < 3; d++) { o.x0[d] = c->x0[d]; o.x1[d] = c->x1[d]; }
+  o.gamma = c->gamma; o.recon = c->recon; o.riemann = c->riemann; o.rk = c->rk; o.cfl = c->cfl;
+  for (int s = 0; s < 6; s++) o.bc[s] = c->bc[s];
+  return o;
+}
+
+void* orc_create(const OrcConfig* c) {
+  try {
+    return new Sim<double>(to_cfg(c));
+  } catch (...) {
+    return nullptr;
+  }
+}
+void orc_destroy(void* h) { delete static_cast<Sim<double>*>(h); }
+
+int orc_set_state(void* h, const double* const* arrays) {
+  load(*static_cast<Sim<double>*>(h), arrays);
+  return 0;
+}
+int orc_get_state(void* h, double* const* arrays) {
+  store(*static_cast<Sim<double>*>(h), arrays);
+  return 0;
+}
+double orc_cfl_dt(void* h) { return static_cast<Sim<double>*>(h)->cfl_dt(); }
+int orc_step(void* h, double dt) {
+  auto* s = static_cast<Sim<double>*>(h);
+  s->step(dt);
+  return s->bad ? -4 : 0;
+}
+double orc_time(void* h) { return static_cast<Sim<double>*>(h)->time; }
+long long orc_fallbacks(void* h) { return static_cast<Sim<double>*>(h)->fallbacks; }
+int orc_status(void* h, long long* bad_cell) {
+  auto* s = static_cast<Sim<double>*>(h);
+  if (bad_cell) *bad_cell = s->bad_cell;
+  return s->bad ? -4 : 0;
+}
+
+// Edge field E_c of the last stage computed, over a-face [0,n_a] x b-face [0,n_b]
+// x c-cell [0,n_c-1], written x fastest.
+int orc_get_emf(void* h, int cc, double* out) {
+  auto* s = static_cast<Sim<double>*>(h);
+  int a = (cc + 1) % 3, b = (cc + 2) % 3;
+  int ext[3];
+  ext[a] = s->n[a] + 1; ext[b] = s->n[b] + 1; ext[cc] = s->n[cc];
+  if (s->ndim == 2) { if (cc != 2) return -1; ext[2] = 1; }
+  for (int k = 0; k < ext[2]; k++)
+    for (int j = 0; j < ext[1]; j++)
+      for (int i = 0; i < ext[0]; i++) *out++ = s->E[cc](i, j, k);
+  return 0;
+}
+// Stage increment L(U^n) for the current state with step dt (no state change).
+int orc_stage_increment(void* h, double dt, double* const* arrays) {
+  auto* s = static_cast<Sim<double>*>(h);
+  s->stage_increment(s->U0, dt);
+  for (int q = 0; q < NQ; q++) {
+    int e[3];
+    Ext<double>::extents(*s, q, e);
+    double* p = arrays[q];
+    for (int k = 0; k < e[2]; k++)
+      for (int j = 0; j < e[1]; j++)
+        for (int i = 0; i < e[0]; i++) {
+          bool upd = true;
+          for (int d = 0; d < s->ndim; d++) {
+            int idx = d == 0 ? i : (d == 1 ? j : k);
+            if (idx >= s->n[d] && !(s->is_face(q, d) && !s->periodic[d])) upd = false;
+          }
+          *p++ = upd ? s->Lq[q](i, j, k) : 0.0;
+        }
+  }
+  return s->bad ? -4 : 0;
+}
+
+// ---- pointwise pieces ----
+void orc_riemann(int solver, const double* wl, const double* wr, double bn, double gamma, double* F, double* ing) {
+  if (solver == RS_HLLD) riemann_hlld<double>(wl, wr, bn, gamma, F, ing);
+  else riemann_hll<double>(wl, wr, bn, gamma, F, ing);
+}
+void orc_side_flux(const double* w, double bn, double gamma, double* F, double* U) {
+  SideState<double> s = side_state<double>(w, bn, gamma);
+  for (int q = 0; q < NW; q++) { F[q] = s.F[q]; U[q] = s.U[q]; }
+}
+void orc_recon(int method, const double* s5, double* plus, double* minus) {
+  if (method == RECON_PLM) recon_plm<double>(s5, *plus, *minus);
+  else if (method == RECON_WENOZ) recon_wenoz<double>(s5, *plus, *minus);
+  else recon_ppm<double>(s5, *plus, *minus);
+}
+void orc_c2p(const double* u8, double gamma, double* V) {
+  cons_to_prim<double>(u8[0], u8[1], u8[2], u8[3], u8[4], u8[5], u8[6], u8[7], gamma, V);
+}
+double orc_fast_speed(double rho, double p, double B2, double bn, double gamma) {
+  return fast_speed<double>(rho, p, B2, bn, gamma);
+}
+
+// ---- algorithmic flop count: nsteps steps of size dt with the Counted scalar ----
+// out[ph * OP_N + op] for phases PH_* and kinds OP_*; also counts the CFL once.
+int orc_count_flops(const OrcConfig* c, const double* const* arrays, int nsteps, double dt,
+                    unsigned long long* out) {
+  Sim<Counted> s(to_cfg(c));
+  load(s, arrays);
+  g_flops.reset();
+  s.cfl_dt();
+  for (int t = 0; t < nsteps; t++) s.step(Counted(dt));
+  for (int ph = 0; ph < PH_N; ph++)
+    for (int op = 0; op < OP_N; op++) out[ph * OP_N + op] = g_flops.n[ph][op];
+  return 0;
+}
+
+}  // extern "C"
