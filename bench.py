@@ -1,0 +1,343 @@
+"""Benchmark: FP64 cell-updates per second of the ideal-MHD CT step on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+A step is one full time step of the workload (CFL dt computed on the device,
+then every RK stage: ghost fill, primitive recovery, three fused
+reconstruct -> Riemann -> flux-difference sweeps, UCT edge fields, CT + RK
+combine).  `value` is cell-updates per second with the state resident in HBM;
+`e2e` is the same metric through the C-ABI with the state copied from pinned
+host memory before, and read back after, every step.  Under torchrun each rank
+runs its own replica (the step is not sharded across GPUs): value = all ranks'
+cell-updates / max rank time.
+
+--impl reference times the FP64 CPU oracle on the host cores, on a bounded
+sample of the same workload (a smaller grid of the same kind), same metric.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2511_20337_b300 import workloads as W  # noqa: E402
+
+METRIC = "FP64 cell-updates/s per B300"
+UNIT = "cell-updates/s"
+
+WORKLOADS = {
+    # name: (generator, flops variant, description)
+    "turbulent3d-256": (lambda: W.turbulent_3d(256), "turbulent3d_plm_hlld_rk2",
+                        "3D ideal MHD 256^3 periodic, uniform rho=1 p=1 B=(1,1,1)/sqrt3 + seeded Gaussian "
+                        "rho/v perturbations (1%, |k|<=8); PLM-minmod + HLLD + SSP-RK2 + UCT-HLL CT, CFL 0.4"),
+    "turbulent3d-128": (lambda: W.turbulent_3d(128), "turbulent3d_plm_hlld_rk2",
+                        "3D ideal MHD 128^3 periodic (profiling size), same recipe and scheme as turbulent3d-256"),
+    "blast3d-512": (lambda: W.blast_3d(512), "blast3d_wenoz_hlld_rk3",
+                    "3D magnetised blast 512^3 outflow, rho=1, p=0.1 / 10 (r<=0.1), B=10/sqrt2 (1,1,0); "
+                    "WENO-Z + HLLD + SSP-RK3 + UCT-HLL CT, CFL 0.4"),
+    "blast3d-512-ppm": (lambda: W.blast_3d(512, recon="ppm"), "blast3d_ppm_hlld_rk3",
+                        "3D magnetised blast 512^3 outflow; PPM + HLLD + SSP-RK3 + UCT-HLL CT, CFL 0.4"),
+    "orszag-tang2d-128": (lambda: W.orszag_tang_2d(128), "orszag_tang2d_plm_hlld_rk2",
+                          "2D Orszag-Tang 128^2 periodic; PLM-minmod + HLLD + SSP-RK2 + UCT-HLL CT, CFL 0.4"),
+}
+# CPU-oracle sample of each workload: the same kind of state on a smaller grid
+SAMPLES = {
+    "turbulent3d-256": (lambda: W.turbulent_3d(48), "turbulent 3D 48^3 (same scheme and field recipe)"),
+    "turbulent3d-128": (lambda: W.turbulent_3d(48), "turbulent 3D 48^3 (same scheme and field recipe)"),
+    "blast3d-512": (lambda: W.blast_3d(32), "blast 3D 32^3 (same scheme and setup)"),
+    "blast3d-512-ppm": (lambda: W.blast_3d(32, recon="ppm"), "blast 3D 32^3 PPM (same scheme and setup)"),
+    "orszag-tang2d-128": (lambda: W.orszag_tang_2d(128), "Orszag-Tang 2D 128^2 (the workload itself)"),
+}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cells_of(cfg):
+    return int(np.prod(cfg["n"][:cfg["ndim"]]))
+
+
+# ---------------------------------------------------------------------------
+# algorithmic flops (per-unit counts of the oracle, stored by tests/golden/make_flops.py)
+# ---------------------------------------------------------------------------
+def flop_model(cfg, variant):
+    path = os.path.join(ROOT, "tests", "golden", "flops_per_unit.json")
+    per = json.load(open(path))["variants"][variant]["per_unit"]
+    nd = cfg["ndim"]
+    n = list(cfg["n"][:nd])
+    G = 2 if cfg["recon"] == "plm" else 3
+    rk = cfg["rk"]
+    cells = int(np.prod(n))
+    sweep = {}
+    for d in range(nd):
+        rows = int(np.prod([n[t] + 2 for t in range(nd) if t != d]))
+        sweep[d] = (per["recon"] * (n[d] + 2) * rows + per["riemann"] * (n[d] + 1) * rows
+                    + per["fluxdiff"] / nd * cells)
+    padded = int(np.prod([m + 2 * G for m in n]))
+    if nd == 2:
+        edges = (n[0] + 1) * (n[1] + 1)
+    else:
+        edges = sum(int(np.prod([n[e] + (1 if e != c else 0) for e in range(3)])) for c in range(3))
+    periodic = [cfg["bc"][2 * d] == "periodic" for d in range(nd)]
+    ct_faces = sum(int(np.prod([n[e] + (1 if (e == d and not periodic[d]) else 0) for e in range(nd)]))
+                   for d in range(nd))
+    elems = cells * (6 if nd == 2 else 5) + ct_faces
+    stage = (per["c2p"] * padded + sum(sweep.values()) + per["emf"] * edges + per["ct"] * ct_faces
+             + per["rk"] * elems)
+    step = rk * stage + per["cfl"] * cells
+    return {"sweep_per_launch": sweep, "step": step, "per_cell_update": step / cells}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(sample_fn, seconds_budget=15.0, max_steps=None):
+    """The oracle as it stands, single-threaded, on the sample grid: cell-updates/s."""
+    import oracle
+    cfg, st = sample_fn()
+    s = oracle.OracleSim(cfg, st)
+    s.advance(1)  # warm
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        s.advance(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_budget or (max_steps and steps >= max_steps):
+            break
+    return cells_of(cfg) * steps / el, steps, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    gen, desc = SAMPLES[args.workload]
+    cfg, st = gen()
+    s = oracle.OracleSim(cfg, st)
+    for _ in range(args.warmup):
+        s.advance(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.advance(1)
+    el = time.perf_counter() - t0
+    value = cells_of(cfg) * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload][2], "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{desc}, {args.steps} steps after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2511_20337_b300 import mhd
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    gen, variant, desc = WORKLOADS[args.workload]
+    cfg, st = gen()
+    ncell = cells_of(cfg)
+    stream = torch.cuda.Stream(device=dev)
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in st.items()}
+    devs = {k: v.to(dev) for k, v in host.items()}
+    del st
+    sim = mhd.Sim(cfg, devs, stream=ctypes_stream(stream))
+    h2d = sum(v.numel() * 8 for v in host.values())
+    out_host = {k: torch.empty_like(v).pin_memory() for k, v in host.items()}
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also captures the step graph)
+    sim.advance(args.warmup)
+    torch.cuda.synchronize(dev)
+    barrier()
+
+    # ---- timed region: K steps, state resident in HBM ----
+    launches0 = sim.launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0.record(stream)
+        sim.advance(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launches - launches0
+    rc, bad = sim.status()
+    if rc != 0:
+        raise RuntimeError(f"device reported {rc} at cell {bad}")
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = ncell * args.steps * world / (t_max * 1e-3)
+
+    # ---- per-kernel device times (events after each launch) for the roofline ----
+    prof_steps = max(1, min(args.steps, 10))
+    kms, kcnt = sim.profile_steps(prof_steps)
+    peak = mhd.probe_fp64_gflops()
+    fm = flop_model(cfg, variant)
+    nd = cfg["ndim"]
+    sweep_ms = sum(kms[f"sweep_{a}"] for a in "xyz"[:nd])
+    sweep_launches = sum(kcnt[f"sweep_{a}"] for a in "xyz"[:nd])
+    sweep_flops = sum(fm["sweep_per_launch"].values()) * cfg["rk"] * prof_steps  # all sweep launches
+    achieved = sweep_flops / (sweep_ms * 1e-3) / 1e9
+    step_ms_prof = sum(kms.values()) / prof_steps
+    step_achieved = fm["step"] / (step_ms_prof * 1e-3) / 1e9
+    roofline = {"bound": "alu", "kernel": "sweep_kernel (fused reconstruct + HLLD + flux difference)",
+                "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
+                "peak_source": "measured in this run: FP64 DFMA probe (mhd_probe_fp64), 2 flops per DFMA",
+                "algorithmic_flops_per_launch": sweep_flops / sweep_launches,
+                "avg_launch_ms": sweep_ms / sweep_launches, "traffic": None,
+                "step_achieved": step_achieved, "step_frac": step_achieved / peak,
+                "flops_per_cell_update": fm["per_cell_update"],
+                "kernel_ms_per_step": {k: v / prof_steps for k, v in kms.items()}}
+
+    # ---- end to end through the C-ABI with host buffers ----
+    sim.set_conserved(host)
+    sim.advance(1)
+    sim.get_conserved(out_host)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_steps = max(1, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_conserved(host)        # H2D of the step's input
+        sim.advance(1)
+        sim.get_conserved(out_host)    # D2H of the step's result (synchronous)
+    el = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([el], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        el = float(t.item())
+    e2e = {"value": ncell * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": h2d, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sgen, sdesc = SAMPLES[args.workload]
+        rate, steps, el = cpu_oracle_rate(sgen, seconds_budget=args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{sdesc}: {steps} steps in {el:.1f} s, single thread"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": desc, "grid": list(cfg["n"]), "cells": ncell,
+                           "l2": f"inputs larger than L2 (state {h2d / 1e9:.2f} GB)",
+                           "dt": "CFL dt computed on the device every step", "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def ctypes_stream(stream):
+    return stream.cuda_stream
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="turbulent3d-256", choices=list(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)   # timing rule: at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

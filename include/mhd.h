@@ -1,0 +1,155 @@
+/*
+ * libmhd — FP64 finite-volume ideal-MHD time step on one B300 (sm_103a).
+ *
+ * The method (paper §2 "Numerical methods"): the conservation law of
+ * Eq. cons_law with the ideal-MHD state and flux tensor of Eq. mhd and the
+ * total energy of Eq. Energy, advanced by the semi-discrete finite-volume
+ * update of Eq. FV with an SSP Runge-Kutta integrator (Eq. RK3, and the
+ * two-stage SSP-RK2).  Each stage recovers primitives (§2.2, the inversion
+ * below Eq. reconstruct), reconstructs interface states (Eq. reconstruct:
+ * PLM-minmod, WENO-Z or PPM), evaluates the Riemann flux of §2.2 (HLL or
+ * HLLD), and evolves the staggered face field by constrained transport with
+ * upwind (UCT) edge electric fields so that the discrete div B stays at
+ * round-off (§2.2, last paragraph before §3).
+ *
+ * Conventions for every entry point:
+ *   - returns 0 (MHD_OK) or a negative MHD_ERR_* code; nothing is thrown;
+ *   - the caller owns every pointer it passes; the library copies in and out
+ *     and never keeps a caller pointer after the call returns;
+ *   - all device work runs on the stream given in mhd_config.stream (NULL =
+ *     the legacy default stream); calls marked "async" return before the work
+ *     is done, calls marked "sync" wait for that stream.
+ *
+ * State layout at the boundary (no ghost zones, x fastest, float64):
+ *   cell arrays rho, mx, my, mz, E (and, in 2D, the cell-centred Bz):
+ *       [nz][ny][nx]                                   (2D: nz = 1)
+ *   face fields, stored at the left face of each cell (x0 + i dx, ...):
+ *       Bx [nz][ny][nx+1],  By [nz][ny+1][nx],  Bz [nz+1][ny][nx] (3D only).
+ *   On a periodic axis the last face equals the first: it is ignored on
+ *   input and written as a copy of the first on output.
+ */
+#ifndef MHD_H
+#define MHD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define MHD_OK              0
+#define MHD_ERR_ARG        -1   /* invalid argument or configuration */
+#define MHD_ERR_CUDA       -2   /* a CUDA runtime call failed */
+#define MHD_ERR_OOM        -3   /* device allocation failed */
+#define MHD_ERR_UNPHYSICAL -4   /* a non-positive (or non-finite) density or pressure met in a stage */
+#define MHD_ERR_TIMEOUT    -5   /* a bounded device-side wait gave up */
+#define MHD_ERR_STATE      -6   /* no state has been set on this context */
+
+/* ---- options ---- */
+#define MHD_RECON_PLM     0     /* piecewise linear, minmod limiter */
+#define MHD_RECON_WENOZ   1     /* fifth-order WENO-Z (Borges et al. 2008) */
+#define MHD_RECON_PPM     2     /* piecewise parabolic (Colella & Woodward 1984) */
+#define MHD_RIEMANN_HLL   0
+#define MHD_RIEMANN_HLLD  1     /* Miyoshi & Kusano 2005 */
+#define MHD_BC_PERIODIC   0
+#define MHD_BC_OUTFLOW    1     /* zero-gradient; normal ghost face field from div B = 0 */
+#define MHD_MEM_HOST      0
+#define MHD_MEM_DEVICE    1
+
+typedef struct {
+  int ndim;             /* 2 or 3 */
+  int nx, ny, nz;       /* interior cells per axis (nz ignored in 2D) */
+  double x0[3], x1[3];  /* domain bounds; dx = (x1 - x0) / n */
+  double gamma;         /* adiabatic index of the ideal equation of state (Eq. Energy) */
+  int recon;            /* MHD_RECON_* */
+  int riemann;          /* MHD_RIEMANN_* */
+  int rk;               /* 2 (SSP-RK2) or 3 (SSP-RK3, Eq. RK3) */
+  double cfl;           /* Courant number of mhd_cfl_dt / mhd_advance */
+  int bc[6];            /* x-, x+, y-, y+, z-, z+: MHD_BC_*; periodic needs both sides periodic */
+  double p_floor;       /* floor on the recovered pressure (0 = none): a recovered pressure below
+                           it is raised to it in the primitives only; the conserved energy is not
+                           changed (the paper is silent on floors; see mhd_counters) */
+  void* stream;         /* cudaStream_t for all device work; NULL = default stream */
+} mhd_config;
+
+typedef struct mhd_ctx mhd_ctx;   /* opaque; owns all device state of one grid */
+
+/* Create a context on the current CUDA device: validates cfg, allocates the
+ * device state (three RK registers, primitives, stage increment, face
+ * ingredients and edge fields; about 55 doubles per padded cell in 3D).
+ * *out receives the handle.  MHD_ERR_ARG on a bad configuration,
+ * MHD_ERR_OOM if the device allocation fails.  Sync. */
+int mhd_create(const mhd_config* cfg, mhd_ctx** out);
+
+/* Release every device allocation of ctx.  Sync.  ctx may be NULL. */
+int mhd_destroy(mhd_ctx* ctx);
+
+/* Set the conserved state.  U[0..4] = rho, mx, my, mz, E (cell arrays);
+ * B[0], B[1] = face Bx, By; B[2] = face Bz (3D) or cell Bz (2D); layout as in
+ * the file header.  mem = MHD_MEM_HOST or MHD_MEM_DEVICE says where the
+ * caller's arrays live (host arrays should be pinned for async copies).
+ * Resets the simulation time to 0.  Async. */
+int mhd_set_conserved(mhd_ctx* ctx, int mem, const double* const* U, const double* const* B);
+
+/* Set the state from primitives: rho, v[0..2], p (cell arrays) and the field
+ * B[0..2] as in mhd_set_conserved.  The conserved variables follow from
+ * m = rho v and Eq. Energy with the cell-centred field (mean of the two
+ * bounding faces; 2D Bz is the cell value).  Async. */
+int mhd_set_prim(mhd_ctx* ctx, int mem, const double* rho, const double* const* v, const double* p,
+                 const double* const* B);
+
+/* Copy the current conserved state out (same layout as mhd_set_conserved).
+ * Sync.  Returns the device status of the last steps (MHD_ERR_UNPHYSICAL if a
+ * non-positive density or pressure was met; see mhd_status). */
+int mhd_get_conserved(mhd_ctx* ctx, int mem, double* const* U, double* const* B);
+
+/* Change the boundary conditions (same encoding as mhd_config.bc).  Only
+ * changes between periodic and outflow that keep the ghost width are allowed. */
+int mhd_set_boundaries(mhd_ctx* ctx, const int bc[6]);
+
+/* CFL time step of the current state (reading of the paper, which is silent):
+ *   dt = cfl / max over interior cells of sum_d (|v_d| + cf_d) / dx_d,
+ * cf_d the fast magnetosonic speed along d with the cell-centred B_d.
+ * Computed on the device with IEEE operations in a fixed order.  Sync. */
+int mhd_cfl_dt(mhd_ctx* ctx, double* dt_out);
+
+/* Advance one time step of size dt (all RK stages).  Async; a non-positive
+ * density or pressure is reported by the next sync call. */
+int mhd_step(mhd_ctx* ctx, double dt);
+
+/* Advance nsteps steps, each with its own CFL dt computed on the device from
+ * the state at the start of that step (no host round trip).  The launch
+ * sequence of a step is captured once in a CUDA graph and replayed.  Async. */
+int mhd_advance(mhd_ctx* ctx, int nsteps);
+
+/* Simulation time (sum of the dt of all steps since the last set).  Sync. */
+int mhd_get_time(mhd_ctx* ctx, double* t_out);
+
+/* dt of the last step taken by mhd_advance (or given to mhd_step).  Sync. */
+int mhd_last_dt(mhd_ctx* ctx, double* dt_out);
+
+/* Wait for the context's stream and report the first device-side error of the
+ * steps since the last call: MHD_OK, or MHD_ERR_UNPHYSICAL with *bad_cell
+ * (may be NULL) = the smallest flat interior index k*ny*nx + j*nx + i of a
+ * cell whose recovered density or pressure was not positive.  Clears it. */
+int mhd_status(mhd_ctx* ctx, long long* bad_cell);
+
+/* Event counters since the last state set (sync):
+ *   *recon_fallbacks: cell reconstructions (per cell, direction and stage)
+ *     that fell back to first order because a reconstructed density or
+ *     pressure was not positive;
+ *   *pressure_floors: interior-cell primitive recoveries (per cell and
+ *     primitive pass) whose pressure was raised to p_floor.
+ * Either pointer may be NULL. */
+int mhd_counters(mhd_ctx* ctx, long long* recon_fallbacks, long long* pressure_floors);
+
+/* Number of kernel launches the library issued on this context so far
+ * (graph replays count the kernels inside the graph). */
+long long mhd_launch_count(const mhd_ctx* ctx);
+
+/* Static text for a return code. */
+const char* mhd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_H */

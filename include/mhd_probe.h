@@ -1,0 +1,45 @@
+/*
+ * libmhd measurement entry points (not part of the method).
+ *
+ * The paper reports wall-clock throughput only (cell-updates per second, §4);
+ * these calls give the per-kernel device times and the FP64 peak that the
+ * benchmark needs to place a kernel on its roofline.  Same conventions as
+ * mhd.h: int return codes, caller-owned pointers, work on the context stream.
+ */
+#ifndef MHD_PROBE_H
+#define MHD_PROBE_H
+
+#include "mhd.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* kernel classes of one time step */
+#define MHD_KCLASS_GHOST    0   /* ghost-zone fill */
+#define MHD_KCLASS_PRIM     1   /* primitive recovery (+ CFL reduction) */
+#define MHD_KCLASS_SWEEP_X  2   /* reconstruction + Riemann + flux difference, x */
+#define MHD_KCLASS_SWEEP_Y  3
+#define MHD_KCLASS_SWEEP_Z  4
+#define MHD_KCLASS_EMF      5   /* UCT edge fields */
+#define MHD_KCLASS_CT_RK    6   /* CT face update + RK combine */
+#define MHD_KCLASS_OTHER    7   /* step-size bookkeeping */
+#define MHD_NKCLASS         8
+
+/* Advance nsteps CFL steps exactly as mhd_advance does, but launching each
+ * kernel eagerly with a CUDA event recorded after it on the context stream.
+ * ms_out[MHD_NKCLASS] receives the summed device time per kernel class
+ * (milliseconds, event-to-event) and launches_out[MHD_NKCLASS] (may be NULL)
+ * the launch counts.  Sync. */
+int mhd_profile_steps(mhd_ctx* ctx, int nsteps, double* ms_out, int* launches_out);
+
+/* Measure the device's FP64 fused multiply-add throughput on the current
+ * device: every SM runs independent chains of dependent DFMA for about
+ * 20 ms; *gflops_out = 2 * DFMA per second / 1e9.  Sync; allocates and frees
+ * a small device buffer. */
+int mhd_probe_fp64(double* gflops_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_PROBE_H */

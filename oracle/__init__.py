@@ -28,7 +28,7 @@ class OrcConfig(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("x0", ctypes.c_double * 3), ("x1", ctypes.c_double * 3), ("gamma", ctypes.c_double),
                 ("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("rk", ctypes.c_int),
-                ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6)]
+                ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6), ("p_floor", ctypes.c_double)]
 
 
 _lib = None
@@ -54,6 +54,8 @@ def lib():
         L.orc_time.argtypes = [P]
         L.orc_fallbacks.restype = ctypes.c_longlong
         L.orc_fallbacks.argtypes = [P]
+        L.orc_floors.restype = ctypes.c_longlong
+        L.orc_floors.argtypes = [P]
         L.orc_status.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
         L.orc_get_emf.argtypes = [P, ctypes.c_int, DP]
         L.orc_stage_increment.argtypes = [P, D, ctypes.POINTER(DP)]
@@ -63,6 +65,8 @@ def lib():
         L.orc_c2p.argtypes = [DP, D, DP]
         L.orc_fast_speed.restype = D
         L.orc_fast_speed.argtypes = [D, D, D, D, D]
+        L.orc_cfl_dt_state.restype = D
+        L.orc_cfl_dt_state.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP)]
         L.orc_count_flops.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
                                       ctypes.POINTER(ctypes.c_ulonglong)]
         _lib = L
@@ -87,6 +91,7 @@ def make_config(cfg):
     c.cfl = cfg["cfl"]
     for s in range(6):
         c.bc[s] = BC[cfg["bc"][s]]
+    c.p_floor = cfg.get("p_floor", 0.0)
     return c
 
 
@@ -165,6 +170,10 @@ class OracleSim:
     def fallbacks(self):
         return lib().orc_fallbacks(self.h)
 
+    @property
+    def floors(self):
+        return lib().orc_floors(self.h)
+
     def emf(self, comp):
         nd = self.cfg["ndim"]
         n = list(self.cfg["n"]) + [1]
@@ -216,6 +225,14 @@ def c2p(u8, gamma):
 
 def fast_speed(rho, p, B2, bn, gamma):
     return lib().orc_fast_speed(rho, p, B2, bn, gamma)
+
+
+def cfl_dt_state(cfg, state):
+    """CFL dt of a state (external layout) without building the padded grid."""
+    c = make_config(cfg)
+    arrs = [np.ascontiguousarray(np.asarray(state[k], dtype=np.float64).reshape(s))
+            for k, s in zip(KEYS, state_shapes(cfg))]
+    return lib().orc_cfl_dt_state(ctypes.byref(c), _ptrs(arrs))
 
 
 def count_flops(cfg, state, nsteps, dt):

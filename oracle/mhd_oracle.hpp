@@ -51,6 +51,7 @@ struct Config {
   int recon, riemann, rk;
   double cfl;
   int bc[6];  // x-, x+, y-, y+, z-, z+
+  double p_floor;  // floor on the recovered pressure (0: none)
 };
 
 template <class R> inline R rmin(R a, R b) { return (b < a) ? b : a; }
@@ -365,6 +366,20 @@ template <class R> inline void recon_ppm(const R s[5], R& plus, R& minus) {
   minus = vm;
 }
 
+// CFL rate of one cell (reading; the paper is silent):
+//   sum over active d of (|v_d| + cf_d) / dx_d,
+// with cf_d the fast speed along d using the cell-centred field component B_d.
+template <class R> inline R cfl_rate(const R V[NP], const R idx[3], int ndim, double gamma) {
+  R B2 = (V[P_BX] * V[P_BX] + V[P_BY] * V[P_BY]) + V[P_BZ] * V[P_BZ];
+  R lam(0.0);
+  for (int d = 0; d < ndim; d++) {
+    R cf = fast_speed(V[P_RHO], V[P_PR], B2, V[P_BX + d], gamma);
+    R term = (fabs(V[P_VX + d]) + cf) * idx[d];
+    lam = d == 0 ? term : lam + term;
+  }
+  return lam;
+}
+
 // ---------------------------------------------------------------------------
 // The scheme on a grid.
 // ---------------------------------------------------------------------------
@@ -382,6 +397,7 @@ template <class R> struct Sim {
   Field<R> E[3];             // edge electric fields E_x, E_y, E_z
   R time = R(0.0);
   long long fallbacks = 0;   // cells where reconstruction fell back to first order
+  long long floors = 0;      // interior cells whose recovered pressure was raised to the floor
   int bad = 0;               // set when a non-positive density or pressure is met
   long long bad_cell = -1;
 
@@ -501,7 +517,7 @@ template <class R> struct Sim {
   }
 
   // ---- c2p on every cell that has both faces (all padded cells) ----
-  void compute_prims(State<R>& S) {
+  void compute_prims(State<R>& S, bool count_floors = true) {
     g_flops.phase = PH_C2P;
     for (int k = lo(2); k < (ndim == 3 ? hi(2) : 1); k++)
       for (int j = lo(1); j < hi(1); j++)
@@ -512,6 +528,13 @@ template <class R> struct Sim {
           R V[NP];
           cons_to_prim(S[Q_RHO](i, j, k), S[Q_MX](i, j, k), S[Q_MY](i, j, k), S[Q_MZ](i, j, k), S[Q_EN](i, j, k),
                        bx, by, bz, c.gamma, V);
+          // Pressure floor (reading; the paper is silent): the recovered
+          // pressure is raised to p_floor when below it; the conserved energy
+          // is left unchanged, so the update stays conservative.
+          if (V[P_PR] < R(c.p_floor)) {
+            V[P_PR] = R(c.p_floor);
+            if (count_floors && i >= 0 && i < n[0] && j >= 0 && j < n[1] && k >= 0 && k < n[2]) floors++;
+          }
           for (int q = 0; q < NP; q++) P[q](i, j, k) = V[q];
         }
   }
@@ -761,7 +784,7 @@ template <class R> struct Sim {
   // with cf_d the fast speed along d using the cell-centred field component B_d.
   R cfl_dt() {
     fill_ghosts(U0);
-    compute_prims(U0);
+    compute_prims(U0, false);  // floors are counted in the stages' passes only
     g_flops.phase = PH_CFL;
     R lmax(0.0);
     R idx[3];
@@ -769,15 +792,9 @@ template <class R> struct Sim {
     for (int k = 0; k < n[2]; k++)
       for (int j = 0; j < n[1]; j++)
         for (int i = 0; i < n[0]; i++) {
-          R rho = P[P_RHO](i, j, k), p = P[P_PR](i, j, k);
-          R bx = P[P_BX](i, j, k), by = P[P_BY](i, j, k), bz = P[P_BZ](i, j, k);
-          R B2 = (bx * bx + by * by) + bz * bz;
-          R lam(0.0);
-          for (int d = 0; d < ndim; d++) {
-            R cf = fast_speed(rho, p, B2, P[P_BX + d](i, j, k), c.gamma);
-            R term = (fabs(P[P_VX + d](i, j, k)) + cf) * idx[d];
-            lam = d == 0 ? term : lam + term;
-          }
+          R V[NP];
+          for (int q = 0; q < NP; q++) V[q] = P[q](i, j, k);
+          R lam = cfl_rate(V, idx, ndim, c.gamma);
           if (lmax < lam) lmax = lam;
         }
     return R(c.cfl) / lmax;

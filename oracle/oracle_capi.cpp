@@ -57,6 +57,7 @@ struct OrcConfig {
   int recon, riemann, rk;
   double cfl;
   int bc[6];
+  double p_floor;
 };
 
 static Config to_cfg(const OrcConfig* c) {
@@ -65,6 +66,7 @@ static Config to_cfg(const OrcConfig* c) {
   for (int d = 0; d < 3; d++) { o.x0[d] = c->x0[d]; o.x1[d] = c->x1[d]; }
   o.gamma = c->gamma; o.recon = c->recon; o.riemann = c->riemann; o.rk = c->rk; o.cfl = c->cfl;
   for (int s = 0; s < 6; s++) o.bc[s] = c->bc[s];
+  o.p_floor = c->p_floor;
   return o;
 }
 
@@ -93,6 +95,7 @@ int orc_step(void* h, double dt) {
 }
 double orc_time(void* h) { return static_cast<Sim<double>*>(h)->time; }
 long long orc_fallbacks(void* h) { return static_cast<Sim<double>*>(h)->fallbacks; }
+long long orc_floors(void* h) { return static_cast<Sim<double>*>(h)->floors; }
 int orc_status(void* h, long long* bad_cell) {
   auto* s = static_cast<Sim<double>*>(h);
   if (bad_cell) *bad_cell = s->bad_cell;
@@ -132,6 +135,45 @@ int orc_stage_increment(void* h, double dt, double* const* arrays) {
         }
   }
   return s->bad ? -4 : 0;
+}
+
+// CFL dt of a state given in the external layout, without building the padded
+// grid: the same cell-centred field, primitive recovery and per-cell rate as
+// Sim::cfl_dt, for grids too large for the full oracle.
+double orc_cfl_dt_state(const OrcConfig* cfg, const double* const* a) {
+  Config c = to_cfg(cfg);
+  int nd = c.ndim;
+  int n[3] = {c.nx, c.ny, nd == 3 ? c.nz : 1};
+  double idx[3];
+  for (int d = 0; d < 3; d++) {
+    double x0 = d < nd ? c.x0[d] : 0.0, x1 = d < nd ? c.x1[d] : 1.0;
+    double dx = (x1 - x0) / n[d];
+    idx[d] = 1.0 / dx;
+  }
+  long long sx1 = n[0] + 1, sy1 = n[1] + 1;
+  double lmax = 0.0;
+  for (int k = 0; k < n[2]; k++)
+    for (int j = 0; j < n[1]; j++)
+      for (int i = 0; i < n[0]; i++) {
+        long long cc = ((long long)k * n[1] + j) * n[0] + i;
+        double bx0 = a[5][((long long)k * n[1] + j) * sx1 + i], bx1 = a[5][((long long)k * n[1] + j) * sx1 + i + 1];
+        double by0 = a[6][((long long)k * sy1 + j) * n[0] + i], by1 = a[6][((long long)k * sy1 + j + 1) * n[0] + i];
+        double bx = 0.5 * (bx0 + bx1);
+        double by = 0.5 * (by0 + by1);
+        double bz;
+        if (nd == 3) {
+          double bz0 = a[7][cc], bz1 = a[7][cc + (long long)n[0] * n[1]];
+          bz = 0.5 * (bz0 + bz1);
+        } else {
+          bz = a[7][cc];
+        }
+        double V[NP];
+        cons_to_prim<double>(a[0][cc], a[1][cc], a[2][cc], a[3][cc], a[4][cc], bx, by, bz, c.gamma, V);
+        if (V[P_PR] < c.p_floor) V[P_PR] = c.p_floor;
+        double lam = cfl_rate<double>(V, idx, nd, c.gamma);
+        if (lmax < lam) lmax = lam;
+      }
+  return c.cfl / lmax;
 }
 
 // ---- pointwise pieces ----

@@ -1,0 +1,617 @@
+// C-ABI of libmhd (declared in include/mhd.h): context management, state
+// import/export and the orchestration of the RK stages of one time step.
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mhd.h"
+#include "mhd_kernels.cuh"
+#include "mhd_probe.h"
+
+using namespace mhd;
+
+struct mhd_ctx {
+  mhd_config cfg;
+  Grid g;
+  cudaStream_t stream;
+  bool own_stream;
+  size_t field_elems;  // padded elements per field (rounded up)
+  double* pool;        // every field lives in this one allocation
+  F8 U[3];             // RK registers (U[0] = U^n)
+  F8 P;                // primitives of the stage input
+  L6 L;                // stage increment of the cell variables
+  Ingr5x3 ING;         // UCT face ingredients
+  E3 E;                // edge fields
+  DevScalars* sc;
+  bool has_state;
+  int seglen;
+  long long launches;
+  int launches_per_step;
+  cudaGraphExec_t graph;
+  bool graph_ready;
+  // profiling: an event after every launch, tagged with its kernel class
+  bool prof_on;
+  int prof_n;
+  cudaEvent_t prof_ev[128];
+  int prof_cls[128];
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return MHD_OK;
+  if (e == cudaErrorMemoryAllocation) return MHD_ERR_OOM;
+  return MHD_ERR_CUDA;
+}
+#define CK(x)                         \
+  do {                                \
+    cudaError_t e_ = (x);             \
+    if (e_ != cudaSuccess) return cuda_err(e_); \
+  } while (0)
+
+void prof_mark(mhd_ctx* c, int cls) {
+  if (!c->prof_on || c->prof_n >= 128) return;
+  cudaEventRecord(c->prof_ev[c->prof_n], c->stream);
+  c->prof_cls[c->prof_n] = cls;
+  c->prof_n++;
+}
+
+int blocks_for(long long work, int threads, int cap = 148 * 32) {
+  long long b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+int validate(const mhd_config* c) {
+  if (!c) return MHD_ERR_ARG;
+  if (c->ndim != 2 && c->ndim != 3) return MHD_ERR_ARG;
+  if (c->nx < 1 || c->ny < 1 || (c->ndim == 3 && c->nz < 1)) return MHD_ERR_ARG;
+  for (int d = 0; d < c->ndim; d++)
+    if (!(c->x1[d] > c->x0[d])) return MHD_ERR_ARG;
+  if (!(c->gamma > 1.0)) return MHD_ERR_ARG;
+  if (c->recon < MHD_RECON_PLM || c->recon > MHD_RECON_PPM) return MHD_ERR_ARG;
+  if (c->riemann != MHD_RIEMANN_HLL && c->riemann != MHD_RIEMANN_HLLD) return MHD_ERR_ARG;
+  if (c->rk != 2 && c->rk != 3) return MHD_ERR_ARG;
+  if (!(c->cfl > 0.0)) return MHD_ERR_ARG;
+  if (!(c->p_floor >= 0.0)) return MHD_ERR_ARG;
+  for (int d = 0; d < c->ndim; d++) {
+    for (int s = 0; s < 2; s++)
+      if (c->bc[2 * d + s] != MHD_BC_PERIODIC && c->bc[2 * d + s] != MHD_BC_OUTFLOW) return MHD_ERR_ARG;
+    if ((c->bc[2 * d] == MHD_BC_PERIODIC) != (c->bc[2 * d + 1] == MHD_BC_PERIODIC)) return MHD_ERR_ARG;
+  }
+  return MHD_OK;
+}
+
+Grid make_grid(const mhd_config* c) {
+  Grid g{};
+  g.ndim = c->ndim;
+  g.n[0] = c->nx;
+  g.n[1] = c->ny;
+  g.n[2] = c->ndim == 3 ? c->nz : 1;
+  g.G = c->recon == MHD_RECON_PLM ? 2 : 3;
+  g.ext[0] = g.n[0] + 2 * g.G + 1;
+  g.ext[1] = g.n[1] + 2 * g.G + 1;
+  g.ext[2] = c->ndim == 3 ? g.n[2] + 2 * g.G + 1 : 1;
+  g.sy = g.ext[0];
+  g.sz = g.ext[0] * g.ext[1];
+  int Gz = c->ndim == 3 ? g.G : 0;
+  g.origin = Gz * g.sz + g.G * g.sy + g.G;
+  for (int d = 0; d < 3; d++) {
+    double x0 = d < c->ndim ? c->x0[d] : 0.0, x1 = d < c->ndim ? c->x1[d] : 1.0;
+    g.dx[d] = (x1 - x0) / g.n[d];
+    g.idx[d] = 1.0 / g.dx[d];
+    g.periodic[d] = d < c->ndim ? (c->bc[2 * d] == MHD_BC_PERIODIC) : 1;
+  }
+  g.gamma = c->gamma;
+  g.gm1 = c->gamma - 1.0;
+  g.igm1 = 1.0 / (c->gamma - 1.0);
+  g.cfl = c->cfl;
+  g.p_floor = c->p_floor;
+  return g;
+}
+
+// --- launch helpers ---
+void ghost_fill(mhd_ctx* c, const F8& S) {
+  const Grid& g = c->g;
+  for (int pass = 0; pass < 2; pass++)
+    for (int d = 0; d < g.ndim; d++) {
+      if ((pass == 0) != (g.periodic[d] != 0)) continue;
+      int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      long long rows = (long long)(g.hi(t1) - g.lo(t1) + 1) * (g.hi(t2) - g.lo(t2) + 1);
+      long long work = rows * (2 * g.G + 1);
+      if (g.periodic[d]) {
+        ghost_periodic_kernel<<<blocks_for(work, 256), 256, 0, c->stream>>>(g, S, d);
+        c->launches++;
+        prof_mark(c, MHD_KCLASS_GHOST);
+      } else {
+        ghost_outflow_copy_kernel<<<blocks_for(work, 256), 256, 0, c->stream>>>(g, S, d);
+        prof_mark(c, MHD_KCLASS_GHOST);
+        ghost_outflow_normal_kernel<<<blocks_for(rows, 128), 128, 0, c->stream>>>(g, S, d);
+        prof_mark(c, MHD_KCLASS_GHOST);
+        c->launches += 2;
+      }
+    }
+}
+
+void prim(mhd_ctx* c, const F8& S, bool cfl) {
+  const Grid& g = c->g;
+  long long work = (long long)(g.n[0] + 2 * g.G) * (g.n[1] + 2 * g.G) * (g.ndim == 3 ? g.n[2] + 2 * g.G : 1);
+  int nb = blocks_for(work, 256);
+  if (g.ndim == 2) {
+    if (cfl) prim_kernel<2, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc);
+    else prim_kernel<2, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc);
+  } else {
+    if (cfl) prim_kernel<3, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc);
+    else prim_kernel<3, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc);
+  }
+  c->launches++;
+  prof_mark(c, MHD_KCLASS_PRIM);
+}
+
+template <int DIR, int NDIM, int RECON, int RS>
+void sweep_one(mhd_ctx* c, const F8& S) {
+  const Grid& g = c->g;
+  constexpr int U = (DIR == 0) ? 1 : 0;
+  constexpr int V = (DIR == 0) ? 2 : (DIR == 1 ? 2 : 1);
+  long long eu = (U < NDIM) ? g.n[U] + 2 : 1, ev = (V < NDIM) ? g.n[V] + 2 : 1;
+  long long nseg = (g.n[DIR] + 1 + c->seglen - 1) / c->seglen;
+  long long threads = eu * ev * nseg;
+  int nb = (int)((threads + 127) / 128);
+  sweep_kernel<DIR, NDIM, RECON, RS><<<nb, 128, 0, c->stream>>>(g, c->P, S.q[5 + DIR], c->L, c->ING, c->sc,
+                                                                c->seglen, DIR > 0 ? 1 : 0);
+  c->launches++;
+  prof_mark(c, MHD_KCLASS_SWEEP_X + DIR);
+}
+
+template <int NDIM, int RECON, int RS>
+void sweeps_t(mhd_ctx* c, const F8& S) {
+  sweep_one<0, NDIM, RECON, RS>(c, S);
+  sweep_one<1, NDIM, RECON, RS>(c, S);
+  if (NDIM == 3) sweep_one<2, NDIM, RECON, RS>(c, S);
+}
+
+template <int NDIM>
+void sweeps_n(mhd_ctx* c, const F8& S) {
+  int r = c->cfg.recon, s = c->cfg.riemann;
+  if (r == MHD_RECON_PLM && s == MHD_RIEMANN_HLLD) sweeps_t<NDIM, RECON_PLM, RS_HLLD>(c, S);
+  else if (r == MHD_RECON_PLM) sweeps_t<NDIM, RECON_PLM, RS_HLL>(c, S);
+  else if (r == MHD_RECON_WENOZ && s == MHD_RIEMANN_HLLD) sweeps_t<NDIM, RECON_WENOZ, RS_HLLD>(c, S);
+  else if (r == MHD_RECON_WENOZ) sweeps_t<NDIM, RECON_WENOZ, RS_HLL>(c, S);
+  else if (s == MHD_RIEMANN_HLLD) sweeps_t<NDIM, RECON_PPM, RS_HLLD>(c, S);
+  else sweeps_t<NDIM, RECON_PPM, RS_HLL>(c, S);
+}
+
+void emf(mhd_ctx* c, const F8& S) {
+  const Grid& g = c->g;
+  long long work = (long long)(g.n[0] + 1) * (g.n[1] + 1) * (g.ndim == 3 ? g.n[2] + 1 : 1);
+  int nb = blocks_for(work, 256);
+  if (g.ndim == 2) emf_kernel<2><<<nb, 256, 0, c->stream>>>(g, S, c->ING, c->E);
+  else emf_kernel<3><<<nb, 256, 0, c->stream>>>(g, S, c->ING, c->E);
+  c->launches++;
+  prof_mark(c, MHD_KCLASS_EMF);
+}
+
+void ct_rk(mhd_ctx* c, const F8& U0, const F8& Us, const F8& Out, int mode) {
+  const Grid& g = c->g;
+  long long work = (long long)(g.n[0] + 1) * (g.n[1] + 1) * (g.ndim == 3 ? g.n[2] + 1 : 1);
+  int nb = blocks_for(work, 256);
+  if (g.ndim == 2) ct_rk_kernel<2><<<nb, 256, 0, c->stream>>>(g, U0, Us, Out, c->L, c->E, c->sc, mode);
+  else ct_rk_kernel<3><<<nb, 256, 0, c->stream>>>(g, U0, Us, Out, c->L, c->E, c->sc, mode);
+  c->launches++;
+  prof_mark(c, MHD_KCLASS_CT_RK);
+}
+
+// One RK stage s of the step; cfl = compute this step's dt in the primitive pass.
+void run_stage(mhd_ctx* c, int s, bool cfl) {
+  const int rk = c->cfg.rk;
+  const F8& U0 = c->U[0];
+  const F8& Us = s == 0 ? c->U[0] : (s == 1 ? c->U[1] : c->U[2]);
+  const F8& Out = s == 0 ? c->U[1] : ((rk == 2 || s == 2) ? c->U[0] : c->U[2]);
+  int mode = s == 0 ? COMB_FIRST : (rk == 2 ? COMB_RK2_FINAL : (s == 1 ? COMB_RK3_SECOND : COMB_RK3_FINAL));
+  ghost_fill(c, Us);
+  prim(c, Us, cfl);
+  if (c->g.ndim == 2) sweeps_n<2>(c, Us);
+  else sweeps_n<3>(c, Us);
+  emf(c, Us);
+  ct_rk(c, U0, Us, Out, mode);
+}
+
+void run_step(mhd_ctx* c, bool device_dt) {
+  for (int s = 0; s < c->cfg.rk; s++) run_stage(c, s, device_dt && s == 0);
+}
+
+void reset_scalars_host(DevScalars* h) {
+  memset(h, 0, sizeof(*h));
+  h->bad_cell = LLONG_MAX;
+}
+
+// cudaMemcpy3D between the caller's dense array (extents e[3]) and the
+// interior of a padded device field.
+int copy_field(mhd_ctx* c, double* field, const double* ext_ptr, double* ext_out, const int e[3], bool to_device) {
+  const Grid& g = c->g;
+  cudaMemcpy3DParms p{};
+  cudaPitchedPtr dense = make_cudaPitchedPtr(to_device ? (void*)ext_ptr : (void*)ext_out, (size_t)e[0] * 8, e[0], e[1]);
+  cudaPitchedPtr padded = make_cudaPitchedPtr((void*)field, (size_t)g.ext[0] * 8, g.ext[0], g.ext[1]);
+  int Gz = g.ndim == 3 ? g.G : 0;
+  if (to_device) {
+    p.srcPtr = dense;
+    p.dstPtr = padded;
+    p.dstPos = make_cudaPos((size_t)g.G * 8, g.G, Gz);
+  } else {
+    p.srcPtr = padded;
+    p.srcPos = make_cudaPos((size_t)g.G * 8, g.G, Gz);
+    p.dstPtr = dense;
+  }
+  p.extent = make_cudaExtent((size_t)e[0] * 8, e[1], e[2]);
+  p.kind = cudaMemcpyDefault;
+  CK(cudaMemcpy3DAsync(&p, c->stream));
+  return MHD_OK;
+}
+
+void slot_extents(const Grid& g, int slot, int e[3]) {
+  e[0] = g.n[0];
+  e[1] = g.n[1];
+  e[2] = g.n[2];
+  if (slot >= 5 && slot - 5 < g.ndim) e[slot - 5] += 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mhd_strerror(int code) {
+  switch (code) {
+    case MHD_OK: return "ok";
+    case MHD_ERR_ARG: return "invalid argument";
+    case MHD_ERR_CUDA: return "CUDA runtime error";
+    case MHD_ERR_OOM: return "device out of memory";
+    case MHD_ERR_UNPHYSICAL: return "non-positive density or pressure";
+    case MHD_ERR_TIMEOUT: return "device-side wait timed out";
+    case MHD_ERR_STATE: return "no state set";
+    default: return "unknown error";
+  }
+}
+
+int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
+  if (!out) return MHD_ERR_ARG;
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc) return rc;
+  Grid g = make_grid(cfg);
+  long long elems = (long long)g.ext[0] * g.ext[1] * g.ext[2];
+  if (elems > (long long)INT_MAX - 1) return MHD_ERR_ARG;
+  mhd_ctx* c = new (std::nothrow) mhd_ctx();
+  if (!c) return MHD_ERR_OOM;
+  c->cfg = *cfg;
+  c->g = g;
+  c->seglen = 16;
+  c->field_elems = (size_t)((elems + 31) / 32 * 32);
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+    c->own_stream = false;
+  } else {
+    // a blocking stream: ordered with the legacy default stream, and capturable
+    if (cudaStreamCreate(&c->stream) != cudaSuccess) { delete c; return MHD_ERR_CUDA; }
+    c->own_stream = true;
+  }
+  const int nfields = 3 * 8 + 8 + 6 + 15 + 3;
+  size_t bytes = c->field_elems * sizeof(double) * nfields;
+  if (cudaMalloc(&c->pool, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return MHD_ERR_OOM;
+  }
+  cudaMemsetAsync(c->pool, 0, bytes, c->stream);
+  double* p = c->pool;
+  auto next = [&]() { double* r = p; p += c->field_elems; return r; };
+  for (int r = 0; r < 3; r++)
+    for (int q = 0; q < 8; q++) c->U[r].q[q] = next();
+  for (int q = 0; q < 8; q++) c->P.q[q] = next();
+  for (int q = 0; q < 6; q++) c->L.q[q] = next();
+  for (int d = 0; d < 3; d++)
+    for (int q = 0; q < 5; q++) c->ING.a[d][q] = next();
+  for (int d = 0; d < 3; d++) c->E.e[d] = next();
+  if (cudaMalloc(&c->sc, sizeof(DevScalars)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->pool);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return MHD_ERR_OOM;
+  }
+  DevScalars h;
+  reset_scalars_host(&h);
+  cudaMemcpyAsync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    mhd_destroy(c);
+    return MHD_ERR_CUDA;
+  }
+  c->launches_per_step = -1;
+  *out = c;
+  return MHD_OK;
+}
+
+int mhd_destroy(mhd_ctx* c) {
+  if (!c) return MHD_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+  cudaFree(c->pool);
+  cudaFree(c->sc);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return MHD_OK;
+}
+
+static int set_common_faces(mhd_ctx* c, const double* const* B) {
+  for (int q = 5; q < 8; q++) {
+    int e[3];
+    slot_extents(c->g, q, e);
+    int rc = copy_field(c, c->U[0].q[q], B[q - 5], nullptr, e, true);
+    if (rc) return rc;
+  }
+  return MHD_OK;
+}
+
+static int reset_time(mhd_ctx* c) {
+  DevScalars h;
+  reset_scalars_host(&h);
+  CK(cudaMemcpyAsync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));  // h lives on this frame
+  return MHD_OK;
+}
+
+int mhd_set_conserved(mhd_ctx* c, int mem, const double* const* U, const double* const* B) {
+  if (!c || !U || !B || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE)) return MHD_ERR_ARG;
+  for (int q = 0; q < 5; q++)
+    if (!U[q]) return MHD_ERR_ARG;
+  for (int q = 0; q < 3; q++)
+    if (!B[q]) return MHD_ERR_ARG;
+  for (int q = 0; q < 5; q++) {
+    int e[3];
+    slot_extents(c->g, q, e);
+    int rc = copy_field(c, c->U[0].q[q], U[q], nullptr, e, true);
+    if (rc) return rc;
+  }
+  int rc = set_common_faces(c, B);
+  if (rc) return rc;
+  c->has_state = true;
+  return reset_time(c);
+}
+
+int mhd_set_prim(mhd_ctx* c, int mem, const double* rho, const double* const* v, const double* p,
+                 const double* const* B) {
+  if (!c || !rho || !v || !p || !B || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE)) return MHD_ERR_ARG;
+  const double* cells[5] = {rho, v[0], v[1], v[2], p};
+  for (int q = 0; q < 5; q++) {
+    if (!cells[q]) return MHD_ERR_ARG;
+    int e[3];
+    slot_extents(c->g, q, e);
+    int rc = copy_field(c, c->U[0].q[q], cells[q], nullptr, e, true);
+    if (rc) return rc;
+  }
+  int rc = set_common_faces(c, B);
+  if (rc) return rc;
+  long long work = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
+  if (c->g.ndim == 2) prim_to_cons_kernel<2><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->U[0]);
+  else prim_to_cons_kernel<3><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->U[0]);
+  c->launches++;
+  CK(cudaGetLastError());
+  c->has_state = true;
+  return reset_time(c);
+}
+
+int mhd_status(mhd_ctx* c, long long* bad_cell) {
+  if (!c) return MHD_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  DevScalars h;
+  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  if (bad_cell) *bad_cell = h.status ? h.bad_cell : -1;
+  if (h.status) {
+    int st = h.status;
+    h.status = 0;
+    h.bad_cell = LLONG_MAX;
+    CK(cudaMemcpy(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice));
+    return st;
+  }
+  return MHD_OK;
+}
+
+int mhd_get_conserved(mhd_ctx* c, int mem, double* const* U, double* const* B) {
+  if (!c || !U || !B || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE)) return MHD_ERR_ARG;
+  if (!c->has_state) return MHD_ERR_STATE;
+  ghost_fill(c, c->U[0]);
+  for (int q = 0; q < 8; q++) {
+    double* dst = q < 5 ? U[q] : B[q - 5];
+    if (!dst) return MHD_ERR_ARG;
+    int e[3];
+    slot_extents(c->g, q, e);
+    int rc = copy_field(c, c->U[0].q[q], nullptr, dst, e, false);
+    if (rc) return rc;
+  }
+  CK(cudaGetLastError());
+  return mhd_status(c, nullptr);
+}
+
+int mhd_set_boundaries(mhd_ctx* c, const int bc[6]) {
+  if (!c || !bc) return MHD_ERR_ARG;
+  mhd_config t = c->cfg;
+  for (int s = 0; s < 6; s++) t.bc[s] = bc[s];
+  int rc = validate(&t);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  c->cfg = t;
+  for (int d = 0; d < c->g.ndim; d++) c->g.periodic[d] = t.bc[2 * d] == MHD_BC_PERIODIC;
+  if (c->graph_ready) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph_ready = false;
+  }
+  return MHD_OK;
+}
+
+int mhd_cfl_dt(mhd_ctx* c, double* dt_out) {
+  if (!c || !dt_out) return MHD_ERR_ARG;
+  if (!c->has_state) return MHD_ERR_STATE;
+  // evaluate the rate without touching the accumulated time
+  DevScalars before;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(&before, c->sc, sizeof(before), cudaMemcpyDeviceToHost));
+  ghost_fill(c, c->U[0]);
+  prim(c, c->U[0], true);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  DevScalars after;
+  CK(cudaMemcpy(&after, c->sc, sizeof(after), cudaMemcpyDeviceToHost));
+  *dt_out = after.dt;
+  after.dt = before.dt;
+  after.time = before.time;
+  CK(cudaMemcpy(c->sc, &after, sizeof(after), cudaMemcpyHostToDevice));
+  return after.status ? after.status : MHD_OK;
+}
+
+int mhd_step(mhd_ctx* c, double dt) {
+  if (!c || !(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_ARG;
+  if (!c->has_state) return MHD_ERR_STATE;
+  set_dt_kernel<<<1, 1, 0, c->stream>>>(c->sc, dt);
+  c->launches++;
+  prof_mark(c, MHD_KCLASS_OTHER);
+  run_step(c, false);
+  CK(cudaGetLastError());
+  return MHD_OK;
+}
+
+int mhd_advance(mhd_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return MHD_ERR_ARG;
+  if (!c->has_state) return MHD_ERR_STATE;
+  if (nsteps == 0) return MHD_OK;
+  if (!c->graph_ready) {
+    long long before = c->launches;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    run_step(c, true);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (e != cudaSuccess) return cuda_err(e);
+    e = cudaGraphInstantiate(&c->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_err(e);
+    c->graph_ready = true;
+    c->launches_per_step = (int)(c->launches - before);
+    c->launches = before;
+  }
+  for (int s = 0; s < nsteps; s++) {
+    CK(cudaGraphLaunch(c->graph, c->stream));
+    c->launches += c->launches_per_step;
+  }
+  return MHD_OK;
+}
+
+int mhd_get_time(mhd_ctx* c, double* t_out) {
+  if (!c || !t_out) return MHD_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  DevScalars h;
+  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  *t_out = h.time;
+  return MHD_OK;
+}
+
+int mhd_last_dt(mhd_ctx* c, double* dt_out) {
+  if (!c || !dt_out) return MHD_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  DevScalars h;
+  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  *dt_out = h.dt;
+  return MHD_OK;
+}
+
+long long mhd_launch_count(const mhd_ctx* c) { return c ? c->launches : -1; }
+
+int mhd_counters(mhd_ctx* c, long long* recon_fallbacks, long long* pressure_floors) {
+  if (!c) return MHD_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  DevScalars h;
+  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  if (recon_fallbacks) *recon_fallbacks = (long long)h.fallbacks;
+  if (pressure_floors) *pressure_floors = (long long)h.floors;
+  return MHD_OK;
+}
+
+int mhd_profile_steps(mhd_ctx* c, int nsteps, double* ms_out, int* launches_out) {
+  if (!c || !ms_out || nsteps < 0) return MHD_ERR_ARG;
+  if (!c->has_state) return MHD_ERR_STATE;
+  for (int k = 0; k < MHD_NKCLASS; k++) {
+    ms_out[k] = 0.0;
+    if (launches_out) launches_out[k] = 0;
+  }
+  for (int i = 0; i < 128; i++) CK(cudaEventCreate(&c->prof_ev[i]));
+  int rc = MHD_OK;
+  for (int s = 0; s < nsteps && rc == MHD_OK; s++) {
+    c->prof_on = true;
+    c->prof_n = 0;
+    prof_mark(c, -1);
+    run_step(c, true);
+    c->prof_on = false;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { rc = cuda_err(e); break; }
+    for (int i = 1; i < c->prof_n; i++) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->prof_ev[i - 1], c->prof_ev[i]);
+      ms_out[c->prof_cls[i]] += ms;
+      if (launches_out) launches_out[c->prof_cls[i]]++;
+    }
+  }
+  for (int i = 0; i < 128; i++) cudaEventDestroy(c->prof_ev[i]);
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+// Independent chains of dependent DFMA per thread; the result is stored so the
+// chains are live.
+__global__ void fp64_probe_kernel(double* out, double a, double b, int iters) {
+  double c0 = threadIdx.x * 1e-3, c1 = c0 + 1, c2 = c0 + 2, c3 = c0 + 3, c4 = c0 + 4, c5 = c0 + 5, c6 = c0 + 6,
+         c7 = c0 + 7;
+  for (int i = 0; i < iters; i++) {
+    c0 = fma(c0, a, b); c1 = fma(c1, a, b); c2 = fma(c2, a, b); c3 = fma(c3, a, b);
+    c4 = fma(c4, a, b); c5 = fma(c5, a, b); c6 = fma(c6, a, b); c7 = fma(c7, a, b);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = ((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7));
+}
+}  // namespace
+
+extern "C" {
+
+int mhd_probe_fp64(double* gflops_out) {
+  if (!gflops_out) return MHD_ERR_ARG;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 256, blocks = sms * 8, iters = 2048;
+  double* buf = nullptr;
+  CK(cudaMalloc(&buf, sizeof(double) * threads * blocks));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 5; rep++) {
+    cudaEventRecord(e0, 0);
+    fp64_probe_kernel<<<blocks, threads>>>(buf, 1.0000001, 1e-7, iters);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_err(e);
+  double flops = 2.0 * 8.0 * iters * (double)threads * blocks;
+  *gflops_out = flops / (best * 1e-3) / 1e9;
+  return MHD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,531 @@
+// Kernels of one finite-volume CT stage of ideal MHD (paper §2.2) on the
+// padded device layout.
+//
+// Device layout: every field (8 state slots, 8 primitives, the stage
+// increment, 5 face ingredients per direction, 3 edge fields) is a separate
+// float64 array over the padded box i in [-G, nx+G], j in [-G, ny+G],
+// k in [-G, nz+G] (2D: k = 0 only), x fastest.  The extra outermost slot holds
+// the last face of face-centred arrays; index i of a face array is the face at
+// x0 + i dx (left face of cell i).  State slots: 0 rho, 1-3 m, 4 E, 5-7 the
+// face fields Bx, By, Bz (2D: slot 7 is the cell-centred Bz).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mhd_math.cuh"
+
+namespace mhd {
+
+enum { RECON_PLM = 0, RECON_WENOZ = 1, RECON_PPM = 2 };
+enum { RS_HLL = 0, RS_HLLD = 1 };
+
+struct Grid {
+  int ndim;
+  int n[3];        // interior cells (n[2] = 1 in 2D)
+  int G;           // ghost width on active axes
+  int ext[3];      // padded extents
+  int sy, sz;      // strides in elements
+  int origin;      // offset of cell (0,0,0)
+  int periodic[3];
+  double dx[3], idx[3];
+  double gamma, gm1, igm1, cfl, p_floor;
+  __host__ __device__ __forceinline__ int at(int i, int j, int k) const { return origin + i + j * sy + k * sz; }
+  __host__ __device__ __forceinline__ int stride(int d) const { return d == 0 ? 1 : (d == 1 ? sy : sz); }
+  __host__ __device__ __forceinline__ int lo(int d) const { return d < ndim ? -G : 0; }
+  __host__ __device__ __forceinline__ int hi(int d) const { return d < ndim ? n[d] + G : 0; }  // inclusive
+};
+
+struct F8 { double* q[8]; };
+struct Ingr5x3 { double* a[3][5]; };   // per direction: a+, a-, d, uL, uR at each face
+struct E3 { double* e[3]; };
+struct L6 { double* q[6]; };            // stage increment of rho, mx, my, mz, E (2D: + Bz)
+
+struct DevScalars {                     // small device-side scalars of one context
+  unsigned long long lmax_bits;         // max CFL rate of this step (as bits of a positive double)
+  unsigned int blocks_done;             // ticket counter of the CFL reduction
+  int status;                           // 0 or MHD_ERR_UNPHYSICAL
+  long long bad_cell;                   // smallest flat index of a bad cell
+  double dt;                            // current step
+  double time;                          // accumulated time
+  unsigned long long fallbacks;         // first-order reconstruction fallbacks
+  unsigned long long floors;            // interior pressures raised to the floor
+};
+
+// ---------------------------------------------------------------------------
+// Ghost zones.  Periodic axes first (x, y, z), then outflow axes (x, y, z);
+// each pass covers the full padded transverse range.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap(int g, int n) {
+  int r = g % n;
+  return r < 0 ? r + n : r;
+}
+
+// Periodic pass along axis d: every slot at d-index in [-G,-1] U [n, n+G].
+__global__ void ghost_periodic_kernel(Grid g, F8 S, int d) {
+  int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  int e1 = g.hi(t1) - g.lo(t1) + 1, e2 = g.hi(t2) - g.lo(t2) + 1;
+  int nl = 2 * g.G + 1;
+  long long total = (long long)e1 * e2 * nl;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int l = (int)(id % nl);
+    long long r = id / nl;
+    int a = (int)(r % e1) + g.lo(t1);
+    int b = (int)(r / e1) + g.lo(t2);
+    int gi = l < g.G ? l - g.G : g.n[d] + (l - g.G);
+    int x[3];
+    x[d] = gi;
+    x[t1] = a;
+    x[t2] = b;
+    int dst = g.at(x[0], x[1], x[2]);
+    x[d] = wrap(gi, g.n[d]);
+    int src = g.at(x[0], x[1], x[2]);
+#pragma unroll
+    for (int q = 0; q < 8; q++) S.q[q][dst] = S.q[q][src];
+  }
+}
+
+// Outflow pass along axis d, part 1: zero-gradient copies of every slot except
+// the normal face field (d-index -1..-G from 0; n..n+G from n-1).
+__global__ void ghost_outflow_copy_kernel(Grid g, F8 S, int d) {
+  int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  int e1 = g.hi(t1) - g.lo(t1) + 1, e2 = g.hi(t2) - g.lo(t2) + 1;
+  int nl = 2 * g.G + 1;
+  long long total = (long long)e1 * e2 * nl;
+  int qn = (d < g.ndim) ? 5 + d : -1;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int l = (int)(id % nl);
+    long long r = id / nl;
+    int a = (int)(r % e1) + g.lo(t1);
+    int b = (int)(r / e1) + g.lo(t2);
+    int gi = l < g.G ? l - g.G : g.n[d] + (l - g.G);
+    int x[3];
+    x[d] = gi;
+    x[t1] = a;
+    x[t2] = b;
+    int dst = g.at(x[0], x[1], x[2]);
+    x[d] = gi < 0 ? 0 : g.n[d] - 1;
+    int src = g.at(x[0], x[1], x[2]);
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+      if (q != qn) S.q[q][dst] = S.q[q][src];
+  }
+}
+
+// Outflow pass along axis d, part 2: the normal face field of each ghost cell
+// from a vanishing discrete div B, marching outward from the boundary face.
+__global__ void ghost_outflow_normal_kernel(Grid g, F8 S, int d) {
+  int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  int e1 = g.hi(t1) - g.lo(t1) + (t1 < g.ndim ? 0 : 1);  // transverse range [-G, n+G-1]
+  int e2 = g.hi(t2) - g.lo(t2) + (t2 < g.ndim ? 0 : 1);
+  long long total = (long long)e1 * e2;
+  double* Bn = S.q[5 + d];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int a = (int)(id % e1) + g.lo(t1);
+    int b = (int)(id / e1) + g.lo(t2);
+    auto divT = [&](int cell) {
+      int x[3];
+      x[d] = cell;
+      x[t1] = a;
+      x[t2] = b;
+      int c = g.at(x[0], x[1], x[2]);
+      double s = 0.0;
+      bool first = true;
+      int ts[2] = {t1, t2};
+      for (int m = 0; m < 2; m++) {
+        int t = ts[m];
+        if (t >= g.ndim) continue;
+        const double* Bt = S.q[5 + t];
+        double term = d_(s_(Bt[c + g.stride(t)], Bt[c]), g.dx[t]);
+        s = first ? term : a_(s, term);
+        first = false;
+      }
+      return s;
+    };
+    int x[3];
+    x[t1] = a;
+    x[t2] = b;
+    for (int m = 1; m <= g.G; m++) {
+      x[d] = -m;
+      int c = g.at(x[0], x[1], x[2]);
+      Bn[c] = a_(Bn[c + g.stride(d)], m_(g.dx[d], divT(-m)));
+    }
+    for (int m = 0; m < g.G; m++) {
+      int cell = g.n[d] + m;
+      x[d] = cell;
+      int c = g.at(x[0], x[1], x[2]);
+      Bn[c + g.stride(d)] = s_(Bn[c], m_(g.dx[d], divT(cell)));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Primitive recovery on every padded cell that has both faces; optional CFL
+// rate over interior cells reduced to a device dt (the last block to finish
+// forms dt = cfl / max rate and adds it to the time).  Also flags interior
+// cells with a non-positive (or NaN) density or pressure.
+// ---------------------------------------------------------------------------
+template <int NDIM, bool CFL>
+__global__ void __launch_bounds__(256) prim_kernel(Grid g, F8 S, F8 P, DevScalars* sc) {
+  const int nxp = g.n[0] + 2 * g.G, nyp = g.n[1] + 2 * g.G;
+  const int nzp = NDIM == 3 ? g.n[2] + 2 * g.G : 1;
+  const long long total = (long long)nxp * nyp * nzp;
+  double lam_max = 0.0;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(id % nxp) - g.G;
+    long long r = id / nxp;
+    int j = (int)(r % nyp) - g.G;
+    int k = NDIM == 3 ? (int)(r / nyp) - g.G : 0;
+    int c = g.at(i, j, k);
+    double bx = m_(0.5, a_(S.q[5][c], S.q[5][c + 1]));
+    double by = m_(0.5, a_(S.q[6][c], S.q[6][c + g.sy]));
+    double bz = NDIM == 3 ? m_(0.5, a_(S.q[7][c], S.q[7][c + g.sz])) : S.q[7][c];
+    Prim8 V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1);
+    bool interior = i >= 0 && i < g.n[0] && j >= 0 && j < g.n[1] && k >= 0 && k < g.n[2];
+    if (V.p < g.p_floor) {  // primitives only; the conserved energy is not changed
+      V.p = g.p_floor;
+      if (interior) atomicAdd(&sc->floors, 1ull);
+    }
+    P.q[0][c] = V.rho;
+    P.q[1][c] = V.vx;
+    P.q[2][c] = V.vy;
+    P.q[3][c] = V.vz;
+    P.q[4][c] = V.bx;
+    P.q[5][c] = V.by;
+    P.q[6][c] = V.bz;
+    P.q[7][c] = V.p;
+    if (interior) {
+      if (!(V.rho > 0.0) || !(V.p > 0.0)) {
+        long long flat = ((long long)k * g.n[1] + j) * g.n[0] + i;
+        atomicExch(&sc->status, -4);
+        atomicMin((unsigned long long*)&sc->bad_cell, (unsigned long long)flat);
+      }
+      if (CFL) {
+        double B2 = a_(a_(m_(V.bx, V.bx), m_(V.by, V.by)), m_(V.bz, V.bz));
+        double lam = m_(a_(fabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
+        lam = a_(lam, m_(a_(fabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
+        if (NDIM == 3) lam = a_(lam, m_(a_(fabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
+        lam_max = (lam > lam_max) ? lam : lam_max;
+      }
+    }
+  }
+  if (CFL) {
+    // rates are positive: their bit patterns order like unsigned integers
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lam_max = fmax(lam_max, __shfl_xor_sync(0xffffffffu, lam_max, o));
+    __shared__ double wmax[8];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wmax[wid] = lam_max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmax(m, wmax[w]);
+      atomicMax(&sc->lmax_bits, (unsigned long long)__double_as_longlong(m));
+      __threadfence();
+      unsigned int ticket = atomicAdd(&sc->blocks_done, 1u);
+      if (ticket == gridDim.x - 1) {
+        __threadfence();
+        double lmax = __longlong_as_double((long long)atomicAdd(&sc->lmax_bits, 0ull));
+        double dt = d_(g.cfl, lmax);
+        sc->dt = dt;
+        sc->time = sc->time + dt;
+        sc->lmax_bits = 0ull;
+        sc->blocks_done = 0u;
+      }
+    }
+  }
+}
+
+// Set the step size from the host value (mhd_step) and add it to the time.
+__global__ void set_dt_kernel(DevScalars* sc, double dt) {
+  sc->dt = dt;
+  sc->time = sc->time + dt;
+}
+
+// ---------------------------------------------------------------------------
+// Sweep along DIR: each thread marches a segment of faces of one pencil,
+// reconstructing each cell once, solving each face's Riemann problem once per
+// segment, writing the face's UCT ingredients and accumulating the flux
+// difference of Eq. FV into the stage increment of the cells it owns.
+// Pencils cover transverse indices [-1, n_t] on active axes (the outer layer
+// feeds the edge fields only).
+// ---------------------------------------------------------------------------
+template <int RECON> struct Stencil { static constexpr int R = RECON == RECON_PLM ? 1 : 2; };
+
+__device__ __forceinline__ void recon_cell(int recon, const double* s, double& plus, double& minus);
+
+template <int DIR, int NDIM, int RECON, int RS>
+__global__ void __launch_bounds__(128) sweep_kernel(Grid g, F8 P, const double* __restrict__ Bface, L6 L,
+                                                    Ingr5x3 ING, DevScalars* sc, int seglen, int accumulate) {
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  constexpr int R = Stencil<RECON>::R;
+  constexpr int W = 2 * R + 1;  // window of cells
+  // transverse ranges: fast index u, slow index w
+  constexpr int U = (DIR == 0) ? 1 : 0;           // x is the fast index unless sweeping x
+  constexpr int V = (DIR == 0) ? 2 : (DIR == 1 ? 2 : 1);
+  const int lu = (U < NDIM) ? -1 : 0, hu = (U < NDIM) ? g.n[U] : 0;
+  const int lv = (V < NDIM) ? -1 : 0, hv = (V < NDIM) ? g.n[V] : 0;
+  const int eu = hu - lu + 1, ev = hv - lv + 1;
+  const int nd = g.n[DIR];
+  const int nseg = (nd + 1 + seglen - 1) / seglen;
+  const long long total = (long long)eu * ev * nseg;
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= total) return;
+  const int iu = (int)(id % eu) + lu;
+  const long long r = id / eu;
+  const int iv = (int)(r % ev) + lv;
+  const int seg = (int)(r / ev);
+  int x[3];
+  x[DIR] = 0;
+  x[U] = iu;
+  x[V] = iv;
+  const bool row_interior = (U >= NDIM || (iu >= 0 && iu < g.n[U])) && (V >= NDIM || (iv >= 0 && iv < g.n[V]));
+  const int base = g.at(x[0], x[1], x[2]);
+  const int st = g.stride(DIR);
+  const int f0 = seg * seglen;
+  const int f1 = min(f0 + seglen, nd + 1);  // owned faces [f0, f1)
+  const int fend = min(f1, nd);             // last face computed
+  const double dt = sc->dt;
+  const double dtdx = dt * g.idx[DIR];
+  // primitive slots in sweep order: rho, v_n, v_t1, v_t2, B_t1, B_t2, p
+  const double* pr[7] = {P.q[0], P.q[1 + DIR], P.q[1 + T1], P.q[1 + T2], P.q[4 + T1], P.q[4 + T2], P.q[7]};
+  double win[7][W];
+  // load window centred on cell f0 - 1
+#pragma unroll
+  for (int m = 0; m < W; m++) {
+    int c = base + (f0 - 1 - R + m) * st;
+#pragma unroll
+    for (int v = 0; v < 7; v++) win[v][m] = pr[v][c];
+  }
+  auto reconstruct = [&](double plus[7], double minus[7], bool count) {
+#pragma unroll
+    for (int v = 0; v < 7; v++) {
+      if (RECON == RECON_PLM) recon_plm(win[v][0], win[v][1], win[v][2], plus[v], minus[v]);
+      else if (RECON == RECON_WENOZ) {
+        plus[v] = wenoz_face(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4]);
+        minus[v] = wenoz_face(win[v][4], win[v][3], win[v][2], win[v][1], win[v][0]);
+      } else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
+    }
+    // positivity fallback: first order in this cell
+    if (!(plus[0] > 0.0) || !(minus[0] > 0.0) || !(plus[6] > 0.0) || !(minus[6] > 0.0)) {
+#pragma unroll
+      for (int v = 0; v < 7; v++) plus[v] = minus[v] = win[v][R];
+      if (count) atomicAdd(&sc->fallbacks, 1ull);
+    }
+  };
+  double wl[7], wr[7], dummy[7];
+  // cells are counted once: cell -1 by the first segment, cell f by the
+  // segment that owns face f
+  reconstruct(wl, dummy, seg == 0);  // V^L at face f0 (plus state of cell f0-1)
+  double Fprev[7];
+  for (int f = f0; f <= fend; f++) {
+    // shift the window to be centred on cell f
+#pragma unroll
+    for (int v = 0; v < 7; v++) {
+#pragma unroll
+      for (int m = 0; m < W - 1; m++) win[v][m] = win[v][m + 1];
+    }
+    {
+      int c = base + (f + R) * st;
+#pragma unroll
+      for (int v = 0; v < 7; v++) win[v][W - 1] = pr[v][c];
+    }
+    double plusN[7];
+    reconstruct(plusN, wr, f < f1);  // cell f: V^L at f+1, V^R at f
+    W7 L7 = {wl[0], wl[1], wl[2], wl[3], wl[4], wl[5], wl[6]};
+    W7 R7 = {wr[0], wr[1], wr[2], wr[3], wr[4], wr[5], wr[6]};
+    int cf = base + f * st;
+    double bn = Bface[cf];
+    Flux7 F;
+    Ingr ing;
+    if (RS == RS_HLLD) riemann_hlld(L7, R7, bn, g.gamma, g.igm1, F, ing);
+    else riemann_hll(L7, R7, bn, g.gamma, g.igm1, F, ing);
+    if (f < f1) {
+      ING.a[DIR][0][cf] = ing.ap;
+      ING.a[DIR][1][cf] = ing.am;
+      ING.a[DIR][2][cf] = ing.dd;
+      ING.a[DIR][3][cf] = ing.uL;
+      ING.a[DIR][4][cf] = ing.uR;
+    }
+    if (f > f0 && row_interior) {
+      int cc = cf - st;  // cell f-1
+      double dv[6];
+      dv[0] = F.f[0] - Fprev[0];
+      double dm[3];
+      dm[DIR] = F.f[1] - Fprev[1];
+      dm[T1] = F.f[2] - Fprev[2];
+      dm[T2] = F.f[3] - Fprev[3];
+      dv[1] = dm[0];
+      dv[2] = dm[1];
+      dv[3] = dm[2];
+      dv[4] = F.f[6] - Fprev[6];
+      constexpr int NV = NDIM == 2 ? 6 : 5;
+      if (NDIM == 2) dv[5] = (DIR == 0) ? F.f[5] - Fprev[5] : F.f[4] - Fprev[4];
+#pragma unroll
+      for (int q = 0; q < NV; q++) {
+        double term = -(dtdx * dv[q]);
+        L.q[q][cc] = accumulate ? L.q[q][cc] + term : term;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 7; v++) {
+      Fprev[v] = F.f[v];
+      wl[v] = plusN[v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// UCT edge fields (reading of the UCT-HLL average):
+//   E_c = -(a+_a u^W B_b^W + a-_a u^E B_b^E) + d_a (B_b^E - B_b^W)
+//         + (a+_b u^S B_a^S + a-_b u^N B_a^N) - d_b (B_a^N - B_a^S)
+// with the a-face ingredients averaged over the two a-faces touching the edge
+// and minmod reconstructions of the face fields to the edge.
+// ---------------------------------------------------------------------------
+template <int C>
+__device__ __forceinline__ double uct_edge(const Grid& g, const F8& S, const Ingr5x3& ING, int c) {
+  constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+  const int sa = g.stride(A), sb = g.stride(B);
+  const int cb = c - sb, ca = c - sa;
+  const double* Ia[5] = {ING.a[A][0], ING.a[A][1], ING.a[A][2], ING.a[A][3], ING.a[A][4]};
+  const double* Ib[5] = {ING.a[B][0], ING.a[B][1], ING.a[B][2], ING.a[B][3], ING.a[B][4]};
+  double apa = 0.5 * (Ia[0][cb] + Ia[0][c]);
+  double ama = 0.5 * (Ia[1][cb] + Ia[1][c]);
+  double dda = 0.5 * (Ia[2][cb] + Ia[2][c]);
+  double uW = 0.5 * (Ia[3][cb] + Ia[3][c]);
+  double uE = 0.5 * (Ia[4][cb] + Ia[4][c]);
+  double apb = 0.5 * (Ib[0][ca] + Ib[0][c]);
+  double amb = 0.5 * (Ib[1][ca] + Ib[1][c]);
+  double ddb = 0.5 * (Ib[2][ca] + Ib[2][c]);
+  double vS = 0.5 * (Ib[3][ca] + Ib[3][c]);
+  double vN = 0.5 * (Ib[4][ca] + Ib[4][c]);
+  const double* Bb = S.q[5 + B];
+  const double* Ba = S.q[5 + A];
+  // B_b along a: values at a-cells -2, -1, 0, +1 relative to the edge
+  double bm2 = Bb[c - 2 * sa], bm1 = Bb[c - sa], b0 = Bb[c], bp1 = Bb[c + sa];
+  double BbW = bm1 + 0.5 * minmod(bm1 - bm2, b0 - bm1);
+  double BbE = b0 - 0.5 * minmod(b0 - bm1, bp1 - b0);
+  double am2 = Ba[c - 2 * sb], am1 = Ba[c - sb], a0 = Ba[c], ap1 = Ba[c + sb];
+  double BaS = am1 + 0.5 * minmod(am1 - am2, a0 - am1);
+  double BaN = a0 - 0.5 * minmod(a0 - am1, ap1 - a0);
+  double e = -fma(apa * uW, BbW, ama * uE * BbE) + dda * (BbE - BbW);
+  e += fma(apb * vS, BaS, amb * vN * BaN);
+  e -= ddb * (BaN - BaS);
+  return e;
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(256) emf_kernel(Grid g, F8 S, Ingr5x3 ING, E3 E) {
+  const int ex = g.n[0] + 1, ey = g.n[1] + 1, ez = NDIM == 3 ? g.n[2] + 1 : 1;
+  const long long total = (long long)ex * ey * ez;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(id % ex);
+    long long r = id / ex;
+    int j = (int)(r % ey);
+    int k = (int)(r / ey);
+    int c = g.at(i, j, k);
+    if (NDIM == 2) {
+      E.e[2][c] = uct_edge<2>(g, S, ING, c);
+    } else {
+      if (k < g.n[2]) E.e[2][c] = uct_edge<2>(g, S, ING, c);  // E_z at (x-face i, y-face j, cell k)
+      if (i < g.n[0]) E.e[0][c] = uct_edge<0>(g, S, ING, c);  // E_x at (cell i, y-face j, z-face k)
+      if (j < g.n[1]) E.e[1][c] = uct_edge<1>(g, S, ING, c);  // E_y at (x-face i, cell j, z-face k)
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CT face increment L_B = -dt curl E and the RK stage combine of every
+// evolved cell and face:  out = a0*U0 + a1*Us + aL*L  in the fixed forms
+//   stage "first":   Us + L
+//   RK2 final:       (U0 + Us + L) / 2
+//   RK3 second:      (3 U0 + Us + L) / 4
+//   RK3 final:       (U0 + 2 Us + 2 L) / 3
+// ---------------------------------------------------------------------------
+enum { COMB_FIRST = 0, COMB_RK2_FINAL = 1, COMB_RK3_SECOND = 2, COMB_RK3_FINAL = 3 };
+
+__device__ __forceinline__ double combine(int mode, double u0, double us, double l) {
+  switch (mode) {
+    case COMB_FIRST: return us + l;
+    case COMB_RK2_FINAL: return 0.5 * ((u0 + us) + l);
+    case COMB_RK3_SECOND: return 0.25 * (fma(3.0, u0, us) + l);
+    default: return (fma(2.0, us, u0) + 2.0 * l) * (1.0 / 3.0);
+  }
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(256) ct_rk_kernel(Grid g, F8 U0, F8 Us, F8 Out, L6 L, E3 E,
+                                                    const DevScalars* sc, int mode) {
+  const int ex = g.n[0] + 1, ey = g.n[1] + 1, ez = NDIM == 3 ? g.n[2] + 1 : 1;
+  const long long total = (long long)ex * ey * ez;
+  const double dt = sc->dt;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(id % ex);
+    long long r = id / ex;
+    int j = (int)(r % ey);
+    int k = (int)(r / ey);
+    int c = g.at(i, j, k);
+    const bool in_x = i < g.n[0], in_y = j < g.n[1], in_z = k < g.n[2];
+    if (in_x && in_y && in_z) {
+      constexpr int NV = NDIM == 2 ? 6 : 5;
+#pragma unroll
+      for (int q = 0; q < NV; q++) {
+        int slot = q < 5 ? q : 7;
+        Out.q[slot][c] = combine(mode, U0.q[slot][c], Us.q[slot][c], L.q[q][c]);
+      }
+    }
+    // faces with normal d: evolved for d-index < n_d, or == n_d on an outflow axis
+#pragma unroll
+    for (int d = 0; d < NDIM; d++) {
+      const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+      int idx3[3] = {i, j, k};
+      bool ok = true;
+#pragma unroll
+      for (int e = 0; e < NDIM; e++) {
+        if (e == d) ok = ok && (idx3[e] < g.n[e] || !g.periodic[e]);
+        else ok = ok && idx3[e] < g.n[e];
+      }
+      if (NDIM == 2) ok = ok && k == 0;
+      if (!ok) continue;
+      const bool has1 = d1 < NDIM, has2 = d2 < NDIM;
+      double t1 = 0.0, t2 = 0.0;
+      if (has1) t1 = (E.e[d2][c + g.stride(d1)] - E.e[d2][c]) * (dt * g.idx[d1]);
+      if (has2) t2 = (E.e[d1][c + g.stride(d2)] - E.e[d1][c]) * (dt * g.idx[d2]);
+      double lb = (has1 && has2) ? t2 - t1 : (has1 ? -t1 : t2);
+      Out.q[5 + d][c] = combine(mode, U0.q[5 + d][c], Us.q[5 + d][c], lb);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// State import / export helpers
+// ---------------------------------------------------------------------------
+// Primitive -> conserved in place on interior cells (slots 0..4 hold
+// rho, vx, vy, vz, p on entry); faces (and 2D cell Bz) already set.
+template <int NDIM>
+__global__ void prim_to_cons_kernel(Grid g, F8 S) {
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(id % g.n[0]);
+    long long r = id / g.n[0];
+    int j = (int)(r % g.n[1]);
+    int k = (int)(r / g.n[1]);
+    int c = g.at(i, j, k);
+    double bx = 0.5 * (S.q[5][c] + S.q[5][c + 1]);
+    double by = 0.5 * (S.q[6][c] + S.q[6][c + g.sy]);
+    double bz = NDIM == 3 ? 0.5 * (S.q[7][c] + S.q[7][c + g.sz]) : S.q[7][c];
+    double rho = S.q[0][c], vx = S.q[1][c], vy = S.q[2][c], vz = S.q[3][c], p = S.q[4][c];
+    S.q[1][c] = rho * vx;
+    S.q[2][c] = rho * vy;
+    S.q[3][c] = rho * vz;
+    S.q[4][c] = p * g.igm1 + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * (bx * bx + by * by + bz * bz);
+  }
+}
+
+}  // namespace mhd

@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libmhd (include/mhd.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library.  There is no fallback: if
+libmhd.so is missing or cannot be loaded, every call raises.
+
+State dictionaries use the library's external layout (see include/mhd.h):
+keys rho, mx, my, mz, E, b0, b1, b2 with b0/b1 the face fields Bx/By and b2
+the face Bz (3D) or the cell-centred Bz (2D).  Values may be numpy arrays
+(host memory) or CUDA torch tensors (device memory).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "libmhd.so")
+
+MHD_OK = 0
+ERRORS = {-1: "MHD_ERR_ARG", -2: "MHD_ERR_CUDA", -3: "MHD_ERR_OOM", -4: "MHD_ERR_UNPHYSICAL",
+          -5: "MHD_ERR_TIMEOUT", -6: "MHD_ERR_STATE"}
+RECON = {"plm": 0, "wenoz": 1, "ppm": 2}
+RIEMANN = {"hll": 0, "hlld": 1}
+BC = {"periodic": 0, "outflow": 1}
+MEM_HOST, MEM_DEVICE = 0, 1
+KEYS = ("rho", "mx", "my", "mz", "E", "b0", "b1", "b2")
+
+# every exported entry point of include/mhd.h
+EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mhd_get_conserved",
+           "mhd_set_boundaries", "mhd_cfl_dt", "mhd_step", "mhd_advance", "mhd_get_time", "mhd_last_dt",
+           "mhd_status", "mhd_launch_count", "mhd_strerror", "mhd_counters", "mhd_profile_steps", "mhd_probe_fp64")
+KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
+
+
+class MhdError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({lib().mhd_strerror(code).decode()})")
+        self.code = code
+
+
+class mhd_config(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x0", ctypes.c_double * 3), ("x1", ctypes.c_double * 3), ("gamma", ctypes.c_double),
+                ("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("rk", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6), ("p_floor", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmhd.so (built in-tree by paper_2511_20337_b300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(SO):
+            raise ImportError(f"libmhd.so not built ({SO}); run python -m paper_2511_20337_b300.build")
+        L = ctypes.CDLL(SO)
+        P = ctypes.c_void_p
+        DPP = ctypes.POINTER(ctypes.c_void_p)
+        I, D = ctypes.c_int, ctypes.c_double
+        sig = {
+            "mhd_create": (I, [ctypes.POINTER(mhd_config), ctypes.POINTER(P)]),
+            "mhd_destroy": (I, [P]),
+            "mhd_set_conserved": (I, [P, I, DPP, DPP]),
+            "mhd_set_prim": (I, [P, I, P, DPP, P, DPP]),
+            "mhd_get_conserved": (I, [P, I, DPP, DPP]),
+            "mhd_set_boundaries": (I, [P, ctypes.POINTER(I)]),
+            "mhd_cfl_dt": (I, [P, ctypes.POINTER(D)]),
+            "mhd_step": (I, [P, D]),
+            "mhd_advance": (I, [P, I]),
+            "mhd_get_time": (I, [P, ctypes.POINTER(D)]),
+            "mhd_last_dt": (I, [P, ctypes.POINTER(D)]),
+            "mhd_status": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "mhd_launch_count": (ctypes.c_longlong, [P]),
+            "mhd_counters": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+            "mhd_strerror": (ctypes.c_char_p, [I]),
+            "mhd_profile_steps": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
+            "mhd_probe_fp64": (I, [ctypes.POINTER(D)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != MHD_OK:
+        raise MhdError(rc, what)
+
+
+def make_config(cfg, stream=None):
+    c = mhd_config()
+    n = list(cfg["n"]) + [1] * (3 - len(cfg["n"]))
+    c.ndim = cfg["ndim"]
+    c.nx, c.ny = n[0], n[1]
+    c.nz = n[2] if cfg["ndim"] == 3 else 1
+    x0 = list(cfg["x0"]) + [0.0] * (3 - len(cfg["x0"]))
+    x1 = list(cfg["x1"]) + [1.0] * (3 - len(cfg["x1"]))
+    for d in range(3):
+        c.x0[d], c.x1[d] = x0[d], x1[d]
+    c.gamma = cfg["gamma"]
+    c.recon = RECON[cfg["recon"]]
+    c.riemann = RIEMANN[cfg["riemann"]]
+    c.rk = cfg["rk"]
+    c.cfl = cfg["cfl"]
+    for s in range(6):
+        c.bc[s] = BC[cfg["bc"][s]]
+    c.p_floor = cfg.get("p_floor", 0.0)
+    c.stream = stream
+    return c
+
+
+def state_shapes(cfg):
+    nd = cfg["ndim"]
+    nx, ny = cfg["n"][0], cfg["n"][1]
+    nz = cfg["n"][2] if nd == 3 else 1
+    cell = (nz, ny, nx)
+    faces = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx) if nd == 3 else (1, ny, nx)]
+    return [cell] * 5 + faces
+
+
+def _is_device(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _ptr(a):
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
+            raise ValueError("tensors must be contiguous float64")
+        return ctypes.c_void_p(a.data_ptr())
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise ValueError("arrays must be C-contiguous float64")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _ptr_array(arrs):
+    out = (ctypes.c_void_p * len(arrs))()
+    for i, a in enumerate(arrs):
+        out[i] = _ptr(a)
+    return out
+
+
+class Sim:
+    """One grid in device memory, advanced by libmhd on one GPU."""
+
+    def __init__(self, cfg, state=None, stream=None):
+        self.cfg = dict(cfg)
+        self.shapes = state_shapes(cfg)
+        self._c = make_config(cfg, stream)
+        h = ctypes.c_void_p()
+        _check(lib().mhd_create(ctypes.byref(self._c), ctypes.byref(h)), "mhd_create")
+        self.h = h
+        if state is not None:
+            self.set_conserved(state)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_conserved(self, state):
+        arrs = [state[k] for k in KEYS]
+        dev = _is_device(arrs[0])
+        if not dev:
+            arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(s)) for a, s in
+                    zip(arrs, self.shapes)]
+        self._keep = arrs
+        U = _ptr_array(arrs[:5])
+        B = _ptr_array(arrs[5:])
+        _check(lib().mhd_set_conserved(self.h, MEM_DEVICE if dev else MEM_HOST, U, B), "mhd_set_conserved")
+
+    def set_prim(self, rho, v, p, B):
+        dev = _is_device(rho)
+        arrs = [rho, *v, p, *B]
+        if not dev:
+            arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in arrs]
+        self._keep = arrs
+        _check(lib().mhd_set_prim(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr(arrs[0]), _ptr_array(arrs[1:4]),
+                                  _ptr(arrs[4]), _ptr_array(arrs[5:8])), "mhd_set_prim")
+
+    def get_conserved(self, out=None):
+        """Copy the state out: into `out` (dict of numpy arrays or CUDA tensors) or new numpy arrays."""
+        if out is None:
+            out = {k: np.zeros(s) for k, s in zip(KEYS, self.shapes)}
+        arrs = [out[k] for k in KEYS]
+        dev = _is_device(arrs[0])
+        _check(lib().mhd_get_conserved(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
+                                       _ptr_array(arrs[5:])), "mhd_get_conserved")
+        return out
+
+    def cfl_dt(self):
+        dt = ctypes.c_double()
+        _check(lib().mhd_cfl_dt(self.h, ctypes.byref(dt)), "mhd_cfl_dt")
+        return dt.value
+
+    def step(self, dt):
+        _check(lib().mhd_step(self.h, float(dt)), "mhd_step")
+
+    def advance(self, nsteps):
+        _check(lib().mhd_advance(self.h, int(nsteps)), "mhd_advance")
+
+    def status(self):
+        bad = ctypes.c_longlong()
+        rc = lib().mhd_status(self.h, ctypes.byref(bad))
+        return rc, bad.value
+
+    def set_boundaries(self, bc):
+        arr = (ctypes.c_int * 6)(*[BC[b] for b in bc])
+        _check(lib().mhd_set_boundaries(self.h, arr), "mhd_set_boundaries")
+
+    @property
+    def time(self):
+        t = ctypes.c_double()
+        _check(lib().mhd_get_time(self.h, ctypes.byref(t)), "mhd_get_time")
+        return t.value
+
+    @property
+    def last_dt(self):
+        t = ctypes.c_double()
+        _check(lib().mhd_last_dt(self.h, ctypes.byref(t)), "mhd_last_dt")
+        return t.value
+
+    def counters(self):
+        """(reconstruction fallbacks, pressure floors) since the last state set."""
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().mhd_counters(self.h, ctypes.byref(a), ctypes.byref(b)), "mhd_counters")
+        return a.value, b.value
+
+    @property
+    def launches(self):
+        return lib().mhd_launch_count(self.h)
+
+    def profile_steps(self, nsteps):
+        """Advance nsteps CFL steps with an event after each kernel: per-class
+        device milliseconds and launch counts."""
+        ms = (ctypes.c_double * len(KCLASSES))()
+        cnt = (ctypes.c_int * len(KCLASSES))()
+        _check(lib().mhd_profile_steps(self.h, int(nsteps), ms, cnt), "mhd_profile_steps")
+        return {k: ms[i] for i, k in enumerate(KCLASSES)}, {k: cnt[i] for i, k in enumerate(KCLASSES)}
+
+
+def probe_fp64_gflops():
+    """Measured FP64 FMA throughput of the current device (GFLOP/s, 2 per DFMA)."""
+    g = ctypes.c_double()
+    _check(lib().mhd_probe_fp64(ctypes.byref(g)), "mhd_probe_fp64")
+    return g.value
