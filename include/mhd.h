@@ -43,6 +43,7 @@ extern "C" {
 #define MHD_ERR_UNPHYSICAL -4   /* a non-positive (or non-finite) density or pressure met in a stage */
 #define MHD_ERR_TIMEOUT    -5   /* a bounded device-side wait gave up */
 #define MHD_ERR_STATE      -6   /* no state has been set on this context */
+#define MHD_ERR_TOO_LARGE  -7   /* grid needs more scratch than mhd_step_noalloc's fixed array */
 
 /* ---- options ---- */
 #define MHD_RECON_PLM     0     /* piecewise linear, minmod limiter */
@@ -148,6 +149,39 @@ long long mhd_launch_count(const mhd_ctx* ctx);
 
 /* Static text for a return code. */
 const char* mhd_strerror(int code);
+
+/* ---- allocation-free variant ----
+ *
+ * For callers that must not allocate device memory: for example code whose
+ * device memory is owned by another allocator or a fixed budget (a framework's
+ * caching pool, a pre-reserved arena), or code that may not block on the
+ * device-wide synchronisation that cudaMalloc and cudaFree can imply.  The
+ * paper has no counterpart; this is a property of the library only.
+ *
+ * mhd_step_noalloc advances the caller's state, held in device memory in the
+ * boundary layout of this file (U[0..4] cells, B[0..2] fields, as in
+ * mhd_set_conserved), by one step of size dt, in place.  It creates no
+ * context: every intermediate array (the padded RK registers, primitives,
+ * stage increment, face ingredients, edge fields and the device scalars)
+ * lives in one file-scope device array of MHD_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits.  The call allocates
+ * nothing (no cudaMalloc, no cudaFree, no allocating library routine).
+ *
+ * Limit: grids whose padded scratch (56 float64 fields over the padded box,
+ * (nx+2G+1)(ny+2G+1)(nz+2G+1) cells with G = 2 for PLM and 3 otherwise; 2D:
+ * no z padding) exceeds the array are rejected with MHD_ERR_TOO_LARGE before
+ * any device work (about 268 x 268 in 2D or 37^3 in 3D with PLM).
+ *
+ * The array is shared by every call and keeps the last call's contents: the
+ * call clears the part it uses before the step.  Calls that overlap on the GPU
+ * (from several host threads or streams at once) race on it and must not be
+ * made.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Work runs on cfg->stream (NULL = legacy default
+ * stream); the call waits for it and returns MHD_ERR_UNPHYSICAL if a
+ * non-positive density or pressure was met.  Sync. */
+#define MHD_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double* const* B, double dt);
 
 #ifdef __cplusplus
 }

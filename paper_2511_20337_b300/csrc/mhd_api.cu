@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "mhd.h"
@@ -271,6 +272,7 @@ const char* mhd_strerror(int code) {
     case MHD_ERR_UNPHYSICAL: return "non-positive density or pressure";
     case MHD_ERR_TIMEOUT: return "device-side wait timed out";
     case MHD_ERR_STATE: return "no state set";
+    case MHD_ERR_TOO_LARGE: return "grid exceeds the fixed scratch of mhd_step_noalloc";
     default: return "unknown error";
   }
 }
@@ -615,3 +617,102 @@ int mhd_probe_fp64(double* gflops_out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free single step.  All scratch lives in one file-scope device
+// array; host code reaches it only through the address cudaGetSymbolAddress
+// returns (the array's name is a host-side stand-in in host code).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocDoubles = MHD_NOALLOC_SCRATCH_BYTES / sizeof(double);
+constexpr int kNoAllocFields = 3 * 8 + 8 + 6 + 15 + 3;  // same carve-up as mhd_create
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kMaxDevices] = {};  // device address of the array, per device
+
+// Once per device, with that device current: look up the array's device address.
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return MHD_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    double* p = nullptr;
+    CK(cudaGetSymbolAddress((void**)&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double* const* B, double dt) {
+  int rc = validate(cfg);
+  if (rc) return rc;
+  if (!U || !B || !(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_ARG;
+  for (int q = 0; q < 5; q++)
+    if (!U[q]) return MHD_ERR_ARG;
+  for (int q = 0; q < 3; q++)
+    if (!B[q]) return MHD_ERR_ARG;
+  Grid g = make_grid(cfg);
+  long long elems = (long long)g.ext[0] * g.ext[1] * g.ext[2];
+  long long field = (elems + 31) / 32 * 32;  // 256-byte aligned fields
+  long long sc_doubles = (long long)((sizeof(DevScalars) + 255) / 256 * 256 / sizeof(double));
+  long long need = field * kNoAllocFields + sc_doubles;
+  if (need > (long long)kNoAllocDoubles) return MHD_ERR_TOO_LARGE;
+  double* base = nullptr;
+  rc = noalloc_scratch(&base);
+  if (rc) return rc;
+
+  // a context on the stack whose arrays are carved out of the static scratch
+  mhd_ctx c{};
+  c.cfg = *cfg;
+  c.g = g;
+  c.stream = (cudaStream_t)cfg->stream;
+  c.own_stream = false;
+  c.field_elems = (size_t)field;
+  c.pool = base;
+  c.seglen = 16;
+  double* p = base;
+  auto next = [&]() { double* r = p; p += field; return r; };
+  for (int r = 0; r < 3; r++)
+    for (int q = 0; q < 8; q++) c.U[r].q[q] = next();
+  for (int q = 0; q < 8; q++) c.P.q[q] = next();
+  for (int q = 0; q < 6; q++) c.L.q[q] = next();
+  for (int d = 0; d < 3; d++)
+    for (int q = 0; q < 5; q++) c.ING.a[d][q] = next();
+  for (int d = 0; d < 3; d++) c.E.e[d] = next();
+  c.sc = reinterpret_cast<DevScalars*>(p);
+  c.has_state = true;
+
+  // the array keeps the previous call's contents: clear what this call uses,
+  // then set the device scalars (bad_cell starts at the largest index)
+  CK(cudaMemsetAsync(base, 0, (size_t)need * sizeof(double), c.stream));
+  DevScalars h;
+  reset_scalars_host(&h);
+  CK(cudaMemcpyAsync(c.sc, &h, sizeof(h), cudaMemcpyHostToDevice, c.stream));
+  for (int q = 0; q < 8; q++) {
+    int e[3];
+    slot_extents(g, q, e);
+    rc = copy_field(&c, c.U[0].q[q], q < 5 ? U[q] : B[q - 5], nullptr, e, true);
+    if (rc) return rc;
+  }
+  set_dt_kernel<<<1, 1, 0, c.stream>>>(c.sc, dt);
+  run_step(&c, false);
+  ghost_fill(&c, c.U[0]);  // the duplicate last face of periodic axes
+  for (int q = 0; q < 8; q++) {
+    int e[3];
+    slot_extents(g, q, e);
+    rc = copy_field(&c, c.U[0].q[q], nullptr, q < 5 ? U[q] : B[q - 5], e, false);
+    if (rc) return rc;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c.stream));
+  CK(cudaMemcpy(&h, c.sc, sizeof(h), cudaMemcpyDeviceToHost));
+  return h.status ? h.status : MHD_OK;
+}

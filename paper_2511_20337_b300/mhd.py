@@ -18,7 +18,7 @@ SO = os.path.join(HERE, "libmhd.so")
 
 MHD_OK = 0
 ERRORS = {-1: "MHD_ERR_ARG", -2: "MHD_ERR_CUDA", -3: "MHD_ERR_OOM", -4: "MHD_ERR_UNPHYSICAL",
-          -5: "MHD_ERR_TIMEOUT", -6: "MHD_ERR_STATE"}
+          -5: "MHD_ERR_TIMEOUT", -6: "MHD_ERR_STATE", -7: "MHD_ERR_TOO_LARGE"}
 RECON = {"plm": 0, "wenoz": 1, "ppm": 2}
 RIEMANN = {"hll": 0, "hlld": 1}
 BC = {"periodic": 0, "outflow": 1}
@@ -28,7 +28,8 @@ KEYS = ("rho", "mx", "my", "mz", "E", "b0", "b1", "b2")
 # every exported entry point of include/mhd.h
 EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mhd_get_conserved",
            "mhd_set_boundaries", "mhd_cfl_dt", "mhd_step", "mhd_advance", "mhd_get_time", "mhd_last_dt",
-           "mhd_status", "mhd_launch_count", "mhd_strerror", "mhd_counters", "mhd_profile_steps", "mhd_probe_fp64")
+           "mhd_status", "mhd_launch_count", "mhd_strerror", "mhd_counters", "mhd_profile_steps", "mhd_probe_fp64",
+           "mhd_step_noalloc")
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 
 
@@ -77,6 +78,7 @@ def lib():
             "mhd_strerror": (ctypes.c_char_p, [I]),
             "mhd_profile_steps": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
             "mhd_probe_fp64": (I, [ctypes.POINTER(D)]),
+            "mhd_step_noalloc": (I, [ctypes.POINTER(mhd_config), DPP, DPP, D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -253,3 +255,16 @@ def probe_fp64_gflops():
     g = ctypes.c_double()
     _check(lib().mhd_probe_fp64(ctypes.byref(g)), "mhd_probe_fp64")
     return g.value
+
+
+def step_noalloc(cfg, state, dt, stream=None):
+    """One step of size dt, in place, on a state held in CUDA tensors (dict with
+    the keys of KEYS), through the allocation-free entry point mhd_step_noalloc:
+    no context and no device allocation; the library's fixed scratch array is
+    used instead (grids beyond it raise MhdError with MHD_ERR_TOO_LARGE)."""
+    arrs = [state[k] for k in KEYS]
+    if not all(_is_device(a) for a in arrs):
+        raise ValueError("mhd_step_noalloc works on device memory: pass CUDA tensors")
+    c = make_config(cfg, stream)
+    _check(lib().mhd_step_noalloc(ctypes.byref(c), _ptr_array(arrs[:5]), _ptr_array(arrs[5:]), float(dt)),
+           "mhd_step_noalloc")
