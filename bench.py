@@ -15,6 +15,8 @@ cell-updates / max rank time.
 sample of the same workload (a smaller grid of the same kind), same metric.
 """
 import argparse
+import glob
+import hashlib
 import json
 import math
 import os
@@ -44,6 +46,8 @@ WORKLOADS = {
     "blast3d-512": (lambda: W.blast_3d(512), "blast3d_wenoz_hlld_rk3",
                     "3D magnetised blast 512^3 outflow, rho=1, p=0.1 / 10 (r<=0.1), B=10/sqrt2 (1,1,0); "
                     "WENO-Z + HLLD + SSP-RK3 + UCT-HLL CT, CFL 0.4"),
+    "blast3d-128": (lambda: W.blast_3d(128), "blast3d_wenoz_hlld_rk3",
+                    "3D magnetised blast 128^3 (profiling size), same setup and scheme as blast3d-512"),
     "blast3d-512-ppm": (lambda: W.blast_3d(512, recon="ppm"), "blast3d_ppm_hlld_rk3",
                         "3D magnetised blast 512^3 outflow; PPM + HLLD + SSP-RK3 + UCT-HLL CT, CFL 0.4"),
     "orszag-tang2d-128": (lambda: W.orszag_tang_2d(128), "orszag_tang2d_plm_hlld_rk2",
@@ -54,6 +58,7 @@ SAMPLES = {
     "turbulent3d-256": (lambda: W.turbulent_3d(48), "turbulent 3D 48^3 (same scheme and field recipe)"),
     "turbulent3d-128": (lambda: W.turbulent_3d(48), "turbulent 3D 48^3 (same scheme and field recipe)"),
     "blast3d-512": (lambda: W.blast_3d(32), "blast 3D 32^3 (same scheme and setup)"),
+    "blast3d-128": (lambda: W.blast_3d(32), "blast 3D 32^3 (same scheme and setup)"),
     "blast3d-512-ppm": (lambda: W.blast_3d(32, recon="ppm"), "blast 3D 32^3 PPM (same scheme and setup)"),
     "orszag-tang2d-128": (lambda: W.orszag_tang_2d(128), "Orszag-Tang 2D 128^2 (the workload itself)"),
 }
@@ -99,6 +104,23 @@ def flop_model(cfg, variant):
              + per["rk"] * elems)
     step = rk * stage + per["cfl"] * cells
     return {"sweep_per_launch": sweep, "step": step, "per_cell_update": step / cells}
+
+
+def sweep_traffic(variant, faces_per_launch):
+    """DRAM bytes per sweep launch from the committed ncu captures
+    (profiles/sweep_traffic.json), scaled by faces per launch; None when the
+    kernel sources changed since the capture or no capture exists."""
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = sorted(glob.glob(os.path.join(ROOT, "paper_2511_20337_b300", "csrc", "*")))
+    h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
+    if rec.get("source_hash") != h or variant not in rec:
+        return None
+    v = rec[variant]
+    per = sum(v["bytes_per_launch"]) / len(v["bytes_per_launch"])
+    return per * faces_per_launch / v["faces_per_launch"]
 
 
 # ---------------------------------------------------------------------------
@@ -267,11 +289,16 @@ def run_ours(args):
     achieved = sweep_flops / (sweep_ms * 1e-3) / 1e9
     step_ms_prof = sum(kms.values()) / prof_steps
     step_achieved = fm["step"] / (step_ms_prof * 1e-3) / 1e9
+    n = list(cfg["n"][:nd])
+    faces_per_launch = sum((n[d] + 1) * int(np.prod([n[t] + 2 for t in range(nd) if t != d])) for d in range(nd)) / nd
     roofline = {"bound": "alu", "kernel": "sweep_kernel (fused reconstruct + HLLD + flux difference)",
                 "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
                 "peak_source": "measured in this run: FP64 DFMA probe (mhd_probe_fp64), 2 flops per DFMA",
                 "algorithmic_flops_per_launch": sweep_flops / sweep_launches,
-                "avg_launch_ms": sweep_ms / sweep_launches, "traffic": None,
+                "avg_launch_ms": sweep_ms / sweep_launches,
+                "traffic": sweep_traffic(variant, faces_per_launch),
+                "traffic_note": "DRAM bytes per sweep launch (mean of the directions) from the ncu capture in "
+                                "profiles/, scaled to this grid by faces; null if the kernels changed since",
                 "step_achieved": step_achieved, "step_frac": step_achieved / peak,
                 "flops_per_cell_update": fm["per_cell_update"],
                 "kernel_ms_per_step": {k: v / prof_steps for k, v in kms.items()}}

@@ -304,13 +304,11 @@ __global__ void __launch_bounds__(128) sweep_kernel(Grid g, F8 P, const double* 
 #pragma unroll
     for (int v = 0; v < 7; v++) {
       if (RECON == RECON_PLM) recon_plm(win[v][0], win[v][1], win[v][2], plus[v], minus[v]);
-      else if (RECON == RECON_WENOZ) {
-        plus[v] = wenoz_face(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4]);
-        minus[v] = wenoz_face(win[v][4], win[v][3], win[v][2], win[v][1], win[v][0]);
-      } else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
+      else if (RECON == RECON_WENOZ) recon_wenoz(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
+      else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
     }
     // positivity fallback: first order in this cell
-    if (!(plus[0] > 0.0) || !(minus[0] > 0.0) || !(plus[6] > 0.0) || !(minus[6] > 0.0)) {
+    if (!gt0(plus[0]) || !gt0(minus[0]) || !gt0(plus[6]) || !gt0(minus[6])) {
 #pragma unroll
       for (int v = 0; v < 7; v++) plus[v] = minus[v] = win[v][R];
       if (count) atomicAdd(&sc->fallbacks, 1ull);
@@ -385,6 +383,8 @@ __global__ void __launch_bounds__(128) sweep_kernel(Grid g, F8 P, const double* 
 // with the a-face ingredients averaged over the two a-faces touching the edge
 // and minmod reconstructions of the face fields to the edge.
 // ---------------------------------------------------------------------------
+// The averages of two face values carry a factor 1/2 each; it is folded into
+// the sums as exact power-of-two scalings: a+ u^W = (1/4)(a1 + a2)(u1 + u2).
 template <int C>
 __device__ __forceinline__ double uct_edge(const Grid& g, const F8& S, const Ingr5x3& ING, int c) {
   constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
@@ -392,29 +392,26 @@ __device__ __forceinline__ double uct_edge(const Grid& g, const F8& S, const Ing
   const int cb = c - sb, ca = c - sa;
   const double* Ia[5] = {ING.a[A][0], ING.a[A][1], ING.a[A][2], ING.a[A][3], ING.a[A][4]};
   const double* Ib[5] = {ING.a[B][0], ING.a[B][1], ING.a[B][2], ING.a[B][3], ING.a[B][4]};
-  double apa = 0.5 * (Ia[0][cb] + Ia[0][c]);
-  double ama = 0.5 * (Ia[1][cb] + Ia[1][c]);
-  double dda = 0.5 * (Ia[2][cb] + Ia[2][c]);
-  double uW = 0.5 * (Ia[3][cb] + Ia[3][c]);
-  double uE = 0.5 * (Ia[4][cb] + Ia[4][c]);
-  double apb = 0.5 * (Ib[0][ca] + Ib[0][c]);
-  double amb = 0.5 * (Ib[1][ca] + Ib[1][c]);
-  double ddb = 0.5 * (Ib[2][ca] + Ib[2][c]);
-  double vS = 0.5 * (Ib[3][ca] + Ib[3][c]);
-  double vN = 0.5 * (Ib[4][ca] + Ib[4][c]);
+  // sums over the two a-faces (b-faces) touching the edge
+  double apa = Ia[0][cb] + Ia[0][c], ama = Ia[1][cb] + Ia[1][c], dda = Ia[2][cb] + Ia[2][c];
+  double uW = Ia[3][cb] + Ia[3][c], uE = Ia[4][cb] + Ia[4][c];
+  double apb = Ib[0][ca] + Ib[0][c], amb = Ib[1][ca] + Ib[1][c], ddb = Ib[2][ca] + Ib[2][c];
+  double vS = Ib[3][ca] + Ib[3][c], vN = Ib[4][ca] + Ib[4][c];
   const double* Bb = S.q[5 + B];
   const double* Ba = S.q[5 + A];
   // B_b along a: values at a-cells -2, -1, 0, +1 relative to the edge
   double bm2 = Bb[c - 2 * sa], bm1 = Bb[c - sa], b0 = Bb[c], bp1 = Bb[c + sa];
-  double BbW = bm1 + 0.5 * minmod(bm1 - bm2, b0 - bm1);
-  double BbE = b0 - 0.5 * minmod(b0 - bm1, bp1 - b0);
+  double dbm = bm1 - bm2, db0 = b0 - bm1, dbp = bp1 - b0;
+  double BbW = fma(0.5, minmod(dbm, db0), bm1);
+  double BbE = fma(-0.5, minmod(db0, dbp), b0);
   double am2 = Ba[c - 2 * sb], am1 = Ba[c - sb], a0 = Ba[c], ap1 = Ba[c + sb];
-  double BaS = am1 + 0.5 * minmod(am1 - am2, a0 - am1);
-  double BaN = a0 - 0.5 * minmod(a0 - am1, ap1 - a0);
-  double e = -fma(apa * uW, BbW, ama * uE * BbE) + dda * (BbE - BbW);
-  e += fma(apb * vS, BaS, amb * vN * BaN);
-  e -= ddb * (BaN - BaS);
-  return e;
+  double dam = am1 - am2, da0 = a0 - am1, dap = ap1 - a0;
+  double BaS = fma(0.5, minmod(dam, da0), am1);
+  double BaN = fma(-0.5, minmod(da0, dap), a0);
+  // 4 E = -(A+a uW BbW + A-a uE BbE) + (A+b vS BaS + A-b vN BaN) + 2 (Da (BbE-BbW) - Db (BaN-BaS))
+  double up = fma(apb * vS, BaS, (amb * vN) * BaN) - fma(apa * uW, BbW, (ama * uE) * BbE);
+  double diss = fma(dda, BbE - BbW, -ddb * (BaN - BaS));
+  return fma(0.25, up, 0.5 * diss);
 }
 
 template <int NDIM>

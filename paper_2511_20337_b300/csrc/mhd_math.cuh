@@ -84,6 +84,61 @@ __device__ __forceinline__ double fast_speed_ieee(double rho, double p, double B
 }
 
 // ---------------------------------------------------------------------------
+// Predicates, min/max and sign changes on the integer pipes.  On this GPU the
+// FP64 pipe is the bottleneck and a double compare (DSETP) costs as much of it
+// as a fused multiply-add, so comparisons, selections and sign flips use the
+// bit patterns: a non-negative double orders like its bits as a signed
+// integer, and key(x) = bits ^ ((bits >> 63) & 0x7fff...) orders every
+// non-NaN double like a signed integer.
+// ---------------------------------------------------------------------------
+constexpr long long kSign = (long long)0x8000000000000000ULL;
+constexpr long long kMag = 0x7fffffffffffffffLL;
+
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double from_bits(long long b) { return __longlong_as_double(b); }
+__device__ __forceinline__ long long order_key(double x) {
+  long long b = bits(x);
+  return b ^ ((b >> 63) & kMag);
+}
+__device__ __forceinline__ bool gt0(double x) { return bits(x) > 0; }                     // x > 0
+__device__ __forceinline__ bool lt0(double x) { long long b = bits(x); return b < 0 && b != kSign; }  // x < 0
+__device__ __forceinline__ bool ge0(double x) { return !lt0(x); }                         // x >= 0
+__device__ __forceinline__ double imin(double a, double b) { return order_key(b) < order_key(a) ? b : a; }
+__device__ __forceinline__ double imax(double a, double b) { return order_key(a) < order_key(b) ? b : a; }
+// both arguments non-negative
+__device__ __forceinline__ double imax_pos(double a, double b) { return bits(a) < bits(b) ? b : a; }
+__device__ __forceinline__ bool lt_pos(double a, double b) { return bits(a) < bits(b); }   // a < b, b >= 0
+// x * (s > 0 ? 1 : -1) by flipping the sign bit
+__device__ __forceinline__ double times_sign(double x, double s) {
+  return from_bits(bits(x) ^ (gt0(s) ? 0LL : kSign));
+}
+
+// sqrt(x) and 1/sqrt(x) for x > 0 from the hardware's ~20-bit reciprocal
+// square-root seed (PTX rsqrt.approx.ftz.f64), refined by one third-order
+// step of the binomial series  (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + ...,
+// e = 1 - x y^2: relative error O(e^3) plus rounding, about one ulp.
+__device__ __forceinline__ double rsqrt_seed(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+__device__ __forceinline__ double fsqrt(double x) {
+  double y = rsqrt_seed(x);
+  double s = x * y;
+  double e = fma(-s, y, 1.0);
+  double t = fma(0.375, e, 0.5) * e;
+  return fma(s, t, s);
+}
+__device__ __forceinline__ double frsqrt(double x) {
+  double y = rsqrt_seed(x);
+  double e = fma(-(x * y), y, 1.0);
+  double t = fma(0.375, e, 0.5) * e;
+  return fma(y, t, y);
+}
+// sqrt(x) for x >= 0 (the seed of 0 is infinite)
+__device__ __forceinline__ double fsqrt0(double x) { return gt0(x) ? fsqrt(x) : 0.0; }
+
+// ---------------------------------------------------------------------------
 // Sweep-frame physics.  W = (rho, u, v, w, b1, b2, p): normal velocity u,
 // transverse (v, w) and transverse field (b1, b2) in the cyclic order of the
 // sweep; bn is the staggered normal field at the face.
@@ -95,17 +150,29 @@ struct Flux7 {
   double f[7];  // rho, m_n, m_t1, m_t2, B_t1, B_t2, E
 };
 
+// Conserved state U = (rho, rho u, rho v, rho w, b1, b2, E) and flux of Eq. mhd
+// along the normal (F of b_n is zero), pT = p + B^2/2, plus the fast speed.
 struct Side {
   double U[7], F[7];
-  double pT, B2, vB, E, irho;
+  double pT, B2, vB, cf;
 };
 
-__device__ __forceinline__ void side_state(const W7& W, double bn, double igm1, Side& s) {
-  s.B2 = fma(bn, bn, fma(W.b1, W.b1, W.b2 * W.b2));
+// Fast magnetosonic speed cf^2 = [(G p + B^2) + sqrt((G p + B^2)^2 - 4 G p bn^2)] / (2 rho).
+__device__ __forceinline__ double fast_speed(double rho, double p, double B2, double bn2, double gamma) {
+  double gp = gamma * p;
+  double s = gp + B2;
+  double disc = fma(s, s, -(4.0 * gp) * bn2);
+  if (lt0(disc)) disc = 0.0;
+  double cf2 = (s + fsqrt0(disc)) * (0.5 * rcp(rho));
+  return fsqrt(cf2);
+}
+
+__device__ __forceinline__ void side_state(const W7& W, double bn, double bn2, double gamma, double igm1, Side& s) {
+  s.B2 = fma(W.b1, W.b1, fma(W.b2, W.b2, bn2));
   s.pT = fma(0.5, s.B2, W.p);
   s.vB = fma(W.u, bn, fma(W.v, W.b1, W.w * W.b2));
   double v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
-  s.E = fma(W.p, igm1, 0.5 * fma(W.rho, v2, s.B2));
+  double E = fma(W.p, igm1, 0.5 * fma(W.rho, v2, s.B2));
   double mu = W.rho * W.u;
   s.U[0] = W.rho;
   s.U[1] = mu;
@@ -113,22 +180,15 @@ __device__ __forceinline__ void side_state(const W7& W, double bn, double igm1, 
   s.U[3] = W.rho * W.w;
   s.U[4] = W.b1;
   s.U[5] = W.b2;
-  s.U[6] = s.E;
+  s.U[6] = E;
   s.F[0] = mu;
-  s.F[1] = fma(mu, W.u, s.pT) - bn * bn;
+  s.F[1] = fma(mu, W.u, s.pT) - bn2;
   s.F[2] = fma(mu, W.v, -bn * W.b1);
   s.F[3] = fma(mu, W.w, -bn * W.b2);
   s.F[4] = fma(W.u, W.b1, -W.v * bn);
   s.F[5] = fma(W.u, W.b2, -W.w * bn);
-  s.F[6] = fma(s.E + s.pT, W.u, -bn * s.vB);
-}
-
-__device__ __forceinline__ double fast_speed(double rho_inv, double p, double B2, double bn, double gamma) {
-  double gp = gamma * p;
-  double s = gp + B2;
-  double disc = fma(s, s, -(4.0 * gp) * (bn * bn));
-  disc = fmax(disc, 0.0);
-  return sqrt(0.5 * (s + sqrt(disc)) * rho_inv);
+  s.F[6] = fma(E + s.pT, W.u, -bn * s.vB);
+  s.cf = fast_speed(W.rho, W.p, s.B2, bn2, gamma);
 }
 
 // Outer speed estimate S_L, S_R (Miyoshi & Kusano 2005) and the UCT-HLL
@@ -136,14 +196,12 @@ __device__ __forceinline__ double fast_speed(double rho_inv, double p, double B2
 struct Ingr {
   double ap, am, dd, uL, uR;
 };
-__device__ __forceinline__ void speeds(const W7& L, const W7& R, const Side& sl, const Side& sr, double bn,
-                                       double gamma, double& SL, double& SR, Ingr& ing) {
-  double cfL = fast_speed(sl.irho, L.p, sl.B2, bn, gamma);
-  double cfR = fast_speed(sr.irho, R.p, sr.B2, bn, gamma);
-  double cmax = fmax(cfL, cfR);
-  SL = fmin(L.u, R.u) - cmax;
-  SR = fmax(L.u, R.u) + cmax;
-  double aR = fmax(0.0, SR), aL = fmin(0.0, SL);
+__device__ __forceinline__ void speeds(const W7& L, const W7& R, const Side& sl, const Side& sr, double& SL,
+                                       double& SR, Ingr& ing) {
+  double cmax = imax_pos(sl.cf, sr.cf);
+  SL = imin(L.u, R.u) - cmax;
+  SR = imax(L.u, R.u) + cmax;
+  double aR = gt0(SR) ? SR : 0.0, aL = lt0(SL) ? SL : 0.0;
   double inv = rcp(aR - aL);
   ing.ap = aR * inv;
   ing.am = -aL * inv;
@@ -154,68 +212,106 @@ __device__ __forceinline__ void speeds(const W7& L, const W7& R, const Side& sl,
 
 __device__ __forceinline__ void riemann_hll(const W7& L, const W7& R, double bn, double gamma, double igm1,
                                             Flux7& F, Ingr& ing) {
+  const double bn2 = bn * bn;
   Side sl, sr;
-  side_state(L, bn, igm1, sl);
-  side_state(R, bn, igm1, sr);
-  sl.irho = rcp(L.rho);
-  sr.irho = rcp(R.rho);
+  side_state(L, bn, bn2, gamma, igm1, sl);
+  side_state(R, bn, bn2, gamma, igm1, sr);
   double SL, SR;
-  speeds(L, R, sl, sr, bn, gamma, SL, SR, ing);
-  if (SL >= 0.0) {
+  speeds(L, R, sl, sr, SL, SR, ing);
+  if (ge0(SL)) {
 #pragma unroll
     for (int q = 0; q < 7; q++) F.f[q] = sl.F[q];
-  } else if (SR <= 0.0) {
+  } else if (!gt0(SR)) {
 #pragma unroll
     for (int q = 0; q < 7; q++) F.f[q] = sr.F[q];
   } else {
     double inv = rcp(SR - SL);
     double sls = SR * SL;
 #pragma unroll
-    for (int q = 0; q < 7; q++) F.f[q] = (fma(SR, sl.F[q], -SL * sr.F[q]) + sls * (sr.U[q] - sl.U[q])) * inv;
+    for (int q = 0; q < 7; q++) F.f[q] = fma(sls, sr.U[q] - sl.U[q], fma(SR, sl.F[q], -SL * sr.F[q])) * inv;
   }
 }
 
+// Total field, total pressure and fast speed of one side (all that HLLD needs
+// from both sides before the contact speed is known).
+struct SideLite {
+  double B2, pT, cf;
+};
+__device__ __forceinline__ void side_lite(const W7& W, double bn2, double gamma, SideLite& s) {
+  s.B2 = fma(W.b1, W.b1, fma(W.b2, W.b2, bn2));
+  s.pT = fma(0.5, s.B2, W.p);
+  s.cf = fast_speed(W.rho, W.p, s.B2, bn2, gamma);
+}
+// Conserved state, energy, v.B and flux of one side, given its total field and pressure.
+__device__ __forceinline__ void side_full(const W7& W, double bn, double bn2, double igm1, const SideLite& l,
+                                          double U[7], double F[7], double& vB) {
+  vB = fma(W.u, bn, fma(W.v, W.b1, W.w * W.b2));
+  double v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
+  double E = fma(W.p, igm1, 0.5 * fma(W.rho, v2, l.B2));
+  double mu = W.rho * W.u;
+  U[0] = W.rho;
+  U[1] = mu;
+  U[2] = W.rho * W.v;
+  U[3] = W.rho * W.w;
+  U[4] = W.b1;
+  U[5] = W.b2;
+  U[6] = E;
+  F[0] = mu;
+  F[1] = fma(mu, W.u, l.pT) - bn2;
+  F[2] = fma(mu, W.v, -bn * W.b1);
+  F[3] = fma(mu, W.w, -bn * W.b2);
+  F[4] = fma(W.u, W.b1, -W.v * bn);
+  F[5] = fma(W.u, W.b2, -W.w * bn);
+  F[6] = fma(E + l.pT, W.u, -bn * vB);
+}
+
 // HLLD (Miyoshi & Kusano 2005): waves S_L < S*_L < S_M < S*_R < S_R with
-// continuous normal velocity and total pressure across the fan.  Only the
-// side of the contact that holds x/t = 0 is assembled into the flux.
+// continuous normal velocity and total pressure across the fan.  Both sides
+// give their total pressure and fast speed; the star transverse states of
+// both sides feed the double-star state; conserved states, energies and the
+// flux are assembled only on the side of the contact that holds x/t = 0.
 __device__ __forceinline__ void riemann_hlld(const W7& L, const W7& R, double bn, double gamma, double igm1,
                                              Flux7& F, Ingr& ing) {
-  Side sl, sr;
-  side_state(L, bn, igm1, sl);
-  side_state(R, bn, igm1, sr);
-  sl.irho = rcp(L.rho);
-  sr.irho = rcp(R.rho);
-  double SL, SR;
-  speeds(L, R, sl, sr, bn, gamma, SL, SR, ing);
-  if (SL > 0.0) {
-#pragma unroll
-    for (int q = 0; q < 7; q++) F.f[q] = sl.F[q];
-    return;
-  }
-  if (SR < 0.0) {
-#pragma unroll
-    for (int q = 0; q < 7; q++) F.f[q] = sr.F[q];
-    return;
-  }
   const double bn2 = bn * bn;
+  SideLite ll, lr;
+  side_lite(L, bn2, gamma, ll);
+  side_lite(R, bn2, gamma, lr);
+  // outer speeds and UCT ingredients
+  double cmax = imax_pos(ll.cf, lr.cf);
+  double SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
+  {
+    double aR = gt0(SR) ? SR : 0.0, aL = lt0(SL) ? SL : 0.0;
+    double inv = rcp(aR - aL);
+    ing.ap = aR * inv;
+    ing.am = -aL * inv;
+    ing.dd = -(aR * aL) * inv;
+    ing.uL = L.u;
+    ing.uR = R.u;
+  }
+  if (gt0(SL) || lt0(SR)) {  // supersonic: the upwind physical flux
+    const bool up_left = gt0(SL);
+    double U[7], vB;
+    side_full(up_left ? L : R, bn, bn2, igm1, up_left ? ll : lr, U, F.f, vB);
+    return;
+  }
   double sdL = SL - L.u, sdR = SR - R.u;
   double rsL = sdL * L.rho, rsR = sdR * R.rho;  // rho (S - u)
   double iden = rcp(rsR - rsL);
-  double SM = ((rsR * R.u - rsL * L.u) - sr.pT + sl.pT) * iden;
-  double pTs = (fma(rsR, sl.pT, -rsL * sr.pT) + (L.rho * rsR) * sdL * (R.u - L.u)) * iden;
+  double SM = ((fma(rsR, R.u, -rsL * L.u) - lr.pT) + ll.pT) * iden;
+  double pTs = fma((L.rho * rsR) * sdL, R.u - L.u, fma(rsR, ll.pT, -rsL * lr.pT)) * iden;
 
-  // star states, both sides (transverse parts are needed for the ** states)
+  // star transverse states of both sides
   double smL = SL - SM, smR = SR - SM;
   double ismL = rcp(smL), ismR = rcp(smR);
   double rhosL = rsL * ismL, rhosR = rsR * ismR;
   double vsL, wsL, b1sL, b2sL, vsR, wsR, b1sR, b2sR;
   {
     double rsm = rsL * smL, D = rsm - bn2;
-    if (fabs(D) < kHlldDegenEps * rsm) {
+    if (lt_pos(fabs(D), kHlldDegenEps * rsm)) {
       vsL = L.v; wsL = L.w; b1sL = L.b1; b2sL = L.b2;
     } else {
       double iD = rcp(D);
-      double cv = bn * (SM - L.u) * iD;
+      double cv = (bn * (SM - L.u)) * iD;
       vsL = fma(-L.b1, cv, L.v);
       wsL = fma(-L.b2, cv, L.w);
       double cb = fma(rsL, sdL, -bn2) * iD;
@@ -225,11 +321,11 @@ __device__ __forceinline__ void riemann_hlld(const W7& L, const W7& R, double bn
   }
   {
     double rsm = rsR * smR, D = rsm - bn2;
-    if (fabs(D) < kHlldDegenEps * rsm) {
+    if (lt_pos(fabs(D), kHlldDegenEps * rsm)) {
       vsR = R.v; wsR = R.w; b1sR = R.b1; b2sR = R.b2;
     } else {
       double iD = rcp(D);
-      double cv = bn * (SM - R.u) * iD;
+      double cv = (bn * (SM - R.u)) * iD;
       vsR = fma(-R.b1, cv, R.v);
       wsR = fma(-R.b2, cv, R.w);
       double cb = fma(rsR, sdR, -bn2) * iD;
@@ -238,96 +334,123 @@ __device__ __forceinline__ void riemann_hlld(const W7& L, const W7& R, double bn
     }
   }
   // the side of the contact that contains x/t = 0
-  const bool left = SM >= 0.0;
+  const bool left = ge0(SM);
   const W7& A = left ? L : R;
-  const Side& sa = left ? sl : sr;
-  double S = left ? SL : SR, sd = left ? sdL : sdR, ism = left ? ismL : ismR, rhos = left ? rhosL : rhosR;
-  double vs = left ? vsL : vsR, ws = left ? wsL : wsR, b1s = left ? b1sL : b1sR, b2s = left ? b2sL : b2sR;
+  double Ua[7], vBa;
+  side_full(A, bn, bn2, igm1, left ? ll : lr, Ua, F.f, vBa);
+  const double pTa = left ? ll.pT : lr.pT;
+  const double S = left ? SL : SR, sd = left ? sdL : sdR, ism = left ? ismL : ismR;
+  const double rhos = left ? rhosL : rhosR;
+  const double vs = left ? vsL : vsR, ws = left ? wsL : wsR, b1s = left ? b1sL : b1sR, b2s = left ? b2sL : b2sR;
   double vBs = fma(SM, bn, fma(vs, b1s, ws * b2s));
-  double Es = (fma(sd, sa.E, -sa.pT * A.u) + fma(pTs, SM, bn * (sa.vB - vBs))) * ism;
+  double Es = (fma(sd, Ua[6], -pTa * A.u) + fma(pTs, SM, bn * (vBa - vBs))) * ism;
   double Us[7] = {rhos, rhos * SM, rhos * vs, rhos * ws, b1s, b2s, Es};
-  double Uss[7] = {Us[0], Us[1], Us[2], Us[3], Us[4], Us[5], Us[6]};
-  double c2 = 0.0;  // speed of the rotational wave on this side, if x/t = 0 lies beyond it
-  if (!(0.5 * bn2 < kHlldBnEps * pTs)) {
-    double sqL = sqrt(rhosL), sqR = sqrt(rhosR);
-    double abn = fabs(bn);
-    double Ss = left ? SM - abn / sqL : SM + abn / sqR;
-    c2 = left ? (Ss < 0.0 ? Ss : 0.0) : (Ss >= 0.0 ? Ss : 0.0);
-    double sgn = bn > 0.0 ? 1.0 : -1.0;
-    double isum = rcp(sqL + sqR);
-    double vss = (fma(sqL, vsL, sqR * vsR) + (b1sR - b1sL) * sgn) * isum;
-    double wss = (fma(sqL, wsL, sqR * wsR) + (b2sR - b2sL) * sgn) * isum;
-    double sq2 = sqL * sqR;
-    double b1ss = (fma(sqL, b1sR, sqR * b1sL) + sq2 * (vsR - vsL) * sgn) * isum;
-    double b2ss = (fma(sqL, b2sR, sqR * b2sL) + sq2 * (wsR - wsL) * sgn) * isum;
-    double vBss = fma(SM, bn, fma(vss, b1ss, wss * b2ss));
-    double sqa = left ? -sqL : sqR;
-    Uss[2] = rhos * vss;
-    Uss[3] = rhos * wss;
-    Uss[4] = b1ss;
-    Uss[5] = b2ss;
-    Uss[6] = fma(sqa * (vBs - vBss), sgn, Es);
-  }
 #pragma unroll
-  for (int q = 0; q < 7; q++) F.f[q] = fma(S, Us[q] - sa.U[q], sa.F[q]) + c2 * (Uss[q] - Us[q]);
+  for (int q = 0; q < 7; q++) F.f[q] = fma(S, Us[q] - Ua[q], F.f[q]);
+  // rotational (Alfven) waves, absent when the normal field vanishes
+  if (!lt_pos(0.5 * bn2, kHlldBnEps * pTs)) {
+    double iqL = frsqrt(rhosL), iqR = frsqrt(rhosR);  // 1/sqrt(rho*)
+    double sqL = rhosL * iqL, sqR = rhosR * iqR;      // sqrt(rho*)
+    double abn = fabs(bn);
+    double Ss = left ? fma(-abn, iqL, SM) : fma(abn, iqR, SM);
+    bool beyond = left ? lt0(Ss) : ge0(Ss);           // x/t = 0 lies between S*_a and S_M
+    if (beyond) {
+      double isum = rcp(sqL + sqR);
+      double vss = fma(sqL, vsL, fma(sqR, vsR, times_sign(b1sR - b1sL, bn))) * isum;
+      double wss = fma(sqL, wsL, fma(sqR, wsR, times_sign(b2sR - b2sL, bn))) * isum;
+      double sq2 = sqL * sqR;
+      double b1ss = fma(sqL, b1sR, fma(sqR, b1sL, times_sign(sq2 * (vsR - vsL), bn))) * isum;
+      double b2ss = fma(sqL, b2sR, fma(sqR, b2sL, times_sign(sq2 * (wsR - wsL), bn))) * isum;
+      double vBss = fma(SM, bn, fma(vss, b1ss, wss * b2ss));
+      double sqa = left ? -sqL : sqR;
+      double Ess = fma(sqa, times_sign(vBs - vBss, bn), Es);
+      // F += S*_a (U** - U*): the density and normal momentum are continuous
+      F.f[2] = fma(Ss, fma(rhos, vss, -Us[2]), F.f[2]);
+      F.f[3] = fma(Ss, fma(rhos, wss, -Us[3]), F.f[3]);
+      F.f[4] = fma(Ss, b1ss - b1s, F.f[4]);
+      F.f[5] = fma(Ss, b2ss - b2s, F.f[5]);
+      F.f[6] = fma(Ss, Ess - Es, F.f[6]);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Reconstruction (Eq. reconstruct).  s0..s4 = V_{i-2..i+2}; plus = V^L_{i+1/2},
 // minus = V^R_{i-1/2}.
 // ---------------------------------------------------------------------------
+// minmod(a, b): 0 when the signs differ (or either is 0), else the argument of
+// smaller magnitude, on integer pipes.
 __device__ __forceinline__ double minmod(double a, double b) {
-  if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) return (fabs(b) < fabs(a)) ? b : a;
-  return 0.0;
+  long long ia = bits(a), ib = bits(b);
+  if ((ia ^ ib) < 0) return 0.0;
+  return (ib & kMag) < (ia & kMag) ? b : a;
 }
 
 __device__ __forceinline__ void recon_plm(double s1, double s2, double s3, double& plus, double& minus) {
-  double d = 0.5 * minmod(s2 - s1, s3 - s2);
-  plus = s2 + d;
-  minus = s2 - d;
+  double d = minmod(s2 - s1, s3 - s2);
+  plus = fma(0.5, d, s2);
+  minus = fma(-0.5, d, s2);
 }
 
-// WENO-Z value at the right face of the middle cell of a0..a4 (Borges et al. 2008).
-__device__ __forceinline__ double wenoz_face(double a0, double a1, double a2, double a3, double a4) {
-  const double i6 = 1.0 / 6.0;
-  double q0 = fma(2.0, a0, fma(-7.0, a1, 11.0 * a2)) * i6;
-  double q1 = fma(-1.0, a1, fma(5.0, a2, 2.0 * a3)) * i6;
-  double q2 = fma(2.0, a2, fma(5.0, a3, -a4)) * i6;
-  double t = fma(-2.0, a1, a0) + a2, u = fma(-4.0, a1, a0) + 3.0 * a2;
-  double b0 = fma(13.0 / 12.0, t * t, 0.25 * (u * u));
+// WENO-Z (Borges et al. 2008) values at both faces of the middle cell of
+// a0..a4 = V_{i-2..i+2}.  Candidate values q_k, Jiang-Shu indicators beta_k,
+// tau5 = |beta_0 - beta_2|, alpha_k = d_k (1 + (tau5 / (beta_k + eps))^2),
+// d = (1/10, 6/10, 3/10).  The mirrored (minus-face) stencil has the same
+// indicators with beta_0 and beta_2 exchanged, so the ratios
+// r_k = tau5 / (beta_k + eps) are formed once for both faces; the factor 1/6
+// of the candidate values is folded into the normalisation.
+__device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, double a3, double a4, double& plus,
+                                            double& minus) {
+  double t = fma(-2.0, a1, a0) + a2, u = fma(3.0, a2, fma(-4.0, a1, a0));
+  double b0 = fma(13.0 / 12.0 * t, t, (0.25 * u) * u);
   t = fma(-2.0, a2, a1) + a3;
   u = a1 - a3;
-  double b1 = fma(13.0 / 12.0, t * t, 0.25 * (u * u));
+  double b1 = fma(13.0 / 12.0 * t, t, (0.25 * u) * u);
   t = fma(-2.0, a3, a2) + a4;
-  u = fma(3.0, a2, -4.0 * a3) + a4;
-  double b2 = fma(13.0 / 12.0, t * t, 0.25 * (u * u));
+  u = fma(3.0, a2, fma(-4.0, a3, a4));
+  double b2 = fma(13.0 / 12.0 * t, t, (0.25 * u) * u);
   double tau = fabs(b0 - b2);
-  double r0 = tau * rcp(b0 + kWenozEps);
-  double r1 = tau * rcp(b1 + kWenozEps);
-  double r2 = tau * rcp(b2 + kWenozEps);
-  double al0 = 0.1 * fma(r0, r0, 1.0);
-  double al1 = 0.6 * fma(r1, r1, 1.0);
-  double al2 = 0.3 * fma(r2, r2, 1.0);
-  return fma(al0, q0, fma(al1, q1, al2 * q2)) * rcp(al0 + al1 + al2);
+  double r0 = tau * rcp(b0 + kWenozEps), r1 = tau * rcp(b1 + kWenozEps), r2 = tau * rcp(b2 + kWenozEps);
+  double g0 = fma(r0, r0, 1.0), g1 = fma(r1, r1, 1.0), g2 = fma(r2, r2, 1.0);
+  // plus face: stencils (a0 a1 a2), (a1 a2 a3), (a2 a3 a4); 6 q_k
+  {
+    double q0 = fma(2.0, a0, fma(-7.0, a1, 11.0 * a2));
+    double q1 = fma(5.0, a2, fma(2.0, a3, -a1));
+    double q2 = fma(2.0, a2, fma(5.0, a3, -a4));
+    double al0 = 0.1 * g0, al1 = 0.6 * g1, al2 = 0.3 * g2;
+    plus = fma(al0, q0, fma(al1, q1, al2 * q2)) * rcp(6.0 * ((al0 + al1) + al2));
+  }
+  // minus face: the mirrored stencils, indicators beta_2, beta_1, beta_0
+  {
+    double q0 = fma(2.0, a4, fma(-7.0, a3, 11.0 * a2));
+    double q1 = fma(5.0, a2, fma(2.0, a1, -a3));
+    double q2 = fma(2.0, a2, fma(5.0, a1, -a0));
+    double al0 = 0.1 * g2, al1 = 0.6 * g1, al2 = 0.3 * g0;
+    minus = fma(al0, q0, fma(al1, q1, al2 * q2)) * rcp(6.0 * ((al0 + al1) + al2));
+  }
 }
 
 __device__ __forceinline__ double ppm_face(double a, double b, double c, double d) {
   double f = fma(7.0 / 12.0, b + c, -(1.0 / 12.0) * (a + d));
-  double lo = fmin(b, c), hi = fmax(b, c);
-  return fmin(fmax(f, lo), hi);
+  double lo = imin(b, c), hi = imax(b, c);
+  return imin(imax(f, lo), hi);
 }
+// Piecewise-parabolic (Colella & Woodward 1984), method-of-lines form:
+// fourth-order face values clipped to their neighbours, then the parabola of
+// the cell flattened at an extremum or steepened on the overshooting side.
 __device__ __forceinline__ void recon_ppm(double s0, double s1, double s2, double s3, double s4, double& plus,
                                           double& minus) {
   double vp = ppm_face(s1, s2, s3, s4);
   double vm = ppm_face(s0, s1, s2, s3);
-  if ((vp - s2) * (s2 - vm) <= 0.0) {
+  if (!gt0((vp - s2) * (s2 - vm))) {
     vp = s2;
     vm = s2;
   } else {
     double dv = vp - vm;
     double v6 = 6.0 * (s2 - 0.5 * (vm + vp));
-    if (dv * v6 > dv * dv) vm = fma(3.0, s2, -2.0 * vp);
-    else if (-(dv * dv) > dv * v6) vp = fma(3.0, s2, -2.0 * vm);
+    double x = dv * v6, y = dv * dv;
+    if (order_key(y) < order_key(x)) vm = fma(3.0, s2, -2.0 * vp);
+    else if (order_key(x) < order_key(-y)) vp = fma(3.0, s2, -2.0 * vm);
   }
   plus = vp;
   minus = vm;
