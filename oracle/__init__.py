@@ -67,6 +67,11 @@ def lib():
         L.orc_fast_speed.argtypes = [D, D, D, D, D]
         L.orc_cfl_dt_state.restype = D
         L.orc_cfl_dt_state.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP)]
+        PP = ctypes.POINTER(DP)
+        L.orc_functional_prim.argtypes = [ctypes.POINTER(OrcConfig), PP, PP, DP, ctypes.c_int, ctypes.c_int, PP, DP,
+                                          ctypes.POINTER(ctypes.c_ulonglong)]
+        L.orc_jvp_prim.argtypes = [ctypes.POINTER(OrcConfig), PP, PP, DP, ctypes.c_int, ctypes.c_int, PP, PP, DP, DP]
+        L.orc_grad_prim.argtypes = [ctypes.POINTER(OrcConfig), PP, PP, DP, ctypes.c_int, ctypes.c_int, PP, DP, PP]
         L.orc_count_flops.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
                                       ctypes.POINTER(ctypes.c_ulonglong)]
         _lib = L
@@ -246,3 +251,65 @@ def count_flops(cfg, state, nsteps, dt):
     for i, ph in enumerate(PHASES):
         res[ph] = {op: int(out[i * len(OPS) + j]) for j, op in enumerate(OPS)}
     return res
+
+
+FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
+
+
+def _parr(arrs):
+    out = (ctypes.POINTER(ctypes.c_double) * len(arrs))()
+    for i, a in enumerate(arrs):
+        out[i] = _dp(a)
+    return out
+
+
+def _prim_args(cfg, prim, B, dts, target):
+    """prim: dict rho, vx, vy, vz, p (cell arrays); B: (b0, b1, b2) in the state layout."""
+    shapes = state_shapes(cfg)
+    P = [np.ascontiguousarray(np.asarray(prim[k], dtype=np.float64).reshape(shapes[0]))
+         for k in ("rho", "vx", "vy", "vz", "p")]
+    Bs = [np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(s)) for b, s in zip(B, shapes[5:])]
+    d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+    T = None
+    if target is not None:
+        T = [np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(shapes[0])) for t in target]
+    keep = (P, Bs, d, T)
+    return keep, _parr(P), _parr(Bs), _dp(d), (_parr(T) if T is not None else None)
+
+
+def functional_prim(cfg, prim, B, dts, which="magnetic_energy", target=None, signature=False):
+    """J after len(dts) steps of the given sizes from initial primitives (p and B
+    fixed); with signature=True also the hash of every branch decision taken."""
+    keep, P, Bp, d, T = _prim_args(cfg, prim, B, dts, target)
+    J = ctypes.c_double()
+    sig = ctypes.c_ulonglong()
+    rc = lib().orc_functional_prim(ctypes.byref(make_config(cfg)), P, Bp, d, len(dts), FUNCTIONALS[which], T,
+                                   ctypes.byref(J), ctypes.byref(sig))
+    if rc:
+        raise FloatingPointError("non-positive density or pressure")
+    return (J.value, sig.value) if signature else J.value
+
+
+def jvp_prim(cfg, prim, B, dts, tangent, which="magnetic_energy", target=None):
+    """(J, dJ): forward-mode derivative of J along tangent = dict rho, vx, vy, vz."""
+    keep, P, Bp, d, T = _prim_args(cfg, prim, B, dts, target)
+    tg = [np.ascontiguousarray(np.asarray(tangent[k], dtype=np.float64).reshape(keep[0][0].shape))
+          for k in ("rho", "vx", "vy", "vz")]
+    J, dJ = ctypes.c_double(), ctypes.c_double()
+    rc = lib().orc_jvp_prim(ctypes.byref(make_config(cfg)), P, Bp, d, len(dts), FUNCTIONALS[which], T, _parr(tg),
+                            ctypes.byref(J), ctypes.byref(dJ))
+    if rc:
+        raise FloatingPointError("non-positive density or pressure")
+    return J.value, dJ.value
+
+
+def grad_prim(cfg, prim, B, dts, which="magnetic_energy", target=None):
+    """(J, grad): reverse-mode gradient of J w.r.t. the initial rho, vx, vy, vz."""
+    keep, P, Bp, d, T = _prim_args(cfg, prim, B, dts, target)
+    g = [np.zeros(keep[0][0].shape) for _ in range(4)]
+    J = ctypes.c_double()
+    rc = lib().orc_grad_prim(ctypes.byref(make_config(cfg)), P, Bp, d, len(dts), FUNCTIONALS[which], T,
+                             ctypes.byref(J), _parr(g))
+    if rc:
+        raise FloatingPointError("non-positive density or pressure")
+    return J.value, dict(zip(("rho", "vx", "vy", "vz"), g))

@@ -54,14 +54,40 @@ struct Config {
   double p_floor;  // floor on the recovered pressure (0: none)
 };
 
-template <class R> inline R rmin(R a, R b) { return (b < a) ? b : a; }
-template <class R> inline R rmax(R a, R b) { return (a < b) ? b : a; }
+// For the branch signature, min/max of (nearly) equal arguments is one
+// neutral decision: the two arguments are then usually the same function
+// (e.g. u_L = u_R = (u_i + u_i+1)/2 when both cells take the shared slope),
+// so which one is returned changes neither the value nor the derivative.
+template <class R> inline bool near_tie(R a, R b) {
+  double x = value(a), y = value(b);
+  return std::fabs(x - y) <= 1e-12 * (std::fabs(x) + std::fabs(y));
+}
+template <class R> inline R rmin(R a, R b) {
+  bool sb = b < a;
+  branch(near_tie(a, b) ? 10 : (sb ? 11 : 12));
+  return sb ? b : a;
+}
+template <class R> inline R rmax(R a, R b) {
+  bool sb = a < b;
+  branch(near_tie(a, b) ? 10 : (sb ? 13 : 14));
+  return sb ? b : a;
+}
+// |x| where the kink at 0 is a branch of the scheme
+template <class R> inline R rabs(R x) {
+  branch(x < R(0.0) ? 15 : 16);
+  return fabs(x);
+}
 
 // minmod(a, b): 0 if a*b <= 0, else the argument of smaller magnitude; on a tie
 // |a| == |b| the first argument is returned (both are equal then).
 template <class R> inline R minmod(R a, R b) {
   const R zero(0.0);
-  if ((a > zero && b > zero) || (a < zero && b < zero)) return (fabs(b) < fabs(a)) ? b : a;
+  if ((a > zero && b > zero) || (a < zero && b < zero)) {
+    bool sb = fabs(b) < fabs(a);
+    branch(sb ? 1 : 2);
+    return sb ? b : a;
+  }
+  branch(3);
   return zero;
 }
 
@@ -112,7 +138,10 @@ template <class R> inline R fast_speed(R rho, R p, R B2, R Bn, double gamma) {
   R gp = R(gamma) * p;
   R s = gp + B2;
   R disc = s * s - (R(4.0) * gp) * (Bn * Bn);
-  if (disc < R(0.0)) disc = R(0.0);
+  if (disc < R(0.0)) {
+    disc = R(0.0);
+    branch(17);
+  }
   R cf2 = (R(0.5) * (s + sqrt(disc))) / rho;
   return sqrt(cf2);
 }
@@ -192,8 +221,9 @@ inline void riemann_hll(const R WL[NW], const R WR[NW], R bn, double gamma, R F[
   SideState<R> L = side_state(WL, bn, gamma), Rs = side_state(WR, bn, gamma);
   R SL, SR;
   signal_speeds(WL, WR, L, Rs, bn, gamma, SL, SR, ing);
-  if (SL >= R(0.0)) { for (int q = 0; q < NW; q++) F[q] = L.F[q]; return; }
-  if (SR <= R(0.0)) { for (int q = 0; q < NW; q++) F[q] = Rs.F[q]; return; }
+  if (SL >= R(0.0)) { branch(21); for (int q = 0; q < NW; q++) F[q] = L.F[q]; return; }
+  if (SR <= R(0.0)) { branch(22); for (int q = 0; q < NW; q++) F[q] = Rs.F[q]; return; }
+  branch(23);
   R inv = R(1.0) / (SR - SL);
   for (int q = 0; q < NW; q++)
     F[q] = ((SR * L.F[q] - SL * Rs.F[q]) + (SR * SL) * (Rs.U[q] - L.U[q])) * inv;
@@ -207,8 +237,8 @@ inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F
   SideState<R> L = side_state(WL, bn, gamma), Rs = side_state(WR, bn, gamma);
   R SL, SR;
   signal_speeds(WL, WR, L, Rs, bn, gamma, SL, SR, ing);
-  if (SL > R(0.0)) { for (int q = 0; q < NW; q++) F[q] = L.F[q]; return; }
-  if (SR < R(0.0)) { for (int q = 0; q < NW; q++) F[q] = Rs.F[q]; return; }
+  if (SL > R(0.0)) { branch(31); for (int q = 0; q < NW; q++) F[q] = L.F[q]; return; }
+  if (SR < R(0.0)) { branch(32); for (int q = 0; q < NW; q++) F[q] = Rs.F[q]; return; }
 
   const R zero(0.0);
   R rhoL = WL[W_RHO], uL = WL[W_VN], rhoR = WR[W_RHO], uR = WR[W_VN];
@@ -228,6 +258,7 @@ inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F
     R rsm = (rho * sd) * sm;
     R D = rsm - bn * bn;
     if (fabs(D) < R(HLLD_DEGEN_EPS) * rsm) {
+      branch(33);
       o.v = v; o.w = w; o.b1 = b1; o.b2 = b2;
     } else {
       R invD = R(1.0) / D;
@@ -256,10 +287,11 @@ inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F
   R SsL = SM, SsR = SM;
   R UssL[NW], UssR[NW];
   bool rot = !(R(0.5) * (bn * bn) < R(HLLD_BN_EPS) * pTs);
+  branch(rot ? 34 : 35);
   if (rot) {
     R sqL = sqrt(sL.rho), sqR = sqrt(sR.rho);
-    SsL = SM - fabs(bn) / sqL;
-    SsR = SM + fabs(bn) / sqR;
+    SsL = SM - rabs(bn) / sqL;
+    SsR = SM + rabs(bn) / sqR;
     R sgn = bn > zero ? R(1.0) : R(-1.0);
     R inv = R(1.0) / (sqL + sqR);
     R vss = ((sqL * sL.v + sqR * sR.v) + (sR.b1 - sL.b1) * sgn) * inv;
@@ -274,6 +306,7 @@ inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F
   }
 
   // Flux at x/t = 0 from the wave fan, Rankine-Hugoniot across each wave.
+  branch(SsL >= zero ? 36 : (SM >= zero ? 37 : (SsR >= zero ? 38 : 39)));
   if (SsL >= zero) {  // S_L <= 0 <= S*_L
     for (int q = 0; q < NW; q++) F[q] = L.F[q] + SL * (UsL[q] - L.U[q]);
   } else if (SM >= zero) {  // S*_L <= 0 <= S_M
@@ -322,7 +355,7 @@ template <class R> inline R wenoz_face(R a0, R a1, R a2, R a3, R a4) {
   t = (a2 - R(2.0) * a3) + a4;
   u = (R(3.0) * a2 - R(4.0) * a3) + a4;
   R b2 = R(13.0 / 12.0) * (t * t) + R(0.25) * (u * u);
-  R tau = fabs(b0 - b2);
+  R tau = rabs(b0 - b2);
   R r0 = tau / (b0 + R(WENOZ_EPS));
   R r1 = tau / (b1 + R(WENOZ_EPS));
   R r2 = tau / (b2 + R(WENOZ_EPS));
@@ -345,8 +378,8 @@ template <class R> inline void recon_wenoz(const R s[5], R& plus, R& minus) {
 template <class R> inline R ppm_face(R a, R b, R c, R d) {  // a=V_{i-1}, b=V_i, c=V_{i+1}, d=V_{i+2}
   R f = R(7.0 / 12.0) * (b + c) - R(1.0 / 12.0) * (a + d);
   R lo = rmin(b, c), hi = rmax(b, c);
-  if (f < lo) f = lo;
-  if (f > hi) f = hi;
+  if (f < lo) { f = lo; branch(41); }
+  if (f > hi) { f = hi; branch(42); }
   return f;
 }
 template <class R> inline void recon_ppm(const R s[5], R& plus, R& minus) {
@@ -354,13 +387,14 @@ template <class R> inline void recon_ppm(const R s[5], R& plus, R& minus) {
   R vp = ppm_face(s[1], s[2], s[3], s[4]);
   R vm = ppm_face(s[0], s[1], s[2], s[3]);
   if ((vp - vc) * (vc - vm) <= R(0.0)) {
+    branch(43);
     vp = vc;
     vm = vc;
   } else {
     R dv = vp - vm;
     R v6 = R(6.0) * (vc - R(0.5) * (vm + vp));
-    if (dv * v6 > dv * dv) vm = R(3.0) * vc - R(2.0) * vp;
-    else if (-(dv * dv) > dv * v6) vp = R(3.0) * vc - R(2.0) * vm;
+    if (dv * v6 > dv * dv) { branch(44); vm = R(3.0) * vc - R(2.0) * vp; }
+    else if (-(dv * dv) > dv * v6) { branch(45); vp = R(3.0) * vc - R(2.0) * vm; }
   }
   plus = vp;
   minus = vm;
@@ -532,6 +566,7 @@ template <class R> struct Sim {
           // pressure is raised to p_floor when below it; the conserved energy
           // is left unchanged, so the update stays conservative.
           if (V[P_PR] < R(c.p_floor)) {
+            branch(52);
             V[P_PR] = R(c.p_floor);
             if (count_floors && i >= 0 && i < n[0] && j >= 0 && j < n[1] && k >= 0 && k < n[2]) floors++;
           }
@@ -580,6 +615,7 @@ template <class R> struct Sim {
           // Positivity fallback (reading): first order in this cell if a
           // reconstructed density or pressure is not positive.
           if (!(wp[W_RHO] > R(0.0)) || !(wm[W_RHO] > R(0.0)) || !(wp[W_PR] > R(0.0)) || !(wm[W_PR] > R(0.0))) {
+            branch(51);
             for (int q = 0; q < NW; q++) wp[q] = wm[q] = wc[q];
             fallbacks++;
           }
@@ -800,5 +836,88 @@ template <class R> struct Sim {
     return R(c.cfl) / lmax;
   }
 };
+
+// ---------------------------------------------------------------------------
+// Functionals of the final state and the map from initial primitives, for the
+// gradient of a final-state functional with respect to the initial density
+// and velocity (the step sizes are given, i.e. frozen).
+// ---------------------------------------------------------------------------
+enum { FUNC_MAGNETIC_ENERGY = 0, FUNC_MISFIT = 1 };
+
+// Initial conserved state from primitives (Eq. Energy): m = rho v,
+// E = p/(G-1) + rho v^2/2 + B^2/2 with the cell field the mean of the faces
+// (2D B_z: the cell value); p and the field are held fixed.
+template <class R>
+void set_from_prims(Sim<R>& s, const R* rho, const R* vx, const R* vy, const R* vz, const double* p,
+                    const double* const* B) {
+  // faces (and the 2D cell B_z) as constants
+  for (int q = Q_B0; q <= Q_B2; q++) {
+    int e[3] = {s.n[0], s.n[1], s.n[2]};
+    for (int d = 0; d < s.ndim; d++)
+      if (s.is_face(q, d)) e[d] += 1;
+    const double* src = B[q - Q_B0];
+    for (int k = 0; k < e[2]; k++)
+      for (int j = 0; j < e[1]; j++)
+        for (int i = 0; i < e[0]; i++) s.U0[q](i, j, k) = R(*src++);
+  }
+  const double gm1 = s.c.gamma - 1.0;
+  size_t c = 0;
+  for (int k = 0; k < s.n[2]; k++)
+    for (int j = 0; j < s.n[1]; j++)
+      for (int i = 0; i < s.n[0]; i++, c++) {
+        R bx = R(0.5) * (s.U0[Q_B0](i, j, k) + s.U0[Q_B0](i + 1, j, k));
+        R by = R(0.5) * (s.U0[Q_B1](i, j, k) + s.U0[Q_B1](i, j + 1, k));
+        R bz = s.ndim == 3 ? R(0.5) * (s.U0[Q_B2](i, j, k) + s.U0[Q_B2](i, j, k + 1)) : s.U0[Q_B2](i, j, k);
+        R v2 = (vx[c] * vx[c] + vy[c] * vy[c]) + vz[c] * vz[c];
+        R B2 = (bx * bx + by * by) + bz * bz;
+        s.U0[Q_RHO](i, j, k) = rho[c];
+        s.U0[Q_MX](i, j, k) = rho[c] * vx[c];
+        s.U0[Q_MY](i, j, k) = rho[c] * vy[c];
+        s.U0[Q_MZ](i, j, k) = rho[c] * vz[c];
+        s.U0[Q_EN](i, j, k) = (R(p[c] / gm1) + (R(0.5) * rho[c]) * v2) + R(0.5) * B2;
+      }
+}
+
+// J = 1/2 sum_cells |B_c|^2 dV (magnetic energy), or
+// J = 1/2 sum_cells sum_q (U_q - T_q)^2 dV over the cell-centred conserved
+// variables (rho, m, E; in 2D also B_z) for a target state T (misfit).
+template <class R> R functional(Sim<R>& s, int which, const double* const* target) {
+  s.fill_ghosts(s.U0);
+  double dV = s.dx[0] * s.dx[1] * (s.ndim == 3 ? s.dx[2] : 1.0);
+  R J(0.0);
+  size_t c = 0;
+  for (int k = 0; k < s.n[2]; k++)
+    for (int j = 0; j < s.n[1]; j++)
+      for (int i = 0; i < s.n[0]; i++, c++) {
+        R cellsum(0.0);
+        if (which == FUNC_MAGNETIC_ENERGY) {
+          R bx = R(0.5) * (s.U0[Q_B0](i, j, k) + s.U0[Q_B0](i + 1, j, k));
+          R by = R(0.5) * (s.U0[Q_B1](i, j, k) + s.U0[Q_B1](i, j + 1, k));
+          R bz = s.ndim == 3 ? R(0.5) * (s.U0[Q_B2](i, j, k) + s.U0[Q_B2](i, j, k + 1)) : s.U0[Q_B2](i, j, k);
+          cellsum = (bx * bx + by * by) + bz * bz;
+        } else {
+          int nq = s.ndim == 2 ? 6 : 5;
+          for (int q = 0; q < nq; q++) {
+            int slot = q < 5 ? q : Q_B2;
+            R dq = s.U0[slot](i, j, k) - R(target[q][c]);
+            cellsum = q == 0 ? dq * dq : cellsum + dq * dq;
+          }
+        }
+        J = J + cellsum;
+      }
+  return R(0.5 * dV) * J;
+}
+
+// J after nsteps steps of the given sizes from the initial primitives.
+template <class R>
+R run_functional(const Config& cfg, const R* rho, const R* vx, const R* vy, const R* vz, const double* p,
+                 const double* const* B, const double* dts, int nsteps, int which, const double* const* target,
+                 int* bad) {
+  Sim<R> s(cfg);
+  set_from_prims(s, rho, vx, vy, vz, p, B);
+  for (int t = 0; t < nsteps; t++) s.step(R(dts[t]));
+  if (bad) *bad = s.bad;
+  return functional(s, which, target);
+}
 
 }  // namespace orc

@@ -211,4 +211,60 @@ int orc_count_flops(const OrcConfig* c, const double* const* arrays, int nsteps,
   return 0;
 }
 
+// ---- final-state functional and its derivatives w.r.t. the initial rho, v ----
+// prim[0..4] = rho, vx, vy, vz, p (cell arrays); B[0..2] as in the state layout;
+// dts[nsteps] the frozen step sizes; which = 0 magnetic energy, 1 misfit to
+// target[0..4 (2D: 5)] (cell arrays of rho, mx, my, mz, E (, Bz)).
+static size_t ncells(const Config& c) { return (size_t)c.nx * c.ny * (c.ndim == 3 ? c.nz : 1); }
+
+int orc_functional_prim(const OrcConfig* oc, const double* const* prim, const double* const* B, const double* dts,
+                        int nsteps, int which, const double* const* target, double* J, unsigned long long* sig) {
+  Config c = to_cfg(oc);
+  int bad = 0;
+  g_branch_sig = 1469598103934665603ULL;
+  *J = run_functional<double>(c, prim[0], prim[1], prim[2], prim[3], prim[4], B, dts, nsteps, which, target, &bad);
+  if (sig) *sig = g_branch_sig;
+  return bad ? -4 : 0;
+}
+
+int orc_jvp_prim(const OrcConfig* oc, const double* const* prim, const double* const* B, const double* dts,
+                 int nsteps, int which, const double* const* target, const double* const* tangent, double* J,
+                 double* dJ) {
+  Config c = to_cfg(oc);
+  size_t N = ncells(c);
+  std::vector<Dual> in[4];
+  for (int q = 0; q < 4; q++) {
+    in[q].resize(N);
+    for (size_t i = 0; i < N; i++) in[q][i] = Dual(prim[q][i], tangent[q][i]);
+  }
+  int bad = 0;
+  Dual r = run_functional<Dual>(c, in[0].data(), in[1].data(), in[2].data(), in[3].data(), prim[4], B, dts, nsteps,
+                                which, target, &bad);
+  *J = r.v;
+  *dJ = r.d;
+  return bad ? -4 : 0;
+}
+
+int orc_grad_prim(const OrcConfig* oc, const double* const* prim, const double* const* B, const double* dts,
+                  int nsteps, int which, const double* const* target, double* J, double* const* grad) {
+  Config c = to_cfg(oc);
+  size_t N = ncells(c);
+  g_tape.clear();
+  std::vector<Tape> in[4];
+  for (int q = 0; q < 4; q++) {
+    in[q].resize(N);
+    for (size_t i = 0; i < N; i++) in[q][i] = Tape::variable(prim[q][i]);
+  }
+  int bad = 0;
+  Tape r = run_functional<Tape>(c, in[0].data(), in[1].data(), in[2].data(), in[3].data(), prim[4], B, dts, nsteps,
+                                which, target, &bad);
+  *J = r.v;
+  std::vector<double> adj = tape_backprop(r);
+  for (int q = 0; q < 4; q++)
+    for (size_t i = 0; i < N; i++) grad[q][i] = in[q][i].i >= 0 ? adj[in[q][i].i] : 0.0;
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return bad ? -4 : 0;
+}
+
 }  // extern "C"
