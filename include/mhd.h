@@ -150,6 +150,52 @@ long long mhd_launch_count(const mhd_ctx* ctx);
 /* Static text for a return code. */
 const char* mhd_strerror(int code);
 
+/* ---- batched ensemble ----
+ *
+ * Many independent grids advanced together (the ensemble workload of the
+ * benchmark: uneven 2D Orszag-Tang runs with their own plasma beta and Mach
+ * number).  All runs share ndim, recon, riemann, rk and the boundary kinds;
+ * each has its own size, domain, gamma, cfl, p_floor and CFL dt.  Every kernel
+ * of a stage is one launch over all runs (each block serves one run, so every
+ * run executes exactly the single-grid arithmetic), and a step is captured
+ * once in a CUDA graph and replayed.  The stream is cfgs[0].stream. */
+typedef struct mhd_batch mhd_batch;
+
+/* Validate every cfgs[r] (same scheme and boundary kinds; MHD_ERR_ARG
+ * otherwise) and allocate the device state of all runs.  Sync. */
+int mhd_batch_create(int nruns, const mhd_config* cfgs, mhd_batch** out);
+int mhd_batch_destroy(mhd_batch* b);
+
+/* State of one run, layout and mem as in mhd_set_conserved / mhd_get_conserved.
+ * Setting resets that run's time and counters.  set: async; get: sync. */
+int mhd_batch_set_conserved(mhd_batch* b, int run, int mem, const double* const* U, const double* const* B);
+int mhd_batch_get_conserved(mhd_batch* b, int run, int mem, double* const* U, double* const* B);
+
+/* Advance every run nsteps steps, each run with its own CFL dt computed on the
+ * device.  Every run must have a state (MHD_ERR_STATE).  Async. */
+int mhd_batch_step(mhd_batch* b, int nsteps);
+
+/* Choose the sweep segment length (faces a thread marches; shorter segments
+ * give more threads, longer ones fewer repeated Riemann solves) for the runs
+ * of at most 128^2 cells and for the larger ones, by timing two steps of each
+ * of 16 candidates on the current states, which are restored afterwards.
+ * Writes the choice (either pointer may be NULL).  Sync; allocates a
+ * temporary copy of the states. */
+int mhd_batch_autotune(mhd_batch* b, int* seglen_small, int* seglen_large);
+
+/* Set the two segment lengths directly (>= 1).  Sync. */
+int mhd_batch_set_seglen(mhd_batch* b, int seglen_small, int seglen_large);
+
+/* Simulation time of every run (t_out[nruns]).  Sync. */
+int mhd_batch_get_times(mhd_batch* b, double* t_out);
+
+/* First device-side error of any run (as mhd_status, with *bad_run the run's
+ * index, -1 if none).  Sync; does not clear. */
+int mhd_batch_status(mhd_batch* b, int* bad_run, long long* bad_cell);
+
+/* Kernel launches issued by the batch so far (graph replays count their kernels). */
+long long mhd_batch_launch_count(const mhd_batch* b);
+
 /* ---- allocation-free variant ----
  *
  * For callers that must not allocate device memory: for example code whose

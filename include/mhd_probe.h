@@ -33,6 +33,10 @@ extern "C" {
  * the launch counts.  Sync. */
 int mhd_profile_steps(mhd_ctx* ctx, int nsteps, double* ms_out, int* launches_out);
 
+/* As mhd_profile_steps, for a batched ensemble (mhd_batch_step's kernels). */
+typedef struct mhd_batch mhd_batch;
+int mhd_batch_profile_steps(mhd_batch* b, int nsteps, double* ms_out, int* launches_out);
+
 /* Measure the device's FP64 fused multiply-add throughput on the current
  * device: every SM runs independent chains of dependent DFMA for about
  * 20 ms; *gflops_out = 2 * DFMA per second / 1e9.  Sync; allocates and frees

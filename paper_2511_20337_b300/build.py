@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 SO = os.path.join(HERE, "libmhd.so")
-SOURCES = ["mhd_api.cu"]
-DEPS = ["mhd_math.cuh", "mhd_kernels.cuh"]
+SOURCES = ["mhd_api.cu", "mhd_batch.cu"]
+DEPS = ["mhd_math.cuh", "mhd_kernels.cuh", "mhd_host.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,7 +37,7 @@ def needs_build():
 def build(force=False, verbose=False):
     if not force and not needs_build():
         return SO
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-shared",
            "-I", INCLUDE, "-I", CSRC, "-cudart", "static"]
     if verbose:
         cmd += ["-Xptxas", "-v"]

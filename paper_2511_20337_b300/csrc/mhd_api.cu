@@ -8,6 +8,7 @@
 #include <new>
 
 #include "mhd.h"
+#include "mhd_host.cuh"
 #include "mhd_kernels.cuh"
 #include "mhd_probe.h"
 
@@ -41,77 +42,11 @@ struct mhd_ctx {
 
 namespace {
 
-int cuda_err(cudaError_t e) {
-  if (e == cudaSuccess) return MHD_OK;
-  if (e == cudaErrorMemoryAllocation) return MHD_ERR_OOM;
-  return MHD_ERR_CUDA;
-}
-#define CK(x)                         \
-  do {                                \
-    cudaError_t e_ = (x);             \
-    if (e_ != cudaSuccess) return cuda_err(e_); \
-  } while (0)
-
 void prof_mark(mhd_ctx* c, int cls) {
   if (!c->prof_on || c->prof_n >= 128) return;
   cudaEventRecord(c->prof_ev[c->prof_n], c->stream);
   c->prof_cls[c->prof_n] = cls;
   c->prof_n++;
-}
-
-int blocks_for(long long work, int threads, int cap = 148 * 32) {
-  long long b = (work + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
-}
-
-int validate(const mhd_config* c) {
-  if (!c) return MHD_ERR_ARG;
-  if (c->ndim != 2 && c->ndim != 3) return MHD_ERR_ARG;
-  if (c->nx < 1 || c->ny < 1 || (c->ndim == 3 && c->nz < 1)) return MHD_ERR_ARG;
-  for (int d = 0; d < c->ndim; d++)
-    if (!(c->x1[d] > c->x0[d])) return MHD_ERR_ARG;
-  if (!(c->gamma > 1.0)) return MHD_ERR_ARG;
-  if (c->recon < MHD_RECON_PLM || c->recon > MHD_RECON_PPM) return MHD_ERR_ARG;
-  if (c->riemann != MHD_RIEMANN_HLL && c->riemann != MHD_RIEMANN_HLLD) return MHD_ERR_ARG;
-  if (c->rk != 2 && c->rk != 3) return MHD_ERR_ARG;
-  if (!(c->cfl > 0.0)) return MHD_ERR_ARG;
-  if (!(c->p_floor >= 0.0)) return MHD_ERR_ARG;
-  for (int d = 0; d < c->ndim; d++) {
-    for (int s = 0; s < 2; s++)
-      if (c->bc[2 * d + s] != MHD_BC_PERIODIC && c->bc[2 * d + s] != MHD_BC_OUTFLOW) return MHD_ERR_ARG;
-    if ((c->bc[2 * d] == MHD_BC_PERIODIC) != (c->bc[2 * d + 1] == MHD_BC_PERIODIC)) return MHD_ERR_ARG;
-  }
-  return MHD_OK;
-}
-
-Grid make_grid(const mhd_config* c) {
-  Grid g{};
-  g.ndim = c->ndim;
-  g.n[0] = c->nx;
-  g.n[1] = c->ny;
-  g.n[2] = c->ndim == 3 ? c->nz : 1;
-  g.G = c->recon == MHD_RECON_PLM ? 2 : 3;
-  g.ext[0] = g.n[0] + 2 * g.G + 1;
-  g.ext[1] = g.n[1] + 2 * g.G + 1;
-  g.ext[2] = c->ndim == 3 ? g.n[2] + 2 * g.G + 1 : 1;
-  g.sy = g.ext[0];
-  g.sz = g.ext[0] * g.ext[1];
-  int Gz = c->ndim == 3 ? g.G : 0;
-  g.origin = Gz * g.sz + g.G * g.sy + g.G;
-  for (int d = 0; d < 3; d++) {
-    double x0 = d < c->ndim ? c->x0[d] : 0.0, x1 = d < c->ndim ? c->x1[d] : 1.0;
-    g.dx[d] = (x1 - x0) / g.n[d];
-    g.idx[d] = 1.0 / g.dx[d];
-    g.periodic[d] = d < c->ndim ? (c->bc[2 * d] == MHD_BC_PERIODIC) : 1;
-  }
-  g.gamma = c->gamma;
-  g.gm1 = c->gamma - 1.0;
-  g.igm1 = 1.0 / (c->gamma - 1.0);
-  g.cfl = c->cfl;
-  g.p_floor = c->p_floor;
-  return g;
 }
 
 // --- launch helpers ---
@@ -224,41 +159,6 @@ void run_step(mhd_ctx* c, bool device_dt) {
   for (int s = 0; s < c->cfg.rk; s++) run_stage(c, s, device_dt && s == 0);
 }
 
-void reset_scalars_host(DevScalars* h) {
-  memset(h, 0, sizeof(*h));
-  h->bad_cell = LLONG_MAX;
-}
-
-// cudaMemcpy3D between the caller's dense array (extents e[3]) and the
-// interior of a padded device field.
-int copy_field(mhd_ctx* c, double* field, const double* ext_ptr, double* ext_out, const int e[3], bool to_device) {
-  const Grid& g = c->g;
-  cudaMemcpy3DParms p{};
-  cudaPitchedPtr dense = make_cudaPitchedPtr(to_device ? (void*)ext_ptr : (void*)ext_out, (size_t)e[0] * 8, e[0], e[1]);
-  cudaPitchedPtr padded = make_cudaPitchedPtr((void*)field, (size_t)g.ext[0] * 8, g.ext[0], g.ext[1]);
-  int Gz = g.ndim == 3 ? g.G : 0;
-  if (to_device) {
-    p.srcPtr = dense;
-    p.dstPtr = padded;
-    p.dstPos = make_cudaPos((size_t)g.G * 8, g.G, Gz);
-  } else {
-    p.srcPtr = padded;
-    p.srcPos = make_cudaPos((size_t)g.G * 8, g.G, Gz);
-    p.dstPtr = dense;
-  }
-  p.extent = make_cudaExtent((size_t)e[0] * 8, e[1], e[2]);
-  p.kind = cudaMemcpyDefault;
-  CK(cudaMemcpy3DAsync(&p, c->stream));
-  return MHD_OK;
-}
-
-void slot_extents(const Grid& g, int slot, int e[3]) {
-  e[0] = g.n[0];
-  e[1] = g.n[1];
-  e[2] = g.n[2];
-  if (slot >= 5 && slot - 5 < g.ndim) e[slot - 5] += 1;
-}
-
 }  // namespace
 
 extern "C" {
@@ -351,7 +251,7 @@ static int set_common_faces(mhd_ctx* c, const double* const* B) {
   for (int q = 5; q < 8; q++) {
     int e[3];
     slot_extents(c->g, q, e);
-    int rc = copy_field(c, c->U[0].q[q], B[q - 5], nullptr, e, true);
+    int rc = copy_field(c->g, c->stream, c->U[0].q[q], B[q - 5], nullptr, e, true);
     if (rc) return rc;
   }
   return MHD_OK;
@@ -374,7 +274,7 @@ int mhd_set_conserved(mhd_ctx* c, int mem, const double* const* U, const double*
   for (int q = 0; q < 5; q++) {
     int e[3];
     slot_extents(c->g, q, e);
-    int rc = copy_field(c, c->U[0].q[q], U[q], nullptr, e, true);
+    int rc = copy_field(c->g, c->stream, c->U[0].q[q], U[q], nullptr, e, true);
     if (rc) return rc;
   }
   int rc = set_common_faces(c, B);
@@ -391,7 +291,7 @@ int mhd_set_prim(mhd_ctx* c, int mem, const double* rho, const double* const* v,
     if (!cells[q]) return MHD_ERR_ARG;
     int e[3];
     slot_extents(c->g, q, e);
-    int rc = copy_field(c, c->U[0].q[q], cells[q], nullptr, e, true);
+    int rc = copy_field(c->g, c->stream, c->U[0].q[q], cells[q], nullptr, e, true);
     if (rc) return rc;
   }
   int rc = set_common_faces(c, B);
@@ -430,7 +330,7 @@ int mhd_get_conserved(mhd_ctx* c, int mem, double* const* U, double* const* B) {
     if (!dst) return MHD_ERR_ARG;
     int e[3];
     slot_extents(c->g, q, e);
-    int rc = copy_field(c, c->U[0].q[q], nullptr, dst, e, false);
+    int rc = copy_field(c->g, c->stream, c->U[0].q[q], nullptr, dst, e, false);
     if (rc) return rc;
   }
   CK(cudaGetLastError());
@@ -699,7 +599,7 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   for (int q = 0; q < 8; q++) {
     int e[3];
     slot_extents(g, q, e);
-    rc = copy_field(&c, c.U[0].q[q], q < 5 ? U[q] : B[q - 5], nullptr, e, true);
+    rc = copy_field(c.g, c.stream, c.U[0].q[q], q < 5 ? U[q] : B[q - 5], nullptr, e, true);
     if (rc) return rc;
   }
   set_dt_kernel<<<1, 1, 0, c.stream>>>(c.sc, dt);
@@ -708,7 +608,7 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   for (int q = 0; q < 8; q++) {
     int e[3];
     slot_extents(g, q, e);
-    rc = copy_field(&c, c.U[0].q[q], nullptr, q < 5 ? U[q] : B[q - 5], e, false);
+    rc = copy_field(c.g, c.stream, c.U[0].q[q], nullptr, q < 5 ? U[q] : B[q - 5], e, false);
     if (rc) return rc;
   }
   CK(cudaGetLastError());

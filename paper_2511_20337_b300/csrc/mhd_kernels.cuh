@@ -61,104 +61,119 @@ __device__ __forceinline__ int wrap(int g, int n) {
 }
 
 // Periodic pass along axis d: every slot at d-index in [-G,-1] U [n, n+G].
-__global__ void ghost_periodic_kernel(Grid g, F8 S, int d) {
+__host__ __device__ __forceinline__ long long ghost_layers_work(const Grid& g, int d) {
   int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-  int e1 = g.hi(t1) - g.lo(t1) + 1, e2 = g.hi(t2) - g.lo(t2) + 1;
+  return (long long)(g.hi(t1) - g.lo(t1) + 1) * (g.hi(t2) - g.lo(t2) + 1) * (2 * g.G + 1);
+}
+__device__ __forceinline__ void ghost_periodic_item(const Grid& g, const F8& S, int d, long long id) {
+  int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  int e1 = g.hi(t1) - g.lo(t1) + 1;
   int nl = 2 * g.G + 1;
-  long long total = (long long)e1 * e2 * nl;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    int l = (int)(id % nl);
-    long long r = id / nl;
-    int a = (int)(r % e1) + g.lo(t1);
-    int b = (int)(r / e1) + g.lo(t2);
-    int gi = l < g.G ? l - g.G : g.n[d] + (l - g.G);
-    int x[3];
-    x[d] = gi;
-    x[t1] = a;
-    x[t2] = b;
-    int dst = g.at(x[0], x[1], x[2]);
-    x[d] = wrap(gi, g.n[d]);
-    int src = g.at(x[0], x[1], x[2]);
+  int l = (int)(id % nl);
+  long long r = id / nl;
+  int a = (int)(r % e1) + g.lo(t1);
+  int b = (int)(r / e1) + g.lo(t2);
+  int gi = l < g.G ? l - g.G : g.n[d] + (l - g.G);
+  int x[3];
+  x[d] = gi;
+  x[t1] = a;
+  x[t2] = b;
+  int dst = g.at(x[0], x[1], x[2]);
+  x[d] = wrap(gi, g.n[d]);
+  int src = g.at(x[0], x[1], x[2]);
 #pragma unroll
-    for (int q = 0; q < 8; q++) S.q[q][dst] = S.q[q][src];
-  }
+  for (int q = 0; q < 8; q++) S.q[q][dst] = S.q[q][src];
+}
+static __global__ void ghost_periodic_kernel(Grid g, F8 S, int d) {
+  const long long total = ghost_layers_work(g, d);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    ghost_periodic_item(g, S, d, id);
 }
 
 // Outflow pass along axis d, part 1: zero-gradient copies of every slot except
 // the normal face field (d-index -1..-G from 0; n..n+G from n-1).
-__global__ void ghost_outflow_copy_kernel(Grid g, F8 S, int d) {
+__device__ __forceinline__ void ghost_outflow_copy_item(const Grid& g, const F8& S, int d, long long id) {
   int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-  int e1 = g.hi(t1) - g.lo(t1) + 1, e2 = g.hi(t2) - g.lo(t2) + 1;
+  int e1 = g.hi(t1) - g.lo(t1) + 1;
   int nl = 2 * g.G + 1;
-  long long total = (long long)e1 * e2 * nl;
   int qn = (d < g.ndim) ? 5 + d : -1;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    int l = (int)(id % nl);
-    long long r = id / nl;
-    int a = (int)(r % e1) + g.lo(t1);
-    int b = (int)(r / e1) + g.lo(t2);
-    int gi = l < g.G ? l - g.G : g.n[d] + (l - g.G);
-    int x[3];
-    x[d] = gi;
-    x[t1] = a;
-    x[t2] = b;
-    int dst = g.at(x[0], x[1], x[2]);
-    x[d] = gi < 0 ? 0 : g.n[d] - 1;
-    int src = g.at(x[0], x[1], x[2]);
+  int l = (int)(id % nl);
+  long long r = id / nl;
+  int a = (int)(r % e1) + g.lo(t1);
+  int b = (int)(r / e1) + g.lo(t2);
+  int gi = l < g.G ? l - g.G : g.n[d] + (l - g.G);
+  int x[3];
+  x[d] = gi;
+  x[t1] = a;
+  x[t2] = b;
+  int dst = g.at(x[0], x[1], x[2]);
+  x[d] = gi < 0 ? 0 : g.n[d] - 1;
+  int src = g.at(x[0], x[1], x[2]);
 #pragma unroll
-    for (int q = 0; q < 8; q++)
-      if (q != qn) S.q[q][dst] = S.q[q][src];
-  }
+  for (int q = 0; q < 8; q++)
+    if (q != qn) S.q[q][dst] = S.q[q][src];
+}
+static __global__ void ghost_outflow_copy_kernel(Grid g, F8 S, int d) {
+  const long long total = ghost_layers_work(g, d);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    ghost_outflow_copy_item(g, S, d, id);
 }
 
 // Outflow pass along axis d, part 2: the normal face field of each ghost cell
 // from a vanishing discrete div B, marching outward from the boundary face.
-__global__ void ghost_outflow_normal_kernel(Grid g, F8 S, int d) {
+__host__ __device__ __forceinline__ long long ghost_rows_work(const Grid& g, int d) {
   int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   int e1 = g.hi(t1) - g.lo(t1) + (t1 < g.ndim ? 0 : 1);  // transverse range [-G, n+G-1]
   int e2 = g.hi(t2) - g.lo(t2) + (t2 < g.ndim ? 0 : 1);
-  long long total = (long long)e1 * e2;
+  return (long long)e1 * e2;
+}
+__device__ __forceinline__ void ghost_outflow_normal_item(const Grid& g, const F8& S, int d, long long id) {
+  int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  int e1 = g.hi(t1) - g.lo(t1) + (t1 < g.ndim ? 0 : 1);
   double* Bn = S.q[5 + d];
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    int a = (int)(id % e1) + g.lo(t1);
-    int b = (int)(id / e1) + g.lo(t2);
-    auto divT = [&](int cell) {
-      int x[3];
-      x[d] = cell;
-      x[t1] = a;
-      x[t2] = b;
-      int c = g.at(x[0], x[1], x[2]);
-      double s = 0.0;
-      bool first = true;
-      int ts[2] = {t1, t2};
-      for (int m = 0; m < 2; m++) {
-        int t = ts[m];
-        if (t >= g.ndim) continue;
-        const double* Bt = S.q[5 + t];
-        double term = d_(s_(Bt[c + g.stride(t)], Bt[c]), g.dx[t]);
-        s = first ? term : a_(s, term);
-        first = false;
-      }
-      return s;
-    };
+  int a = (int)(id % e1) + g.lo(t1);
+  int b = (int)(id / e1) + g.lo(t2);
+  auto divT = [&](int cell) {
     int x[3];
+    x[d] = cell;
     x[t1] = a;
     x[t2] = b;
-    for (int m = 1; m <= g.G; m++) {
-      x[d] = -m;
-      int c = g.at(x[0], x[1], x[2]);
-      Bn[c] = a_(Bn[c + g.stride(d)], m_(g.dx[d], divT(-m)));
+    int c = g.at(x[0], x[1], x[2]);
+    double s = 0.0;
+    bool first = true;
+    int ts[2] = {t1, t2};
+    for (int m = 0; m < 2; m++) {
+      int t = ts[m];
+      if (t >= g.ndim) continue;
+      const double* Bt = S.q[5 + t];
+      double term = d_(s_(Bt[c + g.stride(t)], Bt[c]), g.dx[t]);
+      s = first ? term : a_(s, term);
+      first = false;
     }
-    for (int m = 0; m < g.G; m++) {
-      int cell = g.n[d] + m;
-      x[d] = cell;
-      int c = g.at(x[0], x[1], x[2]);
-      Bn[c + g.stride(d)] = s_(Bn[c], m_(g.dx[d], divT(cell)));
-    }
+    return s;
+  };
+  int x[3];
+  x[t1] = a;
+  x[t2] = b;
+  for (int m = 1; m <= g.G; m++) {
+    x[d] = -m;
+    int c = g.at(x[0], x[1], x[2]);
+    Bn[c] = a_(Bn[c + g.stride(d)], m_(g.dx[d], divT(-m)));
   }
+  for (int m = 0; m < g.G; m++) {
+    int cell = g.n[d] + m;
+    x[d] = cell;
+    int c = g.at(x[0], x[1], x[2]);
+    Bn[c + g.stride(d)] = s_(Bn[c], m_(g.dx[d], divT(cell)));
+  }
+}
+static __global__ void ghost_outflow_normal_kernel(Grid g, F8 S, int d) {
+  const long long total = ghost_rows_work(g, d);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    ghost_outflow_normal_item(g, S, d, id);
 }
 
 // ---------------------------------------------------------------------------
@@ -167,80 +182,96 @@ __global__ void ghost_outflow_normal_kernel(Grid g, F8 S, int d) {
 // forms dt = cfl / max rate and adds it to the time).  Also flags interior
 // cells with a non-positive (or NaN) density or pressure.
 // ---------------------------------------------------------------------------
+template <int NDIM>
+__host__ __device__ __forceinline__ long long prim_work(const Grid& g) {
+  return (long long)(g.n[0] + 2 * g.G) * (g.n[1] + 2 * g.G) * (NDIM == 3 ? g.n[2] + 2 * g.G : 1);
+}
+// One padded cell: primitives, floor, status; returns its CFL rate (interior
+// cells, CFL pass) or 0.
 template <int NDIM, bool CFL>
-__global__ void __launch_bounds__(256) prim_kernel(Grid g, F8 S, F8 P, DevScalars* sc) {
+__device__ __forceinline__ double prim_item(const Grid& g, const F8& S, const F8& P, DevScalars* sc, long long id) {
   const int nxp = g.n[0] + 2 * g.G, nyp = g.n[1] + 2 * g.G;
-  const int nzp = NDIM == 3 ? g.n[2] + 2 * g.G : 1;
-  const long long total = (long long)nxp * nyp * nzp;
-  double lam_max = 0.0;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(id % nxp) - g.G;
-    long long r = id / nxp;
-    int j = (int)(r % nyp) - g.G;
-    int k = NDIM == 3 ? (int)(r / nyp) - g.G : 0;
-    int c = g.at(i, j, k);
-    double bx = m_(0.5, a_(S.q[5][c], S.q[5][c + 1]));
-    double by = m_(0.5, a_(S.q[6][c], S.q[6][c + g.sy]));
-    double bz = NDIM == 3 ? m_(0.5, a_(S.q[7][c], S.q[7][c + g.sz])) : S.q[7][c];
-    Prim8 V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1);
-    bool interior = i >= 0 && i < g.n[0] && j >= 0 && j < g.n[1] && k >= 0 && k < g.n[2];
-    if (V.p < g.p_floor) {  // primitives only; the conserved energy is not changed
-      V.p = g.p_floor;
-      if (interior) atomicAdd(&sc->floors, 1ull);
+  int i = (int)(id % nxp) - g.G;
+  long long r = id / nxp;
+  int j = (int)(r % nyp) - g.G;
+  int k = NDIM == 3 ? (int)(r / nyp) - g.G : 0;
+  int c = g.at(i, j, k);
+  double bx = m_(0.5, a_(S.q[5][c], S.q[5][c + 1]));
+  double by = m_(0.5, a_(S.q[6][c], S.q[6][c + g.sy]));
+  double bz = NDIM == 3 ? m_(0.5, a_(S.q[7][c], S.q[7][c + g.sz])) : S.q[7][c];
+  Prim8 V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1);
+  bool interior = i >= 0 && i < g.n[0] && j >= 0 && j < g.n[1] && k >= 0 && k < g.n[2];
+  if (V.p < g.p_floor) {  // primitives only; the conserved energy is not changed
+    V.p = g.p_floor;
+    if (interior) atomicAdd(&sc->floors, 1ull);
+  }
+  P.q[0][c] = V.rho;
+  P.q[1][c] = V.vx;
+  P.q[2][c] = V.vy;
+  P.q[3][c] = V.vz;
+  P.q[4][c] = V.bx;
+  P.q[5][c] = V.by;
+  P.q[6][c] = V.bz;
+  P.q[7][c] = V.p;
+  double lam = 0.0;
+  if (interior) {
+    if (!(V.rho > 0.0) || !(V.p > 0.0)) {
+      long long flat = ((long long)k * g.n[1] + j) * g.n[0] + i;
+      atomicExch(&sc->status, -4);
+      atomicMin((unsigned long long*)&sc->bad_cell, (unsigned long long)flat);
     }
-    P.q[0][c] = V.rho;
-    P.q[1][c] = V.vx;
-    P.q[2][c] = V.vy;
-    P.q[3][c] = V.vz;
-    P.q[4][c] = V.bx;
-    P.q[5][c] = V.by;
-    P.q[6][c] = V.bz;
-    P.q[7][c] = V.p;
-    if (interior) {
-      if (!(V.rho > 0.0) || !(V.p > 0.0)) {
-        long long flat = ((long long)k * g.n[1] + j) * g.n[0] + i;
-        atomicExch(&sc->status, -4);
-        atomicMin((unsigned long long*)&sc->bad_cell, (unsigned long long)flat);
-      }
-      if (CFL) {
-        double B2 = a_(a_(m_(V.bx, V.bx), m_(V.by, V.by)), m_(V.bz, V.bz));
-        double lam = m_(a_(fabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
-        lam = a_(lam, m_(a_(fabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
-        if (NDIM == 3) lam = a_(lam, m_(a_(fabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
-        lam_max = (lam > lam_max) ? lam : lam_max;
-      }
+    if (CFL) {
+      double B2 = a_(a_(m_(V.bx, V.bx), m_(V.by, V.by)), m_(V.bz, V.bz));
+      lam = m_(a_(fabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
+      lam = a_(lam, m_(a_(fabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
+      if (NDIM == 3) lam = a_(lam, m_(a_(fabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
     }
   }
-  if (CFL) {
-    // rates are positive: their bit patterns order like unsigned integers
+  return lam;
+}
+// Block maximum of the CFL rates, folded into the grid's maximum; the last of
+// the grid's nblocks blocks forms dt = cfl / max rate and adds it to the time.
+// Every thread of the block must call this.
+__device__ __forceinline__ void cfl_block_finish(double lam_max, DevScalars* sc, double cfl, unsigned int nblocks) {
+  // rates are positive: their bit patterns order like unsigned integers
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lam_max = fmax(lam_max, __shfl_xor_sync(0xffffffffu, lam_max, o));
-    __shared__ double wmax[8];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) wmax[wid] = lam_max;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double m = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmax(m, wmax[w]);
-      atomicMax(&sc->lmax_bits, (unsigned long long)__double_as_longlong(m));
+  for (int o = 16; o > 0; o >>= 1) lam_max = fmax(lam_max, __shfl_xor_sync(0xffffffffu, lam_max, o));
+  __shared__ double wmax[8];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wmax[wid] = lam_max;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmax(m, wmax[w]);
+    atomicMax(&sc->lmax_bits, (unsigned long long)__double_as_longlong(m));
+    __threadfence();
+    unsigned int ticket = atomicAdd(&sc->blocks_done, 1u);
+    if (ticket == nblocks - 1) {
       __threadfence();
-      unsigned int ticket = atomicAdd(&sc->blocks_done, 1u);
-      if (ticket == gridDim.x - 1) {
-        __threadfence();
-        double lmax = __longlong_as_double((long long)atomicAdd(&sc->lmax_bits, 0ull));
-        double dt = d_(g.cfl, lmax);
-        sc->dt = dt;
-        sc->time = sc->time + dt;
-        sc->lmax_bits = 0ull;
-        sc->blocks_done = 0u;
-      }
+      double lmax = __longlong_as_double((long long)atomicAdd(&sc->lmax_bits, 0ull));
+      double dt = d_(cfl, lmax);
+      sc->dt = dt;
+      sc->time = sc->time + dt;
+      sc->lmax_bits = 0ull;
+      sc->blocks_done = 0u;
     }
   }
 }
 
+template <int NDIM, bool CFL>
+static __global__ void __launch_bounds__(256) prim_kernel(Grid g, F8 S, F8 P, DevScalars* sc) {
+  const long long total = prim_work<NDIM>(g);
+  double lam_max = 0.0;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    double lam = prim_item<NDIM, CFL>(g, S, P, sc, id);
+    lam_max = (lam > lam_max) ? lam : lam_max;
+  }
+  if (CFL) cfl_block_finish(lam_max, sc, g.cfl, gridDim.x);
+}
+
 // Set the step size from the host value (mhd_step) and add it to the time.
-__global__ void set_dt_kernel(DevScalars* sc, double dt) {
+static __global__ void set_dt_kernel(DevScalars* sc, double dt) {
   sc->dt = dt;
   sc->time = sc->time + dt;
 }
@@ -257,9 +288,18 @@ template <int RECON> struct Stencil { static constexpr int R = RECON == RECON_PL
 
 __device__ __forceinline__ void recon_cell(int recon, const double* s, double& plus, double& minus);
 
+template <int DIR, int NDIM>
+__host__ __device__ __forceinline__ long long sweep_work(const Grid& g, int seglen) {
+  constexpr int U = (DIR == 0) ? 1 : 0;
+  constexpr int V = (DIR == 0) ? 2 : (DIR == 1 ? 2 : 1);
+  long long eu = (U < NDIM) ? g.n[U] + 2 : 1, ev = (V < NDIM) ? g.n[V] + 2 : 1;
+  return eu * ev * ((g.n[DIR] + 1 + seglen - 1) / seglen);
+}
+
 template <int DIR, int NDIM, int RECON, int RS>
-__global__ void __launch_bounds__(128) sweep_kernel(Grid g, F8 P, const double* __restrict__ Bface, L6 L,
-                                                    Ingr5x3 ING, DevScalars* sc, int seglen, int accumulate) {
+__device__ __forceinline__ void sweep_item(const Grid& g, const F8& P, const double* __restrict__ Bface, const L6& L,
+                                           const Ingr5x3& ING, DevScalars* sc, int seglen, int accumulate,
+                                           long long id) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   constexpr int R = Stencil<RECON>::R;
   constexpr int W = 2 * R + 1;  // window of cells
@@ -272,7 +312,6 @@ __global__ void __launch_bounds__(128) sweep_kernel(Grid g, F8 P, const double* 
   const int nd = g.n[DIR];
   const int nseg = (nd + 1 + seglen - 1) / seglen;
   const long long total = (long long)eu * ev * nseg;
-  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= total) return;
   const int iu = (int)(id % eu) + lu;
   const long long r = id / eu;
@@ -363,10 +402,8 @@ __global__ void __launch_bounds__(128) sweep_kernel(Grid g, F8 P, const double* 
       constexpr int NV = NDIM == 2 ? 6 : 5;
       if (NDIM == 2) dv[5] = (DIR == 0) ? F.f[5] - Fprev[5] : F.f[4] - Fprev[4];
 #pragma unroll
-      for (int q = 0; q < NV; q++) {
-        double term = -(dtdx * dv[q]);
-        L.q[q][cc] = accumulate ? L.q[q][cc] + term : term;
-      }
+      for (int q = 0; q < NV; q++)  // explicit roundings: the same in every kernel that inlines this
+        L.q[q][cc] = accumulate ? fma(-dtdx, dv[q], L.q[q][cc]) : -__dmul_rn(dtdx, dv[q]);
     }
 #pragma unroll
     for (int v = 0; v < 7; v++) {
@@ -374,6 +411,13 @@ __global__ void __launch_bounds__(128) sweep_kernel(Grid g, F8 P, const double* 
       wl[v] = plusN[v];
     }
   }
+}
+
+template <int DIR, int NDIM, int RECON, int RS>
+static __global__ void __launch_bounds__(128) sweep_kernel(Grid g, F8 P, const double* __restrict__ Bface, L6 L,
+                                                    Ingr5x3 ING, DevScalars* sc, int seglen, int accumulate) {
+  sweep_item<DIR, NDIM, RECON, RS>(g, P, Bface, L, ING, sc, seglen, accumulate,
+                                   blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,24 +459,31 @@ __device__ __forceinline__ double uct_edge(const Grid& g, const F8& S, const Ing
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(256) emf_kernel(Grid g, F8 S, Ingr5x3 ING, E3 E) {
-  const int ex = g.n[0] + 1, ey = g.n[1] + 1, ez = NDIM == 3 ? g.n[2] + 1 : 1;
-  const long long total = (long long)ex * ey * ez;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(id % ex);
-    long long r = id / ex;
-    int j = (int)(r % ey);
-    int k = (int)(r / ey);
-    int c = g.at(i, j, k);
-    if (NDIM == 2) {
-      E.e[2][c] = uct_edge<2>(g, S, ING, c);
-    } else {
-      if (k < g.n[2]) E.e[2][c] = uct_edge<2>(g, S, ING, c);  // E_z at (x-face i, y-face j, cell k)
-      if (i < g.n[0]) E.e[0][c] = uct_edge<0>(g, S, ING, c);  // E_x at (cell i, y-face j, z-face k)
-      if (j < g.n[1]) E.e[1][c] = uct_edge<1>(g, S, ING, c);  // E_y at (x-face i, cell j, z-face k)
-    }
+__host__ __device__ __forceinline__ long long edge_work(const Grid& g) {
+  return (long long)(g.n[0] + 1) * (g.n[1] + 1) * (NDIM == 3 ? g.n[2] + 1 : 1);
+}
+template <int NDIM>
+__device__ __forceinline__ void emf_item(const Grid& g, const F8& S, const Ingr5x3& ING, const E3& E, long long id) {
+  const int ex = g.n[0] + 1, ey = g.n[1] + 1;
+  int i = (int)(id % ex);
+  long long r = id / ex;
+  int j = (int)(r % ey);
+  int k = (int)(r / ey);
+  int c = g.at(i, j, k);
+  if (NDIM == 2) {
+    E.e[2][c] = uct_edge<2>(g, S, ING, c);
+  } else {
+    if (k < g.n[2]) E.e[2][c] = uct_edge<2>(g, S, ING, c);  // E_z at (x-face i, y-face j, cell k)
+    if (i < g.n[0]) E.e[0][c] = uct_edge<0>(g, S, ING, c);  // E_x at (cell i, y-face j, z-face k)
+    if (j < g.n[1]) E.e[1][c] = uct_edge<1>(g, S, ING, c);  // E_y at (x-face i, cell j, z-face k)
   }
+}
+template <int NDIM>
+static __global__ void __launch_bounds__(256) emf_kernel(Grid g, F8 S, Ingr5x3 ING, E3 E) {
+  const long long total = edge_work<NDIM>(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    emf_item<NDIM>(g, S, ING, E, id);
 }
 
 // ---------------------------------------------------------------------------
@@ -450,53 +501,57 @@ __device__ __forceinline__ double combine(int mode, double u0, double us, double
     case COMB_FIRST: return us + l;
     case COMB_RK2_FINAL: return 0.5 * ((u0 + us) + l);
     case COMB_RK3_SECOND: return 0.25 * (fma(3.0, u0, us) + l);
-    default: return (fma(2.0, us, u0) + 2.0 * l) * (1.0 / 3.0);
+    default: return fma(2.0, l, fma(2.0, us, u0)) * (1.0 / 3.0);
   }
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(256) ct_rk_kernel(Grid g, F8 U0, F8 Us, F8 Out, L6 L, E3 E,
-                                                    const DevScalars* sc, int mode) {
-  const int ex = g.n[0] + 1, ey = g.n[1] + 1, ez = NDIM == 3 ? g.n[2] + 1 : 1;
-  const long long total = (long long)ex * ey * ez;
-  const double dt = sc->dt;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(id % ex);
-    long long r = id / ex;
-    int j = (int)(r % ey);
-    int k = (int)(r / ey);
-    int c = g.at(i, j, k);
-    const bool in_x = i < g.n[0], in_y = j < g.n[1], in_z = k < g.n[2];
-    if (in_x && in_y && in_z) {
-      constexpr int NV = NDIM == 2 ? 6 : 5;
+__device__ __forceinline__ void ct_rk_item(const Grid& g, const F8& U0, const F8& Us, const F8& Out, const L6& L,
+                                           const E3& E, double dt, int mode, long long id) {
+  const int ex = g.n[0] + 1, ey = g.n[1] + 1;
+  int i = (int)(id % ex);
+  long long r = id / ex;
+  int j = (int)(r % ey);
+  int k = (int)(r / ey);
+  int c = g.at(i, j, k);
+  const bool in_x = i < g.n[0], in_y = j < g.n[1], in_z = k < g.n[2];
+  if (in_x && in_y && in_z) {
+    constexpr int NV = NDIM == 2 ? 6 : 5;
 #pragma unroll
-      for (int q = 0; q < NV; q++) {
-        int slot = q < 5 ? q : 7;
-        Out.q[slot][c] = combine(mode, U0.q[slot][c], Us.q[slot][c], L.q[q][c]);
-      }
-    }
-    // faces with normal d: evolved for d-index < n_d, or == n_d on an outflow axis
-#pragma unroll
-    for (int d = 0; d < NDIM; d++) {
-      const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-      int idx3[3] = {i, j, k};
-      bool ok = true;
-#pragma unroll
-      for (int e = 0; e < NDIM; e++) {
-        if (e == d) ok = ok && (idx3[e] < g.n[e] || !g.periodic[e]);
-        else ok = ok && idx3[e] < g.n[e];
-      }
-      if (NDIM == 2) ok = ok && k == 0;
-      if (!ok) continue;
-      const bool has1 = d1 < NDIM, has2 = d2 < NDIM;
-      double t1 = 0.0, t2 = 0.0;
-      if (has1) t1 = (E.e[d2][c + g.stride(d1)] - E.e[d2][c]) * (dt * g.idx[d1]);
-      if (has2) t2 = (E.e[d1][c + g.stride(d2)] - E.e[d1][c]) * (dt * g.idx[d2]);
-      double lb = (has1 && has2) ? t2 - t1 : (has1 ? -t1 : t2);
-      Out.q[5 + d][c] = combine(mode, U0.q[5 + d][c], Us.q[5 + d][c], lb);
+    for (int q = 0; q < NV; q++) {
+      int slot = q < 5 ? q : 7;
+      Out.q[slot][c] = combine(mode, U0.q[slot][c], Us.q[slot][c], L.q[q][c]);
     }
   }
+  // faces with normal d: evolved for d-index < n_d, or == n_d on an outflow axis
+#pragma unroll
+  for (int d = 0; d < NDIM; d++) {
+    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    int idx3[3] = {i, j, k};
+    bool ok = true;
+#pragma unroll
+    for (int e = 0; e < NDIM; e++) {
+      if (e == d) ok = ok && (idx3[e] < g.n[e] || !g.periodic[e]);
+      else ok = ok && idx3[e] < g.n[e];
+    }
+    if (NDIM == 2) ok = ok && k == 0;
+    if (!ok) continue;
+    const bool has1 = d1 < NDIM, has2 = d2 < NDIM;
+    double t1 = 0.0, t2 = 0.0;
+    if (has1) t1 = __dmul_rn(E.e[d2][c + g.stride(d1)] - E.e[d2][c], dt * g.idx[d1]);
+    if (has2) t2 = __dmul_rn(E.e[d1][c + g.stride(d2)] - E.e[d1][c], dt * g.idx[d2]);
+    double lb = (has1 && has2) ? t2 - t1 : (has1 ? -t1 : t2);
+    Out.q[5 + d][c] = combine(mode, U0.q[5 + d][c], Us.q[5 + d][c], lb);
+  }
+}
+template <int NDIM>
+static __global__ void __launch_bounds__(256) ct_rk_kernel(Grid g, F8 U0, F8 Us, F8 Out, L6 L, E3 E,
+                                                    const DevScalars* sc, int mode) {
+  const long long total = edge_work<NDIM>(g);
+  const double dt = sc->dt;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    ct_rk_item<NDIM>(g, U0, Us, Out, L, E, dt, mode, id);
 }
 
 // ---------------------------------------------------------------------------
@@ -505,7 +560,7 @@ __global__ void __launch_bounds__(256) ct_rk_kernel(Grid g, F8 U0, F8 Us, F8 Out
 // Primitive -> conserved in place on interior cells (slots 0..4 hold
 // rho, vx, vy, vz, p on entry); faces (and 2D cell Bz) already set.
 template <int NDIM>
-__global__ void prim_to_cons_kernel(Grid g, F8 S) {
+static __global__ void prim_to_cons_kernel(Grid g, F8 S) {
   const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
@@ -523,6 +578,100 @@ __global__ void prim_to_cons_kernel(Grid g, F8 S) {
     S.q[3][c] = rho * vz;
     S.q[4][c] = p * g.igm1 + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * (bx * bx + by * by + bz * bz);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernels: one launch advances a stage piece of many independent
+// grids (an ensemble).  Each block belongs to exactly one run: run r owns the
+// blocks [blk0[r], blk0[r+1]) of the launch, so a run's CFL reduction stays in
+// its own blocks and no warp mixes runs.  Every run executes the same item
+// bodies as the single-grid kernels, hence the same arithmetic.
+// ---------------------------------------------------------------------------
+struct RunDev {
+  Grid g;
+  F8 U[3];        // RK registers
+  F8 P;           // primitives
+  L6 L;           // stage increment
+  Ingr5x3 ING;    // UCT face ingredients
+  E3 E;           // edge fields
+  DevScalars* sc;
+  int seglen;     // sweep segment length of this run
+};
+
+// largest r with blk0[r] <= blockIdx.x
+__device__ __forceinline__ int block_run(const int* __restrict__ blk0, int nruns) {
+  int lo = 0, hi = nruns - 1;
+  const int b = (int)blockIdx.x;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(blk0 + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ long long block_local_id(const int* __restrict__ blk0, int r) {
+  return (long long)((int)blockIdx.x - __ldg(blk0 + r)) * blockDim.x + threadIdx.x;
+}
+
+static __global__ void __launch_bounds__(256) batch_ghost_periodic_kernel(const RunDev* __restrict__ runs,
+                                                                   const int* __restrict__ blk0, int nruns, int d,
+                                                                   int reg) {
+  const int r = block_run(blk0, nruns);
+  const RunDev& R = runs[r];
+  const long long id = block_local_id(blk0, r);
+  if (id < ghost_layers_work(R.g, d)) ghost_periodic_item(R.g, R.U[reg], d, id);
+}
+static __global__ void __launch_bounds__(256) batch_ghost_outflow_copy_kernel(const RunDev* __restrict__ runs,
+                                                                       const int* __restrict__ blk0, int nruns, int d,
+                                                                       int reg) {
+  const int r = block_run(blk0, nruns);
+  const RunDev& R = runs[r];
+  const long long id = block_local_id(blk0, r);
+  if (id < ghost_layers_work(R.g, d)) ghost_outflow_copy_item(R.g, R.U[reg], d, id);
+}
+static __global__ void __launch_bounds__(256) batch_ghost_outflow_normal_kernel(const RunDev* __restrict__ runs,
+                                                                         const int* __restrict__ blk0, int nruns,
+                                                                         int d, int reg) {
+  const int r = block_run(blk0, nruns);
+  const RunDev& R = runs[r];
+  const long long id = block_local_id(blk0, r);
+  if (id < ghost_rows_work(R.g, d)) ghost_outflow_normal_item(R.g, R.U[reg], d, id);
+}
+template <int NDIM, bool CFL>
+static __global__ void __launch_bounds__(256) batch_prim_kernel(const RunDev* __restrict__ runs,
+                                                         const int* __restrict__ blk0, int nruns, int reg) {
+  const int r = block_run(blk0, nruns);
+  const RunDev& R = runs[r];
+  const long long id = block_local_id(blk0, r);
+  double lam = 0.0;
+  if (id < prim_work<NDIM>(R.g)) lam = prim_item<NDIM, CFL>(R.g, R.U[reg], R.P, R.sc, id);
+  if (CFL) cfl_block_finish(lam, R.sc, R.g.cfl, (unsigned int)(__ldg(blk0 + r + 1) - __ldg(blk0 + r)));
+}
+template <int DIR, int NDIM, int RECON, int RS>
+static __global__ void __launch_bounds__(128) batch_sweep_kernel(const RunDev* __restrict__ runs,
+                                                          const int* __restrict__ blk0, int nruns, int reg,
+                                                          int accumulate) {
+  const int r = block_run(blk0, nruns);
+  const RunDev& R = runs[r];
+  sweep_item<DIR, NDIM, RECON, RS>(R.g, R.P, R.U[reg].q[5 + DIR], R.L, R.ING, R.sc, R.seglen, accumulate,
+                                   block_local_id(blk0, r));
+}
+template <int NDIM>
+static __global__ void __launch_bounds__(256) batch_emf_kernel(const RunDev* __restrict__ runs,
+                                                        const int* __restrict__ blk0, int nruns, int reg) {
+  const int r = block_run(blk0, nruns);
+  const RunDev& R = runs[r];
+  const long long id = block_local_id(blk0, r);
+  if (id < edge_work<NDIM>(R.g)) emf_item<NDIM>(R.g, R.U[reg], R.ING, R.E, id);
+}
+template <int NDIM>
+static __global__ void __launch_bounds__(256) batch_ct_rk_kernel(const RunDev* __restrict__ runs,
+                                                          const int* __restrict__ blk0, int nruns, int reg_s,
+                                                          int reg_out, int mode) {
+  const int r = block_run(blk0, nruns);
+  const RunDev& R = runs[r];
+  const long long id = block_local_id(blk0, r);
+  if (id < edge_work<NDIM>(R.g)) ct_rk_item<NDIM>(R.g, R.U[0], R.U[reg_s], R.U[reg_out], R.L, R.E, R.sc->dt, mode, id);
 }
 
 }  // namespace mhd

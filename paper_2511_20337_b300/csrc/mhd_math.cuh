@@ -3,10 +3,14 @@
 // solvers, and the PLM / WENO-Z / PPM reconstructions (paper §2.2).
 //
 // Two flavours of arithmetic:
-//   *_ieee : fixed-order IEEE operations (__dadd_rn & co., no contraction)
-//            for the primitive recovery and the CFL speed, so that those
-//            values are reproducible to the bit;
-//   the rest: free FMA contraction and reciprocals formed once per quantity.
+//   *_ieee : fixed-order IEEE operations (__dadd_rn & co.) for the primitive
+//            recovery and the CFL speed, so that those values match the
+//            oracle to the bit;
+//   the rest: fused multiply-adds written out as fma(), reciprocals formed
+//            once per quantity.  The library is compiled without implicit
+//            contraction, so every kernel that inlines these functions rounds
+//            them identically (the batched and single-grid paths agree to the
+//            bit).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -137,43 +141,50 @@ __device__ __forceinline__ double frsqrt(double x) {
 }
 // sqrt(x) for x >= 0 (the seed of 0 is infinite)
 __device__ __forceinline__ double fsqrt0(double x) { return gt0(x) ? fsqrt(x) : 0.0; }
+// a * b rounded once, never contracted into a neighbouring add
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 // ---------------------------------------------------------------------------
 // Sweep-frame physics.  W = (rho, u, v, w, b1, b2, p): normal velocity u,
 // transverse (v, w) and transverse field (b1, b2) in the cyclic order of the
 // sweep; bn is the staggered normal field at the face.
 // ---------------------------------------------------------------------------
-struct W7 {
-  double rho, u, v, w, b1, b2, p;
+template <class T> struct W7T {
+  T rho, u, v, w, b1, b2, p;
 };
-struct Flux7 {
-  double f[7];  // rho, m_n, m_t1, m_t2, B_t1, B_t2, E
+template <class T> struct Flux7T {
+  T f[7];  // rho, m_n, m_t1, m_t2, B_t1, B_t2, E
 };
+using W7 = W7T<double>;
+using Flux7 = Flux7T<double>;
 
 // Conserved state U = (rho, rho u, rho v, rho w, b1, b2, E) and flux of Eq. mhd
 // along the normal (F of b_n is zero), pT = p + B^2/2, plus the fast speed.
-struct Side {
-  double U[7], F[7];
-  double pT, B2, vB, cf;
+template <class T> struct SideT {
+  T U[7], F[7];
+  T pT, B2, vB, cf;
 };
+using Side = SideT<double>;
 
 // Fast magnetosonic speed cf^2 = [(G p + B^2) + sqrt((G p + B^2)^2 - 4 G p bn^2)] / (2 rho).
-__device__ __forceinline__ double fast_speed(double rho, double p, double B2, double bn2, double gamma) {
-  double gp = gamma * p;
-  double s = gp + B2;
-  double disc = fma(s, s, -(4.0 * gp) * bn2);
-  if (lt0(disc)) disc = 0.0;
-  double cf2 = (s + fsqrt0(disc)) * (0.5 * rcp(rho));
+template <class T>
+__device__ __forceinline__ T fast_speed(T rho, T p, T B2, T bn2, double gamma) {
+  T gp = mul_rn(T(gamma), p);
+  T s = gp + B2;
+  T disc = fma(s, s, -(4.0 * gp) * bn2);
+  if (lt0(disc)) disc = T(0.0);
+  T cf2 = (s + fsqrt0(disc)) * (0.5 * rcp(rho));
   return fsqrt(cf2);
 }
 
-__device__ __forceinline__ void side_state(const W7& W, double bn, double bn2, double gamma, double igm1, Side& s) {
+template <class T>
+__device__ __forceinline__ void side_state(const W7T<T>& W, T bn, T bn2, double gamma, double igm1, SideT<T>& s) {
   s.B2 = fma(W.b1, W.b1, fma(W.b2, W.b2, bn2));
   s.pT = fma(0.5, s.B2, W.p);
   s.vB = fma(W.u, bn, fma(W.v, W.b1, W.w * W.b2));
-  double v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
-  double E = fma(W.p, igm1, 0.5 * fma(W.rho, v2, s.B2));
-  double mu = W.rho * W.u;
+  T v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
+  T E = fma(W.p, T(igm1), 0.5 * fma(W.rho, v2, s.B2));
+  T mu = W.rho * W.u;
   s.U[0] = W.rho;
   s.U[1] = mu;
   s.U[2] = W.rho * W.v;
@@ -193,16 +204,18 @@ __device__ __forceinline__ void side_state(const W7& W, double bn, double bn2, d
 
 // Outer speed estimate S_L, S_R (Miyoshi & Kusano 2005) and the UCT-HLL
 // ingredients a+ = aR/(aR-aL), a- = -aL/(aR-aL), d = -aR aL/(aR-aL).
-struct Ingr {
-  double ap, am, dd, uL, uR;
+template <class T> struct IngrT {
+  T ap, am, dd, uL, uR;
 };
-__device__ __forceinline__ void speeds(const W7& L, const W7& R, const Side& sl, const Side& sr, double& SL,
-                                       double& SR, Ingr& ing) {
-  double cmax = imax_pos(sl.cf, sr.cf);
+using Ingr = IngrT<double>;
+template <class T>
+__device__ __forceinline__ void speeds(const W7T<T>& L, const W7T<T>& R, const SideT<T>& sl, const SideT<T>& sr, T& SL,
+                                       T& SR, IngrT<T>& ing) {
+  T cmax = imax_pos(sl.cf, sr.cf);
   SL = imin(L.u, R.u) - cmax;
   SR = imax(L.u, R.u) + cmax;
-  double aR = gt0(SR) ? SR : 0.0, aL = lt0(SL) ? SL : 0.0;
-  double inv = rcp(aR - aL);
+  T aR = gt0(SR) ? SR : T(0.0), aL = lt0(SL) ? SL : T(0.0);
+  T inv = rcp(aR - aL);
   ing.ap = aR * inv;
   ing.am = -aL * inv;
   ing.dd = -(aR * aL) * inv;
@@ -210,13 +223,14 @@ __device__ __forceinline__ void speeds(const W7& L, const W7& R, const Side& sl,
   ing.uR = R.u;
 }
 
-__device__ __forceinline__ void riemann_hll(const W7& L, const W7& R, double bn, double gamma, double igm1,
-                                            Flux7& F, Ingr& ing) {
-  const double bn2 = bn * bn;
-  Side sl, sr;
+template <class T>
+__device__ __forceinline__ void riemann_hll(const W7T<T>& L, const W7T<T>& R, T bn, double gamma, double igm1,
+                                            Flux7T<T>& F, IngrT<T>& ing) {
+  const T bn2 = bn * bn;
+  SideT<T> sl, sr;
   side_state(L, bn, bn2, gamma, igm1, sl);
   side_state(R, bn, bn2, gamma, igm1, sr);
-  double SL, SR;
+  T SL, SR;
   speeds(L, R, sl, sr, SL, SR, ing);
   if (ge0(SL)) {
 #pragma unroll
@@ -225,8 +239,8 @@ __device__ __forceinline__ void riemann_hll(const W7& L, const W7& R, double bn,
 #pragma unroll
     for (int q = 0; q < 7; q++) F.f[q] = sr.F[q];
   } else {
-    double inv = rcp(SR - SL);
-    double sls = SR * SL;
+    T inv = rcp(SR - SL);
+    T sls = SR * SL;
 #pragma unroll
     for (int q = 0; q < 7; q++) F.f[q] = fma(sls, sr.U[q] - sl.U[q], fma(SR, sl.F[q], -SL * sr.F[q])) * inv;
   }
@@ -234,21 +248,23 @@ __device__ __forceinline__ void riemann_hll(const W7& L, const W7& R, double bn,
 
 // Total field, total pressure and fast speed of one side (all that HLLD needs
 // from both sides before the contact speed is known).
-struct SideLite {
-  double B2, pT, cf;
+template <class T> struct SideLiteT {
+  T B2, pT, cf;
 };
-__device__ __forceinline__ void side_lite(const W7& W, double bn2, double gamma, SideLite& s) {
+template <class T>
+__device__ __forceinline__ void side_lite(const W7T<T>& W, T bn2, double gamma, SideLiteT<T>& s) {
   s.B2 = fma(W.b1, W.b1, fma(W.b2, W.b2, bn2));
   s.pT = fma(0.5, s.B2, W.p);
   s.cf = fast_speed(W.rho, W.p, s.B2, bn2, gamma);
 }
 // Conserved state, energy, v.B and flux of one side, given its total field and pressure.
-__device__ __forceinline__ void side_full(const W7& W, double bn, double bn2, double igm1, const SideLite& l,
-                                          double U[7], double F[7], double& vB) {
+template <class T>
+__device__ __forceinline__ void side_full(const W7T<T>& W, T bn, T bn2, double igm1, const SideLiteT<T>& l, T U[7],
+                                          T F[7], T& vB) {
   vB = fma(W.u, bn, fma(W.v, W.b1, W.w * W.b2));
-  double v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
-  double E = fma(W.p, igm1, 0.5 * fma(W.rho, v2, l.B2));
-  double mu = W.rho * W.u;
+  T v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
+  T E = fma(W.p, T(igm1), 0.5 * fma(W.rho, v2, l.B2));
+  T mu = W.rho * W.u;
   U[0] = W.rho;
   U[1] = mu;
   U[2] = W.rho * W.v;
@@ -270,18 +286,19 @@ __device__ __forceinline__ void side_full(const W7& W, double bn, double bn2, do
 // give their total pressure and fast speed; the star transverse states of
 // both sides feed the double-star state; conserved states, energies and the
 // flux are assembled only on the side of the contact that holds x/t = 0.
-__device__ __forceinline__ void riemann_hlld(const W7& L, const W7& R, double bn, double gamma, double igm1,
-                                             Flux7& F, Ingr& ing) {
-  const double bn2 = bn * bn;
-  SideLite ll, lr;
+template <class T>
+__device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T bn, double gamma, double igm1,
+                                             Flux7T<T>& F, IngrT<T>& ing) {
+  const T bn2 = bn * bn;
+  SideLiteT<T> ll, lr;
   side_lite(L, bn2, gamma, ll);
   side_lite(R, bn2, gamma, lr);
   // outer speeds and UCT ingredients
-  double cmax = imax_pos(ll.cf, lr.cf);
-  double SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
+  T cmax = imax_pos(ll.cf, lr.cf);
+  T SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
   {
-    double aR = gt0(SR) ? SR : 0.0, aL = lt0(SL) ? SL : 0.0;
-    double inv = rcp(aR - aL);
+    T aR = gt0(SR) ? SR : T(0.0), aL = lt0(SL) ? SL : T(0.0);
+    T inv = rcp(aR - aL);
     ing.ap = aR * inv;
     ing.am = -aL * inv;
     ing.dd = -(aR * aL) * inv;
@@ -290,80 +307,80 @@ __device__ __forceinline__ void riemann_hlld(const W7& L, const W7& R, double bn
   }
   if (gt0(SL) || lt0(SR)) {  // supersonic: the upwind physical flux
     const bool up_left = gt0(SL);
-    double U[7], vB;
+    T U[7], vB;
     side_full(up_left ? L : R, bn, bn2, igm1, up_left ? ll : lr, U, F.f, vB);
     return;
   }
-  double sdL = SL - L.u, sdR = SR - R.u;
-  double rsL = sdL * L.rho, rsR = sdR * R.rho;  // rho (S - u)
-  double iden = rcp(rsR - rsL);
-  double SM = ((fma(rsR, R.u, -rsL * L.u) - lr.pT) + ll.pT) * iden;
-  double pTs = fma((L.rho * rsR) * sdL, R.u - L.u, fma(rsR, ll.pT, -rsL * lr.pT)) * iden;
+  T sdL = SL - L.u, sdR = SR - R.u;
+  T rsL = sdL * L.rho, rsR = sdR * R.rho;  // rho (S - u)
+  T iden = rcp(rsR - rsL);
+  T SM = ((fma(rsR, R.u, -rsL * L.u) - lr.pT) + ll.pT) * iden;
+  T pTs = fma((L.rho * rsR) * sdL, R.u - L.u, fma(rsR, ll.pT, -rsL * lr.pT)) * iden;
 
   // star transverse states of both sides
-  double smL = SL - SM, smR = SR - SM;
-  double ismL = rcp(smL), ismR = rcp(smR);
-  double rhosL = rsL * ismL, rhosR = rsR * ismR;
-  double vsL, wsL, b1sL, b2sL, vsR, wsR, b1sR, b2sR;
+  T smL = SL - SM, smR = SR - SM;
+  T ismL = rcp(smL), ismR = rcp(smR);
+  T rhosL = rsL * ismL, rhosR = rsR * ismR;
+  T vsL, wsL, b1sL, b2sL, vsR, wsR, b1sR, b2sR;
   {
-    double rsm = rsL * smL, D = rsm - bn2;
+    T rsm = mul_rn(rsL, smL), D = rsm - bn2;
     if (lt_pos(fabs(D), kHlldDegenEps * rsm)) {
       vsL = L.v; wsL = L.w; b1sL = L.b1; b2sL = L.b2;
     } else {
-      double iD = rcp(D);
-      double cv = (bn * (SM - L.u)) * iD;
+      T iD = rcp(D);
+      T cv = (bn * (SM - L.u)) * iD;
       vsL = fma(-L.b1, cv, L.v);
       wsL = fma(-L.b2, cv, L.w);
-      double cb = fma(rsL, sdL, -bn2) * iD;
+      T cb = fma(rsL, sdL, -bn2) * iD;
       b1sL = L.b1 * cb;
       b2sL = L.b2 * cb;
     }
   }
   {
-    double rsm = rsR * smR, D = rsm - bn2;
+    T rsm = mul_rn(rsR, smR), D = rsm - bn2;
     if (lt_pos(fabs(D), kHlldDegenEps * rsm)) {
       vsR = R.v; wsR = R.w; b1sR = R.b1; b2sR = R.b2;
     } else {
-      double iD = rcp(D);
-      double cv = (bn * (SM - R.u)) * iD;
+      T iD = rcp(D);
+      T cv = (bn * (SM - R.u)) * iD;
       vsR = fma(-R.b1, cv, R.v);
       wsR = fma(-R.b2, cv, R.w);
-      double cb = fma(rsR, sdR, -bn2) * iD;
+      T cb = fma(rsR, sdR, -bn2) * iD;
       b1sR = R.b1 * cb;
       b2sR = R.b2 * cb;
     }
   }
   // the side of the contact that contains x/t = 0
   const bool left = ge0(SM);
-  const W7& A = left ? L : R;
-  double Ua[7], vBa;
+  const W7T<T>& A = left ? L : R;
+  T Ua[7], vBa;
   side_full(A, bn, bn2, igm1, left ? ll : lr, Ua, F.f, vBa);
-  const double pTa = left ? ll.pT : lr.pT;
-  const double S = left ? SL : SR, sd = left ? sdL : sdR, ism = left ? ismL : ismR;
-  const double rhos = left ? rhosL : rhosR;
-  const double vs = left ? vsL : vsR, ws = left ? wsL : wsR, b1s = left ? b1sL : b1sR, b2s = left ? b2sL : b2sR;
-  double vBs = fma(SM, bn, fma(vs, b1s, ws * b2s));
-  double Es = (fma(sd, Ua[6], -pTa * A.u) + fma(pTs, SM, bn * (vBa - vBs))) * ism;
-  double Us[7] = {rhos, rhos * SM, rhos * vs, rhos * ws, b1s, b2s, Es};
+  const T pTa = left ? ll.pT : lr.pT;
+  const T S = left ? SL : SR, sd = left ? sdL : sdR, ism = left ? ismL : ismR;
+  const T rhos = left ? rhosL : rhosR;
+  const T vs = left ? vsL : vsR, ws = left ? wsL : wsR, b1s = left ? b1sL : b1sR, b2s = left ? b2sL : b2sR;
+  T vBs = fma(SM, bn, fma(vs, b1s, ws * b2s));
+  T Es = (fma(sd, Ua[6], -pTa * A.u) + fma(pTs, SM, bn * (vBa - vBs))) * ism;
+  T Us[7] = {rhos, rhos * SM, rhos * vs, rhos * ws, b1s, b2s, Es};
 #pragma unroll
   for (int q = 0; q < 7; q++) F.f[q] = fma(S, Us[q] - Ua[q], F.f[q]);
   // rotational (Alfven) waves, absent when the normal field vanishes
   if (!lt_pos(0.5 * bn2, kHlldBnEps * pTs)) {
-    double iqL = frsqrt(rhosL), iqR = frsqrt(rhosR);  // 1/sqrt(rho*)
-    double sqL = rhosL * iqL, sqR = rhosR * iqR;      // sqrt(rho*)
-    double abn = fabs(bn);
-    double Ss = left ? fma(-abn, iqL, SM) : fma(abn, iqR, SM);
-    bool beyond = left ? lt0(Ss) : ge0(Ss);           // x/t = 0 lies between S*_a and S_M
+    T iqL = frsqrt(rhosL), iqR = frsqrt(rhosR);  // 1/sqrt(rho*)
+    T sqL = rhosL * iqL, sqR = rhosR * iqR;      // sqrt(rho*)
+    T abn = fabs(bn);
+    T Ss = left ? fma(-abn, iqL, SM) : fma(abn, iqR, SM);
+    bool beyond = left ? lt0(Ss) : ge0(Ss);      // x/t = 0 lies between S*_a and S_M
     if (beyond) {
-      double isum = rcp(sqL + sqR);
-      double vss = fma(sqL, vsL, fma(sqR, vsR, times_sign(b1sR - b1sL, bn))) * isum;
-      double wss = fma(sqL, wsL, fma(sqR, wsR, times_sign(b2sR - b2sL, bn))) * isum;
-      double sq2 = sqL * sqR;
-      double b1ss = fma(sqL, b1sR, fma(sqR, b1sL, times_sign(sq2 * (vsR - vsL), bn))) * isum;
-      double b2ss = fma(sqL, b2sR, fma(sqR, b2sL, times_sign(sq2 * (wsR - wsL), bn))) * isum;
-      double vBss = fma(SM, bn, fma(vss, b1ss, wss * b2ss));
-      double sqa = left ? -sqL : sqR;
-      double Ess = fma(sqa, times_sign(vBs - vBss, bn), Es);
+      T isum = rcp(sqL + sqR);
+      T vss = fma(sqL, vsL, fma(sqR, vsR, times_sign(b1sR - b1sL, bn))) * isum;
+      T wss = fma(sqL, wsL, fma(sqR, wsR, times_sign(b2sR - b2sL, bn))) * isum;
+      T sq2 = sqL * sqR;
+      T b1ss = fma(sqL, b1sR, fma(sqR, b1sL, times_sign(sq2 * (vsR - vsL), bn))) * isum;
+      T b2ss = fma(sqL, b2sR, fma(sqR, b2sL, times_sign(sq2 * (wsR - wsL), bn))) * isum;
+      T vBss = fma(SM, bn, fma(vss, b1ss, wss * b2ss));
+      T sqa = left ? -sqL : sqR;
+      T Ess = fma(sqa, times_sign(vBs - vBss, bn), Es);
       // F += S*_a (U** - U*): the density and normal momentum are continuous
       F.f[2] = fma(Ss, fma(rhos, vss, -Us[2]), F.f[2]);
       F.f[3] = fma(Ss, fma(rhos, wss, -Us[3]), F.f[3]);
@@ -417,7 +434,7 @@ __device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, dou
     double q0 = fma(2.0, a0, fma(-7.0, a1, 11.0 * a2));
     double q1 = fma(5.0, a2, fma(2.0, a3, -a1));
     double q2 = fma(2.0, a2, fma(5.0, a3, -a4));
-    double al0 = 0.1 * g0, al1 = 0.6 * g1, al2 = 0.3 * g2;
+    double al0 = __dmul_rn(0.1, g0), al1 = __dmul_rn(0.6, g1), al2 = __dmul_rn(0.3, g2);
     plus = fma(al0, q0, fma(al1, q1, al2 * q2)) * rcp(6.0 * ((al0 + al1) + al2));
   }
   // minus face: the mirrored stencils, indicators beta_2, beta_1, beta_0
@@ -425,7 +442,7 @@ __device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, dou
     double q0 = fma(2.0, a4, fma(-7.0, a3, 11.0 * a2));
     double q1 = fma(5.0, a2, fma(2.0, a1, -a3));
     double q2 = fma(2.0, a2, fma(5.0, a1, -a0));
-    double al0 = 0.1 * g2, al1 = 0.6 * g1, al2 = 0.3 * g0;
+    double al0 = __dmul_rn(0.1, g2), al1 = __dmul_rn(0.6, g1), al2 = __dmul_rn(0.3, g0);
     minus = fma(al0, q0, fma(al1, q1, al2 * q2)) * rcp(6.0 * ((al0 + al1) + al2));
   }
 }
@@ -447,7 +464,7 @@ __device__ __forceinline__ void recon_ppm(double s0, double s1, double s2, doubl
     vm = s2;
   } else {
     double dv = vp - vm;
-    double v6 = 6.0 * (s2 - 0.5 * (vm + vp));
+    double v6 = 6.0 * fma(-0.5, vm + vp, s2);
     double x = dv * v6, y = dv * dv;
     if (order_key(y) < order_key(x)) vm = fma(3.0, s2, -2.0 * vp);
     else if (order_key(x) < order_key(-y)) vp = fma(3.0, s2, -2.0 * vm);

@@ -29,7 +29,9 @@ KEYS = ("rho", "mx", "my", "mz", "E", "b0", "b1", "b2")
 EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mhd_get_conserved",
            "mhd_set_boundaries", "mhd_cfl_dt", "mhd_step", "mhd_advance", "mhd_get_time", "mhd_last_dt",
            "mhd_status", "mhd_launch_count", "mhd_strerror", "mhd_counters", "mhd_profile_steps", "mhd_probe_fp64",
-           "mhd_step_noalloc")
+           "mhd_step_noalloc", "mhd_batch_create", "mhd_batch_destroy", "mhd_batch_set_conserved",
+           "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
+           "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps")
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 
 
@@ -79,6 +81,17 @@ def lib():
             "mhd_profile_steps": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
             "mhd_probe_fp64": (I, [ctypes.POINTER(D)]),
             "mhd_step_noalloc": (I, [ctypes.POINTER(mhd_config), DPP, DPP, D]),
+            "mhd_batch_create": (I, [I, ctypes.POINTER(mhd_config), ctypes.POINTER(P)]),
+            "mhd_batch_destroy": (I, [P]),
+            "mhd_batch_set_conserved": (I, [P, I, I, DPP, DPP]),
+            "mhd_batch_get_conserved": (I, [P, I, I, DPP, DPP]),
+            "mhd_batch_step": (I, [P, I]),
+            "mhd_batch_autotune": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "mhd_batch_set_seglen": (I, [P, I, I]),
+            "mhd_batch_get_times": (I, [P, ctypes.POINTER(D)]),
+            "mhd_batch_status": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)]),
+            "mhd_batch_launch_count": (ctypes.c_longlong, [P]),
+            "mhd_batch_profile_steps": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -268,3 +281,83 @@ def step_noalloc(cfg, state, dt, stream=None):
     c = make_config(cfg, stream)
     _check(lib().mhd_step_noalloc(ctypes.byref(c), _ptr_array(arrs[:5]), _ptr_array(arrs[5:]), float(dt)),
            "mhd_step_noalloc")
+
+
+class Batch:
+    """An ensemble of independent grids of one scheme advanced together by
+    libmhd's batched entry points (one launch per kernel over all runs)."""
+
+    def __init__(self, cfgs, states=None, stream=None):
+        self.cfgs = [dict(c) for c in cfgs]
+        self.shapes = [state_shapes(c) for c in cfgs]
+        arr = (mhd_config * len(cfgs))()
+        for i, c in enumerate(cfgs):
+            arr[i] = make_config(c, stream if i == 0 else None)
+        h = ctypes.c_void_p()
+        _check(lib().mhd_batch_create(len(cfgs), arr, ctypes.byref(h)), "mhd_batch_create")
+        self.h = h
+        self._keep = {}
+        if states is not None:
+            for r, st in enumerate(states):
+                self.set_conserved(r, st)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mhd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_conserved(self, run, state):
+        arrs = [state[k] for k in KEYS]
+        dev = _is_device(arrs[0])
+        if not dev:
+            arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(s)) for a, s in
+                    zip(arrs, self.shapes[run])]
+        self._keep[run] = arrs
+        _check(lib().mhd_batch_set_conserved(self.h, run, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
+                                             _ptr_array(arrs[5:])), "mhd_batch_set_conserved")
+
+    def get_conserved(self, run, out=None):
+        if out is None:
+            out = {k: np.zeros(s) for k, s in zip(KEYS, self.shapes[run])}
+        arrs = [out[k] for k in KEYS]
+        dev = _is_device(arrs[0])
+        _check(lib().mhd_batch_get_conserved(self.h, run, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
+                                             _ptr_array(arrs[5:])), "mhd_batch_get_conserved")
+        return out
+
+    def step(self, nsteps):
+        _check(lib().mhd_batch_step(self.h, int(nsteps)), "mhd_batch_step")
+
+    def autotune(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().mhd_batch_autotune(self.h, ctypes.byref(a), ctypes.byref(b)), "mhd_batch_autotune")
+        return a.value, b.value
+
+    def set_seglen(self, small, large):
+        _check(lib().mhd_batch_set_seglen(self.h, int(small), int(large)), "mhd_batch_set_seglen")
+
+    def times(self):
+        t = (ctypes.c_double * len(self.cfgs))()
+        _check(lib().mhd_batch_get_times(self.h, t), "mhd_batch_get_times")
+        return list(t)
+
+    def status(self):
+        r, c = ctypes.c_int(), ctypes.c_longlong()
+        rc = lib().mhd_batch_status(self.h, ctypes.byref(r), ctypes.byref(c))
+        return rc, r.value, c.value
+
+    @property
+    def launches(self):
+        return lib().mhd_batch_launch_count(self.h)
+
+    def profile_steps(self, nsteps):
+        ms = (ctypes.c_double * len(KCLASSES))()
+        cnt = (ctypes.c_int * len(KCLASSES))()
+        _check(lib().mhd_batch_profile_steps(self.h, int(nsteps), ms, cnt), "mhd_batch_profile_steps")
+        return {k: ms[i] for i, k in enumerate(KCLASSES)}, {k: cnt[i] for i, k in enumerate(KCLASSES)}
