@@ -196,6 +196,54 @@ int mhd_batch_status(mhd_batch* b, int* bad_run, long long* bad_cell);
 /* Kernel launches issued by the batch so far (graph replays count their kernels). */
 long long mhd_batch_launch_count(const mhd_batch* b);
 
+/* ---- adjoint ----
+ *
+ * Gradient of a functional J of the final state with respect to the initial
+ * state, by the transpose of every kernel of the step (the discrete adjoint:
+ * exact up to rounding for the scheme as executed, with the limiter, wave-fan
+ * and min/max branches the forward values take; where an argument of minmod
+ * is exactly zero, minmod's derivative is taken as zero).  The step sizes are
+ * treated as constants (frozen): the CFL maximum is not differentiated.
+ *   MHD_FUNC_MAGNETIC_ENERGY  J = 1/2 sum_cells |B_c|^2 dV, B_c the mean of
+ *                             the cell's two faces (2D B_z: the cell value);
+ *   MHD_FUNC_MISFIT           J = 1/2 sum_cells sum_q (U_q - T_q)^2 dV over
+ *                             rho, m_x, m_y, m_z, E (2D: and the cell B_z).
+ * Supported: PLM reconstruction, HLL or HLLD, RK2 or RK3, periodic on every
+ * axis with at least 2G+1 = 5 cells (MHD_ERR_ARG otherwise). */
+#define MHD_FUNC_MAGNETIC_ENERGY 0
+#define MHD_FUNC_MISFIT          1
+
+/* Run nsteps steps from the context's state, evaluate J and its gradient with
+ * respect to that initial state, and keep the gradient in the context.
+ *   dts:        host array of nsteps step sizes, or NULL for the CFL dt of
+ *               every step (computed in the forward pass, then frozen);
+ *   ckpt_every: k >= 1; the state is saved every k steps and each block of k
+ *               steps recomputed once in the reverse pass (device memory:
+ *               ceil(nsteps/k) + k*rk + 1 states plus ~128 scratch fields);
+ *   target:     for MHD_FUNC_MISFIT, 5 (3D) or 6 (2D: + B_z) cell arrays in
+ *               the layout of mhd_set_conserved, host or device per mem;
+ *               ignored (may be NULL) otherwise;
+ *   J_out, dts_out (nsteps): J and the step sizes used; may be NULL.
+ * Afterwards the context holds the final state (as after the same steps with
+ * mhd_step), its time advanced by the sum of the step sizes.  Sync;
+ * allocates the adjoint's buffers on first use (freed by mhd_destroy).
+ * MHD_ERR_UNPHYSICAL if the forward pass met a non-positive density or
+ * pressure. */
+int mhd_adjoint_run(mhd_ctx* ctx, int nsteps, const double* dts, int ckpt_every, int functional, int mem,
+                    const double* const* target, double* J_out, double* dts_out);
+
+/* The last mhd_adjoint_run's gradient with respect to the initial conserved
+ * state: gU[5] cell arrays and gB[3] face arrays (2D: gB[2] the cell B_z), in
+ * the layout of mhd_get_conserved.  The duplicate last face of a periodic axis
+ * carries 0: the whole derivative of that face sits on face 0.  MHD_ERR_STATE
+ * before a successful run.  Sync. */
+int mhd_adjoint_grad_conserved(mhd_ctx* ctx, int mem, double* const* gU, double* const* gB);
+
+/* The last mhd_adjoint_run's gradient with respect to the initial density and
+ * velocity, holding the initial pressure and magnetic field fixed (cell
+ * arrays: grad_rho, grad_v[3]).  MHD_ERR_STATE before a successful run.  Sync. */
+int mhd_adjoint_grad_prim(mhd_ctx* ctx, int mem, double* grad_rho, double* const* grad_v);
+
 /* ---- allocation-free variant ----
  *
  * For callers that must not allocate device memory: for example code whose

@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 SO = os.path.join(HERE, "libmhd.so")
-SOURCES = ["mhd_api.cu", "mhd_batch.cu"]
-DEPS = ["mhd_math.cuh", "mhd_kernels.cuh", "mhd_host.cuh"]
+SOURCES = ["mhd_api.cu", "mhd_batch.cu", "mhd_adjoint.cu"]
+DEPS = ["mhd_math.cuh", "mhd_kernels.cuh", "mhd_host.cuh", "mhd_ctx.cuh", "mhd_dual.cuh", "mhd_adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,19 +35,33 @@ def needs_build():
 
 
 def build(force=False, verbose=False):
+    """Compile each source to an object in parallel, then link the shared library."""
     if not force and not needs_build():
         return SO
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-shared",
-           "-I", INCLUDE, "-I", CSRC, "-cudart", "static"]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+             "-I", CSRC]
     if verbose:
-        cmd += ["-Xptxas", "-v"]
-    cmd += [os.path.join(CSRC, s) for s in SOURCES] + ["-o", SO + ".tmp"]
-    res = subprocess.run(cmd, capture_output=True, text=True)
+        flags += ["-Xptxas", "-v"]
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    objs = [os.path.join(objdir, os.path.splitext(s)[0] + ".o") for s in SOURCES]
+    procs = [subprocess.Popen([nvcc(), *flags, "-c", os.path.join(CSRC, s), "-o", o], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for s, o in zip(SOURCES, objs)]
+    failed = False
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            failed = True
+            sys.stderr.write(out + err)
+        elif verbose:
+            sys.stderr.write(err)
+    if failed:
+        raise RuntimeError("nvcc failed building libmhd.so")
+    res = subprocess.run([nvcc(), *ARCH, "-shared", "-cudart", "static", *objs, "-o", SO + ".tmp"],
+                         capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed building libmhd.so")
-    if verbose:
-        sys.stderr.write(res.stderr)
+        raise RuntimeError("nvcc failed linking libmhd.so")
     os.replace(SO + ".tmp", SO)
     return SO
 

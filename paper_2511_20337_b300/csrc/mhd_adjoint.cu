@@ -1,0 +1,362 @@
+// Adjoint entry points of libmhd (declared in include/mhd.h): the gradient of
+// a final-state functional with respect to the initial state, by the
+// transpose of every kernel of the step (mhd_adjoint.cuh), with the step
+// sizes frozen.
+//
+// Schedule for n steps with checkpoints every k steps:
+//   forward   n steps on the context registers; U^0, U^k, U^2k, ... saved;
+//   reverse   for each block of k steps, last block first: recompute its
+//             steps from the checkpoint, keeping every stage input, then run
+//             the stage transposes backwards through the block.
+// Memory: ceil(n/k) + k*S + 1 states (S = RK stages) plus the scratch of the
+// transposes; work: two forward passes and one reverse pass.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mhd.h"
+#include "mhd_adjoint.cuh"
+#include "mhd_ctx.cuh"
+#include "mhd_host.cuh"
+
+using namespace mhd;
+
+namespace mhd {
+
+struct AdjointState {
+  int nsteps = 0, ckpt_every = 0, nck = 0, nstages = 0;
+  size_t fe = 0;              // elements per field
+  double* pool = nullptr;     // scratch of the transposes
+  double* states = nullptr;   // checkpoints, then the block's stage inputs
+  size_t state_count = 0;
+  F8 A[4];                    // cotangent accumulators of the stage inputs (A[3]: incoming)
+  L6 Lb;                      // cotangent of the stage increment (cells)
+  L3 LB;                      // cotangent of the CT face increment
+  E3 Eb;                      // cotangent of the edge fields
+  GE18 GE;                    // edge-local cotangents
+  F8 WbL, WbR;                // cotangents of the face states (7 used)
+  F8 Pb;                      // cotangent of the primitives
+  L6 T;                       // misfit target (padded cells)
+  double* Jcell = nullptr;
+  double* scal = nullptr;     // [0] J, [1..] recorded dt
+  std::vector<double> dts;
+  double J = 0.0;
+  bool has_grad = false;
+};
+
+void adjoint_free(mhd_ctx* c) {
+  if (!c || !c->adj) return;
+  cudaFree(c->adj->pool);
+  cudaFree(c->adj->states);
+  cudaFree(c->adj->Jcell);
+  cudaFree(c->adj->scal);
+  delete c->adj;
+  c->adj = nullptr;
+}
+
+}  // namespace mhd
+
+namespace {
+
+constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 + 3 * 18 + 8 + 8 + 8 + 6;
+
+F8 state_at(const AdjointState* a, size_t idx) {
+  F8 s;
+  for (int q = 0; q < 8; q++) s.q[q] = a->states + (idx * 8 + q) * a->fe;
+  return s;
+}
+
+int ensure_state(mhd_ctx* c, int nsteps, int k) {
+  const int S = c->cfg.rk;
+  const int nck = (nsteps + k - 1) / k;
+  const size_t need_states = (size_t)nck + (size_t)k * S + 1;
+  AdjointState* a = c->adj;
+  if (!a) {
+    a = new (std::nothrow) AdjointState();
+    if (!a) return MHD_ERR_OOM;
+    c->adj = a;
+    a->fe = c->field_elems;
+    size_t bytes = a->fe * sizeof(double) * kScratchFields;
+    if (cudaMalloc(&a->pool, bytes) != cudaSuccess) { cudaGetLastError(); adjoint_free(c); return MHD_ERR_OOM; }
+    CK(cudaMemsetAsync(a->pool, 0, bytes, c->stream));
+    double* p = a->pool;
+    auto next = [&]() { double* r = p; p += a->fe; return r; };
+    for (int r = 0; r < 4; r++)
+      for (int q = 0; q < 8; q++) a->A[r].q[q] = next();
+    for (int q = 0; q < 6; q++) a->Lb.q[q] = next();
+    for (int d = 0; d < 3; d++) a->LB.q[d] = next();
+    for (int d = 0; d < 3; d++) a->Eb.e[d] = next();
+    for (int C = 0; C < 3; C++)
+      for (int m = 0; m < 18; m++) a->GE.q[C][m] = next();
+    for (int q = 0; q < 8; q++) a->WbL.q[q] = next();
+    for (int q = 0; q < 8; q++) a->WbR.q[q] = next();
+    for (int q = 0; q < 8; q++) a->Pb.q[q] = next();
+    for (int q = 0; q < 6; q++) a->T.q[q] = next();
+    long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
+    if (cudaMalloc(&a->Jcell, sizeof(double) * ncell) != cudaSuccess) { cudaGetLastError(); adjoint_free(c); return MHD_ERR_OOM; }
+  }
+  if (a->state_count < need_states) {
+    cudaFree(a->states);
+    a->states = nullptr;
+    a->state_count = 0;
+    if (cudaMalloc(&a->states, need_states * 8 * a->fe * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return MHD_ERR_OOM;
+    }
+    a->state_count = need_states;
+  }
+  if (a->nsteps < nsteps || !a->scal) {
+    cudaFree(a->scal);
+    a->scal = nullptr;
+    if (cudaMalloc(&a->scal, sizeof(double) * (nsteps + 1)) != cudaSuccess) { cudaGetLastError(); return MHD_ERR_OOM; }
+  }
+  a->nsteps = nsteps;
+  a->ckpt_every = k;
+  a->nck = nck;
+  a->nstages = S;
+  a->has_grad = false;
+  return MHD_OK;
+}
+
+int copy_state(mhd_ctx* c, const F8& dst, const F8& src) {
+  // each register's 8 fields are contiguous
+  CK(cudaMemcpyAsync(dst.q[0], src.q[0], 8 * c->field_elems * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return MHD_OK;
+}
+
+void stage_coeffs(int rk, int s, double& c0, double& c1, double& cL) {
+  if (s == 0) { c0 = 0.0; c1 = 1.0; cL = 1.0; return; }
+  if (rk == 2) { c0 = 0.5; c1 = 0.5; cL = 0.5; return; }
+  if (s == 1) { c0 = 0.75; c1 = 0.25; cL = 0.25; return; }
+  c0 = 1.0 / 3.0; c1 = 2.0 / 3.0; cL = 2.0 / 3.0;
+}
+
+template <int NDIM, int RS, int DIR>
+void adj_dir(mhd_ctx* c, const F8& Xs, const F8& As, double dt) {
+  AdjointState* a = c->adj;
+  const Grid& g = c->g;
+  long long faces = 1, cells = 1;
+  for (int d = 0; d < 3; d++) {
+    long long ef = d == DIR ? g.n[d] + 1 : (d < NDIM ? g.n[d] + 2 : 1);
+    long long ec = d == DIR ? g.n[d] + 4 : (d < NDIM ? g.n[d] + 2 : 1);
+    faces *= ef;
+    cells *= ec;
+  }
+  adj_riemann_kernel<DIR, NDIM, RS><<<(int)((faces + 127) / 128), 128, 0, c->stream>>>(
+      g, c->P, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL, a->WbR, As.q[5 + DIR]);
+  adj_recon_kernel<DIR, NDIM><<<(int)((cells + 127) / 128), 128, 0, c->stream>>>(g, c->P, a->WbL, a->WbR, a->Pb);
+  c->launches += 2;
+}
+
+// Transpose of stage s at the stage input Xs: the cotangent Aout of the
+// stage output is distributed to A0 (U^n) and As (the stage input).
+template <int NDIM, int RS>
+int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Aout, const F8& A0, const F8& As, double dt) {
+  AdjointState* a = c->adj;
+  const Grid& g = c->g;
+  // forward recompute of what the transposes read: ghosts, primitives and
+  // the UCT ingredients of Xs
+  ghost_fill(c, Xs);
+  prim(c, Xs, false);
+  sweeps(c, Xs);
+  double c0, c1, cL;
+  stage_coeffs(c->cfg.rk, s, c0, c1, cL);
+  const long long edges = edge_work<NDIM>(g);
+  const int nbe = blocks_for(edges, 256);
+  adj_combine_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->LB, c0, c1, cL);
+  adj_curl_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, a->LB, a->Eb, dt);
+  adj_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Xs, c->ING, a->Eb, a->GE);
+  long long box = (long long)(g.n[0] + 4) * (g.n[1] + 4) * (NDIM == 3 ? g.n[2] + 4 : 1);
+  adj_edge_faces_kernel<NDIM><<<blocks_for(box, 256), 256, 0, c->stream>>>(g, a->GE, As);
+  CK(cudaMemsetAsync(a->Pb.q[0], 0, 8 * a->fe * sizeof(double), c->stream));
+  c->launches += 4;
+  adj_dir<NDIM, RS, 0>(c, Xs, As, dt);
+  adj_dir<NDIM, RS, 1>(c, Xs, As, dt);
+  if constexpr (NDIM == 3) adj_dir<NDIM, RS, 2>(c, Xs, As, dt);
+  adj_c2p_cells_kernel<NDIM><<<blocks_for(prim_work<NDIM>(g), 256), 256, 0, c->stream>>>(g, Xs, c->P, a->Pb, As);
+  long long pad = (long long)g.ext[0] * g.ext[1] * g.ext[2];
+  adj_c2p_faces_kernel<NDIM><<<blocks_for(pad, 256), 256, 0, c->stream>>>(g, a->Pb, As);
+  for (int d = g.ndim - 1; d >= 0; d--)
+    adj_ghost_periodic_kernel<<<blocks_for(ghost_layers_work(g, d), 256), 256, 0, c->stream>>>(g, As, d);
+  c->launches += 2 + g.ndim;
+  CK(cudaGetLastError());
+  return MHD_OK;
+}
+
+int adj_stage(mhd_ctx* c, int s, const F8& Xs, const F8& Aout, const F8& A0, const F8& As, double dt) {
+  const bool hlld = c->cfg.riemann == MHD_RIEMANN_HLLD;
+  if (c->g.ndim == 2)
+    return hlld ? adj_stage_t<2, RS_HLLD>(c, s, Xs, Aout, A0, As, dt) : adj_stage_t<2, RS_HLL>(c, s, Xs, Aout, A0, As, dt);
+  return hlld ? adj_stage_t<3, RS_HLLD>(c, s, Xs, Aout, A0, As, dt) : adj_stage_t<3, RS_HLL>(c, s, Xs, Aout, A0, As, dt);
+}
+
+int seed(mhd_ctx* c, int functional) {
+  AdjointState* a = c->adj;
+  const Grid& g = c->g;
+  ghost_fill(c, c->U[0]);
+  CK(cudaMemsetAsync(a->A[3].q[0], 0, 8 * a->fe * sizeof(double), c->stream));
+  double dV = g.dx[0] * g.dx[1] * (g.ndim == 3 ? g.dx[2] : 1.0);
+  const int nb = blocks_for(g.ndim == 2 ? edge_work<2>(g) : edge_work<3>(g), 256);
+  if (g.ndim == 2) adj_seed_kernel<2><<<nb, 256, 0, c->stream>>>(g, c->U[0], a->A[3], functional, a->T, dV, a->Jcell);
+  else adj_seed_kernel<3><<<nb, 256, 0, c->stream>>>(g, c->U[0], a->A[3], functional, a->T, dV, a->Jcell);
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  adj_sum_kernel<<<1, 1024, 0, c->stream>>>(a->Jcell, ncell, 0.5 * dV, a->scal);
+  for (int d = g.ndim - 1; d >= 0; d--)
+    adj_ghost_periodic_kernel<<<blocks_for(ghost_layers_work(g, d), 256), 256, 0, c->stream>>>(g, a->A[3], d);
+  c->launches += 2 + g.ndim;
+  CK(cudaGetLastError());
+  return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhd_adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int functional, int mem,
+                    const double* const* target, double* J_out, double* dts_out) {
+  if (!c || nsteps < 1 || ckpt_every < 1) return MHD_ERR_ARG;
+  if (functional != MHD_FUNC_MAGNETIC_ENERGY && functional != MHD_FUNC_MISFIT) return MHD_ERR_ARG;
+  if (functional == MHD_FUNC_MISFIT && (!target || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE))) return MHD_ERR_ARG;
+  if (!c->has_state) return MHD_ERR_STATE;
+  const Grid& g = c->g;
+  if (c->cfg.recon != MHD_RECON_PLM) return MHD_ERR_ARG;
+  for (int d = 0; d < g.ndim; d++)
+    if (!g.periodic[d] || g.n[d] < 2 * g.G + 1) return MHD_ERR_ARG;
+  if (dts)
+    for (int n = 0; n < nsteps; n++)
+      if (!(dts[n] > 0.0) || !std::isfinite(dts[n])) return MHD_ERR_ARG;
+  const int k = ckpt_every < nsteps ? ckpt_every : nsteps;
+  int rc = ensure_state(c, nsteps, k);
+  if (rc) return rc;
+  AdjointState* a = c->adj;
+  const int S = c->cfg.rk;
+  if (functional == MHD_FUNC_MISFIT) {
+    const int nq = g.ndim == 2 ? 6 : 5;
+    for (int q = 0; q < nq; q++) {
+      if (!target[q]) return MHD_ERR_ARG;
+      int e[3];
+      slot_extents(g, q < 5 ? q : 7, e);
+      rc = copy_field(g, c->stream, a->T.q[q], target[q], nullptr, e, true);
+      if (rc) return rc;
+    }
+  }
+
+  // forward pass with checkpoints; dt frozen (given) or from the CFL condition
+  for (int n = 0; n < nsteps; n++) {
+    if (n % k == 0) {
+      rc = copy_state(c, state_at(a, n / k), c->U[0]);
+      if (rc) return rc;
+    }
+    if (dts) {
+      set_dt_kernel<<<1, 1, 0, c->stream>>>(c->sc, dts[n]);
+      c->launches++;
+      run_step(c, false);
+    } else {
+      run_step(c, true);
+    }
+    record_dt_kernel<<<1, 1, 0, c->stream>>>(c->sc, a->scal + 1, n);
+    c->launches++;
+  }
+  CK(cudaGetLastError());
+  a->dts.resize(nsteps);
+  CK(cudaMemcpyAsync(a->dts.data(), a->scal + 1, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  // the recompute passes below repeat the forward's counting: keep its scalars
+  DevScalars fwd;
+  CK(cudaMemcpy(&fwd, c->sc, sizeof(fwd), cudaMemcpyDeviceToHost));
+  if (fwd.status) return fwd.status;
+  rc = seed(c, functional);
+  if (rc) return rc;
+
+  // reverse pass, one checkpoint block at a time
+  F8 Ain = a->A[3];
+  for (int b = a->nck - 1; b >= 0; b--) {
+    const int n0 = b * k, n1 = (n0 + k < nsteps) ? n0 + k : nsteps;
+    const size_t base = (size_t)a->nck;  // block stage inputs follow the checkpoints
+    auto X = [&](int n, int s) { return state_at(a, base + (size_t)(n - n0) * S + s); };
+    rc = copy_state(c, X(n0, 0), state_at(a, b));
+    if (rc) return rc;
+    for (int n = n0; n < n1; n++) {
+      set_dt_only_kernel<<<1, 1, 0, c->stream>>>(c->sc, a->dts[n]);
+      c->launches++;
+      for (int s = 0; s < S; s++) {
+        F8 out = s + 1 < S ? X(n, s + 1) : X(n + 1, 0);
+        run_stage_regs(c, s, X(n, 0), X(n, s), out, false);
+      }
+    }
+    for (int n = n1 - 1; n >= n0; n--) {
+      const double dt = a->dts[n];
+      for (int s = 0; s < S; s++) CK(cudaMemsetAsync(a->A[s].q[0], 0, 8 * a->fe * sizeof(double), c->stream));
+      for (int s = S - 1; s >= 0; s--) {
+        const F8& Aout = s == S - 1 ? Ain : a->A[s + 1];
+        rc = adj_stage(c, s, X(n, s), Aout, a->A[0], a->A[s], dt);
+        if (rc) return rc;
+      }
+      // the cotangent of U^n becomes the incoming one of the step before
+      F8 t = Ain;
+      Ain = a->A[0];
+      a->A[0] = t;
+    }
+  }
+  a->A[3] = Ain;  // holds dJ/dU^0
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&a->J, a->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  DevScalars h;
+  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(c->sc, &fwd, sizeof(fwd), cudaMemcpyHostToDevice));
+  if (h.status) return h.status;
+  a->has_grad = true;
+  if (J_out) *J_out = a->J;
+  if (dts_out) std::memcpy(dts_out, a->dts.data(), sizeof(double) * nsteps);
+  return MHD_OK;
+}
+
+int mhd_adjoint_grad_conserved(mhd_ctx* c, int mem, double* const* gU, double* const* gB) {
+  if (!c || !gU || !gB || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE)) return MHD_ERR_ARG;
+  if (!c->adj || !c->adj->has_grad) return MHD_ERR_STATE;
+  AdjointState* a = c->adj;
+  for (int q = 0; q < 8; q++) {
+    double* dst = q < 5 ? gU[q] : gB[q - 5];
+    if (!dst) return MHD_ERR_ARG;
+    int e[3];
+    slot_extents(c->g, q, e);
+    int rc = copy_field(c->g, c->stream, a->A[3].q[q], nullptr, dst, e, false);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+int mhd_adjoint_grad_prim(mhd_ctx* c, int mem, double* grad_rho, double* const* grad_v) {
+  if (!c || !grad_rho || !grad_v || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE)) return MHD_ERR_ARG;
+  for (int q = 0; q < 3; q++)
+    if (!grad_v[q]) return MHD_ERR_ARG;
+  if (!c->adj || !c->adj->has_grad) return MHD_ERR_STATE;
+  AdjointState* a = c->adj;
+  const Grid& g = c->g;
+  // primitives of U^0 (the first checkpoint)
+  F8 X0 = state_at(a, (size_t)a->nck);
+  int rc = copy_state(c, X0, state_at(a, 0));
+  if (rc) return rc;
+  ghost_fill(c, X0);
+  prim(c, X0, false);
+  long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  F8 out = a->Pb;
+  if (g.ndim == 2) adj_to_prim_kernel<2><<<blocks_for(ncell, 256), 256, 0, c->stream>>>(g, a->A[3], c->P, out);
+  else adj_to_prim_kernel<3><<<blocks_for(ncell, 256), 256, 0, c->stream>>>(g, a->A[3], c->P, out);
+  c->launches++;
+  CK(cudaGetLastError());
+  double* dst[4] = {grad_rho, grad_v[0], grad_v[1], grad_v[2]};
+  for (int q = 0; q < 4; q++) {
+    int e[3];
+    slot_extents(g, 0, e);
+    rc = copy_field(g, c->stream, out.q[q], nullptr, dst[q], e, false);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
+}  // extern "C"

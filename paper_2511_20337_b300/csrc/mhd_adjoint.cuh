@@ -1,0 +1,654 @@
+// Reverse-mode (adjoint) kernels of one CT stage (paper §2.2) for PLM
+// reconstruction on periodic grids.  Given the cotangent of a stage's output,
+// they form the cotangent of its input state, transposing each forward kernel
+// of mhd_kernels.cuh in turn:
+//
+//   combine (RK weights)  ->  curl of the edge fields (CT face update)
+//   ->  UCT edge fields   ->  Riemann solver + flux difference (per face)
+//   ->  PLM reconstruction (per cell)  ->  primitive recovery  ->  ghost fill
+//
+// Every transpose is written in gather form (each output element is summed by
+// one thread in a fixed order), so no atomics are needed and the adjoint is
+// deterministic.  Branches (minmod choices, positivity fallbacks, wave-fan
+// regions, min/max) are those the forward values take; where an argument of
+// minmod is exactly zero the derivative of minmod is taken as zero.  The
+// Riemann solver's vector-Jacobian product comes from the templated solvers
+// of mhd_math.cuh instantiated with the multi-tangent number D3: the exact
+// derivative of the same operations the forward executes.
+#pragma once
+#include "mhd_kernels.cuh"
+#include "mhd_dual.cuh"
+
+namespace mhd {
+
+struct L3 { double* q[3]; };              // face arrays, one per normal direction
+struct GE18 { double* q[3][18]; };        // per edge component: 18 edge-local cotangents
+
+// Edge component C exists in the forward step: all three in 3D, E_z in 2D.
+template <int NDIM> __device__ __forceinline__ bool has_edge(int C) { return NDIM == 3 || C == 2; }
+
+// (i,j,k) is an edge of component C computed by the forward step (emf_item).
+template <int NDIM>
+__device__ __forceinline__ bool edge_valid(const Grid& g, int C, int i, int j, int k) {
+  if (i < 0 || j < 0 || k < 0 || i > g.n[0] || j > g.n[1]) return false;
+  if (NDIM == 2) return C == 2 && k == 0;
+  if (k > g.n[2]) return false;
+  return C == 0 ? i < g.n[0] : (C == 1 ? j < g.n[1] : k < g.n[2]);
+}
+
+// Which argument minmod(a, b) passes on, for its derivative: 1 = a, 2 = b,
+// 0 = neither (opposite signs or a zero argument, where the value is 0).
+__device__ __forceinline__ int minmod_pick(double a, double b) {
+  if (!((gt0(a) && gt0(b)) || (lt0(a) && lt0(b)))) return 0;
+  return (bits(b) & kMag) < (bits(a) & kMag) ? 2 : 1;
+}
+
+__device__ __forceinline__ void box_index(long long id, const int lo[3], const int ext[3], int x[3]) {
+  x[0] = (int)(id % ext[0]) + lo[0];
+  long long r = id / ext[0];
+  x[1] = (int)(r % ext[1]) + lo[1];
+  x[2] = (int)(r / ext[1]) + lo[2];
+}
+
+// ---------------------------------------------------------------------------
+// Seed: cotangent of J with respect to the final state (ghost-filled S) and
+// the per-cell terms of J.
+//   magnetic energy: J = 1/2 dV sum_c |B_c|^2, B_c the mean of the two faces
+//   misfit:          J = 1/2 dV sum_c sum_q (U_q - T_q)^2 over rho, m, E
+//                    (2D: and the cell B_z)
+// Written over the box of faces [0, n_d] (cells [0, n_d - 1]); the face at
+// n_d of a periodic axis is the ghost copy of face 0 and is folded back by
+// the ghost transpose.
+// ---------------------------------------------------------------------------
+enum { FUNC_MAGNETIC_ENERGY = 0, FUNC_MISFIT = 1 };
+
+template <int NDIM>
+__device__ __forceinline__ double cell_b(const Grid& g, const F8& S, int d, int c) {
+  if (NDIM == 2 && d == 2) return S.q[7][c];
+  return 0.5 * (S.q[5 + d][c] + S.q[5 + d][c + g.stride(d)]);
+}
+
+template <int NDIM>
+static __global__ void adj_seed_kernel(Grid g, F8 S, F8 A, int which, L6 T, double dV, double* Jcell) {
+  const long long total = edge_work<NDIM>(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int ex = g.n[0] + 1, ey = g.n[1] + 1;
+    int i = (int)(id % ex);
+    long long r = id / ex;
+    int j = (int)(r % ey);
+    int k = (int)(r / ey);
+    const int x[3] = {i, j, k};
+    const int c = g.at(i, j, k);
+    const bool cell = i < g.n[0] && j < g.n[1] && k < g.n[2];
+    if (cell) {
+      double sum = 0.0;
+      if (which == FUNC_MAGNETIC_ENERGY) {
+        double bx = cell_b<NDIM>(g, S, 0, c), by = cell_b<NDIM>(g, S, 1, c), bz = cell_b<NDIM>(g, S, 2, c);
+        sum = (bx * bx + by * by) + bz * bz;
+        if (NDIM == 2) A.q[7][c] = dV * bz;
+      } else {
+        constexpr int NQ = NDIM == 2 ? 6 : 5;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+          int slot = q < 5 ? q : 7;
+          double dq = S.q[slot][c] - T.q[q][c];
+          sum = q == 0 ? dq * dq : sum + dq * dq;
+          A.q[slot][c] = dV * dq;
+        }
+      }
+      Jcell[((long long)k * g.n[1] + j) * g.n[0] + i] = sum;
+    }
+    if (which == FUNC_MAGNETIC_ENERGY) {
+#pragma unroll
+      for (int d = 0; d < NDIM; d++) {
+        bool ok = true;
+#pragma unroll
+        for (int e = 0; e < NDIM; e++)
+          if (e != d && x[e] >= g.n[e]) ok = false;
+        if (!ok) continue;
+        double acc = 0.0;
+        if (x[d] < g.n[d]) acc += cell_b<NDIM>(g, S, d, c);
+        if (x[d] > 0) acc += cell_b<NDIM>(g, S, d, c - g.stride(d));
+        A.q[5 + d][c] = 0.5 * dV * acc;
+      }
+    }
+  }
+}
+
+// Fixed-order sum of n values by one block (deterministic).
+static __global__ void adj_sum_kernel(const double* __restrict__ v, long long n, double scale, double* out) {
+  __shared__ double part[1024];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = scale * part[0];
+}
+
+// ---------------------------------------------------------------------------
+// Transpose of the periodic ghost fill along axis d: every ghost slot's
+// cotangent is added to the interior slot it was copied from, then cleared.
+// The forward fills x, y, z in turn; the transposes run z, y, x.  Distinct
+// ghost slots of one pass have distinct sources when n_d >= 2G + 1.
+// ---------------------------------------------------------------------------
+static __global__ void adj_ghost_periodic_kernel(Grid g, F8 A, int d) {
+  const long long total = ghost_layers_work(g, d);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    int e1 = g.hi(t1) - g.lo(t1) + 1;
+    int nl = 2 * g.G + 1;
+    int l = (int)(id % nl);
+    long long r = id / nl;
+    int a = (int)(r % e1) + g.lo(t1);
+    int b = (int)(r / e1) + g.lo(t2);
+    int gi = l < g.G ? l - g.G : g.n[d] + (l - g.G);
+    int x[3];
+    x[d] = gi;
+    x[t1] = a;
+    x[t2] = b;
+    int dst = g.at(x[0], x[1], x[2]);
+    x[d] = wrap(gi, g.n[d]);
+    int src = g.at(x[0], x[1], x[2]);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      A.q[q][src] += A.q[q][dst];
+      A.q[q][dst] = 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transpose of the stage combine  out = c0 U0 + c1 Us + cL L  (cells), and
+// out_B = c0 B0 + c1 Bs + cL L_B (evolved faces): the cotangents of the stage
+// increment (Lb on cells, LB on faces) and the accumulation into U0 and Us.
+// ---------------------------------------------------------------------------
+template <int NDIM>
+static __global__ void adj_combine_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, L3 LB, double c0, double c1,
+                                          double cL) {
+  const long long total = edge_work<NDIM>(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int ex = g.n[0] + 1, ey = g.n[1] + 1;
+    int i = (int)(id % ex);
+    long long r = id / ex;
+    int j = (int)(r % ey);
+    int k = (int)(r / ey);
+    int c = g.at(i, j, k);
+    if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+      constexpr int NV = NDIM == 2 ? 6 : 5;
+#pragma unroll
+      for (int q = 0; q < NV; q++) {
+        int slot = q < 5 ? q : 7;
+        double x = Aout.q[slot][c];
+        Lb.q[q][c] = cL * x;
+        A0.q[slot][c] += c0 * x;
+        As.q[slot][c] += c1 * x;
+      }
+    }
+    const int idx3[3] = {i, j, k};
+#pragma unroll
+    for (int d = 0; d < NDIM; d++) {
+      bool ok = true;
+#pragma unroll
+      for (int e = 0; e < NDIM; e++) {
+        if (e == d) ok = ok && (idx3[e] < g.n[e] || !g.periodic[e]);
+        else ok = ok && idx3[e] < g.n[e];
+      }
+      if (NDIM == 2) ok = ok && k == 0;
+      if (!ok) continue;
+      double x = Aout.q[5 + d][c];
+      LB.q[d][c] = cL * x;
+      A0.q[5 + d][c] += c0 * x;
+      As.q[5 + d][c] += c1 * x;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transpose of the CT face increment L_B,d = -dt (curl E)_d: the cotangent of
+// each edge field from the face cotangents LB (zero on faces that are not
+// evolved).  E_C enters the faces of normal (C+1)%3 through their
+// (C+2)-difference and the faces of normal (C+2)%3 through their
+// (C+1)-difference.
+// ---------------------------------------------------------------------------
+template <int NDIM>
+static __global__ void adj_curl_kernel(Grid g, L3 LB, E3 Eb, double dt) {
+  const long long total = edge_work<NDIM>(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int ex = g.n[0] + 1, ey = g.n[1] + 1;
+    int i = (int)(id % ex);
+    long long r = id / ex;
+    int j = (int)(r % ey);
+    int k = (int)(r / ey);
+    int c = g.at(i, j, k);
+#pragma unroll
+    for (int C = 0; C < 3; C++) {
+      if (!edge_valid<NDIM>(g, C, i, j, k)) continue;
+      double acc = 0.0;
+      const int d = (C + 1) % 3, d1 = (C + 2) % 3;  // L_B,d = -(E_C[+d1] - E_C) dt/dx_d1 (+ ...)
+      if (d < NDIM && d1 < NDIM) acc += (dt * g.idx[d1]) * (LB.q[d][c] - LB.q[d][c - g.stride(d1)]);
+      const int e = (C + 2) % 3, e2 = (C + 1) % 3;  // L_B,e = (E_C[+e2] - E_C) dt/dx_e2 (+ ...)
+      if (e < NDIM && e2 < NDIM) acc += (dt * g.idx[e2]) * (LB.q[e][c - g.stride(e2)] - LB.q[e][c]);
+      Eb.e[C][c] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transpose of one UCT edge field (uct_edge<C>): the 18 edge-local cotangents
+//   0-4   a-face ingredient sums (a+, a-, d, u^W, u^E), each shared by the two
+//         a-faces touching the edge,
+//   5-9   the same for the b-faces,
+//   10-13 the face field B_b at a-offsets -2, -1, 0, +1,
+//   14-17 the face field B_a at b-offsets -2, -1, 0, +1.
+// ---------------------------------------------------------------------------
+// Cotangents of (v_-2, v_-1, v_0, v_+1) from the cotangents gw, ge of the two
+// minmod-limited edge values  w = v_-1 + m(v_-1 - v_-2, v_0 - v_-1)/2  and
+// e = v_0 - m(v_0 - v_-1, v_+1 - v_0)/2.
+__device__ __forceinline__ void edge_recon_vjp(double vm2, double vm1, double v0, double vp1, double gw, double gev,
+                                               double w[4]) {
+  w[0] = w[1] = w[2] = w[3] = 0.0;
+  int pw = minmod_pick(vm1 - vm2, v0 - vm1);
+  if (pw == 1) { w[0] -= 0.5 * gw; w[1] += 1.5 * gw; }
+  else if (pw == 2) { w[1] += 0.5 * gw; w[2] += 0.5 * gw; }
+  else w[1] += gw;
+  int pe = minmod_pick(v0 - vm1, vp1 - v0);
+  if (pe == 1) { w[1] += 0.5 * gev; w[2] += 0.5 * gev; }
+  else if (pe == 2) { w[2] += 1.5 * gev; w[3] -= 0.5 * gev; }
+  else w[2] += gev;
+}
+
+template <int C>
+__device__ __forceinline__ void uct_edge_vjp(const Grid& g, const F8& S, const Ingr5x3& ING, int c, double eb,
+                                             double* const* ge) {
+  constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+  const int sa = g.stride(A), sb = g.stride(B);
+  const int cb = c - sb, ca = c - sa;
+  const double* Ia[5] = {ING.a[A][0], ING.a[A][1], ING.a[A][2], ING.a[A][3], ING.a[A][4]};
+  const double* Ib[5] = {ING.a[B][0], ING.a[B][1], ING.a[B][2], ING.a[B][3], ING.a[B][4]};
+  double apa = Ia[0][cb] + Ia[0][c], ama = Ia[1][cb] + Ia[1][c], dda = Ia[2][cb] + Ia[2][c];
+  double uW = Ia[3][cb] + Ia[3][c], uE = Ia[4][cb] + Ia[4][c];
+  double apb = Ib[0][ca] + Ib[0][c], amb = Ib[1][ca] + Ib[1][c], ddb = Ib[2][ca] + Ib[2][c];
+  double vS = Ib[3][ca] + Ib[3][c], vN = Ib[4][ca] + Ib[4][c];
+  const double* Bb = S.q[5 + B];
+  const double* Ba = S.q[5 + A];
+  double bm2 = Bb[c - 2 * sa], bm1 = Bb[c - sa], b0 = Bb[c], bp1 = Bb[c + sa];
+  double BbW = fma(0.5, minmod(bm1 - bm2, b0 - bm1), bm1);
+  double BbE = fma(-0.5, minmod(b0 - bm1, bp1 - b0), b0);
+  double am2 = Ba[c - 2 * sb], am1 = Ba[c - sb], a0 = Ba[c], ap1 = Ba[c + sb];
+  double BaS = fma(0.5, minmod(am1 - am2, a0 - am1), am1);
+  double BaN = fma(-0.5, minmod(a0 - am1, ap1 - a0), a0);
+  // E = (1/4) [(apb vS BaS + amb vN BaN) - (apa uW BbW + ama uE BbE)]
+  //   + (1/2) [dda (BbE - BbW) - ddb (BaN - BaS)]
+  const double gu = 0.25 * eb, gd = 0.5 * eb;
+  ge[0][c] = -gu * uW * BbW;
+  ge[1][c] = -gu * uE * BbE;
+  ge[2][c] = gd * (BbE - BbW);
+  ge[3][c] = -gu * apa * BbW;
+  ge[4][c] = -gu * ama * BbE;
+  ge[5][c] = gu * vS * BaS;
+  ge[6][c] = gu * vN * BaN;
+  ge[7][c] = -gd * (BaN - BaS);
+  ge[8][c] = gu * apb * BaS;
+  ge[9][c] = gu * amb * BaN;
+  double w[4];
+  edge_recon_vjp(bm2, bm1, b0, bp1, -gu * apa * uW - gd * dda, -gu * ama * uE + gd * dda, w);
+  ge[10][c] = w[0];
+  ge[11][c] = w[1];
+  ge[12][c] = w[2];
+  ge[13][c] = w[3];
+  edge_recon_vjp(am2, am1, a0, ap1, gu * apb * vS + gd * ddb, gu * amb * vN - gd * ddb, w);
+  ge[14][c] = w[0];
+  ge[15][c] = w[1];
+  ge[16][c] = w[2];
+  ge[17][c] = w[3];
+}
+
+template <int NDIM>
+static __global__ void adj_edge_kernel(Grid g, F8 S, Ingr5x3 ING, E3 Eb, GE18 GE) {
+  const long long total = edge_work<NDIM>(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int ex = g.n[0] + 1, ey = g.n[1] + 1;
+    int i = (int)(id % ex);
+    long long r = id / ex;
+    int j = (int)(r % ey);
+    int k = (int)(r / ey);
+    int c = g.at(i, j, k);
+    if (edge_valid<NDIM>(g, 2, i, j, k)) uct_edge_vjp<2>(g, S, ING, c, Eb.e[2][c], GE.q[2]);
+    if (NDIM == 3) {
+      if (edge_valid<NDIM>(g, 0, i, j, k)) uct_edge_vjp<0>(g, S, ING, c, Eb.e[0][c], GE.q[0]);
+      if (edge_valid<NDIM>(g, 1, i, j, k)) uct_edge_vjp<1>(g, S, ING, c, Eb.e[1][c], GE.q[1]);
+    }
+  }
+}
+
+// Face-field cotangents from the edge reconstructions: the face field of
+// normal D is B_b of E_C for C = (D+1)%3 (reconstructed along a = (D+2)%3)
+// and B_a of E_C for C = (D+2)%3 (along b = (D+1)%3).  Box: [-2, n+1] on
+// every active axis.
+template <int NDIM>
+static __global__ void adj_edge_faces_kernel(Grid g, GE18 GE, F8 A) {
+  int lo[3] = {-2, -2, NDIM == 3 ? -2 : 0};
+  int ext[3] = {g.n[0] + 4, g.n[1] + 4, NDIM == 3 ? g.n[2] + 4 : 1};
+  const long long total = (long long)ext[0] * ext[1] * ext[2];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int x[3];
+    box_index(id, lo, ext, x);
+    const int f = g.at(x[0], x[1], x[2]);
+#pragma unroll
+    for (int D = 0; D < NDIM; D++) {
+      double acc = 0.0;
+      bool any = false;
+#pragma unroll
+      for (int role = 0; role < 2; role++) {
+        const int C = role == 0 ? (D + 1) % 3 : (D + 2) % 3;
+        if (!has_edge<NDIM>(C)) continue;
+        const int ax = role == 0 ? (D + 2) % 3 : (D + 1) % 3;  // reconstruction axis
+        const int base = role == 0 ? 10 : 14;
+#pragma unroll
+        for (int m = 0; m < 4; m++) {  // this face is offset (m - 2) from edge e = f + (2 - m) along ax
+          int y[3] = {x[0], x[1], x[2]};
+          y[ax] += 2 - m;
+          if (!edge_valid<NDIM>(g, C, y[0], y[1], y[2])) continue;
+          acc += GE.q[C][base + m][g.at(y[0], y[1], y[2])];
+          any = true;
+        }
+      }
+      if (any) A.q[5 + D][f] += acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Riemann solver and flux difference, per face of direction DIR (faces
+// [0, n_DIR], transverse [-1, n_t] as in the sweep): recompute the face's PLM
+// states, take the flux cotangent from the stage-increment cotangents of its
+// two cells, the UCT-ingredient cotangents from the edges that use the face,
+// and push both through the solver.  Writes the cotangents of the left and
+// right states and adds that of the normal face field.
+// ---------------------------------------------------------------------------
+// PLM states of one cell from its 3-cell window with the positivity fallback.
+__device__ __forceinline__ bool plm_cell(const double w[7][3], double plus[7], double minus[7]) {
+#pragma unroll
+  for (int v = 0; v < 7; v++) recon_plm(w[v][0], w[v][1], w[v][2], plus[v], minus[v]);
+  if (!gt0(plus[0]) || !gt0(minus[0]) || !gt0(plus[6]) || !gt0(minus[6])) {
+#pragma unroll
+    for (int v = 0; v < 7; v++) plus[v] = minus[v] = w[v][1];
+    return true;
+  }
+  return false;
+}
+
+template <int DIR, int NDIM>
+__device__ __forceinline__ void sweep_box(const Grid& g, int lo[3], int ext[3], int dir_lo, int dir_hi) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    if (a == DIR) { lo[a] = dir_lo; ext[a] = dir_hi - dir_lo + 1; }
+    else if (a < NDIM) { lo[a] = -1; ext[a] = g.n[a] + 2; }
+    else { lo[a] = 0; ext[a] = 1; }
+  }
+}
+
+template <int RS>
+__device__ __forceinline__ void riemann_vjp(const double xin[15], double gamma, double igm1, const double Fb[7],
+                                            const double Ib[5], double xb[15]) {
+#pragma unroll
+  for (int p = 0; p < 5; p++) {
+    D3 in[15];
+#pragma unroll
+    for (int i = 0; i < 15; i++) {
+      in[i] = D3(xin[i]);
+      if (i / 3 == p) in[i].d[i % 3] = 1.0;
+    }
+    W7T<D3> L = {in[0], in[1], in[2], in[3], in[4], in[5], in[6]};
+    W7T<D3> R = {in[7], in[8], in[9], in[10], in[11], in[12], in[13]};
+    Flux7T<D3> F;
+    IngrT<D3> ing;
+    if (RS == RS_HLLD) riemann_hlld(L, R, in[14], gamma, igm1, F, ing);
+    else riemann_hll(L, R, in[14], gamma, igm1, F, ing);
+#pragma unroll
+    for (int t = 0; t < 3; t++) {
+      double acc = Ib[0] * ing.ap.d[t];
+      acc = fma(Ib[1], ing.am.d[t], acc);
+      acc = fma(Ib[2], ing.dd.d[t], acc);
+      acc = fma(Ib[3], ing.uL.d[t], acc);
+      acc = fma(Ib[4], ing.uR.d[t], acc);
+#pragma unroll
+      for (int q = 0; q < 7; q++) acc = fma(Fb[q], F.f[q].d[t], acc);
+      xb[3 * p + t] = acc;
+    }
+  }
+}
+
+template <int DIR, int NDIM, int RS>
+static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, const double* __restrict__ Bn,
+                                                                 L6 Lb, GE18 GE, double dt, F8 WbL, F8 WbR,
+                                                                 double* Bnb) {
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  int lo[3], ext[3];
+  sweep_box<DIR, NDIM>(g, lo, ext, 0, g.n[DIR]);
+  const long long total = (long long)ext[0] * ext[1] * ext[2];
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= total) return;
+  int x[3];
+  box_index(id, lo, ext, x);
+  const int cf = g.at(x[0], x[1], x[2]);
+  const int st = g.stride(DIR);
+  const double* pr[7] = {P.q[0], P.q[1 + DIR], P.q[1 + T1], P.q[1 + T2], P.q[4 + T1], P.q[4 + T2], P.q[7]};
+  // the face's states: plus of cell f-1 and minus of cell f
+  double xin[15];
+  {
+    double w[7][3], plus[7], minus[7];
+#pragma unroll
+    for (int v = 0; v < 7; v++)
+#pragma unroll
+      for (int m = 0; m < 3; m++) w[v][m] = pr[v][cf + (m - 2) * st];
+    plm_cell(w, plus, minus);
+#pragma unroll
+    for (int v = 0; v < 7; v++) xin[v] = plus[v];
+#pragma unroll
+    for (int v = 0; v < 7; v++)
+#pragma unroll
+      for (int m = 0; m < 3; m++) w[v][m] = pr[v][cf + (m - 1) * st];
+    plm_cell(w, plus, minus);
+#pragma unroll
+    for (int v = 0; v < 7; v++) xin[7 + v] = minus[v];
+  }
+  xin[14] = Bn[cf];
+  // flux cotangent: L(cell f-1) gets -dtdx F_f, L(cell f) gets +dtdx F_f
+  const double dtdx = dt * g.idx[DIR];
+  auto lbar = [&](int q) { return dtdx * (Lb.q[q][cf] - Lb.q[q][cf - st]); };
+  double Fb[7];
+  Fb[0] = lbar(0);
+  Fb[1] = lbar(1 + DIR);
+  Fb[2] = lbar(1 + T1);
+  Fb[3] = lbar(1 + T2);
+  Fb[4] = 0.0;
+  Fb[5] = 0.0;
+  Fb[6] = lbar(4);
+  if (NDIM == 2) {
+    if (DIR == 0) Fb[5] = lbar(5);
+    else Fb[4] = lbar(5);
+  }
+  // UCT-ingredient cotangent from the edges that use this face
+  double Ib[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int role = 0; role < 2; role++) {
+    const int C = role == 0 ? (DIR + 2) % 3 : (DIR + 1) % 3;  // this face is an a-face / a b-face of E_C
+    if (!has_edge<NDIM>(C)) continue;
+    const int ax = role == 0 ? (DIR + 1) % 3 : (DIR + 2) % 3;  // the edges at this face and one step up ax
+    const int base = role == 0 ? 0 : 5;
+#pragma unroll
+    for (int m = 0; m < 2; m++) {
+      int y[3] = {x[0], x[1], x[2]};
+      y[ax] += m;
+      if (!edge_valid<NDIM>(g, C, y[0], y[1], y[2])) continue;
+      const int e = g.at(y[0], y[1], y[2]);
+#pragma unroll
+      for (int q = 0; q < 5; q++) Ib[q] += GE.q[C][base + q][e];
+    }
+  }
+  double xb[15];
+  riemann_vjp<RS>(xin, g.gamma, g.igm1, Fb, Ib, xb);
+#pragma unroll
+  for (int v = 0; v < 7; v++) {
+    WbL.q[v][cf] = xb[v];
+    WbR.q[v][cf] = xb[7 + v];
+  }
+  Bnb[cf] += xb[14];
+}
+
+// ---------------------------------------------------------------------------
+// PLM reconstruction, per cell of the sweep box along DIR ([-2, n_DIR + 1]):
+// gather the state cotangents of the three cells whose reconstruction reads
+// this cell and add their contribution to the primitive cotangents.
+// ---------------------------------------------------------------------------
+template <int DIR, int NDIM>
+static __global__ void __launch_bounds__(128) adj_recon_kernel(Grid g, F8 P, F8 WbL, F8 WbR, F8 Pb) {
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  int lo[3], ext[3];
+  sweep_box<DIR, NDIM>(g, lo, ext, -2, g.n[DIR] + 1);
+  const long long total = (long long)ext[0] * ext[1] * ext[2];
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= total) return;
+  int x[3];
+  box_index(id, lo, ext, x);
+  const int c = g.at(x[0], x[1], x[2]);
+  const int st = g.stride(DIR);
+  const int n = g.n[DIR];
+  const int slot[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4 + T1, 4 + T2, 7};
+  double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int o = -1; o <= 1; o++) {  // reconstruction of cell x + o reads this cell at window slot 1 - o
+    const int xo = x[DIR] + o;
+    if (xo < -1 || xo > n) continue;
+    const int co = c + o * st;
+    double w[7][3], plus[7], minus[7];
+#pragma unroll
+    for (int v = 0; v < 7; v++)
+#pragma unroll
+      for (int m = 0; m < 3; m++) w[v][m] = P.q[slot[v]][co + (m - 1) * st];
+    const bool fb = plm_cell(w, plus, minus);
+#pragma unroll
+    for (int v = 0; v < 7; v++) {
+      const double pb = xo + 1 <= n ? WbL.q[v][co + st] : 0.0;  // plus state: left state of face xo+1
+      const double mb = xo >= 0 ? WbR.q[v][co] : 0.0;           // minus state: right state of face xo
+      if (fb) {
+        if (o == 0) acc[v] += pb + mb;
+        continue;
+      }
+      double ws[3] = {0.0, 0.0, 0.0};  // cotangents of the window cells
+      ws[1] = pb + mb;
+      const double db = 0.5 * (pb - mb);
+      const int pick = minmod_pick(w[v][1] - w[v][0], w[v][2] - w[v][1]);
+      if (pick == 1) { ws[1] += db; ws[0] -= db; }
+      else if (pick == 2) { ws[2] += db; ws[1] -= db; }
+      acc[v] += ws[1 - o];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 7; v++) Pb.q[slot[v]][c] += acc[v];
+}
+
+// ---------------------------------------------------------------------------
+// Primitive recovery, cells: v = m/rho, p = (G-1)(E - m.v/2 - B^2/2) with the
+// cell field B; a pressure raised to the floor passes no cotangent.  The
+// total cotangent of the cell field replaces Pb.q[4..6] for the face pass.
+// ---------------------------------------------------------------------------
+template <int NDIM>
+static __global__ void adj_c2p_cells_kernel(Grid g, F8 S, F8 P, F8 Pb, F8 A) {
+  const long long total = prim_work<NDIM>(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int nxp = g.n[0] + 2 * g.G, nyp = g.n[1] + 2 * g.G;
+    int i = (int)(id % nxp) - g.G;
+    long long r = id / nxp;
+    int j = (int)(r % nyp) - g.G;
+    int k = NDIM == 3 ? (int)(r / nyp) - g.G : 0;
+    int c = g.at(i, j, k);
+    const double rho = P.q[0][c], vx = P.q[1][c], vy = P.q[2][c], vz = P.q[3][c];
+    const double bx = P.q[4][c], by = P.q[5][c], bz = P.q[6][c];
+    double pb = Pb.q[7][c];
+    if (g.p_floor > 0.0) {
+      Prim8 V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1);
+      if (V.p < g.p_floor) pb = 0.0;
+    }
+    const double gp = g.gm1 * pb;
+    const double ir = 1.0 / rho;
+    const double vbx = Pb.q[1][c], vby = Pb.q[2][c], vbz = Pb.q[3][c];
+    const double v2 = (vx * vx + vy * vy) + vz * vz;
+    A.q[0][c] += (Pb.q[0][c] - ((vbx * vx + vby * vy) + vbz * vz) * ir) + 0.5 * gp * v2;
+    A.q[1][c] += vbx * ir - gp * vx;
+    A.q[2][c] += vby * ir - gp * vy;
+    A.q[3][c] += vbz * ir - gp * vz;
+    A.q[4][c] += gp;
+    const double bbx = Pb.q[4][c] - gp * bx, bby = Pb.q[5][c] - gp * by, bbz = Pb.q[6][c] - gp * bz;
+    Pb.q[4][c] = bbx;
+    Pb.q[5][c] = bby;
+    if (NDIM == 2) A.q[7][c] += bbz;
+    else Pb.q[6][c] = bbz;
+  }
+}
+
+// Primitive recovery, faces: each face field gets half the cell-field
+// cotangent of the padded cells on either side.
+template <int NDIM>
+static __global__ void adj_c2p_faces_kernel(Grid g, F8 Pb, F8 A) {
+  int lo[3] = {-g.G, -g.G, NDIM == 3 ? -g.G : 0};
+  int ext[3] = {g.n[0] + 2 * g.G + 1, g.n[1] + 2 * g.G + 1, NDIM == 3 ? g.n[2] + 2 * g.G + 1 : 1};
+  const long long total = (long long)ext[0] * ext[1] * ext[2];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int x[3];
+    box_index(id, lo, ext, x);
+    const int f = g.at(x[0], x[1], x[2]);
+#pragma unroll
+    for (int d = 0; d < NDIM; d++) {
+      bool ok = true;  // the transverse indices must be those of padded cells
+#pragma unroll
+      for (int e = 0; e < NDIM; e++)
+        if (e != d && x[e] > g.n[e] + g.G - 1) ok = false;
+      if (!ok) continue;
+      double acc = 0.0;
+      if (x[d] <= g.n[d] + g.G - 1) acc += Pb.q[4 + d][f];
+      if (x[d] - 1 >= -g.G) acc += Pb.q[4 + d][f - g.stride(d)];
+      A.q[5 + d][f] += 0.5 * acc;
+    }
+  }
+}
+
+// Chain of the initial conserved cotangent to the initial primitives with p
+// and B held: m = rho v, E = p/(G-1) + rho v^2/2 + B^2/2.
+template <int NDIM>
+static __global__ void adj_to_prim_kernel(Grid g, F8 A, F8 P, F8 out) {
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(id % g.n[0]);
+    long long r = id / g.n[0];
+    int j = (int)(r % g.n[1]);
+    int k = (int)(r / g.n[1]);
+    int c = g.at(i, j, k);
+    const double rho = P.q[0][c], vx = P.q[1][c], vy = P.q[2][c], vz = P.q[3][c];
+    const double ar = A.q[0][c], mx = A.q[1][c], my = A.q[2][c], mz = A.q[3][c], ae = A.q[4][c];
+    const double v2 = (vx * vx + vy * vy) + vz * vz;
+    out.q[0][c] = ((ar + ((mx * vx + my * vy) + mz * vz)) + 0.5 * ae * v2);
+    out.q[1][c] = rho * (mx + ae * vx);
+    out.q[2][c] = rho * (my + ae * vy);
+    out.q[3][c] = rho * (mz + ae * vz);
+  }
+}
+
+static __global__ void set_dt_only_kernel(DevScalars* sc, double dt) { sc->dt = dt; }
+static __global__ void record_dt_kernel(const DevScalars* sc, double* dts, int n) { dts[n] = sc->dt; }
+
+}  // namespace mhd

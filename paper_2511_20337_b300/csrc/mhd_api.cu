@@ -8,39 +8,14 @@
 #include <new>
 
 #include "mhd.h"
+#include "mhd_ctx.cuh"
 #include "mhd_host.cuh"
 #include "mhd_kernels.cuh"
 #include "mhd_probe.h"
 
 using namespace mhd;
 
-struct mhd_ctx {
-  mhd_config cfg;
-  Grid g;
-  cudaStream_t stream;
-  bool own_stream;
-  size_t field_elems;  // padded elements per field (rounded up)
-  double* pool;        // every field lives in this one allocation
-  F8 U[3];             // RK registers (U[0] = U^n)
-  F8 P;                // primitives of the stage input
-  L6 L;                // stage increment of the cell variables
-  Ingr5x3 ING;         // UCT face ingredients
-  E3 E;                // edge fields
-  DevScalars* sc;
-  bool has_state;
-  int seglen;
-  long long launches;
-  int launches_per_step;
-  cudaGraphExec_t graph;
-  bool graph_ready;
-  // profiling: an event after every launch, tagged with its kernel class
-  bool prof_on;
-  int prof_n;
-  cudaEvent_t prof_ev[128];
-  int prof_cls[128];
-};
-
-namespace {
+namespace mhd {
 
 void prof_mark(mhd_ctx* c, int cls) {
   if (!c->prof_on || c->prof_n >= 128) return;
@@ -106,7 +81,7 @@ template <int NDIM, int RECON, int RS>
 void sweeps_t(mhd_ctx* c, const F8& S) {
   sweep_one<0, NDIM, RECON, RS>(c, S);
   sweep_one<1, NDIM, RECON, RS>(c, S);
-  if (NDIM == 3) sweep_one<2, NDIM, RECON, RS>(c, S);
+  if constexpr (NDIM == 3) sweep_one<2, NDIM, RECON, RS>(c, S);
 }
 
 template <int NDIM>
@@ -140,26 +115,37 @@ void ct_rk(mhd_ctx* c, const F8& U0, const F8& Us, const F8& Out, int mode) {
   prof_mark(c, MHD_KCLASS_CT_RK);
 }
 
-// One RK stage s of the step; cfl = compute this step's dt in the primitive pass.
-void run_stage(mhd_ctx* c, int s, bool cfl) {
-  const int rk = c->cfg.rk;
-  const F8& U0 = c->U[0];
-  const F8& Us = s == 0 ? c->U[0] : (s == 1 ? c->U[1] : c->U[2]);
-  const F8& Out = s == 0 ? c->U[1] : ((rk == 2 || s == 2) ? c->U[0] : c->U[2]);
-  int mode = s == 0 ? COMB_FIRST : (rk == 2 ? COMB_RK2_FINAL : (s == 1 ? COMB_RK3_SECOND : COMB_RK3_FINAL));
+void sweeps(mhd_ctx* c, const F8& S) {
+  if (c->g.ndim == 2) sweeps_n<2>(c, S);
+  else sweeps_n<3>(c, S);
+}
+
+int stage_mode(int rk, int s) {
+  return s == 0 ? COMB_FIRST : (rk == 2 ? COMB_RK2_FINAL : (s == 1 ? COMB_RK3_SECOND : COMB_RK3_FINAL));
+}
+
+void run_stage_regs(mhd_ctx* c, int s, const F8& U0, const F8& Us, const F8& Out, bool cfl) {
   ghost_fill(c, Us);
   prim(c, Us, cfl);
-  if (c->g.ndim == 2) sweeps_n<2>(c, Us);
-  else sweeps_n<3>(c, Us);
+  sweeps(c, Us);
   emf(c, Us);
-  ct_rk(c, U0, Us, Out, mode);
+  ct_rk(c, U0, Us, Out, stage_mode(c->cfg.rk, s));
+}
+
+// One RK stage s of the step on the context's registers; cfl = compute this
+// step's dt in the primitive pass.
+void run_stage(mhd_ctx* c, int s, bool cfl) {
+  const int rk = c->cfg.rk;
+  const F8& Us = s == 0 ? c->U[0] : (s == 1 ? c->U[1] : c->U[2]);
+  const F8& Out = s == 0 ? c->U[1] : ((rk == 2 || s == 2) ? c->U[0] : c->U[2]);
+  run_stage_regs(c, s, c->U[0], Us, Out, cfl);
 }
 
 void run_step(mhd_ctx* c, bool device_dt) {
   for (int s = 0; s < c->cfg.rk; s++) run_stage(c, s, device_dt && s == 0);
 }
 
-}  // namespace
+}  // namespace mhd
 
 extern "C" {
 
@@ -240,6 +226,7 @@ int mhd_destroy(mhd_ctx* c) {
   if (!c) return MHD_OK;
   cudaStreamSynchronize(c->stream);
   if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+  adjoint_free(c);
   cudaFree(c->pool);
   cudaFree(c->sc);
   if (c->own_stream) cudaStreamDestroy(c->stream);

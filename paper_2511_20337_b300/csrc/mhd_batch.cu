@@ -119,7 +119,7 @@ void batch_sweeps(mhd_batch* b, int reg) {
       b->runs_d, table(b, T_SWEEP_Y), R, reg, 1);
   prof_mark(b, MHD_KCLASS_SWEEP_Y);
   b->launches += 2;
-  if (NDIM == 3) {
+  if constexpr (NDIM == 3) {
     batch_sweep_kernel<2, NDIM, RECON, RS><<<table_blocks(b, T_SWEEP_Z), kBlockSweep, 0, b->stream>>>(
         b->runs_d, table(b, T_SWEEP_Z), R, reg, 1);
     prof_mark(b, MHD_KCLASS_SWEEP_Z);

@@ -1,0 +1,54 @@
+// The single-grid context behind mhd_ctx* and the launch helpers of one RK
+// stage, shared by the entry points of mhd_api.cu and the adjoint of
+// mhd_adjoint.cu.  Internal to the library.
+#pragma once
+#include "mhd.h"
+#include "mhd_kernels.cuh"
+
+namespace mhd {
+struct AdjointState;
+}
+
+struct mhd_ctx {
+  mhd_config cfg;
+  mhd::Grid g;
+  cudaStream_t stream;
+  bool own_stream;
+  size_t field_elems;  // padded elements per field (rounded up)
+  double* pool;        // every field lives in this one allocation
+  mhd::F8 U[3];        // RK registers (U[0] = U^n); each register's 8 fields are contiguous
+  mhd::F8 P;           // primitives of the stage input
+  mhd::L6 L;           // stage increment of the cell variables
+  mhd::Ingr5x3 ING;    // UCT face ingredients
+  mhd::E3 E;           // edge fields
+  mhd::DevScalars* sc;
+  bool has_state;
+  int seglen;
+  long long launches;
+  int launches_per_step;
+  cudaGraphExec_t graph;
+  bool graph_ready;
+  // profiling: an event after every launch, tagged with its kernel class
+  bool prof_on;
+  int prof_n;
+  cudaEvent_t prof_ev[128];
+  int prof_cls[128];
+  mhd::AdjointState* adj;  // buffers of the adjoint, made by its first run
+};
+
+namespace mhd {
+
+void prof_mark(mhd_ctx* c, int cls);
+void ghost_fill(mhd_ctx* c, const F8& S);
+void prim(mhd_ctx* c, const F8& S, bool cfl);        // primitives of S into c->P (+ CFL dt)
+void sweeps(mhd_ctx* c, const F8& S);                // all directions: c->L and c->ING
+void emf(mhd_ctx* c, const F8& S);                   // edge fields into c->E
+void ct_rk(mhd_ctx* c, const F8& U0, const F8& Us, const F8& Out, int mode);
+int stage_mode(int rk, int s);                       // COMB_* of stage s
+// Stage s of a step with explicit registers: Out = combine(U0, Us, L(Us)).
+void run_stage_regs(mhd_ctx* c, int s, const F8& U0, const F8& Us, const F8& Out, bool cfl);
+void run_stage(mhd_ctx* c, int s, bool cfl);         // on the context's registers
+void run_step(mhd_ctx* c, bool device_dt);
+void adjoint_free(mhd_ctx* c);                       // defined in mhd_adjoint.cu
+
+}  // namespace mhd

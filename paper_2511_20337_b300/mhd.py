@@ -31,7 +31,9 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_status", "mhd_launch_count", "mhd_strerror", "mhd_counters", "mhd_profile_steps", "mhd_probe_fp64",
            "mhd_step_noalloc", "mhd_batch_create", "mhd_batch_destroy", "mhd_batch_set_conserved",
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
-           "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps")
+           "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
+           "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim")
+FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 
 
@@ -92,6 +94,9 @@ def lib():
             "mhd_batch_status": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)]),
             "mhd_batch_launch_count": (ctypes.c_longlong, [P]),
             "mhd_batch_profile_steps": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
+            "mhd_adjoint_run": (I, [P, I, ctypes.POINTER(D), I, I, I, DPP, ctypes.POINTER(D), ctypes.POINTER(D)]),
+            "mhd_adjoint_grad_conserved": (I, [P, I, DPP, DPP]),
+            "mhd_adjoint_grad_prim": (I, [P, I, P, DPP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -263,6 +268,59 @@ class Sim:
         return {k: ms[i] for i, k in enumerate(KCLASSES)}, {k: cnt[i] for i, k in enumerate(KCLASSES)}
 
 
+    def adjoint(self, nsteps, dts=None, ckpt_every=20, functional="magnetic_energy", target=None):
+        """Run nsteps steps from the current state and take the gradient of the
+        final-state functional J (magnetic_energy, or misfit to `target`, a
+        list of 5 (3D) or 6 (2D) cell arrays rho, mx, my, mz, E[, b2]) with
+        respect to the initial state, the step sizes frozen (given `dts`, else
+        the CFL steps of this run).  Returns (J, dts used); the gradient is
+        read with grad_prim / grad_conserved."""
+        nsteps = int(nsteps)
+        d = None
+        if dts is not None:
+            dts = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+            if dts.shape != (nsteps,):
+                raise ValueError("dts must hold nsteps step sizes")
+            d = dts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        T, mem = None, MEM_HOST
+        if target is not None:
+            tg = list(target)
+            mem = MEM_DEVICE if _is_device(tg[0]) else MEM_HOST
+            if mem == MEM_HOST:
+                tg = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(self.shapes[0])) for a in tg]
+            self._keep_target = tg
+            T = _ptr_array(tg)
+        J = ctypes.c_double()
+        out = np.zeros(nsteps)
+        _check(lib().mhd_adjoint_run(self.h, nsteps, d, int(ckpt_every), FUNCTIONALS[functional], mem, T,
+                                     ctypes.byref(J), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "mhd_adjoint_run")
+        return J.value, out
+
+    def grad_prim(self, out=None):
+        """Gradient of the last adjoint run w.r.t. the initial rho, vx, vy, vz
+        (p and B held): dict of cell arrays, numpy or the given CUDA tensors."""
+        keys = ("rho", "vx", "vy", "vz")
+        if out is None:
+            out = {k: np.zeros(self.shapes[0]) for k in keys}
+        arrs = [out[k] for k in keys]
+        dev = _is_device(arrs[0])
+        _check(lib().mhd_adjoint_grad_prim(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr(arrs[0]),
+                                           _ptr_array(arrs[1:])), "mhd_adjoint_grad_prim")
+        return out
+
+    def grad_conserved(self, out=None):
+        """Gradient of the last adjoint run w.r.t. the initial conserved state
+        (keys of KEYS; the duplicate last face of a periodic axis carries 0)."""
+        if out is None:
+            out = {k: np.zeros(s) for k, s in zip(KEYS, self.shapes)}
+        arrs = [out[k] for k in KEYS]
+        dev = _is_device(arrs[0])
+        _check(lib().mhd_adjoint_grad_conserved(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
+                                                _ptr_array(arrs[5:])), "mhd_adjoint_grad_conserved")
+        return out
+
+
 def probe_fp64_gflops():
     """Measured FP64 FMA throughput of the current device (GFLOP/s, 2 per DFMA)."""
     g = ctypes.c_double()
@@ -361,3 +419,36 @@ class Batch:
         cnt = (ctypes.c_int * len(KCLASSES))()
         _check(lib().mhd_batch_profile_steps(self.h, int(nsteps), ms, cnt), "mhd_batch_profile_steps")
         return {k: ms[i] for i, k in enumerate(KCLASSES)}, {k: cnt[i] for i, k in enumerate(KCLASSES)}
+
+
+def final_functional(cfg, rho, vx, vy, vz, p, B, nsteps, dts=None, ckpt_every=20, functional="magnetic_energy",
+                     target=None):
+    """J(final state) as a differentiable function of the initial rho and v
+    (CUDA float64 tensors of the cell shape; p and the face fields B held
+    fixed), through torch.autograd: the forward runs libmhd's adjoint (the
+    step sizes frozen to `dts`, or to the CFL steps of this run), so backward
+    only scales the stored gradient."""
+    import torch
+
+    class _Final(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, rho_, vx_, vy_, vz_):
+            sim = Sim(cfg)
+            try:
+                sim.set_prim(rho_.contiguous(), [vx_.contiguous(), vy_.contiguous(), vz_.contiguous()],
+                             p.contiguous(), [b.contiguous() for b in B])
+                J, used = sim.adjoint(nsteps, dts, ckpt_every, functional, target)
+                g = {k: torch.empty_like(rho_) for k in ("rho", "vx", "vy", "vz")}
+                sim.grad_prim(g)
+                torch.cuda.synchronize(rho_.device)
+            finally:
+                sim.close()
+            ctx.save_for_backward(g["rho"], g["vx"], g["vy"], g["vz"])
+            ctx.dts = used
+            return torch.tensor(J, dtype=torch.float64, device=rho_.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            return tuple(gJ * t for t in ctx.saved_tensors)
+
+    return _Final.apply(rho, vx, vy, vz)

@@ -320,6 +320,35 @@ def adjoint_2d(n=256, *, seed=5, amp=0.05, kmax=6.0, **kw):
     return cfg, assemble(cfg, rho, vx, vy, vz, p, bx, by, bz)
 
 
+def smooth_2d(n=16, *, seed=5, bpert=0.0):
+    """Smooth 2D periodic state on the unit square with no exactly tied limiter
+    or min/max decision (a field constant along an axis ties minmod(0, 0),
+    where the scheme is only directionally differentiable): Gaussian random
+    rho, vx, vy (5 %, |k| <= 3), and vz, p and the cell B_z varying along both
+    axes; in-plane face field (1, 0.5), plus, for bpert > 0, the curl of the
+    periodic potential A_z = bpert/(2 pi) sin(2 pi x + 0.3) sin(2 pi y + 1.1)
+    (without it the face field is uniform, so derivatives with respect to the
+    initial face field meet minmod(0, 0) in the edge reconstruction).
+    Returns (cfg, state, prims)."""
+    cfg = base_cfg(2, (n, n), (0, 0), (1, 1))
+    rng = np.random.default_rng(seed)
+    X, Y, _ = cell_centres(cfg)
+    tp = 2 * np.pi
+    prim = {"rho": 1 + 0.05 * gaussian_field((n, n), rng, kmax=3.0)[None],
+            "vx": 0.05 * gaussian_field((n, n), rng, kmax=3.0)[None],
+            "vy": 0.05 * gaussian_field((n, n), rng, kmax=3.0)[None],
+            "vz": 0.03 * np.sin(tp * X + 1.0) * np.cos(tp * Y + 0.4),
+            "p": 1 + 0.05 * np.cos(tp * (X + 2 * Y) + 0.7)}
+    bx, by, _ = uniform_faces(cfg, (1.0, 0.5, 0.0))
+    if bpert > 0.0:
+        px, py, _ = faces_from_potential(
+            cfg, Az=lambda x, y, z: bpert / tp * np.sin(tp * x + 0.3) * np.sin(tp * y + 1.1))
+        bx, by = bx + px, by + py
+    bz = 0.2 + 0.1 * np.sin(tp * (2 * X + Y) + 0.3)
+    st = assemble(cfg, prim["rho"], prim["vx"], prim["vy"], prim["vz"], prim["p"], bx, by, bz)
+    return cfg, st, prim
+
+
 def random_state(cfg, seed, *, rho=(0.5, 1.5), v=0.5, p=(0.5, 1.5), bamp=0.5, b0=(0.3, -0.2, 0.25)):
     """White-noise state for parity checks: uniform-random rho, v, p per cell and a
     random edge potential plus a uniform field, so div B = 0 discretely and every

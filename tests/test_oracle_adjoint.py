@@ -73,24 +73,8 @@ def test_tape_gradient_equals_every_unit_jvp():
 
 
 def smooth_state(n=16, seed=5):
-    """Smooth state with no exactly tied limiter or min/max decision (a field
-    constant along an axis would tie minmod(0, 0) there, where the scheme is
-    only directionally differentiable): Gaussian random rho, vx, vy (5 %,
-    |k| <= 3), vz, p and cell B_z varying along both axes, uniform in-plane
-    face field."""
-    cfg = W.base_cfg(2, (n, n), (0, 0), (1, 1))
-    rng = np.random.default_rng(seed)
-    X, Y, _ = W.cell_centres(cfg)
-    tp = 2 * np.pi
-    prim = {"rho": 1 + 0.05 * W.gaussian_field((n, n), rng, kmax=3.0)[None],
-            "vx": 0.05 * W.gaussian_field((n, n), rng, kmax=3.0)[None],
-            "vy": 0.05 * W.gaussian_field((n, n), rng, kmax=3.0)[None],
-            "vz": 0.03 * np.sin(tp * X + 1.0) * np.cos(tp * Y + 0.4),
-            "p": 1 + 0.05 * np.cos(tp * (X + 2 * Y) + 0.7)}
-    bx, by, _ = W.uniform_faces(cfg, (1.0, 0.5, 0.0))
-    bz = 0.2 + 0.1 * np.sin(tp * (2 * X + Y) + 0.3)
-    st = W.assemble(cfg, prim["rho"], prim["vx"], prim["vy"], prim["vz"], prim["p"], bx, by, bz)
-    return cfg, st, prim, (bx, by, bz)
+    cfg, st, prim = W.smooth_2d(n, seed=seed)
+    return cfg, st, prim, (st["b0"], st["b1"], st["b2"])
 
 
 def test_gradient_matches_central_differences_on_smooth_run():
