@@ -56,7 +56,15 @@ WORKLOADS = {
                        "256 independent 2D Orszag-Tang runs (sizes from {64..512}^2, plasma beta in [0.1,10] and "
                        "Mach in [0.5,3] log-uniform, numpy default_rng(4)), PLM-minmod + HLLD + SSP-RK2 + UCT-HLL CT, "
                        "CFL 0.4, per-run CFL dt; batched launches in one CUDA graph, autotuned segment lengths"),
+    "adjoint2d-256": (lambda: W.adjoint_2d(256), "adjoint2d_plm_hlld_rk2",
+                      "adjoint: 2D 256^2 periodic unit square, rho = 1 + 0.05 g, v = 0.05 (g_x, g_y, 0), p = 1, "
+                      "B = (1, 0.5, 0), Gaussian random fields 1 <= |k| <= 6 from numpy default_rng(5); "
+                      "PLM-minmod + HLLD + SSP-RK2 + UCT-HLL CT, 400 CFL steps (dt recorded, then frozen); "
+                      "gradient of the final magnetic energy w.r.t. the initial rho and v, checkpoints every 20 steps"),
+    "adjoint2d-256-hll": (lambda: W.adjoint_2d(256, riemann="hll"), "adjoint2d_plm_hll_rk2",
+                          "adjoint2d-256 with the HLL Riemann solver"),
 }
+ADJOINT_STEPS, ADJOINT_CKPT = 400, 20
 # CPU-oracle sample of each workload: the same kind of state on a smaller grid
 SAMPLES = {
     "turbulent3d-256": (lambda: W.turbulent_3d(48), "turbulent 3D 48^3 (same scheme and field recipe)"),
@@ -67,7 +75,10 @@ SAMPLES = {
     "orszag-tang2d-128": (lambda: W.orszag_tang_2d(128), "Orszag-Tang 2D 128^2 (the workload itself)"),
     "ensemble2d-256": (lambda: ensemble_cases(16, max_n=128)[0],
                        "the first 16 ensemble members of at most 128^2 cells"),
+    "adjoint2d-256": (lambda: W.adjoint_2d(32), "the same recipe on 32^2, 8 steps"),
+    "adjoint2d-256-hll": (lambda: W.adjoint_2d(32, riemann="hll"), "the same recipe on 32^2, 8 steps (HLL)"),
 }
+ADJOINT_SAMPLE_STEPS = 8
 
 
 def ensemble_cases(count=256, max_n=None):
@@ -117,6 +128,33 @@ def flop_model(cfg, variant):
              + per["rk"] * elems)
     step = rk * stage + per["cfl"] * cells
     return {"sweep_per_launch": sweep, "step": step, "per_cell_update": step / cells}
+
+
+def adjoint_flop_model(cfg, variant):
+    """Algorithmic reverse-mode flops of one step (tape count of the oracle:
+    forward flops + partial derivatives + backward sweep, per unit) and of
+    one Riemann-transpose launch (one direction, one stage)."""
+    path = os.path.join(ROOT, "tests", "golden", "flops_per_unit.json")
+    per = json.load(open(path))["variants"][variant]["adjoint_per_unit"]
+    nd = cfg["ndim"]
+    n = list(cfg["n"][:nd])
+    rk = cfg["rk"]
+    cells = int(np.prod(n))
+    padded = int(np.prod([m + 4 for m in n]))
+    recon = faces = 0
+    faces_dir = []
+    for d in range(nd):
+        rows = int(np.prod([n[t] + 2 for t in range(nd) if t != d]))
+        recon += (n[d] + 2) * rows
+        faces += (n[d] + 1) * rows
+        faces_dir.append((n[d] + 1) * rows)
+    edges = (n[0] + 1) * (n[1] + 1) if nd == 2 else sum(
+        int(np.prod([n[e] + (1 if e != c else 0) for e in range(3)])) for c in range(3))
+    ct_faces = cells * nd
+    elems = cells * (6 if nd == 2 else 5) + ct_faces
+    stage = (per["c2p"] * padded + per["recon"] * recon + per["riemann"] * faces + per["fluxdiff"] * cells
+             + per["emf"] * edges + per["ct"] * ct_faces + per["rk"] * elems)
+    return {"step": rk * stage, "riemann_per_launch": per["riemann"] * sum(faces_dir) / nd}
 
 
 def sweep_traffic(variant, faces_per_launch):
@@ -215,7 +253,15 @@ def run_reference(args):
         return 0
     import oracle
     gen, desc = SAMPLES[args.workload]
-    if args.workload == "ensemble2d-256":
+    if args.workload.startswith("adjoint2d"):
+        cfg, st = gen()
+        for _ in range(min(args.warmup, 1)):
+            oracle_gradient_rate(cfg, st, ADJOINT_SAMPLE_STEPS)
+        rates = [oracle_gradient_rate(cfg, st, ADJOINT_SAMPLE_STEPS) for _ in range(args.steps)]
+        el = sum(r[1] for r in rates)
+        value = 3 * cells_of(cfg) * ADJOINT_SAMPLE_STEPS * args.steps / el
+        desc = f"{desc}, one tape gradient per step"
+    elif args.workload == "ensemble2d-256":
         cases = ensemble_cases(16, max_n=128)
         sims = [oracle.OracleSim(c, st) for c, st in cases]
         for _ in range(args.warmup):
@@ -511,6 +557,164 @@ def run_ensemble(args):
     return 0
 
 
+def oracle_gradient_rate(cfg, st, nsteps, which="magnetic_energy", seconds_budget=0.0):
+    """The oracle's reverse-mode (tape) gradient of an nsteps run, as it
+    stands, single-threaded, repeated until seconds_budget has passed:
+    (cell-updates/s counted as for the GPU adjoint, 3 per cell and step;
+    seconds; gradients taken)."""
+    import oracle
+    rho = st["rho"]
+    v = [st[k] / rho for k in ("mx", "my", "mz")]
+    bx, by, bz = W.cell_field(cfg, st["b0"], st["b1"], st["b2"])
+    g = cfg["gamma"]
+    p = (g - 1) * (st["E"] - 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2) - 0.5 * (bx ** 2 + by ** 2 + bz ** 2))
+    prim = {"rho": rho, "vx": v[0], "vy": v[1], "vz": v[2], "p": p}
+    dts = oracle.OracleSim(cfg, st).advance(nsteps, record_dt=True)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.grad_prim(cfg, prim, (st["b0"], st["b1"], st["b2"]), dts, which)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_budget:
+            break
+    return 3 * cells_of(cfg) * nsteps * reps / el, el, reps
+
+
+def run_adjoint(args):
+    """A step is one gradient evaluation: ADJOINT_STEPS forward steps from the
+    initial state with checkpoints, the block recomputes and the reverse pass.
+    Cell-updates count 3 per cell and time step (forward, recompute, reverse);
+    the phases are also reported separately."""
+    import torch
+    from paper_2511_20337_b300 import mhd
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gen, variant, desc = WORKLOADS[args.workload]
+    cfg, st = gen()
+    ncell = cells_of(cfg)
+    N, K = ADJOINT_STEPS, ADJOINT_CKPT
+    stream = torch.cuda.Stream(device=dev)
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in st.items()}
+    devs = {k: v.to(dev) for k, v in host.items()}
+    h2d = sum(v.numel() * 8 for v in host.values())
+    grad_host = {k: torch.empty_like(host["rho"]).pin_memory() for k in ("rho", "vx", "vy", "vz")}
+    d2h = sum(v.numel() * 8 for v in grad_host.values())
+    sim = mhd.Sim(cfg, devs, stream=stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    _, dts = sim.adjoint(N, None, K)  # records the CFL steps, then frozen
+    for _ in range(args.warmup):
+        sim.set_conserved(devs)
+        sim.adjoint(N, dts, K)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = sim.launches
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.set_conserved(devs)
+            J, _ = sim.adjoint(N, dts, K)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launches - launches0
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = 3 * ncell * N * args.steps * world / (t_max * 1e-3)
+
+    # phases and kernel classes (events on the library stream; syncs every reverse step)
+    sim.set_conserved(devs)
+    phases, classes = sim.adjoint_profile(N, dts, K)
+    peak = mhd.probe_fp64_gflops()
+    am = adjoint_flop_model(cfg, variant)
+    nd = cfg["ndim"]
+    riemann_launches = N * cfg["rk"] * nd
+    riemann_ms = classes["adj_riemann"]
+    achieved = am["riemann_per_launch"] * riemann_launches / (riemann_ms * 1e-3) / 1e9
+    eval_ms = t_max / args.steps
+    roofline = {"bound": "alu", "kernel": "adj_riemann_kernel (Riemann solver + flux difference transpose, per face)",
+                "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
+                "peak_source": "measured in this run: FP64 DFMA probe (mhd_probe_fp64), 2 flops per DFMA",
+                "algorithmic_flops_per_launch": am["riemann_per_launch"],
+                "algorithmic_definition": "reverse-mode work of the oracle's Riemann solve from its tape: forward "
+                                          "flops + partial-derivative flops + backward sweep (1 flop per +-1 link, "
+                                          "2 otherwise), per face",
+                "avg_launch_ms": riemann_ms / riemann_launches, "traffic": None,
+                "traffic_note": "no ncu capture of the adjoint kernels",
+                "gradient_achieved": am["step"] * N / (eval_ms * 1e-3) / 1e9,
+                "gradient_frac": am["step"] * N / (eval_ms * 1e-3) / 1e9 / peak,
+                "reverse_ms_by_class": classes}
+    phase_rates = {k: {"ms": v, "cell_updates_per_s": ncell * N / (v * 1e-3)} for k, v in phases.items()}
+
+    # the plain forward step on the same GPU, same grid and steps (graph replay)
+    ref = mhd.Sim(cfg, devs, stream=stream.cuda_stream)
+    ref.advance(3)
+    ref.set_conserved(devs)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    ref.advance(N)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = e0.elapsed_time(e1)
+    ref.close()
+
+    # end to end: state in from pinned host memory, gradient out to pinned host memory
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_conserved(host)
+        sim.adjoint(N, dts, K)
+        sim.grad_prim(grad_host)
+    el = time.perf_counter() - t0
+    e2e = {"value": 3 * ncell * N * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        scfg, sst = SAMPLES[args.workload][0]()
+        rate, sec, reps = oracle_gradient_rate(scfg, sst, ADJOINT_SAMPLE_STEPS, seconds_budget=args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{SAMPLES[args.workload][1]}: {reps} tape gradients in {sec:.1f} s, single thread"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": eval_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": desc, "grid": list(cfg["n"]), "cells": ncell, "time_steps": N,
+                           "checkpoint_every": K, "J": J,
+                           "step": "one gradient evaluation; 3 cell-updates per cell and time step "
+                                   "(forward, recompute, reverse)",
+                           "l2": "each gradient evaluation streams its checkpoints and stage states "
+                                 f"({(N // K + K * cfg['rk'] + 1) * h2d / 1e6:.0f} MB) through HBM, larger than L2",
+                           "dt": "CFL steps of the first run, then frozen", "parallelism": f"replicas x{world}"},
+                "phases": phase_rates,
+                "plain_step": {"value": ncell * N / (plain_ms * 1e-3), "unit": UNIT, "ms_per_step": plain_ms / N,
+                               "gradient_vs_plain_time": eval_ms / plain_ms},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def ctypes_stream(stream):
     return stream.cuda_stream
 
@@ -530,6 +734,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble2d-256":
         return run_ensemble(args)
+    if args.workload.startswith("adjoint2d"):
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -37,6 +37,25 @@ int mhd_profile_steps(mhd_ctx* ctx, int nsteps, double* ms_out, int* launches_ou
 typedef struct mhd_batch mhd_batch;
 int mhd_batch_profile_steps(mhd_batch* b, int nsteps, double* ms_out, int* launches_out);
 
+/* kernel classes of the adjoint's reverse pass (0..7 above: forward kernels
+ * re-run inside the stage transposes) */
+#define MHD_AKCLASS_COMBINE 8   /* RK-combine and CT-curl transposes */
+#define MHD_AKCLASS_EDGE    9   /* UCT edge-field transposes */
+#define MHD_AKCLASS_RIEMANN 10  /* Riemann solver + flux difference transposes */
+#define MHD_AKCLASS_RECON   11  /* PLM reconstruction transposes */
+#define MHD_AKCLASS_C2P     12  /* primitive-recovery transposes */
+#define MHD_AKCLASS_GHOST   13  /* ghost-fill transposes */
+#define MHD_NAKCLASS        14
+
+/* Run mhd_adjoint_run(ctx, nsteps, dts, ckpt_every, MHD_FUNC_MAGNETIC_ENERGY,
+ * ...) with CUDA events on the context stream: phase_ms[3] = device time of
+ * the forward pass, of the block recomputes and of the reverse pass;
+ * class_ms[MHD_NAKCLASS] splits the reverse pass by kernel class (event to
+ * event, so a memset counts with the kernel after it).  Syncs after every
+ * reverse step.  Leaves the context as mhd_adjoint_run does. */
+int mhd_adjoint_profile(mhd_ctx* ctx, int nsteps, const double* dts, int ckpt_every, double* phase_ms,
+                        double* class_ms);
+
 /* Measure the device's FP64 fused multiply-add throughput on the current
  * device: every SM runs independent chains of dependent DFMA for about
  * 20 ms; *gflops_out = 2 * DFMA per second / 1e9.  Sync; allocates and frees

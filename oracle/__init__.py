@@ -74,6 +74,8 @@ def lib():
         L.orc_grad_prim.argtypes = [ctypes.POINTER(OrcConfig), PP, PP, DP, ctypes.c_int, ctypes.c_int, PP, DP, PP]
         L.orc_count_flops.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
                                       ctypes.POINTER(ctypes.c_ulonglong)]
+        L.orc_count_tape.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
+                                     ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
         _lib = L
     return _lib
 
@@ -251,6 +253,18 @@ def count_flops(cfg, state, nsteps, dt):
     for i, ph in enumerate(PHASES):
         res[ph] = {op: int(out[i * len(OPS) + j]) for j, op in enumerate(OPS)}
     return res
+
+
+def count_tape(cfg, state, nsteps, dt):
+    """Reverse-mode work of nsteps steps (every state element a tape
+    variable): dict phase -> (backward-sweep flops, partial-derivative flops)."""
+    c = make_config(cfg)
+    shapes = state_shapes(cfg)
+    arrs = [np.ascontiguousarray(np.asarray(state[k], dtype=np.float64).reshape(s)) for k, s in zip(KEYS, shapes)]
+    links = (ctypes.c_ulonglong * len(PHASES))()
+    pfl = (ctypes.c_ulonglong * len(PHASES))()
+    lib().orc_count_tape(ctypes.byref(c), _ptrs(arrs), int(nsteps), float(dt), links, pfl)
+    return {ph: (int(links[i]), int(pfl[i])) for i, ph in enumerate(PHASES)}
 
 
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}

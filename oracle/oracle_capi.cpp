@@ -211,6 +211,31 @@ int orc_count_flops(const OrcConfig* c, const double* const* arrays, int nsteps,
   return 0;
 }
 
+// Reverse-mode work of nsteps steps of size dt from the given state, every
+// state element (cells and faces) a tape variable: out_links[PH_N] flops of
+// the backward sweep and out_pflops[PH_N] partial-derivative flops per phase.
+int orc_count_tape(const OrcConfig* c, const double* const* arrays, int nsteps, double dt,
+                   unsigned long long* out_links, unsigned long long* out_pflops) {
+  Sim<double> d(to_cfg(c));
+  load(d, arrays);
+  Sim<Tape> s(to_cfg(c));
+  g_tape.clear();
+  for (int q = 0; q < NQ; q++) {
+    auto& src = d.U0[q];
+    auto& dst = s.U0[q];
+    for (size_t i = 0; i < src.a.size(); i++) dst.a[i] = Tape::variable(src.a[i]);
+  }
+  g_tape_count.reset();
+  for (int t = 0; t < nsteps; t++) s.step(Tape(dt));
+  for (int ph = 0; ph < PH_N; ph++) {
+    out_links[ph] = g_tape_count.links[ph];
+    out_pflops[ph] = g_tape_count.partial_flops[ph];
+  }
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return s.bad ? -4 : 0;
+}
+
 // ---- final-state functional and its derivatives w.r.t. the initial rho, v ----
 // prim[0..4] = rho, vx, vy, vz, p (cell arrays); B[0..2] as in the state layout;
 // dts[nsteps] the frozen step sizes; which = 0 magnetic energy, 1 misfit to

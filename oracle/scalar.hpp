@@ -99,6 +99,21 @@ struct TapeNode {
 };
 inline std::vector<TapeNode> g_tape;
 
+// Reverse-mode work recorded on the tape, by phase of the step: the flops of
+// the backward sweep over the parent links (adj += w for a partial of +-1: 1;
+// adj += d w otherwise: 2) and the flops spent forming partial derivatives
+// (1/b and -q/b of a quotient: 2; 1/(2s) of a square root: 1).  Counting
+// only; the values are untouched.
+struct TapeCounter {
+  uint64_t links[PH_N] = {};  // backward-sweep flops
+  uint64_t partial_flops[PH_N] = {};
+  void reset() {
+    for (auto& x : links) x = 0;
+    for (auto& x : partial_flops) x = 0;
+  }
+};
+inline TapeCounter g_tape_count;
+
 struct Tape {
   double v;
   int i;
@@ -109,9 +124,12 @@ struct Tape {
     g_tape.push_back({-1, -1, 0.0, 0.0});
     return Tape(x, (int)g_tape.size() - 1);
   }
-  static Tape node(double x, int a, double da, int b, double db) {
+  static Tape node(double x, int a, double da, int b, double db, int partial_flops = 0) {
     if (a < 0 && b < 0) return Tape(x);
     g_tape.push_back({a, b, da, db});
+    auto cost = [](int p, double d) -> uint64_t { return p < 0 ? 0 : ((d == 1.0 || d == -1.0) ? 1 : 2); };
+    g_tape_count.links[g_flops.phase] += cost(a, da) + cost(b, db);
+    g_tape_count.partial_flops[g_flops.phase] += partial_flops;
     return Tape(x, (int)g_tape.size() - 1);
   }
 };
@@ -120,7 +138,7 @@ inline Tape operator-(Tape a, Tape b) { return Tape::node(a.v - b.v, a.i, 1.0, b
 inline Tape operator*(Tape a, Tape b) { return Tape::node(a.v * b.v, a.i, b.v, b.i, a.v); }
 inline Tape operator/(Tape a, Tape b) {
   double q = a.v / b.v;
-  return Tape::node(q, a.i, 1.0 / b.v, b.i, -q / b.v);
+  return Tape::node(q, a.i, 1.0 / b.v, b.i, -q / b.v, 2);
 }
 inline Tape operator-(Tape a) { return Tape::node(-a.v, a.i, -1.0, -1, 0.0); }
 inline bool operator<(Tape a, Tape b) { return a.v < b.v; }
@@ -130,7 +148,7 @@ inline bool operator>=(Tape a, Tape b) { return a.v >= b.v; }
 inline bool operator==(Tape a, Tape b) { return a.v == b.v; }
 inline Tape sqrt(Tape a) {
   double s = std::sqrt(a.v);
-  return Tape::node(s, a.i, s > 0.0 ? 0.5 / s : 0.0, -1, 0.0);
+  return Tape::node(s, a.i, s > 0.0 ? 0.5 / s : 0.0, -1, 0.0, 1);
 }
 inline Tape fabs(Tape a) { return a.v < 0.0 ? -a : a; }
 inline double value(Tape a) { return a.v; }

@@ -19,6 +19,7 @@
 #include "mhd_adjoint.cuh"
 #include "mhd_ctx.cuh"
 #include "mhd_host.cuh"
+#include "mhd_probe.h"
 
 using namespace mhd;
 
@@ -145,7 +146,9 @@ void adj_dir(mhd_ctx* c, const F8& Xs, const F8& As, double dt) {
   }
   adj_riemann_kernel<DIR, NDIM, RS><<<(int)((faces + 127) / 128), 128, 0, c->stream>>>(
       g, c->P, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL, a->WbR, As.q[5 + DIR]);
+  prof_mark(c, MHD_AKCLASS_RIEMANN);
   adj_recon_kernel<DIR, NDIM><<<(int)((cells + 127) / 128), 128, 0, c->stream>>>(g, c->P, a->WbL, a->WbR, a->Pb);
+  prof_mark(c, MHD_AKCLASS_RECON);
   c->launches += 2;
 }
 
@@ -166,9 +169,11 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Aout, const F8& A0, c
   const int nbe = blocks_for(edges, 256);
   adj_combine_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->LB, c0, c1, cL);
   adj_curl_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, a->LB, a->Eb, dt);
+  prof_mark(c, MHD_AKCLASS_COMBINE);
   adj_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Xs, c->ING, a->Eb, a->GE);
   long long box = (long long)(g.n[0] + 4) * (g.n[1] + 4) * (NDIM == 3 ? g.n[2] + 4 : 1);
   adj_edge_faces_kernel<NDIM><<<blocks_for(box, 256), 256, 0, c->stream>>>(g, a->GE, As);
+  prof_mark(c, MHD_AKCLASS_EDGE);
   CK(cudaMemsetAsync(a->Pb.q[0], 0, 8 * a->fe * sizeof(double), c->stream));
   c->launches += 4;
   adj_dir<NDIM, RS, 0>(c, Xs, As, dt);
@@ -177,8 +182,10 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Aout, const F8& A0, c
   adj_c2p_cells_kernel<NDIM><<<blocks_for(prim_work<NDIM>(g), 256), 256, 0, c->stream>>>(g, Xs, c->P, a->Pb, As);
   long long pad = (long long)g.ext[0] * g.ext[1] * g.ext[2];
   adj_c2p_faces_kernel<NDIM><<<blocks_for(pad, 256), 256, 0, c->stream>>>(g, a->Pb, As);
+  prof_mark(c, MHD_AKCLASS_C2P);
   for (int d = g.ndim - 1; d >= 0; d--)
     adj_ghost_periodic_kernel<<<blocks_for(ghost_layers_work(g, d), 256), 256, 0, c->stream>>>(g, As, d);
+  prof_mark(c, MHD_AKCLASS_GHOST);
   c->launches += 2 + g.ndim;
   CK(cudaGetLastError());
   return MHD_OK;
@@ -209,12 +216,22 @@ int seed(mhd_ctx* c, int functional) {
   return MHD_OK;
 }
 
-}  // namespace
 
-extern "C" {
+// Device times of one adjoint run, by phase and (reverse phase) by kernel class.
+struct Profile {
+  double phase_ms[3];  // forward pass, block recomputes, reverse pass
+  double class_ms[MHD_NAKCLASS];
+  cudaEvent_t e0, e1;
+};
 
-int mhd_adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int functional, int mem,
-                    const double* const* target, double* J_out, double* dts_out) {
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int functional, int mem,
+                const double* const* target, double* J_out, double* dts_out, Profile* prof) {
   if (!c || nsteps < 1 || ckpt_every < 1) return MHD_ERR_ARG;
   if (functional != MHD_FUNC_MAGNETIC_ENERGY && functional != MHD_FUNC_MISFIT) return MHD_ERR_ARG;
   if (functional == MHD_FUNC_MISFIT && (!target || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE))) return MHD_ERR_ARG;
@@ -243,6 +260,7 @@ int mhd_adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, i
   }
 
   // forward pass with checkpoints; dt frozen (given) or from the CFL condition
+  if (prof) CK(cudaEventRecord(prof->e0, c->stream));
   for (int n = 0; n < nsteps; n++) {
     if (n % k == 0) {
       rc = copy_state(c, state_at(a, n / k), c->U[0]);
@@ -259,6 +277,11 @@ int mhd_adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, i
     c->launches++;
   }
   CK(cudaGetLastError());
+  if (prof) {
+    CK(cudaEventRecord(prof->e1, c->stream));
+    CK(cudaEventSynchronize(prof->e1));
+    prof->phase_ms[0] = elapsed(prof->e0, prof->e1);
+  }
   a->dts.resize(nsteps);
   CK(cudaMemcpyAsync(a->dts.data(), a->scal + 1, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -275,6 +298,7 @@ int mhd_adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, i
     const int n0 = b * k, n1 = (n0 + k < nsteps) ? n0 + k : nsteps;
     const size_t base = (size_t)a->nck;  // block stage inputs follow the checkpoints
     auto X = [&](int n, int s) { return state_at(a, base + (size_t)(n - n0) * S + s); };
+    if (prof) CK(cudaEventRecord(prof->e0, c->stream));
     rc = copy_state(c, X(n0, 0), state_at(a, b));
     if (rc) return rc;
     for (int n = n0; n < n1; n++) {
@@ -285,13 +309,35 @@ int mhd_adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, i
         run_stage_regs(c, s, X(n, 0), X(n, s), out, false);
       }
     }
+    if (prof) {
+      CK(cudaEventRecord(prof->e1, c->stream));
+      CK(cudaEventSynchronize(prof->e1));
+      prof->phase_ms[1] += elapsed(prof->e0, prof->e1);
+    }
     for (int n = n1 - 1; n >= n0; n--) {
       const double dt = a->dts[n];
+      if (prof) {
+        c->prof_on = true;
+        c->prof_n = 0;
+        prof_mark(c, -1);
+      }
       for (int s = 0; s < S; s++) CK(cudaMemsetAsync(a->A[s].q[0], 0, 8 * a->fe * sizeof(double), c->stream));
       for (int s = S - 1; s >= 0; s--) {
         const F8& Aout = s == S - 1 ? Ain : a->A[s + 1];
         rc = adj_stage(c, s, X(n, s), Aout, a->A[0], a->A[s], dt);
-        if (rc) return rc;
+        if (rc) {
+          c->prof_on = false;
+          return rc;
+        }
+      }
+      if (prof) {
+        c->prof_on = false;
+        CK(cudaStreamSynchronize(c->stream));
+        for (int i = 1; i < c->prof_n; i++) {
+          double ms = elapsed(c->prof_ev[i - 1], c->prof_ev[i]);
+          prof->class_ms[c->prof_cls[i]] += ms;
+          prof->phase_ms[2] += ms;
+        }
       }
       // the cotangent of U^n becomes the incoming one of the step before
       F8 t = Ain;
@@ -311,6 +357,33 @@ int mhd_adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, i
   if (J_out) *J_out = a->J;
   if (dts_out) std::memcpy(dts_out, a->dts.data(), sizeof(double) * nsteps);
   return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhd_adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int functional, int mem,
+                    const double* const* target, double* J_out, double* dts_out) {
+  return adjoint_run(c, nsteps, dts, ckpt_every, functional, mem, target, J_out, dts_out, nullptr);
+}
+
+int mhd_adjoint_profile(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, double* phase_ms,
+                        double* class_ms) {
+  if (!c || !phase_ms || !class_ms) return MHD_ERR_ARG;
+  Profile p{};
+  for (int i = 0; i < 128; i++) CK(cudaEventCreate(&c->prof_ev[i]));
+  CK(cudaEventCreate(&p.e0));
+  CK(cudaEventCreate(&p.e1));
+  int rc = adjoint_run(c, nsteps, dts, ckpt_every, MHD_FUNC_MAGNETIC_ENERGY, MHD_MEM_HOST, nullptr, nullptr,
+                       nullptr, &p);
+  c->prof_on = false;
+  for (int i = 0; i < 128; i++) cudaEventDestroy(c->prof_ev[i]);
+  cudaEventDestroy(p.e0);
+  cudaEventDestroy(p.e1);
+  for (int i = 0; i < 3; i++) phase_ms[i] = p.phase_ms[i];
+  for (int k = 0; k < MHD_NAKCLASS; k++) class_ms[k] = p.class_ms[k];
+  return rc;
 }
 
 int mhd_adjoint_grad_conserved(mhd_ctx* c, int mem, double* const* gU, double* const* gB) {

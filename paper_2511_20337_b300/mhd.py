@@ -32,9 +32,10 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_step_noalloc", "mhd_batch_create", "mhd_batch_destroy", "mhd_batch_set_conserved",
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
-           "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim")
+           "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
+AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
 
 
 class MhdError(RuntimeError):
@@ -97,6 +98,7 @@ def lib():
             "mhd_adjoint_run": (I, [P, I, ctypes.POINTER(D), I, I, I, DPP, ctypes.POINTER(D), ctypes.POINTER(D)]),
             "mhd_adjoint_grad_conserved": (I, [P, I, DPP, DPP]),
             "mhd_adjoint_grad_prim": (I, [P, I, P, DPP]),
+            "mhd_adjoint_profile": (I, [P, I, ctypes.POINTER(D), I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -296,6 +298,19 @@ class Sim:
                                      ctypes.byref(J), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "mhd_adjoint_run")
         return J.value, out
+
+    def adjoint_profile(self, nsteps, dts=None, ckpt_every=20):
+        """Adjoint run of the magnetic energy with device times: (phase ms
+        {forward, recompute, reverse}, reverse-pass ms per kernel class)."""
+        nsteps = int(nsteps)
+        d = None
+        if dts is not None:
+            dts = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+            d = dts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        ph = (ctypes.c_double * 3)()
+        cl = (ctypes.c_double * len(AKCLASSES))()
+        _check(lib().mhd_adjoint_profile(self.h, nsteps, d, int(ckpt_every), ph, cl), "mhd_adjoint_profile")
+        return dict(zip(("forward", "recompute", "reverse"), ph)), {k: cl[i] for i, k in enumerate(AKCLASSES)}
 
     def grad_prim(self, out=None):
         """Gradient of the last adjoint run w.r.t. the initial rho, vx, vy, vz

@@ -16,6 +16,11 @@ the oracle's own loop ranges:
   ct        per evolved face and stage
   rk        per evolved element and stage
   cfl       per interior cell
+Each variant also gets the reverse-mode (adjoint) work per unit of the same
+phases, from the oracle's tape on one step: the forward flops, plus the flops
+that form the partial derivatives, plus the backward sweep over the tape
+links (an add for a partial of +-1, a multiply-add otherwise).  The CFL phase
+is not differentiated (dt frozen).
 Only this script writes the file, and it calls only oracle/.
 """
 import json
@@ -39,6 +44,8 @@ VARIANTS = {
     "orszag_tang2d_plm_hlld_rk2": lambda: W.orszag_tang_2d(32),
     "orszag_tang2d_plm_hll_rk2": lambda: W.orszag_tang_2d(32, riemann="hll"),
     "orszag_tang2d_wenoz_hlld_rk3": lambda: W.orszag_tang_2d(32, recon="wenoz", rk=3),
+    "adjoint2d_plm_hlld_rk2": lambda: W.adjoint_2d(32),
+    "adjoint2d_plm_hll_rk2": lambda: W.adjoint_2d(32, riemann="hll"),
 }
 
 
@@ -81,8 +88,16 @@ def main():
             tot = sum(counts[ph].values())
             per[ph] = tot / u[ph]
         per["div_sqrt_per_face"] = (counts["riemann"]["div"] + counts["riemann"]["sqrt"]) / u["riemann"]
+        tape = oracle.count_tape(cfg, st, 1, dt)
+        adj = {}
+        for ph in ("c2p", "recon", "riemann", "fluxdiff", "emf", "ct", "rk"):
+            links, pfl = tape[ph]
+            fwd = sum(counts[ph].values())
+            # the counting run's c2p units include the CFL pass, which the tape run does not make
+            u_adj = u[ph] * cfg["rk"] / (cfg["rk"] + 1) if ph == "c2p" else u[ph]
+            adj[ph] = (fwd * u_adj / u[ph] + pfl + links) / u_adj
         out["variants"][name] = {"config": {k: cfg[k] for k in ("ndim", "n", "recon", "riemann", "rk", "bc")},
-                                 "per_unit": per}
+                                 "per_unit": per, "adjoint_per_unit": adj}
     path = os.path.join(HERE, "flops_per_unit.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
