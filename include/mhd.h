@@ -147,6 +147,18 @@ int mhd_counters(mhd_ctx* ctx, long long* recon_fallbacks, long long* pressure_f
  * (graph replays count the kernels inside the graph). */
 long long mhd_launch_count(const mhd_ctx* ctx);
 
+/* Sweep segment length: the number of faces one thread of a sweep marches
+ * (default 16).  Shorter segments give more threads, longer ones fewer
+ * repeated Riemann solves at segment ends (one per segment); the result does
+ * not depend on it.  >= 1.  Sync. */
+int mhd_set_seglen(mhd_ctx* ctx, int seglen);
+
+/* Choose the segment length by timing two CFL steps for each of 2, 4, ..., 64
+ * (up to twice the longest axis) on the current state, which is restored
+ * afterwards together with the time and counters; *seglen_out (may be NULL)
+ * receives the choice.  Sync; allocates a temporary copy of the state. */
+int mhd_autotune(mhd_ctx* ctx, int* seglen_out);
+
 /* Static text for a return code. */
 const char* mhd_strerror(int code);
 

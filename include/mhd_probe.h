@@ -56,6 +56,17 @@ int mhd_batch_profile_steps(mhd_batch* b, int nsteps, double* ms_out, int* launc
 int mhd_adjoint_profile(mhd_ctx* ctx, int nsteps, const double* dts, int ckpt_every, double* phase_ms,
                         double* class_ms);
 
+/* The adjoint's vector-Jacobian product of the Riemann solver
+ * (MHD_RIEMANN_HLL / _HLLD) on n faces, by two independent routes: the
+ * forward-mode multi-tangent evaluation of the solver (dual) and the
+ * hand-written reverse the adjoint uses (hand).  Host arrays:
+ * in[15 n] = (rho, u, v, w, b1, b2, p of the left state, the same of the
+ * right state, b_n) per face in the sweep frame; cot[12 n] = (7 flux
+ * cotangents, 5 UCT-ingredient cotangents a+, a-, d, u_L, u_R); dual and
+ * hand [15 n] receive the cotangents of the 15 inputs.  Sync. */
+int mhd_probe_riemann_vjp(int riemann, int n, double gamma, const double* in, const double* cot, double* dual,
+                          double* hand);
+
 /* Measure the device's FP64 fused multiply-add throughput on the current
  * device: every SM runs independent chains of dependent DFMA for about
  * 20 ms; *gflops_out = 2 * DFMA per second / 1e9.  Sync; allocates and frees

@@ -31,6 +31,8 @@ struct AdjointState {
   double* pool = nullptr;     // scratch of the transposes
   double* states = nullptr;   // checkpoints, then the block's stage inputs
   size_t state_count = 0;
+  double* ings = nullptr;     // UCT ingredients of every stage of the block (5 ndim fields each)
+  size_t ing_count = 0;
   F8 A[4];                    // cotangent accumulators of the stage inputs (A[3]: incoming)
   L6 Lb;                      // cotangent of the stage increment (cells)
   L3 LB;                      // cotangent of the CT face increment
@@ -50,6 +52,7 @@ void adjoint_free(mhd_ctx* c) {
   if (!c || !c->adj) return;
   cudaFree(c->adj->pool);
   cudaFree(c->adj->states);
+  cudaFree(c->adj->ings);
   cudaFree(c->adj->Jcell);
   cudaFree(c->adj->scal);
   delete c->adj;
@@ -66,6 +69,14 @@ F8 state_at(const AdjointState* a, size_t idx) {
   F8 s;
   for (int q = 0; q < 8; q++) s.q[q] = a->states + (idx * 8 + q) * a->fe;
   return s;
+}
+
+// The stored ingredients of stage idx, laid out like the context's (direction-major).
+Ingr5x3 ing_at(const AdjointState* a, int ndim, size_t idx) {
+  Ingr5x3 g{};
+  for (int d = 0; d < ndim; d++)
+    for (int q = 0; q < 5; q++) g.a[d][q] = a->ings + (idx * 5 * ndim + (size_t)d * 5 + q) * a->fe;
+  return g;
 }
 
 int ensure_state(mhd_ctx* c, int nsteps, int k) {
@@ -106,6 +117,17 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
       return MHD_ERR_OOM;
     }
     a->state_count = need_states;
+  }
+  const size_t need_ings = (size_t)k * S;
+  if (a->ing_count < need_ings) {
+    cudaFree(a->ings);
+    a->ings = nullptr;
+    a->ing_count = 0;
+    if (cudaMalloc(&a->ings, need_ings * 5 * c->g.ndim * a->fe * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return MHD_ERR_OOM;
+    }
+    a->ing_count = need_ings;
   }
   if (a->nsteps < nsteps || !a->scal) {
     cudaFree(a->scal);
@@ -155,14 +177,14 @@ void adj_dir(mhd_ctx* c, const F8& Xs, const F8& As, double dt) {
 // Transpose of stage s at the stage input Xs: the cotangent Aout of the
 // stage output is distributed to A0 (U^n) and As (the stage input).
 template <int NDIM, int RS>
-int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Aout, const F8& A0, const F8& As, double dt) {
+int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const Ingr5x3& ING, const F8& Aout, const F8& A0, const F8& As,
+                double dt) {
   AdjointState* a = c->adj;
   const Grid& g = c->g;
-  // forward recompute of what the transposes read: ghosts, primitives and
-  // the UCT ingredients of Xs
+  // forward recompute of what the transposes read: ghosts and primitives of
+  // Xs (its UCT ingredients ING were kept by the block recompute)
   ghost_fill(c, Xs);
   prim(c, Xs, false);
-  sweeps(c, Xs);
   double c0, c1, cL;
   stage_coeffs(c->cfg.rk, s, c0, c1, cL);
   const long long edges = edge_work<NDIM>(g);
@@ -170,7 +192,7 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Aout, const F8& A0, c
   adj_combine_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->LB, c0, c1, cL);
   adj_curl_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, a->LB, a->Eb, dt);
   prof_mark(c, MHD_AKCLASS_COMBINE);
-  adj_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Xs, c->ING, a->Eb, a->GE);
+  adj_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Xs, ING, a->Eb, a->GE);
   long long box = (long long)(g.n[0] + 4) * (g.n[1] + 4) * (NDIM == 3 ? g.n[2] + 4 : 1);
   adj_edge_faces_kernel<NDIM><<<blocks_for(box, 256), 256, 0, c->stream>>>(g, a->GE, As);
   prof_mark(c, MHD_AKCLASS_EDGE);
@@ -191,11 +213,14 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Aout, const F8& A0, c
   return MHD_OK;
 }
 
-int adj_stage(mhd_ctx* c, int s, const F8& Xs, const F8& Aout, const F8& A0, const F8& As, double dt) {
+int adj_stage(mhd_ctx* c, int s, const F8& Xs, const Ingr5x3& ING, const F8& Aout, const F8& A0, const F8& As,
+              double dt) {
   const bool hlld = c->cfg.riemann == MHD_RIEMANN_HLLD;
   if (c->g.ndim == 2)
-    return hlld ? adj_stage_t<2, RS_HLLD>(c, s, Xs, Aout, A0, As, dt) : adj_stage_t<2, RS_HLL>(c, s, Xs, Aout, A0, As, dt);
-  return hlld ? adj_stage_t<3, RS_HLLD>(c, s, Xs, Aout, A0, As, dt) : adj_stage_t<3, RS_HLL>(c, s, Xs, Aout, A0, As, dt);
+    return hlld ? adj_stage_t<2, RS_HLLD>(c, s, Xs, ING, Aout, A0, As, dt)
+                : adj_stage_t<2, RS_HLL>(c, s, Xs, ING, Aout, A0, As, dt);
+  return hlld ? adj_stage_t<3, RS_HLLD>(c, s, Xs, ING, Aout, A0, As, dt)
+              : adj_stage_t<3, RS_HLL>(c, s, Xs, ING, Aout, A0, As, dt);
 }
 
 int seed(mhd_ctx* c, int functional) {
@@ -307,6 +332,10 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
       for (int s = 0; s < S; s++) {
         F8 out = s + 1 < S ? X(n, s + 1) : X(n + 1, 0);
         run_stage_regs(c, s, X(n, 0), X(n, s), out, false);
+        // keep the stage's UCT ingredients (the context's are contiguous, direction-major)
+        const Ingr5x3 keep = ing_at(a, g.ndim, (size_t)(n - n0) * S + s);
+        CK(cudaMemcpyAsync(keep.a[0][0], c->ING.a[0][0], (size_t)5 * g.ndim * a->fe * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->stream));
       }
     }
     if (prof) {
@@ -324,7 +353,7 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
       for (int s = 0; s < S; s++) CK(cudaMemsetAsync(a->A[s].q[0], 0, 8 * a->fe * sizeof(double), c->stream));
       for (int s = S - 1; s >= 0; s--) {
         const F8& Aout = s == S - 1 ? Ain : a->A[s + 1];
-        rc = adj_stage(c, s, X(n, s), Aout, a->A[0], a->A[s], dt);
+        rc = adj_stage(c, s, X(n, s), ing_at(a, g.ndim, (size_t)(n - n0) * S + s), Aout, a->A[0], a->A[s], dt);
         if (rc) {
           c->prof_on = false;
           return rc;
@@ -384,6 +413,33 @@ int mhd_adjoint_profile(mhd_ctx* c, int nsteps, const double* dts, int ckpt_ever
   for (int i = 0; i < 3; i++) phase_ms[i] = p.phase_ms[i];
   for (int k = 0; k < MHD_NAKCLASS; k++) class_ms[k] = p.class_ms[k];
   return rc;
+}
+
+int mhd_probe_riemann_vjp(int riemann, int n, double gamma, const double* in, const double* cot, double* dual,
+                          double* hand) {
+  if (n < 1 || !in || !cot || !dual || !hand || !(gamma > 1.0)) return MHD_ERR_ARG;
+  if (riemann != MHD_RIEMANN_HLL && riemann != MHD_RIEMANN_HLLD) return MHD_ERR_ARG;
+  double *d_in = nullptr, *d_cot = nullptr, *d_dual = nullptr, *d_hand = nullptr;
+  const size_t nin = (size_t)15 * n, ncot = (size_t)12 * n;
+  cudaError_t e = cudaMalloc(&d_in, nin * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_cot, ncot * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_dual, nin * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_hand, nin * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, in, nin * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_cot, cot, ncot * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int nb = (n + 127) / 128;
+    if (riemann == MHD_RIEMANN_HLLD) riemann_vjp_probe_kernel<RS_HLLD><<<nb, 128>>>(n, gamma, d_in, d_cot, d_dual, d_hand);
+    else riemann_vjp_probe_kernel<RS_HLL><<<nb, 128>>>(n, gamma, d_in, d_cot, d_dual, d_hand);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(dual, d_dual, nin * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(hand, d_hand, nin * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d_in);
+  cudaFree(d_cot);
+  cudaFree(d_dual);
+  cudaFree(d_hand);
+  return cuda_err(e);
 }
 
 int mhd_adjoint_grad_conserved(mhd_ctx* c, int mem, double* const* gU, double* const* gB) {

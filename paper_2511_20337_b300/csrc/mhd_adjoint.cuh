@@ -18,6 +18,7 @@
 #pragma once
 #include "mhd_kernels.cuh"
 #include "mhd_dual.cuh"
+#include "mhd_riemann_adj.cuh"
 
 namespace mhd {
 
@@ -398,9 +399,12 @@ __device__ __forceinline__ void sweep_box(const Grid& g, int lo[3], int ext[3], 
   }
 }
 
+// Vector-Jacobian product of the Riemann solver by forward-mode numbers: five
+// passes of three tangents over the 15 inputs (W_L, W_R, b_n).  Kept as the
+// cross-check of the hand-written reverse below.
 template <int RS>
-__device__ __forceinline__ void riemann_vjp(const double xin[15], double gamma, double igm1, const double Fb[7],
-                                            const double Ib[5], double xb[15]) {
+__device__ __forceinline__ void riemann_vjp_dual(const double xin[15], double gamma, double igm1, const double Fb[7],
+                                                 const double Ib[5], double xb[15]) {
 #pragma unroll
   for (int p = 0; p < 5; p++) {
     D3 in[15];
@@ -427,6 +431,45 @@ __device__ __forceinline__ void riemann_vjp(const double xin[15], double gamma, 
       xb[3 * p + t] = acc;
     }
   }
+}
+
+// Vector-Jacobian product of the Riemann solver by its hand-written reverse.
+template <int RS>
+__device__ __forceinline__ void riemann_vjp(const double xin[15], double gamma, double igm1, const double Fb[7],
+                                            const double Ib[5], double xb[15]) {
+  const W7 L = {xin[0], xin[1], xin[2], xin[3], xin[4], xin[5], xin[6]};
+  const W7 R = {xin[7], xin[8], xin[9], xin[10], xin[11], xin[12], xin[13]};
+  W7b Lb, Rb;
+  double bnb = 0.0;
+  if (RS == RS_HLLD) riemann_hlld_vjp(L, R, xin[14], gamma, igm1, Fb, Ib, Lb, Rb, bnb);
+  else riemann_hll_vjp(L, R, xin[14], gamma, igm1, Fb, Ib, Lb, Rb, bnb);
+  const double out[15] = {Lb.rho, Lb.u, Lb.v, Lb.w, Lb.b1, Lb.b2, Lb.p,
+                          Rb.rho, Rb.u, Rb.v, Rb.w, Rb.b1, Rb.b2, Rb.p, bnb};
+#pragma unroll
+  for (int i = 0; i < 15; i++) xb[i] = out[i];
+}
+
+// Both products on n faces: in[15 n] = (W_L, W_R, b_n) per face, cot[12 n] =
+// (flux cotangent 7, ingredient cotangent 5); dual / hand [15 n].
+template <int RS>
+static __global__ void riemann_vjp_probe_kernel(int n, double gamma, const double* __restrict__ in,
+                                                const double* __restrict__ cot, double* dual, double* hand) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  double x[15], Fb[7], Ib[5], xb[15];
+#pragma unroll
+  for (int i = 0; i < 15; i++) x[i] = in[15 * f + i];
+#pragma unroll
+  for (int i = 0; i < 7; i++) Fb[i] = cot[12 * f + i];
+#pragma unroll
+  for (int i = 0; i < 5; i++) Ib[i] = cot[12 * f + 7 + i];
+  const double igm1 = 1.0 / (gamma - 1.0);
+  riemann_vjp_dual<RS>(x, gamma, igm1, Fb, Ib, xb);
+#pragma unroll
+  for (int i = 0; i < 15; i++) dual[15 * f + i] = xb[i];
+  riemann_vjp<RS>(x, gamma, igm1, Fb, Ib, xb);
+#pragma unroll
+  for (int i = 0; i < 15; i++) hand[15 * f + i] = xb[i];
 }
 
 template <int DIR, int NDIM, int RS>

@@ -416,6 +416,64 @@ int mhd_last_dt(mhd_ctx* c, double* dt_out) {
 
 long long mhd_launch_count(const mhd_ctx* c) { return c ? c->launches : -1; }
 
+int mhd_set_seglen(mhd_ctx* c, int seglen) {
+  if (!c || seglen < 1) return MHD_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  c->seglen = seglen;
+  if (c->graph_ready) {  // the captured sweeps carry the old segment length
+    cudaGraphExecDestroy(c->graph);
+    c->graph_ready = false;
+  }
+  return MHD_OK;
+}
+
+int mhd_autotune(mhd_ctx* c, int* seglen_out) {
+  if (!c) return MHD_ERR_ARG;
+  if (!c->has_state) return MHD_ERR_STATE;
+  CK(cudaStreamSynchronize(c->stream));
+  DevScalars sc_h;
+  CK(cudaMemcpy(&sc_h, c->sc, sizeof(sc_h), cudaMemcpyDeviceToHost));
+  const size_t bytes = 8 * c->field_elems * sizeof(double);  // U[0]'s 8 fields are contiguous
+  double* backup = nullptr;
+  CK(cudaMalloc(&backup, bytes));
+  CK(cudaMemcpyAsync(backup, c->U[0].q[0], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  const int cand[6] = {2, 4, 8, 16, 32, 64};
+  int longest = 0;
+  for (int d = 0; d < c->g.ndim; d++) longest = c->g.n[d] + 1 > longest ? c->g.n[d] + 1 : longest;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int pick = c->seglen, rc = MHD_OK;
+  for (int i = 0; i < 6 && rc == MHD_OK; i++) {
+    if (cand[i] > 2 * longest) break;
+    c->seglen = cand[i];
+    run_step(c, true);  // warm
+    cudaEventRecord(e0, c->stream);
+    run_step(c, true);
+    run_step(c, true);
+    cudaEventRecord(e1, c->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { rc = cuda_err(e); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; pick = cand[i]; }
+    cudaMemcpyAsync(c->U[0].q[0], backup, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(backup);
+  CK(cudaMemcpy(c->sc, &sc_h, sizeof(sc_h), cudaMemcpyHostToDevice));
+  c->seglen = pick;
+  if (c->graph_ready) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph_ready = false;
+  }
+  if (seglen_out) *seglen_out = pick;
+  return rc;
+}
+
 int mhd_counters(mhd_ctx* c, long long* recon_fallbacks, long long* pressure_floors) {
   if (!c) return MHD_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));

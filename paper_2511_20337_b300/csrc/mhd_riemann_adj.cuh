@@ -1,0 +1,516 @@
+// Hand-written reverse (vector-Jacobian product) of the HLL and HLLD solvers
+// of mhd_math.cuh.  Each function first repeats the forward arithmetic of its
+// solver, with the same operations in the same order, so that every branch
+// (wave fan, degeneracies, min/max, clamps) is decided by the same values;
+// it then walks the operations backwards, accumulating cotangents.  The
+// derivative conventions are those of the forward-mode numbers of
+// mhd_dual.cuh: a clamped or selected quantity passes the derivative of the
+// branch taken, sqrt(0) has derivative 0.
+#pragma once
+#include "mhd_math.cuh"
+
+namespace mhd {
+
+// Cotangents of one side's sweep-frame primitives W = (rho, u, v, w, b1, b2, p).
+struct W7b {
+  double rho = 0.0, u = 0.0, v = 0.0, w = 0.0, b1 = 0.0, b2 = 0.0, p = 0.0;
+};
+
+// fast_speed: cotangents of rho, p, B2, bn2 from that of cf.
+__device__ __forceinline__ void fast_speed_vjp(double rho, double p, double B2, double bn2, double gamma, double cfb,
+                                               double& rhob, double& pb, double& B2b, double& bn2b) {
+  const double gp = mul_rn(gamma, p);
+  const double s = gp + B2;
+  double disc = fma(s, s, -(4.0 * gp) * bn2);
+  if (lt0(disc)) disc = 0.0;
+  const double sq = fsqrt0(disc);
+  const double irho = rcp(rho);
+  const double h = 0.5 * irho;
+  const double t = s + sq;
+  const double cf = fsqrt(t * h);
+  // reverse
+  const double cf2b = cfb * (0.5 * rcp(cf));
+  const double tb = cf2b * h;
+  rhob += (0.5 * (cf2b * t)) * (-(irho * irho));
+  double sb = tb, gpb = 0.0;
+  if (gt0(disc)) {
+    const double discb = tb * (0.5 * rcp(sq));
+    sb += discb * (2.0 * s);
+    gpb += discb * (-4.0 * bn2);
+    bn2b += discb * (-4.0 * gp);
+  }
+  gpb += sb;
+  B2b += sb;
+  pb += gamma * gpb;
+}
+
+// Total field, total pressure and fast speed of one side (side_lite):
+// cotangents of W and bn2 from those of B2 (direct uses), pT and cf.
+__device__ __forceinline__ void side_lite_vjp(const W7& W, double bn2, double gamma, double B2, double B2b, double pTb,
+                                              double cfb, W7b& Wb, double& bn2b) {
+  fast_speed_vjp(W.rho, W.p, B2, bn2, gamma, cfb, Wb.rho, Wb.p, B2b, bn2b);
+  Wb.p += pTb;
+  B2b += 0.5 * pTb;
+  Wb.b1 += (2.0 * W.b1) * B2b;
+  Wb.b2 += (2.0 * W.b2) * B2b;
+  bn2b += B2b;
+}
+
+// Conserved state U, flux F and v.B of one side (side_full) given its B2 and
+// pT: cotangents of W, bn, bn2, B2 and pT from those of U, F and v.B.
+__device__ __forceinline__ void side_full_vjp(const W7& W, double bn, double igm1, double B2, double pT,
+                                              const double Ub[7], const double Fb[7], double vBb, W7b& Wb,
+                                              double& bnb, double& bn2b, double& B2b, double& pTb) {
+  const double vB = fma(W.u, bn, fma(W.v, W.b1, W.w * W.b2));
+  const double v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
+  const double E = fma(W.p, igm1, 0.5 * fma(W.rho, v2, B2));
+  const double mu = W.rho * W.u;
+  double mub = Fb[0] + Ub[1];
+  double Eb = Ub[6];
+  // F1 = mu u + pT - bn2
+  mub += Fb[1] * W.u;
+  Wb.u += Fb[1] * mu;
+  pTb += Fb[1];
+  bn2b -= Fb[1];
+  // F2 = mu v - bn b1, F3 = mu w - bn b2
+  mub += Fb[2] * W.v + Fb[3] * W.w;
+  Wb.v += Fb[2] * mu;
+  Wb.w += Fb[3] * mu;
+  bnb -= Fb[2] * W.b1 + Fb[3] * W.b2;
+  Wb.b1 -= Fb[2] * bn;
+  Wb.b2 -= Fb[3] * bn;
+  // F4 = u b1 - v bn, F5 = u b2 - w bn
+  Wb.u += Fb[4] * W.b1 + Fb[5] * W.b2;
+  Wb.b1 += Fb[4] * W.u;
+  Wb.b2 += Fb[5] * W.u;
+  Wb.v -= Fb[4] * bn;
+  Wb.w -= Fb[5] * bn;
+  bnb -= Fb[4] * W.v + Fb[5] * W.w;
+  // F6 = (E + pT) u - bn vB
+  Eb += Fb[6] * W.u;
+  pTb += Fb[6] * W.u;
+  Wb.u += Fb[6] * (E + pT);
+  bnb -= Fb[6] * vB;
+  vBb -= Fb[6] * bn;
+  // U = (rho, mu, rho v, rho w, b1, b2, E)
+  Wb.rho += Ub[0] + Ub[2] * W.v + Ub[3] * W.w;
+  Wb.v += Ub[2] * W.rho;
+  Wb.w += Ub[3] * W.rho;
+  Wb.b1 += Ub[4];
+  Wb.b2 += Ub[5];
+  // mu = rho u
+  Wb.rho += mub * W.u;
+  Wb.u += mub * W.rho;
+  // E = p/(G-1) + (rho v2 + B2)/2
+  Wb.p += Eb * igm1;
+  Wb.rho += (0.5 * Eb) * v2;
+  const double v2b = (0.5 * Eb) * W.rho;
+  B2b += 0.5 * Eb;
+  Wb.u += (2.0 * W.u) * v2b;
+  Wb.v += (2.0 * W.v) * v2b;
+  Wb.w += (2.0 * W.w) * v2b;
+  // vB = u bn + v b1 + w b2
+  Wb.u += vBb * bn;
+  bnb += vBb * W.u;
+  Wb.v += vBb * W.b1;
+  Wb.b1 += vBb * W.v;
+  Wb.w += vBb * W.b2;
+  Wb.b2 += vBb * W.w;
+}
+
+// Outer speeds and UCT ingredients (speeds / the head of riemann_hlld):
+// cotangents of uL, uR, cfL, cfR from those of the ingredients and of SL, SR.
+__device__ __forceinline__ void speeds_vjp(double uL, double uR, double cfL, double cfR, const double Ib[5],
+                                           double SLb, double SRb, double& uLb, double& uRb, double& cfLb,
+                                           double& cfRb) {
+  const bool c_right = bits(cfL) < bits(cfR);              // imax_pos picks cfR
+  const double cmax = c_right ? cfR : cfL;
+  const bool min_right = order_key(uR) < order_key(uL);     // imin picks uR
+  const bool max_right = order_key(uL) < order_key(uR);     // imax picks uR
+  const double SL = (min_right ? uR : uL) - cmax;
+  const double SR = (max_right ? uR : uL) + cmax;
+  const double aR = gt0(SR) ? SR : 0.0, aL = lt0(SL) ? SL : 0.0;
+  const double inv = rcp(aR - aL);
+  // ap = aR inv, am = -aL inv, dd = -(aR aL) inv
+  const double invb = Ib[0] * aR - Ib[1] * aL - Ib[2] * (aR * aL);
+  double aRb = (Ib[0] - Ib[2] * aL) * inv;
+  double aLb = (-Ib[1] - Ib[2] * aR) * inv;
+  const double denb = invb * (-(inv * inv));
+  aRb += denb;
+  aLb -= denb;
+  if (gt0(SR)) SRb += aRb;
+  if (lt0(SL)) SLb += aLb;
+  uLb += Ib[3];
+  uRb += Ib[4];
+  if (max_right) uRb += SRb;
+  else uLb += SRb;
+  if (min_right) uRb += SLb;
+  else uLb += SLb;
+  const double cmaxb = SRb - SLb;
+  if (c_right) cfRb += cmaxb;
+  else cfLb += cmaxb;
+}
+
+// ---------------------------------------------------------------------------
+// HLL
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void riemann_hll_vjp(const W7& L, const W7& R, double bn, double gamma, double igm1,
+                                                const double Fb[7], const double Ib[5], W7b& Lb, W7b& Rb,
+                                                double& bnb) {
+  const double bn2 = bn * bn;
+  Side sl, sr;
+  side_state(L, bn, bn2, gamma, igm1, sl);
+  side_state(R, bn, bn2, gamma, igm1, sr);
+  const double cmax = imax_pos(sl.cf, sr.cf);
+  const double SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
+  double ULb[7] = {0, 0, 0, 0, 0, 0, 0}, FLb[7] = {0, 0, 0, 0, 0, 0, 0};
+  double URb[7] = {0, 0, 0, 0, 0, 0, 0}, FRb[7] = {0, 0, 0, 0, 0, 0, 0};
+  double SLb = 0.0, SRb = 0.0;
+  if (ge0(SL)) {
+#pragma unroll
+    for (int q = 0; q < 7; q++) FLb[q] = Fb[q];
+  } else if (!gt0(SR)) {
+#pragma unroll
+    for (int q = 0; q < 7; q++) FRb[q] = Fb[q];
+  } else {
+    // F = (SR SL (UR - UL) + SR FL - SL FR) inv,  inv = 1/(SR - SL)
+    const double inv = rcp(SR - SL);
+    const double sls = SR * SL;
+    double invb = 0.0, slsb = 0.0;
+#pragma unroll
+    for (int q = 0; q < 7; q++) {
+      const double dU = sr.U[q] - sl.U[q];
+      const double N = fma(sls, dU, fma(SR, sl.F[q], -SL * sr.F[q]));
+      const double Nb = Fb[q] * inv;
+      invb += Fb[q] * N;
+      slsb += Nb * dU;
+      URb[q] += Nb * sls;
+      ULb[q] -= Nb * sls;
+      SRb += Nb * sl.F[q];
+      FLb[q] += Nb * SR;
+      SLb -= Nb * sr.F[q];
+      FRb[q] -= Nb * SL;
+    }
+    SRb += slsb * SL;
+    SLb += slsb * SR;
+    const double db = invb * (-(inv * inv));
+    SRb += db;
+    SLb -= db;
+  }
+  double uLb = 0.0, uRb = 0.0, cfLb = 0.0, cfRb = 0.0;
+  speeds_vjp(L.u, R.u, sl.cf, sr.cf, Ib, SLb, SRb, uLb, uRb, cfLb, cfRb);
+  Lb.u += uLb;
+  Rb.u += uRb;
+  double bn2b = 0.0, B2bL = 0.0, pTbL = 0.0, B2bR = 0.0, pTbR = 0.0;
+  side_full_vjp(L, bn, igm1, sl.B2, sl.pT, ULb, FLb, 0.0, Lb, bnb, bn2b, B2bL, pTbL);
+  side_full_vjp(R, bn, igm1, sr.B2, sr.pT, URb, FRb, 0.0, Rb, bnb, bn2b, B2bR, pTbR);
+  side_lite_vjp(L, bn2, gamma, sl.B2, B2bL, pTbL, cfLb, Lb, bn2b);
+  side_lite_vjp(R, bn2, gamma, sr.B2, B2bR, pTbR, cfRb, Rb, bn2b);
+  bnb += (2.0 * bn) * bn2b;
+}
+
+// ---------------------------------------------------------------------------
+// HLLD
+// ---------------------------------------------------------------------------
+// Star transverse state of one side (both branches of riemann_hlld), with the
+// intermediates the reverse needs.
+struct StarT {
+  double sd, rs, sm, ism, rhos, vs, ws, b1s, b2s;
+  double iD, cv, cb;  // regular branch only
+  bool degen;
+};
+__device__ __forceinline__ void star_side(const W7& W, double S, double SM, double bn, double bn2, StarT& t) {
+  t.sd = S - W.u;
+  t.rs = t.sd * W.rho;
+  t.sm = S - SM;
+  t.ism = rcp(t.sm);
+  t.rhos = t.rs * t.ism;
+  const double rsm = mul_rn(t.rs, t.sm), D = rsm - bn2;
+  t.degen = lt_pos(fabs(D), kHlldDegenEps * rsm);
+  if (t.degen) {
+    t.vs = W.v; t.ws = W.w; t.b1s = W.b1; t.b2s = W.b2;
+    t.iD = t.cv = t.cb = 0.0;
+  } else {
+    t.iD = rcp(D);
+    t.cv = (bn * (SM - W.u)) * t.iD;
+    t.vs = fma(-W.b1, t.cv, W.v);
+    t.ws = fma(-W.b2, t.cv, W.w);
+    t.cb = fma(t.rs, t.sd, -bn2) * t.iD;
+    t.b1s = W.b1 * t.cb;
+    t.b2s = W.b2 * t.cb;
+  }
+}
+// Cotangents of one side's star quantities, accumulated by the reverse.
+struct StarB {
+  double rhos = 0.0, vs = 0.0, ws = 0.0, b1s = 0.0, b2s = 0.0, ism = 0.0, sd = 0.0, rs = 0.0;
+};
+// Reverse of star_side down to rs and sd (their own reverse, rs = sd rho and
+// sd = S - u, runs after the contact-speed reverse has added to them).
+__device__ __forceinline__ void star_side_vjp(const W7& W, double SM, double bn, double bn2, const StarT& t, StarB& b,
+                                              W7b& Wb, double& Sb, double& SMb, double& bnb, double& bn2b) {
+  double smb = 0.0;
+  if (t.degen) {
+    Wb.v += b.vs;
+    Wb.w += b.ws;
+    Wb.b1 += b.b1s;
+    Wb.b2 += b.b2s;
+  } else {
+    Wb.b1 += b.b1s * t.cb - b.vs * t.cv;
+    Wb.b2 += b.b2s * t.cb - b.ws * t.cv;
+    Wb.v += b.vs;
+    Wb.w += b.ws;
+    const double cbb = b.b1s * W.b1 + b.b2s * W.b2;
+    const double cvb = -(b.vs * W.b1 + b.ws * W.b2);
+    // cb = (rs sd - bn2) iD
+    const double Nbb = cbb * t.iD;
+    double iDb = cbb * fma(t.rs, t.sd, -bn2);
+    b.rs += Nbb * t.sd;
+    b.sd += Nbb * t.rs;
+    bn2b -= Nbb;
+    // cv = bn (SM - u) iD
+    const double du = SM - W.u;
+    const double Nvb = cvb * t.iD;
+    iDb += cvb * (bn * du);
+    bnb += Nvb * du;
+    SMb += Nvb * bn;
+    Wb.u -= Nvb * bn;
+    // iD = 1/D, D = rs sm - bn2
+    const double Db = iDb * (-(t.iD * t.iD));
+    bn2b -= Db;
+    b.rs += Db * t.sm;
+    smb += Db * t.rs;
+  }
+  // rhos = rs ism, ism = 1/sm, sm = S - SM
+  b.rs += b.rhos * t.ism;
+  b.ism += b.rhos * t.rs;
+  smb += b.ism * (-(t.ism * t.ism));
+  Sb += smb;
+  SMb -= smb;
+}
+
+__device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, double bn, double gamma, double igm1,
+                                                 const double Fb[7], const double Ib[5], W7b& Lb, W7b& Rb,
+                                                 double& bnb) {
+  const double bn2 = bn * bn;
+  SideLiteT<double> ll, lr;
+  side_lite(L, bn2, gamma, ll);
+  side_lite(R, bn2, gamma, lr);
+  const double cmax = imax_pos(ll.cf, lr.cf);
+  const double SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
+  double SLb = 0.0, SRb = 0.0, bn2b = 0.0;
+  double B2bL = 0.0, pTbL = 0.0, B2bR = 0.0, pTbR = 0.0;
+  if (gt0(SL) || lt0(SR)) {  // supersonic: the upwind physical flux
+    const bool up_left = gt0(SL);
+    const double Ub[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (up_left) side_full_vjp(L, bn, igm1, ll.B2, ll.pT, Ub, Fb, 0.0, Lb, bnb, bn2b, B2bL, pTbL);
+    else side_full_vjp(R, bn, igm1, lr.B2, lr.pT, Ub, Fb, 0.0, Rb, bnb, bn2b, B2bR, pTbR);
+  } else {
+    // ---- primal, as in riemann_hlld ----
+    const double sdL = SL - L.u, sdR = SR - R.u;
+    const double rsL = sdL * L.rho, rsR = sdR * R.rho;
+    const double iden = rcp(rsR - rsL);
+    const double NM = (fma(rsR, R.u, -rsL * L.u) - lr.pT) + ll.pT;
+    const double SM = NM * iden;
+    const double a1 = (L.rho * rsR) * sdL;
+    const double Np = fma(a1, R.u - L.u, fma(rsR, ll.pT, -rsL * lr.pT));
+    const double pTs = Np * iden;
+    StarT tL, tR;
+    star_side(L, SL, SM, bn, bn2, tL);
+    star_side(R, SR, SM, bn, bn2, tR);
+    const bool left = ge0(SM);
+    const W7& A = left ? L : R;
+    const StarT& ta = left ? tL : tR;
+    const double pTa = left ? ll.pT : lr.pT, B2a = left ? ll.B2 : lr.B2;
+    const double S = left ? SL : SR;
+    double Ua[7], Fa[7], vBa;
+    side_full(A, bn, bn2, igm1, left ? ll : lr, Ua, Fa, vBa);
+    const double vBs = fma(SM, bn, fma(ta.vs, ta.b1s, ta.ws * ta.b2s));
+    const double NE = fma(ta.sd, Ua[6], -pTa * A.u) + fma(pTs, SM, bn * (vBa - vBs));
+    const double Es = NE * ta.ism;
+    const double Us[7] = {ta.rhos, ta.rhos * SM, ta.rhos * ta.vs, ta.rhos * ta.ws, ta.b1s, ta.b2s, Es};
+    StarB bL, bR;
+    StarB& ba = left ? bL : bR;
+    double SMb = 0.0, pTsb = 0.0, Sb = 0.0, Esb = 0.0, vBsb = 0.0;
+    double Usb[7] = {0, 0, 0, 0, 0, 0, 0};
+    // ---- rotational waves ----
+    if (!lt_pos(0.5 * bn2, kHlldBnEps * pTs)) {
+      const double iqL = frsqrt(tL.rhos), iqR = frsqrt(tR.rhos);
+      const double sqL = tL.rhos * iqL, sqR = tR.rhos * iqR;
+      const double abn = fabs(bn);
+      const double Ss = left ? fma(-abn, iqL, SM) : fma(abn, iqR, SM);
+      const bool beyond = left ? lt0(Ss) : ge0(Ss);
+      if (beyond) {
+        const double sg = gt0(bn) ? 1.0 : -1.0;
+        const double isum = rcp(sqL + sqR);
+        const double Nv = fma(sqL, tL.vs, fma(sqR, tR.vs, times_sign(tR.b1s - tL.b1s, bn)));
+        const double Nw = fma(sqL, tL.ws, fma(sqR, tR.ws, times_sign(tR.b2s - tL.b2s, bn)));
+        const double vss = Nv * isum, wss = Nw * isum;
+        const double sq2 = sqL * sqR;
+        const double N1 = fma(sqL, tR.b1s, fma(sqR, tL.b1s, times_sign(sq2 * (tR.vs - tL.vs), bn)));
+        const double N2 = fma(sqL, tR.b2s, fma(sqR, tL.b2s, times_sign(sq2 * (tR.ws - tL.ws), bn)));
+        const double b1ss = N1 * isum, b2ss = N2 * isum;
+        const double vBss = fma(SM, bn, fma(vss, b1ss, wss * b2ss));
+        const double sqa = left ? -sqL : sqR;
+        const double dvB = vBs - vBss;
+        const double Ess = fma(sqa, times_sign(dvB, bn), Es);
+        // F2..F6 += S*_a (U** - U*)
+        double Ssb = Fb[2] * fma(ta.rhos, vss, -Us[2]) + Fb[3] * fma(ta.rhos, wss, -Us[3]) +
+                     Fb[4] * (b1ss - ta.b1s) + Fb[5] * (b2ss - ta.b2s) + Fb[6] * (Ess - Es);
+        ba.rhos += Ss * (Fb[2] * vss + Fb[3] * wss);
+        double vssb = Fb[2] * Ss * ta.rhos, wssb = Fb[3] * Ss * ta.rhos;
+        Usb[2] -= Fb[2] * Ss;
+        Usb[3] -= Fb[3] * Ss;
+        double b1ssb = Fb[4] * Ss, b2ssb = Fb[5] * Ss;
+        ba.b1s -= Fb[4] * Ss;
+        ba.b2s -= Fb[5] * Ss;
+        const double Essb = Fb[6] * Ss;
+        Esb -= Fb[6] * Ss;
+        // Ess = Es + sqa sg (vBs - vBss)
+        Esb += Essb;
+        const double sqab = Essb * sg * dvB;
+        vBsb += Essb * sqa * sg;
+        const double vBssb = -Essb * sqa * sg;
+        double sqLb = left ? -sqab : 0.0, sqRb = left ? 0.0 : sqab;
+        // vBss = SM bn + vss b1ss + wss b2ss
+        SMb += vBssb * bn;
+        bnb += vBssb * SM;
+        vssb += vBssb * b1ss;
+        b1ssb += vBssb * vss;
+        wssb += vBssb * b2ss;
+        b2ssb += vBssb * wss;
+        // b1ss, b2ss
+        double isumb = b1ssb * N1 + b2ssb * N2 + vssb * Nv + wssb * Nw;
+        const double N1b = b1ssb * isum, N2b = b2ssb * isum, Nvb = vssb * isum, Nwb = wssb * isum;
+        sqLb += N1b * tR.b1s + N2b * tR.b2s + Nvb * tL.vs + Nwb * tL.ws;
+        sqRb += N1b * tL.b1s + N2b * tL.b2s + Nvb * tR.vs + Nwb * tR.ws;
+        bR.b1s += N1b * sqL + Nvb * sg;
+        bL.b1s += N1b * sqR - Nvb * sg;
+        bR.b2s += N2b * sqL + Nwb * sg;
+        bL.b2s += N2b * sqR - Nwb * sg;
+        const double t1 = N1b * sg, t2 = N2b * sg;
+        const double sq2b = t1 * (tR.vs - tL.vs) + t2 * (tR.ws - tL.ws);
+        bR.vs += t1 * sq2 + Nvb * sqR;
+        bL.vs += -t1 * sq2 + Nvb * sqL;
+        bR.ws += t2 * sq2 + Nwb * sqR;
+        bL.ws += -t2 * sq2 + Nwb * sqL;
+        sqLb += sq2b * sqR;
+        sqRb += sq2b * sqL;
+        // isum = 1/(sqL + sqR)
+        const double db = isumb * (-(isum * isum));
+        sqLb += db;
+        sqRb += db;
+        // Ss
+        SMb += Ssb;
+        double iqLb = 0.0, iqRb = 0.0, abnb;
+        if (left) {
+          abnb = -Ssb * iqL;
+          iqLb -= Ssb * abn;
+        } else {
+          abnb = Ssb * iqR;
+          iqRb += Ssb * abn;
+        }
+        bnb += lt0(bn) ? -abnb : abnb;
+        // sq = rhos iq, iq = rhos^(-1/2)
+        bL.rhos += sqLb * iqL;
+        iqLb += sqLb * tL.rhos;
+        bR.rhos += sqRb * iqR;
+        iqRb += sqRb * tR.rhos;
+        bL.rhos += iqLb * (-0.5 * (iqL * iqL) * iqL);
+        bR.rhos += iqRb * (-0.5 * (iqR * iqR) * iqR);
+      }
+    }
+    // ---- F = F_a + S_a (U*_a - U_a) ----
+    double Uab[7];
+#pragma unroll
+    for (int q = 0; q < 7; q++) {
+      Sb += Fb[q] * (Us[q] - Ua[q]);
+      Usb[q] += Fb[q] * S;
+      Uab[q] = -Fb[q] * S;
+    }
+    // U*_a = (rhos, rhos SM, rhos vs, rhos ws, b1s, b2s, Es)
+    ba.rhos += Usb[0] + Usb[1] * SM + Usb[2] * ta.vs + Usb[3] * ta.ws;
+    SMb += Usb[1] * ta.rhos;
+    ba.vs += Usb[2] * ta.rhos;
+    ba.ws += Usb[3] * ta.rhos;
+    ba.b1s += Usb[4];
+    ba.b2s += Usb[5];
+    Esb += Usb[6];
+    // Es = [(sd E_a - pT_a u_a) + (pT* SM + bn (vB_a - vB*))] ism
+    const double NEb = Esb * ta.ism;
+    ba.ism += Esb * NE;
+    ba.sd += NEb * Ua[6];
+    Uab[6] += NEb * ta.sd;
+    double pTab = -NEb * A.u;
+    const double uab = -NEb * pTa;
+    pTsb += NEb * SM;
+    SMb += NEb * pTs;
+    bnb += NEb * (vBa - vBs);
+    const double vBab = NEb * bn;
+    vBsb -= NEb * bn;
+    // vB* = SM bn + vs b1s + ws b2s
+    SMb += vBsb * bn;
+    bnb += vBsb * SM;
+    ba.vs += vBsb * ta.b1s;
+    ba.b1s += vBsb * ta.vs;
+    ba.ws += vBsb * ta.b2s;
+    ba.b2s += vBsb * ta.ws;
+    // side a: conserved state, flux, v.B
+    W7b& Wab = left ? Lb : Rb;
+    Wab.u += uab;
+    double B2ab = 0.0;
+    side_full_vjp(A, bn, igm1, B2a, pTa, Uab, Fb, vBab, Wab, bnb, bn2b, B2ab, pTab);
+    if (left) { B2bL += B2ab; pTbL += pTab; }
+    else { B2bR += B2ab; pTbR += pTab; }
+    if (left) SLb += Sb;
+    else SRb += Sb;
+    // star states of both sides
+    star_side_vjp(L, SM, bn, bn2, tL, bL, Lb, SLb, SMb, bnb, bn2b);
+    star_side_vjp(R, SM, bn, bn2, tR, bR, Rb, SRb, SMb, bnb, bn2b);
+    // pT* = a1 (uR - uL) + (rsR pTL - rsL pTR), times iden; a1 = (rhoL rsR) sdL
+    const double Npb = pTsb * iden;
+    double idenb = pTsb * Np;
+    const double a1b = Npb * (R.u - L.u);
+    Rb.u += Npb * a1;
+    Lb.u -= Npb * a1;
+    bR.rs += Npb * ll.pT;
+    pTbL += Npb * rsR;
+    bL.rs -= Npb * lr.pT;
+    pTbR -= Npb * rsL;
+    const double rr = L.rho * rsR;
+    bL.sd += a1b * rr;
+    const double rrb = a1b * sdL;
+    Lb.rho += rrb * rsR;
+    bR.rs += rrb * L.rho;
+    // SM = [(rsR uR - rsL uL) - pTR + pTL] iden
+    const double NMb = SMb * iden;
+    idenb += SMb * NM;
+    bR.rs += NMb * R.u;
+    Rb.u += NMb * rsR;
+    bL.rs -= NMb * L.u;
+    Lb.u -= NMb * rsL;
+    pTbR -= NMb;
+    pTbL += NMb;
+    // iden = 1/(rsR - rsL)
+    const double d = idenb * (-(iden * iden));
+    bR.rs += d;
+    bL.rs -= d;
+    // rs = sd rho, sd = S - u
+    bL.sd += bL.rs * L.rho;
+    Lb.rho += bL.rs * sdL;
+    bR.sd += bR.rs * R.rho;
+    Rb.rho += bR.rs * sdR;
+    SLb += bL.sd;
+    Lb.u -= bL.sd;
+    SRb += bR.sd;
+    Rb.u -= bR.sd;
+  }
+  double uLb = 0.0, uRb = 0.0, cfLb = 0.0, cfRb = 0.0;
+  speeds_vjp(L.u, R.u, ll.cf, lr.cf, Ib, SLb, SRb, uLb, uRb, cfLb, cfRb);
+  Lb.u += uLb;
+  Rb.u += uRb;
+  side_lite_vjp(L, bn2, gamma, ll.B2, B2bL, pTbL, cfLb, Lb, bn2b);
+  side_lite_vjp(R, bn2, gamma, lr.B2, B2bR, pTbR, cfRb, Rb, bn2b);
+  bnb += (2.0 * bn) * bn2b;
+}
+
+}  // namespace mhd

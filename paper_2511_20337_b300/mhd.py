@@ -32,7 +32,8 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_step_noalloc", "mhd_batch_create", "mhd_batch_destroy", "mhd_batch_set_conserved",
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
-           "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile")
+           "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
+           "mhd_set_seglen", "mhd_autotune")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -99,6 +100,9 @@ def lib():
             "mhd_adjoint_grad_conserved": (I, [P, I, DPP, DPP]),
             "mhd_adjoint_grad_prim": (I, [P, I, P, DPP]),
             "mhd_adjoint_profile": (I, [P, I, ctypes.POINTER(D), I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+            "mhd_probe_riemann_vjp": (I, [I, I, D, P, P, P, P]),
+            "mhd_set_seglen": (I, [P, I]),
+            "mhd_autotune": (I, [P, ctypes.POINTER(I)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -235,6 +239,15 @@ class Sim:
         rc = lib().mhd_status(self.h, ctypes.byref(bad))
         return rc, bad.value
 
+    def set_seglen(self, seglen):
+        _check(lib().mhd_set_seglen(self.h, int(seglen)), "mhd_set_seglen")
+
+    def autotune(self):
+        """Pick the sweep segment length by timing (state restored); returns it."""
+        s = ctypes.c_int()
+        _check(lib().mhd_autotune(self.h, ctypes.byref(s)), "mhd_autotune")
+        return s.value
+
     def set_boundaries(self, bc):
         arr = (ctypes.c_int * 6)(*[BC[b] for b in bc])
         _check(lib().mhd_set_boundaries(self.h, arr), "mhd_set_boundaries")
@@ -334,6 +347,19 @@ class Sim:
         _check(lib().mhd_adjoint_grad_conserved(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
                                                 _ptr_array(arrs[5:])), "mhd_adjoint_grad_conserved")
         return out
+
+
+def probe_riemann_vjp(solver, inputs, cotangents, gamma):
+    """The Riemann solver's vector-Jacobian product on the GPU by forward-mode
+    numbers and by the hand-written reverse: inputs (n, 15), cotangents (n, 12)
+    -> (dual, hand), each (n, 15)."""
+    x = np.ascontiguousarray(np.asarray(inputs, dtype=np.float64))
+    c = np.ascontiguousarray(np.asarray(cotangents, dtype=np.float64))
+    n = x.shape[0]
+    dual, hand = np.zeros((n, 15)), np.zeros((n, 15))
+    _check(lib().mhd_probe_riemann_vjp(RIEMANN[solver], n, float(gamma), _ptr(x), _ptr(c), _ptr(dual), _ptr(hand)),
+           "mhd_probe_riemann_vjp")
+    return dual, hand
 
 
 def probe_fp64_gflops():

@@ -259,3 +259,38 @@ def test_low_beta_blast_floors_and_fallbacks_match(mhd, recon):
     fb, fl = g.counters()
     assert (fb, fl) == (o.fallbacks, o.floors)
     assert fl > 0
+
+
+@pytest.mark.parametrize("case", ["ot2d", "turb3d"])
+def test_segment_length_does_not_change_the_result(mhd, case):
+    """Each face is solved by the same arithmetic whatever segment marches it,
+    so any segment length gives the same state, bitwise."""
+    cfg, st = W.orszag_tang_2d(40) if case == "ot2d" else W.turbulent_3d(20)
+    out = []
+    for seg in (1, 2, 5, 16, 64):
+        sim = mhd.Sim(cfg, st)
+        sim.set_seglen(seg)
+        sim.advance(3)
+        out.append(sim.get_conserved())
+    for o in out[1:]:
+        for k in KEYS:
+            assert np.array_equal(o[k], out[0][k]), k
+
+
+def test_autotune_restores_state_and_time(mhd):
+    cfg, st = W.orszag_tang_2d(64)
+    sim = mhd.Sim(cfg, st)
+    sim.advance(2)
+    before, t0 = sim.get_conserved(), sim.time
+    seg = sim.autotune()
+    assert seg in (2, 4, 8, 16, 32, 64)
+    after = sim.get_conserved()
+    for k in KEYS:
+        assert np.array_equal(before[k], after[k]), k
+    assert sim.time == t0
+    ref = mhd.Sim(cfg, st)
+    ref.advance(5)
+    sim.advance(3)
+    a, b = sim.get_conserved(), ref.get_conserved()
+    for k in KEYS:
+        assert np.array_equal(a[k], b[k]), k
