@@ -320,7 +320,11 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    seg = sim.autotune() if ncell <= 256 ** 3 else None  # larger grids keep the default 16
+    if args.seglen:
+        sim.set_seglen(args.seglen)
+        seg = args.seglen
+    else:
+        seg = sim.autotune() if ncell <= 256 ** 3 else None  # larger grids keep the default 16
     # warm-up (also captures the step graph)
     sim.advance(args.warmup)
     torch.cuda.synchronize(dev)
@@ -615,7 +619,11 @@ def run_adjoint(args):
         if world > 1:
             torch.distributed.barrier()
 
-    seg = sim.autotune()
+    if args.seglen:
+        sim.set_seglen(args.seglen)
+        seg = args.seglen
+    else:
+        seg = sim.autotune()
     _, dts = sim.adjoint(N, None, K)  # records the CFL steps, then frozen
     for _ in range(args.warmup):
         sim.set_conserved(devs)
@@ -734,6 +742,8 @@ def main():
     ap.add_argument("--workload", default="turbulent3d-256", choices=list(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seglen", type=int, default=0,
+                    help="sweep segment length of single-grid workloads (0: autotune)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # timing rule: at least 3 untimed warm-up steps
     if args.impl == "reference":
