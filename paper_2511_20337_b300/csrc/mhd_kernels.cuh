@@ -286,6 +286,12 @@ static __global__ void set_dt_kernel(DevScalars* sc, double dt) {
 // ---------------------------------------------------------------------------
 template <int RECON> struct Stencil { static constexpr int R = RECON == RECON_PLM ? 1 : 2; };
 
+// Resident 128-thread sweep blocks per SM the compiler must allow for (caps
+// the registers per thread at 65536 / (128 * this)).
+#ifndef MHD_SWEEP_MIN_BLOCKS
+#define MHD_SWEEP_MIN_BLOCKS 1
+#endif
+
 __device__ __forceinline__ void recon_cell(int recon, const double* s, double& plus, double& minus);
 
 template <int DIR, int NDIM>
@@ -414,7 +420,7 @@ __device__ __forceinline__ void sweep_item(const Grid& g, const F8& P, const dou
 }
 
 template <int DIR, int NDIM, int RECON, int RS>
-static __global__ void __launch_bounds__(128) sweep_kernel(Grid g, F8 P, const double* __restrict__ Bface, L6 L,
+static __global__ void __launch_bounds__(128, MHD_SWEEP_MIN_BLOCKS) sweep_kernel(Grid g, F8 P, const double* __restrict__ Bface, L6 L,
                                                     Ingr5x3 ING, DevScalars* sc, int seglen, int accumulate) {
   sweep_item<DIR, NDIM, RECON, RS>(g, P, Bface, L, ING, sc, seglen, accumulate,
                                    blockIdx.x * (long long)blockDim.x + threadIdx.x);
@@ -648,7 +654,7 @@ static __global__ void __launch_bounds__(256) batch_prim_kernel(const RunDev* __
   if (CFL) cfl_block_finish(lam, R.sc, R.g.cfl, (unsigned int)(__ldg(blk0 + r + 1) - __ldg(blk0 + r)));
 }
 template <int DIR, int NDIM, int RECON, int RS>
-static __global__ void __launch_bounds__(128) batch_sweep_kernel(const RunDev* __restrict__ runs,
+static __global__ void __launch_bounds__(128, MHD_SWEEP_MIN_BLOCKS) batch_sweep_kernel(const RunDev* __restrict__ runs,
                                                           const int* __restrict__ blk0, int nruns, int reg,
                                                           int accumulate) {
   const int r = block_run(blk0, nruns);

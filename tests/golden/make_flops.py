@@ -44,6 +44,8 @@ VARIANTS = {
     "orszag_tang2d_plm_hlld_rk2": lambda: W.orszag_tang_2d(32),
     "orszag_tang2d_plm_hll_rk2": lambda: W.orszag_tang_2d(32, riemann="hll"),
     "orszag_tang2d_wenoz_hlld_rk3": lambda: W.orszag_tang_2d(32, recon="wenoz", rk=3),
+    "orszag_tang3d_wenoz_hlld_rk3": lambda: W.orszag_tang_3d(16, recon="wenoz", rk=3),
+    "cpa3d_wenoz_hlld_rk3": lambda: W.cpa_3d(16, recon="wenoz", rk=3),
     "adjoint2d_plm_hlld_rk2": lambda: W.adjoint_2d(32),
     "adjoint2d_plm_hll_rk2": lambda: W.adjoint_2d(32, riemann="hll"),
 }
