@@ -108,6 +108,21 @@ def dist_info():
     return rank, world, local
 
 
+def job_time_ms(ms, world, dev):
+    """The job's time: the slowest rank's (all-reduce MAX over the ranks)."""
+    if world == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, t_max_ms):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (t_max_ms * 1e-3)
+
+
 def cells_of(cfg):
     return int(np.prod(cfg["n"][:cfg["ndim"]]))
 
@@ -360,12 +375,8 @@ def run_ours(args):
     rc, bad = sim.status()
     if rc != 0:
         raise RuntimeError(f"device reported {rc} at cell {bad}")
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ncell * args.steps * world / (t_max * 1e-3)
+    t_max = job_time_ms(ms, world, dev)
+    value = job_rate(ncell * args.steps, world, t_max)
 
     # ---- per-kernel device times (events after each launch) for the roofline ----
     prof_steps = max(1, min(args.steps, 10))
@@ -405,11 +416,7 @@ def run_ours(args):
         sim.set_conserved(host)        # H2D of the step's input
         sim.advance(1)
         sim.get_conserved(out_host)    # D2H of the step's result (synchronous)
-    el = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([el], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        el = float(t.item())
+    el = job_time_ms(time.perf_counter() - t0, world, dev)
     e2e = {"value": ncell * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d, "steps": e2e_steps}
 
@@ -492,12 +499,8 @@ def run_ensemble(args):
     rc, bad_run, bad = bt.status()
     if rc != 0:
         raise RuntimeError(f"device reported {rc} in run {bad_run} at cell {bad}")
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ncell * args.steps * world / (t_max * 1e-3)
+    t_max = job_time_ms(ms, world, dev)
+    value = job_rate(ncell * args.steps, world, t_max)
 
     # roofline of the batched sweep (events after each launch)
     prof_steps = max(1, min(args.steps, 5))
@@ -664,12 +667,8 @@ def run_adjoint(args):
         barrier()
     ms = e0.elapsed_time(e1)
     launches = sim.launches - launches0
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = 3 * ncell * N * args.steps * world / (t_max * 1e-3)
+    t_max = job_time_ms(ms, world, dev)
+    value = job_rate(3 * ncell * N * args.steps, world, t_max)
 
     # phases and kernel classes (events on the library stream; syncs every reverse step)
     sim.set_conserved(devs)
