@@ -65,14 +65,19 @@ void prim(mhd_ctx* c, const F8& S, bool cfl) {
 template <int DIR, int NDIM, int RECON, int RS>
 void sweep_one(mhd_ctx* c, const F8& S) {
   const Grid& g = c->g;
-  constexpr int U = (DIR == 0) ? 1 : 0;
-  constexpr int V = (DIR == 0) ? 2 : (DIR == 1 ? 2 : 1);
-  long long eu = (U < NDIM) ? g.n[U] + 2 : 1, ev = (V < NDIM) ? g.n[V] + 2 : 1;
-  long long nseg = (g.n[DIR] + 1 + c->seglen - 1) / c->seglen;
-  long long threads = eu * ev * nseg;
-  int nb = (int)((threads + 127) / 128);
-  sweep_kernel<DIR, NDIM, RECON, RS><<<nb, 128, 0, c->stream>>>(g, c->P, S.q[5 + DIR], c->L, c->ING, c->sc,
-                                                                c->seglen, DIR > 0 ? 1 : 0);
+  const long long threads = sweep_work<DIR, NDIM>(g, c->seglen);
+  const int nb = (int)((threads + kSweepThreads - 1) / kSweepThreads);
+  if constexpr (DIR == 0) {
+    if (sweep_staged<DIR, NDIM>(g)) {
+      sweep_kernel<DIR, NDIM, RECON, RS, true><<<nb, kSweepThreads, kXStageBytes, c->stream>>>(
+          g, c->P, S.q[5 + DIR], c->L, c->ING, c->sc, c->seglen, 0);
+      c->launches++;
+      prof_mark(c, MHD_KCLASS_SWEEP_X + DIR);
+      return;
+    }
+  }
+  sweep_kernel<DIR, NDIM, RECON, RS><<<nb, kSweepThreads, 0, c->stream>>>(g, c->P, S.q[5 + DIR], c->L, c->ING,
+                                                                          c->sc, c->seglen, DIR > 0 ? 1 : 0);
   c->launches++;
   prof_mark(c, MHD_KCLASS_SWEEP_X + DIR);
 }
@@ -82,6 +87,25 @@ void sweeps_t(mhd_ctx* c, const F8& S) {
   sweep_one<0, NDIM, RECON, RS>(c, S);
   sweep_one<1, NDIM, RECON, RS>(c, S);
   if constexpr (NDIM == 3) sweep_one<2, NDIM, RECON, RS>(c, S);
+}
+
+// The staged x sweep uses more than the default 48 KB of dynamic shared
+// memory; the attribute is set once per context, outside any graph capture.
+template <int NDIM, int RECON, int RS>
+cudaError_t allow_stage_t() {
+  return cudaFuncSetAttribute(sweep_kernel<0, NDIM, RECON, RS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kXStageBytes);
+}
+template <int NDIM>
+cudaError_t allow_stage_n(int r, int s) {
+  const bool hlld = s == MHD_RIEMANN_HLLD;
+  if (r == MHD_RECON_PLM) return hlld ? allow_stage_t<NDIM, RECON_PLM, RS_HLLD>() : allow_stage_t<NDIM, RECON_PLM, RS_HLL>();
+  if (r == MHD_RECON_WENOZ)
+    return hlld ? allow_stage_t<NDIM, RECON_WENOZ, RS_HLLD>() : allow_stage_t<NDIM, RECON_WENOZ, RS_HLL>();
+  return hlld ? allow_stage_t<NDIM, RECON_PPM, RS_HLLD>() : allow_stage_t<NDIM, RECON_PPM, RS_HLL>();
+}
+cudaError_t allow_stage(const mhd_config* cfg) {
+  return cfg->ndim == 2 ? allow_stage_n<2>(cfg->recon, cfg->riemann) : allow_stage_n<3>(cfg->recon, cfg->riemann);
 }
 
 template <int NDIM>
@@ -214,6 +238,10 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
   reset_scalars_host(&h);
   cudaMemcpyAsync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    mhd_destroy(c);
+    return MHD_ERR_CUDA;
+  }
+  if (allow_stage(cfg) != cudaSuccess) {
     mhd_destroy(c);
     return MHD_ERR_CUDA;
   }
@@ -614,6 +642,7 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   rc = noalloc_scratch(&base);
   if (rc) return rc;
 
+  CK(allow_stage(cfg));
   // a context on the stack whose arrays are carved out of the static scratch
   mhd_ctx c{};
   c.cfg = *cfg;

@@ -62,6 +62,14 @@ void prof_mark(mhd_batch* b, int cls) {
 const int* table(const mhd_batch* b, int t) { return b->blk_d + (size_t)t * (b->nruns + 1); }
 int table_blocks(const mhd_batch* b, int t) { return b->blk[(size_t)t * (b->nruns + 1) + b->nruns]; }
 
+// Threads of a batched (direct-load) sweep along d: pencils x segments.
+long long sweep_rows_direct(const Grid& g, int d, int nd, int seglen) {
+  long long rows = 1;
+  for (int t = 0; t < nd; t++)
+    if (t != d) rows *= g.n[t] + 2;
+  return rows * ((g.n[d] + 1 + seglen - 1) / seglen);
+}
+
 // Block tables of every kernel class from each run's work and block size.
 int build_tables(mhd_batch* b) {
   const int R = b->nruns, nd = b->cfg0.ndim;
@@ -78,15 +86,15 @@ int build_tables(mhd_batch* b) {
         case T_ROWS_X: case T_ROWS_Y: case T_ROWS_Z: work = ghost_rows_work(g, t - T_ROWS_X); break;
         case T_PRIM: work = nd == 2 ? prim_work<2>(g) : prim_work<3>(g); break;
         case T_SWEEP_X:
-          work = nd == 2 ? sweep_work<0, 2>(g, run.seglen) : sweep_work<0, 3>(g, run.seglen);
+          work = sweep_rows_direct(g, 0, nd, run.seglen);
           bs = kBlockSweep;
           break;
         case T_SWEEP_Y:
-          work = nd == 2 ? sweep_work<1, 2>(g, run.seglen) : sweep_work<1, 3>(g, run.seglen);
+          work = sweep_rows_direct(g, 1, nd, run.seglen);
           bs = kBlockSweep;
           break;
         case T_SWEEP_Z:
-          work = nd == 3 ? sweep_work<2, 3>(g, run.seglen) : 0;
+          work = nd == 3 ? sweep_rows_direct(g, 2, nd, run.seglen) : 0;
           bs = kBlockSweep;
           break;
         case T_EDGE: work = nd == 2 ? edge_work<2>(g) : edge_work<3>(g); break;

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
 #include "mhd_math.cuh"
 
 namespace mhd {
@@ -277,33 +279,169 @@ static __global__ void set_dt_kernel(DevScalars* sc, double dt) {
 }
 
 // ---------------------------------------------------------------------------
-// Sweep along DIR: each thread marches a segment of faces of one pencil,
-// reconstructing each cell once, solving each face's Riemann problem once per
-// segment, writing the face's UCT ingredients and accumulating the flux
-// difference of Eq. FV into the stage increment of the cells it owns.
-// Pencils cover transverse indices [-1, n_t] on active axes (the outer layer
-// feeds the edge fields only).
+// Sweeps (see sweep_item below)
 // ---------------------------------------------------------------------------
 template <int RECON> struct Stencil { static constexpr int R = RECON == RECON_PLM ? 1 : 2; };
 
-// Resident 128-thread sweep blocks per SM the compiler must allow for (caps
-// the registers per thread at 65536 / (128 * this)).
-#ifndef MHD_SWEEP_MIN_BLOCKS
-#define MHD_SWEEP_MIN_BLOCKS 1
+// Launch bounds of the sweep kernels (128 threads).  Defining
+// MHD_SWEEP_MIN_BLOCKS asks the compiler to allow that many resident blocks
+// per SM (registers capped at 65536 / (128 * it)); by default the compiler
+// chooses (an explicit minimum of 1 changes its register choice).
+#ifdef MHD_SWEEP_MIN_BLOCKS
+#define MHD_SWEEP_BOUNDS __launch_bounds__(128, MHD_SWEEP_MIN_BLOCKS)
+#else
+#define MHD_SWEEP_BOUNDS __launch_bounds__(128)
 #endif
 
-__device__ __forceinline__ void recon_cell(int recon, const double* s, double& plus, double& minus);
+// The x sweep marches its pencils along the contiguous axis: a warp's 32
+// lanes hold 32 rows, so a direct load of one cell per lane touches 32
+// sectors.  Instead the warp stages its rows' cells in shared memory, kXChunk
+// cells at a time, with loads that cover 8 rows x 32 contiguous bytes each.
+// All lanes of a warp then march the same segment in lockstep: the x sweep
+// pads its row count to a multiple of 32 (padding lanes load, never store).
+constexpr int kXChunk = 4;
+constexpr int kXStride = kXChunk + 1;               // row pitch in the stage: no bank conflicts
+constexpr int kXStageBuf = 7 * 32 * kXStride;       // doubles per chunk buffer of one warp
+constexpr int kXStageWarp = 2 * kXStageBuf;         // double-buffered: the next chunk is in flight
+constexpr int kSweepThreads = 128;
+constexpr int kXStageBytes = kSweepThreads / 32 * kXStageWarp * (int)sizeof(double);  // per block (dynamic)
+
+// Asynchronous 8-byte global -> shared copies (cp.async, committed in groups).
+__device__ __forceinline__ void cp_async8(double* smem_dst, const double* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <int DIR, int NDIM>
-__host__ __device__ __forceinline__ long long sweep_work(const Grid& g, int seglen) {
+__host__ __device__ __forceinline__ long long sweep_rows(const Grid& g) {
   constexpr int U = (DIR == 0) ? 1 : 0;
   constexpr int V = (DIR == 0) ? 2 : (DIR == 1 ? 2 : 1);
   long long eu = (U < NDIM) ? g.n[U] + 2 : 1, ev = (V < NDIM) ? g.n[V] + 2 : 1;
-  return eu * ev * ((g.n[DIR] + 1 + seglen - 1) / seglen);
+  return eu * ev;
+}
+// The x sweep stages through shared memory when its pencils number at least
+// this many (large 3D grids: the padding to whole warps costs < 2 %, and the
+// data no longer fits in L2); smaller grids load directly.
+constexpr long long kXStageMinRows = 2048;
+template <int DIR, int NDIM>
+__host__ __device__ __forceinline__ bool sweep_staged(const Grid& g) {
+  return DIR == 0 && sweep_rows<DIR, NDIM>(g) >= kXStageMinRows;
+}
+template <int DIR, int NDIM>
+__host__ __device__ __forceinline__ long long sweep_work(const Grid& g, int seglen) {
+  long long rows = sweep_rows<DIR, NDIM>(g);
+  if (sweep_staged<DIR, NDIM>(g)) rows = (rows + 31) / 32 * 32;
+  return rows * ((g.n[DIR] + 1 + seglen - 1) / seglen);
 }
 
+// One segment of one pencil.  FETCH(x, v7) delivers the 7 sweep-order
+// primitives of cell x of this pencil; it is called with x increasing by one
+// from f0 - 1 - R (and identically on every lane of a warp when staged).
+template <int DIR, int NDIM, int RECON, int RS, class FETCH>
+__device__ __forceinline__ void sweep_body(const Grid& g, const double* __restrict__ Bface, const L6& L,
+                                           const Ingr5x3& ING, DevScalars* sc, int seglen, int accumulate, int base,
+                                           int seg, bool active, bool row_interior, FETCH&& fetch) {
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  constexpr int R = Stencil<RECON>::R;
+  constexpr int W = 2 * R + 1;  // window of cells
+  const int st = g.stride(DIR);
+  const int nd = g.n[DIR];
+  const int f0 = seg * seglen;
+  const int f1 = min(f0 + seglen, nd + 1);  // owned faces [f0, f1)
+  const int fend = min(f1, nd);             // last face computed
+  const double dt = sc->dt;
+  const double dtdx = dt * g.idx[DIR];
+  double win[7][W];
+  // load window centred on cell f0 - 1
+#pragma unroll
+  for (int m = 0; m < W; m++) {
+    double v7[7];
+    fetch(f0 - 1 - R + m, v7);
+#pragma unroll
+    for (int v = 0; v < 7; v++) win[v][m] = v7[v];
+  }
+  auto reconstruct = [&](double plus[7], double minus[7], bool count) {
+#pragma unroll
+    for (int v = 0; v < 7; v++) {
+      if (RECON == RECON_PLM) recon_plm(win[v][0], win[v][1], win[v][2], plus[v], minus[v]);
+      else if (RECON == RECON_WENOZ) recon_wenoz(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
+      else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
+    }
+    // positivity fallback: first order in this cell
+    if (!gt0(plus[0]) || !gt0(minus[0]) || !gt0(plus[6]) || !gt0(minus[6])) {
+#pragma unroll
+      for (int v = 0; v < 7; v++) plus[v] = minus[v] = win[v][R];
+      if (count) atomicAdd(&sc->fallbacks, 1ull);
+    }
+  };
+  double wl[7], wr[7], dummy[7];
+  // cells are counted once: cell -1 by the first segment, cell f by the
+  // segment that owns face f
+  reconstruct(wl, dummy, active && seg == 0);  // V^L at face f0 (plus state of cell f0-1)
+  double Fprev[7];
+  for (int f = f0; f <= fend; f++) {
+    // shift the window to be centred on cell f
+#pragma unroll
+    for (int v = 0; v < 7; v++) {
+#pragma unroll
+      for (int m = 0; m < W - 1; m++) win[v][m] = win[v][m + 1];
+    }
+    {
+      double v7[7];
+      fetch(f + R, v7);
+#pragma unroll
+      for (int v = 0; v < 7; v++) win[v][W - 1] = v7[v];
+    }
+    double plusN[7];
+    reconstruct(plusN, wr, active && f < f1);  // cell f: V^L at f+1, V^R at f
+    W7 L7 = {wl[0], wl[1], wl[2], wl[3], wl[4], wl[5], wl[6]};
+    W7 R7 = {wr[0], wr[1], wr[2], wr[3], wr[4], wr[5], wr[6]};
+    int cf = base + f * st;
+    double bn = Bface[cf];
+    Flux7 F;
+    Ingr ing;
+    if (RS == RS_HLLD) riemann_hlld(L7, R7, bn, g.gamma, g.igm1, F, ing);
+    else riemann_hll(L7, R7, bn, g.gamma, g.igm1, F, ing);
+    if (active && f < f1) {
+      ING.a[DIR][0][cf] = ing.ap;
+      ING.a[DIR][1][cf] = ing.am;
+      ING.a[DIR][2][cf] = ing.dd;
+      ING.a[DIR][3][cf] = ing.uL;
+      ING.a[DIR][4][cf] = ing.uR;
+    }
+    if (f > f0 && row_interior) {
+      int cc = cf - st;  // cell f-1
+      double dv[6];
+      dv[0] = F.f[0] - Fprev[0];
+      double dm[3];
+      dm[DIR] = F.f[1] - Fprev[1];
+      dm[T1] = F.f[2] - Fprev[2];
+      dm[T2] = F.f[3] - Fprev[3];
+      dv[1] = dm[0];
+      dv[2] = dm[1];
+      dv[3] = dm[2];
+      dv[4] = F.f[6] - Fprev[6];
+      constexpr int NV = NDIM == 2 ? 6 : 5;
+      if (NDIM == 2) dv[5] = (DIR == 0) ? F.f[5] - Fprev[5] : F.f[4] - Fprev[4];
+#pragma unroll
+      for (int q = 0; q < NV; q++)  // explicit roundings: the same in every kernel that inlines this
+        L.q[q][cc] = accumulate ? fma(-dtdx, dv[q], L.q[q][cc]) : -__dmul_rn(dtdx, dv[q]);
+    }
+#pragma unroll
+    for (int v = 0; v < 7; v++) {
+      Fprev[v] = F.f[v];
+      wl[v] = plusN[v];
+    }
+  }
+}
+
+// Direct-load sweep item: every direction, and the x sweep of smaller grids
+// (see sweep_item below for what a sweep item does).
 template <int DIR, int NDIM, int RECON, int RS>
-__device__ __forceinline__ void sweep_item(const Grid& g, const F8& P, const double* __restrict__ Bface, const L6& L,
+__device__ __forceinline__ void sweep_item_direct(const Grid& g, const F8& P, const double* __restrict__ Bface, const L6& L,
                                            const Ingr5x3& ING, DevScalars* sc, int seglen, int accumulate,
                                            long long id) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
@@ -419,11 +557,94 @@ __device__ __forceinline__ void sweep_item(const Grid& g, const F8& P, const dou
   }
 }
 
-template <int DIR, int NDIM, int RECON, int RS>
-static __global__ void __launch_bounds__(128, MHD_SWEEP_MIN_BLOCKS) sweep_kernel(Grid g, F8 P, const double* __restrict__ Bface, L6 L,
-                                                    Ingr5x3 ING, DevScalars* sc, int seglen, int accumulate) {
-  sweep_item<DIR, NDIM, RECON, RS>(g, P, Bface, L, ING, sc, seglen, accumulate,
-                                   blockIdx.x * (long long)blockDim.x + threadIdx.x);
+// Staged x-sweep item (grids for which sweep_staged holds): the warp's 32
+// lanes march 32 pencils of one segment in lockstep; `stage` is this warp's
+// shared-memory stage of kXStageWarp doubles (two chunk buffers).
+template <int NDIM, int RECON, int RS>
+__device__ __forceinline__ void sweep_item_staged(const Grid& g, const F8& P, const double* __restrict__ Bface,
+                                                  const L6& L, const Ingr5x3& ING, DevScalars* sc, int seglen,
+                                                  int accumulate, long long id, double* stage) {
+  constexpr int DIR = 0, T1 = 1, T2 = 2;
+  const int lu = -1, lv = NDIM == 3 ? -1 : 0;
+  const int eu = g.n[1] + 2;
+  const long long rows = sweep_rows<DIR, NDIM>(g);
+  const long long prow = (rows + 31) / 32 * 32;  // whole warps per segment
+  if (id >= prow * ((g.n[DIR] + 1 + seglen - 1) / seglen)) return;  // whole warps
+  long long row = id % prow;
+  const int seg = (int)(id / prow);
+  const bool active = row < rows;  // padding lanes load and march but never store
+  if (!active) row = 0;
+  const int iu = (int)(row % eu) + lu;
+  const int iv = (int)(row / eu) + lv;
+  const bool row_interior = active && iu >= 0 && iu < g.n[1] && (NDIM == 2 || (iv >= 0 && iv < g.n[2]));
+  const int base = g.at(0, iu, iv);
+  const double* pr[7] = {P.q[0], P.q[1 + DIR], P.q[1 + T1], P.q[1 + T2], P.q[4 + T1], P.q[4 + T2], P.q[7]};
+  const int lane = threadIdx.x & 31;
+  // lane's share of a chunk copy: element k*32 + lane is row (k*32+lane)/kXChunk, cell (k*32+lane)%kXChunk
+  int rbase[kXChunk];
+#pragma unroll
+  for (int k = 0; k < kXChunk; k++) rbase[k] = __shfl_sync(0xffffffffu, base, (k * 32 + lane) / kXChunk);
+  const int cix = lane % kXChunk;
+  auto issue = [&](int x0, double* buf) {  // the warp's rows, cells [x0, x0 + kXChunk), all 7 primitives
+#pragma unroll
+    for (int k = 0; k < kXChunk; k++) {
+      const int r = (k * 32 + lane) / kXChunk;
+#pragma unroll
+      for (int v = 0; v < 7; v++) cp_async8(buf + (v * 32 + r) * kXStride + cix, pr[v] + rbase[k] + x0 + cix);
+    }
+    cp_async_commit();
+  };
+  // Cells are requested in increasing order from f0 - 1 - R (the same on every
+  // lane, so every branch below is warp-uniform).  Two chunks are in flight
+  // ahead of the one being read; reads past the pencil end land in the next
+  // padded row of the same field.
+  int xc = (seg * seglen) - 1 - Stencil<RECON>::R;
+  int cur = 0;
+  issue(xc, stage);
+  issue(xc + kXChunk, stage + kXStageBuf);
+  cp_async_wait_all_but_one();
+  __syncwarp();
+  auto fetch = [&](int xi, double v7[7]) {
+    if (xi >= xc + kXChunk) {
+      __syncwarp();                                    // every lane is done with buffer cur
+      issue(xc + 2 * kXChunk, stage + cur * kXStageBuf);
+      xc += kXChunk;
+      cur ^= 1;
+      cp_async_wait_all_but_one();                     // the chunk at xc has landed
+      __syncwarp();
+    }
+    const double* buf = stage + cur * kXStageBuf;
+#pragma unroll
+    for (int v = 0; v < 7; v++) v7[v] = buf[(v * 32 + lane) * kXStride + (xi - xc)];
+  };
+  sweep_body<DIR, NDIM, RECON, RS>(g, Bface, L, ING, sc, seglen, accumulate, base, seg, active, row_interior, fetch);
+  cp_async_wait_all();  // no copy may still target this block's shared memory when it exits
+}
+
+// ---------------------------------------------------------------------------
+// Sweep along DIR: each thread marches a segment of faces of one pencil,
+// reconstructing each cell once, solving each face's Riemann problem once per
+// segment, writing the face's UCT ingredients and accumulating the flux
+// difference of Eq. FV into the stage increment of the cells it owns.
+// Pencils cover transverse indices [-1, n_t] on active axes (the outer layer
+// feeds the edge fields only).  The direct and staged items execute the
+// same arithmetic (sweep_body repeats sweep_item_direct's), so their results
+// agree to the bit.
+// ---------------------------------------------------------------------------
+template <int DIR, int NDIM, int RECON, int RS, bool STAGED = false>
+static __global__ void MHD_SWEEP_BOUNDS
+    sweep_kernel(Grid g, F8 P, const double* __restrict__ Bface, L6 L, Ingr5x3 ING, DevScalars* sc, int seglen,
+                 int accumulate) {
+  if constexpr (STAGED) {
+    static_assert(DIR == 0, "only the x sweep stages");
+    extern __shared__ double stage[];  // kXStageBytes, dynamic
+    sweep_item_staged<NDIM, RECON, RS>(g, P, Bface, L, ING, sc, seglen, accumulate,
+                                       blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                                       stage + (threadIdx.x >> 5) * kXStageWarp);
+  } else {
+    sweep_item_direct<DIR, NDIM, RECON, RS>(g, P, Bface, L, ING, sc, seglen, accumulate,
+                                            blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -653,14 +874,16 @@ static __global__ void __launch_bounds__(256) batch_prim_kernel(const RunDev* __
   if (id < prim_work<NDIM>(R.g)) lam = prim_item<NDIM, CFL>(R.g, R.U[reg], R.P, R.sc, id);
   if (CFL) cfl_block_finish(lam, R.sc, R.g.cfl, (unsigned int)(__ldg(blk0 + r + 1) - __ldg(blk0 + r)));
 }
+// Batched sweeps load directly (the ensemble's grids are small); a run whose
+// x sweep would be staged is served by the same direct path here.
 template <int DIR, int NDIM, int RECON, int RS>
-static __global__ void __launch_bounds__(128, MHD_SWEEP_MIN_BLOCKS) batch_sweep_kernel(const RunDev* __restrict__ runs,
-                                                          const int* __restrict__ blk0, int nruns, int reg,
-                                                          int accumulate) {
+static __global__ void MHD_SWEEP_BOUNDS
+    batch_sweep_kernel(const RunDev* __restrict__ runs, const int* __restrict__ blk0, int nruns, int reg,
+                       int accumulate) {
   const int r = block_run(blk0, nruns);
   const RunDev& R = runs[r];
-  sweep_item<DIR, NDIM, RECON, RS>(R.g, R.P, R.U[reg].q[5 + DIR], R.L, R.ING, R.sc, R.seglen, accumulate,
-                                   block_local_id(blk0, r));
+  sweep_item_direct<DIR, NDIM, RECON, RS>(R.g, R.P, R.U[reg].q[5 + DIR], R.L, R.ING, R.sc, R.seglen, accumulate,
+                                          block_local_id(blk0, r));
 }
 template <int NDIM>
 static __global__ void __launch_bounds__(256) batch_emf_kernel(const RunDev* __restrict__ runs,
