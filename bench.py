@@ -41,6 +41,9 @@ WORKLOADS = {
     "turbulent3d-256": (lambda: W.turbulent_3d(256), "turbulent3d_plm_hlld_rk2",
                         "3D ideal MHD 256^3 periodic, uniform rho=1 p=1 B=(1,1,1)/sqrt3 + seeded Gaussian "
                         "rho/v perturbations (1%, |k|<=8); PLM-minmod + HLLD + SSP-RK2 + UCT-HLL CT, CFL 0.4"),
+    "turbulent3d-512": (lambda: W.turbulent_3d(512), "turbulent3d_plm_hlld_rk2",
+                        "3D ideal MHD 512^3 periodic, the turbulent3d-256 recipe and scheme at 512^3 "
+                        "(PLM-minmod + HLLD + SSP-RK2 + UCT-HLL CT, CFL 0.4)"),
     "turbulent3d-128": (lambda: W.turbulent_3d(128), "turbulent3d_plm_hlld_rk2",
                         "3D ideal MHD 128^3 periodic (profiling size), same recipe and scheme as turbulent3d-256"),
     "blast3d-512": (lambda: W.blast_3d(512), "blast3d_wenoz_hlld_rk3",
@@ -80,6 +83,7 @@ PAPER_PER_GPU = {"orszag-tang3d-704": {"H100 (MareNostrum 5 ACC)": 1.511e8 / 4, 
 SAMPLES = {
     "turbulent3d-256": (lambda: W.turbulent_3d(48), "turbulent 3D 48^3 (same scheme and field recipe)"),
     "turbulent3d-128": (lambda: W.turbulent_3d(48), "turbulent 3D 48^3 (same scheme and field recipe)"),
+    "turbulent3d-512": (lambda: W.turbulent_3d(48), "turbulent 3D 48^3 (same scheme and field recipe)"),
     "blast3d-512": (lambda: W.blast_3d(32), "blast 3D 32^3 (same scheme and setup)"),
     "blast3d-128": (lambda: W.blast_3d(32), "blast 3D 32^3 (same scheme and setup)"),
     "blast3d-512-ppm": (lambda: W.blast_3d(32, recon="ppm"), "blast 3D 32^3 PPM (same scheme and setup)"),

@@ -74,6 +74,18 @@ def lib():
         L.orc_grad_prim.argtypes = [ctypes.POINTER(OrcConfig), PP, PP, DP, ctypes.c_int, ctypes.c_int, PP, DP, PP]
         L.orc_count_flops.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
                                       ctypes.POINTER(ctypes.c_ulonglong)]
+        L.orc_glm_create.restype = P
+        L.orc_glm_create.argtypes = [ctypes.POINTER(OrcConfig), D]
+        L.orc_glm_destroy.argtypes = [P]
+        L.orc_glm_set_state.argtypes = [P, ctypes.POINTER(DP)]
+        L.orc_glm_get_state.argtypes = [P, ctypes.POINTER(DP)]
+        L.orc_glm_cfl_dt.restype = D
+        L.orc_glm_cfl_dt.argtypes = [P]
+        L.orc_glm_step.argtypes = [P, D]
+        L.orc_glm_ch.restype = D
+        L.orc_glm_ch.argtypes = [P]
+        L.orc_glm_fallbacks.restype = ctypes.c_longlong
+        L.orc_glm_fallbacks.argtypes = [P]
         L.orc_count_tape.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
                                      ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
         _lib = L
@@ -107,7 +119,8 @@ def _dp(a):
 
 
 def _ptrs(arrays):
-    arr = (ctypes.POINTER(ctypes.c_double) * 8)()
+    arrays = list(arrays)
+    arr = (ctypes.POINTER(ctypes.c_double) * max(8, len(arrays)))()
     for q, a in enumerate(arrays):
         arr[q] = _dp(a)
     return arr
@@ -195,6 +208,61 @@ class OracleSim:
         arrs = [np.zeros(s) for s in self.shapes]
         lib().orc_stage_increment(self.h, float(dt), _ptrs(arrs))
         return dict(zip(KEYS, arrs))
+
+
+GLM_KEYS = ("rho", "mx", "my", "mz", "E", "bx", "by", "bz", "psi")
+
+
+class OracleGlm:
+    """One grid advanced by the oracle scheme with GLM divergence cleaning
+    (glm_oracle.hpp): 9 cell-centred variables, GLM_KEYS."""
+
+    def __init__(self, cfg, state=None, alpha=0.1):
+        self.cfg = dict(cfg)
+        self._c = make_config(cfg)
+        self.h = lib().orc_glm_create(ctypes.byref(self._c), float(alpha))
+        if not self.h:
+            raise ValueError("oracle rejected the configuration")
+        self.shape = state_shapes(cfg)[0]
+        if state is not None:
+            self.set_state(state)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_glm_destroy(self.h)
+            self.h = None
+
+    def set_state(self, state):
+        arrs = [np.ascontiguousarray(np.asarray(state[k], dtype=np.float64).reshape(self.shape)) for k in GLM_KEYS]
+        lib().orc_glm_set_state(self.h, _ptrs(arrs))
+
+    def get_state(self):
+        arrs = [np.zeros(self.shape) for _ in GLM_KEYS]
+        lib().orc_glm_get_state(self.h, _ptrs(arrs))
+        return dict(zip(GLM_KEYS, arrs))
+
+    def cfl_dt(self):
+        return lib().orc_glm_cfl_dt(self.h)
+
+    def step(self, dt):
+        if lib().orc_glm_step(self.h, float(dt)) != 0:
+            raise FloatingPointError("oracle met a non-positive density or pressure")
+
+    def advance(self, nsteps, record_dt=False):
+        dts = []
+        for _ in range(nsteps):
+            dt = self.cfl_dt()
+            self.step(dt)
+            dts.append(dt)
+        return dts if record_dt else None
+
+    @property
+    def ch(self):
+        return lib().orc_glm_ch(self.h)
+
+    @property
+    def fallbacks(self):
+        return lib().orc_glm_fallbacks(self.h)
 
 
 def riemann(solver, wl, wr, bn, gamma):

@@ -11,7 +11,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SO = os.path.join(HERE, "liboracle.so")
-SOURCES = ["oracle_capi.cpp", "mhd_oracle.hpp", "scalar.hpp"]
+SOURCES = ["oracle_capi.cpp", "mhd_oracle.hpp", "glm_oracle.hpp", "scalar.hpp"]
 
 
 def needs_build():

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <memory>
 
+#include "glm_oracle.hpp"
 #include "mhd_oracle.hpp"
 
 using namespace orc;
@@ -94,6 +95,45 @@ int orc_step(void* h, double dt) {
   return s->bad ? -4 : 0;
 }
 double orc_time(void* h) { return static_cast<Sim<double>*>(h)->time; }
+
+// ---- the scheme with GLM divergence cleaning (glm_oracle.hpp) ----
+// State: 9 cell arrays [nz][ny][nx]: rho, mx, my, mz, E, Bx, By, Bz, psi.
+void* orc_glm_create(const OrcConfig* c, double alpha) {
+  try {
+    return new GlmSim<double>(to_cfg(c), alpha);
+  } catch (...) {
+    return nullptr;
+  }
+}
+void orc_glm_destroy(void* h) { delete static_cast<GlmSim<double>*>(h); }
+int orc_glm_set_state(void* h, const double* const* arrays) {
+  auto* s = static_cast<GlmSim<double>*>(h);
+  for (int q = 0; q < NG; q++) {
+    const double* p = arrays[q];
+    for (int k = 0; k < s->n[2]; k++)
+      for (int j = 0; j < s->n[1]; j++)
+        for (int i = 0; i < s->n[0]; i++) s->U0[q](i, j, k) = *p++;
+  }
+  return 0;
+}
+int orc_glm_get_state(void* h, double* const* arrays) {
+  auto* s = static_cast<GlmSim<double>*>(h);
+  for (int q = 0; q < NG; q++) {
+    double* p = arrays[q];
+    for (int k = 0; k < s->n[2]; k++)
+      for (int j = 0; j < s->n[1]; j++)
+        for (int i = 0; i < s->n[0]; i++) *p++ = s->U0[q](i, j, k);
+  }
+  return 0;
+}
+double orc_glm_cfl_dt(void* h) { return static_cast<GlmSim<double>*>(h)->cfl_dt(); }
+int orc_glm_step(void* h, double dt) {
+  auto* s = static_cast<GlmSim<double>*>(h);
+  s->step(dt);
+  return s->bad ? -4 : 0;
+}
+double orc_glm_ch(void* h) { return static_cast<GlmSim<double>*>(h)->ch; }
+long long orc_glm_fallbacks(void* h) { return static_cast<GlmSim<double>*>(h)->fallbacks; }
 long long orc_fallbacks(void* h) { return static_cast<Sim<double>*>(h)->fallbacks; }
 long long orc_floors(void* h) { return static_cast<Sim<double>*>(h)->floors; }
 int orc_status(void* h, long long* bad_cell) {
