@@ -61,6 +61,13 @@ WORKLOADS = {
     "cpa3d-704": (lambda: W.cpa_3d((704, 704, 352), recon="wenoz", rk=3), "cpa3d_wenoz_hlld_rk3",
                   "3D circularly polarised Alfven wave of paper §4.2 at 704x704x352 on the unit periodic cube, "
                   "eps = 0.1, rho0 = 1, p0 = 0.1, k = 2 pi (1,1,1); WENO-Z + HLLD + SSP-RK3 + CT (UCT-HLL), CFL 0.4"),
+    "turbulent3d-256-glm": (lambda: W.to_glm(*W.turbulent_3d(256)), "turbulent3d_plm_hlld_rk2_glm",
+                            "turbulent3d-256 with GLM divergence cleaning instead of CT (cell-centred B, psi, "
+                            "alpha = 0.1); PLM-minmod + HLLD + SSP-RK2, CFL 0.4"),
+    "orszag-tang3d-704-glm": (lambda: W.to_glm(*W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3)),
+                              "orszag_tang3d_wenoz_hlld_rk3_glm",
+                              "3D Orszag-Tang of paper §4.1 at 704x704x352 with GLM divergence cleaning (the "
+                              "paper's strong-scaling configuration); WENO-Z + HLLD + SSP-RK3, alpha = 0.1, CFL 0.4"),
     "orszag-tang2d-128": (lambda: W.orszag_tang_2d(128), "orszag_tang2d_plm_hlld_rk2",
                           "2D Orszag-Tang 128^2 periodic; PLM-minmod + HLLD + SSP-RK2 + UCT-HLL CT, CFL 0.4"),
     "ensemble2d-256": (None, "orszag_tang2d_plm_hlld_rk2",
@@ -89,6 +96,9 @@ SAMPLES = {
     "blast3d-512-ppm": (lambda: W.blast_3d(32, recon="ppm"), "blast 3D 32^3 PPM (same scheme and setup)"),
     "orszag-tang3d-704": (lambda: W.orszag_tang_3d(32, recon="wenoz", rk=3), "3D Orszag-Tang 32^3 (same scheme)"),
     "cpa3d-704": (lambda: W.cpa_3d(32, recon="wenoz", rk=3), "3D CPA 32^3 (same scheme)"),
+    "turbulent3d-256-glm": (lambda: W.to_glm(*W.turbulent_3d(48)), "turbulent 3D 48^3 with GLM (same scheme)"),
+    "orszag-tang3d-704-glm": (lambda: W.to_glm(*W.orszag_tang_3d(32, recon="wenoz", rk=3)),
+                              "3D Orszag-Tang 32^3 with GLM (same scheme)"),
     "orszag-tang2d-128": (lambda: W.orszag_tang_2d(128), "Orszag-Tang 2D 128^2 (the workload itself)"),
     "ensemble2d-256": (lambda: ensemble_cases(16, max_n=128)[0],
                        "the first 16 ensemble members of at most 128^2 cells"),
@@ -134,9 +144,27 @@ def cells_of(cfg):
 # ---------------------------------------------------------------------------
 # algorithmic flops (per-unit counts of the oracle, stored by tests/golden/make_flops.py)
 # ---------------------------------------------------------------------------
+def glm_flop_model(cfg, per):
+    """Algorithmic flops of the GLM scheme (its own loop ranges: interior pencils, 9 variables)."""
+    nd = cfg["ndim"]
+    n = list(cfg["n"][:nd])
+    G = 2 if cfg["recon"] == "plm" else 3
+    cells = int(np.prod(n))
+    sweep = {}
+    for d in range(nd):
+        rows = int(np.prod([n[t] for t in range(nd) if t != d]))
+        sweep[d] = per["recon"] * (n[d] + 2) * rows + per["riemann"] * (n[d] + 1) * rows + per["fluxdiff"] / nd * cells
+    padded = int(np.prod([m + 2 * G for m in n]))
+    stage = per["c2p"] * padded + sum(sweep.values()) + per["rk"] * 9 * cells
+    step = cfg["rk"] * stage + per["cfl"] * cells
+    return {"sweep_per_launch": sweep, "step": step, "per_cell_update": step / cells}
+
+
 def flop_model(cfg, variant):
     path = os.path.join(ROOT, "tests", "golden", "flops_per_unit.json")
     per = json.load(open(path))["variants"][variant]["per_unit"]
+    if cfg.get("divb", "ct") == "glm":
+        return glm_flop_model(cfg, per)
     nd = cfg["ndim"]
     n = list(cfg["n"][:nd])
     G = 2 if cfg["recon"] == "plm" else 3
@@ -266,7 +294,8 @@ def cpu_oracle_rate(sample_fn, seconds_budget=15.0, max_steps=None):
     """The oracle as it stands, single-threaded, on the sample grid: cell-updates/s."""
     import oracle
     cfg, st = sample_fn()
-    s = oracle.OracleSim(cfg, st)
+    s = (oracle.OracleGlm(cfg, st, alpha=cfg["glm_alpha"]) if cfg.get("divb", "ct") == "glm"
+         else oracle.OracleSim(cfg, st))
     s.advance(1)  # warm
     steps = 0
     t0 = time.perf_counter()
@@ -307,7 +336,8 @@ def run_reference(args):
         value = sum(cells_of(c) for c, _ in cases) * args.steps / el
     else:
         cfg, st = gen()
-        s = oracle.OracleSim(cfg, st)
+        s = (oracle.OracleGlm(cfg, st, alpha=cfg["glm_alpha"]) if cfg.get("divb", "ct") == "glm"
+             else oracle.OracleSim(cfg, st))
         for _ in range(args.warmup):
             s.advance(1)
         t0 = time.perf_counter()
@@ -396,7 +426,9 @@ def run_ours(args):
     step_achieved = fm["step"] / (step_ms_prof * 1e-3) / 1e9
     n = list(cfg["n"][:nd])
     faces_per_launch = sum((n[d] + 1) * int(np.prod([n[t] + 2 for t in range(nd) if t != d])) for d in range(nd)) / nd
-    roofline = {"bound": "alu", "kernel": "sweep_kernel (fused reconstruct + HLLD + flux difference)",
+    sweep_name = ("glm_sweep_kernel (fused reconstruct + (B_n, psi) solve + HLLD + flux difference)"
+                  if cfg.get("divb", "ct") == "glm" else "sweep_kernel (fused reconstruct + HLLD + flux difference)")
+    roofline = {"bound": "alu", "kernel": sweep_name,
                 "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
                 "peak_source": "measured in this run: FP64 DFMA probe (mhd_probe_fp64), 2 flops per DFMA",
                 "algorithmic_flops_per_launch": sweep_flops / sweep_launches,

@@ -70,7 +70,14 @@ typedef struct {
                            it is raised to it in the primitives only; the conserved energy is not
                            changed (the paper is silent on floors; see mhd_counters) */
   void* stream;         /* cudaStream_t for all device work; NULL = default stream */
+  int divb;             /* MHD_DIVB_CT (0, constrained transport on staggered faces) or
+                           MHD_DIVB_GLM (cell-centred B with GLM divergence cleaning) */
+  double glm_alpha;     /* GLM damping constant alpha >= 0: after each step
+                           psi <- psi exp(-alpha c_h dt / min dx); ignored for CT */
 } mhd_config;
+
+#define MHD_DIVB_CT  0
+#define MHD_DIVB_GLM 1
 
 typedef struct mhd_ctx mhd_ctx;   /* opaque; owns all device state of one grid */
 
@@ -161,6 +168,26 @@ int mhd_autotune(mhd_ctx* ctx, int* seglen_out);
 
 /* Static text for a return code. */
 const char* mhd_strerror(int code);
+
+/* ---- divergence cleaning (divb = MHD_DIVB_GLM) ----
+ *
+ * The div B control the paper uses for its strong-scaling runs (§2.1, citing
+ * Dedner et al. 2002 and Mignone et al. 2010; §4.1, §4.2): cell-centred B and
+ * a scalar psi.  At each face the (B_n, psi) system, linear with speeds
+ * -+c_h, is solved exactly (B_m = (B_n^L + B_n^R)/2 - (psi^R - psi^L)/(2 c_h),
+ * psi_m = (psi^L + psi^R)/2 - c_h (B_n^R - B_n^L)/2; fluxes psi_m for B_n and
+ * c_h^2 B_m for psi) and the Riemann solver runs with normal field B_m.
+ * c_h = cfl / (dt sum_d 1/dx_d); after each step psi is multiplied by
+ * exp(-glm_alpha c_h dt / min dx).  In this mode the B arrays of
+ * mhd_set_conserved, mhd_set_prim and mhd_get_conserved are cell arrays
+ * [nz][ny][nx] (Bx, By, Bz), setting the state sets psi = 0, and there is no
+ * pressure floor (p_floor must be 0).  The batched, adjoint and
+ * allocation-free entry points are CT-only (MHD_ERR_ARG). */
+
+/* psi in or out: one cell array [nz][ny][nx], host or device per mem.
+ * MHD_ERR_ARG on a CT context.  set: async; get: sync. */
+int mhd_set_psi(mhd_ctx* ctx, int mem, const double* psi);
+int mhd_get_psi(mhd_ctx* ctx, int mem, double* psi);
 
 /* ---- batched ensemble ----
  *

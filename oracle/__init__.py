@@ -84,6 +84,8 @@ def lib():
         L.orc_glm_step.argtypes = [P, D]
         L.orc_glm_ch.restype = D
         L.orc_glm_ch.argtypes = [P]
+        L.orc_glm_count_flops.argtypes = [ctypes.POINTER(OrcConfig), D, ctypes.POINTER(DP), ctypes.c_int, D,
+                                          ctypes.POINTER(ctypes.c_ulonglong)]
         L.orc_glm_fallbacks.restype = ctypes.c_longlong
         L.orc_glm_fallbacks.argtypes = [P]
         L.orc_count_tape.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
@@ -259,6 +261,13 @@ class OracleGlm:
     @property
     def ch(self):
         return lib().orc_glm_ch(self.h)
+
+    def count_flops(self, nsteps, dt, alpha=0.1):
+        """Counted-scalar run from the current state: dict phase -> dict op -> count."""
+        arrs = [np.ascontiguousarray(a) for a in self.get_state().values()]
+        out = (ctypes.c_ulonglong * (len(PHASES) * len(OPS)))()
+        lib().orc_glm_count_flops(ctypes.byref(self._c), float(alpha), _ptrs(arrs), int(nsteps), float(dt), out)
+        return {ph: {op: int(out[i * len(OPS) + j]) for j, op in enumerate(OPS)} for i, ph in enumerate(PHASES)}
 
     @property
     def fallbacks(self):

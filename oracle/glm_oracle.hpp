@@ -42,6 +42,8 @@ template <class R> struct GlmSim {
   bool periodic[3] = {true, true, true};
   std::array<Field<R>, NG> U0, U1, U2, Lq;
   Field<R> P[NGP];
+  Field<R> Wp[9], Wm[9];  // reconstructed states of the current direction
+  Field<R> Fx[NG];        // face fluxes of the current direction (face f at index f)
   R ch = R(0.0);  // cleaning speed of the current step
   R time = R(0.0);
   long long fallbacks = 0;
@@ -57,6 +59,9 @@ template <class R> struct GlmSim {
     auto initf = [&](Field<R>& f) { f.init(n[0], n[1], n[2], G, ndim); };
     for (auto* S : {&U0, &U1, &U2, &Lq}) for (auto& f : *S) initf(f);
     for (auto& f : P) initf(f);
+    for (auto& f : Wp) initf(f);
+    for (auto& f : Wm) initf(f);
+    for (auto& f : Fx) initf(f);
   }
   int lo(int d) const { return (d < ndim) ? -G : 0; }
   int hi(int d) const { return (d < ndim) ? n[d] + G : 0; }
@@ -82,6 +87,7 @@ template <class R> struct GlmSim {
   }
 
   void compute_prims(std::array<Field<R>, NG>& S) {
+    g_flops.phase = PH_C2P;
     for (int k = lo(2); k < (ndim == 3 ? hi(2) : 1); k++)
       for (int j = lo(1); j < hi(1); j++)
         for (int i = lo(0); i < hi(0); i++) {
@@ -95,74 +101,106 @@ template <class R> struct GlmSim {
         }
   }
 
+  // Reconstruction in direction d of the 9 sweep-frame primitives
+  // (rho, v_n, v_t1, v_t2, B_n, B_t1, B_t2, p, psi) for cells [-1, n_d] of the
+  // interior rows, with the positivity fallback of the CT scheme.
+  void reconstruct(int d) {
+    g_flops.phase = PH_RECON;
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const int comp[9] = {GP_RHO, GP_VX + d, GP_VX + t1, GP_VX + t2, GP_BX + d, GP_BX + t1, GP_BX + t2, GP_PR, GP_PSI};
+    int ext[3] = {n[0], n[1], n[2]};
+    for (int k = 0; k < ext[2]; k++)
+      for (int j = 0; j < ext[1]; j++)
+        for (int i = 0; i < ext[0]; i++) {
+          int x[3] = {i, j, k};
+          if (x[d] != 0) continue;  // one pencil per transverse position
+          for (int cidx = -1; cidx <= n[d]; cidx++) {
+            x[d] = cidx;
+            R wp[9], wm[9], wc[9];
+            for (int q = 0; q < 9; q++) {
+              R s5[5];
+              for (int m = -2; m <= 2; m++) {
+                int y[3] = {x[0], x[1], x[2]};
+                y[d] += m;
+                bool need = c.recon != RECON_PLM || (m >= -1 && m <= 1);
+                s5[m + 2] = need ? P[comp[q]](y[0], y[1], y[2]) : R(0.0);
+              }
+              wc[q] = s5[2];
+              if (c.recon == RECON_PLM) recon_plm(s5, wp[q], wm[q]);
+              else if (c.recon == RECON_WENOZ) recon_wenoz(s5, wp[q], wm[q]);
+              else recon_ppm(s5, wp[q], wm[q]);
+            }
+            if (!(wp[0] > R(0.0)) || !(wm[0] > R(0.0)) || !(wp[7] > R(0.0)) || !(wm[7] > R(0.0))) {
+              branch(51);
+              for (int q = 0; q < 9; q++) wp[q] = wm[q] = wc[q];
+              if (cidx >= 0 && cidx < n[d]) fallbacks++;
+            }
+            for (int q = 0; q < 9; q++) {
+              Wp[q](x[0], x[1], x[2]) = wp[q];
+              Wm[q](x[0], x[1], x[2]) = wm[q];
+            }
+          }
+        }
+  }
+
+  // Face fluxes in direction d at faces [0, n_d] of the interior rows: the
+  // exact (B_n, psi) solution, then the MHD solver with normal field B_m.
+  void riemann(int d) {
+    g_flops.phase = PH_RIEMANN;
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    for (int k = 0; k < n[2]; k++)
+      for (int j = 0; j < n[1]; j++)
+        for (int i = 0; i < n[0]; i++) {
+          int x[3] = {i, j, k};
+          if (x[d] != 0) continue;
+          for (int f = 0; f <= n[d]; f++) {
+            int xr[3] = {x[0], x[1], x[2]}, xl[3] = {x[0], x[1], x[2]};
+            xr[d] = f;
+            xl[d] = f - 1;
+            R WL[9], WR[9];
+            for (int q = 0; q < 9; q++) {
+              WL[q] = Wp[q](xl[0], xl[1], xl[2]);
+              WR[q] = Wm[q](xr[0], xr[1], xr[2]);
+            }
+            R Bm = R(0.5) * (WL[4] + WR[4]) - (WR[8] - WL[8]) / (R(2.0) * ch);
+            R psim = R(0.5) * (WL[8] + WR[8]) - R(0.5) * ch * (WR[4] - WL[4]);
+            R wl7[NW] = {WL[0], WL[1], WL[2], WL[3], WL[5], WL[6], WL[7]};
+            R wr7[NW] = {WR[0], WR[1], WR[2], WR[3], WR[5], WR[6], WR[7]};
+            R F7[NW], ing[NI];
+            if (c.riemann == RS_HLLD) riemann_hlld(wl7, wr7, Bm, c.gamma, F7, ing);
+            else riemann_hll(wl7, wr7, Bm, c.gamma, F7, ing);
+            Fx[G_RHO](xr[0], xr[1], xr[2]) = F7[W_RHO];
+            Fx[G_MX + d](xr[0], xr[1], xr[2]) = F7[W_VN];
+            Fx[G_MX + t1](xr[0], xr[1], xr[2]) = F7[W_VT1];
+            Fx[G_MX + t2](xr[0], xr[1], xr[2]) = F7[W_VT2];
+            Fx[G_EN](xr[0], xr[1], xr[2]) = F7[W_PR];  // the energy flux sits in the last sweep slot
+            Fx[G_BX + d](xr[0], xr[1], xr[2]) = psim;
+            Fx[G_BX + t1](xr[0], xr[1], xr[2]) = F7[W_BT1];
+            Fx[G_BX + t2](xr[0], xr[1], xr[2]) = F7[W_BT2];
+            Fx[G_PSI](xr[0], xr[1], xr[2]) = (ch * ch) * Bm;
+          }
+        }
+  }
+
   // One stage increment L(S) (Eq. FV with the GLM fluxes), dt included.
   void stage_increment(std::array<Field<R>, NG>& S, R dt) {
+    g_flops.phase = PH_GHOST;
     fill_ghosts(S);
     compute_prims(S);
-    for (int q = 0; q < NG; q++)
-      for (int k = 0; k < n[2]; k++)
-        for (int j = 0; j < n[1]; j++)
-          for (int i = 0; i < n[0]; i++) Lq[q](i, j, k) = R(0.0);
     for (int d = 0; d < ndim; d++) {
-      const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-      // sweep-frame primitives: rho, v_n, v_t1, v_t2, B_n, B_t1, B_t2, p, psi
-      const int comp[9] = {GP_RHO, GP_VX + d, GP_VX + t1, GP_VX + t2, GP_BX + d, GP_BX + t1, GP_BX + t2, GP_PR, GP_PSI};
+      reconstruct(d);
+      riemann(d);
+      g_flops.phase = PH_FLUXDIFF;
       const R dtdx = dt / R(dx[d]);
       for (int k = 0; k < n[2]; k++)
         for (int j = 0; j < n[1]; j++)
           for (int i = 0; i < n[0]; i++) {
-            // fluxes through the left (f = cell) and right (f = cell + 1) faces of this cell
-            R Fface[2][9];
-            for (int side = 0; side < 2; side++) {
-              int xr[3] = {i, j, k};
-              xr[d] += side;  // right cell of the face
-              R WL[9], WR[9];
-              for (int cellside = 0; cellside < 2; cellside++) {  // 0: left cell (xr - e_d), 1: right cell
-                int xc[3] = {xr[0], xr[1], xr[2]};
-                xc[d] -= 1 - cellside;
-                R wp[9], wm[9], wc[9];
-                for (int q = 0; q < 9; q++) {
-                  R s[5];
-                  for (int m = -2; m <= 2; m++) {
-                    int y[3] = {xc[0], xc[1], xc[2]};
-                    y[d] += m;
-                    bool need = c.recon != RECON_PLM || (m >= -1 && m <= 1);
-                    s[m + 2] = need ? P[comp[q]](y[0], y[1], y[2]) : R(0.0);
-                  }
-                  wc[q] = s[2];
-                  if (c.recon == RECON_PLM) recon_plm(s, wp[q], wm[q]);
-                  else if (c.recon == RECON_WENOZ) recon_wenoz(s, wp[q], wm[q]);
-                  else recon_ppm(s, wp[q], wm[q]);
-                }
-                // positivity fallback (as in the CT scheme): first order in this cell
-                if (!(wp[0] > R(0.0)) || !(wm[0] > R(0.0)) || !(wp[7] > R(0.0)) || !(wm[7] > R(0.0))) {
-                  branch(51);
-                  for (int q = 0; q < 9; q++) wp[q] = wm[q] = wc[q];
-                  if (side == 1 && cellside == 0) fallbacks++;  // each interior cell counted once
-                }
-                for (int q = 0; q < 9; q++) (cellside == 0 ? WL : WR)[q] = cellside == 0 ? wp[q] : wm[q];
-              }
-              // the (B_n, psi) subsystem, solved exactly
-              R Bm = R(0.5) * (WL[4] + WR[4]) - (WR[8] - WL[8]) / (R(2.0) * ch);
-              R psim = R(0.5) * (WL[8] + WR[8]) - R(0.5) * ch * (WR[4] - WL[4]);
-              // the MHD solver with normal field B_m
-              R wl7[NW] = {WL[0], WL[1], WL[2], WL[3], WL[5], WL[6], WL[7]};
-              R wr7[NW] = {WR[0], WR[1], WR[2], WR[3], WR[5], WR[6], WR[7]};
-              R F7[NW], ing[NI];
-              if (c.riemann == RS_HLLD) riemann_hlld(wl7, wr7, Bm, c.gamma, F7, ing);
-              else riemann_hll(wl7, wr7, Bm, c.gamma, F7, ing);
-              R* Fo = Fface[side];
-              Fo[G_RHO] = F7[W_RHO];
-              Fo[G_MX + d] = F7[W_VN];
-              Fo[G_MX + t1] = F7[W_VT1];
-              Fo[G_MX + t2] = F7[W_VT2];
-              Fo[G_EN] = F7[W_PR];  // energy flux sits in the last sweep slot
-              Fo[G_BX + d] = psim;
-              Fo[G_BX + t1] = F7[W_BT1];
-              Fo[G_BX + t2] = F7[W_BT2];
-              Fo[G_PSI] = (ch * ch) * Bm;
+            int xp[3] = {i, j, k};
+            xp[d] += 1;
+            for (int q = 0; q < NG; q++) {
+              R term = -(dtdx * (Fx[q](xp[0], xp[1], xp[2]) - Fx[q](i, j, k)));
+              Lq[q](i, j, k) = d == 0 ? term : Lq[q](i, j, k) + term;
             }
-            for (int q = 0; q < NG; q++) Lq[q](i, j, k) = Lq[q](i, j, k) - dtdx * (Fface[1][q] - Fface[0][q]);
           }
     }
   }
@@ -186,8 +224,10 @@ template <class R> struct GlmSim {
   void step(R dt) {
     ch = cleaning_speed(dt);
     stage_increment(U0, dt);
+    g_flops.phase = PH_RK;
     each_cell([&](int q, int i, int j, int k) { U1[q](i, j, k) = U0[q](i, j, k) + Lq[q](i, j, k); });
     stage_increment(U1, dt);
+    g_flops.phase = PH_RK;
     if (c.rk == 2) {
       each_cell([&](int q, int i, int j, int k) {
         U0[q](i, j, k) = R(0.5) * ((U0[q](i, j, k) + U1[q](i, j, k)) + Lq[q](i, j, k));
@@ -197,6 +237,7 @@ template <class R> struct GlmSim {
         U2[q](i, j, k) = R(0.25) * ((R(3.0) * U0[q](i, j, k) + U1[q](i, j, k)) + Lq[q](i, j, k));
       });
       stage_increment(U2, dt);
+      g_flops.phase = PH_RK;
       each_cell([&](int q, int i, int j, int k) {
         U0[q](i, j, k) = ((U0[q](i, j, k) + R(2.0) * U2[q](i, j, k)) + R(2.0) * Lq[q](i, j, k)) / R(3.0);
       });
@@ -214,6 +255,7 @@ template <class R> struct GlmSim {
   R cfl_dt() {
     fill_ghosts(U0);
     compute_prims(U0);
+    g_flops.phase = PH_CFL;
     R lmax(0.0);
     R idx[3];
     for (int d = 0; d < 3; d++) idx[d] = R(1.0) / R(dx[d]);

@@ -133,6 +133,24 @@ int orc_glm_step(void* h, double dt) {
   return s->bad ? -4 : 0;
 }
 double orc_glm_ch(void* h) { return static_cast<GlmSim<double>*>(h)->ch; }
+// Counted-scalar run of the GLM scheme: one CFL evaluation and nsteps steps
+// of size dt from the 9 given cell arrays; out[PH_N * OP_N] as orc_count_flops.
+int orc_glm_count_flops(const OrcConfig* c, double alpha, const double* const* arrays, int nsteps, double dt,
+                        unsigned long long* out) {
+  GlmSim<Counted> s(to_cfg(c), alpha);
+  for (int q = 0; q < NG; q++) {
+    const double* p = arrays[q];
+    for (int k = 0; k < s.n[2]; k++)
+      for (int j = 0; j < s.n[1]; j++)
+        for (int i = 0; i < s.n[0]; i++) s.U0[q](i, j, k) = Counted(*p++);
+  }
+  g_flops.reset();
+  s.cfl_dt();
+  for (int t = 0; t < nsteps; t++) s.step(Counted(dt));
+  for (int ph = 0; ph < PH_N; ph++)
+    for (int op = 0; op < OP_N; op++) out[ph * OP_N + op] = g_flops.n[ph][op];
+  return 0;
+}
 long long orc_glm_fallbacks(void* h) { return static_cast<GlmSim<double>*>(h)->fallbacks; }
 long long orc_fallbacks(void* h) { return static_cast<Sim<double>*>(h)->fallbacks; }
 long long orc_floors(void* h) { return static_cast<Sim<double>*>(h)->floors; }

@@ -262,7 +262,7 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
   if (functional == MHD_FUNC_MISFIT && (!target || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE))) return MHD_ERR_ARG;
   if (!c->has_state) return MHD_ERR_STATE;
   const Grid& g = c->g;
-  if (c->cfg.recon != MHD_RECON_PLM) return MHD_ERR_ARG;
+  if (c->cfg.recon != MHD_RECON_PLM || c->g.glm) return MHD_ERR_ARG;
   for (int d = 0; d < g.ndim; d++)
     if (!g.periodic[d] || g.n[d] < 2 * g.G + 1) return MHD_ERR_ARG;
   if (dts)

@@ -156,9 +156,86 @@ void run_stage_regs(mhd_ctx* c, int s, const F8& U0, const F8& Us, const F8& Out
   ct_rk(c, U0, Us, Out, stage_mode(c->cfg.rk, s));
 }
 
+// --- divergence cleaning (GLM) helpers ---
+void glm_ghost_fill(mhd_ctx* c, const F9& S) {
+  const Grid& g = c->g;
+  for (int pass = 0; pass < 2; pass++)
+    for (int d = 0; d < g.ndim; d++) {
+      if ((pass == 0) != (g.periodic[d] != 0)) continue;
+      glm_ghost_kernel<<<blocks_for(ghost_layers_work(g, d), 256), 256, 0, c->stream>>>(g, S, d);
+      c->launches++;
+      prof_mark(c, MHD_KCLASS_GHOST);
+    }
+}
+
+void glm_prim(mhd_ctx* c, const F9& S, bool cfl) {
+  const Grid& g = c->g;
+  int nb = blocks_for(g.ndim == 2 ? prim_work<2>(g) : prim_work<3>(g), 256);
+  if (g.ndim == 2) {
+    if (cfl) glm_prim_kernel<2, true><<<nb, 256, 0, c->stream>>>(g, S, c->GP, c->sc);
+    else glm_prim_kernel<2, false><<<nb, 256, 0, c->stream>>>(g, S, c->GP, c->sc);
+  } else {
+    if (cfl) glm_prim_kernel<3, true><<<nb, 256, 0, c->stream>>>(g, S, c->GP, c->sc);
+    else glm_prim_kernel<3, false><<<nb, 256, 0, c->stream>>>(g, S, c->GP, c->sc);
+  }
+  c->launches++;
+  prof_mark(c, MHD_KCLASS_PRIM);
+}
+
+template <int DIR, int NDIM, int RECON, int RS>
+void glm_sweep_one(mhd_ctx* c) {
+  const long long threads = glm_sweep_work<DIR, NDIM>(c->g, c->seglen);
+  glm_sweep_kernel<DIR, NDIM, RECON, RS><<<(int)((threads + 127) / 128), 128, 0, c->stream>>>(
+      c->g, c->GP, c->GL, c->sc, c->seglen, DIR > 0 ? 1 : 0);
+  c->launches++;
+  prof_mark(c, MHD_KCLASS_SWEEP_X + DIR);
+}
+template <int NDIM, int RECON, int RS>
+void glm_sweeps_t(mhd_ctx* c) {
+  glm_sweep_one<0, NDIM, RECON, RS>(c);
+  glm_sweep_one<1, NDIM, RECON, RS>(c);
+  if constexpr (NDIM == 3) glm_sweep_one<2, NDIM, RECON, RS>(c);
+}
+template <int NDIM>
+void glm_sweeps_n(mhd_ctx* c) {
+  int r = c->cfg.recon, s = c->cfg.riemann;
+  const bool hlld = s == MHD_RIEMANN_HLLD;
+  if (r == MHD_RECON_PLM) hlld ? glm_sweeps_t<NDIM, RECON_PLM, RS_HLLD>(c) : glm_sweeps_t<NDIM, RECON_PLM, RS_HLL>(c);
+  else if (r == MHD_RECON_WENOZ)
+    hlld ? glm_sweeps_t<NDIM, RECON_WENOZ, RS_HLLD>(c) : glm_sweeps_t<NDIM, RECON_WENOZ, RS_HLL>(c);
+  else hlld ? glm_sweeps_t<NDIM, RECON_PPM, RS_HLLD>(c) : glm_sweeps_t<NDIM, RECON_PPM, RS_HLL>(c);
+}
+
+void glm_run_stage(mhd_ctx* c, int s, bool cfl) {
+  const Grid& g = c->g;
+  const int rk = c->cfg.rk;
+  const F9& Us = s == 0 ? c->GU[0] : (s == 1 ? c->GU[1] : c->GU[2]);
+  const F9& Out = s == 0 ? c->GU[1] : ((rk == 2 || s == 2) ? c->GU[0] : c->GU[2]);
+  glm_ghost_fill(c, Us);
+  glm_prim(c, Us, cfl);
+  if (g.ndim == 2) glm_sweeps_n<2>(c);
+  else glm_sweeps_n<3>(c);
+  double dh = g.dx[0];
+  for (int d = 1; d < g.ndim; d++) dh = g.dx[d] < dh ? g.dx[d] : dh;
+  const long long cells = (long long)g.n[0] * g.n[1] * g.n[2];
+  const int last = s == rk - 1;
+  if (g.ndim == 2)
+    glm_combine_kernel<2><<<blocks_for(cells, 256), 256, 0, c->stream>>>(g, c->GU[0], Us, Out, c->GL, c->sc,
+                                                                         stage_mode(rk, s), last, c->cfg.glm_alpha, dh);
+  else
+    glm_combine_kernel<3><<<blocks_for(cells, 256), 256, 0, c->stream>>>(g, c->GU[0], Us, Out, c->GL, c->sc,
+                                                                         stage_mode(rk, s), last, c->cfg.glm_alpha, dh);
+  c->launches++;
+  prof_mark(c, MHD_KCLASS_CT_RK);
+}
+
 // One RK stage s of the step on the context's registers; cfl = compute this
 // step's dt in the primitive pass.
 void run_stage(mhd_ctx* c, int s, bool cfl) {
+  if (c->g.glm) {
+    glm_run_stage(c, s, cfl);
+    return;
+  }
   const int rk = c->cfg.rk;
   const F8& Us = s == 0 ? c->U[0] : (s == 1 ? c->U[1] : c->U[2]);
   const F8& Out = s == 0 ? c->U[1] : ((rk == 2 || s == 2) ? c->U[0] : c->U[2]);
@@ -209,7 +286,9 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
     if (cudaStreamCreate(&c->stream) != cudaSuccess) { delete c; return MHD_ERR_CUDA; }
     c->own_stream = true;
   }
-  const int nfields = 3 * 8 + 8 + 6 + 15 + 3;
+  // CT: 3 registers of 8, primitives 8, increment 6, ingredients 15, edges 3;
+  // GLM: 3 registers of 9, primitives 9, increment 9
+  const int nfields = g.glm ? 3 * 9 + 9 + 9 : 3 * 8 + 8 + 6 + 15 + 3;
   size_t bytes = c->field_elems * sizeof(double) * nfields;
   if (cudaMalloc(&c->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -220,13 +299,25 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
   cudaMemsetAsync(c->pool, 0, bytes, c->stream);
   double* p = c->pool;
   auto next = [&]() { double* r = p; p += c->field_elems; return r; };
-  for (int r = 0; r < 3; r++)
-    for (int q = 0; q < 8; q++) c->U[r].q[q] = next();
-  for (int q = 0; q < 8; q++) c->P.q[q] = next();
-  for (int q = 0; q < 6; q++) c->L.q[q] = next();
-  for (int d = 0; d < 3; d++)
-    for (int q = 0; q < 5; q++) c->ING.a[d][q] = next();
-  for (int d = 0; d < 3; d++) c->E.e[d] = next();
+  if (g.glm) {
+    c->reg_fields = 9;
+    for (int r = 0; r < 3; r++)
+      for (int q = 0; q < 9; q++) {
+        c->GU[r].q[q] = next();
+        if (q < 8) c->U[r].q[q] = c->GU[r].q[q];
+      }
+    for (int q = 0; q < 9; q++) c->GP.q[q] = next();
+    for (int q = 0; q < 9; q++) c->GL.q[q] = next();
+  } else {
+    c->reg_fields = 8;
+    for (int r = 0; r < 3; r++)
+      for (int q = 0; q < 8; q++) c->U[r].q[q] = next();
+    for (int q = 0; q < 8; q++) c->P.q[q] = next();
+    for (int q = 0; q < 6; q++) c->L.q[q] = next();
+    for (int d = 0; d < 3; d++)
+      for (int q = 0; q < 5; q++) c->ING.a[d][q] = next();
+    for (int d = 0; d < 3; d++) c->E.e[d] = next();
+  }
   if (cudaMalloc(&c->sc, sizeof(DevScalars)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->pool);
@@ -294,6 +385,7 @@ int mhd_set_conserved(mhd_ctx* c, int mem, const double* const* U, const double*
   }
   int rc = set_common_faces(c, B);
   if (rc) return rc;
+  if (c->g.glm) CK(cudaMemsetAsync(c->GU[0].q[8], 0, c->field_elems * sizeof(double), c->stream));
   c->has_state = true;
   return reset_time(c);
 }
@@ -312,8 +404,15 @@ int mhd_set_prim(mhd_ctx* c, int mem, const double* rho, const double* const* v,
   int rc = set_common_faces(c, B);
   if (rc) return rc;
   long long work = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
-  if (c->g.ndim == 2) prim_to_cons_kernel<2><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->U[0]);
-  else prim_to_cons_kernel<3><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->U[0]);
+  if (c->g.glm) {
+    CK(cudaMemsetAsync(c->GU[0].q[8], 0, c->field_elems * sizeof(double), c->stream));
+    if (c->g.ndim == 2) glm_prim_to_cons_kernel<2><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->GU[0]);
+    else glm_prim_to_cons_kernel<3><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->GU[0]);
+  } else if (c->g.ndim == 2) {
+    prim_to_cons_kernel<2><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->U[0]);
+  } else {
+    prim_to_cons_kernel<3><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->U[0]);
+  }
   c->launches++;
   CK(cudaGetLastError());
   c->has_state = true;
@@ -339,7 +438,7 @@ int mhd_status(mhd_ctx* c, long long* bad_cell) {
 int mhd_get_conserved(mhd_ctx* c, int mem, double* const* U, double* const* B) {
   if (!c || !U || !B || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE)) return MHD_ERR_ARG;
   if (!c->has_state) return MHD_ERR_STATE;
-  ghost_fill(c, c->U[0]);
+  if (!c->g.glm) ghost_fill(c, c->U[0]);  // the duplicate last face of periodic axes
   for (int q = 0; q < 8; q++) {
     double* dst = q < 5 ? U[q] : B[q - 5];
     if (!dst) return MHD_ERR_ARG;
@@ -375,8 +474,13 @@ int mhd_cfl_dt(mhd_ctx* c, double* dt_out) {
   DevScalars before;
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(&before, c->sc, sizeof(before), cudaMemcpyDeviceToHost));
-  ghost_fill(c, c->U[0]);
-  prim(c, c->U[0], true);
+  if (c->g.glm) {
+    glm_ghost_fill(c, c->GU[0]);
+    glm_prim(c, c->GU[0], true);
+  } else {
+    ghost_fill(c, c->U[0]);
+    prim(c, c->U[0], true);
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
   DevScalars after;
@@ -444,6 +548,24 @@ int mhd_last_dt(mhd_ctx* c, double* dt_out) {
 
 long long mhd_launch_count(const mhd_ctx* c) { return c ? c->launches : -1; }
 
+int mhd_set_psi(mhd_ctx* c, int mem, const double* psi) {
+  if (!c || !psi || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE) || !c->g.glm) return MHD_ERR_ARG;
+  int e[3];
+  slot_extents(c->g, 0, e);
+  return copy_field(c->g, c->stream, c->GU[0].q[8], psi, nullptr, e, true);
+}
+
+int mhd_get_psi(mhd_ctx* c, int mem, double* psi) {
+  if (!c || !psi || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE) || !c->g.glm) return MHD_ERR_ARG;
+  if (!c->has_state) return MHD_ERR_STATE;
+  int e[3];
+  slot_extents(c->g, 0, e);
+  int rc = copy_field(c->g, c->stream, c->GU[0].q[8], nullptr, psi, e, false);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return MHD_OK;
+}
+
 int mhd_set_seglen(mhd_ctx* c, int seglen) {
   if (!c || seglen < 1) return MHD_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
@@ -461,7 +583,7 @@ int mhd_autotune(mhd_ctx* c, int* seglen_out) {
   CK(cudaStreamSynchronize(c->stream));
   DevScalars sc_h;
   CK(cudaMemcpy(&sc_h, c->sc, sizeof(sc_h), cudaMemcpyDeviceToHost));
-  const size_t bytes = 8 * c->field_elems * sizeof(double);  // U[0]'s 8 fields are contiguous
+  const size_t bytes = (size_t)c->reg_fields * c->field_elems * sizeof(double);  // U[0]'s fields are contiguous
   double* backup = nullptr;
   CK(cudaMalloc(&backup, bytes));
   CK(cudaMemcpyAsync(backup, c->U[0].q[0], bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -627,6 +749,7 @@ int noalloc_scratch(double** out) {
 extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double* const* B, double dt) {
   int rc = validate(cfg);
   if (rc) return rc;
+  if (cfg->divb != MHD_DIVB_CT) return MHD_ERR_ARG;
   if (!U || !B || !(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_ARG;
   for (int q = 0; q < 5; q++)
     if (!U[q]) return MHD_ERR_ARG;

@@ -236,6 +236,7 @@ int mhd_batch_create(int nruns, const mhd_config* cfgs, mhd_batch** out) {
   *out = nullptr;
   for (int r = 0; r < nruns; r++) {
     int rc = validate(&cfgs[r]);
+    if (!rc && cfgs[r].divb != MHD_DIVB_CT) rc = MHD_ERR_ARG;  // the batched kernels are CT-only
     if (rc) return rc;
     if (!same_scheme(cfgs[0], cfgs[r])) return MHD_ERR_ARG;
   }

@@ -3,6 +3,7 @@
 // mhd_adjoint.cu.  Internal to the library.
 #pragma once
 #include "mhd.h"
+#include "mhd_glm.cuh"
 #include "mhd_kernels.cuh"
 
 namespace mhd {
@@ -34,6 +35,10 @@ struct mhd_ctx {
   cudaEvent_t prof_ev[128];
   int prof_cls[128];
   mhd::AdjointState* adj;  // buffers of the adjoint, made by its first run
+  // divergence cleaning (g.glm): 9-field registers; GU[r].q[0..7] alias U[r]
+  // (cell B in slots 5..7), GU[r].q[8] is psi
+  mhd::F9 GU[3], GP, GL;
+  int reg_fields;          // fields per RK register: 8 (CT) or 9 (GLM); contiguous
 };
 
 namespace mhd {

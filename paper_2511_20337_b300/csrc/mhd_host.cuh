@@ -40,6 +40,8 @@ inline int validate(const mhd_config* c) {
   if (c->rk != 2 && c->rk != 3) return MHD_ERR_ARG;
   if (!(c->cfl > 0.0)) return MHD_ERR_ARG;
   if (!(c->p_floor >= 0.0)) return MHD_ERR_ARG;
+  if (c->divb != MHD_DIVB_CT && c->divb != MHD_DIVB_GLM) return MHD_ERR_ARG;
+  if (c->divb == MHD_DIVB_GLM && (!(c->glm_alpha >= 0.0) || c->p_floor != 0.0)) return MHD_ERR_ARG;
   for (int d = 0; d < c->ndim; d++) {
     for (int s = 0; s < 2; s++)
       if (c->bc[2 * d + s] != MHD_BC_PERIODIC && c->bc[2 * d + s] != MHD_BC_OUTFLOW) return MHD_ERR_ARG;
@@ -73,6 +75,7 @@ inline Grid make_grid(const mhd_config* c) {
   g.igm1 = 1.0 / (c->gamma - 1.0);
   g.cfl = c->cfl;
   g.p_floor = c->p_floor;
+  g.glm = c->divb == MHD_DIVB_GLM;
   return g;
 }
 
@@ -104,11 +107,13 @@ inline int copy_field(const Grid& g, cudaStream_t stream, double* field, const d
   return MHD_OK;
 }
 
+// Extents of state slot q in the boundary layout: cells, or the staggered
+// face fields of the CT scheme (slots 5..7; cell arrays with GLM).
 inline void slot_extents(const Grid& g, int slot, int e[3]) {
   e[0] = g.n[0];
   e[1] = g.n[1];
   e[2] = g.n[2];
-  if (slot >= 5 && slot - 5 < g.ndim) e[slot - 5] += 1;
+  if (!g.glm && slot >= 5 && slot < 8 && slot - 5 < g.ndim) e[slot - 5] += 1;
 }
 
 

@@ -31,6 +31,7 @@ struct Grid {
   int periodic[3];
   double dx[3], idx[3];
   double gamma, gm1, igm1, cfl, p_floor;
+  int glm;         // 1: cell-centred B and psi (divergence cleaning), 0: CT
   __host__ __device__ __forceinline__ int at(int i, int j, int k) const { return origin + i + j * sy + k * sz; }
   __host__ __device__ __forceinline__ int stride(int d) const { return d == 0 ? 1 : (d == 1 ? sy : sz); }
   __host__ __device__ __forceinline__ int lo(int d) const { return d < ndim ? -G : 0; }

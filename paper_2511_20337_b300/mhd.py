@@ -24,6 +24,9 @@ RIEMANN = {"hll": 0, "hlld": 1}
 BC = {"periodic": 0, "outflow": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
 KEYS = ("rho", "mx", "my", "mz", "E", "b0", "b1", "b2")
+DIVB = {"ct": 0, "glm": 1}
+# divergence cleaning: cell-centred field and psi
+GLM_KEYS = ("rho", "mx", "my", "mz", "E", "bx", "by", "bz", "psi")
 
 # every exported entry point of include/mhd.h
 EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mhd_get_conserved",
@@ -33,7 +36,7 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
-           "mhd_set_seglen", "mhd_autotune")
+           "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -50,7 +53,7 @@ class mhd_config(ctypes.Structure):
                 ("x0", ctypes.c_double * 3), ("x1", ctypes.c_double * 3), ("gamma", ctypes.c_double),
                 ("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("rk", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6), ("p_floor", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("divb", ctypes.c_int), ("glm_alpha", ctypes.c_double)]
 
 
 _lib = None
@@ -103,6 +106,8 @@ def lib():
             "mhd_probe_riemann_vjp": (I, [I, I, D, P, P, P, P]),
             "mhd_set_seglen": (I, [P, I]),
             "mhd_autotune": (I, [P, ctypes.POINTER(I)]),
+            "mhd_set_psi": (I, [P, I, P]),
+            "mhd_get_psi": (I, [P, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -136,6 +141,8 @@ def make_config(cfg, stream=None):
         c.bc[s] = BC[cfg["bc"][s]]
     c.p_floor = cfg.get("p_floor", 0.0)
     c.stream = stream
+    c.divb = DIVB[cfg.get("divb", "ct")]
+    c.glm_alpha = cfg.get("glm_alpha", 0.1)
     return c
 
 
@@ -144,6 +151,8 @@ def state_shapes(cfg):
     nx, ny = cfg["n"][0], cfg["n"][1]
     nz = cfg["n"][2] if nd == 3 else 1
     cell = (nz, ny, nx)
+    if cfg.get("divb", "ct") == "glm":
+        return [cell] * 8
     faces = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx) if nd == 3 else (1, ny, nx)]
     return [cell] * 5 + faces
 
@@ -193,8 +202,19 @@ class Sim:
         except Exception:
             pass
 
+    @property
+    def glm(self):
+        return self.cfg.get("divb", "ct") == "glm"
+
+    @property
+    def keys(self):
+        """State keys: KEYS (CT: face fields b0, b1, b2) or GLM_KEYS (cell field and psi)."""
+        return GLM_KEYS if self.glm else KEYS
+
     def set_conserved(self, state):
-        arrs = [state[k] for k in KEYS]
+        """Set the state from a dict of self.keys (GLM: psi optional, default 0)."""
+        keys = self.keys[:8]
+        arrs = [state[k] for k in keys]
         dev = _is_device(arrs[0])
         if not dev:
             arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(s)) for a, s in
@@ -203,6 +223,21 @@ class Sim:
         U = _ptr_array(arrs[:5])
         B = _ptr_array(arrs[5:])
         _check(lib().mhd_set_conserved(self.h, MEM_DEVICE if dev else MEM_HOST, U, B), "mhd_set_conserved")
+        if self.glm and state.get("psi") is not None:
+            self.set_psi(state["psi"])
+
+    def set_psi(self, psi):
+        dev = _is_device(psi)
+        if not dev:
+            psi = np.ascontiguousarray(np.asarray(psi, dtype=np.float64).reshape(self.shapes[0]))
+        self._keep_psi = psi
+        _check(lib().mhd_set_psi(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr(psi)), "mhd_set_psi")
+
+    def get_psi(self, out=None):
+        if out is None:
+            out = np.zeros(self.shapes[0])
+        _check(lib().mhd_get_psi(self.h, MEM_DEVICE if _is_device(out) else MEM_HOST, _ptr(out)), "mhd_get_psi")
+        return out
 
     def set_prim(self, rho, v, p, B):
         dev = _is_device(rho)
@@ -214,13 +249,19 @@ class Sim:
                                   _ptr(arrs[4]), _ptr_array(arrs[5:8])), "mhd_set_prim")
 
     def get_conserved(self, out=None):
-        """Copy the state out: into `out` (dict of numpy arrays or CUDA tensors) or new numpy arrays."""
+        """Copy the state out: into `out` (dict of numpy arrays or CUDA tensors) or new numpy arrays;
+        keys self.keys (GLM: psi included)."""
+        keys = self.keys[:8]
         if out is None:
-            out = {k: np.zeros(s) for k, s in zip(KEYS, self.shapes)}
-        arrs = [out[k] for k in KEYS]
+            out = {k: np.zeros(s) for k, s in zip(keys, self.shapes)}
+        arrs = [out[k] for k in keys]
         dev = _is_device(arrs[0])
         _check(lib().mhd_get_conserved(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
                                        _ptr_array(arrs[5:])), "mhd_get_conserved")
+        if self.glm:
+            if "psi" not in out:
+                out["psi"] = np.zeros(self.shapes[0])
+            self.get_psi(out["psi"])
         return out
 
     def cfl_dt(self):

@@ -320,6 +320,17 @@ def adjoint_2d(n=256, *, seed=5, amp=0.05, kmax=6.0, **kw):
     return cfg, assemble(cfg, rho, vx, vy, vz, p, bx, by, bz)
 
 
+def to_glm(cfg, st, alpha=0.1):
+    """The same initial state for the scheme with GLM divergence cleaning:
+    cell-centred field = mean of the two faces (2D B_z: the cell value),
+    psi = 0.  Returns (cfg with divb = glm, state with the GLM keys)."""
+    bx, by, bz = cell_field(cfg, st["b0"], st["b1"], st["b2"])
+    out = {k: st[k] for k in ("rho", "mx", "my", "mz", "E")}
+    out.update(bx=np.ascontiguousarray(bx), by=np.ascontiguousarray(by), bz=np.ascontiguousarray(bz),
+               psi=np.zeros_like(bx))
+    return dict(cfg, divb="glm", glm_alpha=alpha), out
+
+
 def smooth_2d(n=16, *, seed=5, bpert=0.0):
     """Smooth 2D periodic state on the unit square with no exactly tied limiter
     or min/max decision (a field constant along an axis ties minmod(0, 0),

@@ -21,6 +21,10 @@ phases, from the oracle's tape on one step: the forward flops, plus the flops
 that form the partial derivatives, plus the backward sweep over the tape
 links (an add for a partial of +-1, a multiply-add otherwise).  The CFL phase
 is not differentiated (dt frozen).
+The GLM variants (divergence cleaning) are counted on the oracle's GLM scheme
+with its own loop ranges: recon per cell and direction ((n_d + 2) cells x the
+interior pencils), riemann per face (the (B_n, psi) solution and the MHD
+solver), fluxdiff per cell and stage, rk per variable (9) and cell per stage.
 Only this script writes the file, and it calls only oracle/.
 """
 import json
@@ -77,6 +81,39 @@ def units(cfg):
             "emf": edges * rk, "ct": ct_faces * rk, "rk": elems * rk, "cfl": cells}
 
 
+# The scheme with GLM divergence cleaning (oracle/glm_oracle.hpp): its own
+# loop ranges (interior pencils only, no edges or faces), 9 variables.
+GLM_VARIANTS = {
+    "turbulent3d_plm_hlld_rk2_glm": lambda: W.turbulent_3d(16, seed=1),
+    "orszag_tang3d_wenoz_hlld_rk3_glm": lambda: W.orszag_tang_3d(16, recon="wenoz", rk=3),
+}
+
+
+def units_glm(cfg):
+    nd = cfg["ndim"]
+    n = list(cfg["n"])
+    G = 2 if cfg["recon"] == "plm" else 3
+    rk = cfg["rk"]
+    cells = int(np.prod(n))
+    padded = int(np.prod([m + 2 * G for m in n]))
+    recon = faces = 0
+    for d in range(nd):
+        rows = int(np.prod([n[t] for t in range(nd) if t != d]))
+        recon += (n[d] + 2) * rows
+        faces += (n[d] + 1) * rows
+    return {"c2p": padded * (rk + 1), "recon": recon * rk, "riemann": faces * rk, "fluxdiff": cells * rk,
+            "rk": 9 * cells * rk, "cfl": cells}
+
+
+def glm_counts(cfg, st):
+    bx, by, bz = W.cell_field(cfg, st["b0"], st["b1"], st["b2"])
+    g = {k: st[k] for k in ("rho", "mx", "my", "mz", "E")}
+    g.update(bx=bx, by=by, bz=bz, psi=np.zeros_like(bx))
+    o = oracle.OracleGlm(cfg, g)
+    dt = o.cfl_dt()
+    return o.count_flops(1, dt)
+
+
 def main():
     out = {"convention": "flops per unit: +,-,*,/,sqrt = 1; a*b+c = 2; compare/abs/min/max = 0",
            "variants": {}}
@@ -100,6 +137,13 @@ def main():
             adj[ph] = (fwd * u_adj / u[ph] + pfl + links) / u_adj
         out["variants"][name] = {"config": {k: cfg[k] for k in ("ndim", "n", "recon", "riemann", "rk", "bc")},
                                  "per_unit": per, "adjoint_per_unit": adj}
+    for name, make in GLM_VARIANTS.items():
+        cfg, st = make()
+        counts = glm_counts(cfg, st)
+        u = units_glm(cfg)
+        per = {ph: sum(counts[ph].values()) / u[ph] for ph in ("c2p", "recon", "riemann", "fluxdiff", "rk", "cfl")}
+        out["variants"][name] = {"config": {k: cfg[k] for k in ("ndim", "n", "recon", "riemann", "rk", "bc")},
+                                 "divb": "glm", "per_unit": per}
     path = os.path.join(HERE, "flops_per_unit.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
