@@ -300,10 +300,10 @@ int mhd_adjoint_grad_prim(mhd_ctx* ctx, int mem, double* grad_rho, double* const
  * GPU loading the library holds until the process exits.  The call allocates
  * nothing (no cudaMalloc, no cudaFree, no allocating library routine).
  *
- * Limit: grids whose padded scratch (56 float64 fields over the padded box,
+ * Limit: grids whose padded scratch (57 float64 fields over the padded box,
  * (nx+2G+1)(ny+2G+1)(nz+2G+1) cells with G = 2 for PLM and 3 otherwise; 2D:
  * no z padding) exceeds the array are rejected with MHD_ERR_TOO_LARGE before
- * any device work (about 268 x 268 in 2D or 37^3 in 3D with PLM).
+ * any device work (about 266 x 266 in 2D or 36^3 in 3D with PLM).
  *
  * The array is shared by every call and keeps the last call's contents: the
  * call clears the part it uses before the step.  Calls that overlap on the GPU

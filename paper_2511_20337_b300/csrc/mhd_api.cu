@@ -52,14 +52,21 @@ void prim(mhd_ctx* c, const F8& S, bool cfl) {
   long long work = (long long)(g.n[0] + 2 * g.G) * (g.n[1] + 2 * g.G) * (g.ndim == 3 ? g.n[2] + 2 * g.G : 1);
   int nb = blocks_for(work, 256);
   if (g.ndim == 2) {
-    if (cfl) prim_kernel<2, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc);
-    else prim_kernel<2, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc);
+    if (cfl) prim_kernel<2, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
+    else prim_kernel<2, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
   } else {
-    if (cfl) prim_kernel<3, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc);
-    else prim_kernel<3, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc);
+    if (cfl) prim_kernel<3, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
+    else prim_kernel<3, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
   }
   c->launches++;
   prof_mark(c, MHD_KCLASS_PRIM);
+  if (cfl) {  // the IEEE decision among the candidates, and dt
+    const long long cells = (long long)g.n[0] * g.n[1] * g.n[2];
+    if (g.ndim == 2) cfl_exact_kernel<2><<<blocks_for(cells, 256), 256, 0, c->stream>>>(g, c->P, c->lam, c->sc);
+    else cfl_exact_kernel<3><<<blocks_for(cells, 256), 256, 0, c->stream>>>(g, c->P, c->lam, c->sc);
+    c->launches++;
+    prof_mark(c, MHD_KCLASS_PRIM);
+  }
 }
 
 template <int DIR, int NDIM, int RECON, int RS>
@@ -288,7 +295,7 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
   }
   // CT: 3 registers of 8, primitives 8, increment 6, ingredients 15, edges 3;
   // GLM: 3 registers of 9, primitives 9, increment 9
-  const int nfields = g.glm ? 3 * 9 + 9 + 9 : 3 * 8 + 8 + 6 + 15 + 3;
+  const int nfields = (g.glm ? 3 * 9 + 9 + 9 : 3 * 8 + 8 + 6 + 15 + 3) + 1;  // + the CFL rates
   size_t bytes = c->field_elems * sizeof(double) * nfields;
   if (cudaMalloc(&c->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -318,6 +325,7 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
       for (int q = 0; q < 5; q++) c->ING.a[d][q] = next();
     for (int d = 0; d < 3; d++) c->E.e[d] = next();
   }
+  c->lam = next();
   if (cudaMalloc(&c->sc, sizeof(DevScalars)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->pool);
@@ -721,7 +729,7 @@ int mhd_probe_fp64(double* gflops_out) {
 namespace {
 
 constexpr size_t kNoAllocDoubles = MHD_NOALLOC_SCRATCH_BYTES / sizeof(double);
-constexpr int kNoAllocFields = 3 * 8 + 8 + 6 + 15 + 3;  // same carve-up as mhd_create
+constexpr int kNoAllocFields = 3 * 8 + 8 + 6 + 15 + 3 + 1;  // same carve-up as mhd_create (CT)
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
@@ -784,6 +792,7 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   for (int d = 0; d < 3; d++)
     for (int q = 0; q < 5; q++) c.ING.a[d][q] = next();
   for (int d = 0; d < 3; d++) c.E.e[d] = next();
+  c.lam = next();
   c.sc = reinterpret_cast<DevScalars*>(p);
   c.has_state = true;
 

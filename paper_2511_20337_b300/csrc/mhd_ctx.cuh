@@ -22,6 +22,7 @@ struct mhd_ctx {
   mhd::L6 L;           // stage increment of the cell variables
   mhd::Ingr5x3 ING;    // UCT face ingredients
   mhd::E3 E;           // edge fields
+  double* lam;         // near-IEEE CFL rate of every cell (the candidate pass of the CFL step)
   mhd::DevScalars* sc;
   bool has_state;
   int seglen;

@@ -52,6 +52,7 @@ struct DevScalars {                     // small device-side scalars of one cont
   double time;                          // accumulated time
   unsigned long long fallbacks;         // first-order reconstruction fallbacks
   unsigned long long floors;            // interior pressures raised to the floor
+  unsigned long long lapx_bits;         // max of the near-IEEE CFL rates (candidate search)
 };
 
 // ---------------------------------------------------------------------------
@@ -232,6 +233,22 @@ __device__ __forceinline__ double prim_item(const Grid& g, const F8& S, const F8
   }
   return lam;
 }
+// Block maximum of rates (positive doubles: their bits order like unsigned
+// integers), folded into *dst.  Every thread of the block must call this.
+__device__ __forceinline__ void block_max_into(double lam_max, unsigned long long* dst) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lam_max = fmax(lam_max, __shfl_xor_sync(0xffffffffu, lam_max, o));
+  __shared__ double wm[8];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wm[wid] = lam_max;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmax(m, wm[w]);
+    atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
 // Block maximum of the CFL rates, folded into the grid's maximum; the last of
 // the grid's nblocks blocks forms dt = cfl / max rate and adds it to the time.
 // Every thread of the block must call this.
@@ -256,21 +273,90 @@ __device__ __forceinline__ void cfl_block_finish(double lam_max, DevScalars* sc,
       sc->dt = dt;
       sc->time = sc->time + dt;
       sc->lmax_bits = 0ull;
+      sc->lapx_bits = 0ull;
       sc->blocks_done = 0u;
     }
   }
 }
 
+// CFL rate of one interior cell from its primitives: with IEEE operations
+// throughout (prim_item's rate), or with the square roots and division
+// replaced by refined seeds (fast_speed_near_ieee, within ~1e-14 of it).
+template <int NDIM>
+__device__ __forceinline__ double cfl_rate_near_ieee(const Grid& g, const Prim8& V) {
+  double B2 = a_(a_(m_(V.bx, V.bx), m_(V.by, V.by)), m_(V.bz, V.bz));
+  double lam = m_(a_(fabs(V.vx), fast_speed_near_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
+  lam = a_(lam, m_(a_(fabs(V.vy), fast_speed_near_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
+  if (NDIM == 3) lam = a_(lam, m_(a_(fabs(V.vz), fast_speed_near_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
+  return lam;
+}
+template <int NDIM>
+__device__ __forceinline__ double cfl_rate_ieee(const Grid& g, const Prim8& V) {
+  double B2 = a_(a_(m_(V.bx, V.bx), m_(V.by, V.by)), m_(V.bz, V.bz));
+  double lam = m_(a_(fabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
+  lam = a_(lam, m_(a_(fabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
+  if (NDIM == 3) lam = a_(lam, m_(a_(fabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
+  return lam;
+}
+// Primitive pass of the single grid; with CFL, the near-IEEE rate of every
+// interior cell goes to lam_near and its maximum to sc->lapx_bits (the
+// IEEE decision follows in cfl_exact_kernel).
 template <int NDIM, bool CFL>
-static __global__ void __launch_bounds__(256) prim_kernel(Grid g, F8 S, F8 P, DevScalars* sc) {
+static __global__ void __launch_bounds__(256) prim_kernel(Grid g, F8 S, F8 P, DevScalars* sc, double* lam_near) {
   const long long total = prim_work<NDIM>(g);
   double lam_max = 0.0;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
-    double lam = prim_item<NDIM, CFL>(g, S, P, sc, id);
-    lam_max = (lam > lam_max) ? lam : lam_max;
+    prim_item<NDIM, false>(g, S, P, sc, id);
+    if (CFL) {
+      const int nxp = g.n[0] + 2 * g.G, nyp = g.n[1] + 2 * g.G;
+      int i = (int)(id % nxp) - g.G;
+      long long r = id / nxp;
+      int j = (int)(r % nyp) - g.G;
+      int k = NDIM == 3 ? (int)(r / nyp) - g.G : 0;
+      if (i >= 0 && i < g.n[0] && j >= 0 && j < g.n[1] && k >= 0 && k < g.n[2]) {
+        const int c = g.at(i, j, k);
+        Prim8 V;
+        V.rho = P.q[0][c]; V.vx = P.q[1][c]; V.vy = P.q[2][c]; V.vz = P.q[3][c];
+        V.bx = P.q[4][c]; V.by = P.q[5][c]; V.bz = P.q[6][c]; V.p = P.q[7][c];
+        const double lam = cfl_rate_near_ieee<NDIM>(g, V);
+        lam_near[c] = lam;
+        lam_max = (lam > lam_max) ? lam : lam_max;
+      }
+    }
   }
-  if (CFL) cfl_block_finish(lam_max, sc, g.cfl, gridDim.x);
+  if (CFL) block_max_into(lam_max, &sc->lapx_bits);
+}
+
+// CFL step in two passes (single-grid path): the primitive pass stores, per
+// interior cell, the rate computed with fast_speed_near_ieee (within ~1e-14
+// of the IEEE rate) and its maximum M; this pass recomputes the IEEE rate of
+// prim_item only where the stored rate is within 4e-13 of M -- the cell of
+// the largest IEEE rate is among them -- and forms dt from their maximum:
+// the same dt, to the bit, as the IEEE rate of every cell.
+template <int NDIM>
+static __global__ void __launch_bounds__(256) cfl_exact_kernel(Grid g, F8 P, const double* __restrict__ lam_near,
+                                                               DevScalars* sc) {
+  const double M = __longlong_as_double((long long)sc->lapx_bits);
+  const double T = M * (1.0 - 4e-13);
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  double lam_max = 0.0;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(id % g.n[0]);
+    long long r = id / g.n[0];
+    int j = (int)(r % g.n[1]);
+    int k = (int)(r / g.n[1]);
+    int c = g.at(i, j, k);
+    if (lam_near[c] >= T) {
+      Prim8 V;
+      V.rho = P.q[0][c]; V.vx = P.q[1][c]; V.vy = P.q[2][c]; V.vz = P.q[3][c];
+      V.bx = P.q[4][c]; V.by = P.q[5][c]; V.bz = P.q[6][c]; V.p = P.q[7][c];
+      const double lam = cfl_rate_ieee<NDIM>(g, V);
+      lam_max = (lam > lam_max) ? lam : lam_max;
+    }
+  }
+  cfl_block_finish(lam_max, sc, g.cfl, gridDim.x);
 }
 
 // Set the step size from the host value (mhd_step) and add it to the time.

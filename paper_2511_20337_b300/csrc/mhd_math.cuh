@@ -141,6 +141,20 @@ __device__ __forceinline__ double frsqrt(double x) {
 }
 // sqrt(x) for x >= 0 (the seed of 0 is infinite)
 __device__ __forceinline__ double fsqrt0(double x) { return gt0(x) ? fsqrt(x) : 0.0; }
+
+// fast_speed_ieee with its square roots and division replaced by the refined
+// seeds (about one ulp each), everything else in the same IEEE operations:
+// the discriminant is bit-identical, so the result stays within ~10 ulp of
+// fast_speed_ieee even where the discriminant cancels.  Used to find the
+// candidates for the largest CFL rate, which fast_speed_ieee then decides.
+__device__ __forceinline__ double fast_speed_near_ieee(double rho, double p, double B2, double bn, double gamma) {
+  double gp = __dmul_rn(gamma, p);
+  double s = __dadd_rn(gp, B2);
+  double disc = __dsub_rn(__dmul_rn(s, s), __dmul_rn(__dmul_rn(4.0, gp), __dmul_rn(bn, bn)));
+  double sq = lt_pos(disc, 1e-290) ? 0.0 : fsqrt(disc);  // 0 for disc <= 0 and for subnormal disc
+  double cf2 = __dmul_rn(__dmul_rn(0.5, __dadd_rn(s, sq)), rcp(rho));
+  return fsqrt(cf2);
+}
 // a * b rounded once, never contracted into a neighbouring add
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
