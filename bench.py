@@ -15,7 +15,6 @@ cell-updates / max rank time.
 sample of the same workload (a smaller grid of the same kind), same metric.
 """
 import argparse
-import glob
 import hashlib
 import json
 import math
@@ -217,16 +216,23 @@ def adjoint_flop_model(cfg, variant):
     return {"step": rk * stage, "riemann_per_launch": per["riemann"] * sum(faces_dir) / nd}
 
 
+SWEEP_SOURCES = ("mhd_math.cuh", "mhd_kernels.cuh")  # everything the sweep kernels are compiled from
+
+
+def sweep_source_hash():
+    src = [os.path.join(ROOT, "paper_2511_20337_b300", "csrc", f) for f in SWEEP_SOURCES]
+    return hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
+
+
 def sweep_traffic(variant, faces_per_launch):
     """DRAM bytes per sweep launch from the committed ncu captures
     (profiles/sweep_traffic.json), scaled by faces per launch; None when the
-    kernel sources changed since the capture or no capture exists."""
+    sweep kernels' sources changed since the capture or no capture exists."""
     path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    src = sorted(glob.glob(os.path.join(ROOT, "paper_2511_20337_b300", "csrc", "*")))
-    h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
+    h = sweep_source_hash()
     if rec.get("source_hash") != h or variant not in rec:
         return None
     v = rec[variant]

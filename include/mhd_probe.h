@@ -67,6 +67,16 @@ int mhd_adjoint_profile(mhd_ctx* ctx, int nsteps, const double* dts, int ckpt_ev
 int mhd_probe_riemann_vjp(int riemann, int n, double gamma, const double* in, const double* cot, double* dual,
                           double* hand);
 
+/* Both per-cell CFL rates of the single-grid step (the rate of the CFL
+ * reading: sum over the ndim axes of (|v_d| + c_f,d) / dx_d, c_f,d the fast
+ * speed with the cell field B_d) for n primitive states: near_out[n] gets the
+ * candidate-pass rate (IEEE products and sums, approximate square roots and
+ * reciprocal) and ieee_out[n] the IEEE rate that decides the step.  prim is
+ * a host array [n][8] = (rho, vx, vy, vz, bx, by, bz, p); dx[3] the cell
+ * widths (> 0); gamma > 1.  Sync. */
+int mhd_probe_cfl_rate(int ndim, double gamma, const double* dx, int n, const double* prim, double* near_out,
+                       double* ieee_out);
+
 /* Measure the device's FP64 fused multiply-add throughput on the current
  * device: every SM runs independent chains of dependent DFMA for about
  * 20 ms; *gflops_out = 2 * DFMA per second / 1e9.  Sync; allocates and frees

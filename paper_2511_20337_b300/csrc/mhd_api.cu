@@ -686,6 +686,20 @@ __global__ void fp64_probe_kernel(double* out, double a, double b, int iters) {
 }
 }  // namespace
 
+// Both CFL rates of n primitive states (rho, vx, vy, vz, bx, by, bz, p each).
+template <int NDIM>
+static __global__ void cfl_rate_probe_kernel(mhd::Grid g, int n, const double* __restrict__ prim, double* near_out,
+                                             double* ieee_out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double* w = prim + (size_t)8 * t;
+  mhd::Prim8 V;
+  V.rho = w[0]; V.vx = w[1]; V.vy = w[2]; V.vz = w[3];
+  V.bx = w[4]; V.by = w[5]; V.bz = w[6]; V.p = w[7];
+  near_out[t] = mhd::cfl_rate_near_ieee<NDIM>(g, V);
+  ieee_out[t] = mhd::cfl_rate_ieee<NDIM>(g, V);
+}
+
 extern "C" {
 
 int mhd_probe_fp64(double* gflops_out) {
@@ -717,6 +731,37 @@ int mhd_probe_fp64(double* gflops_out) {
   double flops = 2.0 * 8.0 * iters * (double)threads * blocks;
   *gflops_out = flops / (best * 1e-3) / 1e9;
   return MHD_OK;
+}
+
+int mhd_probe_cfl_rate(int ndim, double gamma, const double* dx, int n, const double* prim, double* near_out,
+                       double* ieee_out) {
+  if ((ndim != 2 && ndim != 3) || !(gamma > 1.0) || !dx || n < 1 || !prim || !near_out || !ieee_out)
+    return MHD_ERR_ARG;
+  mhd::Grid g{};
+  g.ndim = ndim;
+  g.gamma = gamma;
+  for (int d = 0; d < 3; d++) {
+    if (!(dx[d] > 0.0)) return MHD_ERR_ARG;
+    g.dx[d] = dx[d];
+    g.idx[d] = 1.0 / dx[d];
+  }
+  double *d_prim = nullptr, *d_near = nullptr, *d_ieee = nullptr;
+  cudaError_t e = cudaMalloc(&d_prim, sizeof(double) * 8 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&d_near, sizeof(double) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&d_ieee, sizeof(double) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMemcpy(d_prim, prim, sizeof(double) * 8 * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int nb = (n + 255) / 256;
+    if (ndim == 3) cfl_rate_probe_kernel<3><<<nb, 256>>>(g, n, d_prim, d_near, d_ieee);
+    else cfl_rate_probe_kernel<2><<<nb, 256>>>(g, n, d_prim, d_near, d_ieee);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(near_out, d_near, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ieee_out, d_ieee, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(d_prim);
+  cudaFree(d_near);
+  cudaFree(d_ieee);
+  return cuda_err(e);
 }
 
 }  // extern "C"

@@ -36,7 +36,7 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
-           "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi")
+           "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -108,6 +108,7 @@ def lib():
             "mhd_autotune": (I, [P, ctypes.POINTER(I)]),
             "mhd_set_psi": (I, [P, I, P]),
             "mhd_get_psi": (I, [P, I, P]),
+            "mhd_probe_cfl_rate": (I, [I, D, P, I, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -401,6 +402,18 @@ def probe_riemann_vjp(solver, inputs, cotangents, gamma):
     _check(lib().mhd_probe_riemann_vjp(RIEMANN[solver], n, float(gamma), _ptr(x), _ptr(c), _ptr(dual), _ptr(hand)),
            "mhd_probe_riemann_vjp")
     return dual, hand
+
+
+def probe_cfl_rate(ndim, gamma, dx, prim):
+    """Both CFL rates of the device for primitive states prim (n, 8) =
+    (rho, vx, vy, vz, bx, by, bz, p): (candidate-pass rate, IEEE rate)."""
+    x = np.ascontiguousarray(np.asarray(prim, dtype=np.float64))
+    d = np.ascontiguousarray(np.asarray(dx, dtype=np.float64))
+    n = x.shape[0]
+    near, ieee = np.zeros(n), np.zeros(n)
+    _check(lib().mhd_probe_cfl_rate(int(ndim), float(gamma), _ptr(d), n, _ptr(x), _ptr(near), _ptr(ieee)),
+           "mhd_probe_cfl_rate")
+    return near, ieee
 
 
 def probe_fp64_gflops():

@@ -1,0 +1,253 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark times: inputs resident on the device, the library on a side stream,
+the segment length autotuned up to 256^3 cells (16 above), the CFL step taken
+on the device and the step graph captured, then replayed.
+
+* One step of each 3D workload against the oracle on sampled boxes.  The
+  sampled-window oracle (window.py) equals the full-grid oracle on its box to
+  the bit.  The boxes include the periodic wrap and the outflow corners.  The
+  device's CFL step equals the oracle's to the bit.
+* The replayed step graph gives the captured step's state bitwise.
+* The 256-run ensemble in one batched step: every run's CFL step against the
+  oracle's; sampled runs compared whole.  The bound for those runs is 1e-12
+  plus four times the oracle's own spread under ulp-level input changes, which
+  reaches ~2e-12 relative on the Orszag-Tang symmetry lines of the 512^2 runs.
+* The 400-step adjoint of the 256^2 workload against central differences of
+  the GPU forward run.  This property holds at any size; no oracle tape of
+  400 steps on 256^2 cells finishes in seconds.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_20337_b300 import mhd
+from paper_2511_20337_b300 import workloads as W
+from window import window_step, halo_for, box, blockwise_cfl_dt
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# Normalisation groups: a variable's error is measured against the largest
+# oracle magnitude of its group over all sampled boxes (the momentum of a
+# quiet corner is exactly 0; psi is measured against the field it cleans).
+GROUP = {"rho": "rho", "mx": "m", "my": "m", "mz": "m", "E": "E",
+         "b0": "B", "b1": "B", "b2": "B", "bx": "B", "by": "B", "bz": "B", "psi": "B"}
+TOL = 1e-12  # one step, as in the small-grid parity tests
+
+
+def keys_of(cfg):
+    return oracle.GLM_KEYS if cfg.get("divb", "ct") == "glm" else oracle.KEYS
+
+
+def cells(cfg):
+    return int(np.prod(cfg["n"][:cfg["ndim"]]))
+
+
+def bench_step(cfg, st):
+    """One CFL step as the benchmark launches it; checks the graph replay
+    against the captured run.  Returns (device dt, host state after the step)."""
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    keys = keys_of(cfg)
+    devs = {k: torch.from_numpy(np.ascontiguousarray(st[k])).to(dev) for k in keys}
+    sim = mhd.Sim(cfg, devs, stream=stream.cuda_stream)
+    try:
+        if cells(cfg) <= 256 ** 3:
+            sim.autotune()
+        outs = []
+        for _ in range(2):  # the first advance captures the step graph, the second replays it
+            sim.set_conserved(devs)
+            sim.advance(1)
+            out = {k: torch.empty_like(devs[k]) for k in keys}
+            sim.get_conserved(out)
+            torch.cuda.synchronize(dev)
+            rc, bad = sim.status()
+            assert rc == 0, f"device status {rc} at cell {bad}"
+            outs.append((sim.last_dt, out))
+        (dt, a), (dt2, b) = outs
+        assert dt2 == dt
+        for k in keys:
+            assert torch.equal(a[k], b[k]), f"graph replay differs in {k}"
+        del b
+        host = {k: a[k].cpu().numpy() for k in keys}
+    finally:
+        sim.close()
+        del devs
+        torch.cuda.empty_cache()
+    return dt, host
+
+
+def compare_boxes(cfg, st, out, dt, boxes, size):
+    nd = cfg["ndim"]
+    keys = keys_of(cfg)
+    sz = [size] * nd
+    rows = [(lo, window_step(cfg, st, lo, sz, halo_for(cfg), dt)) for lo in boxes]
+    scale = {}
+    for _, ref in rows:
+        for k in keys:
+            scale[GROUP[k]] = max(scale.get(GROUP[k], 0.0), float(np.max(np.abs(ref[k]))))
+    for lo, ref in rows:
+        for k in keys:
+            got = box(out[k], lo, sz, cfg["n"])
+            err = float(np.max(np.abs(got - ref[k])))
+            assert err <= TOL * scale[GROUP[k]], (k, lo, err, scale[GROUP[k]])
+
+
+def random_boxes(cfg, size, count, seed):
+    rng = np.random.default_rng(seed)
+    n = cfg["n"]
+    return [[int(rng.integers(0, n[d] - size + 1)) for d in range(cfg["ndim"])] for _ in range(count)]
+
+
+def test_turbulent3d_256_ct():
+    """PLM + HLLD + SSP-RK2 + UCT, periodic 256^3 (staged x sweep, autotuned segments)."""
+    cfg, st = W.turbulent_3d(256)
+    dt, out = bench_step(cfg, st)
+    assert dt == oracle.cfl_dt_state(cfg, st)
+    boxes = [[254, 255, 253], [0, 0, 0], [127, 63, 200]] + random_boxes(cfg, 4, 4, 1)
+    compare_boxes(cfg, st, out, dt, boxes, 4)
+
+
+def test_turbulent3d_256_glm():
+    """The same workload with GLM divergence cleaning (cell B and psi)."""
+    cfg, st = W.to_glm(*W.turbulent_3d(256))
+    dt, out = bench_step(cfg, st)
+    assert dt == blockwise_cfl_dt(cfg, st, 64)
+    boxes = [[253, 254, 255], [31, 200, 100]] + random_boxes(cfg, 4, 4, 2)
+    compare_boxes(cfg, st, out, dt, boxes, 4)
+
+
+def test_blast3d_512():
+    """WENO-Z + HLLD + SSP-RK3 + UCT with outflow boundaries and the pressure
+    floor: boxes in the blast, across its rim, at two corners and at random."""
+    cfg, st = W.blast_3d(512)
+    dt, out = bench_step(cfg, st)
+    assert dt == oracle.cfl_dt_state(cfg, st)
+    # r = 0.1 is 51.2 cells from the centre (face 256)
+    boxes = [[254, 254, 254], [305, 254, 255], [254, 203, 300], [0, 0, 0], [508, 508, 508], [508, 0, 300]]
+    boxes += random_boxes(cfg, 4, 2, 3)
+    compare_boxes(cfg, st, out, dt, boxes, 4)
+
+
+def test_orszag_tang3d_704():
+    """The paper's 3D Orszag-Tang setup at 704 x 704 x 352 with WENO-Z + HLLD + SSP-RK3."""
+    cfg, st = W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3)
+    dt, out = bench_step(cfg, st)
+    assert dt == oracle.cfl_dt_state(cfg, st)
+    boxes = [[702, 703, 350], [352, 176, 88], [0, 500, 351]] + random_boxes(cfg, 4, 3, 4)
+    compare_boxes(cfg, st, out, dt, boxes, 4)
+
+
+def test_ensemble_256_runs():
+    """256 Orszag-Tang runs of 64^2 .. 512^2 cells in one batched, graph-captured step."""
+    members = W.ensemble_members(256, seed=4)
+    cases = [W.ensemble_member_state(m) for m in members]
+    cfgs = [c for c, _ in cases]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    bt = mhd.Batch(cfgs, stream=stream.cuda_stream)
+    try:
+        for r, (_, s) in enumerate(cases):
+            bt.set_conserved(r, s)
+        bt.autotune()
+        runs = []
+        for _ in range(2):  # capture, then replay
+            for r, (_, s) in enumerate(cases):
+                bt.set_conserved(r, s)
+            bt.step(1)
+            rc, bad_run, bad = bt.status()
+            assert rc == 0, (rc, bad_run, bad)
+            runs.append(bt.times())
+        dts = runs[1]
+        assert runs[0] == dts
+        for r, (c, s) in enumerate(cases):
+            assert dts[r] == oracle.cfl_dt_state(c, s), f"CFL step of run {r}"
+        ns = [m["n"] for m in members]
+        betas = [m["beta"] for m in members]
+        machs = [m["mach"] for m in members]
+        pick = {int(np.argmin(ns)), int(np.argmax(ns)), int(np.argmin(betas)), int(np.argmax(betas)),
+                int(np.argmax(machs)), 0, 255}
+        pick |= {int(v) for v in np.random.default_rng(5).integers(0, 256, 3)}
+        rng = np.random.default_rng(6)
+        for r in sorted(pick):
+            c, s = cases[r]
+            o = oracle.OracleSim(c, s)
+            o.step(dts[r])
+            ref = o.get_state()
+            spread = oracle_spread(c, s, dts[r], ref, rng)
+            got = bt.get_conserved(r)
+            scale = {}
+            for k in oracle.KEYS:
+                scale[GROUP[k]] = max(scale.get(GROUP[k], 0.0), float(np.max(np.abs(ref[k]))))
+            for k in oracle.KEYS:
+                err = float(np.max(np.abs(got[k] - ref[k])))
+                assert err <= TOL * scale[GROUP[k]] + 4 * spread[k], (r, members[r], k, err, spread[k])
+    finally:
+        bt.close()
+
+
+def ulp_jitter(st, rng):
+    """Every nonzero input value moved by -1, 0 or +1 ulp at random (the
+    duplicate last face of each periodic axis kept equal to face 0)."""
+    out = {}
+    for k, v in st.items():
+        r = rng.integers(-1, 2, size=v.shape)
+        w = np.where(r > 0, np.nextafter(v, np.inf), np.where(r < 0, np.nextafter(v, -np.inf), v))
+        out[k] = np.where(v == 0.0, v, w)
+    out["b0"][..., -1] = out["b0"][..., 0]
+    out["b1"][:, -1, :] = out["b1"][:, 0, :]
+    return out
+
+
+def oracle_spread(cfg, st, dt, ref, rng, trials=2):
+    """How far the oracle's own step moves when its input moves by an ulp:
+    the largest change per variable over a few jittered inputs.  On the
+    ensemble's Orszag-Tang symmetry lines (x = 1/4, 1/2, 3/4, where sin 4 pi x
+    changes sign) the HLLD step is ill-conditioned there, turning ulp-level
+    input changes into relative changes of ~2e-12 in the momentum and energy,
+    so two correct implementations that round differently disagree by as much."""
+    spread = {k: 0.0 for k in oracle.KEYS}
+    for _ in range(trials):
+        o = oracle.OracleSim(cfg, ulp_jitter(st, rng))
+        o.step(dt)
+        out = o.get_state()
+        for k in oracle.KEYS:
+            spread[k] = max(spread[k], float(np.max(np.abs(out[k] - ref[k]))))
+    return spread
+
+
+def test_adjoint2d_256_400_steps_central_differences():
+    """<dJ/d(rho, vx, vy), d> of the 400-step gradient (checkpoints every 20,
+    step sizes frozen) against (J(+h d) - J(-h d)) / 2h of the GPU forward.
+    The directions leave v_z, p and B alone: those start uniform, so their
+    slopes sit at minmod(0, 0), where J is only directionally differentiable."""
+    cfg, st = W.adjoint_2d(256)
+    rho = st["rho"]
+    v = [st["mx"] / rho, st["my"] / rho, st["mz"] / rho]
+    p = np.ones_like(rho)
+    B = (st["b0"], st["b1"], st["b2"])
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    sim = mhd.Sim(cfg, stream=stream.cuda_stream)
+    try:
+        sim.set_prim(rho, v, p, B)
+        sim.autotune()
+        sim.set_prim(rho, v, p, B)
+        _, dts = sim.adjoint(400, None, 20)
+        assert np.all(dts > 0)
+        g = sim.grad_prim()
+        X, Y, _ = W.cell_centres(cfg)
+        tp = 2 * np.pi
+        ph = np.random.default_rng(23).uniform(0, tp, 3)
+        d = {"rho": 0.05 * np.sin(tp * X + ph[0]) * np.cos(2 * tp * Y),
+             "vx": 0.05 * np.cos(tp * (X + Y) + ph[1]), "vy": 0.05 * np.sin(tp * (X - 2 * Y) + ph[2])}
+        dot = sum(float(np.sum(g[k] * d[k])) for k in d)
+
+        def J(h):
+            sim.set_prim(rho + h * d["rho"], [v[0] + h * d["vx"], v[1] + h * d["vy"], v[2]], p, B)
+            return sim.adjoint(400, dts, 20)[0]
+
+        errs = [abs((J(h) - J(-h)) / (2 * h) - dot) / abs(dot) for h in (1e-5, 1e-6)]
+        assert min(errs) <= 1e-5, (errs, dot)
+    finally:
+        sim.close()

@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 from paper_2511_20337_b300 import workloads as W
-from window import window_step, box, halo_for
+from window import window_step, box, halo_for, blockwise_cfl_dt
 
 CASES = [
     ("rand3d-plm-hlld-rk2", lambda: (lambda c: (c, W.random_state(c, 41)))(W.base_cfg(3, (20, 18, 19), (0, 0, 0), (1, 1, 1)))),
@@ -35,3 +35,35 @@ def test_window_matches_full_grid(name, make):
         for k in oracle.KEYS:
             exp = box(ref[k], lo, size, n)
             np.testing.assert_array_equal(got[k], exp, err_msg=f"{k} lo={lo}")
+
+
+BLOCK_CASES = [
+    ("rand3d-40x36x34-ct", 16, lambda: (lambda c: (c, W.random_state(c, 43)))(W.base_cfg(3, (40, 36, 34), (0, 0, 0), (1, 0.9, 1.1)))),
+    ("blast3d-40-outflow-ct", 16, lambda: W.blast_3d(40)),
+    ("ot2d-80-ct", 16, lambda: W.orszag_tang_2d(80)),
+    ("turbulent3d-32-glm", 8, lambda: W.to_glm(*W.turbulent_3d(32))),
+    ("rand3d-24x20x18-glm", 8, lambda: W.to_glm(*(lambda c: (c, W.random_state(c, 44)))(
+        W.base_cfg(3, (24, 20, 18), (0, 0, 0), (1, 1, 1))))),
+]
+
+
+@pytest.mark.parametrize("name,block,make", BLOCK_CASES, ids=[c[0] for c in BLOCK_CASES])
+def test_blockwise_cfl_equals_full_grid_cfl(name, block, make):
+    cfg, st = make()
+    glm = cfg.get("divb", "ct") == "glm"
+    full = (oracle.OracleGlm(cfg, st) if glm else oracle.OracleSim(cfg, st)).cfl_dt()
+    assert blockwise_cfl_dt(cfg, st, block) == full
+
+
+def test_glm_window_matches_full_grid():
+    cfg, st = W.to_glm(*W.orszag_tang_2d(64, recon="wenoz", rk=3), alpha=0.2)
+    rng = np.random.default_rng(9)
+    st["psi"] = 0.01 * rng.standard_normal(st["rho"].shape)
+    full = oracle.OracleGlm(cfg, st, alpha=0.2)
+    dt = full.cfl_dt()
+    full.step(dt)
+    ref = full.get_state()
+    for lo in ([0, 0], [61, 3], [30, 62]):
+        got = window_step(cfg, st, lo, [3, 3], halo_for(cfg), dt)
+        for k in oracle.GLM_KEYS:
+            np.testing.assert_array_equal(got[k], box(ref[k], lo, [3, 3], cfg["n"]), err_msg=f"{k} lo={lo}")

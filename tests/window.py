@@ -79,7 +79,7 @@ def extract(cfg, state, lo, size, halo):
     wcfg["bc"] = bc + ["periodic"] * (6 - len(bc))
 
     def take(a, face_axis):
-        out = a
+        sl, gathers = [slice(None)] * a.ndim, []
         for d in range(nd):
             ax = 2 - d  # arrays are [z][y][x]
             ids = idx[d]
@@ -87,23 +87,36 @@ def extract(cfg, state, lo, size, halo):
                 ids = np.concatenate([ids, ids[-1:] + 1])
             if cfg["bc"][2 * d] == "periodic":
                 ids = ids % n[d]   # the duplicate last face of a periodic axis is face 0
+            if ids[-1] - ids[0] == len(ids) - 1:
+                sl[ax] = slice(int(ids[0]), int(ids[-1]) + 1)   # a plain range: a view
+            else:
+                gathers.append((ax, ids))
+        out = a[tuple(sl)]
+        for ax, ids in gathers:  # wrapped ranges, on the already reduced array
             out = np.take(out, ids, axis=ax)
         return out
 
     ws = {}
-    for q, k in enumerate(KEYS):
-        fa = q - 5 if (q >= 5 and (q - 5) < nd) else -1
+    glm = cfg.get("divb", "ct") == "glm"
+    for q, k in enumerate(oracle.GLM_KEYS if glm else KEYS):
+        fa = q - 5 if (not glm and q >= 5 and (q - 5) < nd) else -1  # GLM: every field is cell-centred
         ws[k] = np.ascontiguousarray(take(state[k], fa))
     return wcfg, ws, inner
 
 
 def window_step(cfg, state, lo, size, halo, dt):
-    """Oracle values of the cells (and their left faces) of the box after one step of dt."""
+    """Oracle values of the cells (and their left faces) of the box after one
+    step of dt (the GLM scheme's oracle when cfg has divb = glm)."""
     wcfg, ws, offs = extract(cfg, state, lo, size, halo)
-    s = oracle.OracleSim(wcfg, ws)
+    if cfg.get("divb", "ct") == "glm":
+        s = oracle.OracleGlm(wcfg, ws, alpha=cfg["glm_alpha"])
+        keys = oracle.GLM_KEYS
+    else:
+        s = oracle.OracleSim(wcfg, ws)
+        keys = KEYS
     s.step(dt)
     out = s.get_state()
-    return {k: box(out[k], offs, size, wcfg["n"]) for k in KEYS}
+    return {k: box(out[k], offs, size, wcfg["n"]) for k in keys}
 
 
 def box(a, lo, size, n):
@@ -114,3 +127,24 @@ def box(a, lo, size, n):
         ids = np.arange(lo[d], lo[d] + size[d]) % n[d]
         out = np.take(out, ids, axis=2 - d)
     return out
+
+
+def blockwise_cfl_dt(cfg, state, block=64):
+    """The oracle's CFL step of the whole grid, taken block by block: each
+    block's oracle returns C / (its largest cell rate), a cell's rate depending
+    on that cell alone; division rounded to nearest is monotone, so the least
+    block step is C / (the grid's largest rate), to the bit.  Keeps the oracle's
+    memory to one block for grids far larger than a test would hold whole."""
+    nd = cfg["ndim"]
+    glm = cfg.get("divb", "ct") == "glm"
+    starts = [range(0, cfg["n"][d], block) for d in range(nd)]
+    best = None
+    for lo in np.array(np.meshgrid(*starts, indexing="ij")).reshape(nd, -1).T:
+        size = [min(block, cfg["n"][d] - int(lo[d])) for d in range(nd)]
+        wcfg, ws, _ = extract(cfg, state, [int(v) for v in lo], size, 0)
+        if list(wcfg["n"][:nd]) != size:
+            raise ValueError("block sizes must be powers of two dividing the grid")
+        o = oracle.OracleGlm(wcfg, ws) if glm else oracle.OracleSim(wcfg, ws)
+        dt = o.cfl_dt()
+        best = dt if best is None else min(best, dt)
+    return best
