@@ -447,20 +447,43 @@ def run_ours(args):
                 "kernel_ms_per_step": {k: v / prof_steps for k, v in kms.items()}}
 
     # ---- end to end through the C-ABI with host buffers ----
-    sim.set_conserved(host)
-    sim.advance(1)
-    sim.get_conserved(out_host)
+    # Two contexts on two streams take the steps in turn: a step's host-to-device
+    # copy overlaps the other context's step, and its device-to-host copy the
+    # next one's.  Each step waits for the previous one to end (two steps at once
+    # would share the SMs and finish together, leaving the GPU idle while both
+    # copy).  Every step still copies its whole input in from pinned host memory
+    # and its whole result out.
+    streams = (stream, torch.cuda.Stream(device=dev))
+    sim2 = mhd.Sim(cfg, devs, stream=ctypes_stream(streams[1]))
+    if seg is not None:
+        sim2.set_seglen(seg)
+    ctxs = (sim, sim2)
+    for c in ctxs:
+        c.set_conserved(host)
+        c.advance(1)                   # captures the step graph
+        c.get_conserved(out_host)
     torch.cuda.synchronize(dev)
     barrier()
-    e2e_steps = max(1, min(args.steps, 10))
+    e2e_steps = max(2, min(args.steps, 20))
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        sim.set_conserved(host)        # H2D of the step's input
-        sim.advance(1)
-        sim.get_conserved(out_host)    # D2H of the step's result (synchronous)
+    prev, done = None, None
+    for s in range(e2e_steps):
+        c, cs = ctxs[s % 2], streams[s % 2]
+        c.set_conserved(host)          # H2D of this step's input
+        if done is not None:
+            cs.wait_event(done)        # after the previous step
+        c.advance(1)
+        done = torch.cuda.Event()
+        done.record(cs)
+        if prev is not None:
+            prev.get_conserved(out_host)   # D2H of the previous step's result (synchronous)
+        prev = c
+    prev.get_conserved(out_host)
     el = job_time_ms(time.perf_counter() - t0, world, dev)
     e2e = {"value": ncell * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": h2d, "steps": e2e_steps}
+           "d2h_bytes_per_step": h2d, "steps": e2e_steps,
+           "pipeline": "two contexts alternate, steps in order; copies of one overlap the other's step"}
+    sim2.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -580,19 +603,41 @@ def run_ensemble(args):
         sm.close()
     del sims
 
-    # end to end: every run's state in from pinned host memory, one step, every state out
-    e2e_steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    # end to end: every run's state in from pinned host memory, one step, every
+    # state out; two batches on two streams take the steps in turn, so one's
+    # copies overlap the other's step (each step after the previous one)
+    streams = (stream, torch.cuda.Stream(device=dev))
+    bt2 = mhd.Batch(cfgs, stream=streams[1].cuda_stream)
+    bt2.set_seglen(*seg)
+    bts = (bt, bt2)
+    for b in bts:
         for r, h in enumerate(host):
-            bt.set_conserved(r, h)
-        bt.step(1)
-        for r, o in enumerate(out_host):
-            bt.get_conserved(r, o)
-    el = time.perf_counter() - t0
+            b.set_conserved(r, h)
+        b.step(1)                      # captures the step graph
+    torch.cuda.synchronize(dev)
+    e2e_steps = max(2, min(args.steps, 10))
+    t0 = time.perf_counter()
+    prev, done = None, None
+    for s in range(e2e_steps):
+        b, bs = bts[s % 2], streams[s % 2]
+        for r, h in enumerate(host):
+            b.set_conserved(r, h)
+        if done is not None:
+            bs.wait_event(done)
+        b.step(1)
+        done = torch.cuda.Event()
+        done.record(bs)
+        if prev is not None:
+            for r, o in enumerate(out_host):
+                prev.get_conserved(r, o)
+        prev = b
+    for r, o in enumerate(out_host):
+        prev.get_conserved(r, o)
+    el = job_time_ms(time.perf_counter() - t0, world, dev)
     e2e = {"value": ncell * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": h2d, "steps": e2e_steps}
+           "d2h_bytes_per_step": h2d, "steps": e2e_steps,
+           "pipeline": "two batches alternate, steps in order; copies of one overlap the other's step"}
+    bt2.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

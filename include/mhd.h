@@ -95,7 +95,10 @@ int mhd_destroy(mhd_ctx* ctx);
  * B[0], B[1] = face Bx, By; B[2] = face Bz (3D) or cell Bz (2D); layout as in
  * the file header.  mem = MHD_MEM_HOST or MHD_MEM_DEVICE says where the
  * caller's arrays live (host arrays should be pinned for async copies).
- * Resets the simulation time to 0.  Async. */
+ * Resets the simulation time to 0.  Async: the copies may still be running
+ * when the call returns (pageable host arrays are staged before it returns,
+ * pinned ones and device arrays are read later), so keep pinned or device
+ * arrays unchanged until the stream has passed the copies. */
 int mhd_set_conserved(mhd_ctx* ctx, int mem, const double* const* U, const double* const* B);
 
 /* Set the state from primitives: rho, v[0..2], p (cell arrays) and the field

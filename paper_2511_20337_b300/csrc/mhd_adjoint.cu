@@ -312,7 +312,7 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
   CK(cudaStreamSynchronize(c->stream));
   // the recompute passes below repeat the forward's counting: keep its scalars
   DevScalars fwd;
-  CK(cudaMemcpy(&fwd, c->sc, sizeof(fwd), cudaMemcpyDeviceToHost));
+  CK(copy_sync(&fwd, c->sc, sizeof(fwd), cudaMemcpyDeviceToHost, c->stream));
   if (fwd.status) return fwd.status;
   rc = seed(c, functional);
   if (rc) return rc;
@@ -379,8 +379,8 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
   CK(cudaMemcpyAsync(&a->J, a->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   DevScalars h;
-  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(c->sc, &fwd, sizeof(fwd), cudaMemcpyHostToDevice));
+  CK(copy_sync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(copy_sync(c->sc, &fwd, sizeof(fwd), cudaMemcpyHostToDevice, c->stream));
   if (h.status) return h.status;
   a->has_grad = true;
   if (J_out) *J_out = a->J;

@@ -372,10 +372,7 @@ static int set_common_faces(mhd_ctx* c, const double* const* B) {
 }
 
 static int reset_time(mhd_ctx* c) {
-  DevScalars h;
-  reset_scalars_host(&h);
-  CK(cudaMemcpyAsync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaStreamSynchronize(c->stream));  // h lives on this frame
+  CK(cudaMemcpyAsync(c->sc, reset_scalars_source(), sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
   return MHD_OK;
 }
 
@@ -431,13 +428,13 @@ int mhd_status(mhd_ctx* c, long long* bad_cell) {
   if (!c) return MHD_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
   DevScalars h;
-  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(copy_sync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   if (bad_cell) *bad_cell = h.status ? h.bad_cell : -1;
   if (h.status) {
     int st = h.status;
     h.status = 0;
     h.bad_cell = LLONG_MAX;
-    CK(cudaMemcpy(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice));
+    CK(copy_sync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
     return st;
   }
   return MHD_OK;
@@ -481,7 +478,7 @@ int mhd_cfl_dt(mhd_ctx* c, double* dt_out) {
   // evaluate the rate without touching the accumulated time
   DevScalars before;
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaMemcpy(&before, c->sc, sizeof(before), cudaMemcpyDeviceToHost));
+  CK(copy_sync(&before, c->sc, sizeof(before), cudaMemcpyDeviceToHost, c->stream));
   if (c->g.glm) {
     glm_ghost_fill(c, c->GU[0]);
     glm_prim(c, c->GU[0], true);
@@ -492,11 +489,11 @@ int mhd_cfl_dt(mhd_ctx* c, double* dt_out) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
   DevScalars after;
-  CK(cudaMemcpy(&after, c->sc, sizeof(after), cudaMemcpyDeviceToHost));
+  CK(copy_sync(&after, c->sc, sizeof(after), cudaMemcpyDeviceToHost, c->stream));
   *dt_out = after.dt;
   after.dt = before.dt;
   after.time = before.time;
-  CK(cudaMemcpy(c->sc, &after, sizeof(after), cudaMemcpyHostToDevice));
+  CK(copy_sync(c->sc, &after, sizeof(after), cudaMemcpyHostToDevice, c->stream));
   return after.status ? after.status : MHD_OK;
 }
 
@@ -540,7 +537,7 @@ int mhd_get_time(mhd_ctx* c, double* t_out) {
   if (!c || !t_out) return MHD_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
   DevScalars h;
-  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(copy_sync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   *t_out = h.time;
   return MHD_OK;
 }
@@ -549,7 +546,7 @@ int mhd_last_dt(mhd_ctx* c, double* dt_out) {
   if (!c || !dt_out) return MHD_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
   DevScalars h;
-  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(copy_sync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   *dt_out = h.dt;
   return MHD_OK;
 }
@@ -590,7 +587,7 @@ int mhd_autotune(mhd_ctx* c, int* seglen_out) {
   if (!c->has_state) return MHD_ERR_STATE;
   CK(cudaStreamSynchronize(c->stream));
   DevScalars sc_h;
-  CK(cudaMemcpy(&sc_h, c->sc, sizeof(sc_h), cudaMemcpyDeviceToHost));
+  CK(copy_sync(&sc_h, c->sc, sizeof(sc_h), cudaMemcpyDeviceToHost, c->stream));
   const size_t bytes = (size_t)c->reg_fields * c->field_elems * sizeof(double);  // U[0]'s fields are contiguous
   double* backup = nullptr;
   CK(cudaMalloc(&backup, bytes));
@@ -622,7 +619,7 @@ int mhd_autotune(mhd_ctx* c, int* seglen_out) {
   cudaEventDestroy(e1);
   cudaStreamSynchronize(c->stream);
   cudaFree(backup);
-  CK(cudaMemcpy(c->sc, &sc_h, sizeof(sc_h), cudaMemcpyHostToDevice));
+  CK(copy_sync(c->sc, &sc_h, sizeof(sc_h), cudaMemcpyHostToDevice, c->stream));
   c->seglen = pick;
   if (c->graph_ready) {
     cudaGraphExecDestroy(c->graph);
@@ -636,7 +633,7 @@ int mhd_counters(mhd_ctx* c, long long* recon_fallbacks, long long* pressure_flo
   if (!c) return MHD_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
   DevScalars h;
-  CK(cudaMemcpy(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost));
+  CK(copy_sync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   if (recon_fallbacks) *recon_fallbacks = (long long)h.fallbacks;
   if (pressure_floors) *pressure_floors = (long long)h.floors;
   return MHD_OK;
@@ -844,9 +841,7 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   // the array keeps the previous call's contents: clear what this call uses,
   // then set the device scalars (bad_cell starts at the largest index)
   CK(cudaMemsetAsync(base, 0, (size_t)need * sizeof(double), c.stream));
-  DevScalars h;
-  reset_scalars_host(&h);
-  CK(cudaMemcpyAsync(c.sc, &h, sizeof(h), cudaMemcpyHostToDevice, c.stream));
+  CK(cudaMemcpyAsync(c.sc, reset_scalars_source(), sizeof(DevScalars), cudaMemcpyHostToDevice, c.stream));
   for (int q = 0; q < 8; q++) {
     int e[3];
     slot_extents(g, q, e);
@@ -864,6 +859,7 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c.stream));
-  CK(cudaMemcpy(&h, c.sc, sizeof(h), cudaMemcpyDeviceToHost));
+  DevScalars h;
+  CK(copy_sync(&h, c.sc, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
   return h.status ? h.status : MHD_OK;
 }

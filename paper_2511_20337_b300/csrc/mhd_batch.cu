@@ -43,6 +43,9 @@ struct mhd_batch {
   int launches_per_step = 0;
   cudaGraphExec_t graph{};
   bool graph_ready = false;
+  // the ghost shell of U^n matches its interior (set by a read-out's ghost
+  // fill, cleared by anything that changes U^n)
+  bool u0_ghosts_fresh = false;
   // profiling: an event after every launch, tagged with its kernel class
   bool prof_on = false;
   int prof_n = 0;
@@ -193,6 +196,7 @@ void batch_stage(mhd_batch* b, int s) {
 }
 
 void batch_run_step(mhd_batch* b) {
+  b->u0_ghosts_fresh = false;
   for (int s = 0; s < b->cfg0.rk; s++) batch_stage(b, s);
 }
 
@@ -321,11 +325,9 @@ int mhd_batch_set_conserved(mhd_batch* b, int run, int mem, const double* const*
     int rc = copy_field(R.g, b->stream, R.U[0].q[q], q < 5 ? U[q] : B[q - 5], nullptr, e, true);
     if (rc) return rc;
   }
-  DevScalars h;
-  reset_scalars_host(&h);
-  CK(cudaMemcpyAsync(R.sc, &h, sizeof(h), cudaMemcpyHostToDevice, b->stream));
-  CK(cudaStreamSynchronize(b->stream));  // h lives on this frame
+  CK(cudaMemcpyAsync(R.sc, reset_scalars_source(), sizeof(DevScalars), cudaMemcpyHostToDevice, b->stream));
   b->has_state[run] = 1;
+  b->u0_ghosts_fresh = false;
   return MHD_OK;
 }
 
@@ -333,7 +335,10 @@ int mhd_batch_get_conserved(mhd_batch* b, int run, int mem, double* const* U, do
   if (!b || run < 0 || run >= b->nruns || !U || !B || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE))
     return MHD_ERR_ARG;
   if (!b->has_state[run]) return MHD_ERR_STATE;
-  batch_ghost_u0(b);
+  if (!b->u0_ghosts_fresh) {  // once per state: the read-outs of all runs share it
+    batch_ghost_u0(b);
+    b->u0_ghosts_fresh = true;
+  }
   const RunDev& R = b->runs[run];
   for (int q = 0; q < 8; q++) {
     double* dst = q < 5 ? U[q] : B[q - 5];
@@ -369,6 +374,7 @@ int mhd_batch_step(mhd_batch* b, int nsteps) {
   }
   for (int s = 0; s < nsteps; s++) {
     CK(cudaGraphLaunch(b->graph, b->stream));
+    b->u0_ghosts_fresh = false;
     b->launches += b->launches_per_step;
   }
   return MHD_OK;
@@ -458,7 +464,7 @@ int mhd_batch_get_times(mhd_batch* b, double* t_out) {
   if (!b || !t_out) return MHD_ERR_ARG;
   CK(cudaStreamSynchronize(b->stream));
   std::vector<DevScalars> h(b->nruns);
-  CK(cudaMemcpy(h.data(), b->sc, sizeof(DevScalars) * b->nruns, cudaMemcpyDeviceToHost));
+  CK(copy_sync(h.data(), b->sc, sizeof(DevScalars) * b->nruns, cudaMemcpyDeviceToHost, b->stream));
   for (int r = 0; r < b->nruns; r++) t_out[r] = h[r].time;
   return MHD_OK;
 }
@@ -467,7 +473,7 @@ int mhd_batch_status(mhd_batch* b, int* bad_run, long long* bad_cell) {
   if (!b) return MHD_ERR_ARG;
   CK(cudaStreamSynchronize(b->stream));
   std::vector<DevScalars> h(b->nruns);
-  CK(cudaMemcpy(h.data(), b->sc, sizeof(DevScalars) * b->nruns, cudaMemcpyDeviceToHost));
+  CK(copy_sync(h.data(), b->sc, sizeof(DevScalars) * b->nruns, cudaMemcpyDeviceToHost, b->stream));
   if (bad_run) *bad_run = -1;
   if (bad_cell) *bad_cell = -1;
   for (int r = 0; r < b->nruns; r++)

@@ -148,10 +148,20 @@ static __global__ void __launch_bounds__(128) glm_sweep_kernel(Grid g, F9 P, F9 
 #pragma unroll
     for (int v = 0; v < 9; v++) win[v][m] = pr[v][c];
   }
+  // PLM: the left difference of the window's centre cell, carried along the pencil
+  double dl[9];
+  if (RECON == RECON_PLM) {
+#pragma unroll
+    for (int v = 0; v < 9; v++) dl[v] = win[v][1] - win[v][0];
+  }
   auto reconstruct = [&](double plus[9], double minus[9], bool count) {
 #pragma unroll
     for (int v = 0; v < 9; v++) {
-      if (RECON == RECON_PLM) recon_plm(win[v][0], win[v][1], win[v][2], plus[v], minus[v]);
+      if (RECON == RECON_PLM) {
+        const double dr = win[v][2] - win[v][1];
+        recon_plm_d(win[v][1], dl[v], dr, plus[v], minus[v]);
+        dl[v] = dr;
+      }
       else if (RECON == RECON_WENOZ) recon_wenoz(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
       else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
     }

@@ -83,6 +83,24 @@ inline void reset_scalars_host(DevScalars* h) {
   memset(h, 0, sizeof(*h));
   h->bad_cell = LLONG_MAX;
 }
+// A small host<->device copy in a stream's order, waited for.  Unlike
+// cudaMemcpy it does not go through the legacy default stream, so it never
+// waits for the work of other contexts.
+inline cudaError_t copy_sync(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, s);
+  return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+}
+
+// The reset values in host memory that lives as long as the library, so that
+// a context can copy them to the device without waiting for the copy.
+inline const DevScalars* reset_scalars_source() {
+  static const DevScalars h = [] {
+    DevScalars s;
+    reset_scalars_host(&s);
+    return s;
+  }();
+  return &h;
+}
 
 // cudaMemcpy3D between the caller's dense array (extents e[3]) and the
 // interior of a padded device field.

@@ -450,11 +450,35 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
 #pragma unroll
     for (int v = 0; v < 7; v++) win[v][m] = v7[v];
   }
+  // PLM: the left difference of the window's centre cell, carried along the pencil
+  double dl[7];
+  if (RECON == RECON_PLM) {
+#pragma unroll
+    for (int v = 0; v < 7; v++) dl[v] = win[v][1] - win[v][0];
+  }
+  // WENO-Z: the curvatures of the stencils centred on the window's cells 1 and 2
+  Curv cv[7][2];
+  if (RECON == RECON_WENOZ) {
+#pragma unroll
+    for (int v = 0; v < 7; v++) {
+      cv[v][0] = curv(win[v][0], win[v][1], win[v][2]);
+      cv[v][1] = curv(win[v][1], win[v][2], win[v][3]);
+    }
+  }
   auto reconstruct = [&](double plus[7], double minus[7], bool count) {
 #pragma unroll
     for (int v = 0; v < 7; v++) {
-      if (RECON == RECON_PLM) recon_plm(win[v][0], win[v][1], win[v][2], plus[v], minus[v]);
-      else if (RECON == RECON_WENOZ) recon_wenoz(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
+      if (RECON == RECON_PLM) {
+        const double dr = win[v][2] - win[v][1];
+        recon_plm_d(win[v][1], dl[v], dr, plus[v], minus[v]);
+        dl[v] = dr;
+      }
+      else if (RECON == RECON_WENOZ) {
+        Curv c2;
+        recon_wenoz_c(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], cv[v][0], cv[v][1], c2, plus[v], minus[v]);
+        cv[v][0] = cv[v][1];
+        cv[v][1] = c2;
+      }
       else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
     }
     // positivity fallback: first order in this cell
@@ -570,11 +594,35 @@ __device__ __forceinline__ void sweep_item_direct(const Grid& g, const F8& P, co
 #pragma unroll
     for (int v = 0; v < 7; v++) win[v][m] = pr[v][c];
   }
+  // PLM: the left difference of the window's centre cell, carried along the pencil
+  double dl[7];
+  if (RECON == RECON_PLM) {
+#pragma unroll
+    for (int v = 0; v < 7; v++) dl[v] = win[v][1] - win[v][0];
+  }
+  // WENO-Z: the curvatures of the stencils centred on the window's cells 1 and 2
+  Curv cv[7][2];
+  if (RECON == RECON_WENOZ) {
+#pragma unroll
+    for (int v = 0; v < 7; v++) {
+      cv[v][0] = curv(win[v][0], win[v][1], win[v][2]);
+      cv[v][1] = curv(win[v][1], win[v][2], win[v][3]);
+    }
+  }
   auto reconstruct = [&](double plus[7], double minus[7], bool count) {
 #pragma unroll
     for (int v = 0; v < 7; v++) {
-      if (RECON == RECON_PLM) recon_plm(win[v][0], win[v][1], win[v][2], plus[v], minus[v]);
-      else if (RECON == RECON_WENOZ) recon_wenoz(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
+      if (RECON == RECON_PLM) {
+        const double dr = win[v][2] - win[v][1];
+        recon_plm_d(win[v][1], dl[v], dr, plus[v], minus[v]);
+        dl[v] = dr;
+      }
+      else if (RECON == RECON_WENOZ) {
+        Curv c2;
+        recon_wenoz_c(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], cv[v][0], cv[v][1], c2, plus[v], minus[v]);
+        cv[v][0] = cv[v][1];
+        cv[v][1] = c2;
+      }
       else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
     }
     // positivity fallback: first order in this cell

@@ -176,22 +176,36 @@ using Flux7 = Flux7T<double>;
 // along the normal (F of b_n is zero), pT = p + B^2/2, plus the fast speed.
 template <class T> struct SideT {
   T U[7], F[7];
-  T pT, B2, vB, cf;
+  T pT, B2, vB, cf, n;  // cf: fast speed (reverse mode), n: its numerator (forward solvers)
 };
 using Side = SideT<double>;
 
-// Fast magnetosonic speed cf^2 = [(G p + B^2) + sqrt((G p + B^2)^2 - 4 G p bn^2)] / (2 rho).
+// Fast magnetosonic speed cf^2 = n / (2 rho) with the numerator
+// n = (G p + B^2) + sqrt((G p + B^2)^2 - 4 G p bn^2).
 template <class T>
-__device__ __forceinline__ T fast_speed(T rho, T p, T B2, T bn2, double gamma) {
+__device__ __forceinline__ T fast_speed_num(T p, T B2, T bn2, double gamma) {
   T gp = mul_rn(T(gamma), p);
   T s = gp + B2;
   T disc = fma(s, s, -(4.0 * gp) * bn2);
   if (lt0(disc)) disc = T(0.0);
-  T cf2 = (s + fsqrt0(disc)) * (0.5 * rcp(rho));
-  return fsqrt(cf2);
+  return s + fsqrt0(disc);
+}
+template <class T>
+__device__ __forceinline__ T fast_speed(T rho, T p, T B2, T bn2, double gamma) {
+  return fsqrt(fast_speed_num(p, B2, bn2, gamma) * (0.5 * rcp(rho)));
+}
+// max(cf_L, cf_R), the only use of the two fast speeds in the solvers' outer
+// wave speeds, with one reciprocal and one square root: the side with the
+// larger n / rho is found by comparing n_L rho_R with n_R rho_L; the result is
+// that side's fast_speed (a near-tie may pick the other side, ~1 ulp away).
+template <class T>
+__device__ __forceinline__ T fast_speed_max(T nL, T rhoL, T nR, T rhoR) {
+  const bool right = lt_pos(nL * rhoR, nR * rhoL);
+  return fsqrt((right ? nR : nL) * (0.5 * rcp(right ? rhoR : rhoL)));
 }
 
-template <class T>
+// With CF the side's fast speed goes to s.cf, else its numerator to s.n.
+template <class T, bool CF = true>
 __device__ __forceinline__ void side_state(const W7T<T>& W, T bn, T bn2, double gamma, double igm1, SideT<T>& s) {
   s.B2 = fma(W.b1, W.b1, fma(W.b2, W.b2, bn2));
   s.pT = fma(0.5, s.B2, W.p);
@@ -213,7 +227,8 @@ __device__ __forceinline__ void side_state(const W7T<T>& W, T bn, T bn2, double 
   s.F[4] = fma(W.u, W.b1, -W.v * bn);
   s.F[5] = fma(W.u, W.b2, -W.w * bn);
   s.F[6] = fma(E + s.pT, W.u, -bn * s.vB);
-  s.cf = fast_speed(W.rho, W.p, s.B2, bn2, gamma);
+  if (CF) s.cf = fast_speed(W.rho, W.p, s.B2, bn2, gamma);
+  else s.n = fast_speed_num(W.p, s.B2, bn2, gamma);
 }
 
 // Outer speed estimate S_L, S_R (Miyoshi & Kusano 2005) and the UCT-HLL
@@ -223,9 +238,7 @@ template <class T> struct IngrT {
 };
 using Ingr = IngrT<double>;
 template <class T>
-__device__ __forceinline__ void speeds(const W7T<T>& L, const W7T<T>& R, const SideT<T>& sl, const SideT<T>& sr, T& SL,
-                                       T& SR, IngrT<T>& ing) {
-  T cmax = imax_pos(sl.cf, sr.cf);
+__device__ __forceinline__ void speeds(const W7T<T>& L, const W7T<T>& R, T cmax, T& SL, T& SR, IngrT<T>& ing) {
   SL = imin(L.u, R.u) - cmax;
   SR = imax(L.u, R.u) + cmax;
   T aR = gt0(SR) ? SR : T(0.0), aL = lt0(SL) ? SL : T(0.0);
@@ -242,10 +255,10 @@ __device__ __forceinline__ void riemann_hll(const W7T<T>& L, const W7T<T>& R, T 
                                             Flux7T<T>& F, IngrT<T>& ing) {
   const T bn2 = bn * bn;
   SideT<T> sl, sr;
-  side_state(L, bn, bn2, gamma, igm1, sl);
-  side_state(R, bn, bn2, gamma, igm1, sr);
+  side_state<T, false>(L, bn, bn2, gamma, igm1, sl);
+  side_state<T, false>(R, bn, bn2, gamma, igm1, sr);
   T SL, SR;
-  speeds(L, R, sl, sr, SL, SR, ing);
+  speeds(L, R, fast_speed_max(sl.n, L.rho, sr.n, R.rho), SL, SR, ing);
   if (ge0(SL)) {
 #pragma unroll
     for (int q = 0; q < 7; q++) F.f[q] = sl.F[q];
@@ -271,9 +284,20 @@ __device__ __forceinline__ void side_lite(const W7T<T>& W, T bn2, double gamma, 
   s.pT = fma(0.5, s.B2, W.p);
   s.cf = fast_speed(W.rho, W.p, s.B2, bn2, gamma);
 }
-// Conserved state, energy, v.B and flux of one side, given its total field and pressure.
+// The same with the fast-speed numerator (see fast_speed_max), for the forward solver.
+template <class T> struct SideNumT {
+  T B2, pT, n;
+};
 template <class T>
-__device__ __forceinline__ void side_full(const W7T<T>& W, T bn, T bn2, double igm1, const SideLiteT<T>& l, T U[7],
+__device__ __forceinline__ void side_num(const W7T<T>& W, T bn2, double gamma, SideNumT<T>& s) {
+  s.B2 = fma(W.b1, W.b1, fma(W.b2, W.b2, bn2));
+  s.pT = fma(0.5, s.B2, W.p);
+  s.n = fast_speed_num(W.p, s.B2, bn2, gamma);
+}
+// Conserved state, energy, v.B and flux of one side, given its total field and
+// pressure (l: any side record with B2 and pT).
+template <class T, class SideInfo>
+__device__ __forceinline__ void side_full(const W7T<T>& W, T bn, T bn2, double igm1, const SideInfo& l, T U[7],
                                           T F[7], T& vB) {
   vB = fma(W.u, bn, fma(W.v, W.b1, W.w * W.b2));
   T v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
@@ -304,11 +328,11 @@ template <class T>
 __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T bn, double gamma, double igm1,
                                              Flux7T<T>& F, IngrT<T>& ing) {
   const T bn2 = bn * bn;
-  SideLiteT<T> ll, lr;
-  side_lite(L, bn2, gamma, ll);
-  side_lite(R, bn2, gamma, lr);
+  SideNumT<T> ll, lr;
+  side_num(L, bn2, gamma, ll);
+  side_num(R, bn2, gamma, lr);
   // outer speeds and UCT ingredients
-  T cmax = imax_pos(ll.cf, lr.cf);
+  T cmax = fast_speed_max(ll.n, L.rho, lr.n, R.rho);
   T SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
   {
     T aR = gt0(SR) ? SR : T(0.0), aL = lt0(SL) ? SL : T(0.0);
@@ -379,7 +403,7 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
 #pragma unroll
   for (int q = 0; q < 7; q++) F.f[q] = fma(S, Us[q] - Ua[q], F.f[q]);
   // rotational (Alfven) waves, absent when the normal field vanishes
-  if (!lt_pos(0.5 * bn2, kHlldBnEps * pTs)) {
+  if (!lt_pos(bn2, (2.0 * kHlldBnEps) * pTs)) {  // 0.5 bn2 >= eps pTs, scaled by 2 exactly
     T iqL = frsqrt(rhosL), iqR = frsqrt(rhosR);  // 1/sqrt(rho*)
     T sqL = rhosL * iqL, sqR = rhosR * iqR;      // sqrt(rho*)
     T abn = fabs(bn);
@@ -417,10 +441,15 @@ __device__ __forceinline__ double minmod(double a, double b) {
   return (ib & kMag) < (ia & kMag) ? b : a;
 }
 
-__device__ __forceinline__ void recon_plm(double s1, double s2, double s3, double& plus, double& minus) {
-  double d = minmod(s2 - s1, s3 - s2);
+// PLM from the two one-sided differences of cell value s2 (a marching sweep
+// carries the right difference of a cell over as the left one of the next).
+__device__ __forceinline__ void recon_plm_d(double s2, double dl, double dr, double& plus, double& minus) {
+  double d = minmod(dl, dr);
   plus = fma(0.5, d, s2);
   minus = fma(-0.5, d, s2);
+}
+__device__ __forceinline__ void recon_plm(double s1, double s2, double s3, double& plus, double& minus) {
+  recon_plm_d(s2, s2 - s1, s3 - s2, plus, minus);
 }
 
 // WENO-Z (Borges et al. 2008) values at both faces of the middle cell of
@@ -430,16 +459,29 @@ __device__ __forceinline__ void recon_plm(double s1, double s2, double s3, doubl
 // indicators with beta_0 and beta_2 exchanged, so the ratios
 // r_k = tau5 / (beta_k + eps) are formed once for both faces; the factor 1/6
 // of the candidate values is folded into the normalisation.
-__device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, double a3, double a4, double& plus,
-                                            double& minus) {
-  double t = fma(-2.0, a1, a0) + a2, u = fma(3.0, a2, fma(-4.0, a1, a0));
-  double b0 = fma(13.0 / 12.0 * t, t, (0.25 * u) * u);
-  t = fma(-2.0, a2, a1) + a3;
+//
+// beta_k's curvature term (13/12) (a_{j-1} - 2 a_j + a_{j+1})^2 belongs to the
+// three-cell stencil centred at j = i-1, i, i+1; a sweep marching along a
+// pencil passes those of i-1 and i in (c0, c1) and gets that of i+1 back in c2
+// for the next cell (the same operations on the same values as forming them here).
+struct Curv {
+  double t, k;  // a_{j-1} - 2 a_j + a_{j+1} and 13/12 of it
+};
+__device__ __forceinline__ Curv curv(double l, double m, double r) {
+  Curv c;
+  c.t = fma(-2.0, m, l) + r;
+  c.k = 13.0 / 12.0 * c.t;
+  return c;
+}
+__device__ __forceinline__ void recon_wenoz_c(double a0, double a1, double a2, double a3, double a4, const Curv& c0,
+                                              const Curv& c1, Curv& c2, double& plus, double& minus) {
+  double u = fma(3.0, a2, fma(-4.0, a1, a0));
+  double b0 = fma(c0.k, c0.t, (0.25 * u) * u);
   u = a1 - a3;
-  double b1 = fma(13.0 / 12.0 * t, t, (0.25 * u) * u);
-  t = fma(-2.0, a3, a2) + a4;
+  double b1 = fma(c1.k, c1.t, (0.25 * u) * u);
+  c2 = curv(a2, a3, a4);
   u = fma(3.0, a2, fma(-4.0, a3, a4));
-  double b2 = fma(13.0 / 12.0 * t, t, (0.25 * u) * u);
+  double b2 = fma(c2.k, c2.t, (0.25 * u) * u);
   double tau = fabs(b0 - b2);
   double r0 = tau * rcp(b0 + kWenozEps), r1 = tau * rcp(b1 + kWenozEps), r2 = tau * rcp(b2 + kWenozEps);
   double g0 = fma(r0, r0, 1.0), g1 = fma(r1, r1, 1.0), g2 = fma(r2, r2, 1.0);
@@ -459,6 +501,11 @@ __device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, dou
     double al0 = __dmul_rn(0.1, g2), al1 = __dmul_rn(0.6, g1), al2 = __dmul_rn(0.3, g0);
     minus = fma(al0, q0, fma(al1, q1, al2 * q2)) * rcp(6.0 * ((al0 + al1) + al2));
   }
+}
+__device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, double a3, double a4, double& plus,
+                                            double& minus) {
+  Curv c2;
+  recon_wenoz_c(a0, a1, a2, a3, a4, curv(a0, a1, a2), curv(a1, a2, a3), c2, plus, minus);
 }
 
 __device__ __forceinline__ double ppm_face(double a, double b, double c, double d) {
