@@ -154,6 +154,17 @@ static __global__ void __launch_bounds__(128) glm_sweep_kernel(Grid g, F9 P, F9 
 #pragma unroll
     for (int v = 0; v < 9; v++) dl[v] = win[v][1] - win[v][0];
   }
+  // WENO-Z: the curvatures of the stencils centred on the window's cells 1 and
+  // 2 (their 13/12 multiples are formed again: nine variables' worth would not
+  // fit in registers)
+  double cv[9][2];
+  if (RECON == RECON_WENOZ) {
+#pragma unroll
+    for (int v = 0; v < 9; v++) {
+      cv[v][0] = curv(win[v][0], win[v][1], win[v][2]).t;
+      cv[v][1] = curv(win[v][1], win[v][2], win[v][3]).t;
+    }
+  }
   auto reconstruct = [&](double plus[9], double minus[9], bool count) {
 #pragma unroll
     for (int v = 0; v < 9; v++) {
@@ -162,7 +173,13 @@ static __global__ void __launch_bounds__(128) glm_sweep_kernel(Grid g, F9 P, F9 
         recon_plm_d(win[v][1], dl[v], dr, plus[v], minus[v]);
         dl[v] = dr;
       }
-      else if (RECON == RECON_WENOZ) recon_wenoz(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
+      else if (RECON == RECON_WENOZ) {
+        Curv c2;
+        recon_wenoz_c(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], curv_of(cv[v][0]), curv_of(cv[v][1]), c2,
+                      plus[v], minus[v]);
+        cv[v][0] = cv[v][1];
+        cv[v][1] = c2.t;
+      }
       else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
     }
     if (!gt0(plus[0]) || !gt0(minus[0]) || !gt0(plus[7]) || !gt0(minus[7])) {

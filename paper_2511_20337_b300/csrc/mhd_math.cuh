@@ -467,12 +467,13 @@ __device__ __forceinline__ void recon_plm(double s1, double s2, double s3, doubl
 struct Curv {
   double t, k;  // a_{j-1} - 2 a_j + a_{j+1} and 13/12 of it
 };
-__device__ __forceinline__ Curv curv(double l, double m, double r) {
+__device__ __forceinline__ Curv curv_of(double t) {
   Curv c;
-  c.t = fma(-2.0, m, l) + r;
-  c.k = 13.0 / 12.0 * c.t;
+  c.t = t;
+  c.k = 13.0 / 12.0 * t;
   return c;
 }
+__device__ __forceinline__ Curv curv(double l, double m, double r) { return curv_of(fma(-2.0, m, l) + r); }
 __device__ __forceinline__ void recon_wenoz_c(double a0, double a1, double a2, double a3, double a4, const Curv& c0,
                                               const Curv& c1, Curv& c2, double& plus, double& minus) {
   double u = fma(3.0, a2, fma(-4.0, a1, a0));
