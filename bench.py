@@ -224,20 +224,24 @@ def sweep_source_hash():
     return hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
 
 
-def sweep_traffic(variant, faces_per_launch):
+def sweep_traffic(cfg, faces_per_launch):
     """DRAM bytes per sweep launch from the committed ncu captures
-    (profiles/sweep_traffic.json), scaled by faces per launch; None when the
-    sweep kernels' sources changed since the capture or no capture exists."""
+    (profiles/sweep_traffic.json) of the same sweep kernel (dimension,
+    reconstruction, Riemann solver, divergence control), scaled by faces per
+    launch; None when the sweep kernels' sources changed since the capture or
+    no capture of that kernel exists."""
     path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    h = sweep_source_hash()
-    if rec.get("source_hash") != h or variant not in rec:
+    if rec.get("source_hash") != sweep_source_hash():
         return None
-    v = rec[variant]
-    per = sum(v["bytes_per_launch"]) / len(v["bytes_per_launch"])
-    return per * faces_per_launch / v["faces_per_launch"]
+    scheme = {"ndim": cfg["ndim"], "recon": cfg["recon"], "riemann": cfg["riemann"], "divb": cfg.get("divb", "ct")}
+    for v in rec.values():
+        if isinstance(v, dict) and v.get("scheme") == scheme:
+            per = sum(v["bytes_per_launch"]) / len(v["bytes_per_launch"])
+            return per * faces_per_launch / v["faces_per_launch"]
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -439,7 +443,7 @@ def run_ours(args):
                 "peak_source": "measured in this run: FP64 DFMA probe (mhd_probe_fp64), 2 flops per DFMA",
                 "algorithmic_flops_per_launch": sweep_flops / sweep_launches,
                 "avg_launch_ms": sweep_ms / sweep_launches,
-                "traffic": sweep_traffic(variant, faces_per_launch),
+                "traffic": sweep_traffic(cfg, faces_per_launch),
                 "traffic_note": "DRAM bytes per sweep launch (mean of the directions) from the ncu capture in "
                                 "profiles/, scaled to this grid by faces; null if the kernels changed since",
                 "step_achieved": step_achieved, "step_frac": step_achieved / peak,
