@@ -396,7 +396,7 @@ def run_ours(args):
         sim.set_seglen(args.seglen)
         seg = args.seglen
     else:
-        seg = sim.autotune() if ncell <= 256 ** 3 else None  # larger grids keep the default 16
+        seg = sim.autotune() if ncell <= 256 ** 3 else None  # larger grids keep the library's default
     # warm-up (also captures the step graph)
     sim.advance(args.warmup)
     torch.cuda.synchronize(dev)
@@ -501,7 +501,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": desc, "grid": list(cfg["n"]), "cells": ncell,
-                           "seglen": seg if seg is not None else 16,
+                           "seglen": sim.seglen,
                            "l2": (f"inputs larger than L2 (state {h2d / 1e9:.2f} GB)" if h2d > 126e6 else
                                   f"state {h2d / 1e6:.1f} MB fits in L2 and is not flushed between steps "
                                   "(a parity-size workload, not the headline)"),

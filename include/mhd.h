@@ -158,13 +158,21 @@ int mhd_counters(mhd_ctx* ctx, long long* recon_fallbacks, long long* pressure_f
 long long mhd_launch_count(const mhd_ctx* ctx);
 
 /* Sweep segment length: the number of faces one thread of a sweep marches
- * (default 16).  Shorter segments give more threads, longer ones fewer
- * repeated Riemann solves at segment ends (one per segment); the result does
- * not depend on it.  >= 1.  Sync. */
+ * (default: the longest of 2..64 that leaves about eight waves of threads
+ * on the device in the sweep with the fewest faces).  Shorter segments give
+ * more threads, longer ones fewer repeated Riemann solves and reconstructions
+ * at segment ends (one each per segment); the result does not depend on it.
+ * >= 1.  Sync. */
 int mhd_set_seglen(mhd_ctx* ctx, int seglen);
 
-/* Choose the segment length by timing two CFL steps for each of 2, 4, ..., 64
- * (up to twice the longest axis) on the current state, which is restored
+/* The segment length in use (the default, the last mhd_set_seglen or the
+ * mhd_autotune choice). */
+int mhd_get_seglen(const mhd_ctx* ctx, int* seglen_out);
+
+/* Choose the segment length by timing two CFL steps for each of 2, 4, 8, 12,
+ * 16, 20, 24, 28, 32, 40, 48, 64 and the lengths that split the longest
+ * pencil's faces into 4..12 equal segments (up to twice the longest axis) on
+ * the current state, which is restored
  * afterwards together with the time and counters; *seglen_out (may be NULL)
  * receives the choice.  Sync; allocates a temporary copy of the state. */
 int mhd_autotune(mhd_ctx* ctx, int* seglen_out);

@@ -1,5 +1,6 @@
 // C-ABI of libmhd (declared in include/mhd.h): context management, state
 // import/export and the orchestration of the RK stages of one time step.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -255,6 +256,25 @@ void run_step(mhd_ctx* c, bool device_dt) {
 
 }  // namespace mhd
 
+// Default sweep segment length: each segment repeats one face and one
+// reconstruction at its end, so long segments waste less, while short ones
+// give more threads.  Take the longest (2..64) that still leaves about eight
+// waves of 384-thread SM loads in the sweep with the fewest faces.
+static int default_seglen(const Grid& g) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 148;
+  long long fewest = LLONG_MAX;
+  for (int d = 0; d < g.ndim; d++) {
+    long long faces = g.n[d] + 1;
+    for (int t = 0; t < g.ndim; t++)
+      if (t != d) faces *= g.n[t] + 2;
+    fewest = faces < fewest ? faces : fewest;
+  }
+  const long long per_thread = fewest / (8LL * sms * 384);
+  return (int)(per_thread < 2 ? 2 : (per_thread > 64 ? 64 : per_thread));
+}
+
 extern "C" {
 
 const char* mhd_strerror(int code) {
@@ -283,7 +303,7 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
   if (!c) return MHD_ERR_OOM;
   c->cfg = *cfg;
   c->g = g;
-  c->seglen = 16;
+  c->seglen = default_seglen(g);
   c->field_elems = (size_t)((elems + 31) / 32 * 32);
   if (cfg->stream) {
     c->stream = (cudaStream_t)cfg->stream;
@@ -582,6 +602,12 @@ int mhd_set_seglen(mhd_ctx* c, int seglen) {
   return MHD_OK;
 }
 
+int mhd_get_seglen(const mhd_ctx* c, int* seglen_out) {
+  if (!c || !seglen_out) return MHD_ERR_ARG;
+  *seglen_out = c->seglen;
+  return MHD_OK;
+}
+
 int mhd_autotune(mhd_ctx* c, int* seglen_out) {
   if (!c) return MHD_ERR_ARG;
   if (!c->has_state) return MHD_ERR_STATE;
@@ -592,15 +618,22 @@ int mhd_autotune(mhd_ctx* c, int* seglen_out) {
   double* backup = nullptr;
   CK(cudaMalloc(&backup, bytes));
   CK(cudaMemcpyAsync(backup, c->U[0].q[0], bytes, cudaMemcpyDeviceToDevice, c->stream));
-  const int cand[6] = {2, 4, 8, 16, 32, 64};
-  int longest = 0;
+  int longest = 0;  // faces per pencil along the longest axis
   for (int d = 0; d < c->g.ndim; d++) longest = c->g.n[d] + 1 > longest ? c->g.n[d] + 1 : longest;
+  // powers of two and lengths between them, plus the lengths that split the
+  // longest pencil into 4..12 equal segments: the segment count sets how many
+  // waves of blocks a sweep takes and how short its last segment is
+  int cand[32], ncand = 0;
+  for (int s : {2, 4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 64}) cand[ncand++] = s;
+  for (int k = 4; k <= 12; k++) cand[ncand++] = (longest + k - 1) / k;
+  std::sort(cand, cand + ncand);
+  ncand = (int)(std::unique(cand, cand + ncand) - cand);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
   int pick = c->seglen, rc = MHD_OK;
-  for (int i = 0; i < 6 && rc == MHD_OK; i++) {
+  for (int i = 0; i < ncand && rc == MHD_OK; i++) {
     if (cand[i] > 2 * longest) break;
     c->seglen = cand[i];
     run_step(c, true);  // warm

@@ -36,7 +36,7 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
-           "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate")
+           "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -109,6 +109,7 @@ def lib():
             "mhd_set_psi": (I, [P, I, P]),
             "mhd_get_psi": (I, [P, I, P]),
             "mhd_probe_cfl_rate": (I, [I, D, P, I, P, P, P]),
+            "mhd_get_seglen": (I, [P, ctypes.POINTER(I)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -283,6 +284,12 @@ class Sim:
 
     def set_seglen(self, seglen):
         _check(lib().mhd_set_seglen(self.h, int(seglen)), "mhd_set_seglen")
+
+    @property
+    def seglen(self):
+        s = ctypes.c_int()
+        _check(lib().mhd_get_seglen(self.h, ctypes.byref(s)), "mhd_get_seglen")
+        return s.value
 
     def autotune(self):
         """Pick the sweep segment length by timing (state restored); returns it."""
