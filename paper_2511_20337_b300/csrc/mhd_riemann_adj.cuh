@@ -31,17 +31,17 @@ __device__ __forceinline__ void fast_speed_vjp(double rho, double p, double B2, 
   // reverse
   const double cf2b = cfb * (0.5 * rcp(cf));
   const double tb = cf2b * h;
-  rhob += (0.5 * (cf2b * t)) * (-(irho * irho));
+  rhob = fma((0.5 * (cf2b * t)), (-(irho * irho)), rhob);
   double sb = tb, gpb = 0.0;
   if (gt0(disc)) {
     const double discb = tb * (0.5 * rcp(sq));
-    sb += discb * (2.0 * s);
-    gpb += discb * (-4.0 * bn2);
-    bn2b += discb * (-4.0 * gp);
+    sb = fma(discb, (2.0 * s), sb);
+    gpb = fma(discb, (-4.0 * bn2), gpb);
+    bn2b = fma(discb, (-4.0 * gp), bn2b);
   }
   gpb += sb;
   B2b += sb;
-  pb += gamma * gpb;
+  pb = fma(gamma, gpb, pb);
 }
 
 // Total field, total pressure and fast speed of one side (side_lite):
@@ -50,9 +50,9 @@ __device__ __forceinline__ void side_lite_vjp(const W7& W, double bn2, double ga
                                               double cfb, W7b& Wb, double& bn2b) {
   fast_speed_vjp(W.rho, W.p, B2, bn2, gamma, cfb, Wb.rho, Wb.p, B2b, bn2b);
   Wb.p += pTb;
-  B2b += 0.5 * pTb;
-  Wb.b1 += (2.0 * W.b1) * B2b;
-  Wb.b2 += (2.0 * W.b2) * B2b;
+  B2b = fma(0.5, pTb, B2b);
+  Wb.b1 = fma((2.0 * W.b1), B2b, Wb.b1);
+  Wb.b2 = fma((2.0 * W.b2), B2b, Wb.b2);
   bn2b += B2b;
 }
 
@@ -68,54 +68,54 @@ __device__ __forceinline__ void side_full_vjp(const W7& W, double bn, double igm
   double mub = Fb[0] + Ub[1];
   double Eb = Ub[6];
   // F1 = mu u + pT - bn2
-  mub += Fb[1] * W.u;
-  Wb.u += Fb[1] * mu;
+  mub = fma(Fb[1], W.u, mub);
+  Wb.u = fma(Fb[1], mu, Wb.u);
   pTb += Fb[1];
   bn2b -= Fb[1];
   // F2 = mu v - bn b1, F3 = mu w - bn b2
-  mub += Fb[2] * W.v + Fb[3] * W.w;
-  Wb.v += Fb[2] * mu;
-  Wb.w += Fb[3] * mu;
-  bnb -= Fb[2] * W.b1 + Fb[3] * W.b2;
-  Wb.b1 -= Fb[2] * bn;
-  Wb.b2 -= Fb[3] * bn;
+  mub = fma(Fb[2], W.v, fma(Fb[3], W.w, mub));
+  Wb.v = fma(Fb[2], mu, Wb.v);
+  Wb.w = fma(Fb[3], mu, Wb.w);
+  bnb = fma(-Fb[2], W.b1, fma(-Fb[3], W.b2, bnb));
+  Wb.b1 = fma(-Fb[2], bn, Wb.b1);
+  Wb.b2 = fma(-Fb[3], bn, Wb.b2);
   // F4 = u b1 - v bn, F5 = u b2 - w bn
-  Wb.u += Fb[4] * W.b1 + Fb[5] * W.b2;
-  Wb.b1 += Fb[4] * W.u;
-  Wb.b2 += Fb[5] * W.u;
-  Wb.v -= Fb[4] * bn;
-  Wb.w -= Fb[5] * bn;
-  bnb -= Fb[4] * W.v + Fb[5] * W.w;
+  Wb.u = fma(Fb[4], W.b1, fma(Fb[5], W.b2, Wb.u));
+  Wb.b1 = fma(Fb[4], W.u, Wb.b1);
+  Wb.b2 = fma(Fb[5], W.u, Wb.b2);
+  Wb.v = fma(-Fb[4], bn, Wb.v);
+  Wb.w = fma(-Fb[5], bn, Wb.w);
+  bnb = fma(-Fb[4], W.v, fma(-Fb[5], W.w, bnb));
   // F6 = (E + pT) u - bn vB
-  Eb += Fb[6] * W.u;
-  pTb += Fb[6] * W.u;
-  Wb.u += Fb[6] * (E + pT);
-  bnb -= Fb[6] * vB;
-  vBb -= Fb[6] * bn;
+  Eb = fma(Fb[6], W.u, Eb);
+  pTb = fma(Fb[6], W.u, pTb);
+  Wb.u = fma(Fb[6], (E + pT), Wb.u);
+  bnb = fma(-Fb[6], vB, bnb);
+  vBb = fma(-Fb[6], bn, vBb);
   // U = (rho, mu, rho v, rho w, b1, b2, E)
-  Wb.rho += Ub[0] + Ub[2] * W.v + Ub[3] * W.w;
-  Wb.v += Ub[2] * W.rho;
-  Wb.w += Ub[3] * W.rho;
+  Wb.rho = fma(Ub[2], W.v, fma(Ub[3], W.w, Wb.rho + Ub[0]));
+  Wb.v = fma(Ub[2], W.rho, Wb.v);
+  Wb.w = fma(Ub[3], W.rho, Wb.w);
   Wb.b1 += Ub[4];
   Wb.b2 += Ub[5];
   // mu = rho u
-  Wb.rho += mub * W.u;
-  Wb.u += mub * W.rho;
+  Wb.rho = fma(mub, W.u, Wb.rho);
+  Wb.u = fma(mub, W.rho, Wb.u);
   // E = p/(G-1) + (rho v2 + B2)/2
-  Wb.p += Eb * igm1;
-  Wb.rho += (0.5 * Eb) * v2;
+  Wb.p = fma(Eb, igm1, Wb.p);
+  Wb.rho = fma((0.5 * Eb), v2, Wb.rho);
   const double v2b = (0.5 * Eb) * W.rho;
-  B2b += 0.5 * Eb;
-  Wb.u += (2.0 * W.u) * v2b;
-  Wb.v += (2.0 * W.v) * v2b;
-  Wb.w += (2.0 * W.w) * v2b;
+  B2b = fma(0.5, Eb, B2b);
+  Wb.u = fma((2.0 * W.u), v2b, Wb.u);
+  Wb.v = fma((2.0 * W.v), v2b, Wb.v);
+  Wb.w = fma((2.0 * W.w), v2b, Wb.w);
   // vB = u bn + v b1 + w b2
-  Wb.u += vBb * bn;
-  bnb += vBb * W.u;
-  Wb.v += vBb * W.b1;
-  Wb.b1 += vBb * W.v;
-  Wb.w += vBb * W.b2;
-  Wb.b2 += vBb * W.w;
+  Wb.u = fma(vBb, bn, Wb.u);
+  bnb = fma(vBb, W.u, bnb);
+  Wb.v = fma(vBb, W.b1, Wb.v);
+  Wb.b1 = fma(vBb, W.v, Wb.b1);
+  Wb.w = fma(vBb, W.b2, Wb.w);
+  Wb.b2 = fma(vBb, W.w, Wb.b2);
 }
 
 // Outer speeds and UCT ingredients (speeds / the head of riemann_hlld):
@@ -132,9 +132,9 @@ __device__ __forceinline__ void speeds_vjp(double uL, double uR, double cfL, dou
   const double aR = gt0(SR) ? SR : 0.0, aL = lt0(SL) ? SL : 0.0;
   const double inv = rcp(aR - aL);
   // ap = aR inv, am = -aL inv, dd = -(aR aL) inv
-  const double invb = Ib[0] * aR - Ib[1] * aL - Ib[2] * (aR * aL);
-  double aRb = (Ib[0] - Ib[2] * aL) * inv;
-  double aLb = (-Ib[1] - Ib[2] * aR) * inv;
+  const double invb = fma(Ib[0], aR, fma(-Ib[1], aL, -Ib[2] * (aR * aL)));
+  double aRb = fma(-Ib[2], aL, Ib[0]) * inv;
+  double aLb = fma(-Ib[2], aR, -Ib[1]) * inv;
   const double denb = invb * (-(inv * inv));
   aRb += denb;
   aLb -= denb;
@@ -182,17 +182,17 @@ __device__ __forceinline__ void riemann_hll_vjp(const W7& L, const W7& R, double
       const double dU = sr.U[q] - sl.U[q];
       const double N = fma(sls, dU, fma(SR, sl.F[q], -SL * sr.F[q]));
       const double Nb = Fb[q] * inv;
-      invb += Fb[q] * N;
-      slsb += Nb * dU;
-      URb[q] += Nb * sls;
-      ULb[q] -= Nb * sls;
-      SRb += Nb * sl.F[q];
-      FLb[q] += Nb * SR;
-      SLb -= Nb * sr.F[q];
-      FRb[q] -= Nb * SL;
+      invb = fma(Fb[q], N, invb);
+      slsb = fma(Nb, dU, slsb);
+      URb[q] = fma(Nb, sls, URb[q]);
+      ULb[q] = fma(-Nb, sls, ULb[q]);
+      SRb = fma(Nb, sl.F[q], SRb);
+      FLb[q] = fma(Nb, SR, FLb[q]);
+      SLb = fma(-Nb, sr.F[q], SLb);
+      FRb[q] = fma(-Nb, SL, FRb[q]);
     }
-    SRb += slsb * SL;
-    SLb += slsb * SR;
+    SRb = fma(slsb, SL, SRb);
+    SLb = fma(slsb, SR, SLb);
     const double db = invb * (-(inv * inv));
     SRb += db;
     SLb -= db;
@@ -206,7 +206,7 @@ __device__ __forceinline__ void riemann_hll_vjp(const W7& L, const W7& R, double
   side_full_vjp(R, bn, igm1, sr.B2, sr.pT, URb, FRb, 0.0, Rb, bnb, bn2b, B2bR, pTbR);
   side_lite_vjp(L, bn2, gamma, sl.B2, B2bL, pTbL, cfLb, Lb, bn2b);
   side_lite_vjp(R, bn2, gamma, sr.B2, B2bR, pTbR, cfRb, Rb, bn2b);
-  bnb += (2.0 * bn) * bn2b;
+  bnb = fma((2.0 * bn), bn2b, bnb);
 }
 
 // ---------------------------------------------------------------------------
@@ -255,35 +255,35 @@ __device__ __forceinline__ void star_side_vjp(const W7& W, double SM, double bn,
     Wb.b1 += b.b1s;
     Wb.b2 += b.b2s;
   } else {
-    Wb.b1 += b.b1s * t.cb - b.vs * t.cv;
-    Wb.b2 += b.b2s * t.cb - b.ws * t.cv;
+    Wb.b1 = fma(b.b1s, t.cb, fma(-b.vs, t.cv, Wb.b1));
+    Wb.b2 = fma(b.b2s, t.cb, fma(-b.ws, t.cv, Wb.b2));
     Wb.v += b.vs;
     Wb.w += b.ws;
-    const double cbb = b.b1s * W.b1 + b.b2s * W.b2;
-    const double cvb = -(b.vs * W.b1 + b.ws * W.b2);
+    const double cbb = fma(b.b1s, W.b1, b.b2s * W.b2);
+    const double cvb = fma(-b.vs, W.b1, -(b.ws * W.b2));
     // cb = (rs sd - bn2) iD
     const double Nbb = cbb * t.iD;
     double iDb = cbb * fma(t.rs, t.sd, -bn2);
-    b.rs += Nbb * t.sd;
-    b.sd += Nbb * t.rs;
+    b.rs = fma(Nbb, t.sd, b.rs);
+    b.sd = fma(Nbb, t.rs, b.sd);
     bn2b -= Nbb;
     // cv = bn (SM - u) iD
     const double du = SM - W.u;
     const double Nvb = cvb * t.iD;
-    iDb += cvb * (bn * du);
-    bnb += Nvb * du;
-    SMb += Nvb * bn;
-    Wb.u -= Nvb * bn;
+    iDb = fma(cvb, (bn * du), iDb);
+    bnb = fma(Nvb, du, bnb);
+    SMb = fma(Nvb, bn, SMb);
+    Wb.u = fma(-Nvb, bn, Wb.u);
     // iD = 1/D, D = rs sm - bn2
     const double Db = iDb * (-(t.iD * t.iD));
     bn2b -= Db;
-    b.rs += Db * t.sm;
-    smb += Db * t.rs;
+    b.rs = fma(Db, t.sm, b.rs);
+    smb = fma(Db, t.rs, smb);
   }
   // rhos = rs ism, ism = 1/sm, sm = S - SM
-  b.rs += b.rhos * t.ism;
-  b.ism += b.rhos * t.rs;
-  smb += b.ism * (-(t.ism * t.ism));
+  b.rs = fma(b.rhos, t.ism, b.rs);
+  b.ism = fma(b.rhos, t.rs, b.ism);
+  smb = fma(b.ism, (-(t.ism * t.ism)), smb);
   Sb += smb;
   SMb -= smb;
 }
@@ -354,47 +354,48 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
         const double dvB = vBs - vBss;
         const double Ess = fma(sqa, times_sign(dvB, bn), Es);
         // F2..F6 += S*_a (U** - U*)
-        double Ssb = Fb[2] * fma(ta.rhos, vss, -Us[2]) + Fb[3] * fma(ta.rhos, wss, -Us[3]) +
-                     Fb[4] * (b1ss - ta.b1s) + Fb[5] * (b2ss - ta.b2s) + Fb[6] * (Ess - Es);
-        ba.rhos += Ss * (Fb[2] * vss + Fb[3] * wss);
+        double Ssb = fma(Fb[2], fma(ta.rhos, vss, -Us[2]),
+                         fma(Fb[3], fma(ta.rhos, wss, -Us[3]),
+                             fma(Fb[4], b1ss - ta.b1s, fma(Fb[5], b2ss - ta.b2s, Fb[6] * (Ess - Es)))));
+        ba.rhos = fma(Ss, fma(Fb[2], vss, Fb[3] * wss), ba.rhos);
         double vssb = Fb[2] * Ss * ta.rhos, wssb = Fb[3] * Ss * ta.rhos;
-        Usb[2] -= Fb[2] * Ss;
-        Usb[3] -= Fb[3] * Ss;
+        Usb[2] = fma(-Fb[2], Ss, Usb[2]);
+        Usb[3] = fma(-Fb[3], Ss, Usb[3]);
         double b1ssb = Fb[4] * Ss, b2ssb = Fb[5] * Ss;
-        ba.b1s -= Fb[4] * Ss;
-        ba.b2s -= Fb[5] * Ss;
+        ba.b1s = fma(-Fb[4], Ss, ba.b1s);
+        ba.b2s = fma(-Fb[5], Ss, ba.b2s);
         const double Essb = Fb[6] * Ss;
-        Esb -= Fb[6] * Ss;
+        Esb = fma(-Fb[6], Ss, Esb);
         // Ess = Es + sqa sg (vBs - vBss)
         Esb += Essb;
         const double sqab = Essb * sg * dvB;
-        vBsb += Essb * sqa * sg;
+        vBsb = fma((Essb * sqa), sg, vBsb);
         const double vBssb = -Essb * sqa * sg;
         double sqLb = left ? -sqab : 0.0, sqRb = left ? 0.0 : sqab;
         // vBss = SM bn + vss b1ss + wss b2ss
-        SMb += vBssb * bn;
-        bnb += vBssb * SM;
-        vssb += vBssb * b1ss;
-        b1ssb += vBssb * vss;
-        wssb += vBssb * b2ss;
-        b2ssb += vBssb * wss;
+        SMb = fma(vBssb, bn, SMb);
+        bnb = fma(vBssb, SM, bnb);
+        vssb = fma(vBssb, b1ss, vssb);
+        b1ssb = fma(vBssb, vss, b1ssb);
+        wssb = fma(vBssb, b2ss, wssb);
+        b2ssb = fma(vBssb, wss, b2ssb);
         // b1ss, b2ss
-        double isumb = b1ssb * N1 + b2ssb * N2 + vssb * Nv + wssb * Nw;
+        double isumb = fma(b1ssb, N1, fma(b2ssb, N2, fma(vssb, Nv, wssb * Nw)));
         const double N1b = b1ssb * isum, N2b = b2ssb * isum, Nvb = vssb * isum, Nwb = wssb * isum;
-        sqLb += N1b * tR.b1s + N2b * tR.b2s + Nvb * tL.vs + Nwb * tL.ws;
-        sqRb += N1b * tL.b1s + N2b * tL.b2s + Nvb * tR.vs + Nwb * tR.ws;
-        bR.b1s += N1b * sqL + Nvb * sg;
-        bL.b1s += N1b * sqR - Nvb * sg;
-        bR.b2s += N2b * sqL + Nwb * sg;
-        bL.b2s += N2b * sqR - Nwb * sg;
+        sqLb = fma(N1b, tR.b1s, fma(N2b, tR.b2s, fma(Nvb, tL.vs, fma(Nwb, tL.ws, sqLb))));
+        sqRb = fma(N1b, tL.b1s, fma(N2b, tL.b2s, fma(Nvb, tR.vs, fma(Nwb, tR.ws, sqRb))));
+        bR.b1s = fma(N1b, sqL, fma(Nvb, sg, bR.b1s));
+        bL.b1s = fma(N1b, sqR, fma(-Nvb, sg, bL.b1s));
+        bR.b2s = fma(N2b, sqL, fma(Nwb, sg, bR.b2s));
+        bL.b2s = fma(N2b, sqR, fma(-Nwb, sg, bL.b2s));
         const double t1 = N1b * sg, t2 = N2b * sg;
-        const double sq2b = t1 * (tR.vs - tL.vs) + t2 * (tR.ws - tL.ws);
-        bR.vs += t1 * sq2 + Nvb * sqR;
-        bL.vs += -t1 * sq2 + Nvb * sqL;
-        bR.ws += t2 * sq2 + Nwb * sqR;
-        bL.ws += -t2 * sq2 + Nwb * sqL;
-        sqLb += sq2b * sqR;
-        sqRb += sq2b * sqL;
+        const double sq2b = fma(t1, (tR.vs - tL.vs), t2 * (tR.ws - tL.ws));
+        bR.vs = fma(t1, sq2, fma(Nvb, sqR, bR.vs));
+        bL.vs = fma(-t1, sq2, fma(Nvb, sqL, bL.vs));
+        bR.ws = fma(t2, sq2, fma(Nwb, sqR, bR.ws));
+        bL.ws = fma(-t2, sq2, fma(Nwb, sqL, bL.ws));
+        sqLb = fma(sq2b, sqR, sqLb);
+        sqRb = fma(sq2b, sqL, sqRb);
         // isum = 1/(sqL + sqR)
         const double db = isumb * (-(isum * isum));
         sqLb += db;
@@ -404,56 +405,56 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
         double iqLb = 0.0, iqRb = 0.0, abnb;
         if (left) {
           abnb = -Ssb * iqL;
-          iqLb -= Ssb * abn;
+          iqLb = fma(-Ssb, abn, iqLb);
         } else {
           abnb = Ssb * iqR;
-          iqRb += Ssb * abn;
+          iqRb = fma(Ssb, abn, iqRb);
         }
         bnb += lt0(bn) ? -abnb : abnb;
         // sq = rhos iq, iq = rhos^(-1/2)
-        bL.rhos += sqLb * iqL;
-        iqLb += sqLb * tL.rhos;
-        bR.rhos += sqRb * iqR;
-        iqRb += sqRb * tR.rhos;
-        bL.rhos += iqLb * (-0.5 * (iqL * iqL) * iqL);
-        bR.rhos += iqRb * (-0.5 * (iqR * iqR) * iqR);
+        bL.rhos = fma(sqLb, iqL, bL.rhos);
+        iqLb = fma(sqLb, tL.rhos, iqLb);
+        bR.rhos = fma(sqRb, iqR, bR.rhos);
+        iqRb = fma(sqRb, tR.rhos, iqRb);
+        bL.rhos = fma(iqLb, (-0.5 * (iqL * iqL) * iqL), bL.rhos);
+        bR.rhos = fma(iqRb, (-0.5 * (iqR * iqR) * iqR), bR.rhos);
       }
     }
     // ---- F = F_a + S_a (U*_a - U_a) ----
     double Uab[7];
 #pragma unroll
     for (int q = 0; q < 7; q++) {
-      Sb += Fb[q] * (Us[q] - Ua[q]);
-      Usb[q] += Fb[q] * S;
+      Sb = fma(Fb[q], (Us[q] - Ua[q]), Sb);
+      Usb[q] = fma(Fb[q], S, Usb[q]);
       Uab[q] = -Fb[q] * S;
     }
     // U*_a = (rhos, rhos SM, rhos vs, rhos ws, b1s, b2s, Es)
-    ba.rhos += Usb[0] + Usb[1] * SM + Usb[2] * ta.vs + Usb[3] * ta.ws;
-    SMb += Usb[1] * ta.rhos;
-    ba.vs += Usb[2] * ta.rhos;
-    ba.ws += Usb[3] * ta.rhos;
+    ba.rhos = fma(Usb[1], SM, fma(Usb[2], ta.vs, fma(Usb[3], ta.ws, ba.rhos + Usb[0])));
+    SMb = fma(Usb[1], ta.rhos, SMb);
+    ba.vs = fma(Usb[2], ta.rhos, ba.vs);
+    ba.ws = fma(Usb[3], ta.rhos, ba.ws);
     ba.b1s += Usb[4];
     ba.b2s += Usb[5];
     Esb += Usb[6];
     // Es = [(sd E_a - pT_a u_a) + (pT* SM + bn (vB_a - vB*))] ism
     const double NEb = Esb * ta.ism;
-    ba.ism += Esb * NE;
-    ba.sd += NEb * Ua[6];
-    Uab[6] += NEb * ta.sd;
+    ba.ism = fma(Esb, NE, ba.ism);
+    ba.sd = fma(NEb, Ua[6], ba.sd);
+    Uab[6] = fma(NEb, ta.sd, Uab[6]);
     double pTab = -NEb * A.u;
     const double uab = -NEb * pTa;
-    pTsb += NEb * SM;
-    SMb += NEb * pTs;
-    bnb += NEb * (vBa - vBs);
+    pTsb = fma(NEb, SM, pTsb);
+    SMb = fma(NEb, pTs, SMb);
+    bnb = fma(NEb, (vBa - vBs), bnb);
     const double vBab = NEb * bn;
-    vBsb -= NEb * bn;
+    vBsb = fma(-NEb, bn, vBsb);
     // vB* = SM bn + vs b1s + ws b2s
-    SMb += vBsb * bn;
-    bnb += vBsb * SM;
-    ba.vs += vBsb * ta.b1s;
-    ba.b1s += vBsb * ta.vs;
-    ba.ws += vBsb * ta.b2s;
-    ba.b2s += vBsb * ta.ws;
+    SMb = fma(vBsb, bn, SMb);
+    bnb = fma(vBsb, SM, bnb);
+    ba.vs = fma(vBsb, ta.b1s, ba.vs);
+    ba.b1s = fma(vBsb, ta.vs, ba.b1s);
+    ba.ws = fma(vBsb, ta.b2s, ba.ws);
+    ba.b2s = fma(vBsb, ta.ws, ba.b2s);
     // side a: conserved state, flux, v.B
     W7b& Wab = left ? Lb : Rb;
     Wab.u += uab;
@@ -470,24 +471,24 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     const double Npb = pTsb * iden;
     double idenb = pTsb * Np;
     const double a1b = Npb * (R.u - L.u);
-    Rb.u += Npb * a1;
-    Lb.u -= Npb * a1;
-    bR.rs += Npb * ll.pT;
-    pTbL += Npb * rsR;
-    bL.rs -= Npb * lr.pT;
-    pTbR -= Npb * rsL;
+    Rb.u = fma(Npb, a1, Rb.u);
+    Lb.u = fma(-Npb, a1, Lb.u);
+    bR.rs = fma(Npb, ll.pT, bR.rs);
+    pTbL = fma(Npb, rsR, pTbL);
+    bL.rs = fma(-Npb, lr.pT, bL.rs);
+    pTbR = fma(-Npb, rsL, pTbR);
     const double rr = L.rho * rsR;
-    bL.sd += a1b * rr;
+    bL.sd = fma(a1b, rr, bL.sd);
     const double rrb = a1b * sdL;
-    Lb.rho += rrb * rsR;
-    bR.rs += rrb * L.rho;
+    Lb.rho = fma(rrb, rsR, Lb.rho);
+    bR.rs = fma(rrb, L.rho, bR.rs);
     // SM = [(rsR uR - rsL uL) - pTR + pTL] iden
     const double NMb = SMb * iden;
-    idenb += SMb * NM;
-    bR.rs += NMb * R.u;
-    Rb.u += NMb * rsR;
-    bL.rs -= NMb * L.u;
-    Lb.u -= NMb * rsL;
+    idenb = fma(SMb, NM, idenb);
+    bR.rs = fma(NMb, R.u, bR.rs);
+    Rb.u = fma(NMb, rsR, Rb.u);
+    bL.rs = fma(-NMb, L.u, bL.rs);
+    Lb.u = fma(-NMb, rsL, Lb.u);
     pTbR -= NMb;
     pTbL += NMb;
     // iden = 1/(rsR - rsL)
@@ -495,10 +496,10 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     bR.rs += d;
     bL.rs -= d;
     // rs = sd rho, sd = S - u
-    bL.sd += bL.rs * L.rho;
-    Lb.rho += bL.rs * sdL;
-    bR.sd += bR.rs * R.rho;
-    Rb.rho += bR.rs * sdR;
+    bL.sd = fma(bL.rs, L.rho, bL.sd);
+    Lb.rho = fma(bL.rs, sdL, Lb.rho);
+    bR.sd = fma(bR.rs, R.rho, bR.sd);
+    Rb.rho = fma(bR.rs, sdR, Rb.rho);
     SLb += bL.sd;
     Lb.u -= bL.sd;
     SRb += bR.sd;
@@ -510,7 +511,7 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
   Rb.u += uRb;
   side_lite_vjp(L, bn2, gamma, ll.B2, B2bL, pTbL, cfLb, Lb, bn2b);
   side_lite_vjp(R, bn2, gamma, lr.B2, B2bR, pTbR, cfRb, Rb, bn2b);
-  bnb += (2.0 * bn) * bn2b;
+  bnb = fma((2.0 * bn), bn2b, bnb);
 }
 
 }  // namespace mhd
