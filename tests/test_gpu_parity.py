@@ -295,3 +295,20 @@ def test_autotune_restores_state_and_time(mhd):
     a, b = sim.get_conserved(), ref.get_conserved()
     for k in KEYS:
         assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("n", [(128, 128), (64, 48, 40), (256, 256, 256)])
+def test_default_segment_length_and_setter(mhd, n):
+    """The default is the longest of 2..64 that leaves about eight waves of
+    384-thread SM loads in the sweep with the fewest faces; set/get round-trip."""
+    torch = pytest.importorskip("torch")
+    nd = len(n)
+    cfg = W.base_cfg(nd, n, (0.0,) * nd, (1.0,) * nd)
+    sim = mhd.Sim(cfg)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fewest = min((n[d] + 1) * int(np.prod([n[t] + 2 for t in range(nd) if t != d])) for d in range(nd))
+    assert sim.seglen == min(64, max(2, fewest // (8 * sms * 384)))
+    sim.set_seglen(7)
+    assert sim.seglen == 7
+    with pytest.raises(mhd.MhdError):
+        sim.set_seglen(0)
