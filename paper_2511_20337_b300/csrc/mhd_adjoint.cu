@@ -181,9 +181,10 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const Ingr5x3& ING, const F8& A
                 double dt) {
   AdjointState* a = c->adj;
   const Grid& g = c->g;
-  // forward recompute of what the transposes read: ghosts and primitives of
-  // Xs (its UCT ingredients ING were kept by the block recompute)
-  ghost_fill(c, Xs);
+  // forward recompute of what the transposes read: the primitives of Xs.  Its
+  // ghost cells need no fill: the block recompute ran the forward stage on
+  // Xs, whose ghost fill wrote them in place (periodic, so idempotent), and
+  // its UCT ingredients ING were kept then too.
   prim(c, Xs, false);
   double c0, c1, cL;
   stage_coeffs(c->cfg.rk, s, c0, c1, cL);
