@@ -38,7 +38,7 @@ struct AdjointState {
   L3 LB;                      // cotangent of the CT face increment
   E3 Eb;                      // cotangent of the edge fields
   GE18 GE;                    // edge-local cotangents
-  F8 WbL, WbR;                // cotangents of the face states (7 used)
+  F8 WbL, WbR;                // cotangents of the face states (7 used; WbL.q[7] holds the PLM codes)
   F8 Pb;                      // cotangent of the primitives
   L6 T;                       // misfit target (padded cells)
   double* Jcell = nullptr;
@@ -64,6 +64,10 @@ void adjoint_free(mhd_ctx* c) {
 namespace {
 
 constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 + 3 * 18 + 8 + 8 + 8 + 6;
+
+// The per-cell PLM decisions of the current direction (adj_riemann_kernel ->
+// adj_recon_kernel) live in the face-state cotangent fields' spare slot 7.
+unsigned* plm_codes(const AdjointState* a) { return reinterpret_cast<unsigned*>(a->WbL.q[7]); }
 
 F8 state_at(const AdjointState* a, size_t idx) {
   F8 s;
@@ -167,9 +171,10 @@ void adj_dir(mhd_ctx* c, const F8& Xs, const F8& As, double dt) {
     cells *= ec;
   }
   adj_riemann_kernel<DIR, NDIM, RS><<<(int)((faces + 127) / 128), 128, 0, c->stream>>>(
-      g, c->P, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL, a->WbR, As.q[5 + DIR]);
+      g, c->P, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL, a->WbR, As.q[5 + DIR], plm_codes(a));
   prof_mark(c, MHD_AKCLASS_RIEMANN);
-  adj_recon_kernel<DIR, NDIM><<<(int)((cells + 127) / 128), 128, 0, c->stream>>>(g, c->P, a->WbL, a->WbR, a->Pb);
+  adj_recon_kernel<DIR, NDIM><<<(int)((cells + 127) / 128), 128, 0, c->stream>>>(g, plm_codes(a), a->WbL, a->WbR,
+                                                                                   a->Pb);
   prof_mark(c, MHD_AKCLASS_RECON);
   c->launches += 2;
 }

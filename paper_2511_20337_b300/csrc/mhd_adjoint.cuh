@@ -375,7 +375,9 @@ static __global__ void adj_edge_faces_kernel(Grid g, GE18 GE, F8 A) {
 // states, take the flux cotangent from the stage-increment cotangents of its
 // two cells, the UCT-ingredient cotangents from the edges that use the face,
 // and push both through the solver.  Writes the cotangents of the left and
-// right states and adds that of the normal face field.
+// right states, adds that of the normal face field, and records the PLM
+// decisions of cell f (and of cell -1 at face 0) for the reconstruction
+// reverse.
 // ---------------------------------------------------------------------------
 // PLM states of one cell from its 3-cell window with the positivity fallback.
 __device__ __forceinline__ bool plm_cell(const double w[7][3], double plus[7], double minus[7]) {
@@ -387,6 +389,17 @@ __device__ __forceinline__ bool plm_cell(const double w[7][3], double plus[7], d
     return true;
   }
   return false;
+}
+
+// The PLM decisions of one cell for its reverse: the minmod pick of every
+// primitive (2 bits each: 0 none, 1 the left difference, 2 the right one) and
+// the positivity fallback (bit 14).
+constexpr unsigned kPlmFallbackBit = 1u << 14;
+__device__ __forceinline__ unsigned plm_code(const double w[7][3], bool fallback) {
+  unsigned code = fallback ? kPlmFallbackBit : 0u;
+#pragma unroll
+  for (int v = 0; v < 7; v++) code |= (unsigned)minmod_pick(w[v][1] - w[v][0], w[v][2] - w[v][1]) << (2 * v);
+  return code;
 }
 
 template <int DIR, int NDIM>
@@ -475,7 +488,7 @@ static __global__ void riemann_vjp_probe_kernel(int n, double gamma, const doubl
 template <int DIR, int NDIM, int RS>
 static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, const double* __restrict__ Bn,
                                                                  L6 Lb, GE18 GE, double dt, F8 WbL, F8 WbR,
-                                                                 double* Bnb) {
+                                                                 double* Bnb, unsigned* plm_codes) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   int lo[3], ext[3];
   sweep_box<DIR, NDIM>(g, lo, ext, 0, g.n[DIR]);
@@ -495,14 +508,16 @@ static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, c
     for (int v = 0; v < 7; v++)
 #pragma unroll
       for (int m = 0; m < 3; m++) w[v][m] = pr[v][cf + (m - 2) * st];
-    plm_cell(w, plus, minus);
+    bool fb = plm_cell(w, plus, minus);
+    if (x[DIR] == 0) plm_codes[cf - st] = plm_code(w, fb);  // cell -1
 #pragma unroll
     for (int v = 0; v < 7; v++) xin[v] = plus[v];
 #pragma unroll
     for (int v = 0; v < 7; v++)
 #pragma unroll
       for (int m = 0; m < 3; m++) w[v][m] = pr[v][cf + (m - 1) * st];
-    plm_cell(w, plus, minus);
+    fb = plm_cell(w, plus, minus);
+    plm_codes[cf] = plm_code(w, fb);  // cell f
 #pragma unroll
     for (int v = 0; v < 7; v++) xin[7 + v] = minus[v];
   }
@@ -553,10 +568,12 @@ static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, c
 // ---------------------------------------------------------------------------
 // PLM reconstruction, per cell of the sweep box along DIR ([-2, n_DIR + 1]):
 // gather the state cotangents of the three cells whose reconstruction reads
-// this cell and add their contribution to the primitive cotangents.
+// this cell and add their contribution to the primitive cotangents, with the
+// PLM decisions adj_riemann_kernel recorded for those cells.
 // ---------------------------------------------------------------------------
 template <int DIR, int NDIM>
-static __global__ void __launch_bounds__(128) adj_recon_kernel(Grid g, F8 P, F8 WbL, F8 WbR, F8 Pb) {
+static __global__ void __launch_bounds__(128) adj_recon_kernel(Grid g, const unsigned* __restrict__ plm_codes, F8 WbL,
+                                                               F8 WbR, F8 Pb) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   int lo[3], ext[3];
   sweep_box<DIR, NDIM>(g, lo, ext, -2, g.n[DIR] + 1);
@@ -575,12 +592,8 @@ static __global__ void __launch_bounds__(128) adj_recon_kernel(Grid g, F8 P, F8 
     const int xo = x[DIR] + o;
     if (xo < -1 || xo > n) continue;
     const int co = c + o * st;
-    double w[7][3], plus[7], minus[7];
-#pragma unroll
-    for (int v = 0; v < 7; v++)
-#pragma unroll
-      for (int m = 0; m < 3; m++) w[v][m] = P.q[slot[v]][co + (m - 1) * st];
-    const bool fb = plm_cell(w, plus, minus);
+    const unsigned code = plm_codes[co];
+    const bool fb = (code & kPlmFallbackBit) != 0u;
 #pragma unroll
     for (int v = 0; v < 7; v++) {
       const double pb = xo + 1 <= n ? WbL.q[v][co + st] : 0.0;  // plus state: left state of face xo+1
@@ -592,7 +605,7 @@ static __global__ void __launch_bounds__(128) adj_recon_kernel(Grid g, F8 P, F8 
       double ws[3] = {0.0, 0.0, 0.0};  // cotangents of the window cells
       ws[1] = pb + mb;
       const double db = 0.5 * (pb - mb);
-      const int pick = minmod_pick(w[v][1] - w[v][0], w[v][2] - w[v][1]);
+      const int pick = (int)((code >> (2 * v)) & 3u);
       if (pick == 1) { ws[1] += db; ws[0] -= db; }
       else if (pick == 2) { ws[2] += db; ws[1] -= db; }
       acc[v] += ws[1 - o];
