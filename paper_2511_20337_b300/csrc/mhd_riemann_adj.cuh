@@ -44,11 +44,9 @@ __device__ __forceinline__ void fast_speed_vjp(double rho, double p, double B2, 
   pb = fma(gamma, gpb, pb);
 }
 
-// Total field, total pressure and fast speed of one side (side_lite):
-// cotangents of W and bn2 from those of B2 (direct uses), pT and cf.
-__device__ __forceinline__ void side_lite_vjp(const W7& W, double bn2, double gamma, double B2, double B2b, double pTb,
-                                              double cfb, W7b& Wb, double& bn2b) {
-  fast_speed_vjp(W.rho, W.p, B2, bn2, gamma, cfb, Wb.rho, Wb.p, B2b, bn2b);
+// Total field and total pressure of one side (side_num): cotangents of W
+// and bn2 from those of B2 (direct uses) and pT.
+__device__ __forceinline__ void side_num_vjp(const W7& W, double B2b, double pTb, W7b& Wb, double& bn2b) {
   Wb.p += pTb;
   B2b = fma(0.5, pTb, B2b);
   Wb.b1 = fma((2.0 * W.b1), B2b, Wb.b1);
@@ -118,13 +116,11 @@ __device__ __forceinline__ void side_full_vjp(const W7& W, double bn, double igm
   Wb.b2 = fma(vBb, W.w, Wb.b2);
 }
 
-// Outer speeds and UCT ingredients (speeds / the head of riemann_hlld):
-// cotangents of uL, uR, cfL, cfR from those of the ingredients and of SL, SR.
-__device__ __forceinline__ void speeds_vjp(double uL, double uR, double cfL, double cfR, const double Ib[5],
-                                           double SLb, double SRb, double& uLb, double& uRb, double& cfLb,
-                                           double& cfRb) {
-  const bool c_right = bits(cfL) < bits(cfR);              // imax_pos picks cfR
-  const double cmax = c_right ? cfR : cfL;
+// Outer speeds and UCT ingredients (speeds / the head of riemann_hlld), with
+// cmax = max(cf_L, cf_R) as fast_speed_max forms it: cotangents of uL, uR
+// and cmax from those of the ingredients and of SL, SR.
+__device__ __forceinline__ void speeds_vjp(double uL, double uR, double cmax, const double Ib[5], double SLb,
+                                           double SRb, double& uLb, double& uRb, double& cmaxb) {
   const bool min_right = order_key(uR) < order_key(uL);     // imin picks uR
   const bool max_right = order_key(uL) < order_key(uR);     // imax picks uR
   const double SL = (min_right ? uR : uL) - cmax;
@@ -146,9 +142,22 @@ __device__ __forceinline__ void speeds_vjp(double uL, double uR, double cfL, dou
   else uLb += SRb;
   if (min_right) uRb += SLb;
   else uLb += SLb;
-  const double cmaxb = SRb - SLb;
-  if (c_right) cfRb += cmaxb;
-  else cfLb += cmaxb;
+  cmaxb += SRb - SLb;
+}
+
+// The side that sets cmax (fast_speed_max's choice) and the reverse of its
+// fast speed: cotangents of that side's rho, p, B2 and of bn2 from cmax's.
+__device__ __forceinline__ bool cmax_right(double nL, double rhoL, double nR, double rhoR) {
+  return lt_pos(nL * rhoR, nR * rhoL);
+}
+__device__ __forceinline__ void cmax_vjp(const W7& L, const W7& R, bool right, double B2L, double B2R, double bn2,
+                                         double gamma, double cmaxb, W7b& Lb, W7b& Rb, double& B2bL, double& B2bR,
+                                         double& bn2b) {
+  const W7& W = right ? R : L;
+  double rhob = 0.0, pb = 0.0, B2b = 0.0;
+  fast_speed_vjp(W.rho, W.p, right ? B2R : B2L, bn2, gamma, cmaxb, rhob, pb, B2b, bn2b);
+  if (right) { Rb.rho += rhob; Rb.p += pb; B2bR += B2b; }
+  else { Lb.rho += rhob; Lb.p += pb; B2bL += B2b; }
 }
 
 // ---------------------------------------------------------------------------
@@ -159,9 +168,10 @@ __device__ __forceinline__ void riemann_hll_vjp(const W7& L, const W7& R, double
                                                 double& bnb) {
   const double bn2 = bn * bn;
   Side sl, sr;
-  side_state(L, bn, bn2, gamma, igm1, sl);
-  side_state(R, bn, bn2, gamma, igm1, sr);
-  const double cmax = imax_pos(sl.cf, sr.cf);
+  side_state<double, false>(L, bn, bn2, gamma, igm1, sl);
+  side_state<double, false>(R, bn, bn2, gamma, igm1, sr);
+  const bool c_right = cmax_right(sl.n, L.rho, sr.n, R.rho);
+  const double cmax = fast_speed_max(sl.n, L.rho, sr.n, R.rho);
   const double SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
   double ULb[7] = {0, 0, 0, 0, 0, 0, 0}, FLb[7] = {0, 0, 0, 0, 0, 0, 0};
   double URb[7] = {0, 0, 0, 0, 0, 0, 0}, FRb[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -197,15 +207,16 @@ __device__ __forceinline__ void riemann_hll_vjp(const W7& L, const W7& R, double
     SRb += db;
     SLb -= db;
   }
-  double uLb = 0.0, uRb = 0.0, cfLb = 0.0, cfRb = 0.0;
-  speeds_vjp(L.u, R.u, sl.cf, sr.cf, Ib, SLb, SRb, uLb, uRb, cfLb, cfRb);
+  double uLb = 0.0, uRb = 0.0, cmaxb = 0.0;
+  speeds_vjp(L.u, R.u, cmax, Ib, SLb, SRb, uLb, uRb, cmaxb);
   Lb.u += uLb;
   Rb.u += uRb;
   double bn2b = 0.0, B2bL = 0.0, pTbL = 0.0, B2bR = 0.0, pTbR = 0.0;
   side_full_vjp(L, bn, igm1, sl.B2, sl.pT, ULb, FLb, 0.0, Lb, bnb, bn2b, B2bL, pTbL);
   side_full_vjp(R, bn, igm1, sr.B2, sr.pT, URb, FRb, 0.0, Rb, bnb, bn2b, B2bR, pTbR);
-  side_lite_vjp(L, bn2, gamma, sl.B2, B2bL, pTbL, cfLb, Lb, bn2b);
-  side_lite_vjp(R, bn2, gamma, sr.B2, B2bR, pTbR, cfRb, Rb, bn2b);
+  cmax_vjp(L, R, c_right, sl.B2, sr.B2, bn2, gamma, cmaxb, Lb, Rb, B2bL, B2bR, bn2b);
+  side_num_vjp(L, B2bL, pTbL, Lb, bn2b);
+  side_num_vjp(R, B2bR, pTbR, Rb, bn2b);
   bnb = fma((2.0 * bn), bn2b, bnb);
 }
 
@@ -292,10 +303,11 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
                                                  const double Fb[7], const double Ib[5], W7b& Lb, W7b& Rb,
                                                  double& bnb) {
   const double bn2 = bn * bn;
-  SideLiteT<double> ll, lr;
-  side_lite(L, bn2, gamma, ll);
-  side_lite(R, bn2, gamma, lr);
-  const double cmax = imax_pos(ll.cf, lr.cf);
+  SideNumT<double> ll, lr;
+  side_num(L, bn2, gamma, ll);
+  side_num(R, bn2, gamma, lr);
+  const bool c_right = cmax_right(ll.n, L.rho, lr.n, R.rho);
+  const double cmax = fast_speed_max(ll.n, L.rho, lr.n, R.rho);
   const double SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
   double SLb = 0.0, SRb = 0.0, bn2b = 0.0;
   double B2bL = 0.0, pTbL = 0.0, B2bR = 0.0, pTbR = 0.0;
@@ -505,12 +517,13 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     SRb += bR.sd;
     Rb.u -= bR.sd;
   }
-  double uLb = 0.0, uRb = 0.0, cfLb = 0.0, cfRb = 0.0;
-  speeds_vjp(L.u, R.u, ll.cf, lr.cf, Ib, SLb, SRb, uLb, uRb, cfLb, cfRb);
+  double uLb = 0.0, uRb = 0.0, cmaxb = 0.0;
+  speeds_vjp(L.u, R.u, cmax, Ib, SLb, SRb, uLb, uRb, cmaxb);
   Lb.u += uLb;
   Rb.u += uRb;
-  side_lite_vjp(L, bn2, gamma, ll.B2, B2bL, pTbL, cfLb, Lb, bn2b);
-  side_lite_vjp(R, bn2, gamma, lr.B2, B2bR, pTbR, cfRb, Rb, bn2b);
+  cmax_vjp(L, R, c_right, ll.B2, lr.B2, bn2, gamma, cmaxb, Lb, Rb, B2bL, B2bR, bn2b);
+  side_num_vjp(L, B2bL, pTbL, Lb, bn2b);
+  side_num_vjp(R, B2bR, pTbR, Rb, bn2b);
   bnb = fma((2.0 * bn), bn2b, bnb);
 }
 
