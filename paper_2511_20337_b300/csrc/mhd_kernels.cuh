@@ -556,16 +556,13 @@ __device__ __forceinline__ void sweep_item_direct(const Grid& g, const F8& P, co
                                            const Ingr5x3& ING, DevScalars* sc, int seglen, int accumulate,
                                            long long id) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
-  constexpr int R = Stencil<RECON>::R;
-  constexpr int W = 2 * R + 1;  // window of cells
   // transverse ranges: fast index u, slow index w
   constexpr int U = (DIR == 0) ? 1 : 0;           // x is the fast index unless sweeping x
   constexpr int V = (DIR == 0) ? 2 : (DIR == 1 ? 2 : 1);
   const int lu = (U < NDIM) ? -1 : 0, hu = (U < NDIM) ? g.n[U] : 0;
   const int lv = (V < NDIM) ? -1 : 0, hv = (V < NDIM) ? g.n[V] : 0;
   const int eu = hu - lu + 1, ev = hv - lv + 1;
-  const int nd = g.n[DIR];
-  const int nseg = (nd + 1 + seglen - 1) / seglen;
+  const int nseg = (g.n[DIR] + 1 + seglen - 1) / seglen;
   const long long total = (long long)eu * ev * nseg;
   if (id >= total) return;
   const int iu = (int)(id % eu) + lu;
@@ -579,117 +576,14 @@ __device__ __forceinline__ void sweep_item_direct(const Grid& g, const F8& P, co
   const bool row_interior = (U >= NDIM || (iu >= 0 && iu < g.n[U])) && (V >= NDIM || (iv >= 0 && iv < g.n[V]));
   const int base = g.at(x[0], x[1], x[2]);
   const int st = g.stride(DIR);
-  const int f0 = seg * seglen;
-  const int f1 = min(f0 + seglen, nd + 1);  // owned faces [f0, f1)
-  const int fend = min(f1, nd);             // last face computed
-  const double dt = sc->dt;
-  const double dtdx = dt * g.idx[DIR];
   // primitive slots in sweep order: rho, v_n, v_t1, v_t2, B_t1, B_t2, p
   const double* pr[7] = {P.q[0], P.q[1 + DIR], P.q[1 + T1], P.q[1 + T2], P.q[4 + T1], P.q[4 + T2], P.q[7]};
-  double win[7][W];
-  // load window centred on cell f0 - 1
+  auto fetch = [&](int xi, double v7[7]) {
+    const int c = base + xi * st;
 #pragma unroll
-  for (int m = 0; m < W; m++) {
-    int c = base + (f0 - 1 - R + m) * st;
-#pragma unroll
-    for (int v = 0; v < 7; v++) win[v][m] = pr[v][c];
-  }
-  // PLM: the left difference of the window's centre cell, carried along the pencil
-  double dl[7];
-  if (RECON == RECON_PLM) {
-#pragma unroll
-    for (int v = 0; v < 7; v++) dl[v] = win[v][1] - win[v][0];
-  }
-  // WENO-Z: the curvatures of the stencils centred on the window's cells 1 and 2
-  Curv cv[7][2];
-  if (RECON == RECON_WENOZ) {
-#pragma unroll
-    for (int v = 0; v < 7; v++) {
-      cv[v][0] = curv(win[v][0], win[v][1], win[v][2]);
-      cv[v][1] = curv(win[v][1], win[v][2], win[v][3]);
-    }
-  }
-  auto reconstruct = [&](double plus[7], double minus[7], bool count) {
-#pragma unroll
-    for (int v = 0; v < 7; v++) {
-      if (RECON == RECON_PLM) {
-        const double dr = win[v][2] - win[v][1];
-        recon_plm_d(win[v][1], dl[v], dr, plus[v], minus[v]);
-        dl[v] = dr;
-      }
-      else if (RECON == RECON_WENOZ) {
-        Curv c2;
-        recon_wenoz_c(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], cv[v][0], cv[v][1], c2, plus[v], minus[v]);
-        cv[v][0] = cv[v][1];
-        cv[v][1] = c2;
-      }
-      else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
-    }
-    // positivity fallback: first order in this cell
-    if (!gt0(plus[0]) || !gt0(minus[0]) || !gt0(plus[6]) || !gt0(minus[6])) {
-#pragma unroll
-      for (int v = 0; v < 7; v++) plus[v] = minus[v] = win[v][R];
-      if (count) atomicAdd(&sc->fallbacks, 1ull);
-    }
+    for (int v = 0; v < 7; v++) v7[v] = pr[v][c];
   };
-  double wl[7], wr[7], dummy[7];
-  // cells are counted once: cell -1 by the first segment, cell f by the
-  // segment that owns face f
-  reconstruct(wl, dummy, seg == 0);  // V^L at face f0 (plus state of cell f0-1)
-  double Fprev[7];
-  for (int f = f0; f <= fend; f++) {
-    // shift the window to be centred on cell f
-#pragma unroll
-    for (int v = 0; v < 7; v++) {
-#pragma unroll
-      for (int m = 0; m < W - 1; m++) win[v][m] = win[v][m + 1];
-    }
-    {
-      int c = base + (f + R) * st;
-#pragma unroll
-      for (int v = 0; v < 7; v++) win[v][W - 1] = pr[v][c];
-    }
-    double plusN[7];
-    reconstruct(plusN, wr, f < f1);  // cell f: V^L at f+1, V^R at f
-    W7 L7 = {wl[0], wl[1], wl[2], wl[3], wl[4], wl[5], wl[6]};
-    W7 R7 = {wr[0], wr[1], wr[2], wr[3], wr[4], wr[5], wr[6]};
-    int cf = base + f * st;
-    double bn = Bface[cf];
-    Flux7 F;
-    Ingr ing;
-    if (RS == RS_HLLD) riemann_hlld(L7, R7, bn, g.gamma, g.igm1, F, ing);
-    else riemann_hll(L7, R7, bn, g.gamma, g.igm1, F, ing);
-    if (f < f1) {
-      ING.a[DIR][0][cf] = ing.ap;
-      ING.a[DIR][1][cf] = ing.am;
-      ING.a[DIR][2][cf] = ing.dd;
-      ING.a[DIR][3][cf] = ing.uL;
-      ING.a[DIR][4][cf] = ing.uR;
-    }
-    if (f > f0 && row_interior) {
-      int cc = cf - st;  // cell f-1
-      double dv[6];
-      dv[0] = F.f[0] - Fprev[0];
-      double dm[3];
-      dm[DIR] = F.f[1] - Fprev[1];
-      dm[T1] = F.f[2] - Fprev[2];
-      dm[T2] = F.f[3] - Fprev[3];
-      dv[1] = dm[0];
-      dv[2] = dm[1];
-      dv[3] = dm[2];
-      dv[4] = F.f[6] - Fprev[6];
-      constexpr int NV = NDIM == 2 ? 6 : 5;
-      if (NDIM == 2) dv[5] = (DIR == 0) ? F.f[5] - Fprev[5] : F.f[4] - Fprev[4];
-#pragma unroll
-      for (int q = 0; q < NV; q++)  // explicit roundings: the same in every kernel that inlines this
-        L.q[q][cc] = accumulate ? fma(-dtdx, dv[q], L.q[q][cc]) : -__dmul_rn(dtdx, dv[q]);
-    }
-#pragma unroll
-    for (int v = 0; v < 7; v++) {
-      Fprev[v] = F.f[v];
-      wl[v] = plusN[v];
-    }
-  }
+  sweep_body<DIR, NDIM, RECON, RS>(g, Bface, L, ING, sc, seglen, accumulate, base, seg, true, row_interior, fetch);
 }
 
 // Staged x-sweep item (grids for which sweep_staged holds): the warp's 32
