@@ -608,40 +608,51 @@ def run_ensemble(args):
     del sims
 
     # end to end: every run's state in from pinned host memory, one step, every
-    # state out; two batches on two streams take the steps in turn, so one's
-    # copies overlap the other's step (each step after the previous one)
-    streams = (stream, torch.cuda.Stream(device=dev))
-    bt2 = mhd.Batch(cfgs, stream=streams[1].cuda_stream)
-    bt2.set_seglen(*seg)
-    bts = (bt, bt2)
+    # state out.  Three batches on three streams take the steps in turn, each
+    # step after the previous one: while one batch steps, the previous one's
+    # states are read out and the next one's are written (with two, the host
+    # could only refill a batch after reading it, so the two copies ran in series).
+    streams = (stream, torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev))
+    bts = (bt, mhd.Batch(cfgs, stream=streams[1].cuda_stream), mhd.Batch(cfgs, stream=streams[2].cuda_stream))
+    for b in bts[1:]:
+        b.set_seglen(*seg)
     for b in bts:
         for r, h in enumerate(host):
             b.set_conserved(r, h)
         b.step(1)                      # captures the step graph
     torch.cuda.synchronize(dev)
-    e2e_steps = max(2, min(args.steps, 10))
-    t0 = time.perf_counter()
-    prev, done = None, None
-    for s in range(e2e_steps):
-        b, bs = bts[s % 2], streams[s % 2]
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def write(b):
         for r, h in enumerate(host):
             b.set_conserved(r, h)
+
+    def read(b):
+        for r, o in enumerate(out_host):
+            b.get_conserved(r, o, wait=False)
+        b.synchronize()                # one wait for all runs' copies
+
+    t0 = time.perf_counter()
+    write(bts[0])
+    done = None
+    for s in range(e2e_steps):
+        b, bs = bts[s % 3], streams[s % 3]
         if done is not None:
-            bs.wait_event(done)
+            bs.wait_event(done)        # after the previous step
         b.step(1)
         done = torch.cuda.Event()
         done.record(bs)
-        if prev is not None:
-            for r, o in enumerate(out_host):
-                prev.get_conserved(r, o)
-        prev = b
-    for r, o in enumerate(out_host):
-        prev.get_conserved(r, o)
+        if s + 1 < e2e_steps:
+            write(bts[(s + 1) % 3])    # the next step's states, into the batch read out a step ago
+        if s > 0:
+            read(bts[(s - 1) % 3])     # the previous step's states
+    read(bts[(e2e_steps - 1) % 3])
     el = job_time_ms(time.perf_counter() - t0, world, dev)
     e2e = {"value": ncell * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d, "steps": e2e_steps,
-           "pipeline": "two batches alternate, steps in order; copies of one overlap the other's step"}
-    bt2.close()
+           "pipeline": "three batches in turn, steps in order; one's copies in and another's out overlap the third's step"}
+    for b in bts[1:]:
+        b.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

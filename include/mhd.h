@@ -221,6 +221,15 @@ int mhd_batch_destroy(mhd_batch* b);
 int mhd_batch_set_conserved(mhd_batch* b, int run, int mem, const double* const* U, const double* const* B);
 int mhd_batch_get_conserved(mhd_batch* b, int run, int mem, double* const* U, double* const* B);
 
+/* As mhd_batch_get_conserved, without waiting: the copies are queued in the
+ * batch's stream order, so reading many runs costs one wait
+ * (mhd_batch_synchronize) instead of one per run.  The destination arrays
+ * must stay valid, and host ones pinned, until that wait returns.  Async. */
+int mhd_batch_get_conserved_async(mhd_batch* b, int run, int mem, double* const* U, double* const* B);
+
+/* Wait until the batch's queued work and copies are done.  Sync. */
+int mhd_batch_synchronize(mhd_batch* b);
+
 /* Advance every run nsteps steps, each run with its own CFL dt computed on the
  * device.  Every run must have a state (MHD_ERR_STATE).  Async. */
 int mhd_batch_step(mhd_batch* b, int nsteps);

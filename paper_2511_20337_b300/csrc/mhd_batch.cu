@@ -332,6 +332,19 @@ int mhd_batch_set_conserved(mhd_batch* b, int run, int mem, const double* const*
 }
 
 int mhd_batch_get_conserved(mhd_batch* b, int run, int mem, double* const* U, double* const* B) {
+  const int rc = mhd_batch_get_conserved_async(b, run, mem, U, B);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(b->stream));
+  return MHD_OK;
+}
+
+int mhd_batch_synchronize(mhd_batch* b) {
+  if (!b) return MHD_ERR_ARG;
+  CK(cudaStreamSynchronize(b->stream));
+  return MHD_OK;
+}
+
+int mhd_batch_get_conserved_async(mhd_batch* b, int run, int mem, double* const* U, double* const* B) {
   if (!b || run < 0 || run >= b->nruns || !U || !B || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE))
     return MHD_ERR_ARG;
   if (!b->has_state[run]) return MHD_ERR_STATE;
@@ -349,7 +362,6 @@ int mhd_batch_get_conserved(mhd_batch* b, int run, int mem, double* const* U, do
     if (rc) return rc;
   }
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(b->stream));
   return MHD_OK;
 }
 

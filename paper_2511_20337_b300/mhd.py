@@ -36,7 +36,8 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
-           "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen")
+           "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen",
+           "mhd_batch_get_conserved_async", "mhd_batch_synchronize")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -92,6 +93,8 @@ def lib():
             "mhd_batch_destroy": (I, [P]),
             "mhd_batch_set_conserved": (I, [P, I, I, DPP, DPP]),
             "mhd_batch_get_conserved": (I, [P, I, I, DPP, DPP]),
+            "mhd_batch_get_conserved_async": (I, [P, I, I, DPP, DPP]),
+            "mhd_batch_synchronize": (I, [P]),
             "mhd_batch_step": (I, [P, I]),
             "mhd_batch_autotune": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
             "mhd_batch_set_seglen": (I, [P, I, I]),
@@ -457,6 +460,7 @@ class Batch:
         _check(lib().mhd_batch_create(len(cfgs), arr, ctypes.byref(h)), "mhd_batch_create")
         self.h = h
         self._keep = {}
+        self._pending = []  # destinations of queued read-outs, kept alive until synchronize()
         if states is not None:
             for r, st in enumerate(states):
                 self.set_conserved(r, st)
@@ -482,14 +486,25 @@ class Batch:
         _check(lib().mhd_batch_set_conserved(self.h, run, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
                                              _ptr_array(arrs[5:])), "mhd_batch_set_conserved")
 
-    def get_conserved(self, run, out=None):
+    def get_conserved(self, run, out=None, wait=True):
+        """Copy run's state out (dict of numpy arrays or CUDA tensors, or new
+        numpy arrays).  wait=False queues the copies only (out must be pinned
+        host memory or device memory, and is complete after synchronize())."""
         if out is None:
             out = {k: np.zeros(s) for k, s in zip(KEYS, self.shapes[run])}
         arrs = [out[k] for k in KEYS]
         dev = _is_device(arrs[0])
-        _check(lib().mhd_batch_get_conserved(self.h, run, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
-                                             _ptr_array(arrs[5:])), "mhd_batch_get_conserved")
+        fn = lib().mhd_batch_get_conserved if wait else lib().mhd_batch_get_conserved_async
+        _check(fn(self.h, run, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]), _ptr_array(arrs[5:])),
+               "mhd_batch_get_conserved")
+        if not wait:
+            self._pending.append(arrs)
         return out
+
+    def synchronize(self):
+        """Wait for the queued work and copies (get_conserved(wait=False))."""
+        _check(lib().mhd_batch_synchronize(self.h), "mhd_batch_synchronize")
+        self._pending = []
 
     def step(self, nsteps):
         _check(lib().mhd_batch_step(self.h, int(nsteps)), "mhd_batch_step")

@@ -84,8 +84,14 @@ def test_two_contexts_in_turn_equal_one_context(case):
             b.step(1)
             done = torch.cuda.Event()
             done.record(bs)
-            if prev is not None:
-                got[prev[1]] = [prev[0].get_conserved(r) for r in range(len(cases))]
+            if prev is not None:  # queued read-outs into pinned buffers, one wait
+                pb, pt = prev
+                got[pt] = [{k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in want[pt][r].items()}
+                           for r in range(len(cases))]
+                for r in range(len(cases)):
+                    pb.get_conserved(r, got[pt][r], wait=False)
+                pb.synchronize()
+                got[pt] = [{k: v.numpy() for k, v in d.items()} for d in got[pt]]
             prev = (b, t)
         got[prev[1]] = [prev[0].get_conserved(r) for r in range(len(cases))]
         for t in range(3):
