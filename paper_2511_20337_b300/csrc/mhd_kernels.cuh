@@ -95,6 +95,56 @@ static __global__ void ghost_periodic_kernel(Grid g, F8 S, int d) {
     ghost_periodic_item(g, S, d, id);
 }
 
+// All axes periodic: every ghost cell in one pass, copied from its interior
+// cell with every index wrapped.  The same values as the passes above (there a
+// corner takes a stale copy in the first pass and the wrapped one in a later
+// pass).  The shell is enumerated as slabs, one per axis d: d-index in the
+// ghost layers, the axes after d interior and the axes before d over the full
+// padded range (so each ghost cell is in the slab of its highest ghost axis).
+template <int NDIM>
+__host__ __device__ __forceinline__ long long ghost_shell_slab(const Grid& g, int d) {
+  long long w = 2 * g.G + 1;
+  for (int t = 0; t < NDIM; t++)
+    if (t < d) w *= g.n[t] + 2 * g.G + 1;
+    else if (t > d) w *= g.n[t];
+  return w;
+}
+template <int NDIM>
+__host__ __device__ __forceinline__ long long ghost_shell_work(const Grid& g) {
+  long long w = 0;
+  for (int d = 0; d < NDIM; d++) w += ghost_shell_slab<NDIM>(g, d);
+  return w;
+}
+template <int NDIM>
+__device__ __forceinline__ void ghost_shell_item(const Grid& g, const F8& S, long long id) {
+  int d = NDIM - 1;
+  while (d > 0) {  // slabs of the outer axes come first
+    const long long w = ghost_shell_slab<NDIM>(g, d);
+    if (id < w) break;
+    id -= w;
+    d--;
+  }
+  const int nl = 2 * g.G + 1;
+  int x[3] = {0, 0, 0};
+  for (int t = 0; t < NDIM; t++) {  // axis t: full range (t < d), ghost layer (t == d), interior (t > d)
+    const int e = t < d ? g.n[t] + nl : (t == d ? nl : g.n[t]);
+    const int v = (int)(id % e);
+    id /= e;
+    x[t] = t < d ? v - g.G : (t == d ? (v < g.G ? v - g.G : g.n[t] + (v - g.G)) : v);
+  }
+  const int dst = g.at(x[0], x[1], x[2]);
+  const int src = g.at(wrap(x[0], g.n[0]), NDIM > 1 ? wrap(x[1], g.n[1]) : 0, NDIM > 2 ? wrap(x[2], g.n[2]) : 0);
+#pragma unroll
+  for (int q = 0; q < 8; q++) S.q[q][dst] = S.q[q][src];
+}
+template <int NDIM>
+static __global__ void ghost_shell_kernel(Grid g, F8 S) {
+  const long long total = ghost_shell_work<NDIM>(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    ghost_shell_item<NDIM>(g, S, id);
+}
+
 // Outflow pass along axis d, part 1: zero-gradient copies of every slot except
 // the normal face field (d-index -1..-G from 0; n..n+G from n-1).
 __device__ __forceinline__ void ghost_outflow_copy_item(const Grid& g, const F8& S, int d, long long id) {
