@@ -79,31 +79,50 @@ void prim(mhd_ctx* c, const F8& S, bool cfl) {
   }
 }
 
+bool split_now(const mhd_ctx* c) { return c->split && !c->prof_on; }
+
+// One direction's sweep on stream st into the increment target T: mode 0
+// writes -dt/dx dF, 1 adds it, 2 stores the raw difference dF (split sweeps).
 template <int DIR, int NDIM, int RECON, int RS>
-void sweep_one(mhd_ctx* c, const F8& S) {
+void sweep_one(mhd_ctx* c, const F8& S, cudaStream_t st, const L6& T, int mode) {
   const Grid& g = c->g;
   const long long threads = sweep_work<DIR, NDIM>(g, c->seglen);
   const int nb = (int)((threads + kSweepThreads - 1) / kSweepThreads);
   if constexpr (DIR == 0) {
     if (sweep_staged<DIR, NDIM>(g)) {
-      sweep_kernel<DIR, NDIM, RECON, RS, true><<<nb, kSweepThreads, kXStageBytes, c->stream>>>(
-          g, c->P, S.q[5 + DIR], c->L, c->ING, c->sc, c->seglen, 0);
+      sweep_kernel<DIR, NDIM, RECON, RS, true><<<nb, kSweepThreads, kXStageBytes, st>>>(
+          g, c->P, S.q[5 + DIR], T, c->ING, c->sc, c->seglen, mode);
       c->launches++;
       prof_mark(c, MHD_KCLASS_SWEEP_X + DIR);
       return;
     }
   }
-  sweep_kernel<DIR, NDIM, RECON, RS><<<nb, kSweepThreads, 0, c->stream>>>(g, c->P, S.q[5 + DIR], c->L, c->ING,
-                                                                          c->sc, c->seglen, DIR > 0 ? 1 : 0);
+  sweep_kernel<DIR, NDIM, RECON, RS><<<nb, kSweepThreads, 0, st>>>(g, c->P, S.q[5 + DIR], T, c->ING, c->sc,
+                                                                   c->seglen, mode);
   c->launches++;
   prof_mark(c, MHD_KCLASS_SWEEP_X + DIR);
 }
 
 template <int NDIM, int RECON, int RS>
 void sweeps_t(mhd_ctx* c, const F8& S) {
-  sweep_one<0, NDIM, RECON, RS>(c, S);
-  sweep_one<1, NDIM, RECON, RS>(c, S);
-  if constexpr (NDIM == 3) sweep_one<2, NDIM, RECON, RS>(c, S);
+  if (split_now(c)) {  // y (and z) beside x; the main stream waits for both
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0);
+    sweep_one<1, NDIM, RECON, RS>(c, S, c->aux[0], c->D[0], 2);
+    cudaEventRecord(c->ev_join[0], c->aux[0]);
+    if constexpr (NDIM == 3) {
+      cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0);
+      sweep_one<2, NDIM, RECON, RS>(c, S, c->aux[1], c->D[1], 2);
+      cudaEventRecord(c->ev_join[1], c->aux[1]);
+    }
+    sweep_one<0, NDIM, RECON, RS>(c, S, c->stream, c->L, 0);
+    cudaStreamWaitEvent(c->stream, c->ev_join[0], 0);
+    if constexpr (NDIM == 3) cudaStreamWaitEvent(c->stream, c->ev_join[1], 0);
+    return;
+  }
+  sweep_one<0, NDIM, RECON, RS>(c, S, c->stream, c->L, 0);
+  sweep_one<1, NDIM, RECON, RS>(c, S, c->stream, c->L, 1);
+  if constexpr (NDIM == 3) sweep_one<2, NDIM, RECON, RS>(c, S, c->stream, c->L, 1);
 }
 
 // The staged x sweep uses more than the default 48 KB of dynamic shared
@@ -150,8 +169,14 @@ void ct_rk(mhd_ctx* c, const F8& U0, const F8& Us, const F8& Out, int mode) {
   const Grid& g = c->g;
   long long work = (long long)(g.n[0] + 1) * (g.n[1] + 1) * (g.ndim == 3 ? g.n[2] + 1 : 1);
   int nb = blocks_for(work, 256);
-  if (g.ndim == 2) ct_rk_kernel<2><<<nb, 256, 0, c->stream>>>(g, U0, Us, Out, c->L, c->E, c->sc, mode);
-  else ct_rk_kernel<3><<<nb, 256, 0, c->stream>>>(g, U0, Us, Out, c->L, c->E, c->sc, mode);
+  if (split_now(c)) {
+    if (g.ndim == 2) ct_rk_split_kernel<2><<<nb, 256, 0, c->stream>>>(g, U0, Us, Out, c->L, c->D[0], c->D[1], c->E, c->sc, mode);
+    else ct_rk_split_kernel<3><<<nb, 256, 0, c->stream>>>(g, U0, Us, Out, c->L, c->D[0], c->D[1], c->E, c->sc, mode);
+  } else if (g.ndim == 2) {
+    ct_rk_kernel<2><<<nb, 256, 0, c->stream>>>(g, U0, Us, Out, c->L, c->E, c->sc, mode);
+  } else {
+    ct_rk_kernel<3><<<nb, 256, 0, c->stream>>>(g, U0, Us, Out, c->L, c->E, c->sc, mode);
+  }
   c->launches++;
   prof_mark(c, MHD_KCLASS_CT_RK);
 }
@@ -269,7 +294,7 @@ void run_step(mhd_ctx* c, bool device_dt) {
 // reconstruction at its end, so long segments waste less, while short ones
 // give more threads.  Take the longest (2..64) that still leaves about eight
 // waves of 384-thread SM loads in the sweep with the fewest faces.
-static int default_seglen(const Grid& g) {
+static long long faces_per_thread_target(const Grid& g) {
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 148;
@@ -280,9 +305,15 @@ static int default_seglen(const Grid& g) {
       if (t != d) faces *= g.n[t] + 2;
     fewest = faces < fewest ? faces : fewest;
   }
-  const long long per_thread = fewest / (8LL * sms * 384);
+  return fewest / (8LL * sms * 384);
+}
+static int default_seglen(const Grid& g) {
+  const long long per_thread = faces_per_thread_target(g);
   return (int)(per_thread < 2 ? 2 : (per_thread > 64 ? 64 : per_thread));
 }
+// Sweeps side by side when even segments of 2 faces leave fewer than about
+// eight waves of threads in one sweep (CT only).
+static bool split_sweeps(const Grid& g) { return !g.glm && g.ndim > 1 && faces_per_thread_target(g) < 2; }
 
 extern "C" {
 
@@ -313,6 +344,7 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
   c->cfg = *cfg;
   c->g = g;
   c->seglen = default_seglen(g);
+  c->split = split_sweeps(g);
   c->field_elems = (size_t)((elems + 31) / 32 * 32);
   if (cfg->stream) {
     c->stream = (cudaStream_t)cfg->stream;
@@ -324,7 +356,8 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
   }
   // CT: 3 registers of 8, primitives 8, increment 6, ingredients 15, edges 3;
   // GLM: 3 registers of 9, primitives 9, increment 9
-  const int nfields = (g.glm ? 3 * 9 + 9 + 9 : 3 * 8 + 8 + 6 + 15 + 3) + 1;  // + the CFL rates
+  // (+ the CFL rates; + the raw flux differences of the split y and z sweeps)
+  const int nfields = (g.glm ? 3 * 9 + 9 + 9 : 3 * 8 + 8 + 6 + 15 + 3) + 1 + (c->split ? 6 * (g.ndim - 1) : 0);
   size_t bytes = c->field_elems * sizeof(double) * nfields;
   if (cudaMalloc(&c->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -355,6 +388,9 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
     for (int d = 0; d < 3; d++) c->E.e[d] = next();
   }
   c->lam = next();
+  if (c->split)
+    for (int d = 0; d < g.ndim - 1; d++)
+      for (int q = 0; q < 6; q++) c->D[d].q[q] = next();
   if (cudaMalloc(&c->sc, sizeof(DevScalars)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->pool);
@@ -373,6 +409,16 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
     mhd_destroy(c);
     return MHD_ERR_CUDA;
   }
+  if (c->split) {
+    bool ok = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int d = 0; d < 2 && ok; d++)
+      ok = cudaStreamCreateWithFlags(&c->aux[d], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->ev_join[d], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      mhd_destroy(c);
+      return MHD_ERR_CUDA;
+    }
+  }
   c->launches_per_step = -1;
   *out = c;
   return MHD_OK;
@@ -385,6 +431,11 @@ int mhd_destroy(mhd_ctx* c) {
   adjoint_free(c);
   cudaFree(c->pool);
   cudaFree(c->sc);
+  for (int d = 0; d < 2; d++) {
+    if (c->aux[d]) cudaStreamDestroy(c->aux[d]);
+    if (c->ev_join[d]) cudaEventDestroy(c->ev_join[d]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return MHD_OK;

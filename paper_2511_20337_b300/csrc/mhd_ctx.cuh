@@ -40,6 +40,14 @@ struct mhd_ctx {
   // (cell B in slots 5..7), GU[r].q[8] is psi
   mhd::F9 GU[3], GP, GL;
   int reg_fields;          // fields per RK register: 8 (CT) or 9 (GLM); contiguous
+  // grids too small to fill the device with one sweep (CT): the y (and z)
+  // sweeps run beside the x sweep on streams aux[], joined by events, and
+  // leave their raw flux differences in D[0] (D[1]); ct_rk completes the stage
+  // increment in the sequential order, so the result is the same to the bit
+  bool split;
+  cudaStream_t aux[2];
+  cudaEvent_t ev_fork, ev_join[2];
+  mhd::L6 D[2];
 };
 
 namespace mhd {
@@ -56,5 +64,6 @@ void run_stage_regs(mhd_ctx* c, int s, const F8& U0, const F8& Us, const F8& Out
 void run_stage(mhd_ctx* c, int s, bool cfl);         // on the context's registers
 void run_step(mhd_ctx* c, bool device_dt);
 void adjoint_free(mhd_ctx* c);                       // defined in mhd_adjoint.cu
+bool split_now(const mhd_ctx* c);                    // sweeps side by side in this launch sequence
 
 }  // namespace mhd

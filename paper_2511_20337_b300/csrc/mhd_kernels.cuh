@@ -589,7 +589,7 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
       if (NDIM == 2) dv[5] = (DIR == 0) ? F.f[5] - Fprev[5] : F.f[4] - Fprev[4];
 #pragma unroll
       for (int q = 0; q < NV; q++)  // explicit roundings: the same in every kernel that inlines this
-        L.q[q][cc] = accumulate ? fma(-dtdx, dv[q], L.q[q][cc]) : -__dmul_rn(dtdx, dv[q]);
+        L.q[q][cc] = accumulate == 2 ? dv[q] : (accumulate ? fma(-dtdx, dv[q], L.q[q][cc]) : -__dmul_rn(dtdx, dv[q]));
     }
 #pragma unroll
     for (int v = 0; v < 7; v++) {
@@ -811,9 +811,13 @@ __device__ __forceinline__ double combine(int mode, double u0, double us, double
   }
 }
 
-template <int NDIM>
+// SPLIT: the y (and z) sweeps ran beside the x sweep and left their raw flux
+// differences in Dy (Dz); the stage increment is completed here exactly as the
+// sequential sweeps accumulate it, L = fma(-dt/dz, Dz, fma(-dt/dy, Dy, L_x)).
+template <int NDIM, bool SPLIT = false>
 __device__ __forceinline__ void ct_rk_item(const Grid& g, const F8& U0, const F8& Us, const F8& Out, const L6& L,
-                                           const E3& E, double dt, int mode, long long id) {
+                                           const E3& E, double dt, int mode, long long id, const L6* Dy = nullptr,
+                                           const L6* Dz = nullptr) {
   const int ex = g.n[0] + 1, ey = g.n[1] + 1;
   int i = (int)(id % ex);
   long long r = id / ex;
@@ -826,7 +830,12 @@ __device__ __forceinline__ void ct_rk_item(const Grid& g, const F8& U0, const F8
 #pragma unroll
     for (int q = 0; q < NV; q++) {
       int slot = q < 5 ? q : 7;
-      Out.q[slot][c] = combine(mode, U0.q[slot][c], Us.q[slot][c], L.q[q][c]);
+      double l = L.q[q][c];
+      if (SPLIT) {
+        l = fma(-(dt * g.idx[1]), Dy->q[q][c], l);
+        if (NDIM == 3) l = fma(-(dt * g.idx[2]), Dz->q[q][c], l);
+      }
+      Out.q[slot][c] = combine(mode, U0.q[slot][c], Us.q[slot][c], l);
     }
   }
   // faces with normal d: evolved for d-index < n_d, or == n_d on an outflow axis
@@ -858,6 +867,15 @@ static __global__ void __launch_bounds__(256) ct_rk_kernel(Grid g, F8 U0, F8 Us,
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x)
     ct_rk_item<NDIM>(g, U0, Us, Out, L, E, dt, mode, id);
+}
+template <int NDIM>
+static __global__ void __launch_bounds__(256) ct_rk_split_kernel(Grid g, F8 U0, F8 Us, F8 Out, L6 L, L6 Dy, L6 Dz,
+                                                          E3 E, const DevScalars* sc, int mode) {
+  const long long total = edge_work<NDIM>(g);
+  const double dt = sc->dt;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    ct_rk_item<NDIM, true>(g, U0, Us, Out, L, E, dt, mode, id, &Dy, &Dz);
 }
 
 // ---------------------------------------------------------------------------
