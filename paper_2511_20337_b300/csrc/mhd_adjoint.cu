@@ -38,7 +38,7 @@ struct AdjointState {
   L3 LB;                      // cotangent of the CT face increment
   E3 Eb;                      // cotangent of the edge fields
   GE18 GE;                    // edge-local cotangents
-  F8 WbL, WbR;                // cotangents of the face states (7 used; WbL.q[7] holds the PLM codes)
+  F8 WbL[3], WbR[3];          // per direction: cotangents of the face states (7 used; WbL.q[7] holds the PLM codes)
   F8 Pb;                      // cotangent of the primitives
   L6 T;                       // misfit target (padded cells)
   double* Jcell = nullptr;
@@ -63,11 +63,11 @@ void adjoint_free(mhd_ctx* c) {
 
 namespace {
 
-constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 + 3 * 18 + 8 + 8 + 8 + 6;
+constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 + 3 * 18 + 3 * (8 + 8) + 8 + 6;
 
 // The per-cell PLM decisions of the current direction (adj_riemann_kernel ->
 // adj_recon_kernel) live in the face-state cotangent fields' spare slot 7.
-unsigned* plm_codes(const AdjointState* a) { return reinterpret_cast<unsigned*>(a->WbL.q[7]); }
+unsigned* plm_codes(const AdjointState* a, int d) { return reinterpret_cast<unsigned*>(a->WbL[d].q[7]); }
 
 F8 state_at(const AdjointState* a, size_t idx) {
   F8 s;
@@ -105,8 +105,11 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
     for (int d = 0; d < 3; d++) a->Eb.e[d] = next();
     for (int C = 0; C < 3; C++)
       for (int m = 0; m < 18; m++) a->GE.q[C][m] = next();
-    for (int q = 0; q < 8; q++) a->WbL.q[q] = next();
-    for (int q = 0; q < 8; q++) a->WbR.q[q] = next();
+    for (int d = 0; d < 3; d++)
+      for (int q = 0; q < 8; q++) {
+        a->WbL[d].q[q] = next();
+        a->WbR[d].q[q] = next();
+      }
     for (int q = 0; q < 8; q++) a->Pb.q[q] = next();
     for (int q = 0; q < 6; q++) a->T.q[q] = next();
     long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
@@ -159,24 +162,30 @@ void stage_coeffs(int rk, int s, double& c0, double& c1, double& cL) {
   c0 = 1.0 / 3.0; c1 = 2.0 / 3.0; cL = 2.0 / 3.0;
 }
 
+// Riemann transpose of direction DIR on stream st (its own face-state
+// cotangents and PLM codes), then, separately, its reconstruction transpose,
+// which adds into Pb and so runs on the context stream in direction order.
 template <int NDIM, int RS, int DIR>
-void adj_dir(mhd_ctx* c, const F8& Xs, const F8& As, double dt) {
+void adj_riemann_dir(mhd_ctx* c, const F8& Xs, const F8& As, double dt, cudaStream_t st) {
   AdjointState* a = c->adj;
   const Grid& g = c->g;
-  long long faces = 1, cells = 1;
-  for (int d = 0; d < 3; d++) {
-    long long ef = d == DIR ? g.n[d] + 1 : (d < NDIM ? g.n[d] + 2 : 1);
-    long long ec = d == DIR ? g.n[d] + 4 : (d < NDIM ? g.n[d] + 2 : 1);
-    faces *= ef;
-    cells *= ec;
-  }
-  adj_riemann_kernel<DIR, NDIM, RS><<<(int)((faces + 127) / 128), 128, 0, c->stream>>>(
-      g, c->P, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL, a->WbR, As.q[5 + DIR], plm_codes(a));
+  long long faces = 1;
+  for (int d = 0; d < 3; d++) faces *= d == DIR ? g.n[d] + 1 : (d < NDIM ? g.n[d] + 2 : 1);
+  adj_riemann_kernel<DIR, NDIM, RS><<<(int)((faces + 127) / 128), 128, 0, st>>>(
+      g, c->P, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL[DIR], a->WbR[DIR], As.q[5 + DIR], plm_codes(a, DIR));
   prof_mark(c, MHD_AKCLASS_RIEMANN);
-  adj_recon_kernel<DIR, NDIM><<<(int)((cells + 127) / 128), 128, 0, c->stream>>>(g, plm_codes(a), a->WbL, a->WbR,
-                                                                                   a->Pb);
+  c->launches++;
+}
+template <int NDIM, int DIR>
+void adj_recon_dir(mhd_ctx* c) {
+  AdjointState* a = c->adj;
+  const Grid& g = c->g;
+  long long cells = 1;
+  for (int d = 0; d < 3; d++) cells *= d == DIR ? g.n[d] + 4 : (d < NDIM ? g.n[d] + 2 : 1);
+  adj_recon_kernel<DIR, NDIM><<<(int)((cells + 127) / 128), 128, 0, c->stream>>>(g, plm_codes(a, DIR), a->WbL[DIR],
+                                                                                   a->WbR[DIR], a->Pb);
   prof_mark(c, MHD_AKCLASS_RECON);
-  c->launches += 2;
+  c->launches++;
 }
 
 // Transpose of stage s at the stage input Xs: the cotangent Aout of the
@@ -204,9 +213,32 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const Ingr5x3& ING, const F8& A
   prof_mark(c, MHD_AKCLASS_EDGE);
   CK(cudaMemsetAsync(a->Pb.q[0], 0, 8 * a->fe * sizeof(double), c->stream));
   c->launches += 4;
-  adj_dir<NDIM, RS, 0>(c, Xs, As, dt);
-  adj_dir<NDIM, RS, 1>(c, Xs, As, dt);
-  if constexpr (NDIM == 3) adj_dir<NDIM, RS, 2>(c, Xs, As, dt);
+  if (split_now(c)) {  // the directions' Riemann transposes side by side (small grids)
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0);
+    adj_riemann_dir<NDIM, RS, 1>(c, Xs, As, dt, c->aux[0]);
+    cudaEventRecord(c->ev_join[0], c->aux[0]);
+    if constexpr (NDIM == 3) {
+      cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0);
+      adj_riemann_dir<NDIM, RS, 2>(c, Xs, As, dt, c->aux[1]);
+      cudaEventRecord(c->ev_join[1], c->aux[1]);
+    }
+    adj_riemann_dir<NDIM, RS, 0>(c, Xs, As, dt, c->stream);
+    cudaStreamWaitEvent(c->stream, c->ev_join[0], 0);
+    if constexpr (NDIM == 3) cudaStreamWaitEvent(c->stream, c->ev_join[1], 0);
+    adj_recon_dir<NDIM, 0>(c);
+    adj_recon_dir<NDIM, 1>(c);
+    if constexpr (NDIM == 3) adj_recon_dir<NDIM, 2>(c);
+  } else {
+    adj_riemann_dir<NDIM, RS, 0>(c, Xs, As, dt, c->stream);
+    adj_recon_dir<NDIM, 0>(c);
+    adj_riemann_dir<NDIM, RS, 1>(c, Xs, As, dt, c->stream);
+    adj_recon_dir<NDIM, 1>(c);
+    if constexpr (NDIM == 3) {
+      adj_riemann_dir<NDIM, RS, 2>(c, Xs, As, dt, c->stream);
+      adj_recon_dir<NDIM, 2>(c);
+    }
+  }
   adj_c2p_cells_kernel<NDIM><<<blocks_for(prim_work<NDIM>(g), 256), 256, 0, c->stream>>>(g, Xs, c->P, a->Pb, As);
   long long pad = (long long)g.ext[0] * g.ext[1] * g.ext[2];
   adj_c2p_faces_kernel<NDIM><<<blocks_for(pad, 256), 256, 0, c->stream>>>(g, a->Pb, As);
