@@ -538,7 +538,6 @@ def run_ensemble(args):
     stream = torch.cuda.Stream(device=dev)
     host = [{k: torch.from_numpy(v).pin_memory() for k, v in st.items()} for _, st in cases]
     h2d = sum(v.numel() * 8 for h in host for v in h.values())
-    out_host = [{k: torch.empty_like(v).pin_memory() for k, v in h.items()} for h in host]
     del cases
 
     def barrier():
@@ -608,29 +607,29 @@ def run_ensemble(args):
     del sims
 
     # end to end: every run's state in from pinned host memory, one step, every
-    # state out.  Three batches on three streams take the steps in turn, each
-    # step after the previous one: while one batch steps, the previous one's
-    # states are read out and the next one's are written (with two, the host
-    # could only refill a batch after reading it, so the two copies ran in series).
+    # state out, all runs as one packed array (one copy and one scatter or
+    # gather kernel each way).  Three batches on three streams take the steps in
+    # turn, each step after the previous one: while one batch steps, the next
+    # one's states are written and the previous one's read out.
     streams = (stream, torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev))
     bts = (bt, mhd.Batch(cfgs, stream=streams[1].cuda_stream), mhd.Batch(cfgs, stream=streams[2].cuda_stream))
     for b in bts[1:]:
         b.set_seglen(*seg)
+    in_packed = bt.pack(host, out=torch.empty(bt.packed_size(), dtype=torch.float64).pin_memory())
+    out_packed = torch.empty(bt.packed_size(), dtype=torch.float64).pin_memory()
+    assert in_packed.numel() * 8 == h2d
     for b in bts:
-        for r, h in enumerate(host):
-            b.set_conserved(r, h)
+        b.set_conserved_packed(in_packed)
         b.step(1)                      # captures the step graph
+        b.get_conserved_packed(out_packed)
     torch.cuda.synchronize(dev)
     e2e_steps = max(3, min(args.steps, 10))
 
     def write(b):
-        for r, h in enumerate(host):
-            b.set_conserved(r, h)
+        b.set_conserved_packed(in_packed)
 
     def read(b):
-        for r, o in enumerate(out_host):
-            b.get_conserved(r, o, wait=False)
-        b.synchronize()                # one wait for all runs' copies
+        b.get_conserved_packed(out_packed)   # waits for its copy
 
     t0 = time.perf_counter()
     write(bts[0])
@@ -650,7 +649,7 @@ def run_ensemble(args):
     el = job_time_ms(time.perf_counter() - t0, world, dev)
     e2e = {"value": ncell * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d, "steps": e2e_steps,
-           "pipeline": "three batches in turn, steps in order; one's copies in and another's out overlap the third's step"}
+           "pipeline": "packed I/O; three batches in turn, steps in order; one's copies in and another's out overlap the third's step"}
     for b in bts[1:]:
         b.close()
 

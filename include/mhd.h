@@ -230,6 +230,20 @@ int mhd_batch_get_conserved_async(mhd_batch* b, int run, int mem, double* const*
 /* Wait until the batch's queued work and copies are done.  Sync. */
 int mhd_batch_synchronize(mhd_batch* b);
 
+/* Packed state I/O: the states of all runs as one contiguous array of
+ * mhd_batch_packed_size(b) doubles -- run 0's 8 slots (rho, mx, my, mz, E,
+ * B[0], B[1], B[2], each in the layout of mhd_batch_set_conserved, x
+ * fastest), then run 1's, and so on.  One copy and one scatter (gather)
+ * kernel replace 8 copies per run.  A host array is staged through a device
+ * buffer of that size, allocated on first use (the call then waits for it);
+ * a device array is read or written in place.  Setting resets every run's
+ * time and counters.  Both calls are async: keep the array unchanged (set)
+ * or unread (get) until mhd_batch_synchronize returns; host arrays should be
+ * pinned. */
+long long mhd_batch_packed_size(const mhd_batch* b);
+int mhd_batch_set_conserved_packed(mhd_batch* b, int mem, const double* packed);
+int mhd_batch_get_conserved_packed(mhd_batch* b, int mem, double* packed);
+
 /* Advance every run nsteps steps, each run with its own CFL dt computed on the
  * device.  Every run must have a state (MHD_ERR_STATE).  Async. */
 int mhd_batch_step(mhd_batch* b, int nsteps);

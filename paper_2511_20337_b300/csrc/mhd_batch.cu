@@ -46,6 +46,10 @@ struct mhd_batch {
   // the ghost shell of U^n matches its interior (set by a read-out's ghost
   // fill, cleared by anything that changes U^n)
   bool u0_ghosts_fresh = false;
+  // packed state I/O: run r's slots start at pack_off[r] (nruns+1 entries)
+  std::vector<long long> pack_off;
+  long long* pack_off_d = nullptr;
+  double* pack_stage = nullptr;  // device staging of host packed arrays (first use)
   // profiling: an event after every launch, tagged with its kernel class
   bool prof_on = false;
   int prof_n = 0;
@@ -224,6 +228,50 @@ void batch_ghost_u0(mhd_batch* b) {
     }
 }
 
+// Packed state I/O: one thread per element of the packed array; its run by
+// binary search over the run offsets, then its slot and dense index, then
+// the padded cell (the mapping of copy_field).
+__device__ __forceinline__ int pack_run(const long long* __restrict__ off, int nruns, long long id) {
+  int lo = 0, hi = nruns;  // off[lo] <= id < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= id) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+template <bool TO_FIELDS>
+__global__ void batch_pack_kernel(const RunDev* __restrict__ runs, const long long* __restrict__ off, int nruns,
+                                  double* pack) {
+  const long long total = off[nruns];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int r = pack_run(off, nruns, id);
+    const RunDev& R = runs[r];
+    long long l = id - off[r];
+    int q = 0, e[3];
+    for (; q < 8; q++) {
+      slot_extents(R.g, q, e);
+      const long long nq = (long long)e[0] * e[1] * e[2];
+      if (l < nq) break;
+      l -= nq;
+    }
+    const int li = (int)l;  // a slot of one run holds fewer than 2^31 elements
+    const int t = li / e[0];
+    const int c = R.g.at(li - t * e[0], t % e[1], t / e[1]);
+    if (TO_FIELDS) R.U[0].q[q][c] = pack[id];
+    else pack[id] = R.U[0].q[q][c];
+  }
+}
+// Reset every run's device scalars (bad_cell starts at the largest index).
+__global__ void batch_reset_scalars_kernel(DevScalars* sc, int nruns) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nruns) return;
+  DevScalars z{};
+  z.bad_cell = LLONG_MAX;
+  sc[r] = z;
+}
+
 bool same_scheme(const mhd_config& a, const mhd_config& c) {
   if (a.ndim != c.ndim || a.recon != c.recon || a.riemann != c.riemann || a.rk != c.rk) return false;
   for (int s = 0; s < 2 * a.ndim; s++)
@@ -294,7 +342,83 @@ int mhd_batch_create(int nruns, const mhd_config* cfgs, mhd_batch** out) {
   int rc = build_tables(b);  // synchronises the stream (hs lives on this frame)
   if (rc) { mhd_batch_destroy(b); return rc; }
   b->has_state.assign(nruns, 0);
+  // packed I/O offsets: run r's 8 slots in the layout of mhd_batch_set_conserved
+  b->pack_off.assign(nruns + 1, 0);
+  for (int r = 0; r < nruns; r++) {
+    long long n = 0;
+    for (int q = 0; q < 8; q++) {
+      int e[3];
+      slot_extents(b->runs[r].g, q, e);
+      n += (long long)e[0] * e[1] * e[2];
+    }
+    b->pack_off[r + 1] = b->pack_off[r] + n;
+  }
+  if (cudaMalloc(&b->pack_off_d, sizeof(long long) * (nruns + 1)) != cudaSuccess ||
+      cudaMemcpy(b->pack_off_d, b->pack_off.data(), sizeof(long long) * (nruns + 1), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    mhd_batch_destroy(b);
+    return MHD_ERR_OOM;
+  }
   *out = b;
+  return MHD_OK;
+}
+
+long long mhd_batch_packed_size(const mhd_batch* b) { return b ? b->pack_off[b->nruns] : -1; }
+
+namespace {
+// The device array a packed transfer reads or writes: the caller's device
+// array, or the staging buffer for a host one (allocated on first use).
+int pack_target(mhd_batch* b, int mem, const double* user, double** dev) {
+  if (mem == MHD_MEM_DEVICE) {
+    *dev = const_cast<double*>(user);
+    return MHD_OK;
+  }
+  if (!b->pack_stage && cudaMalloc(&b->pack_stage, sizeof(double) * b->pack_off[b->nruns]) != cudaSuccess) {
+    cudaGetLastError();
+    b->pack_stage = nullptr;
+    return MHD_ERR_OOM;
+  }
+  *dev = b->pack_stage;
+  return MHD_OK;
+}
+int pack_blocks(const mhd_batch* b) {
+  const long long n = b->pack_off[b->nruns];
+  const long long nb = (n + 255) / 256;
+  return (int)(nb < 65535LL * 64 ? nb : 65535LL * 64);
+}
+}  // namespace
+
+int mhd_batch_set_conserved_packed(mhd_batch* b, int mem, const double* packed) {
+  if (!b || !packed || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE)) return MHD_ERR_ARG;
+  double* src = nullptr;
+  int rc = pack_target(b, mem, packed, &src);
+  if (rc) return rc;
+  if (mem == MHD_MEM_HOST)
+    CK(cudaMemcpyAsync(src, packed, sizeof(double) * b->pack_off[b->nruns], cudaMemcpyHostToDevice, b->stream));
+  batch_pack_kernel<true><<<pack_blocks(b), 256, 0, b->stream>>>(b->runs_d, b->pack_off_d, b->nruns, src);
+  batch_reset_scalars_kernel<<<(b->nruns + 255) / 256, 256, 0, b->stream>>>(b->sc, b->nruns);
+  CK(cudaGetLastError());
+  b->has_state.assign(b->nruns, 1);
+  b->u0_ghosts_fresh = false;
+  return MHD_OK;
+}
+
+int mhd_batch_get_conserved_packed(mhd_batch* b, int mem, double* packed) {
+  if (!b || !packed || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE)) return MHD_ERR_ARG;
+  for (int r = 0; r < b->nruns; r++)
+    if (!b->has_state[r]) return MHD_ERR_STATE;
+  double* dst = nullptr;
+  int rc = pack_target(b, mem, packed, &dst);
+  if (rc) return rc;
+  if (!b->u0_ghosts_fresh) {
+    batch_ghost_u0(b);
+    b->u0_ghosts_fresh = true;
+  }
+  batch_pack_kernel<false><<<pack_blocks(b), 256, 0, b->stream>>>(b->runs_d, b->pack_off_d, b->nruns, dst);
+  CK(cudaGetLastError());
+  if (mem == MHD_MEM_HOST)
+    CK(cudaMemcpyAsync(packed, dst, sizeof(double) * b->pack_off[b->nruns], cudaMemcpyDeviceToHost, b->stream));
   return MHD_OK;
 }
 
@@ -302,6 +426,8 @@ int mhd_batch_destroy(mhd_batch* b) {
   if (!b) return MHD_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graph(b);
+  cudaFree(b->pack_off_d);
+  cudaFree(b->pack_stage);
   cudaFree(b->pool);
   cudaFree(b->sc);
   cudaFree(b->runs_d);

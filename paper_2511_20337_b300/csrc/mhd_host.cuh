@@ -127,7 +127,7 @@ inline int copy_field(const Grid& g, cudaStream_t stream, double* field, const d
 
 // Extents of state slot q in the boundary layout: cells, or the staggered
 // face fields of the CT scheme (slots 5..7; cell arrays with GLM).
-inline void slot_extents(const Grid& g, int slot, int e[3]) {
+__host__ __device__ inline void slot_extents(const Grid& g, int slot, int e[3]) {
   e[0] = g.n[0];
   e[1] = g.n[1];
   e[2] = g.n[2];

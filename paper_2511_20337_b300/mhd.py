@@ -37,7 +37,8 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
            "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen",
-           "mhd_batch_get_conserved_async", "mhd_batch_synchronize")
+           "mhd_batch_get_conserved_async", "mhd_batch_synchronize", "mhd_batch_packed_size",
+           "mhd_batch_set_conserved_packed", "mhd_batch_get_conserved_packed")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -95,6 +96,9 @@ def lib():
             "mhd_batch_get_conserved": (I, [P, I, I, DPP, DPP]),
             "mhd_batch_get_conserved_async": (I, [P, I, I, DPP, DPP]),
             "mhd_batch_synchronize": (I, [P]),
+            "mhd_batch_packed_size": (ctypes.c_longlong, [P]),
+            "mhd_batch_set_conserved_packed": (I, [P, I, P]),
+            "mhd_batch_get_conserved_packed": (I, [P, I, P]),
             "mhd_batch_step": (I, [P, I]),
             "mhd_batch_autotune": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
             "mhd_batch_set_seglen": (I, [P, I, I]),
@@ -176,6 +180,20 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data)
 
 
+def _host_arrays(arrs, shapes):
+    """Host arrays as the library reads them: C-contiguous float64 of the slot
+    shapes.  Contiguous float64 CPU tensors of the right size are passed as
+    they are (no conversion); anything else goes through numpy."""
+    out = []
+    for a, s in zip(arrs, shapes):
+        if hasattr(a, "data_ptr") and str(a.dtype) == "torch.float64" and a.is_contiguous() \
+                and a.numel() == int(np.prod(s)):
+            out.append(a)
+        else:
+            out.append(np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(s)))
+    return out
+
+
 def _ptr_array(arrs):
     out = (ctypes.c_void_p * len(arrs))()
     for i, a in enumerate(arrs):
@@ -222,8 +240,7 @@ class Sim:
         arrs = [state[k] for k in keys]
         dev = _is_device(arrs[0])
         if not dev:
-            arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(s)) for a, s in
-                    zip(arrs, self.shapes)]
+            arrs = _host_arrays(arrs, self.shapes)
         self._keep = arrs
         U = _ptr_array(arrs[:5])
         B = _ptr_array(arrs[5:])
@@ -480,8 +497,7 @@ class Batch:
         arrs = [state[k] for k in KEYS]
         dev = _is_device(arrs[0])
         if not dev:
-            arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(s)) for a, s in
-                    zip(arrs, self.shapes[run])]
+            arrs = _host_arrays(arrs, self.shapes[run])
         self._keep[run] = arrs
         _check(lib().mhd_batch_set_conserved(self.h, run, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
                                              _ptr_array(arrs[5:])), "mhd_batch_set_conserved")
@@ -502,9 +518,66 @@ class Batch:
         return out
 
     def synchronize(self):
-        """Wait for the queued work and copies (get_conserved(wait=False))."""
+        """Wait for the queued work and copies (get_conserved(wait=False), the packed calls)."""
         _check(lib().mhd_batch_synchronize(self.h), "mhd_batch_synchronize")
         self._pending = []
+
+    # ---- packed state I/O: every run's 8 slots in one contiguous array ----
+    def packed_size(self):
+        return int(lib().mhd_batch_packed_size(self.h))
+
+    def pack(self, states, out=None):
+        """The packed array of a list of per-run states (KEYS layout): numpy,
+        or written into `out` (e.g. a pinned CPU tensor)."""
+        out = np.empty(self.packed_size()) if out is None else out
+        flat = out if isinstance(out, np.ndarray) else out.numpy()
+        o = 0
+        for st, shapes in zip(states, self.shapes):
+            for k, s in zip(KEYS, shapes):
+                n = int(np.prod(s))
+                flat[o:o + n] = np.asarray(st[k], dtype=np.float64).reshape(-1)
+                o += n
+        return out
+
+    def unpack(self, packed):
+        """Per-run state dicts (numpy views) of a packed array."""
+        flat = np.asarray(packed.cpu() if hasattr(packed, "cpu") else packed).reshape(-1)
+        out, o = [], 0
+        for shapes in self.shapes:
+            d = {}
+            for k, s in zip(KEYS, shapes):
+                n = int(np.prod(s))
+                d[k] = flat[o:o + n].reshape(s)
+                o += n
+            out.append(d)
+        return out
+
+    def set_conserved_packed(self, packed):
+        """Set every run's state from one packed array (numpy, CPU tensor --
+        pinned for an overlapped copy -- or CUDA tensor).  Async: keep it
+        unchanged until synchronize()."""
+        if int(np.prod(packed.shape)) != self.packed_size():
+            raise ValueError("packed array of the wrong size")
+        dev = _is_device(packed)
+        self._keep["packed"] = packed
+        _check(lib().mhd_batch_set_conserved_packed(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr(packed)),
+               "mhd_batch_set_conserved_packed")
+
+    def get_conserved_packed(self, out=None, wait=True):
+        """Every run's state into one packed array (new numpy array, or `out`:
+        a pinned CPU tensor or a CUDA tensor for wait=False)."""
+        if out is None:
+            out = np.empty(self.packed_size())
+        if int(np.prod(out.shape)) != self.packed_size():
+            raise ValueError("packed array of the wrong size")
+        dev = _is_device(out)
+        _check(lib().mhd_batch_get_conserved_packed(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr(out)),
+               "mhd_batch_get_conserved_packed")
+        if wait:
+            self.synchronize()
+        else:
+            self._pending.append(out)
+        return out
 
     def step(self, nsteps):
         _check(lib().mhd_batch_step(self.h, int(nsteps)), "mhd_batch_step")

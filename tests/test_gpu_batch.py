@@ -155,3 +155,43 @@ def test_staged_x_sweep_equals_direct_loads_bitwise(mhd, case):
             assert np.max(np.abs(out[k] - ref[k])) <= 1e-12 * bmax, k
         else:
             assert relerr(out[k], ref[k]) <= 1e-12, k
+
+
+def test_packed_io_equals_per_run_io(mhd):
+    """Packed state I/O (one array for all runs) against the per-run calls,
+    host and device arrays, bitwise; a step after a packed set equals a step
+    after per-run sets."""
+    torch = pytest.importorskip("torch")
+    cases = ensemble([12, 16, 20, 14])
+    cfgs = [c for c, _ in cases]
+    states = [s for _, s in cases]
+    a = mhd.Batch(cfgs, states)
+    b = mhd.Batch(cfgs)
+    packed = b.pack(states)
+    assert packed.size == b.packed_size()
+    b.set_conserved_packed(packed)
+    b.synchronize()
+    for r in range(len(cases)):
+        got = b.get_conserved(r)
+        for k in KEYS:
+            assert np.array_equal(got[k], states[r][k]), (r, k)
+    a.step(2)
+    b.step(2)
+    out = b.unpack(b.get_conserved_packed())
+    for r in range(len(cases)):
+        want = a.get_conserved(r)
+        for k in KEYS:
+            assert np.array_equal(out[r][k], want[k]), (r, k)
+    # device packed arrays, and a pinned host array read without waiting
+    d = torch.from_numpy(packed).cuda()
+    b.set_conserved_packed(d)
+    b.step(2)
+    dev_out = torch.empty_like(d)
+    b.get_conserved_packed(dev_out, wait=False)
+    pin = torch.empty(b.packed_size(), dtype=torch.float64).pin_memory()
+    b.get_conserved_packed(pin, wait=False)
+    b.synchronize()
+    assert np.array_equal(dev_out.cpu().numpy(), pin.numpy())
+    assert np.array_equal(pin.numpy(), a.pack([a.get_conserved(r) for r in range(len(cases))]))
+    with pytest.raises(ValueError):
+        b.set_conserved_packed(np.zeros(3))
