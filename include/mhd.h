@@ -135,6 +135,12 @@ int mhd_advance(mhd_ctx* ctx, int nsteps);
 /* Simulation time (sum of the dt of all steps since the last set).  Sync. */
 int mhd_get_time(mhd_ctx* ctx, double* t_out);
 
+/* Set the simulation time (after mhd_set_conserved, which resets it to 0):
+ * with mhd_get_conserved and mhd_get_time this checkpoints a run and resumes
+ * it, the resumed steps equal to the bit to those of the uninterrupted run.
+ * t must not be NaN.  Async. */
+int mhd_set_time(mhd_ctx* ctx, double t);
+
 /* dt of the last step taken by mhd_advance (or given to mhd_step).  Sync. */
 int mhd_last_dt(mhd_ctx* ctx, double* dt_out);
 

@@ -613,6 +613,13 @@ int mhd_advance(mhd_ctx* c, int nsteps) {
   return MHD_OK;
 }
 
+int mhd_set_time(mhd_ctx* c, double t) {
+  if (!c || !(t == t)) return MHD_ERR_ARG;
+  set_time_kernel<<<1, 1, 0, c->stream>>>(c->sc, t);
+  CK(cudaGetLastError());
+  return MHD_OK;
+}
+
 int mhd_get_time(mhd_ctx* c, double* t_out) {
   if (!c || !t_out) return MHD_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));

@@ -38,7 +38,7 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
            "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen",
            "mhd_batch_get_conserved_async", "mhd_batch_synchronize", "mhd_batch_packed_size",
-           "mhd_batch_set_conserved_packed", "mhd_batch_get_conserved_packed")
+           "mhd_batch_set_conserved_packed", "mhd_batch_get_conserved_packed", "mhd_set_time")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -97,6 +97,7 @@ def lib():
             "mhd_batch_get_conserved_async": (I, [P, I, I, DPP, DPP]),
             "mhd_batch_synchronize": (I, [P]),
             "mhd_batch_packed_size": (ctypes.c_longlong, [P]),
+            "mhd_set_time": (I, [P, D]),
             "mhd_batch_set_conserved_packed": (I, [P, I, P]),
             "mhd_batch_get_conserved_packed": (I, [P, I, P]),
             "mhd_batch_step": (I, [P, I]),
@@ -326,6 +327,10 @@ class Sim:
         t = ctypes.c_double()
         _check(lib().mhd_get_time(self.h, ctypes.byref(t)), "mhd_get_time")
         return t.value
+
+    @time.setter
+    def time(self, t):
+        _check(lib().mhd_set_time(self.h, float(t)), "mhd_set_time")
 
     @property
     def last_dt(self):

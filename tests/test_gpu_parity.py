@@ -312,3 +312,28 @@ def test_default_segment_length_and_setter(mhd, n):
     assert sim.seglen == 7
     with pytest.raises(mhd.MhdError):
         sim.set_seglen(0)
+
+
+@pytest.mark.parametrize("divb", ["ct", "glm"])
+def test_checkpoint_and_resume_equals_uninterrupted_run(mhd, divb):
+    """Save the state and time after 4 CFL steps, resume in a new context and
+    take 3 more: the state and time equal those of 7 uninterrupted steps."""
+    cfg, st = W.orszag_tang_2d(48, recon="wenoz", rk=3)
+    if divb == "glm":
+        cfg, st = W.to_glm(cfg, st)
+    a = mhd.Sim(cfg, st)
+    a.advance(7)
+    want, t_want = a.get_conserved(), a.time
+    b = mhd.Sim(cfg, st)
+    b.advance(4)
+    saved, t_saved = b.get_conserved(), b.time
+    b.close()
+    c = mhd.Sim(cfg, saved)
+    c.time = t_saved
+    c.advance(3)
+    got = c.get_conserved()
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
+    assert c.time == t_want
+    with pytest.raises(mhd.MhdError):
+        c.time = float("nan")
