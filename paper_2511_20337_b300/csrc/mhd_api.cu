@@ -613,6 +613,13 @@ int mhd_advance(mhd_ctx* c, int nsteps) {
   return MHD_OK;
 }
 
+}  // extern "C"
+
+// Set the simulation time (a resumed run).
+static __global__ void set_time_kernel(DevScalars* sc, double t) { sc->time = t; }
+
+extern "C" {
+
 int mhd_set_time(mhd_ctx* c, double t) {
   if (!c || !(t == t)) return MHD_ERR_ARG;
   set_time_kernel<<<1, 1, 0, c->stream>>>(c->sc, t);

@@ -409,9 +409,6 @@ static __global__ void __launch_bounds__(256) cfl_exact_kernel(Grid g, F8 P, con
   cfl_block_finish(lam_max, sc, g.cfl, gridDim.x);
 }
 
-// Set the simulation time (a resumed run).
-static __global__ void set_time_kernel(DevScalars* sc, double t) { sc->time = t; }
-
 // Set the step size from the host value (mhd_step) and add it to the time.
 static __global__ void set_dt_kernel(DevScalars* sc, double dt) {
   sc->dt = dt;
