@@ -251,3 +251,44 @@ def test_adjoint2d_256_400_steps_central_differences():
         assert min(errs) <= 1e-5, (errs, dot)
     finally:
         sim.close()
+
+
+def div_b(cfg, st):
+    """Largest |discrete div B| of the face field, relative to max |B| / dx."""
+    n = cfg["n"]
+    dx = [(cfg["x1"][d] - cfg["x0"][d]) / n[d] for d in range(3)]
+    d = (np.diff(st["b0"], axis=2) / dx[0] + np.diff(st["b1"], axis=1) / dx[1] + np.diff(st["b2"], axis=0) / dx[2])
+    bmax = max(np.max(np.abs(st[k])) for k in ("b0", "b1", "b2"))
+    return float(np.max(np.abs(d))) / (bmax / min(dx))
+
+
+@pytest.mark.parametrize("name,nsteps", [("turbulent3d-256", 50), ("orszag-tang3d-704", 3)])
+def test_conservation_and_div_b_at_full_size(name, nsteps):
+    """Many CFL steps of a full-size periodic workload, launched as the
+    benchmark launches them: the totals of rho, m and E stay put to
+    round-off (1e-12 of the sum of magnitudes) and the discrete div B of the
+    face field stays at its initial round-off level (constrained transport)."""
+    if name == "turbulent3d-256":
+        cfg, st = W.turbulent_3d(256)
+    else:
+        cfg, st = W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    devs = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in st.items()}
+    sim = mhd.Sim(cfg, devs, stream=stream.cuda_stream)
+    try:
+        if cells(cfg) <= 256 ** 3:
+            sim.autotune()
+        sim.advance(nsteps)
+        out = sim.get_conserved()
+        rc, bad = sim.status()
+        assert rc == 0, (rc, bad)
+    finally:
+        sim.close()
+        del devs
+        torch.cuda.empty_cache()
+    for k in ("rho", "mx", "my", "mz", "E"):
+        scale = max(np.sum(np.abs(st[k])), np.sum(np.abs(out[k])))
+        assert abs(np.sum(out[k]) - np.sum(st[k])) <= 1e-12 * scale, k
+    d0, d1 = div_b(cfg, st), div_b(cfg, out)
+    assert d1 <= max(10 * d0, 1e-12), (d0, d1)
