@@ -19,6 +19,7 @@ from . import build as _build
 RECON = {"plm": 0, "wenoz": 1, "ppm": 2}
 RIEMANN = {"hll": 0, "hlld": 1}
 BC = {"periodic": 0, "outflow": 1}
+EMF = {"uct_hll": 0, "uct_hlld": 1}
 KEYS = ("rho", "mx", "my", "mz", "E", "b0", "b1", "b2")
 PHASES = ("ghost", "c2p", "recon", "riemann", "fluxdiff", "emf", "ct", "rk", "cfl")
 OPS = ("add", "mul", "div", "sqrt")
@@ -28,7 +29,8 @@ class OrcConfig(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("x0", ctypes.c_double * 3), ("x1", ctypes.c_double * 3), ("gamma", ctypes.c_double),
                 ("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("rk", ctypes.c_int),
-                ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6), ("p_floor", ctypes.c_double)]
+                ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6), ("p_floor", ctypes.c_double),
+                ("emf", ctypes.c_int)]
 
 
 _lib = None
@@ -113,6 +115,7 @@ def make_config(cfg):
     for s in range(6):
         c.bc[s] = BC[cfg["bc"][s]]
     c.p_floor = cfg.get("p_floor", 0.0)
+    c.emf = EMF[cfg.get("emf", "uct_hll")]
     return c
 
 
@@ -274,13 +277,20 @@ class OracleGlm:
         return lib().orc_glm_fallbacks(self.h)
 
 
-def riemann(solver, wl, wr, bn, gamma):
-    """Riemann flux (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and UCT ingredients (a+, a-, d, uL, uR)."""
+def riemann(solver, wl, wr, bn, gamma, emf="uct_hll"):
+    """Riemann flux (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and UCT ingredients
+    (a^L, a^R, d^L, uL, uR, d^R); emf="uct_hlld" (HLLD only) gives the HLLD
+    solver's own weights instead of the HLL ones."""
     wl = np.ascontiguousarray(wl, dtype=np.float64)
     wr = np.ascontiguousarray(wr, dtype=np.float64)
     F = np.zeros(7)
-    ing = np.zeros(5)
-    lib().orc_riemann(RIEMANN[solver], _dp(wl), _dp(wr), float(bn), float(gamma), _dp(F), _dp(ing))
+    ing = np.zeros(6)
+    code = RIEMANN[solver]
+    if emf == "uct_hlld":
+        if solver != "hlld":
+            raise ValueError("UCT-HLLD ingredients need the HLLD solver")
+        code = 2
+    lib().orc_riemann(code, _dp(wl), _dp(wr), float(bn), float(gamma), _dp(F), _dp(ing))
     return F, ing
 
 

@@ -37,6 +37,9 @@ using std::sqrt;
 enum { RECON_PLM = 0, RECON_WENOZ = 1, RECON_PPM = 2 };
 enum { RS_HLL = 0, RS_HLLD = 1 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
+// Edge-field weights (the paper names the UCT-HLLD average for its benchmarks):
+// the UCT form with HLL coefficients, or with the HLLD solver's own coefficients.
+enum { EMF_UCT_HLL = 0, EMF_UCT_HLLD = 1 };
 
 // Thresholds of the degenerate HLLD branches (reading: the paper is silent).
 constexpr double HLLD_DEGEN_EPS = 1e-12;  // |D_a| below this * rho_a (S_a-u_a)(S_a-S_M)
@@ -52,6 +55,7 @@ struct Config {
   double cfl;
   int bc[6];  // x-, x+, y-, y+, z-, z+
   double p_floor;  // floor on the recovered pressure (0: none)
+  int emf;         // EMF_UCT_HLL or EMF_UCT_HLLD (needs the HLLD solver)
 };
 
 // For the branch signature, min/max of (nearly) equal arguments is one
@@ -122,8 +126,13 @@ enum { P_RHO = 0, P_VX, P_VY, P_VZ, P_BX, P_BY, P_BZ, P_PR, NP };
 // Reconstructed / Riemann variables in the frame of a sweep with normal n and
 // cyclic transverse directions t1 = (n+1)%3, t2 = (n+2)%3.
 enum { W_RHO = 0, W_VN, W_VT1, W_VT2, W_BT1, W_BT2, W_PR, NW };
-// Face ingredients kept for the UCT electric field (HLL weights and normal velocities).
-enum { I_AP = 0, I_AM, I_DD, I_UL, I_UR, NI };
+// Face ingredients kept for the UCT electric field: the weights a^L, a^R of the
+// two sides' induction fluxes, the dissipation coefficients d^L, d^R of their
+// transverse fields and the reconstructed normal velocities, such that the
+// flux of either transverse field component B_t at the face is
+//   a^L F_L + a^R F_R + d^L B_t,L - d^R B_t,R,   F = u B_t - v_t B_n.
+// UCT-HLL: a^L = a+, a^R = a-, d^L = d^R = d (I_DR repeats I_DD).
+enum { I_AP = 0, I_AM, I_DD, I_UL, I_UR, I_DR, NI };
 
 template <class R> using State = std::array<Field<R>, NQ>;
 
@@ -212,6 +221,7 @@ inline void signal_speeds(const R WL[NW], const R WR[NW], const SideState<R>& L,
   ing[I_DD] = -((aR * aL) * inv);
   ing[I_UL] = WL[W_VN];
   ing[I_UR] = WR[W_VN];
+  ing[I_DR] = ing[I_DD];
 }
 
 // HLL flux (Harten, Lax & van Leer; the dissipative form of the Riemann flux in §2.2):
@@ -232,13 +242,45 @@ inline void riemann_hll(const R WL[NW], const R WR[NW], R bn, double gamma, R F[
 // HLLD flux (Miyoshi & Kusano 2005), restated from its mathematics: five waves
 // S_L < S*_L < S_M < S*_R < S_R separating U_L, U*_L, U**_L, U**_R, U*_R, U_R;
 // normal velocity and total pressure continuous across the fan.
+//
+// With uct_hlld the UCT ingredients are the HLLD solver's own coefficients
+// (reading of the UCT-HLLD average; the paper cites it without formulas).
+// In every region of the fan the flux of a transverse field component B_t is
+// linear in the two sides' (v_t, B_t), with coefficients made of the wave
+// speeds, rho* and the star ratio e = B*_t / B_t (the same for both
+// components).  Written in the form a^L F_L + a^R F_R + d^L B_t,L - d^R B_t,R:
+//   0 <= S_L:              a^L = 1, a^R = 0, d^L = d^R = 0;
+//   S_L < 0 <= S*_L:       a^L = 1, a^R = 0, d^L = S_L (e_L - 1), d^R = 0;
+//   S*_L < 0 <= S*_R:      a^L = S*_R / (S*_R - S*_L), a^R = -S*_L / (S*_R - S*_L),
+//                          d^L = a^L ((S_L - S*_L) e_L - S_L),
+//                          d^R = a^R (S_R - (S_R - S*_R) e_R);
+//   S*_R < 0 <= S_R:       a^L = 0, a^R = 1, d^L = 0, d^R = S_R (1 - e_R);
+//   S_R < 0:               a^L = 0, a^R = 1, d^L = d^R = 0.
+// (The double-star row follows from the double-star transverse states, in
+// which v_t,L enters with weight -sgn(B_n) sqrt(rho*_L rho*_R) S*_R / (sqrt(rho*_L) + sqrt(rho*_R)),
+// i.e. -B_n a^L with S*_R - S*_L = |B_n| (1/sqrt(rho*_L) + 1/sqrt(rho*_R)).)
 template <class R>
-inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F[NW], R ing[NI]) {
+inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F[NW], R ing[NI],
+                         bool uct_hlld = false) {
   SideState<R> L = side_state(WL, bn, gamma), Rs = side_state(WR, bn, gamma);
   R SL, SR;
   signal_speeds(WL, WR, L, Rs, bn, gamma, SL, SR, ing);
-  if (SL > R(0.0)) { branch(31); for (int q = 0; q < NW; q++) F[q] = L.F[q]; return; }
-  if (SR < R(0.0)) { branch(32); for (int q = 0; q < NW; q++) F[q] = Rs.F[q]; return; }
+  auto set_weights = [&](R aL, R aR, R dL, R dR) {
+    if (!uct_hlld) return;
+    ing[I_AP] = aL; ing[I_AM] = aR; ing[I_DD] = dL; ing[I_DR] = dR;
+  };
+  if (SL > R(0.0)) {
+    branch(31);
+    for (int q = 0; q < NW; q++) F[q] = L.F[q];
+    set_weights(R(1.0), R(0.0), R(0.0), R(0.0));
+    return;
+  }
+  if (SR < R(0.0)) {
+    branch(32);
+    for (int q = 0; q < NW; q++) F[q] = Rs.F[q];
+    set_weights(R(0.0), R(1.0), R(0.0), R(0.0));
+    return;
+  }
 
   const R zero(0.0);
   R rhoL = WL[W_RHO], uL = WL[W_VN], rhoR = WR[W_RHO], uR = WR[W_VN];
@@ -249,7 +291,7 @@ inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F
   R pTs = (((sdR * rhoR) * L.pT - (sdL * rhoL) * Rs.pT) + ((rhoL * rhoR) * (sdR * sdL)) * (uR - uL)) / den;
 
   // Star states on each side.
-  struct Star { R rho, v, w, b1, b2, E, vB, S; };
+  struct Star { R rho, v, w, b1, b2, E, vB, S, e; };  // e = B*_t / B_t
   auto star = [&](const R W[NW], const SideState<R>& s, R S) {
     Star o;
     R rho = W[W_RHO], u = W[W_VN], v = W[W_VT1], w = W[W_VT2], b1 = W[W_BT1], b2 = W[W_BT2];
@@ -260,6 +302,7 @@ inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F
     if (fabs(D) < R(HLLD_DEGEN_EPS) * rsm) {
       branch(33);
       o.v = v; o.w = w; o.b1 = b1; o.b2 = b2;
+      o.e = R(1.0);
     } else {
       R invD = R(1.0) / D;
       R cv = (bn * (SM - u)) * invD;
@@ -268,6 +311,7 @@ inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F
       R cb = ((rho * sd) * sd - bn * bn) * invD;
       o.b1 = b1 * cb;
       o.b2 = b2 * cb;
+      o.e = cb;
     }
     o.vB = (SM * bn + o.v * o.b1) + o.w * o.b2;
     o.E = (((sd * s.E - s.pT * u) + pTs * SM) + bn * (s.vB - o.vB)) / sm;
@@ -321,6 +365,14 @@ inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F
     }
   } else {  // S*_R < 0 <= S_R
     for (int q = 0; q < NW; q++) F[q] = Rs.F[q] + SR * (UsR[q] - Rs.U[q]);
+  }
+  if (SsL >= zero) {
+    set_weights(R(1.0), zero, SL * (sL.e - R(1.0)), zero);
+  } else if (SsR >= zero) {  // only with rotational waves: S*_L < 0 <= S*_R
+    R aL = SsR / (SsR - SsL), aR = -SsL / (SsR - SsL);
+    set_weights(aL, aR, aL * ((SL - SsL) * sL.e - SL), aR * (SR - (SR - SsR) * sR.e));
+  } else {
+    set_weights(zero, R(1.0), zero, SR * (R(1.0) - sR.e));
   }
 }
 
@@ -438,6 +490,8 @@ template <class R> struct Sim {
   explicit Sim(const Config& cfg) : c(cfg) {
     ndim = cfg.ndim;
     if (ndim != 2 && ndim != 3) throw std::invalid_argument("ndim must be 2 or 3");
+    if (cfg.emf == EMF_UCT_HLLD && cfg.riemann != RS_HLLD)
+      throw std::invalid_argument("UCT-HLLD edge fields need the HLLD solver");
     G = cfg.recon == RECON_PLM ? 2 : 3;
     n[0] = cfg.nx; n[1] = cfg.ny; n[2] = ndim == 3 ? cfg.nz : 1;
     for (int d = 0; d < 3; d++) dx[d] = (cfg.x1[d] - cfg.x0[d]) / n[d];
@@ -644,7 +698,7 @@ template <class R> struct Sim {
             WR[q] = Wm[d][q](x[0], x[1], x[2]);
           }
           R bn = S[Q_B0 + d](x[0], x[1], x[2]);
-          if (c.riemann == RS_HLLD) riemann_hlld(WL, WR, bn, c.gamma, Fx, ing);
+          if (c.riemann == RS_HLLD) riemann_hlld(WL, WR, bn, c.gamma, Fx, ing, c.emf == EMF_UCT_HLLD);
           else riemann_hll(WL, WR, bn, c.gamma, Fx, ing);
           for (int q = 0; q < NW; q++) F[d][q](x[0], x[1], x[2]) = Fx[q];
           for (int q = 0; q < NI; q++) I[d][q](x[0], x[1], x[2]) = ing[q];
@@ -658,6 +712,9 @@ template <class R> struct Sim {
   // with the a-face ingredients averaged over the two a-faces touching the
   // edge, B_b^{W,E} the minmod reconstructions of the b-face field along a to
   // the edge from either side, and likewise for the b-faces.
+  // UCT-HLLD: the same form with the HLLD coefficients and separate d^L, d^R:
+  //   E_c = -(a^L_a u^W B_b^W + a^R_a u^E B_b^E) + (d^R_a B_b^E - d^L_a B_b^W)
+  //         + (a^L_b u^S B_a^S + a^R_b u^N B_a^N) - (d^R_b B_a^N - d^L_b B_a^S).
   R face_to_edge(Field<R>& B, int x[3], int along, bool from_minus) {
     // Field B sampled at x - e_along (from_minus) or x, reconstructed to the
     // edge plane between them with a minmod slope along `along`.
@@ -697,11 +754,18 @@ template <class R> struct Sim {
           R ddb = h * (I[b][I_DD](xa[0], xa[1], xa[2]) + I[b][I_DD](i, j, k));
           R vS = h * (I[b][I_UL](xa[0], xa[1], xa[2]) + I[b][I_UL](i, j, k));
           R vN = h * (I[b][I_UR](xa[0], xa[1], xa[2]) + I[b][I_UR](i, j, k));
+          R dra = h * (I[a][I_DR](xb[0], xb[1], xb[2]) + I[a][I_DR](i, j, k));
+          R drb = h * (I[b][I_DR](xa[0], xa[1], xa[2]) + I[b][I_DR](i, j, k));
           R BbW = face_to_edge(S[Q_B0 + b], x, a, true);
           R BbE = face_to_edge(S[Q_B0 + b], x, a, false);
           R BaS = face_to_edge(S[Q_B0 + a], x, b, true);
           R BaN = face_to_edge(S[Q_B0 + a], x, b, false);
-          R e = ((-(apa * uW * BbW + ama * uE * BbE) + dda * (BbE - BbW)) + (apb * vS * BaS + amb * vN * BaN)) -
+          R e;
+          if (c.emf == EMF_UCT_HLLD)
+            e = ((-(apa * uW * BbW + ama * uE * BbE) + (dra * BbE - dda * BbW)) + (apb * vS * BaS + amb * vN * BaN)) -
+                (drb * BaN - ddb * BaS);
+          else
+            e = ((-(apa * uW * BbW + ama * uE * BbE) + dda * (BbE - BbW)) + (apb * vS * BaS + amb * vN * BaN)) -
                 ddb * (BaN - BaS);
           E[cc](i, j, k) = e;
         }

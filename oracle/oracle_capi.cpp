@@ -59,6 +59,7 @@ struct OrcConfig {
   double cfl;
   int bc[6];
   double p_floor;
+  int emf;
 };
 
 static Config to_cfg(const OrcConfig* c) {
@@ -68,6 +69,7 @@ static Config to_cfg(const OrcConfig* c) {
   o.gamma = c->gamma; o.recon = c->recon; o.riemann = c->riemann; o.rk = c->rk; o.cfl = c->cfl;
   for (int s = 0; s < 6; s++) o.bc[s] = c->bc[s];
   o.p_floor = c->p_floor;
+  o.emf = c->emf;
   return o;
 }
 
@@ -235,8 +237,9 @@ double orc_cfl_dt_state(const OrcConfig* cfg, const double* const* a) {
 }
 
 // ---- pointwise pieces ----
+// solver: RS_HLL, RS_HLLD, or 2 = HLLD with the UCT-HLLD ingredients; ing has NI entries.
 void orc_riemann(int solver, const double* wl, const double* wr, double bn, double gamma, double* F, double* ing) {
-  if (solver == RS_HLLD) riemann_hlld<double>(wl, wr, bn, gamma, F, ing);
+  if (solver == RS_HLLD || solver == 2) riemann_hlld<double>(wl, wr, bn, gamma, F, ing, solver == 2);
   else riemann_hll<double>(wl, wr, bn, gamma, F, ing);
 }
 void orc_side_flux(const double* w, double bn, double gamma, double* F, double* U) {

@@ -23,11 +23,12 @@ GAMMA = 5.0 / 3.0
 
 
 def base_cfg(ndim, n, x0, x1, *, gamma=GAMMA, recon="plm", riemann="hlld", rk=2, cfl=0.4, bc="periodic",
-             p_floor=0.0):
+             p_floor=0.0, emf="uct_hll"):
     if isinstance(bc, str):
         bc = [bc] * 6
     return {"ndim": ndim, "n": tuple(n), "x0": tuple(x0), "x1": tuple(x1), "gamma": gamma,
-            "recon": recon, "riemann": riemann, "rk": rk, "cfl": cfl, "bc": list(bc), "p_floor": p_floor}
+            "recon": recon, "riemann": riemann, "rk": rk, "cfl": cfl, "bc": list(bc), "p_floor": p_floor,
+            "emf": emf}
 
 
 def _grid(cfg):

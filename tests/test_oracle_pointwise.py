@@ -215,7 +215,8 @@ def test_hll_matches_two_wave_formula():
             expect = (SR * FL - SL * FR + SL * SR * (UR - UL)) / (SR - SL)
         np.testing.assert_allclose(F, expect, rtol=1e-12, atol=1e-12)
         aR, aL = max(0.0, SR), min(0.0, SL)
-        np.testing.assert_allclose(ing, [aR / (aR - aL), -aL / (aR - aL), -aR * aL / (aR - aL), wl[1], wr[1]],
+        d = -aR * aL / (aR - aL)
+        np.testing.assert_allclose(ing, [aR / (aR - aL), -aL / (aR - aL), d, wl[1], wr[1], d],
                                    rtol=1e-14, atol=1e-15)
 
 

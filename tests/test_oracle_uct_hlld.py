@@ -1,0 +1,277 @@
+"""Oracle pins of the UCT-HLLD edge field (the edge-field average the paper
+names for its benchmarks, §4.1): the HLLD solver's own weights a^L, a^R, d^L,
+d^R must reproduce the solver's flux of both transverse field components in
+every region of the wave fan; identical states give a^L + a^R = 1 and
+d^L = d^R (so a uniform state's edge field is -(v x B)); a plane-parallel
+problem with B_n = 0 evolves the staggered B_y by CT exactly as the
+finite-volume cell B_z (which the UCT-HLL weights do not); and the scheme with
+these weights conserves, keeps div B at round-off, commutes with rotations and
+converges at second order (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_20337_b300 import workloads as W
+from conftest import relerr
+
+G = 5.0 / 3.0
+KEYS = oracle.KEYS
+
+
+def random_pair(rng, trial):
+    """Sweep-frame primitive pairs (rho, u, v, w, B_t1, B_t2, p) spanning the
+    wave-fan regions: supersonic both ways, strong and weak jumps, near-equal
+    sides and a nearly vanishing normal field."""
+    scale = 10 ** rng.uniform(-2, 1)
+
+    def side():
+        return np.array([10 ** rng.uniform(-1, 1), 2 * rng.normal(), rng.normal(), rng.normal(),
+                         scale * rng.normal(), scale * rng.normal(), 10 ** rng.uniform(-2, 1)])
+
+    wl, wr = side(), side()
+    if trial % 3 == 0:
+        wr = wl + 0.01 * rng.normal(size=7) * np.abs(wl)
+    if trial % 7 == 0:  # supersonic flow to either side
+        shift = (8.0 + 4.0 * rng.uniform()) * (1 if trial % 2 else -1) * max(1.0, scale)
+        wl[1] += shift
+        wr[1] += shift
+    bn = scale * rng.normal() * (10 ** rng.uniform(-7, 0) if trial % 5 == 0 else 1.0)
+    return wl, wr, bn
+
+
+def region(ing):
+    aL, aR, dL, dR = ing[0], ing[1], ing[2], ing[5]
+    if aR == 0.0 and aL == 1.0:
+        return "left" if dL == 0.0 else "star-left"
+    if aL == 0.0 and aR == 1.0:
+        return "right" if dR == 0.0 else "star-right"
+    return "double-star"
+
+
+def test_weights_reproduce_hlld_transverse_flux():
+    """F_t = a^L (u_L B_t,L - B_n v_t,L) + a^R (u_R B_t,R - B_n v_t,R)
+    + d^L B_t,L - d^R B_t,R for t = 1, 2, to 1e-13 of the terms' size, in
+    every region of the HLLD fan."""
+    rng = np.random.default_rng(2511)
+    seen = {}
+    for trial in range(6000):
+        wl, wr, bn = random_pair(rng, trial)
+        F, ing = oracle.riemann("hlld", wl, wr, bn, G, emf="uct_hlld")
+        F_hll, ing_hll = oracle.riemann("hlld", wl, wr, bn, G)
+        np.testing.assert_array_equal(F, F_hll)  # the weights do not touch the flux
+        np.testing.assert_array_equal(ing[3:5], ing_hll[3:5])  # normal velocities
+        aL, aR, dL, dR = ing[0], ing[1], ing[2], ing[5]
+        assert aL + aR == pytest.approx(1.0, abs=1e-14)
+        assert -1e-15 <= aL <= 1.0 + 1e-15
+        r = region(ing)
+        seen[r] = seen.get(r, 0) + 1
+        for iB, iv in ((4, 2), (5, 3)):
+            FL = wl[1] * wl[iB] - bn * wl[iv]
+            FR = wr[1] * wr[iB] - bn * wr[iv]
+            dec = aL * FL + aR * FR + dL * wl[iB] - dR * wr[iB]
+            size = abs(aL * FL) + abs(aR * FR) + abs(dL * wl[iB]) + abs(dR * wr[iB]) + abs(F[iB]) + 1e-300
+            assert abs(dec - F[iB]) <= 1e-13 * size, (trial, r, iB, dec, F[iB])
+    for r in ("left", "right", "star-left", "star-right", "double-star"):
+        assert seen.get(r, 0) >= 50, seen
+
+
+def test_hll_ingredients_keep_one_dissipation_coefficient():
+    rng = np.random.default_rng(7)
+    for trial in range(200):
+        wl, wr, bn = random_pair(rng, trial)
+        for solver in ("hll", "hlld"):
+            _, ing = oracle.riemann(solver, wl, wr, bn, G)
+            assert ing[5] == ing[2]
+    with pytest.raises(ValueError):
+        oracle.riemann("hll", wl, wr, bn, G, emf="uct_hlld")
+
+
+def test_identical_states_give_symmetric_weights():
+    """With U_L = U_R the star ratio is 1, so d^L = d^R and a^L + a^R = 1:
+    the flux is the physical one whatever the weights."""
+    rng = np.random.default_rng(8)
+    for trial in range(500):
+        w, _, bn = random_pair(rng, trial)
+        F, ing = oracle.riemann("hlld", w, w, bn, G, emf="uct_hlld")
+        assert ing[0] + ing[1] == pytest.approx(1.0, abs=1e-15)
+        speed = abs(w[1]) + math.sqrt((G * w[6] + bn * bn + w[4] ** 2 + w[5] ** 2) / w[0])
+        assert ing[2] == pytest.approx(ing[5], rel=1e-12, abs=1e-13 * speed)
+
+
+def test_uniform_state_emf_is_minus_v_cross_b():
+    cfg = W.base_cfg(3, (4, 5, 6), (0, 0, 0), (1, 1, 1), emf="uct_hlld")
+    one = np.ones((6, 5, 4))
+    v = np.array([0.2, -0.1, 0.35])
+    B = np.array([0.3, -0.7, 0.45])
+    bx, by, bz = W.uniform_faces(cfg, B)
+    st = W.assemble(cfg, 1.3 * one, *(c * one for c in v), 0.8 * one, bx, by, bz)
+    s = oracle.OracleSim(cfg, st)
+    s.stage_increment(1e-3)
+    E = -np.cross(v, B)
+    for c in range(3):
+        np.testing.assert_allclose(s.emf(c), E[c], rtol=1e-14, atol=1e-16)
+
+
+def plane_parallel_state(n, seed):
+    """2D state varying along x only, B_n = B_x = 0, v_y = v_z = 0, and the
+    staggered B_y equal to the cell-centred B_z: in the x sweep the two
+    transverse components are images of each other."""
+    cfg = W.base_cfg(2, (n, 4), (0, 0), (1.0, 0.25))
+    rng = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) / n
+    prof = lambda a0, a1, k: a0 + a1 * np.sin(2 * np.pi * k * x + rng.uniform(0, 6.3))  # noqa: E731
+    row = lambda a: np.tile(a, (4, 1))[None]  # noqa: E731
+    rho = row(prof(1.0, 0.4, 1) + 0.2 * (x > 0.5))
+    u = row(prof(0.0, 0.6, 2))
+    p = row(prof(1.0, 0.3, 1))
+    b = prof(0.0, 0.8, 1) + 0.5 * (x > 0.3)
+    zero = 0 * rho
+    bx = np.zeros((1, 4, n + 1))
+    by = np.tile(b, (5, 1))[None]
+    st = W.assemble(cfg, rho, u, zero, zero, p, bx, by, row(b))
+    return cfg, st
+
+
+@pytest.mark.parametrize("rk", [2, 3])
+def test_plane_parallel_staggered_by_matches_cell_bz(rk):
+    """With the HLLD weights the UCT edge field of a plane-parallel problem is
+    minus the x sweep's flux of B_y, so the CT-evolved face B_y follows the
+    finite-volume cell B_z of the same profile to round-off; the HLL weights
+    give a different (more diffusive) edge field."""
+    n = 48
+    cfg, st = plane_parallel_state(n, 3)
+    cfg = dict(cfg, rk=rk)
+    gaps = {}
+    for emf in ("uct_hlld", "uct_hll"):
+        s = oracle.OracleSim(dict(cfg, emf=emf), st)
+        s.advance(30)
+        out = s.get_state()
+        by_face = out["b1"][0, 0, :]
+        bz_cell = out["b2"][0, 0, :]
+        assert np.all(out["b1"][0] == by_face), "y-invariance lost"
+        gaps[emf] = np.max(np.abs(by_face - bz_cell)) / np.max(np.abs(bz_cell))
+        assert np.all(out["my"] == 0.0) and np.all(out["mz"] == 0.0)
+    assert gaps["uct_hlld"] <= 1e-13, gaps
+    assert gaps["uct_hll"] >= 1e-5, gaps
+
+
+def test_emf_one_dimensional_reduction():
+    """2D data uniform in y: E_z at every vertex is the x face's
+    -(a^L u_L By_L + a^R u_R By_R) + (d^R By_R - d^L By_L) from the HLLD
+    weights, plus the centred v_y B_x of the y faces."""
+    nx, ny = 12, 4
+    cfg = W.base_cfg(2, (nx, ny), (0, 0), (1.0, 0.5), emf="uct_hlld")
+    rng = np.random.default_rng(12)
+    row = lambda lo, hi: np.tile(rng.uniform(lo, hi, nx), (ny, 1))[None]  # noqa: E731
+    rho, vx, vy, vz, p = row(0.5, 1.5), row(-0.4, 0.4), row(-0.4, 0.4), row(-0.4, 0.4), row(0.5, 1.5)
+    bxval = 0.6
+    byrow = rng.uniform(-0.5, 0.5, nx)
+    bx = np.full((1, ny, nx + 1), bxval)
+    by = np.tile(byrow, (ny + 1, 1))[None]
+    bz = row(-0.5, 0.5)
+    st = W.assemble(cfg, rho, vx, vy, vz, p, bx, by, bz)
+    s = oracle.OracleSim(cfg, st)
+    s.stage_increment(1e-3)
+    Ez = s.emf(2)[0]
+
+    def minmod(a, b):
+        return np.where(a * b > 0, np.where(np.abs(b) < np.abs(a), b, a), 0.0)
+
+    V = {"rho": rho[0, 0], "u": vx[0, 0], "v": vy[0, 0], "w": vz[0, 0], "by": byrow, "bz": bz[0, 0], "p": p[0, 0]}
+    plus, minus = {}, {}
+    for k, a in V.items():
+        d = minmod(a - np.roll(a, 1), np.roll(a, -1) - a)
+        plus[k], minus[k] = a + 0.5 * d, a - 0.5 * d
+    kinds = set()
+    for i in range(nx + 1):
+        L = {k: plus[k][(i - 1) % nx] for k in V}
+        R = {k: minus[k][i % nx] for k in V}
+        wl = [L["rho"], L["u"], L["v"], L["w"], L["by"], L["bz"], L["p"]]
+        wr = [R["rho"], R["u"], R["v"], R["w"], R["by"], R["bz"], R["p"]]
+        _, ing = oracle.riemann("hlld", wl, wr, bxval, cfg["gamma"], emf="uct_hlld")
+        kinds.add(region(ing))
+        aL, aR, dL, dR = ing[0], ing[1], ing[2], ing[5]
+        vbar = 0.5 * (vy[0, 0][(i - 1) % nx] + vy[0, 0][i % nx])
+        expect = -(aL * L["u"] * L["by"] + aR * R["u"] * R["by"]) + (dR * R["by"] - dL * L["by"]) + vbar * bxval
+        np.testing.assert_allclose(Ez[:, i], expect, rtol=1e-13, atol=1e-14)
+    assert "double-star" in kinds
+
+
+CASES = {
+    "ot2d-plm-rk2": lambda: W.orszag_tang_2d(32, emf="uct_hlld"),
+    "rand3d-plm-rk2": lambda: (lambda c: (c, W.random_state(c, 4)))(
+        W.base_cfg(3, (6, 7, 5), (0, 0, 0), (1.2, 1.4, 1.0), emf="uct_hlld")),
+    "rand3d-wenoz-rk3": lambda: (lambda c: (c, W.random_state(c, 5)))(
+        W.base_cfg(3, (6, 6, 6), (0, 0, 0), (1, 1, 1), recon="wenoz", rk=3, emf="uct_hlld")),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_conservation_and_div_b(case):
+    from test_oracle_scheme import div_b, totals
+    cfg, st = CASES[case]()
+    s = oracle.OracleSim(cfg, st)
+    s.advance(4)
+    out = s.get_state()
+    t0, t1 = totals(cfg, st), totals(cfg, out)
+    for k in t0:
+        assert abs(t1[k][0] - t0[k][0]) <= 1e-13 * max(t0[k][1], t1[k][1], 1e-300), k
+    div, scale = div_b(cfg, out)
+    assert div <= 1e-12 * scale
+    # and the weights matter: the HLL-weighted run differs
+    s2 = oracle.OracleSim(dict(cfg, emf="uct_hll"), st)
+    s2.advance(4)
+    assert relerr(s2.get_state()["b0"], out["b0"]) > 1e-8
+
+
+def test_rotation_commutes_with_step():
+    from test_oracle_scheme import _advance, _norm_periodic, rot90_2d, rotz90_3d
+    cfg = W.base_cfg(2, (8, 8), (0, 0), (1, 1), emf="uct_hlld")
+    st = _norm_periodic(W.random_state(cfg, 31))
+    dt = 0.2 * oracle.OracleSim(cfg, st).cfl_dt()
+    a = rot90_2d(_advance(cfg, st, 2, dt))
+    b = _advance(cfg, rot90_2d(st), 2, dt)
+    for k in KEYS:
+        assert relerr(b[k], a[k]) < 1e-13, k
+    cfg = W.base_cfg(3, (6, 6, 5), (0, 0, 0), (1, 1, 0.8), recon="wenoz", rk=3, emf="uct_hlld")
+    st = _norm_periodic(W.random_state(cfg, 32))
+    dt = 0.2 * oracle.OracleSim(cfg, st).cfl_dt()
+    a = rotz90_3d(_advance(cfg, st, 2, dt))
+    b = _advance(cfg, rotz90_3d(st), 2, dt)
+    for k in KEYS:
+        assert relerr(b[k], a[k]) < 1e-13, k
+
+
+def test_uct_hlld_needs_hlld_solver():
+    cfg = W.base_cfg(2, (8, 8), (0, 0), (1, 1), riemann="hll", emf="uct_hlld")
+    st = W.random_state(cfg, 1)
+    with pytest.raises(Exception):
+        oracle.OracleSim(cfg, st)
+
+
+@pytest.mark.slow
+def test_cpa_2d_converges_to_exact_translation():
+    """The circularly polarised Alfven wave (§4.2) with the HLLD edge weights:
+    second order, and no larger an error than with the HLL weights."""
+    from test_oracle_scheme import cpa_error
+    T = 1.0 / math.sqrt(2.0)
+
+    def err(n, emf):
+        import test_oracle_scheme as S
+        gen = W.cpa_2d
+        cfg, st = gen(n, emf=emf)
+        _, exact = gen(n, t=T, emf=emf)
+        s = oracle.OracleSim(cfg, st)
+        t = 0.0
+        while t < T - 1e-14:
+            dt = min(s.cfl_dt(), T - t)
+            s.step(dt)
+            t += dt
+        out = s.get_state()
+        return sum(np.mean(np.abs(out[k] - exact[k])) for k in S.KEYS)
+
+    e = [err(n, "uct_hlld") for n in (16, 32, 64)]
+    assert e[0] / e[1] > 2.4 and e[1] / e[2] > 2.3, e
+    assert e[2] <= 1.05 * cpa_error(64, 2, T)
