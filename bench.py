@@ -52,14 +52,21 @@ WORKLOADS = {
                     "3D magnetised blast 128^3 (profiling size), same setup and scheme as blast3d-512"),
     "blast3d-512-ppm": (lambda: W.blast_3d(512, recon="ppm"), "blast3d_ppm_hlld_rk3",
                         "3D magnetised blast 512^3 outflow; PPM + HLLD + SSP-RK3 + UCT-HLL CT, CFL 0.4"),
-    "orszag-tang3d-704": (lambda: W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3),
-                          "orszag_tang3d_wenoz_hlld_rk3",
+    "orszag-tang3d-704": (lambda: W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3, emf="uct_hlld"),
+                          "orszag_tang3d_wenoz_hlld_rk3_ucthlld",
                           "3D Orszag-Tang of paper §4.1 at its per-node resolution 704x704x352 on the unit periodic cube, "
-                          "rho = 25/9, p = 5/3; WENO-Z + HLLD + SSP-RK3 + CT (UCT-HLL edge fields; the paper uses "
-                          "UCT-HLLD), CFL 0.4"),
-    "cpa3d-704": (lambda: W.cpa_3d((704, 704, 352), recon="wenoz", rk=3), "cpa3d_wenoz_hlld_rk3",
+                          "rho = 25/9, p = 5/3; WENO-Z + HLLD + SSP-RK3 + CT with UCT-HLLD edge fields (the paper's "
+                          "scheme), CFL 0.4"),
+    "orszag-tang3d-704-ucthll": (lambda: W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3),
+                                 "orszag_tang3d_wenoz_hlld_rk3",
+                                 "orszag-tang3d-704 with UCT-HLL instead of UCT-HLLD edge fields"),
+    "orszag-tang3d-128": (lambda: W.orszag_tang_3d(128, recon="wenoz", rk=3, emf="uct_hlld"),
+                          "orszag_tang3d_wenoz_hlld_rk3_ucthlld",
+                          "3D Orszag-Tang 128^3 (profiling size), same setup and scheme as orszag-tang3d-704"),
+    "cpa3d-704": (lambda: W.cpa_3d((704, 704, 352), recon="wenoz", rk=3, emf="uct_hlld"), "cpa3d_wenoz_hlld_rk3_ucthlld",
                   "3D circularly polarised Alfven wave of paper §4.2 at 704x704x352 on the unit periodic cube, "
-                  "eps = 0.1, rho0 = 1, p0 = 0.1, k = 2 pi (1,1,1); WENO-Z + HLLD + SSP-RK3 + CT (UCT-HLL), CFL 0.4"),
+                  "eps = 0.1, rho0 = 1, p0 = 0.1, k = 2 pi (1,1,1); WENO-Z + HLLD + SSP-RK3 + CT with UCT-HLLD edge "
+                  "fields (the paper's scheme), CFL 0.4"),
     "turbulent3d-128-glm": (lambda: W.to_glm(*W.turbulent_3d(128)), "turbulent3d_plm_hlld_rk2_glm",
                             "turbulent3d-128 with GLM divergence cleaning (profiling size), same scheme as "
                             "turbulent3d-256-glm"),
@@ -96,8 +103,12 @@ SAMPLES = {
     "blast3d-512": (lambda: W.blast_3d(32), "blast 3D 32^3 (same scheme and setup)"),
     "blast3d-128": (lambda: W.blast_3d(32), "blast 3D 32^3 (same scheme and setup)"),
     "blast3d-512-ppm": (lambda: W.blast_3d(32, recon="ppm"), "blast 3D 32^3 PPM (same scheme and setup)"),
-    "orszag-tang3d-704": (lambda: W.orszag_tang_3d(32, recon="wenoz", rk=3), "3D Orszag-Tang 32^3 (same scheme)"),
-    "cpa3d-704": (lambda: W.cpa_3d(32, recon="wenoz", rk=3), "3D CPA 32^3 (same scheme)"),
+    "orszag-tang3d-704": (lambda: W.orszag_tang_3d(32, recon="wenoz", rk=3, emf="uct_hlld"),
+                          "3D Orszag-Tang 32^3 (same scheme)"),
+    "orszag-tang3d-704-ucthll": (lambda: W.orszag_tang_3d(32, recon="wenoz", rk=3), "3D Orszag-Tang 32^3 (same scheme)"),
+    "orszag-tang3d-128": (lambda: W.orszag_tang_3d(32, recon="wenoz", rk=3, emf="uct_hlld"),
+                          "3D Orszag-Tang 32^3 (same scheme)"),
+    "cpa3d-704": (lambda: W.cpa_3d(32, recon="wenoz", rk=3, emf="uct_hlld"), "3D CPA 32^3 (same scheme)"),
     "turbulent3d-256-glm": (lambda: W.to_glm(*W.turbulent_3d(48)), "turbulent 3D 48^3 with GLM (same scheme)"),
     "turbulent3d-128-glm": (lambda: W.to_glm(*W.turbulent_3d(48)), "turbulent 3D 48^3 with GLM (same scheme)"),
     "orszag-tang3d-704-glm": (lambda: W.to_glm(*W.orszag_tang_3d(32, recon="wenoz", rk=3)),
@@ -258,6 +269,8 @@ def sweep_traffic(cfg, faces_per_launch):
         return None
     rec = json.load(open(path))
     scheme = {"ndim": cfg["ndim"], "recon": cfg["recon"], "riemann": cfg["riemann"], "divb": cfg.get("divb", "ct")}
+    if scheme["divb"] == "ct":
+        scheme["emf"] = cfg.get("emf", "uct_hll")
     files = GLM_SWEEP_SOURCES if scheme["divb"] == "glm" else SWEEP_SOURCES
     for v in rec.values():
         if isinstance(v, dict) and v.get("scheme") == scheme:

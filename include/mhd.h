@@ -74,10 +74,19 @@ typedef struct {
                            MHD_DIVB_GLM (cell-centred B with GLM divergence cleaning) */
   double glm_alpha;     /* GLM damping constant alpha >= 0: after each step
                            psi <- psi exp(-alpha c_h dt / min dx); ignored for CT */
+  int emf;              /* CT edge fields (§4.1 "UCT HLLD average"):
+                           MHD_EMF_UCT_HLL (0): the UCT form with the HLL weights
+                             a+ = S_R+/(S_R+ - S_L-), a- = -S_L-/(..), d = -S_R+ S_L-/(..);
+                           MHD_EMF_UCT_HLLD (1, needs MHD_RIEMANN_HLLD and CT): the same form
+                             with the HLLD solver's own weights, which write its flux of a
+                             transverse field component as a^L F_L + a^R F_R + d^L B_L - d^R B_R
+                             (three more face fields); not supported by mhd_adjoint */
 } mhd_config;
 
 #define MHD_DIVB_CT  0
 #define MHD_DIVB_GLM 1
+#define MHD_EMF_UCT_HLL  0
+#define MHD_EMF_UCT_HLLD 1
 
 typedef struct mhd_ctx mhd_ctx;   /* opaque; owns all device state of one grid */
 

@@ -67,6 +67,14 @@ int mhd_adjoint_profile(mhd_ctx* ctx, int nsteps, const double* dts, int ckpt_ev
 int mhd_probe_riemann_vjp(int riemann, int n, double gamma, const double* in, const double* cot, double* dual,
                           double* hand);
 
+/* The sweeps' Riemann solver (MHD_RIEMANN_HLL / _HLLD) on n faces, with the
+ * UCT-HLL or (emf = MHD_EMF_UCT_HLLD, HLLD only) UCT-HLLD face weights.
+ * Host arrays: in[15 n] as for mhd_probe_riemann_vjp; F[7 n] receives the
+ * sweep-frame flux (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and ing[6 n] the
+ * ingredients (a^L, a^R, d^L, u_L, u_R, d^R; UCT-HLL: a+, a-, d, u_L, u_R, d).
+ * Sync. */
+int mhd_probe_riemann(int riemann, int emf, int n, double gamma, const double* in, double* F, double* ing);
+
 /* Both per-cell CFL rates of the single-grid step (the rate of the CFL
  * reading: sum over the ndim axes of (|v_d| + c_f,d) / dx_d, c_f,d the fast
  * speed with the cell field B_d) for n primitive states: near_out[n] gets the

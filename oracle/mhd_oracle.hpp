@@ -366,6 +366,7 @@ inline void riemann_hlld(const R WL[NW], const R WR[NW], R bn, double gamma, R F
   } else {  // S*_R < 0 <= S_R
     for (int q = 0; q < NW; q++) F[q] = Rs.F[q] + SR * (UsR[q] - Rs.U[q]);
   }
+  if (!uct_hlld) return;
   if (SsL >= zero) {
     set_weights(R(1.0), zero, SL * (sL.e - R(1.0)), zero);
   } else if (SsR >= zero) {  // only with rotational waves: S*_L < 0 <= S*_R
@@ -754,17 +755,17 @@ template <class R> struct Sim {
           R ddb = h * (I[b][I_DD](xa[0], xa[1], xa[2]) + I[b][I_DD](i, j, k));
           R vS = h * (I[b][I_UL](xa[0], xa[1], xa[2]) + I[b][I_UL](i, j, k));
           R vN = h * (I[b][I_UR](xa[0], xa[1], xa[2]) + I[b][I_UR](i, j, k));
-          R dra = h * (I[a][I_DR](xb[0], xb[1], xb[2]) + I[a][I_DR](i, j, k));
-          R drb = h * (I[b][I_DR](xa[0], xa[1], xa[2]) + I[b][I_DR](i, j, k));
           R BbW = face_to_edge(S[Q_B0 + b], x, a, true);
           R BbE = face_to_edge(S[Q_B0 + b], x, a, false);
           R BaS = face_to_edge(S[Q_B0 + a], x, b, true);
           R BaN = face_to_edge(S[Q_B0 + a], x, b, false);
           R e;
-          if (c.emf == EMF_UCT_HLLD)
+          if (c.emf == EMF_UCT_HLLD) {
+            R dra = h * (I[a][I_DR](xb[0], xb[1], xb[2]) + I[a][I_DR](i, j, k));
+            R drb = h * (I[b][I_DR](xa[0], xa[1], xa[2]) + I[b][I_DR](i, j, k));
             e = ((-(apa * uW * BbW + ama * uE * BbE) + (dra * BbE - dda * BbW)) + (apb * vS * BaS + amb * vN * BaN)) -
                 (drb * BaN - ddb * BaS);
-          else
+          } else
             e = ((-(apa * uW * BbW + ama * uE * BbE) + dda * (BbE - BbW)) + (apb * vS * BaS + amb * vN * BaN)) -
                 ddb * (BaN - BaS);
           E[cc](i, j, k) = e;

@@ -76,8 +76,8 @@ F8 state_at(const AdjointState* a, size_t idx) {
 }
 
 // The stored ingredients of stage idx, laid out like the context's (direction-major).
-Ingr5x3 ing_at(const AdjointState* a, int ndim, size_t idx) {
-  Ingr5x3 g{};
+FaceIngr ing_at(const AdjointState* a, int ndim, size_t idx) {
+  FaceIngr g{};
   for (int d = 0; d < ndim; d++)
     for (int q = 0; q < 5; q++) g.a[d][q] = a->ings + (idx * 5 * ndim + (size_t)d * 5 + q) * a->fe;
   return g;
@@ -191,7 +191,7 @@ void adj_recon_dir(mhd_ctx* c) {
 // Transpose of stage s at the stage input Xs: the cotangent Aout of the
 // stage output is distributed to A0 (U^n) and As (the stage input).
 template <int NDIM, int RS>
-int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const Ingr5x3& ING, const F8& Aout, const F8& A0, const F8& As,
+int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const FaceIngr& ING, const F8& Aout, const F8& A0, const F8& As,
                 double dt) {
   AdjointState* a = c->adj;
   const Grid& g = c->g;
@@ -251,7 +251,7 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const Ingr5x3& ING, const F8& A
   return MHD_OK;
 }
 
-int adj_stage(mhd_ctx* c, int s, const F8& Xs, const Ingr5x3& ING, const F8& Aout, const F8& A0, const F8& As,
+int adj_stage(mhd_ctx* c, int s, const F8& Xs, const FaceIngr& ING, const F8& Aout, const F8& A0, const F8& As,
               double dt) {
   const bool hlld = c->cfg.riemann == MHD_RIEMANN_HLLD;
   if (c->g.ndim == 2)
@@ -300,7 +300,7 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
   if (functional == MHD_FUNC_MISFIT && (!target || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE))) return MHD_ERR_ARG;
   if (!c->has_state) return MHD_ERR_STATE;
   const Grid& g = c->g;
-  if (c->cfg.recon != MHD_RECON_PLM || c->g.glm) return MHD_ERR_ARG;
+  if (c->cfg.recon != MHD_RECON_PLM || c->g.glm || c->cfg.emf != MHD_EMF_UCT_HLL) return MHD_ERR_ARG;
   for (int d = 0; d < g.ndim; d++)
     if (!g.periodic[d] || g.n[d] < 2 * g.G + 1) return MHD_ERR_ARG;
   if (dts)
@@ -371,7 +371,7 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
         F8 out = s + 1 < S ? X(n, s + 1) : X(n + 1, 0);
         run_stage_regs(c, s, X(n, 0), X(n, s), out, false);
         // keep the stage's UCT ingredients (the context's are contiguous, direction-major)
-        const Ingr5x3 keep = ing_at(a, g.ndim, (size_t)(n - n0) * S + s);
+        const FaceIngr keep = ing_at(a, g.ndim, (size_t)(n - n0) * S + s);
         CK(cudaMemcpyAsync(keep.a[0][0], c->ING.a[0][0], (size_t)5 * g.ndim * a->fe * sizeof(double),
                            cudaMemcpyDeviceToDevice, c->stream));
       }

@@ -267,7 +267,7 @@ __device__ __forceinline__ void edge_recon_vjp(double vm2, double vm1, double v0
 }
 
 template <int C>
-__device__ __forceinline__ void uct_edge_vjp(const Grid& g, const F8& S, const Ingr5x3& ING, int c, double eb,
+__device__ __forceinline__ void uct_edge_vjp(const Grid& g, const F8& S, const FaceIngr& ING, int c, double eb,
                                              double* const* ge) {
   constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
   const int sa = g.stride(A), sb = g.stride(B);
@@ -313,7 +313,7 @@ __device__ __forceinline__ void uct_edge_vjp(const Grid& g, const F8& S, const I
 }
 
 template <int NDIM>
-static __global__ void adj_edge_kernel(Grid g, F8 S, Ingr5x3 ING, E3 Eb, GE18 GE) {
+static __global__ void adj_edge_kernel(Grid g, F8 S, FaceIngr ING, E3 Eb, GE18 GE) {
   const long long total = edge_work<NDIM>(g);
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {

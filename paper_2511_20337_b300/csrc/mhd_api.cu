@@ -132,35 +132,53 @@ cudaError_t allow_stage_t() {
   return cudaFuncSetAttribute(sweep_kernel<0, NDIM, RECON, RS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               kXStageBytes);
 }
+// The sweeps' Riemann-solver template value of a configuration.
+int sweep_rs(const mhd_config* cfg) {
+  if (cfg->riemann != MHD_RIEMANN_HLLD) return RS_HLL;
+  return cfg->emf == MHD_EMF_UCT_HLLD ? RS_HLLD_UCT : RS_HLLD;
+}
+template <int NDIM, int RECON>
+cudaError_t allow_stage_r(int rs) {
+  if (rs == RS_HLLD_UCT) return allow_stage_t<NDIM, RECON, RS_HLLD_UCT>();
+  return rs == RS_HLLD ? allow_stage_t<NDIM, RECON, RS_HLLD>() : allow_stage_t<NDIM, RECON, RS_HLL>();
+}
 template <int NDIM>
-cudaError_t allow_stage_n(int r, int s) {
-  const bool hlld = s == MHD_RIEMANN_HLLD;
-  if (r == MHD_RECON_PLM) return hlld ? allow_stage_t<NDIM, RECON_PLM, RS_HLLD>() : allow_stage_t<NDIM, RECON_PLM, RS_HLL>();
-  if (r == MHD_RECON_WENOZ)
-    return hlld ? allow_stage_t<NDIM, RECON_WENOZ, RS_HLLD>() : allow_stage_t<NDIM, RECON_WENOZ, RS_HLL>();
-  return hlld ? allow_stage_t<NDIM, RECON_PPM, RS_HLLD>() : allow_stage_t<NDIM, RECON_PPM, RS_HLL>();
+cudaError_t allow_stage_n(int r, int rs) {
+  if (r == MHD_RECON_PLM) return allow_stage_r<NDIM, RECON_PLM>(rs);
+  if (r == MHD_RECON_WENOZ) return allow_stage_r<NDIM, RECON_WENOZ>(rs);
+  return allow_stage_r<NDIM, RECON_PPM>(rs);
 }
 cudaError_t allow_stage(const mhd_config* cfg) {
-  return cfg->ndim == 2 ? allow_stage_n<2>(cfg->recon, cfg->riemann) : allow_stage_n<3>(cfg->recon, cfg->riemann);
+  return cfg->ndim == 2 ? allow_stage_n<2>(cfg->recon, sweep_rs(cfg)) : allow_stage_n<3>(cfg->recon, sweep_rs(cfg));
 }
 
+template <int NDIM, int RECON>
+void sweeps_r(mhd_ctx* c, const F8& S) {
+  const int rs = sweep_rs(&c->cfg);
+  if (rs == RS_HLLD_UCT) sweeps_t<NDIM, RECON, RS_HLLD_UCT>(c, S);
+  else if (rs == RS_HLLD) sweeps_t<NDIM, RECON, RS_HLLD>(c, S);
+  else sweeps_t<NDIM, RECON, RS_HLL>(c, S);
+}
 template <int NDIM>
 void sweeps_n(mhd_ctx* c, const F8& S) {
-  int r = c->cfg.recon, s = c->cfg.riemann;
-  if (r == MHD_RECON_PLM && s == MHD_RIEMANN_HLLD) sweeps_t<NDIM, RECON_PLM, RS_HLLD>(c, S);
-  else if (r == MHD_RECON_PLM) sweeps_t<NDIM, RECON_PLM, RS_HLL>(c, S);
-  else if (r == MHD_RECON_WENOZ && s == MHD_RIEMANN_HLLD) sweeps_t<NDIM, RECON_WENOZ, RS_HLLD>(c, S);
-  else if (r == MHD_RECON_WENOZ) sweeps_t<NDIM, RECON_WENOZ, RS_HLL>(c, S);
-  else if (s == MHD_RIEMANN_HLLD) sweeps_t<NDIM, RECON_PPM, RS_HLLD>(c, S);
-  else sweeps_t<NDIM, RECON_PPM, RS_HLL>(c, S);
+  const int r = c->cfg.recon;
+  if (r == MHD_RECON_PLM) sweeps_r<NDIM, RECON_PLM>(c, S);
+  else if (r == MHD_RECON_WENOZ) sweeps_r<NDIM, RECON_WENOZ>(c, S);
+  else sweeps_r<NDIM, RECON_PPM>(c, S);
 }
 
 void emf(mhd_ctx* c, const F8& S) {
   const Grid& g = c->g;
   long long work = (long long)(g.n[0] + 1) * (g.n[1] + 1) * (g.ndim == 3 ? g.n[2] + 1 : 1);
   int nb = blocks_for(work, 256);
-  if (g.ndim == 2) emf_kernel<2><<<nb, 256, 0, c->stream>>>(g, S, c->ING, c->E);
-  else emf_kernel<3><<<nb, 256, 0, c->stream>>>(g, S, c->ING, c->E);
+  const bool hlld = c->cfg.emf == MHD_EMF_UCT_HLLD;
+  if (g.ndim == 2) {
+    if (hlld) emf_kernel<2, true><<<nb, 256, 0, c->stream>>>(g, S, c->ING, c->E);
+    else emf_kernel<2, false><<<nb, 256, 0, c->stream>>>(g, S, c->ING, c->E);
+  } else {
+    if (hlld) emf_kernel<3, true><<<nb, 256, 0, c->stream>>>(g, S, c->ING, c->E);
+    else emf_kernel<3, false><<<nb, 256, 0, c->stream>>>(g, S, c->ING, c->E);
+  }
   c->launches++;
   prof_mark(c, MHD_KCLASS_EMF);
 }
@@ -354,10 +372,12 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
     if (cudaStreamCreate(&c->stream) != cudaSuccess) { delete c; return MHD_ERR_CUDA; }
     c->own_stream = true;
   }
-  // CT: 3 registers of 8, primitives 8, increment 6, ingredients 15, edges 3;
-  // GLM: 3 registers of 9, primitives 9, increment 9
-  // (+ the CFL rates; + the raw flux differences of the split y and z sweeps)
-  const int nfields = (g.glm ? 3 * 9 + 9 + 9 : 3 * 8 + 8 + 6 + 15 + 3) + 1 + (c->split ? 6 * (g.ndim - 1) : 0);
+  // CT: 3 registers of 8, primitives 8, increment 6, ingredients 15 (18 with
+  // the UCT-HLLD weights), edges 3; GLM: 3 registers of 9, primitives 9,
+  // increment 9 (+ the CFL rates; + the raw flux differences of the split y
+  // and z sweeps)
+  const int ningr = cfg->emf == MHD_EMF_UCT_HLLD ? 6 : 5;
+  const int nfields = (g.glm ? 3 * 9 + 9 + 9 : 3 * 8 + 8 + 6 + 3 * ningr + 3) + 1 + (c->split ? 6 * (g.ndim - 1) : 0);
   size_t bytes = c->field_elems * sizeof(double) * nfields;
   if (cudaMalloc(&c->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -384,7 +404,7 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
     for (int q = 0; q < 8; q++) c->P.q[q] = next();
     for (int q = 0; q < 6; q++) c->L.q[q] = next();
     for (int d = 0; d < 3; d++)
-      for (int q = 0; q < 5; q++) c->ING.a[d][q] = next();
+      for (int q = 0; q < ningr; q++) c->ING.a[d][q] = next();
     for (int d = 0; d < 3; d++) c->E.e[d] = next();
   }
   c->lam = next();
@@ -804,7 +824,55 @@ static __global__ void cfl_rate_probe_kernel(mhd::Grid g, int n, const double* _
   ieee_out[t] = mhd::cfl_rate_ieee<NDIM>(g, V);
 }
 
+// The sweeps' Riemann solver at n faces: in[15] = left (rho, u, v, w, b1, b2,
+// p), right (same), b_n; out F[7] and the UCT ingredients ing[6].
+template <int RS>
+static __global__ void riemann_probe_kernel(int n, double gamma, const double* __restrict__ in,
+                                            double* __restrict__ F_out, double* __restrict__ ing_out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double* x = in + (size_t)15 * t;
+  mhd::W7 L = {x[0], x[1], x[2], x[3], x[4], x[5], x[6]};
+  mhd::W7 R = {x[7], x[8], x[9], x[10], x[11], x[12], x[13]};
+  mhd::Flux7 F;
+  mhd::Ingr ing;
+  ing.dr = 0.0;
+  const double igm1 = 1.0 / (gamma - 1.0);
+  if (RS == mhd::RS_HLL) mhd::riemann_hll(L, R, x[14], gamma, igm1, F, ing);
+  else mhd::riemann_hlld<double, RS == mhd::RS_HLLD_UCT>(L, R, x[14], gamma, igm1, F, ing);
+  if (RS != mhd::RS_HLLD_UCT) ing.dr = ing.dd;
+  for (int q = 0; q < 7; q++) F_out[(size_t)7 * t + q] = F.f[q];
+  const double v6[6] = {ing.ap, ing.am, ing.dd, ing.uL, ing.uR, ing.dr};
+  for (int q = 0; q < 6; q++) ing_out[(size_t)6 * t + q] = v6[q];
+}
+
 extern "C" {
+
+int mhd_probe_riemann(int riemann, int emf, int n, double gamma, const double* in, double* F, double* ing) {
+  if (n < 1 || !in || !F || !ing || !(gamma > 1.0)) return MHD_ERR_ARG;
+  if (riemann != MHD_RIEMANN_HLL && riemann != MHD_RIEMANN_HLLD) return MHD_ERR_ARG;
+  if (emf != MHD_EMF_UCT_HLL && emf != MHD_EMF_UCT_HLLD) return MHD_ERR_ARG;
+  if (emf == MHD_EMF_UCT_HLLD && riemann != MHD_RIEMANN_HLLD) return MHD_ERR_ARG;
+  double *d_in = nullptr, *d_F = nullptr, *d_ing = nullptr;
+  cudaError_t e = cudaMalloc(&d_in, sizeof(double) * 15 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&d_F, sizeof(double) * 7 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&d_ing, sizeof(double) * 6 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, in, sizeof(double) * 15 * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int nb = (n + 127) / 128;
+    if (riemann == MHD_RIEMANN_HLL) riemann_probe_kernel<mhd::RS_HLL><<<nb, 128>>>(n, gamma, d_in, d_F, d_ing);
+    else if (emf == MHD_EMF_UCT_HLLD)
+      riemann_probe_kernel<mhd::RS_HLLD_UCT><<<nb, 128>>>(n, gamma, d_in, d_F, d_ing);
+    else riemann_probe_kernel<mhd::RS_HLLD><<<nb, 128>>>(n, gamma, d_in, d_F, d_ing);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(F, d_F, sizeof(double) * 7 * (size_t)n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ing, d_ing, sizeof(double) * 6 * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(d_in);
+  cudaFree(d_F);
+  cudaFree(d_ing);
+  return cuda_err(e);
+}
 
 int mhd_probe_fp64(double* gflops_out) {
   if (!gflops_out) return MHD_ERR_ARG;
@@ -878,7 +946,7 @@ int mhd_probe_cfl_rate(int ndim, double gamma, const double* dx, int n, const do
 namespace {
 
 constexpr size_t kNoAllocDoubles = MHD_NOALLOC_SCRATCH_BYTES / sizeof(double);
-constexpr int kNoAllocFields = 3 * 8 + 8 + 6 + 15 + 3 + 1;  // same carve-up as mhd_create (CT)
+constexpr int kNoAllocFields = 3 * 8 + 8 + 6 + 15 + 3 + 1;  // same carve-up as mhd_create (CT, UCT-HLL)
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
@@ -916,7 +984,8 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   long long elems = (long long)g.ext[0] * g.ext[1] * g.ext[2];
   long long field = (elems + 31) / 32 * 32;  // 256-byte aligned fields
   long long sc_doubles = (long long)((sizeof(DevScalars) + 255) / 256 * 256 / sizeof(double));
-  long long need = field * kNoAllocFields + sc_doubles;
+  const int ningr = cfg->emf == MHD_EMF_UCT_HLLD ? 6 : 5;
+  long long need = field * (kNoAllocFields + 3 * (ningr - 5)) + sc_doubles;
   if (need > (long long)kNoAllocDoubles) return MHD_ERR_TOO_LARGE;
   double* base = nullptr;
   rc = noalloc_scratch(&base);
@@ -939,7 +1008,7 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   for (int q = 0; q < 8; q++) c.P.q[q] = next();
   for (int q = 0; q < 6; q++) c.L.q[q] = next();
   for (int d = 0; d < 3; d++)
-    for (int q = 0; q < 5; q++) c.ING.a[d][q] = next();
+    for (int q = 0; q < ningr; q++) c.ING.a[d][q] = next();
   for (int d = 0; d < 3; d++) c.E.e[d] = next();
   c.lam = next();
   c.sc = reinterpret_cast<DevScalars*>(p);

@@ -141,15 +141,18 @@ void batch_sweeps(mhd_batch* b, int reg) {
     b->launches++;
   }
 }
+template <int NDIM, int RECON>
+void batch_sweeps_r(mhd_batch* b, int reg) {
+  if (b->cfg0.riemann != MHD_RIEMANN_HLLD) batch_sweeps<NDIM, RECON, RS_HLL>(b, reg);
+  else if (b->cfg0.emf == MHD_EMF_UCT_HLLD) batch_sweeps<NDIM, RECON, RS_HLLD_UCT>(b, reg);
+  else batch_sweeps<NDIM, RECON, RS_HLLD>(b, reg);
+}
 template <int NDIM>
 void batch_sweeps_n(mhd_batch* b, int reg) {
-  int r = b->cfg0.recon, s = b->cfg0.riemann;
-  if (r == MHD_RECON_PLM && s == MHD_RIEMANN_HLLD) batch_sweeps<NDIM, RECON_PLM, RS_HLLD>(b, reg);
-  else if (r == MHD_RECON_PLM) batch_sweeps<NDIM, RECON_PLM, RS_HLL>(b, reg);
-  else if (r == MHD_RECON_WENOZ && s == MHD_RIEMANN_HLLD) batch_sweeps<NDIM, RECON_WENOZ, RS_HLLD>(b, reg);
-  else if (r == MHD_RECON_WENOZ) batch_sweeps<NDIM, RECON_WENOZ, RS_HLL>(b, reg);
-  else if (s == MHD_RIEMANN_HLLD) batch_sweeps<NDIM, RECON_PPM, RS_HLLD>(b, reg);
-  else batch_sweeps<NDIM, RECON_PPM, RS_HLL>(b, reg);
+  const int r = b->cfg0.recon;
+  if (r == MHD_RECON_PLM) batch_sweeps_r<NDIM, RECON_PLM>(b, reg);
+  else if (r == MHD_RECON_WENOZ) batch_sweeps_r<NDIM, RECON_WENOZ>(b, reg);
+  else batch_sweeps_r<NDIM, RECON_PPM>(b, reg);
 }
 
 // One RK stage s of every run (the CFL dt of each run in the first stage).
@@ -190,8 +193,14 @@ void batch_stage(mhd_batch* b, int s) {
   if (nd == 2) batch_sweeps_n<2>(b, reg);
   else batch_sweeps_n<3>(b, reg);
   const int ne = table_blocks(b, T_EDGE);
-  if (nd == 2) batch_emf_kernel<2><<<ne, kBlockBig, 0, b->stream>>>(b->runs_d, table(b, T_EDGE), R, reg);
-  else batch_emf_kernel<3><<<ne, kBlockBig, 0, b->stream>>>(b->runs_d, table(b, T_EDGE), R, reg);
+  const bool hlld = b->cfg0.emf == MHD_EMF_UCT_HLLD;
+  if (nd == 2) {
+    if (hlld) batch_emf_kernel<2, true><<<ne, kBlockBig, 0, b->stream>>>(b->runs_d, table(b, T_EDGE), R, reg);
+    else batch_emf_kernel<2, false><<<ne, kBlockBig, 0, b->stream>>>(b->runs_d, table(b, T_EDGE), R, reg);
+  } else {
+    if (hlld) batch_emf_kernel<3, true><<<ne, kBlockBig, 0, b->stream>>>(b->runs_d, table(b, T_EDGE), R, reg);
+    else batch_emf_kernel<3, false><<<ne, kBlockBig, 0, b->stream>>>(b->runs_d, table(b, T_EDGE), R, reg);
+  }
   prof_mark(b, MHD_KCLASS_EMF);
   if (nd == 2) batch_ct_rk_kernel<2><<<ne, kBlockBig, 0, b->stream>>>(b->runs_d, table(b, T_EDGE), R, reg, out, mode);
   else batch_ct_rk_kernel<3><<<ne, kBlockBig, 0, b->stream>>>(b->runs_d, table(b, T_EDGE), R, reg, out, mode);
@@ -273,7 +282,8 @@ __global__ void batch_reset_scalars_kernel(DevScalars* sc, int nruns) {
 }
 
 bool same_scheme(const mhd_config& a, const mhd_config& c) {
-  if (a.ndim != c.ndim || a.recon != c.recon || a.riemann != c.riemann || a.rk != c.rk) return false;
+  if (a.ndim != c.ndim || a.recon != c.recon || a.riemann != c.riemann || a.rk != c.rk || a.emf != c.emf)
+    return false;
   for (int s = 0; s < 2 * a.ndim; s++)
     if (a.bc[s] != c.bc[s]) return false;
   return true;
@@ -302,7 +312,8 @@ int mhd_batch_create(int nruns, const mhd_config* cfgs, mhd_batch** out) {
     if (cudaStreamCreate(&b->stream) != cudaSuccess) { delete b; return MHD_ERR_CUDA; }
     b->own_stream = true;
   }
-  const int nfields = 3 * 8 + 8 + 6 + 15 + 3;
+  const int ningr = cfgs[0].emf == MHD_EMF_UCT_HLLD ? 6 : 5;  // face ingredients per direction
+  const int nfields = 3 * 8 + 8 + 6 + 3 * ningr + 3;
   std::vector<size_t> field(nruns);
   size_t total = 0;
   b->runs.resize(nruns);
@@ -331,7 +342,7 @@ int mhd_batch_create(int nruns, const mhd_config* cfgs, mhd_batch** out) {
     for (int q = 0; q < 8; q++) run.P.q[q] = next();
     for (int q = 0; q < 6; q++) run.L.q[q] = next();
     for (int d = 0; d < 3; d++)
-      for (int q = 0; q < 5; q++) run.ING.a[d][q] = next();
+      for (int q = 0; q < ningr; q++) run.ING.a[d][q] = next();
     for (int d = 0; d < 3; d++) run.E.e[d] = next();
     run.sc = b->sc + r;
   }

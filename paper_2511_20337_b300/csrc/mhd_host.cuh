@@ -42,6 +42,8 @@ inline int validate(const mhd_config* c) {
   if (!(c->p_floor >= 0.0)) return MHD_ERR_ARG;
   if (c->divb != MHD_DIVB_CT && c->divb != MHD_DIVB_GLM) return MHD_ERR_ARG;
   if (c->divb == MHD_DIVB_GLM && (!(c->glm_alpha >= 0.0) || c->p_floor != 0.0)) return MHD_ERR_ARG;
+  if (c->emf != MHD_EMF_UCT_HLL && c->emf != MHD_EMF_UCT_HLLD) return MHD_ERR_ARG;
+  if (c->emf == MHD_EMF_UCT_HLLD && (c->riemann != MHD_RIEMANN_HLLD || c->divb != MHD_DIVB_CT)) return MHD_ERR_ARG;
   for (int d = 0; d < c->ndim; d++) {
     for (int s = 0; s < 2; s++)
       if (c->bc[2 * d + s] != MHD_BC_PERIODIC && c->bc[2 * d + s] != MHD_BC_OUTFLOW) return MHD_ERR_ARG;

@@ -19,7 +19,9 @@
 namespace mhd {
 
 enum { RECON_PLM = 0, RECON_WENOZ = 1, RECON_PPM = 2 };
-enum { RS_HLL = 0, RS_HLLD = 1 };
+// Riemann solver of the sweeps; RS_HLLD_UCT is the HLLD flux with the solver's
+// own UCT weights (UCT-HLLD edge fields) in place of the HLL ones.
+enum { RS_HLL = 0, RS_HLLD = 1, RS_HLLD_UCT = 2 };
 
 struct Grid {
   int ndim;
@@ -39,7 +41,10 @@ struct Grid {
 };
 
 struct F8 { double* q[8]; };
-struct Ingr5x3 { double* a[3][5]; };   // per direction: a+, a-, d, uL, uR at each face
+// UCT face ingredients per direction: a^L, a^R, d^L, u_L, u_R and (UCT-HLLD
+// only, else null) d^R at each face; the flux of a transverse field component
+// at the face is a^L F_L + a^R F_R + d^L B_L - d^R B_R (UCT-HLL: d^R = d^L).
+struct FaceIngr { double* a[3][6]; };
 struct E3 { double* e[3]; };
 struct L6 { double* q[6]; };            // stage increment of rho, mx, my, mz, E (2D: + Bz)
 
@@ -479,7 +484,7 @@ __host__ __device__ __forceinline__ long long sweep_work(const Grid& g, int segl
 // from f0 - 1 - R (and identically on every lane of a warp when staged).
 template <int DIR, int NDIM, int RECON, int RS, class FETCH>
 __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restrict__ Bface, const L6& L,
-                                           const Ingr5x3& ING, DevScalars* sc, int seglen, int accumulate, int base,
+                                           const FaceIngr& ING, DevScalars* sc, int seglen, int accumulate, int base,
                                            int seg, bool active, bool row_interior, FETCH&& fetch) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   constexpr int R = Stencil<RECON>::R;
@@ -564,7 +569,7 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
     double bn = Bface[cf];
     Flux7 F;
     Ingr ing;
-    if (RS == RS_HLLD) riemann_hlld(L7, R7, bn, g.gamma, g.igm1, F, ing);
+    if (RS != RS_HLL) riemann_hlld<double, RS == RS_HLLD_UCT>(L7, R7, bn, g.gamma, g.igm1, F, ing);
     else riemann_hll(L7, R7, bn, g.gamma, g.igm1, F, ing);
     if (active && f < f1) {
       ING.a[DIR][0][cf] = ing.ap;
@@ -572,6 +577,7 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
       ING.a[DIR][2][cf] = ing.dd;
       ING.a[DIR][3][cf] = ing.uL;
       ING.a[DIR][4][cf] = ing.uR;
+      if (RS == RS_HLLD_UCT) ING.a[DIR][5][cf] = ing.dr;
     }
     if (f > f0 && row_interior) {
       int cc = cf - st;  // cell f-1
@@ -603,7 +609,7 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
 // (see sweep_item below for what a sweep item does).
 template <int DIR, int NDIM, int RECON, int RS>
 __device__ __forceinline__ void sweep_item_direct(const Grid& g, const F8& P, const double* __restrict__ Bface, const L6& L,
-                                           const Ingr5x3& ING, DevScalars* sc, int seglen, int accumulate,
+                                           const FaceIngr& ING, DevScalars* sc, int seglen, int accumulate,
                                            long long id) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   // transverse ranges: fast index u, slow index w
@@ -641,7 +647,7 @@ __device__ __forceinline__ void sweep_item_direct(const Grid& g, const F8& P, co
 // shared-memory stage of kXStageWarp doubles (two chunk buffers).
 template <int NDIM, int RECON, int RS>
 __device__ __forceinline__ void sweep_item_staged(const Grid& g, const F8& P, const double* __restrict__ Bface,
-                                                  const L6& L, const Ingr5x3& ING, DevScalars* sc, int seglen,
+                                                  const L6& L, const FaceIngr& ING, DevScalars* sc, int seglen,
                                                   int accumulate, long long id, double* stage) {
   constexpr int DIR = 0, T1 = 1, T2 = 2;
   const int lu = -1, lv = NDIM == 3 ? -1 : 0;
@@ -712,7 +718,7 @@ __device__ __forceinline__ void sweep_item_staged(const Grid& g, const F8& P, co
 // ---------------------------------------------------------------------------
 template <int DIR, int NDIM, int RECON, int RS, bool STAGED = false>
 static __global__ void MHD_SWEEP_BOUNDS
-    sweep_kernel(Grid g, F8 P, const double* __restrict__ Bface, L6 L, Ingr5x3 ING, DevScalars* sc, int seglen,
+    sweep_kernel(Grid g, F8 P, const double* __restrict__ Bface, L6 L, FaceIngr ING, DevScalars* sc, int seglen,
                  int accumulate) {
   if constexpr (STAGED) {
     static_assert(DIR == 0, "only the x sweep stages");
@@ -731,12 +737,15 @@ static __global__ void MHD_SWEEP_BOUNDS
 //   E_c = -(a+_a u^W B_b^W + a-_a u^E B_b^E) + d_a (B_b^E - B_b^W)
 //         + (a+_b u^S B_a^S + a-_b u^N B_a^N) - d_b (B_a^N - B_a^S)
 // with the a-face ingredients averaged over the two a-faces touching the edge
-// and minmod reconstructions of the face fields to the edge.
+// and minmod reconstructions of the face fields to the edge.  UCT-HLLD
+// (HLLD = true): the same form with the HLLD weights a^L, a^R and separate
+// d^L, d^R, i.e. the dissipation terms (d^R_a B_b^E - d^L_a B_b^W) and
+// -(d^R_b B_a^N - d^L_b B_a^S).
 // ---------------------------------------------------------------------------
 // The averages of two face values carry a factor 1/2 each; it is folded into
 // the sums as exact power-of-two scalings: a+ u^W = (1/4)(a1 + a2)(u1 + u2).
-template <int C>
-__device__ __forceinline__ double uct_edge(const Grid& g, const F8& S, const Ingr5x3& ING, int c) {
+template <int C, bool HLLD = false>
+__device__ __forceinline__ double uct_edge(const Grid& g, const F8& S, const FaceIngr& ING, int c) {
   constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
   const int sa = g.stride(A), sb = g.stride(B);
   const int cb = c - sb, ca = c - sa;
@@ -760,7 +769,13 @@ __device__ __forceinline__ double uct_edge(const Grid& g, const F8& S, const Ing
   double BaN = fma(-0.5, minmod(da0, dap), a0);
   // 4 E = -(A+a uW BbW + A-a uE BbE) + (A+b vS BaS + A-b vN BaN) + 2 (Da (BbE-BbW) - Db (BaN-BaS))
   double up = fma(apb * vS, BaS, (amb * vN) * BaN) - fma(apa * uW, BbW, (ama * uE) * BbE);
-  double diss = fma(dda, BbE - BbW, -ddb * (BaN - BaS));
+  double diss;
+  if (HLLD) {
+    const double dra = ING.a[A][5][cb] + ING.a[A][5][c], drb = ING.a[B][5][ca] + ING.a[B][5][c];
+    diss = fma(dra, BbE, -dda * BbW) - fma(drb, BaN, -ddb * BaS);
+  } else {
+    diss = fma(dda, BbE - BbW, -ddb * (BaN - BaS));
+  }
   return fma(0.25, up, 0.5 * diss);
 }
 
@@ -768,8 +783,8 @@ template <int NDIM>
 __host__ __device__ __forceinline__ long long edge_work(const Grid& g) {
   return (long long)(g.n[0] + 1) * (g.n[1] + 1) * (NDIM == 3 ? g.n[2] + 1 : 1);
 }
-template <int NDIM>
-__device__ __forceinline__ void emf_item(const Grid& g, const F8& S, const Ingr5x3& ING, const E3& E, long long id) {
+template <int NDIM, bool HLLD = false>
+__device__ __forceinline__ void emf_item(const Grid& g, const F8& S, const FaceIngr& ING, const E3& E, long long id) {
   const int ex = g.n[0] + 1, ey = g.n[1] + 1;
   int i = (int)(id % ex);
   long long r = id / ex;
@@ -777,19 +792,19 @@ __device__ __forceinline__ void emf_item(const Grid& g, const F8& S, const Ingr5
   int k = (int)(r / ey);
   int c = g.at(i, j, k);
   if (NDIM == 2) {
-    E.e[2][c] = uct_edge<2>(g, S, ING, c);
+    E.e[2][c] = uct_edge<2, HLLD>(g, S, ING, c);
   } else {
-    if (k < g.n[2]) E.e[2][c] = uct_edge<2>(g, S, ING, c);  // E_z at (x-face i, y-face j, cell k)
-    if (i < g.n[0]) E.e[0][c] = uct_edge<0>(g, S, ING, c);  // E_x at (cell i, y-face j, z-face k)
-    if (j < g.n[1]) E.e[1][c] = uct_edge<1>(g, S, ING, c);  // E_y at (x-face i, cell j, z-face k)
+    if (k < g.n[2]) E.e[2][c] = uct_edge<2, HLLD>(g, S, ING, c);  // E_z at (x-face i, y-face j, cell k)
+    if (i < g.n[0]) E.e[0][c] = uct_edge<0, HLLD>(g, S, ING, c);  // E_x at (cell i, y-face j, z-face k)
+    if (j < g.n[1]) E.e[1][c] = uct_edge<1, HLLD>(g, S, ING, c);  // E_y at (x-face i, cell j, z-face k)
   }
 }
-template <int NDIM>
-static __global__ void __launch_bounds__(256) emf_kernel(Grid g, F8 S, Ingr5x3 ING, E3 E) {
+template <int NDIM, bool HLLD>
+static __global__ void __launch_bounds__(256) emf_kernel(Grid g, F8 S, FaceIngr ING, E3 E) {
   const long long total = edge_work<NDIM>(g);
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x)
-    emf_item<NDIM>(g, S, ING, E, id);
+    emf_item<NDIM, HLLD>(g, S, ING, E, id);
 }
 
 // ---------------------------------------------------------------------------
@@ -916,7 +931,7 @@ struct RunDev {
   F8 U[3];        // RK registers
   F8 P;           // primitives
   L6 L;           // stage increment
-  Ingr5x3 ING;    // UCT face ingredients
+  FaceIngr ING;    // UCT face ingredients
   E3 E;           // edge fields
   DevScalars* sc;
   int seglen;     // sweep segment length of this run
@@ -982,13 +997,13 @@ static __global__ void MHD_SWEEP_BOUNDS
   sweep_item_direct<DIR, NDIM, RECON, RS>(R.g, R.P, R.U[reg].q[5 + DIR], R.L, R.ING, R.sc, R.seglen, accumulate,
                                           block_local_id(blk0, r));
 }
-template <int NDIM>
+template <int NDIM, bool HLLD>
 static __global__ void __launch_bounds__(256) batch_emf_kernel(const RunDev* __restrict__ runs,
                                                         const int* __restrict__ blk0, int nruns, int reg) {
   const int r = block_run(blk0, nruns);
   const RunDev& R = runs[r];
   const long long id = block_local_id(blk0, r);
-  if (id < edge_work<NDIM>(R.g)) emf_item<NDIM>(R.g, R.U[reg], R.ING, R.E, id);
+  if (id < edge_work<NDIM>(R.g)) emf_item<NDIM, HLLD>(R.g, R.U[reg], R.ING, R.E, id);
 }
 template <int NDIM>
 static __global__ void __launch_bounds__(256) batch_ct_rk_kernel(const RunDev* __restrict__ runs,

@@ -232,9 +232,11 @@ __device__ __forceinline__ void side_state(const W7T<T>& W, T bn, T bn2, double 
 }
 
 // Outer speed estimate S_L, S_R (Miyoshi & Kusano 2005) and the UCT-HLL
-// ingredients a+ = aR/(aR-aL), a- = -aL/(aR-aL), d = -aR aL/(aR-aL).
+// ingredients a+ = aR/(aR-aL), a- = -aL/(aR-aL), d = -aR aL/(aR-aL).  With
+// the UCT-HLLD weights (riemann_hlld<T, true>) ap, am, dd, dr hold a^L, a^R,
+// d^L, d^R instead.
 template <class T> struct IngrT {
-  T ap, am, dd, uL, uR;
+  T ap, am, dd, uL, uR, dr;
 };
 using Ingr = IngrT<double>;
 template <class T>
@@ -324,7 +326,17 @@ __device__ __forceinline__ void side_full(const W7T<T>& W, T bn, T bn2, double i
 // give their total pressure and fast speed; the star transverse states of
 // both sides feed the double-star state; conserved states, energies and the
 // flux are assembled only on the side of the contact that holds x/t = 0.
-template <class T>
+//
+// UCT: the edge-field weights of the HLLD flux itself (UCT-HLLD).  In every
+// region of the fan the flux of a transverse field component equals
+// a^L F_L + a^R F_R + d^L B_L - d^R B_R with F = u B_t - v_t B_n, and with
+// e = B*_t / B_t the star ratio of a side:
+//   supersonic:          (1, 0, 0, 0) or (0, 1, 0, 0);
+//   S_L < 0 <= S*_L:     (1, 0, S_L (e_L - 1), 0);
+//   S*_L < 0 <= S*_R:    a^L = S*_R / (S*_R - S*_L), a^R = -S*_L / (S*_R - S*_L),
+//                        d^L = a^L ((S_L - S*_L) e_L - S_L), d^R = a^R (S_R - (S_R - S*_R) e_R);
+//   S*_R < 0 <= S_R:     (0, 1, 0, S_R (1 - e_R)).
+template <class T, bool UCT = false>
 __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T bn, double gamma, double igm1,
                                              Flux7T<T>& F, IngrT<T>& ing) {
   const T bn2 = bn * bn;
@@ -347,6 +359,12 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
     const bool up_left = gt0(SL);
     T U[7], vB;
     side_full(up_left ? L : R, bn, bn2, igm1, up_left ? ll : lr, U, F.f, vB);
+    if (UCT) {
+      ing.ap = up_left ? T(1.0) : T(0.0);
+      ing.am = up_left ? T(0.0) : T(1.0);
+      ing.dd = T(0.0);
+      ing.dr = T(0.0);
+    }
     return;
   }
   T sdL = SL - L.u, sdR = SR - R.u;
@@ -360,6 +378,7 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
   T ismL = rcp(smL), ismR = rcp(smR);
   T rhosL = rsL * ismL, rhosR = rsR * ismR;
   T vsL, wsL, b1sL, b2sL, vsR, wsR, b1sR, b2sR;
+  T eL(1.0), eR(1.0);  // star ratios B*_t / B_t (UCT weights)
   {
     T rsm = mul_rn(rsL, smL), D = rsm - bn2;
     if (lt_pos(fabs(D), kHlldDegenEps * rsm)) {
@@ -372,6 +391,7 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
       T cb = fma(rsL, sdL, -bn2) * iD;
       b1sL = L.b1 * cb;
       b2sL = L.b2 * cb;
+      if (UCT) eL = cb;
     }
   }
   {
@@ -386,7 +406,15 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
       T cb = fma(rsR, sdR, -bn2) * iD;
       b1sR = R.b1 * cb;
       b2sR = R.b2 * cb;
+      if (UCT) eR = cb;
     }
+  }
+  if (UCT) {  // the single-star region of the contact's side; replaced below in the double-star one
+    const bool lc = ge0(SM);
+    ing.ap = lc ? T(1.0) : T(0.0);
+    ing.am = lc ? T(0.0) : T(1.0);
+    ing.dd = lc ? SL * (eL - T(1.0)) : T(0.0);
+    ing.dr = lc ? T(0.0) : SR * (T(1.0) - eR);
   }
   // the side of the contact that contains x/t = 0
   const bool left = ge0(SM);
@@ -409,6 +437,15 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
     T abn = fabs(bn);
     T Ss = left ? fma(-abn, iqL, SM) : fma(abn, iqR, SM);
     bool beyond = left ? lt0(Ss) : ge0(Ss);      // x/t = 0 lies between S*_a and S_M
+    if (UCT && beyond) {                         // S*_L < 0 <= S*_R
+      T SsL = fma(-abn, iqL, SM), SsR = fma(abn, iqR, SM);
+      T iw = rcp(SsR - SsL);
+      T aL = SsR * iw, aR = -SsL * iw;
+      ing.ap = aL;
+      ing.am = aR;
+      ing.dd = aL * fma(SL - SsL, eL, -SL);
+      ing.dr = aR * fma(SsR - SR, eR, SR);
+    }
     if (beyond) {
       T isum = rcp(sqL + sqR);
       T vss = fma(sqL, vsL, fma(sqR, vsR, times_sign(b1sR - b1sL, bn))) * isum;

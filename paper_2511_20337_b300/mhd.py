@@ -25,6 +25,7 @@ BC = {"periodic": 0, "outflow": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
 KEYS = ("rho", "mx", "my", "mz", "E", "b0", "b1", "b2")
 DIVB = {"ct": 0, "glm": 1}
+EMF = {"uct_hll": 0, "uct_hlld": 1}
 # divergence cleaning: cell-centred field and psi
 GLM_KEYS = ("rho", "mx", "my", "mz", "E", "bx", "by", "bz", "psi")
 
@@ -38,7 +39,8 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
            "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen",
            "mhd_batch_get_conserved_async", "mhd_batch_synchronize", "mhd_batch_packed_size",
-           "mhd_batch_set_conserved_packed", "mhd_batch_get_conserved_packed", "mhd_set_time")
+           "mhd_batch_set_conserved_packed", "mhd_batch_get_conserved_packed", "mhd_set_time",
+           "mhd_probe_riemann")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -55,7 +57,8 @@ class mhd_config(ctypes.Structure):
                 ("x0", ctypes.c_double * 3), ("x1", ctypes.c_double * 3), ("gamma", ctypes.c_double),
                 ("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("rk", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6), ("p_floor", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("divb", ctypes.c_int), ("glm_alpha", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("divb", ctypes.c_int), ("glm_alpha", ctypes.c_double),
+                ("emf", ctypes.c_int)]
 
 
 _lib = None
@@ -117,6 +120,7 @@ def lib():
             "mhd_set_psi": (I, [P, I, P]),
             "mhd_get_psi": (I, [P, I, P]),
             "mhd_probe_cfl_rate": (I, [I, D, P, I, P, P, P]),
+            "mhd_probe_riemann": (I, [I, I, I, D, P, P, P]),
             "mhd_get_seglen": (I, [P, ctypes.POINTER(I)]),
         }
         for name, (res, args) in sig.items():
@@ -153,6 +157,7 @@ def make_config(cfg, stream=None):
     c.stream = stream
     c.divb = DIVB[cfg.get("divb", "ct")]
     c.glm_alpha = cfg.get("glm_alpha", 0.1)
+    c.emf = EMF[cfg.get("emf", "uct_hll")]
     return c
 
 
@@ -434,6 +439,19 @@ def probe_riemann_vjp(solver, inputs, cotangents, gamma):
     _check(lib().mhd_probe_riemann_vjp(RIEMANN[solver], n, float(gamma), _ptr(x), _ptr(c), _ptr(dual), _ptr(hand)),
            "mhd_probe_riemann_vjp")
     return dual, hand
+
+
+def probe_riemann(solver, inputs, gamma, emf="uct_hll"):
+    """The sweeps' Riemann solver on the GPU at faces inputs (n, 15) = left
+    (rho, u, v, w, b1, b2, p), right (same), b_n -> (F (n, 7), ingredients
+    (n, 6) = a^L, a^R, d^L, u_L, u_R, d^R); emf="uct_hlld" gives the HLLD
+    weights (HLLD only)."""
+    x = np.ascontiguousarray(np.asarray(inputs, dtype=np.float64))
+    n = x.shape[0]
+    F, ing = np.zeros((n, 7)), np.zeros((n, 6))
+    _check(lib().mhd_probe_riemann(RIEMANN[solver], EMF[emf], n, float(gamma), _ptr(x), _ptr(F), _ptr(ing)),
+           "mhd_probe_riemann")
+    return F, ing
 
 
 def probe_cfl_rate(ndim, gamma, dx, prim):

@@ -50,6 +50,8 @@ VARIANTS = {
     "orszag_tang2d_wenoz_hlld_rk3": lambda: W.orszag_tang_2d(32, recon="wenoz", rk=3),
     "orszag_tang3d_wenoz_hlld_rk3": lambda: W.orszag_tang_3d(16, recon="wenoz", rk=3),
     "cpa3d_wenoz_hlld_rk3": lambda: W.cpa_3d(16, recon="wenoz", rk=3),
+    "orszag_tang3d_wenoz_hlld_rk3_ucthlld": lambda: W.orszag_tang_3d(16, recon="wenoz", rk=3, emf="uct_hlld"),
+    "cpa3d_wenoz_hlld_rk3_ucthlld": lambda: W.cpa_3d(16, recon="wenoz", rk=3, emf="uct_hlld"),
     "adjoint2d_plm_hlld_rk2": lambda: W.adjoint_2d(32),
     "adjoint2d_plm_hll_rk2": lambda: W.adjoint_2d(32, riemann="hll"),
 }
@@ -135,7 +137,7 @@ def main():
             # the counting run's c2p units include the CFL pass, which the tape run does not make
             u_adj = u[ph] * cfg["rk"] / (cfg["rk"] + 1) if ph == "c2p" else u[ph]
             adj[ph] = (fwd * u_adj / u[ph] + pfl + links) / u_adj
-        out["variants"][name] = {"config": {k: cfg[k] for k in ("ndim", "n", "recon", "riemann", "rk", "bc")},
+        out["variants"][name] = {"config": {k: cfg[k] for k in ("ndim", "n", "recon", "riemann", "rk", "bc", "emf")},
                                  "per_unit": per, "adjoint_per_unit": adj}
     for name, make in GLM_VARIANTS.items():
         cfg, st = make()

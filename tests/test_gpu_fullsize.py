@@ -130,8 +130,8 @@ def test_blast3d_512():
 
 
 def test_orszag_tang3d_704():
-    """The paper's 3D Orszag-Tang setup at 704 x 704 x 352 with WENO-Z + HLLD + SSP-RK3."""
-    cfg, st = W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3)
+    """The paper's 3D Orszag-Tang setup at 704 x 704 x 352 with WENO-Z + HLLD + SSP-RK3 and UCT-HLLD edge fields."""
+    cfg, st = W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3, emf="uct_hlld")
     dt, out = bench_step(cfg, st)
     assert dt == oracle.cfl_dt_state(cfg, st)
     boxes = [[702, 703, 350], [352, 176, 88], [0, 500, 351]] + random_boxes(cfg, 4, 3, 4)
@@ -271,7 +271,7 @@ def test_conservation_and_div_b_at_full_size(name, nsteps):
     if name == "turbulent3d-256":
         cfg, st = W.turbulent_3d(256)
     else:
-        cfg, st = W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3)
+        cfg, st = W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3, emf="uct_hlld")
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     devs = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in st.items()}
