@@ -243,8 +243,11 @@ def sweep_source_hash(files=SWEEP_SOURCES):
 def fp64_peak(dev):
     """The FP64 ALU roofline: SMs x 2 FP64 FMAs per clock (the FP64 pipe rate;
     1.25 TFLOP/s nominal) x 2 flops x the maximum SM clock of MEASURED_PEAKS.json
-    (2032 MHz on this B300), with the DFMA-chain probe's measured rate for
-    context.  Returns (peak GFLOP/s, its source, probe GFLOP/s)."""
+    (2032 MHz on this B300).  Also returns the pipe's measured issue rates by
+    instruction form (mhd_probe_fp64_forms, GFLOP/s equivalents): a DFMA chain
+    with its operands in registers reaches the derived peak; DFMA with a
+    constant operand, DMUL and DADD issue at a lower rate.
+    Returns (peak GFLOP/s, its source, rates)."""
     import torch
     from paper_2511_20337_b300 import mhd
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -254,8 +257,8 @@ def fp64_peak(dev):
         mhz = float(json.load(open(path)).get("sm_max_mhz", mhz))
     peak = sms * 2 * 2 * mhz * 1e6 / 1e9
     src = (f"derived: {sms} SMs x 2 FP64 FMA per clock x 2 flops x {mhz:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz); "
-           "a DFMA-chain probe reaches probe_gflops of it")
-    return peak, src, mhd.probe_fp64_gflops()
+           "fp64_issue_rates gives the measured pipe rate by instruction form (probe_gflops: DFMA with register operands)")
+    return peak, src, mhd.probe_fp64_forms()
 
 
 def sweep_traffic(cfg, faces_per_launch):
@@ -462,7 +465,8 @@ def run_ours(args):
     # ---- per-kernel device times (events after each launch) for the roofline ----
     prof_steps = max(1, min(args.steps, 10))
     kms, kcnt = sim.profile_steps(prof_steps)
-    peak, peak_src, probe = fp64_peak(dev)
+    peak, peak_src, rates = fp64_peak(dev)
+    probe = rates["dfma"]
     fm = flop_model(cfg, variant)
     nd = cfg["ndim"]
     sweep_ms = sum(kms[f"sweep_{a}"] for a in "xyz"[:nd])
@@ -478,6 +482,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": sweep_name,
                 "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
                 "peak_source": peak_src, "probe_gflops": probe, "frac_of_probe": achieved / probe,
+                "fp64_issue_rates": rates,
                 "algorithmic_flops_per_launch": sweep_flops / sweep_launches,
                 "avg_launch_ms": sweep_ms / sweep_launches,
                 "traffic": sweep_traffic(cfg, faces_per_launch),
@@ -610,7 +615,8 @@ def run_ensemble(args):
     # roofline of the batched sweep (events after each launch)
     prof_steps = max(1, min(args.steps, 5))
     kms, kcnt = bt.profile_steps(prof_steps)
-    peak, peak_src, probe = fp64_peak(dev)
+    peak, peak_src, rates = fp64_peak(dev)
+    probe = rates["dfma"]
     fms = [flop_model(c, variant) for c in cfgs]
     sweep_ms = kms["sweep_x"] + kms["sweep_y"]
     sweep_launches = kcnt["sweep_x"] + kcnt["sweep_y"]
@@ -621,6 +627,7 @@ def run_ensemble(args):
     roofline = {"bound": "alu", "kernel": "batch_sweep_kernel (fused reconstruct + HLLD + flux difference, all runs)",
                 "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
                 "peak_source": peak_src, "probe_gflops": probe, "frac_of_probe": achieved / probe,
+                "fp64_issue_rates": rates,
                 "algorithmic_flops_per_launch": sweep_flops / sweep_launches,
                 "avg_launch_ms": sweep_ms / sweep_launches, "traffic": None,
                 "traffic_note": "no ncu capture of the batched sweep",
@@ -811,7 +818,8 @@ def run_adjoint(args):
     # phases and kernel classes (events on the library stream; syncs every reverse step)
     sim.set_conserved(devs)
     phases, classes = sim.adjoint_profile(N, dts, K)
-    peak, peak_src, probe = fp64_peak(dev)
+    peak, peak_src, rates = fp64_peak(dev)
+    probe = rates["dfma"]
     am = adjoint_flop_model(cfg, variant)
     nd = cfg["ndim"]
     riemann_launches = N * cfg["rk"] * nd
@@ -821,6 +829,7 @@ def run_adjoint(args):
     roofline = {"bound": "alu", "kernel": "adj_riemann_kernel (Riemann solver + flux difference transpose, per face)",
                 "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
                 "peak_source": peak_src, "probe_gflops": probe, "frac_of_probe": achieved / probe,
+                "fp64_issue_rates": rates,
                 "algorithmic_flops_per_launch": am["riemann_per_launch"],
                 "algorithmic_definition": "reverse-mode work of the oracle's Riemann solve from its tape: forward "
                                           "flops + partial-derivative flops + backward sweep (1 flop per +-1 link, "

@@ -85,11 +85,24 @@ int mhd_probe_riemann(int riemann, int emf, int n, double gamma, const double* i
 int mhd_probe_cfl_rate(int ndim, double gamma, const double* dx, int n, const double* prim, double* near_out,
                        double* ieee_out);
 
-/* Measure the device's FP64 fused multiply-add throughput on the current
- * device: every SM runs independent chains of dependent DFMA for about
- * 20 ms; *gflops_out = 2 * DFMA per second / 1e9.  Sync; allocates and frees
- * a small device buffer. */
+/* Measure the FP64 pipe's throughput on the current device: every SM runs
+ * eight independent chains of dependent DFMA per thread (all operands in
+ * registers, the addend shared by the chains) for about 20 ms;
+ * *gflops_out = 2 * DFMA per second / 1e9.  Sync; allocates and frees a
+ * small device buffer. */
 int mhd_probe_fp64(double* gflops_out);
+
+/* The issue rate of the FP64 pipe for the instruction forms below, each
+ * measured as mhd_probe_fp64 is, reported as 2 * instructions per second / 1e9
+ * (so directly comparable with a DFMA peak).  rates[MHD_FP64_NFORMS]; about
+ * 0.1 s.  Sync. */
+#define MHD_FP64_FORM_DFMA          0  /* DFMA, operands in registers, shared addend (= mhd_probe_fp64) */
+#define MHD_FP64_FORM_DFMA_CONST    1  /* DFMA with a kernel-parameter (constant-bank) operand */
+#define MHD_FP64_FORM_DFMA_DISTINCT 2  /* DFMA, register operands, a different addend register per chain */
+#define MHD_FP64_FORM_DMUL          3  /* DMUL of two registers */
+#define MHD_FP64_FORM_DADD          4  /* DADD of two registers */
+#define MHD_FP64_NFORMS             5
+int mhd_probe_fp64_forms(double* rates);
 
 #ifdef __cplusplus
 }

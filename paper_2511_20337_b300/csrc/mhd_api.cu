@@ -797,16 +797,79 @@ int mhd_profile_steps(mhd_ctx* c, int nsteps, double* ms_out, int* launches_out)
 }  // extern "C"
 
 namespace {
-// Independent chains of dependent DFMA per thread; the result is stored so the
-// chains are live.
-__global__ void fp64_probe_kernel(double* out, double a, double b, int iters) {
-  double c0 = threadIdx.x * 1e-3, c1 = c0 + 1, c2 = c0 + 2, c3 = c0 + 3, c4 = c0 + 4, c5 = c0 + 5, c6 = c0 + 6,
-         c7 = c0 + 7;
+// Eight independent chains of dependent FP64 instructions per thread, in one of
+// the instruction forms of MHD_FP64_FORM_*; the result is stored so the chains
+// are live.  The operands a, b come from device memory (registers), except in
+// the constant-operand form, where they are kernel parameters.
+template <int FORM>
+__global__ void fp64_probe_kernel(double* out, const double* __restrict__ ab, double pa, double pb, int iters) {
+  const double a = FORM == MHD_FP64_FORM_DFMA_CONST ? pa : ab[0];
+  const double b = FORM == MHD_FP64_FORM_DFMA_CONST ? pb : ab[1];
+  const double b2 = ab[2], b3 = ab[3];
+  double c[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) c[q] = threadIdx.x * 1e-3 + q;
   for (int i = 0; i < iters; i++) {
-    c0 = fma(c0, a, b); c1 = fma(c1, a, b); c2 = fma(c2, a, b); c3 = fma(c3, a, b);
-    c4 = fma(c4, a, b); c5 = fma(c5, a, b); c6 = fma(c6, a, b); c7 = fma(c7, a, b);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      if (FORM == MHD_FP64_FORM_DMUL) c[q] = c[q] * a;
+      else if (FORM == MHD_FP64_FORM_DADD) c[q] = c[q] + b;
+      else if (FORM == MHD_FP64_FORM_DFMA_DISTINCT) c[q] = fma(c[q], a, (q & 1) ? b3 : ((q & 2) ? b2 : b));
+      else c[q] = fma(c[q], a, b);
+    }
   }
-  out[blockIdx.x * blockDim.x + threadIdx.x] = ((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7));
+  out[blockIdx.x * blockDim.x + threadIdx.x] = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+}
+template <int FORM>
+float time_probe(double* buf, const double* ab, int blocks, int threads, int iters) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 5; rep++) {
+    cudaEventRecord(e0, 0);
+    fp64_probe_kernel<FORM><<<blocks, threads>>>(buf, ab, 0.999999, 1e-7, iters);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+// Rates of the forms in GFLOP/s equivalents (2 flops per FP64 instruction).
+int probe_forms(double* rates, int nforms) {
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 256, blocks = sms * 8, iters = 4096;
+  double *buf = nullptr, *ab = nullptr;
+  CK(cudaMalloc(&buf, sizeof(double) * threads * blocks));
+  if (cudaMalloc(&ab, 4 * sizeof(double)) != cudaSuccess) {
+    cudaFree(buf);
+    return MHD_ERR_OOM;
+  }
+  const double h[4] = {0.999999, 1e-7, 2e-7, 3e-7};
+  cudaError_t e = cudaMemcpy(ab, h, sizeof(h), cudaMemcpyHostToDevice);
+  const double inst = 8.0 * iters * (double)threads * blocks;
+  float ms[MHD_FP64_NFORMS] = {};
+  if (e == cudaSuccess) {
+    ms[0] = time_probe<0>(buf, ab, blocks, threads, iters);
+    if (nforms > 1) {
+      ms[1] = time_probe<1>(buf, ab, blocks, threads, iters);
+      ms[2] = time_probe<2>(buf, ab, blocks, threads, iters);
+      ms[3] = time_probe<3>(buf, ab, blocks, threads, iters);
+      ms[4] = time_probe<4>(buf, ab, blocks, threads, iters);
+    }
+    e = cudaGetLastError();
+  }
+  cudaFree(buf);
+  cudaFree(ab);
+  if (e != cudaSuccess) return cuda_err(e);
+  for (int f = 0; f < nforms; f++) rates[f] = 2.0 * inst / (ms[f] * 1e-3) / 1e9;
+  return MHD_OK;
 }
 }  // namespace
 
@@ -876,33 +939,12 @@ int mhd_probe_riemann(int riemann, int emf, int n, double gamma, const double* i
 
 int mhd_probe_fp64(double* gflops_out) {
   if (!gflops_out) return MHD_ERR_ARG;
-  int dev = 0, sms = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int threads = 256, blocks = sms * 8, iters = 2048;
-  double* buf = nullptr;
-  CK(cudaMalloc(&buf, sizeof(double) * threads * blocks));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float best = 1e30f;
-  for (int rep = 0; rep < 5; rep++) {
-    cudaEventRecord(e0, 0);
-    fp64_probe_kernel<<<blocks, threads>>>(buf, 1.0000001, 1e-7, iters);
-    cudaEventRecord(e1, 0);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) best = ms;
-  }
-  cudaError_t e = cudaGetLastError();
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFree(buf);
-  if (e != cudaSuccess) return cuda_err(e);
-  double flops = 2.0 * 8.0 * iters * (double)threads * blocks;
-  *gflops_out = flops / (best * 1e-3) / 1e9;
-  return MHD_OK;
+  return probe_forms(gflops_out, 1);
+}
+
+int mhd_probe_fp64_forms(double* rates) {
+  if (!rates) return MHD_ERR_ARG;
+  return probe_forms(rates, MHD_FP64_NFORMS);
 }
 
 int mhd_probe_cfl_rate(int ndim, double gamma, const double* dx, int n, const double* prim, double* near_out,

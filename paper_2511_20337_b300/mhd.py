@@ -40,7 +40,7 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen",
            "mhd_batch_get_conserved_async", "mhd_batch_synchronize", "mhd_batch_packed_size",
            "mhd_batch_set_conserved_packed", "mhd_batch_get_conserved_packed", "mhd_set_time",
-           "mhd_probe_riemann")
+           "mhd_probe_riemann", "mhd_probe_fp64_forms")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -92,6 +92,7 @@ def lib():
             "mhd_strerror": (ctypes.c_char_p, [I]),
             "mhd_profile_steps": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I)]),
             "mhd_probe_fp64": (I, [ctypes.POINTER(D)]),
+            "mhd_probe_fp64_forms": (I, [P]),
             "mhd_step_noalloc": (I, [ctypes.POINTER(mhd_config), DPP, DPP, D]),
             "mhd_batch_create": (I, [I, ctypes.POINTER(mhd_config), ctypes.POINTER(P)]),
             "mhd_batch_destroy": (I, [P]),
@@ -471,6 +472,17 @@ def probe_fp64_gflops():
     g = ctypes.c_double()
     _check(lib().mhd_probe_fp64(ctypes.byref(g)), "mhd_probe_fp64")
     return g.value
+
+
+FP64_FORMS = ("dfma", "dfma_constant_operand", "dfma_distinct_addends", "dmul", "dadd")
+
+
+def probe_fp64_forms():
+    """Issue rates of the FP64 pipe by instruction form, as GFLOP/s
+    equivalents (2 per instruction): dict over FP64_FORMS."""
+    r = np.zeros(len(FP64_FORMS))
+    _check(lib().mhd_probe_fp64_forms(_ptr(r)), "mhd_probe_fp64_forms")
+    return dict(zip(FP64_FORMS, r.tolist()))
 
 
 def step_noalloc(cfg, state, dt, stream=None):
