@@ -68,6 +68,12 @@ __device__ __forceinline__ D3 mul_rn(const D3& a, const D3& b) {
   for (int k = 0; k < KT; k++) r.d[k] = fma(a.d[k], b.v, a.v * b.d[k]);
   return r;
 }
+// The DFMA forms of the double arithmetic (fmul, fadd, fsub, kmul of
+// mhd_math.cuh) are the plain operations on these numbers.
+__device__ __forceinline__ D3 fmul(const D3& a, const D3& b) { return a * b; }
+__device__ __forceinline__ D3 fadd(const D3& a, const D3& b) { return a + b; }
+__device__ __forceinline__ D3 fsub(const D3& a, const D3& b) { return a - b; }
+__device__ __forceinline__ D3 kmul(int i, const D3& x) { return rk(i) * x; }
 __device__ __forceinline__ D3 fma(const D3& a, const D3& b, const D3& c) {
   D3 r;
   r.v = fma(a.v, b.v, c.v);

@@ -509,7 +509,7 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
   double dl[7];
   if (RECON == RECON_PLM) {
 #pragma unroll
-    for (int v = 0; v < 7; v++) dl[v] = win[v][1] - win[v][0];
+    for (int v = 0; v < 7; v++) dl[v] = fsub(win[v][1], win[v][0]);
   }
   // WENO-Z: the curvatures of the stencils centred on the window's cells 1 and 2
   Curv cv[7][2];
@@ -524,7 +524,7 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
 #pragma unroll
     for (int v = 0; v < 7; v++) {
       if (RECON == RECON_PLM) {
-        const double dr = win[v][2] - win[v][1];
+        const double dr = fsub(win[v][2], win[v][1]);
         recon_plm_d(win[v][1], dl[v], dr, plus[v], minus[v]);
         dl[v] = dr;
       }
@@ -582,20 +582,20 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
     if (f > f0 && row_interior) {
       int cc = cf - st;  // cell f-1
       double dv[6];
-      dv[0] = F.f[0] - Fprev[0];
+      dv[0] = fsub(F.f[0], Fprev[0]);
       double dm[3];
-      dm[DIR] = F.f[1] - Fprev[1];
-      dm[T1] = F.f[2] - Fprev[2];
-      dm[T2] = F.f[3] - Fprev[3];
+      dm[DIR] = fsub(F.f[1], Fprev[1]);
+      dm[T1] = fsub(F.f[2], Fprev[2]);
+      dm[T2] = fsub(F.f[3], Fprev[3]);
       dv[1] = dm[0];
       dv[2] = dm[1];
       dv[3] = dm[2];
-      dv[4] = F.f[6] - Fprev[6];
+      dv[4] = fsub(F.f[6], Fprev[6]);
       constexpr int NV = NDIM == 2 ? 6 : 5;
-      if (NDIM == 2) dv[5] = (DIR == 0) ? F.f[5] - Fprev[5] : F.f[4] - Fprev[4];
+      if (NDIM == 2) dv[5] = (DIR == 0) ? fsub(F.f[5], Fprev[5]) : fsub(F.f[4], Fprev[4]);
 #pragma unroll
       for (int q = 0; q < NV; q++)  // explicit roundings: the same in every kernel that inlines this
-        L.q[q][cc] = accumulate == 2 ? dv[q] : (accumulate ? fma(-dtdx, dv[q], L.q[q][cc]) : -__dmul_rn(dtdx, dv[q]));
+        L.q[q][cc] = accumulate == 2 ? dv[q] : (accumulate ? fma(-dtdx, dv[q], L.q[q][cc]) : -fmul(dtdx, dv[q]));
     }
 #pragma unroll
     for (int v = 0; v < 7; v++) {
@@ -751,32 +751,35 @@ __device__ __forceinline__ double uct_edge(const Grid& g, const F8& S, const Fac
   const int cb = c - sb, ca = c - sa;
   const double* Ia[5] = {ING.a[A][0], ING.a[A][1], ING.a[A][2], ING.a[A][3], ING.a[A][4]};
   const double* Ib[5] = {ING.a[B][0], ING.a[B][1], ING.a[B][2], ING.a[B][3], ING.a[B][4]};
+  auto add = [](double x, double y) { return fadd(x, y); };
+  auto sub = [](double x, double y) { return fsub(x, y); };
+  auto mul = [](double x, double y) { return fmul(x, y); };
   // sums over the two a-faces (b-faces) touching the edge
-  double apa = Ia[0][cb] + Ia[0][c], ama = Ia[1][cb] + Ia[1][c], dda = Ia[2][cb] + Ia[2][c];
-  double uW = Ia[3][cb] + Ia[3][c], uE = Ia[4][cb] + Ia[4][c];
-  double apb = Ib[0][ca] + Ib[0][c], amb = Ib[1][ca] + Ib[1][c], ddb = Ib[2][ca] + Ib[2][c];
-  double vS = Ib[3][ca] + Ib[3][c], vN = Ib[4][ca] + Ib[4][c];
+  double apa = add(Ia[0][cb], Ia[0][c]), ama = add(Ia[1][cb], Ia[1][c]), dda = add(Ia[2][cb], Ia[2][c]);
+  double uW = add(Ia[3][cb], Ia[3][c]), uE = add(Ia[4][cb], Ia[4][c]);
+  double apb = add(Ib[0][ca], Ib[0][c]), amb = add(Ib[1][ca], Ib[1][c]), ddb = add(Ib[2][ca], Ib[2][c]);
+  double vS = add(Ib[3][ca], Ib[3][c]), vN = add(Ib[4][ca], Ib[4][c]);
   const double* Bb = S.q[5 + B];
   const double* Ba = S.q[5 + A];
   // B_b along a: values at a-cells -2, -1, 0, +1 relative to the edge
   double bm2 = Bb[c - 2 * sa], bm1 = Bb[c - sa], b0 = Bb[c], bp1 = Bb[c + sa];
-  double dbm = bm1 - bm2, db0 = b0 - bm1, dbp = bp1 - b0;
-  double BbW = fma(0.5, minmod(dbm, db0), bm1);
-  double BbE = fma(-0.5, minmod(db0, dbp), b0);
+  double dbm = sub(bm1, bm2), db0 = sub(b0, bm1), dbp = sub(bp1, b0);
+  double BbW = fma(rk(RK_HALF), minmod(dbm, db0), bm1);
+  double BbE = fma(rk(RK_MHALF), minmod(db0, dbp), b0);
   double am2 = Ba[c - 2 * sb], am1 = Ba[c - sb], a0 = Ba[c], ap1 = Ba[c + sb];
-  double dam = am1 - am2, da0 = a0 - am1, dap = ap1 - a0;
-  double BaS = fma(0.5, minmod(dam, da0), am1);
-  double BaN = fma(-0.5, minmod(da0, dap), a0);
+  double dam = sub(am1, am2), da0 = sub(a0, am1), dap = sub(ap1, a0);
+  double BaS = fma(rk(RK_HALF), minmod(dam, da0), am1);
+  double BaN = fma(rk(RK_MHALF), minmod(da0, dap), a0);
   // 4 E = -(A+a uW BbW + A-a uE BbE) + (A+b vS BaS + A-b vN BaN) + 2 (Da (BbE-BbW) - Db (BaN-BaS))
-  double up = fma(apb * vS, BaS, (amb * vN) * BaN) - fma(apa * uW, BbW, (ama * uE) * BbE);
+  double up = sub(fma(mul(apb, vS), BaS, mul(mul(amb, vN), BaN)), fma(mul(apa, uW), BbW, mul(mul(ama, uE), BbE)));
   double diss;
   if (HLLD) {
-    const double dra = ING.a[A][5][cb] + ING.a[A][5][c], drb = ING.a[B][5][ca] + ING.a[B][5][c];
-    diss = fma(dra, BbE, -dda * BbW) - fma(drb, BaN, -ddb * BaS);
+    const double dra = add(ING.a[A][5][cb], ING.a[A][5][c]), drb = add(ING.a[B][5][ca], ING.a[B][5][c]);
+    diss = sub(fma(dra, BbE, -mul(dda, BbW)), fma(drb, BaN, -mul(ddb, BaS)));
   } else {
-    diss = fma(dda, BbE - BbW, -ddb * (BaN - BaS));
+    diss = fma(dda, sub(BbE, BbW), -mul(ddb, sub(BaN, BaS)));
   }
-  return fma(0.25, up, 0.5 * diss);
+  return fma(rk(RK_QUARTER), up, mul(rk(RK_HALF), diss));
 }
 
 template <int NDIM>

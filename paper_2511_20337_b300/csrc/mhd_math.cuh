@@ -24,6 +24,25 @@ constexpr double kHlldBnEps = 1e-12;
 constexpr double kWenozEps = 1e-40;
 
 // ---------------------------------------------------------------------------
+// Products, sums and differences as fused multiply-adds.  The FP64 pipe issues
+// DMUL and DADD at about 5/6 of the rate of DFMA (mhd_probe_fp64_forms), so
+// the hot arithmetic writes a b, a + b and a - b in the exact DFMA forms
+//   fma(a, b, -0) = a b,  fma(a, 1, b) = a + b,  fma(b, -1, a) = a - b
+// (x + (-0) = x for every x, and a product with +-1 is exact), and scales by
+// constants held in registers.  The constants come from a mutable device
+// table, so the compiler can fold them neither back into DMUL / DADD nor into
+// constant operands.  Every result is the same, to the bit, as the plain
+// operation's.
+// ---------------------------------------------------------------------------
+enum { RK_NZ = 0, RK_ONE, RK_MONE, RK_HALF, RK_MHALF, RK_3_8, RK_QUARTER, RK_FOUR, RK_EPS, RK_2EPS, RK_NK };
+__device__ double kRegK[RK_NK] = {-0.0, 1.0, -1.0, 0.5, -0.5, 0.375, 0.25, 4.0, kHlldDegenEps, 2.0 * kHlldBnEps};
+__device__ __forceinline__ double rk(int i) { return __ldg(&kRegK[i]); }
+__device__ __forceinline__ double fmul(double a, double b) { return fma(a, b, rk(RK_NZ)); }
+__device__ __forceinline__ double fadd(double a, double b) { return fma(a, rk(RK_ONE), b); }
+__device__ __forceinline__ double fsub(double a, double b) { return fma(b, rk(RK_MONE), a); }
+__device__ __forceinline__ double kmul(int i, double x) { return fma(rk(i), x, rk(RK_NZ)); }  // rk(i) x
+
+// ---------------------------------------------------------------------------
 // reciprocal / square root
 // ---------------------------------------------------------------------------
 #ifndef MHD_FAST_RCP
@@ -39,7 +58,7 @@ __device__ __forceinline__ double rcp(double x) {
 #if MHD_FAST_RCP
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
+  double e = fma(-x, r, rk(RK_ONE));
   return fma(r, fma(e, e, e), r);
 #else
   return 1.0 / x;
@@ -49,9 +68,9 @@ __device__ __forceinline__ double rcp(double x) {
 // ---------------------------------------------------------------------------
 // IEEE fixed-order pieces (bitwise reproducible)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double a_(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double s_(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double m_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double a_(double a, double b) { return fadd(a, b); }  // = __dadd_rn
+__device__ __forceinline__ double s_(double a, double b) { return fsub(a, b); }  // = __dsub_rn
+__device__ __forceinline__ double m_(double a, double b) { return fmul(a, b); }  // = __dmul_rn
 __device__ __forceinline__ double d_(double a, double b) { return __ddiv_rn(a, b); }
 
 // Conservative -> primitive (§2.2): v = m / rho, p = (G-1)(E - m.v/2 - B^2/2),
@@ -66,9 +85,9 @@ __device__ __forceinline__ Prim8 c2p_ieee(double rho, double mx, double my, doub
   o.vx = m_(mx, inv);
   o.vy = m_(my, inv);
   o.vz = m_(mz, inv);
-  double kin = m_(0.5, a_(a_(m_(mx, o.vx), m_(my, o.vy)), m_(mz, o.vz)));
+  double kin = m_(rk(RK_HALF), a_(a_(m_(mx, o.vx), m_(my, o.vy)), m_(mz, o.vz)));
   double B2 = a_(a_(m_(bx, bx), m_(by, by)), m_(bz, bz));
-  o.p = m_(gm1, s_(s_(en, kin), m_(0.5, B2)));
+  o.p = m_(gm1, s_(s_(en, kin), m_(rk(RK_HALF), B2)));
   o.rho = rho;
   o.bx = bx;
   o.by = by;
@@ -81,9 +100,9 @@ __device__ __forceinline__ Prim8 c2p_ieee(double rho, double mx, double my, doub
 __device__ __forceinline__ double fast_speed_ieee(double rho, double p, double B2, double bn, double gamma) {
   double gp = m_(gamma, p);
   double s = a_(gp, B2);
-  double disc = s_(m_(s, s), m_(m_(4.0, gp), m_(bn, bn)));
+  double disc = s_(m_(s, s), m_(m_(rk(RK_FOUR), gp), m_(bn, bn)));
   if (disc < 0.0) disc = 0.0;
-  double cf2 = d_(m_(0.5, a_(s, __dsqrt_rn(disc))), rho);
+  double cf2 = d_(m_(rk(RK_HALF), a_(s, __dsqrt_rn(disc))), rho);
   return __dsqrt_rn(cf2);
 }
 
@@ -128,15 +147,15 @@ __device__ __forceinline__ double rsqrt_seed(double x) {
 }
 __device__ __forceinline__ double fsqrt(double x) {
   double y = rsqrt_seed(x);
-  double s = x * y;
-  double e = fma(-s, y, 1.0);
-  double t = fma(0.375, e, 0.5) * e;
+  double s = fmul(x, y);
+  double e = fma(-s, y, rk(RK_ONE));
+  double t = fmul(fma(rk(RK_3_8), e, rk(RK_HALF)), e);
   return fma(s, t, s);
 }
 __device__ __forceinline__ double frsqrt(double x) {
   double y = rsqrt_seed(x);
-  double e = fma(-(x * y), y, 1.0);
-  double t = fma(0.375, e, 0.5) * e;
+  double e = fma(-fmul(x, y), y, rk(RK_ONE));
+  double t = fmul(fma(rk(RK_3_8), e, rk(RK_HALF)), e);
   return fma(y, t, y);
 }
 // sqrt(x) for x >= 0 (the seed of 0 is infinite)
@@ -156,7 +175,7 @@ __device__ __forceinline__ double fast_speed_near_ieee(double rho, double p, dou
   return fsqrt(cf2);
 }
 // a * b rounded once, never contracted into a neighbouring add
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return fmul(a, b); }
 
 // ---------------------------------------------------------------------------
 // Sweep-frame physics.  W = (rho, u, v, w, b1, b2, p): normal velocity u,
@@ -185,14 +204,14 @@ using Side = SideT<double>;
 template <class T>
 __device__ __forceinline__ T fast_speed_num(T p, T B2, T bn2, double gamma) {
   T gp = mul_rn(T(gamma), p);
-  T s = gp + B2;
-  T disc = fma(s, s, -(4.0 * gp) * bn2);
+  T s = fadd(gp, B2);
+  T disc = fma(s, s, -fmul(kmul(RK_FOUR, gp), bn2));
   if (lt0(disc)) disc = T(0.0);
-  return s + fsqrt0(disc);
+  return fadd(s, fsqrt0(disc));
 }
 template <class T>
 __device__ __forceinline__ T fast_speed(T rho, T p, T B2, T bn2, double gamma) {
-  return fsqrt(fast_speed_num(p, B2, bn2, gamma) * (0.5 * rcp(rho)));
+  return fsqrt(fmul(fast_speed_num(p, B2, bn2, gamma), kmul(RK_HALF, rcp(rho))));
 }
 // max(cf_L, cf_R), the only use of the two fast speeds in the solvers' outer
 // wave speeds, with one reciprocal and one square root: the side with the
@@ -200,33 +219,33 @@ __device__ __forceinline__ T fast_speed(T rho, T p, T B2, T bn2, double gamma) {
 // that side's fast_speed (a near-tie may pick the other side, ~1 ulp away).
 template <class T>
 __device__ __forceinline__ T fast_speed_max(T nL, T rhoL, T nR, T rhoR) {
-  const bool right = lt_pos(nL * rhoR, nR * rhoL);
-  return fsqrt((right ? nR : nL) * (0.5 * rcp(right ? rhoR : rhoL)));
+  const bool right = lt_pos(fmul(nL, rhoR), fmul(nR, rhoL));
+  return fsqrt(fmul(right ? nR : nL, kmul(RK_HALF, rcp(right ? rhoR : rhoL))));
 }
 
 // With CF the side's fast speed goes to s.cf, else its numerator to s.n.
 template <class T, bool CF = true>
 __device__ __forceinline__ void side_state(const W7T<T>& W, T bn, T bn2, double gamma, double igm1, SideT<T>& s) {
   s.B2 = fma(W.b1, W.b1, fma(W.b2, W.b2, bn2));
-  s.pT = fma(0.5, s.B2, W.p);
-  s.vB = fma(W.u, bn, fma(W.v, W.b1, W.w * W.b2));
-  T v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
-  T E = fma(W.p, T(igm1), 0.5 * fma(W.rho, v2, s.B2));
-  T mu = W.rho * W.u;
+  s.pT = fma(rk(RK_HALF), s.B2, W.p);
+  s.vB = fma(W.u, bn, fma(W.v, W.b1, fmul(W.w, W.b2)));
+  T v2 = fma(W.u, W.u, fma(W.v, W.v, fmul(W.w, W.w)));
+  T E = fma(W.p, T(igm1), kmul(RK_HALF, fma(W.rho, v2, s.B2)));
+  T mu = fmul(W.rho, W.u);
   s.U[0] = W.rho;
   s.U[1] = mu;
-  s.U[2] = W.rho * W.v;
-  s.U[3] = W.rho * W.w;
+  s.U[2] = fmul(W.rho, W.v);
+  s.U[3] = fmul(W.rho, W.w);
   s.U[4] = W.b1;
   s.U[5] = W.b2;
   s.U[6] = E;
   s.F[0] = mu;
-  s.F[1] = fma(mu, W.u, s.pT) - bn2;
-  s.F[2] = fma(mu, W.v, -bn * W.b1);
-  s.F[3] = fma(mu, W.w, -bn * W.b2);
-  s.F[4] = fma(W.u, W.b1, -W.v * bn);
-  s.F[5] = fma(W.u, W.b2, -W.w * bn);
-  s.F[6] = fma(E + s.pT, W.u, -bn * s.vB);
+  s.F[1] = fsub(fma(mu, W.u, s.pT), bn2);
+  s.F[2] = fma(mu, W.v, -fmul(bn, W.b1));
+  s.F[3] = fma(mu, W.w, -fmul(bn, W.b2));
+  s.F[4] = fma(W.u, W.b1, -fmul(W.v, bn));
+  s.F[5] = fma(W.u, W.b2, -fmul(W.w, bn));
+  s.F[6] = fma(fadd(E, s.pT), W.u, -fmul(bn, s.vB));
   if (CF) s.cf = fast_speed(W.rho, W.p, s.B2, bn2, gamma);
   else s.n = fast_speed_num(W.p, s.B2, bn2, gamma);
 }
@@ -241,13 +260,13 @@ template <class T> struct IngrT {
 using Ingr = IngrT<double>;
 template <class T>
 __device__ __forceinline__ void speeds(const W7T<T>& L, const W7T<T>& R, T cmax, T& SL, T& SR, IngrT<T>& ing) {
-  SL = imin(L.u, R.u) - cmax;
-  SR = imax(L.u, R.u) + cmax;
+  SL = fsub(imin(L.u, R.u), cmax);
+  SR = fadd(imax(L.u, R.u), cmax);
   T aR = gt0(SR) ? SR : T(0.0), aL = lt0(SL) ? SL : T(0.0);
-  T inv = rcp(aR - aL);
-  ing.ap = aR * inv;
-  ing.am = -aL * inv;
-  ing.dd = -(aR * aL) * inv;
+  T inv = rcp(fsub(aR, aL));
+  ing.ap = fmul(aR, inv);
+  ing.am = fmul(-aL, inv);
+  ing.dd = fmul(-fmul(aR, aL), inv);
   ing.uL = L.u;
   ing.uR = R.u;
 }
@@ -268,10 +287,11 @@ __device__ __forceinline__ void riemann_hll(const W7T<T>& L, const W7T<T>& R, T 
 #pragma unroll
     for (int q = 0; q < 7; q++) F.f[q] = sr.F[q];
   } else {
-    T inv = rcp(SR - SL);
-    T sls = SR * SL;
+    T inv = rcp(fsub(SR, SL));
+    T sls = fmul(SR, SL);
 #pragma unroll
-    for (int q = 0; q < 7; q++) F.f[q] = fma(sls, sr.U[q] - sl.U[q], fma(SR, sl.F[q], -SL * sr.F[q])) * inv;
+    for (int q = 0; q < 7; q++)
+      F.f[q] = fmul(fma(sls, fsub(sr.U[q], sl.U[q]), fma(SR, sl.F[q], -fmul(SL, sr.F[q]))), inv);
   }
 }
 
@@ -283,7 +303,7 @@ template <class T> struct SideLiteT {
 template <class T>
 __device__ __forceinline__ void side_lite(const W7T<T>& W, T bn2, double gamma, SideLiteT<T>& s) {
   s.B2 = fma(W.b1, W.b1, fma(W.b2, W.b2, bn2));
-  s.pT = fma(0.5, s.B2, W.p);
+  s.pT = fma(rk(RK_HALF), s.B2, W.p);
   s.cf = fast_speed(W.rho, W.p, s.B2, bn2, gamma);
 }
 // The same with the fast-speed numerator (see fast_speed_max), for the forward solver.
@@ -293,7 +313,7 @@ template <class T> struct SideNumT {
 template <class T>
 __device__ __forceinline__ void side_num(const W7T<T>& W, T bn2, double gamma, SideNumT<T>& s) {
   s.B2 = fma(W.b1, W.b1, fma(W.b2, W.b2, bn2));
-  s.pT = fma(0.5, s.B2, W.p);
+  s.pT = fma(rk(RK_HALF), s.B2, W.p);
   s.n = fast_speed_num(W.p, s.B2, bn2, gamma);
 }
 // Conserved state, energy, v.B and flux of one side, given its total field and
@@ -301,24 +321,24 @@ __device__ __forceinline__ void side_num(const W7T<T>& W, T bn2, double gamma, S
 template <class T, class SideInfo>
 __device__ __forceinline__ void side_full(const W7T<T>& W, T bn, T bn2, double igm1, const SideInfo& l, T U[7],
                                           T F[7], T& vB) {
-  vB = fma(W.u, bn, fma(W.v, W.b1, W.w * W.b2));
-  T v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
-  T E = fma(W.p, T(igm1), 0.5 * fma(W.rho, v2, l.B2));
-  T mu = W.rho * W.u;
+  vB = fma(W.u, bn, fma(W.v, W.b1, fmul(W.w, W.b2)));
+  T v2 = fma(W.u, W.u, fma(W.v, W.v, fmul(W.w, W.w)));
+  T E = fma(W.p, T(igm1), kmul(RK_HALF, fma(W.rho, v2, l.B2)));
+  T mu = fmul(W.rho, W.u);
   U[0] = W.rho;
   U[1] = mu;
-  U[2] = W.rho * W.v;
-  U[3] = W.rho * W.w;
+  U[2] = fmul(W.rho, W.v);
+  U[3] = fmul(W.rho, W.w);
   U[4] = W.b1;
   U[5] = W.b2;
   U[6] = E;
   F[0] = mu;
-  F[1] = fma(mu, W.u, l.pT) - bn2;
-  F[2] = fma(mu, W.v, -bn * W.b1);
-  F[3] = fma(mu, W.w, -bn * W.b2);
-  F[4] = fma(W.u, W.b1, -W.v * bn);
-  F[5] = fma(W.u, W.b2, -W.w * bn);
-  F[6] = fma(E + l.pT, W.u, -bn * vB);
+  F[1] = fsub(fma(mu, W.u, l.pT), bn2);
+  F[2] = fma(mu, W.v, -fmul(bn, W.b1));
+  F[3] = fma(mu, W.w, -fmul(bn, W.b2));
+  F[4] = fma(W.u, W.b1, -fmul(W.v, bn));
+  F[5] = fma(W.u, W.b2, -fmul(W.w, bn));
+  F[6] = fma(fadd(E, l.pT), W.u, -fmul(bn, vB));
 }
 
 // HLLD (Miyoshi & Kusano 2005): waves S_L < S*_L < S_M < S*_R < S_R with
@@ -339,19 +359,19 @@ __device__ __forceinline__ void side_full(const W7T<T>& W, T bn, T bn2, double i
 template <class T, bool UCT = false>
 __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T bn, double gamma, double igm1,
                                              Flux7T<T>& F, IngrT<T>& ing) {
-  const T bn2 = bn * bn;
+  const T bn2 = fmul(bn, bn);
   SideNumT<T> ll, lr;
   side_num(L, bn2, gamma, ll);
   side_num(R, bn2, gamma, lr);
   // outer speeds and UCT ingredients
   T cmax = fast_speed_max(ll.n, L.rho, lr.n, R.rho);
-  T SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
+  T SL = fsub(imin(L.u, R.u), cmax), SR = fadd(imax(L.u, R.u), cmax);
   {
     T aR = gt0(SR) ? SR : T(0.0), aL = lt0(SL) ? SL : T(0.0);
-    T inv = rcp(aR - aL);
-    ing.ap = aR * inv;
-    ing.am = -aL * inv;
-    ing.dd = -(aR * aL) * inv;
+    T inv = rcp(fsub(aR, aL));
+    ing.ap = fmul(aR, inv);
+    ing.am = fmul(-aL, inv);
+    ing.dd = fmul(-fmul(aR, aL), inv);
     ing.uL = L.u;
     ing.uR = R.u;
   }
@@ -367,45 +387,45 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
     }
     return;
   }
-  T sdL = SL - L.u, sdR = SR - R.u;
-  T rsL = sdL * L.rho, rsR = sdR * R.rho;  // rho (S - u)
-  T iden = rcp(rsR - rsL);
-  T SM = ((fma(rsR, R.u, -rsL * L.u) - lr.pT) + ll.pT) * iden;
-  T pTs = fma((L.rho * rsR) * sdL, R.u - L.u, fma(rsR, ll.pT, -rsL * lr.pT)) * iden;
+  T sdL = fsub(SL, L.u), sdR = fsub(SR, R.u);
+  T rsL = fmul(sdL, L.rho), rsR = fmul(sdR, R.rho);  // rho (S - u)
+  T iden = rcp(fsub(rsR, rsL));
+  T SM = fmul(fadd(fsub(fma(rsR, R.u, -fmul(rsL, L.u)), lr.pT), ll.pT), iden);
+  T pTs = fmul(fma(fmul(fmul(L.rho, rsR), sdL), fsub(R.u, L.u), fma(rsR, ll.pT, -fmul(rsL, lr.pT))), iden);
 
   // star transverse states of both sides
-  T smL = SL - SM, smR = SR - SM;
+  T smL = fsub(SL, SM), smR = fsub(SR, SM);
   T ismL = rcp(smL), ismR = rcp(smR);
-  T rhosL = rsL * ismL, rhosR = rsR * ismR;
+  T rhosL = fmul(rsL, ismL), rhosR = fmul(rsR, ismR);
   T vsL, wsL, b1sL, b2sL, vsR, wsR, b1sR, b2sR;
   T eL(1.0), eR(1.0);  // star ratios B*_t / B_t (UCT weights)
   {
-    T rsm = mul_rn(rsL, smL), D = rsm - bn2;
-    if (lt_pos(fabs(D), kHlldDegenEps * rsm)) {
+    T rsm = mul_rn(rsL, smL), D = fsub(rsm, bn2);
+    if (lt_pos(fabs(D), kmul(RK_EPS, rsm))) {
       vsL = L.v; wsL = L.w; b1sL = L.b1; b2sL = L.b2;
     } else {
       T iD = rcp(D);
-      T cv = (bn * (SM - L.u)) * iD;
+      T cv = fmul(fmul(bn, fsub(SM, L.u)), iD);
       vsL = fma(-L.b1, cv, L.v);
       wsL = fma(-L.b2, cv, L.w);
-      T cb = fma(rsL, sdL, -bn2) * iD;
-      b1sL = L.b1 * cb;
-      b2sL = L.b2 * cb;
+      T cb = fmul(fma(rsL, sdL, -bn2), iD);
+      b1sL = fmul(L.b1, cb);
+      b2sL = fmul(L.b2, cb);
       if (UCT) eL = cb;
     }
   }
   {
-    T rsm = mul_rn(rsR, smR), D = rsm - bn2;
-    if (lt_pos(fabs(D), kHlldDegenEps * rsm)) {
+    T rsm = mul_rn(rsR, smR), D = fsub(rsm, bn2);
+    if (lt_pos(fabs(D), kmul(RK_EPS, rsm))) {
       vsR = R.v; wsR = R.w; b1sR = R.b1; b2sR = R.b2;
     } else {
       T iD = rcp(D);
-      T cv = (bn * (SM - R.u)) * iD;
+      T cv = fmul(fmul(bn, fsub(SM, R.u)), iD);
       vsR = fma(-R.b1, cv, R.v);
       wsR = fma(-R.b2, cv, R.w);
-      T cb = fma(rsR, sdR, -bn2) * iD;
-      b1sR = R.b1 * cb;
-      b2sR = R.b2 * cb;
+      T cb = fmul(fma(rsR, sdR, -bn2), iD);
+      b1sR = fmul(R.b1, cb);
+      b2sR = fmul(R.b2, cb);
       if (UCT) eR = cb;
     }
   }
@@ -413,8 +433,8 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
     const bool lc = ge0(SM);
     ing.ap = lc ? T(1.0) : T(0.0);
     ing.am = lc ? T(0.0) : T(1.0);
-    ing.dd = lc ? SL * (eL - T(1.0)) : T(0.0);
-    ing.dr = lc ? T(0.0) : SR * (T(1.0) - eR);
+    ing.dd = lc ? fmul(SL, fsub(eL, T(1.0))) : T(0.0);
+    ing.dr = lc ? T(0.0) : fmul(SR, fsub(T(1.0), eR));
   }
   // the side of the contact that contains x/t = 0
   const bool left = ge0(SM);
@@ -425,43 +445,43 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
   const T S = left ? SL : SR, sd = left ? sdL : sdR, ism = left ? ismL : ismR;
   const T rhos = left ? rhosL : rhosR;
   const T vs = left ? vsL : vsR, ws = left ? wsL : wsR, b1s = left ? b1sL : b1sR, b2s = left ? b2sL : b2sR;
-  T vBs = fma(SM, bn, fma(vs, b1s, ws * b2s));
-  T Es = (fma(sd, Ua[6], -pTa * A.u) + fma(pTs, SM, bn * (vBa - vBs))) * ism;
-  T Us[7] = {rhos, rhos * SM, rhos * vs, rhos * ws, b1s, b2s, Es};
+  T vBs = fma(SM, bn, fma(vs, b1s, fmul(ws, b2s)));
+  T Es = fmul(fadd(fma(sd, Ua[6], -fmul(pTa, A.u)), fma(pTs, SM, fmul(bn, fsub(vBa, vBs)))), ism);
+  T Us[7] = {rhos, fmul(rhos, SM), fmul(rhos, vs), fmul(rhos, ws), b1s, b2s, Es};
 #pragma unroll
-  for (int q = 0; q < 7; q++) F.f[q] = fma(S, Us[q] - Ua[q], F.f[q]);
+  for (int q = 0; q < 7; q++) F.f[q] = fma(S, fsub(Us[q], Ua[q]), F.f[q]);
   // rotational (Alfven) waves, absent when the normal field vanishes
-  if (!lt_pos(bn2, (2.0 * kHlldBnEps) * pTs)) {  // 0.5 bn2 >= eps pTs, scaled by 2 exactly
+  if (!lt_pos(bn2, kmul(RK_2EPS, pTs))) {  // 0.5 bn2 >= eps pTs, scaled by 2 exactly
     T iqL = frsqrt(rhosL), iqR = frsqrt(rhosR);  // 1/sqrt(rho*)
-    T sqL = rhosL * iqL, sqR = rhosR * iqR;      // sqrt(rho*)
+    T sqL = fmul(rhosL, iqL), sqR = fmul(rhosR, iqR);  // sqrt(rho*)
     T abn = fabs(bn);
     T Ss = left ? fma(-abn, iqL, SM) : fma(abn, iqR, SM);
     bool beyond = left ? lt0(Ss) : ge0(Ss);      // x/t = 0 lies between S*_a and S_M
     if (UCT && beyond) {                         // S*_L < 0 <= S*_R
       T SsL = fma(-abn, iqL, SM), SsR = fma(abn, iqR, SM);
-      T iw = rcp(SsR - SsL);
-      T aL = SsR * iw, aR = -SsL * iw;
+      T iw = rcp(fsub(SsR, SsL));
+      T aL = fmul(SsR, iw), aR = fmul(-SsL, iw);
       ing.ap = aL;
       ing.am = aR;
-      ing.dd = aL * fma(SL - SsL, eL, -SL);
-      ing.dr = aR * fma(SsR - SR, eR, SR);
+      ing.dd = fmul(aL, fma(fsub(SL, SsL), eL, -SL));
+      ing.dr = fmul(aR, fma(fsub(SsR, SR), eR, SR));
     }
     if (beyond) {
-      T isum = rcp(sqL + sqR);
-      T vss = fma(sqL, vsL, fma(sqR, vsR, times_sign(b1sR - b1sL, bn))) * isum;
-      T wss = fma(sqL, wsL, fma(sqR, wsR, times_sign(b2sR - b2sL, bn))) * isum;
-      T sq2 = sqL * sqR;
-      T b1ss = fma(sqL, b1sR, fma(sqR, b1sL, times_sign(sq2 * (vsR - vsL), bn))) * isum;
-      T b2ss = fma(sqL, b2sR, fma(sqR, b2sL, times_sign(sq2 * (wsR - wsL), bn))) * isum;
-      T vBss = fma(SM, bn, fma(vss, b1ss, wss * b2ss));
+      T isum = rcp(fadd(sqL, sqR));
+      T vss = fmul(fma(sqL, vsL, fma(sqR, vsR, times_sign(fsub(b1sR, b1sL), bn))), isum);
+      T wss = fmul(fma(sqL, wsL, fma(sqR, wsR, times_sign(fsub(b2sR, b2sL), bn))), isum);
+      T sq2 = fmul(sqL, sqR);
+      T b1ss = fmul(fma(sqL, b1sR, fma(sqR, b1sL, times_sign(fmul(sq2, fsub(vsR, vsL)), bn))), isum);
+      T b2ss = fmul(fma(sqL, b2sR, fma(sqR, b2sL, times_sign(fmul(sq2, fsub(wsR, wsL)), bn))), isum);
+      T vBss = fma(SM, bn, fma(vss, b1ss, fmul(wss, b2ss)));
       T sqa = left ? -sqL : sqR;
-      T Ess = fma(sqa, times_sign(vBs - vBss, bn), Es);
+      T Ess = fma(sqa, times_sign(fsub(vBs, vBss), bn), Es);
       // F += S*_a (U** - U*): the density and normal momentum are continuous
       F.f[2] = fma(Ss, fma(rhos, vss, -Us[2]), F.f[2]);
       F.f[3] = fma(Ss, fma(rhos, wss, -Us[3]), F.f[3]);
-      F.f[4] = fma(Ss, b1ss - b1s, F.f[4]);
-      F.f[5] = fma(Ss, b2ss - b2s, F.f[5]);
-      F.f[6] = fma(Ss, Ess - Es, F.f[6]);
+      F.f[4] = fma(Ss, fsub(b1ss, b1s), F.f[4]);
+      F.f[5] = fma(Ss, fsub(b2ss, b2s), F.f[5]);
+      F.f[6] = fma(Ss, fsub(Ess, Es), F.f[6]);
     }
   }
 }
@@ -482,11 +502,11 @@ __device__ __forceinline__ double minmod(double a, double b) {
 // carries the right difference of a cell over as the left one of the next).
 __device__ __forceinline__ void recon_plm_d(double s2, double dl, double dr, double& plus, double& minus) {
   double d = minmod(dl, dr);
-  plus = fma(0.5, d, s2);
-  minus = fma(-0.5, d, s2);
+  plus = fma(rk(RK_HALF), d, s2);
+  minus = fma(rk(RK_MHALF), d, s2);
 }
 __device__ __forceinline__ void recon_plm(double s1, double s2, double s3, double& plus, double& minus) {
-  recon_plm_d(s2, s2 - s1, s3 - s2, plus, minus);
+  recon_plm_d(s2, fsub(s2, s1), fsub(s3, s2), plus, minus);
 }
 
 // WENO-Z (Borges et al. 2008) values at both faces of the middle cell of
