@@ -97,7 +97,7 @@ int mhd_probe_fp64(double* gflops_out);
  * (so directly comparable with a DFMA peak).  rates[MHD_FP64_NFORMS]; about
  * 0.1 s.  Sync. */
 #define MHD_FP64_FORM_DFMA          0  /* DFMA, operands in registers, shared addend (= mhd_probe_fp64) */
-#define MHD_FP64_FORM_DFMA_CONST    1  /* DFMA with a kernel-parameter (constant-bank) operand */
+#define MHD_FP64_FORM_DFMA_CONST    1  /* DFMA with literal (constant) multiplier and addend */
 #define MHD_FP64_FORM_DFMA_DISTINCT 2  /* DFMA, register operands, a different addend register per chain */
 #define MHD_FP64_FORM_DMUL          3  /* DMUL of two registers */
 #define MHD_FP64_FORM_DADD          4  /* DADD of two registers */

@@ -800,11 +800,10 @@ namespace {
 // Eight independent chains of dependent FP64 instructions per thread, in one of
 // the instruction forms of MHD_FP64_FORM_*; the result is stored so the chains
 // are live.  The operands a, b come from device memory (registers), except in
-// the constant-operand form, where they are kernel parameters.
+// the constant-operand form, where they are literals.
 template <int FORM>
-__global__ void fp64_probe_kernel(double* out, const double* __restrict__ ab, double pa, double pb, int iters) {
-  const double a = FORM == MHD_FP64_FORM_DFMA_CONST ? pa : ab[0];
-  const double b = FORM == MHD_FP64_FORM_DFMA_CONST ? pb : ab[1];
+__global__ void fp64_probe_kernel(double* out, const double* __restrict__ ab, int iters) {
+  const double a = ab[0], b = ab[1];
   const double b2 = ab[2], b3 = ab[3];
   double c[8];
 #pragma unroll
@@ -815,6 +814,7 @@ __global__ void fp64_probe_kernel(double* out, const double* __restrict__ ab, do
       if (FORM == MHD_FP64_FORM_DMUL) c[q] = c[q] * a;
       else if (FORM == MHD_FP64_FORM_DADD) c[q] = c[q] + b;
       else if (FORM == MHD_FP64_FORM_DFMA_DISTINCT) c[q] = fma(c[q], a, (q & 1) ? b3 : ((q & 2) ? b2 : b));
+      else if (FORM == MHD_FP64_FORM_DFMA_CONST) c[q] = fma(c[q], 0.999999, 1e-7);  // literal operands
       else c[q] = fma(c[q], a, b);
     }
   }
@@ -828,7 +828,7 @@ float time_probe(double* buf, const double* ab, int blocks, int threads, int ite
   float best = 1e30f;
   for (int rep = 0; rep < 5; rep++) {
     cudaEventRecord(e0, 0);
-    fp64_probe_kernel<FORM><<<blocks, threads>>>(buf, ab, 0.999999, 1e-7, iters);
+    fp64_probe_kernel<FORM><<<blocks, threads>>>(buf, ab, iters);
     cudaEventRecord(e1, 0);
     cudaEventSynchronize(e1);
     float ms = 0.f;

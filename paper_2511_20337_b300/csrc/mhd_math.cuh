@@ -34,8 +34,14 @@ constexpr double kWenozEps = 1e-40;
 // constant operands.  Every result is the same, to the bit, as the plain
 // operation's.
 // ---------------------------------------------------------------------------
-enum { RK_NZ = 0, RK_ONE, RK_MONE, RK_HALF, RK_MHALF, RK_3_8, RK_QUARTER, RK_FOUR, RK_EPS, RK_2EPS, RK_NK };
-__device__ double kRegK[RK_NK] = {-0.0, 1.0, -1.0, 0.5, -0.5, 0.375, 0.25, 4.0, kHlldDegenEps, 2.0 * kHlldBnEps};
+enum {
+  RK_NZ = 0, RK_ONE, RK_MONE, RK_HALF, RK_MHALF, RK_3_8, RK_QUARTER, RK_FOUR, RK_EPS, RK_2EPS,
+  // WENO-Z
+  RK_13_12, RK_M2, RK_3, RK_M4, RK_WEPS, RK_2, RK_M7, RK_11, RK_5, RK_0_1, RK_0_6, RK_0_3, RK_6,
+  RK_NK
+};
+__device__ double kRegK[RK_NK] = {-0.0, 1.0, -1.0, 0.5, -0.5, 0.375, 0.25, 4.0, kHlldDegenEps, 2.0 * kHlldBnEps,
+                                  13.0 / 12.0, -2.0, 3.0, -4.0, kWenozEps, 2.0, -7.0, 11.0, 5.0, 0.1, 0.6, 0.3, 6.0};
 __device__ __forceinline__ double rk(int i) { return __ldg(&kRegK[i]); }
 __device__ __forceinline__ double fmul(double a, double b) { return fma(a, b, rk(RK_NZ)); }
 __device__ __forceinline__ double fadd(double a, double b) { return fma(a, rk(RK_ONE), b); }
@@ -527,37 +533,38 @@ struct Curv {
 __device__ __forceinline__ Curv curv_of(double t) {
   Curv c;
   c.t = t;
-  c.k = 13.0 / 12.0 * t;
+  c.k = kmul(RK_13_12, t);
   return c;
 }
-__device__ __forceinline__ Curv curv(double l, double m, double r) { return curv_of(fma(-2.0, m, l) + r); }
+__device__ __forceinline__ Curv curv(double l, double m, double r) { return curv_of(fadd(fma(rk(RK_M2), m, l), r)); }
 __device__ __forceinline__ void recon_wenoz_c(double a0, double a1, double a2, double a3, double a4, const Curv& c0,
                                               const Curv& c1, Curv& c2, double& plus, double& minus) {
-  double u = fma(3.0, a2, fma(-4.0, a1, a0));
-  double b0 = fma(c0.k, c0.t, (0.25 * u) * u);
-  u = a1 - a3;
-  double b1 = fma(c1.k, c1.t, (0.25 * u) * u);
+  double u = fma(rk(RK_3), a2, fma(rk(RK_M4), a1, a0));
+  double b0 = fma(c0.k, c0.t, fmul(kmul(RK_QUARTER, u), u));
+  u = fsub(a1, a3);
+  double b1 = fma(c1.k, c1.t, fmul(kmul(RK_QUARTER, u), u));
   c2 = curv(a2, a3, a4);
-  u = fma(3.0, a2, fma(-4.0, a3, a4));
-  double b2 = fma(c2.k, c2.t, (0.25 * u) * u);
-  double tau = fabs(b0 - b2);
-  double r0 = tau * rcp(b0 + kWenozEps), r1 = tau * rcp(b1 + kWenozEps), r2 = tau * rcp(b2 + kWenozEps);
-  double g0 = fma(r0, r0, 1.0), g1 = fma(r1, r1, 1.0), g2 = fma(r2, r2, 1.0);
+  u = fma(rk(RK_3), a2, fma(rk(RK_M4), a3, a4));
+  double b2 = fma(c2.k, c2.t, fmul(kmul(RK_QUARTER, u), u));
+  double tau = fabs(fsub(b0, b2));
+  const double weps = rk(RK_WEPS);
+  double r0 = fmul(tau, rcp(fadd(b0, weps))), r1 = fmul(tau, rcp(fadd(b1, weps))), r2 = fmul(tau, rcp(fadd(b2, weps)));
+  double g0 = fma(r0, r0, rk(RK_ONE)), g1 = fma(r1, r1, rk(RK_ONE)), g2 = fma(r2, r2, rk(RK_ONE));
   // plus face: stencils (a0 a1 a2), (a1 a2 a3), (a2 a3 a4); 6 q_k
   {
-    double q0 = fma(2.0, a0, fma(-7.0, a1, 11.0 * a2));
-    double q1 = fma(5.0, a2, fma(2.0, a3, -a1));
-    double q2 = fma(2.0, a2, fma(5.0, a3, -a4));
-    double al0 = __dmul_rn(0.1, g0), al1 = __dmul_rn(0.6, g1), al2 = __dmul_rn(0.3, g2);
-    plus = fma(al0, q0, fma(al1, q1, al2 * q2)) * rcp(6.0 * ((al0 + al1) + al2));
+    double q0 = fma(rk(RK_2), a0, fma(rk(RK_M7), a1, kmul(RK_11, a2)));
+    double q1 = fma(rk(RK_5), a2, fma(rk(RK_2), a3, -a1));
+    double q2 = fma(rk(RK_2), a2, fma(rk(RK_5), a3, -a4));
+    double al0 = kmul(RK_0_1, g0), al1 = kmul(RK_0_6, g1), al2 = kmul(RK_0_3, g2);
+    plus = fmul(fma(al0, q0, fma(al1, q1, fmul(al2, q2))), rcp(kmul(RK_6, fadd(fadd(al0, al1), al2))));
   }
   // minus face: the mirrored stencils, indicators beta_2, beta_1, beta_0
   {
-    double q0 = fma(2.0, a4, fma(-7.0, a3, 11.0 * a2));
-    double q1 = fma(5.0, a2, fma(2.0, a1, -a3));
-    double q2 = fma(2.0, a2, fma(5.0, a1, -a0));
-    double al0 = __dmul_rn(0.1, g2), al1 = __dmul_rn(0.6, g1), al2 = __dmul_rn(0.3, g0);
-    minus = fma(al0, q0, fma(al1, q1, al2 * q2)) * rcp(6.0 * ((al0 + al1) + al2));
+    double q0 = fma(rk(RK_2), a4, fma(rk(RK_M7), a3, kmul(RK_11, a2)));
+    double q1 = fma(rk(RK_5), a2, fma(rk(RK_2), a1, -a3));
+    double q2 = fma(rk(RK_2), a2, fma(rk(RK_5), a1, -a0));
+    double al0 = kmul(RK_0_1, g2), al1 = kmul(RK_0_6, g1), al2 = kmul(RK_0_3, g0);
+    minus = fmul(fma(al0, q0, fma(al1, q1, fmul(al2, q2))), rcp(kmul(RK_6, fadd(fadd(al0, al1), al2))));
   }
 }
 __device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, double a3, double a4, double& plus,
