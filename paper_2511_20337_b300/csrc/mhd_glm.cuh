@@ -136,9 +136,9 @@ static __global__ void __launch_bounds__(128) glm_sweep_kernel(Grid g, F9 P, F9 
   const int f1 = min(f0 + seglen, nd + 1);
   const int fend = min(f1, nd);
   const double dt = sc->dt;
-  const double dtdx = dt * g.idx[DIR];
+  const double dtdx = fmul(dt, g.idx[DIR]);
   const double ch = glm_ch(g, dt);
-  const double hich = 0.5 * rcp(ch), ch2 = ch * ch;
+  const double hich = kmul(RK_HALF, rcp(ch)), ch2 = fmul(ch, ch);
   const double* pr[9] = {P.q[0], P.q[1 + DIR], P.q[1 + T1], P.q[1 + T2], P.q[4 + DIR],
                          P.q[4 + T1], P.q[4 + T2], P.q[7], P.q[8]};
   double win[9][W];
@@ -152,7 +152,7 @@ static __global__ void __launch_bounds__(128) glm_sweep_kernel(Grid g, F9 P, F9 
   double dl[9];
   if (RECON == RECON_PLM) {
 #pragma unroll
-    for (int v = 0; v < 9; v++) dl[v] = win[v][1] - win[v][0];
+    for (int v = 0; v < 9; v++) dl[v] = fsub(win[v][1], win[v][0]);
   }
   // WENO-Z: the curvatures of the stencils centred on the window's cells 1 and
   // 2 (their 13/12 multiples are formed again: nine variables' worth would not
@@ -169,7 +169,7 @@ static __global__ void __launch_bounds__(128) glm_sweep_kernel(Grid g, F9 P, F9 
 #pragma unroll
     for (int v = 0; v < 9; v++) {
       if (RECON == RECON_PLM) {
-        const double dr = win[v][2] - win[v][1];
+        const double dr = fsub(win[v][2], win[v][1]);
         recon_plm_d(win[v][1], dl[v], dr, plus[v], minus[v]);
         dl[v] = dr;
       }
@@ -205,8 +205,8 @@ static __global__ void __launch_bounds__(128) glm_sweep_kernel(Grid g, F9 P, F9 
     double plusN[9];
     reconstruct(plusN, wr, f < f1 && f < nd);  // cell f, counted once by the segment owning face f
     // the (B_n, psi) subsystem
-    const double Bm = fma(0.5, wl[4] + wr[4], -(wr[8] - wl[8]) * hich);
-    const double psim = fma(0.5, wl[8] + wr[8], -(0.5 * ch) * (wr[4] - wl[4]));
+    const double Bm = fma(rk(RK_HALF), fadd(wl[4], wr[4]), -fmul(fsub(wr[8], wl[8]), hich));
+    const double psim = fma(rk(RK_HALF), fadd(wl[8], wr[8]), -fmul(kmul(RK_HALF, ch), fsub(wr[4], wl[4])));
     W7 L7 = {wl[0], wl[1], wl[2], wl[3], wl[5], wl[6], wl[7]};
     W7 R7 = {wr[0], wr[1], wr[2], wr[3], wr[5], wr[6], wr[7]};
     Flux7 F7;
@@ -223,13 +223,13 @@ static __global__ void __launch_bounds__(128) glm_sweep_kernel(Grid g, F9 P, F9 
     F[5 + DIR] = psim;
     F[5 + T1] = F7.f[4];
     F[5 + T2] = F7.f[5];
-    F[8] = ch2 * Bm;
+    F[8] = fmul(ch2, Bm);
     if (f > f0) {
       const int cc = base + (f - 1) * st;  // cell f - 1
 #pragma unroll
       for (int q = 0; q < 9; q++) {
-        const double dv = F[q] - Fprev[q];
-        L.q[q][cc] = accumulate ? fma(-dtdx, dv, L.q[q][cc]) : -__dmul_rn(dtdx, dv);
+        const double dv = fsub(F[q], Fprev[q]);
+        L.q[q][cc] = accumulate ? fma(-dtdx, dv, L.q[q][cc]) : -fmul(dtdx, dv);
       }
     }
 #pragma unroll

@@ -495,7 +495,7 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
   const int f1 = min(f0 + seglen, nd + 1);  // owned faces [f0, f1)
   const int fend = min(f1, nd);             // last face computed
   const double dt = sc->dt;
-  const double dtdx = dt * g.idx[DIR];
+  const double dtdx = fmul(dt, g.idx[DIR]);
   double win[7][W];
   // load window centred on cell f0 - 1
 #pragma unroll
@@ -822,10 +822,10 @@ enum { COMB_FIRST = 0, COMB_RK2_FINAL = 1, COMB_RK3_SECOND = 2, COMB_RK3_FINAL =
 
 __device__ __forceinline__ double combine(int mode, double u0, double us, double l) {
   switch (mode) {
-    case COMB_FIRST: return us + l;
-    case COMB_RK2_FINAL: return 0.5 * ((u0 + us) + l);
-    case COMB_RK3_SECOND: return 0.25 * (fma(3.0, u0, us) + l);
-    default: return fma(2.0, l, fma(2.0, us, u0)) * (1.0 / 3.0);
+    case COMB_FIRST: return fadd(us, l);
+    case COMB_RK2_FINAL: return kmul(RK_HALF, fadd(fadd(u0, us), l));
+    case COMB_RK3_SECOND: return kmul(RK_QUARTER, fadd(fma(rk(RK_3), u0, us), l));
+    default: return fmul(fma(rk(RK_2), l, fma(rk(RK_2), us, u0)), rk(RK_THIRD));
   }
 }
 
@@ -850,8 +850,8 @@ __device__ __forceinline__ void ct_rk_item(const Grid& g, const F8& U0, const F8
       int slot = q < 5 ? q : 7;
       double l = L.q[q][c];
       if (SPLIT) {
-        l = fma(-(dt * g.idx[1]), Dy->q[q][c], l);
-        if (NDIM == 3) l = fma(-(dt * g.idx[2]), Dz->q[q][c], l);
+        l = fma(-fmul(dt, g.idx[1]), Dy->q[q][c], l);
+        if (NDIM == 3) l = fma(-fmul(dt, g.idx[2]), Dz->q[q][c], l);
       }
       Out.q[slot][c] = combine(mode, U0.q[slot][c], Us.q[slot][c], l);
     }
@@ -871,9 +871,9 @@ __device__ __forceinline__ void ct_rk_item(const Grid& g, const F8& U0, const F8
     if (!ok) continue;
     const bool has1 = d1 < NDIM, has2 = d2 < NDIM;
     double t1 = 0.0, t2 = 0.0;
-    if (has1) t1 = __dmul_rn(E.e[d2][c + g.stride(d1)] - E.e[d2][c], dt * g.idx[d1]);
-    if (has2) t2 = __dmul_rn(E.e[d1][c + g.stride(d2)] - E.e[d1][c], dt * g.idx[d2]);
-    double lb = (has1 && has2) ? t2 - t1 : (has1 ? -t1 : t2);
+    if (has1) t1 = fmul(fsub(E.e[d2][c + g.stride(d1)], E.e[d2][c]), fmul(dt, g.idx[d1]));
+    if (has2) t2 = fmul(fsub(E.e[d1][c + g.stride(d2)], E.e[d1][c]), fmul(dt, g.idx[d2]));
+    double lb = (has1 && has2) ? fsub(t2, t1) : (has1 ? -t1 : t2);
     Out.q[5 + d][c] = combine(mode, U0.q[5 + d][c], Us.q[5 + d][c], lb);
   }
 }

@@ -38,10 +38,13 @@ enum {
   RK_NZ = 0, RK_ONE, RK_MONE, RK_HALF, RK_MHALF, RK_3_8, RK_QUARTER, RK_FOUR, RK_EPS, RK_2EPS,
   // WENO-Z
   RK_13_12, RK_M2, RK_3, RK_M4, RK_WEPS, RK_2, RK_M7, RK_11, RK_5, RK_0_1, RK_0_6, RK_0_3, RK_6,
+  // PPM, RK3
+  RK_7_12, RK_1_12, RK_THIRD,
   RK_NK
 };
 __device__ double kRegK[RK_NK] = {-0.0, 1.0, -1.0, 0.5, -0.5, 0.375, 0.25, 4.0, kHlldDegenEps, 2.0 * kHlldBnEps,
-                                  13.0 / 12.0, -2.0, 3.0, -4.0, kWenozEps, 2.0, -7.0, 11.0, 5.0, 0.1, 0.6, 0.3, 6.0};
+                                  13.0 / 12.0, -2.0, 3.0, -4.0, kWenozEps, 2.0, -7.0, 11.0, 5.0, 0.1, 0.6, 0.3, 6.0,
+                                  7.0 / 12.0, 1.0 / 12.0, 1.0 / 3.0};
 __device__ __forceinline__ double rk(int i) { return __ldg(&kRegK[i]); }
 __device__ __forceinline__ double fmul(double a, double b) { return fma(a, b, rk(RK_NZ)); }
 __device__ __forceinline__ double fadd(double a, double b) { return fma(a, rk(RK_ONE), b); }
@@ -173,11 +176,11 @@ __device__ __forceinline__ double fsqrt0(double x) { return gt0(x) ? fsqrt(x) : 
 // fast_speed_ieee even where the discriminant cancels.  Used to find the
 // candidates for the largest CFL rate, which fast_speed_ieee then decides.
 __device__ __forceinline__ double fast_speed_near_ieee(double rho, double p, double B2, double bn, double gamma) {
-  double gp = __dmul_rn(gamma, p);
-  double s = __dadd_rn(gp, B2);
-  double disc = __dsub_rn(__dmul_rn(s, s), __dmul_rn(__dmul_rn(4.0, gp), __dmul_rn(bn, bn)));
+  double gp = m_(gamma, p);
+  double s = a_(gp, B2);
+  double disc = s_(m_(s, s), m_(m_(rk(RK_FOUR), gp), m_(bn, bn)));
   double sq = lt_pos(disc, 1e-290) ? 0.0 : fsqrt(disc);  // 0 for disc <= 0 and for subnormal disc
-  double cf2 = __dmul_rn(__dmul_rn(0.5, __dadd_rn(s, sq)), rcp(rho));
+  double cf2 = m_(m_(rk(RK_HALF), a_(s, sq)), rcp(rho));
   return fsqrt(cf2);
 }
 // a * b rounded once, never contracted into a neighbouring add
@@ -574,7 +577,7 @@ __device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, dou
 }
 
 __device__ __forceinline__ double ppm_face(double a, double b, double c, double d) {
-  double f = fma(7.0 / 12.0, b + c, -(1.0 / 12.0) * (a + d));
+  double f = fma(rk(RK_7_12), fadd(b, c), -kmul(RK_1_12, fadd(a, d)));
   double lo = imin(b, c), hi = imax(b, c);
   return imin(imax(f, lo), hi);
 }
@@ -585,15 +588,15 @@ __device__ __forceinline__ void recon_ppm(double s0, double s1, double s2, doubl
                                           double& minus) {
   double vp = ppm_face(s1, s2, s3, s4);
   double vm = ppm_face(s0, s1, s2, s3);
-  if (!gt0((vp - s2) * (s2 - vm))) {
+  if (!gt0(fmul(fsub(vp, s2), fsub(s2, vm)))) {
     vp = s2;
     vm = s2;
   } else {
-    double dv = vp - vm;
-    double v6 = 6.0 * fma(-0.5, vm + vp, s2);
-    double x = dv * v6, y = dv * dv;
-    if (order_key(y) < order_key(x)) vm = fma(3.0, s2, -2.0 * vp);
-    else if (order_key(x) < order_key(-y)) vp = fma(3.0, s2, -2.0 * vm);
+    double dv = fsub(vp, vm);
+    double v6 = kmul(RK_6, fma(rk(RK_MHALF), fadd(vm, vp), s2));
+    double x = fmul(dv, v6), y = fmul(dv, dv);
+    if (order_key(y) < order_key(x)) vm = fma(rk(RK_3), s2, -kmul(RK_2, vp));
+    else if (order_key(x) < order_key(-y)) vp = fma(rk(RK_3), s2, -kmul(RK_2, vm));
   }
   plus = vp;
   minus = vm;
