@@ -256,14 +256,14 @@ static __global__ void adj_curl_kernel(Grid g, L3 LB, E3 Eb, double dt) {
 __device__ __forceinline__ void edge_recon_vjp(double vm2, double vm1, double v0, double vp1, double gw, double gev,
                                                double w[4]) {
   w[0] = w[1] = w[2] = w[3] = 0.0;
-  int pw = minmod_pick(vm1 - vm2, v0 - vm1);
-  if (pw == 1) { w[0] -= 0.5 * gw; w[1] += 1.5 * gw; }
-  else if (pw == 2) { w[1] += 0.5 * gw; w[2] += 0.5 * gw; }
-  else w[1] += gw;
-  int pe = minmod_pick(v0 - vm1, vp1 - v0);
-  if (pe == 1) { w[1] += 0.5 * gev; w[2] += 0.5 * gev; }
-  else if (pe == 2) { w[2] += 1.5 * gev; w[3] -= 0.5 * gev; }
-  else w[2] += gev;
+  int pw = minmod_pick(fsub(vm1, vm2), fsub(v0, vm1));
+  if (pw == 1) { w[0] = fsub(w[0], kmul(RK_HALF, gw)); w[1] = fadd(w[1], fmul(1.5, gw)); }
+  else if (pw == 2) { w[1] = fadd(w[1], kmul(RK_HALF, gw)); w[2] = fadd(w[2], kmul(RK_HALF, gw)); }
+  else w[1] = fadd(w[1], gw);
+  int pe = minmod_pick(fsub(v0, vm1), fsub(vp1, v0));
+  if (pe == 1) { w[1] = fadd(w[1], kmul(RK_HALF, gev)); w[2] = fadd(w[2], kmul(RK_HALF, gev)); }
+  else if (pe == 2) { w[2] = fadd(w[2], fmul(1.5, gev)); w[3] = fsub(w[3], kmul(RK_HALF, gev)); }
+  else w[2] = fadd(w[2], gev);
 }
 
 template <int C>
@@ -274,38 +274,40 @@ __device__ __forceinline__ void uct_edge_vjp(const Grid& g, const F8& S, const F
   const int cb = c - sb, ca = c - sa;
   const double* Ia[5] = {ING.a[A][0], ING.a[A][1], ING.a[A][2], ING.a[A][3], ING.a[A][4]};
   const double* Ib[5] = {ING.a[B][0], ING.a[B][1], ING.a[B][2], ING.a[B][3], ING.a[B][4]};
-  double apa = Ia[0][cb] + Ia[0][c], ama = Ia[1][cb] + Ia[1][c], dda = Ia[2][cb] + Ia[2][c];
-  double uW = Ia[3][cb] + Ia[3][c], uE = Ia[4][cb] + Ia[4][c];
-  double apb = Ib[0][ca] + Ib[0][c], amb = Ib[1][ca] + Ib[1][c], ddb = Ib[2][ca] + Ib[2][c];
-  double vS = Ib[3][ca] + Ib[3][c], vN = Ib[4][ca] + Ib[4][c];
+  double apa = fadd(Ia[0][cb], Ia[0][c]), ama = fadd(Ia[1][cb], Ia[1][c]), dda = fadd(Ia[2][cb], Ia[2][c]);
+  double uW = fadd(Ia[3][cb], Ia[3][c]), uE = fadd(Ia[4][cb], Ia[4][c]);
+  double apb = fadd(Ib[0][ca], Ib[0][c]), amb = fadd(Ib[1][ca], Ib[1][c]), ddb = fadd(Ib[2][ca], Ib[2][c]);
+  double vS = fadd(Ib[3][ca], Ib[3][c]), vN = fadd(Ib[4][ca], Ib[4][c]);
   const double* Bb = S.q[5 + B];
   const double* Ba = S.q[5 + A];
   double bm2 = Bb[c - 2 * sa], bm1 = Bb[c - sa], b0 = Bb[c], bp1 = Bb[c + sa];
-  double BbW = fma(0.5, minmod(bm1 - bm2, b0 - bm1), bm1);
-  double BbE = fma(-0.5, minmod(b0 - bm1, bp1 - b0), b0);
+  double BbW = fma(rk(RK_HALF), minmod(fsub(bm1, bm2), fsub(b0, bm1)), bm1);
+  double BbE = fma(rk(RK_MHALF), minmod(fsub(b0, bm1), fsub(bp1, b0)), b0);
   double am2 = Ba[c - 2 * sb], am1 = Ba[c - sb], a0 = Ba[c], ap1 = Ba[c + sb];
-  double BaS = fma(0.5, minmod(am1 - am2, a0 - am1), am1);
-  double BaN = fma(-0.5, minmod(a0 - am1, ap1 - a0), a0);
+  double BaS = fma(rk(RK_HALF), minmod(fsub(am1, am2), fsub(a0, am1)), am1);
+  double BaN = fma(rk(RK_MHALF), minmod(fsub(a0, am1), fsub(ap1, a0)), a0);
   // E = (1/4) [(apb vS BaS + amb vN BaN) - (apa uW BbW + ama uE BbE)]
   //   + (1/2) [dda (BbE - BbW) - ddb (BaN - BaS)]
-  const double gu = 0.25 * eb, gd = 0.5 * eb;
-  ge[0][c] = -gu * uW * BbW;
-  ge[1][c] = -gu * uE * BbE;
-  ge[2][c] = gd * (BbE - BbW);
-  ge[3][c] = -gu * apa * BbW;
-  ge[4][c] = -gu * ama * BbE;
-  ge[5][c] = gu * vS * BaS;
-  ge[6][c] = gu * vN * BaN;
-  ge[7][c] = -gd * (BaN - BaS);
-  ge[8][c] = gu * apb * BaS;
-  ge[9][c] = gu * amb * BaN;
+  const double gu = kmul(RK_QUARTER, eb), gd = kmul(RK_HALF, eb);
+  ge[0][c] = fmul(fmul(-gu, uW), BbW);
+  ge[1][c] = fmul(fmul(-gu, uE), BbE);
+  ge[2][c] = fmul(gd, (fsub(BbE, BbW)));
+  ge[3][c] = fmul(fmul(-gu, apa), BbW);
+  ge[4][c] = fmul(fmul(-gu, ama), BbE);
+  ge[5][c] = fmul(fmul(gu, vS), BaS);
+  ge[6][c] = fmul(fmul(gu, vN), BaN);
+  ge[7][c] = fmul(-gd, (fsub(BaN, BaS)));
+  ge[8][c] = fmul(fmul(gu, apb), BaS);
+  ge[9][c] = fmul(fmul(gu, amb), BaN);
   double w[4];
-  edge_recon_vjp(bm2, bm1, b0, bp1, -gu * apa * uW - gd * dda, -gu * ama * uE + gd * dda, w);
+  edge_recon_vjp(bm2, bm1, b0, bp1, fsub(fmul(fmul(-gu, apa), uW), fmul(gd, dda)),
+                 fadd(fmul(fmul(-gu, ama), uE), fmul(gd, dda)), w);
   ge[10][c] = w[0];
   ge[11][c] = w[1];
   ge[12][c] = w[2];
   ge[13][c] = w[3];
-  edge_recon_vjp(am2, am1, a0, ap1, gu * apb * vS + gd * ddb, gu * amb * vN - gd * ddb, w);
+  edge_recon_vjp(am2, am1, a0, ap1, fadd(fmul(fmul(gu, apb), vS), fmul(gd, ddb)),
+                 fsub(fmul(fmul(gu, amb), vN), fmul(gd, ddb)), w);
   ge[14][c] = w[0];
   ge[15][c] = w[1];
   ge[16][c] = w[2];

@@ -20,38 +20,38 @@ struct W7b {
 __device__ __forceinline__ void fast_speed_vjp(double rho, double p, double B2, double bn2, double gamma, double cfb,
                                                double& rhob, double& pb, double& B2b, double& bn2b) {
   const double gp = mul_rn(gamma, p);
-  const double s = gp + B2;
-  double disc = fma(s, s, -(4.0 * gp) * bn2);
+  const double s = fadd(gp, B2);
+  double disc = fma(s, s, fmul(-(kmul(RK_FOUR, gp)), bn2));
   if (lt0(disc)) disc = 0.0;
   const double sq = fsqrt0(disc);
   const double irho = rcp(rho);
-  const double h = 0.5 * irho;
-  const double t = s + sq;
-  const double cf = fsqrt(t * h);
+  const double h = kmul(RK_HALF, irho);
+  const double t = fadd(s, sq);
+  const double cf = fsqrt(fmul(t, h));
   // reverse
-  const double cf2b = cfb * (0.5 * rcp(cf));
-  const double tb = cf2b * h;
-  rhob = fma((0.5 * (cf2b * t)), (-(irho * irho)), rhob);
+  const double cf2b = fmul(cfb, (kmul(RK_HALF, rcp(cf))));
+  const double tb = fmul(cf2b, h);
+  rhob = fma((kmul(RK_HALF, (fmul(cf2b, t)))), (-(fmul(irho, irho))), rhob);
   double sb = tb, gpb = 0.0;
   if (gt0(disc)) {
-    const double discb = tb * (0.5 * rcp(sq));
-    sb = fma(discb, (2.0 * s), sb);
-    gpb = fma(discb, (-4.0 * bn2), gpb);
-    bn2b = fma(discb, (-4.0 * gp), bn2b);
+    const double discb = fmul(tb, (kmul(RK_HALF, rcp(sq))));
+    sb = fma(discb, (kmul(RK_2, s)), sb);
+    gpb = fma(discb, (kmul(RK_M4, bn2)), gpb);
+    bn2b = fma(discb, (kmul(RK_M4, gp)), bn2b);
   }
-  gpb += sb;
-  B2b += sb;
+  gpb = fadd(gpb, sb);
+  B2b = fadd(B2b, sb);
   pb = fma(gamma, gpb, pb);
 }
 
 // Total field and total pressure of one side (side_num): cotangents of W
 // and bn2 from those of B2 (direct uses) and pT.
 __device__ __forceinline__ void side_num_vjp(const W7& W, double B2b, double pTb, W7b& Wb, double& bn2b) {
-  Wb.p += pTb;
-  B2b = fma(0.5, pTb, B2b);
-  Wb.b1 = fma((2.0 * W.b1), B2b, Wb.b1);
-  Wb.b2 = fma((2.0 * W.b2), B2b, Wb.b2);
-  bn2b += B2b;
+  Wb.p = fadd(Wb.p, pTb);
+  B2b = fma(rk(RK_HALF), pTb, B2b);
+  Wb.b1 = fma((kmul(RK_2, W.b1)), B2b, Wb.b1);
+  Wb.b2 = fma((kmul(RK_2, W.b2)), B2b, Wb.b2);
+  bn2b = fadd(bn2b, B2b);
 }
 
 // Conserved state U, flux F and v.B of one side (side_full) given its B2 and
@@ -59,17 +59,17 @@ __device__ __forceinline__ void side_num_vjp(const W7& W, double B2b, double pTb
 __device__ __forceinline__ void side_full_vjp(const W7& W, double bn, double igm1, double B2, double pT,
                                               const double Ub[7], const double Fb[7], double vBb, W7b& Wb,
                                               double& bnb, double& bn2b, double& B2b, double& pTb) {
-  const double vB = fma(W.u, bn, fma(W.v, W.b1, W.w * W.b2));
-  const double v2 = fma(W.u, W.u, fma(W.v, W.v, W.w * W.w));
-  const double E = fma(W.p, igm1, 0.5 * fma(W.rho, v2, B2));
-  const double mu = W.rho * W.u;
-  double mub = Fb[0] + Ub[1];
+  const double vB = fma(W.u, bn, fma(W.v, W.b1, fmul(W.w, W.b2)));
+  const double v2 = fma(W.u, W.u, fma(W.v, W.v, fmul(W.w, W.w)));
+  const double E = fma(W.p, igm1, kmul(RK_HALF, fma(W.rho, v2, B2)));
+  const double mu = fmul(W.rho, W.u);
+  double mub = fadd(Fb[0], Ub[1]);
   double Eb = Ub[6];
   // F1 = mu u + pT - bn2
   mub = fma(Fb[1], W.u, mub);
   Wb.u = fma(Fb[1], mu, Wb.u);
-  pTb += Fb[1];
-  bn2b -= Fb[1];
+  pTb = fadd(pTb, Fb[1]);
+  bn2b = fsub(bn2b, Fb[1]);
   // F2 = mu v - bn b1, F3 = mu w - bn b2
   mub = fma(Fb[2], W.v, fma(Fb[3], W.w, mub));
   Wb.v = fma(Fb[2], mu, Wb.v);
@@ -87,26 +87,26 @@ __device__ __forceinline__ void side_full_vjp(const W7& W, double bn, double igm
   // F6 = (E + pT) u - bn vB
   Eb = fma(Fb[6], W.u, Eb);
   pTb = fma(Fb[6], W.u, pTb);
-  Wb.u = fma(Fb[6], (E + pT), Wb.u);
+  Wb.u = fma(Fb[6], (fadd(E, pT)), Wb.u);
   bnb = fma(-Fb[6], vB, bnb);
   vBb = fma(-Fb[6], bn, vBb);
   // U = (rho, mu, rho v, rho w, b1, b2, E)
-  Wb.rho = fma(Ub[2], W.v, fma(Ub[3], W.w, Wb.rho + Ub[0]));
+  Wb.rho = fma(Ub[2], W.v, fma(Ub[3], W.w, fadd(Wb.rho, Ub[0])));
   Wb.v = fma(Ub[2], W.rho, Wb.v);
   Wb.w = fma(Ub[3], W.rho, Wb.w);
-  Wb.b1 += Ub[4];
-  Wb.b2 += Ub[5];
+  Wb.b1 = fadd(Wb.b1, Ub[4]);
+  Wb.b2 = fadd(Wb.b2, Ub[5]);
   // mu = rho u
   Wb.rho = fma(mub, W.u, Wb.rho);
   Wb.u = fma(mub, W.rho, Wb.u);
   // E = p/(G-1) + (rho v2 + B2)/2
   Wb.p = fma(Eb, igm1, Wb.p);
-  Wb.rho = fma((0.5 * Eb), v2, Wb.rho);
-  const double v2b = (0.5 * Eb) * W.rho;
-  B2b = fma(0.5, Eb, B2b);
-  Wb.u = fma((2.0 * W.u), v2b, Wb.u);
-  Wb.v = fma((2.0 * W.v), v2b, Wb.v);
-  Wb.w = fma((2.0 * W.w), v2b, Wb.w);
+  Wb.rho = fma((kmul(RK_HALF, Eb)), v2, Wb.rho);
+  const double v2b = fmul((kmul(RK_HALF, Eb)), W.rho);
+  B2b = fma(rk(RK_HALF), Eb, B2b);
+  Wb.u = fma((kmul(RK_2, W.u)), v2b, Wb.u);
+  Wb.v = fma((kmul(RK_2, W.v)), v2b, Wb.v);
+  Wb.w = fma((kmul(RK_2, W.w)), v2b, Wb.w);
   // vB = u bn + v b1 + w b2
   Wb.u = fma(vBb, bn, Wb.u);
   bnb = fma(vBb, W.u, bnb);
@@ -123,32 +123,32 @@ __device__ __forceinline__ void speeds_vjp(double uL, double uR, double cmax, co
                                            double SRb, double& uLb, double& uRb, double& cmaxb) {
   const bool min_right = order_key(uR) < order_key(uL);     // imin picks uR
   const bool max_right = order_key(uL) < order_key(uR);     // imax picks uR
-  const double SL = (min_right ? uR : uL) - cmax;
-  const double SR = (max_right ? uR : uL) + cmax;
+  const double SL = fsub((min_right ? uR : uL), cmax);
+  const double SR = fadd((max_right ? uR : uL), cmax);
   const double aR = gt0(SR) ? SR : 0.0, aL = lt0(SL) ? SL : 0.0;
-  const double inv = rcp(aR - aL);
+  const double inv = rcp(fsub(aR, aL));
   // ap = aR inv, am = -aL inv, dd = -(aR aL) inv
-  const double invb = fma(Ib[0], aR, fma(-Ib[1], aL, -Ib[2] * (aR * aL)));
-  double aRb = fma(-Ib[2], aL, Ib[0]) * inv;
-  double aLb = fma(-Ib[2], aR, -Ib[1]) * inv;
-  const double denb = invb * (-(inv * inv));
-  aRb += denb;
-  aLb -= denb;
+  const double invb = fma(Ib[0], aR, fma(-Ib[1], aL, fmul(-Ib[2], (fmul(aR, aL)))));
+  double aRb = fmul(fma(-Ib[2], aL, Ib[0]), inv);
+  double aLb = fmul(fma(-Ib[2], aR, -Ib[1]), inv);
+  const double denb = fmul(invb, (-(fmul(inv, inv))));
+  aRb = fadd(aRb, denb);
+  aLb = fsub(aLb, denb);
   if (gt0(SR)) SRb += aRb;
   if (lt0(SL)) SLb += aLb;
-  uLb += Ib[3];
-  uRb += Ib[4];
+  uLb = fadd(uLb, Ib[3]);
+  uRb = fadd(uRb, Ib[4]);
   if (max_right) uRb += SRb;
   else uLb += SRb;
   if (min_right) uRb += SLb;
   else uLb += SLb;
-  cmaxb += SRb - SLb;
+  cmaxb = fadd(cmaxb, fsub(SRb, SLb));
 }
 
 // The side that sets cmax (fast_speed_max's choice) and the reverse of its
 // fast speed: cotangents of that side's rho, p, B2 and of bn2 from cmax's.
 __device__ __forceinline__ bool cmax_right(double nL, double rhoL, double nR, double rhoR) {
-  return lt_pos(nL * rhoR, nR * rhoL);
+  return lt_pos(fmul(nL, rhoR), fmul(nR, rhoL));
 }
 __device__ __forceinline__ void cmax_vjp(const W7& L, const W7& R, bool right, double B2L, double B2R, double bn2,
                                          double gamma, double cmaxb, W7b& Lb, W7b& Rb, double& B2bL, double& B2bR,
@@ -166,13 +166,13 @@ __device__ __forceinline__ void cmax_vjp(const W7& L, const W7& R, bool right, d
 __device__ __forceinline__ void riemann_hll_vjp(const W7& L, const W7& R, double bn, double gamma, double igm1,
                                                 const double Fb[7], const double Ib[5], W7b& Lb, W7b& Rb,
                                                 double& bnb) {
-  const double bn2 = bn * bn;
+  const double bn2 = fmul(bn, bn);
   Side sl, sr;
   side_state<double, false>(L, bn, bn2, gamma, igm1, sl);
   side_state<double, false>(R, bn, bn2, gamma, igm1, sr);
   const bool c_right = cmax_right(sl.n, L.rho, sr.n, R.rho);
   const double cmax = fast_speed_max(sl.n, L.rho, sr.n, R.rho);
-  const double SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
+  const double SL = fsub(imin(L.u, R.u), cmax), SR = fadd(imax(L.u, R.u), cmax);
   double ULb[7] = {0, 0, 0, 0, 0, 0, 0}, FLb[7] = {0, 0, 0, 0, 0, 0, 0};
   double URb[7] = {0, 0, 0, 0, 0, 0, 0}, FRb[7] = {0, 0, 0, 0, 0, 0, 0};
   double SLb = 0.0, SRb = 0.0;
@@ -184,14 +184,14 @@ __device__ __forceinline__ void riemann_hll_vjp(const W7& L, const W7& R, double
     for (int q = 0; q < 7; q++) FRb[q] = Fb[q];
   } else {
     // F = (SR SL (UR - UL) + SR FL - SL FR) inv,  inv = 1/(SR - SL)
-    const double inv = rcp(SR - SL);
-    const double sls = SR * SL;
+    const double inv = rcp(fsub(SR, SL));
+    const double sls = fmul(SR, SL);
     double invb = 0.0, slsb = 0.0;
 #pragma unroll
     for (int q = 0; q < 7; q++) {
-      const double dU = sr.U[q] - sl.U[q];
-      const double N = fma(sls, dU, fma(SR, sl.F[q], -SL * sr.F[q]));
-      const double Nb = Fb[q] * inv;
+      const double dU = fsub(sr.U[q], sl.U[q]);
+      const double N = fma(sls, dU, fma(SR, sl.F[q], fmul(-SL, sr.F[q])));
+      const double Nb = fmul(Fb[q], inv);
       invb = fma(Fb[q], N, invb);
       slsb = fma(Nb, dU, slsb);
       URb[q] = fma(Nb, sls, URb[q]);
@@ -203,21 +203,21 @@ __device__ __forceinline__ void riemann_hll_vjp(const W7& L, const W7& R, double
     }
     SRb = fma(slsb, SL, SRb);
     SLb = fma(slsb, SR, SLb);
-    const double db = invb * (-(inv * inv));
-    SRb += db;
-    SLb -= db;
+    const double db = fmul(invb, (-(fmul(inv, inv))));
+    SRb = fadd(SRb, db);
+    SLb = fsub(SLb, db);
   }
   double uLb = 0.0, uRb = 0.0, cmaxb = 0.0;
   speeds_vjp(L.u, R.u, cmax, Ib, SLb, SRb, uLb, uRb, cmaxb);
-  Lb.u += uLb;
-  Rb.u += uRb;
+  Lb.u = fadd(Lb.u, uLb);
+  Rb.u = fadd(Rb.u, uRb);
   double bn2b = 0.0, B2bL = 0.0, pTbL = 0.0, B2bR = 0.0, pTbR = 0.0;
   side_full_vjp(L, bn, igm1, sl.B2, sl.pT, ULb, FLb, 0.0, Lb, bnb, bn2b, B2bL, pTbL);
   side_full_vjp(R, bn, igm1, sr.B2, sr.pT, URb, FRb, 0.0, Rb, bnb, bn2b, B2bR, pTbR);
   cmax_vjp(L, R, c_right, sl.B2, sr.B2, bn2, gamma, cmaxb, Lb, Rb, B2bL, B2bR, bn2b);
   side_num_vjp(L, B2bL, pTbL, Lb, bn2b);
   side_num_vjp(R, B2bR, pTbR, Rb, bn2b);
-  bnb = fma((2.0 * bn), bn2b, bnb);
+  bnb = fma((kmul(RK_2, bn)), bn2b, bnb);
 }
 
 // ---------------------------------------------------------------------------
@@ -231,24 +231,24 @@ struct StarT {
   bool degen;
 };
 __device__ __forceinline__ void star_side(const W7& W, double S, double SM, double bn, double bn2, StarT& t) {
-  t.sd = S - W.u;
-  t.rs = t.sd * W.rho;
-  t.sm = S - SM;
+  t.sd = fsub(S, W.u);
+  t.rs = fmul(t.sd, W.rho);
+  t.sm = fsub(S, SM);
   t.ism = rcp(t.sm);
-  t.rhos = t.rs * t.ism;
-  const double rsm = mul_rn(t.rs, t.sm), D = rsm - bn2;
-  t.degen = lt_pos(fabs(D), kHlldDegenEps * rsm);
+  t.rhos = fmul(t.rs, t.ism);
+  const double rsm = mul_rn(t.rs, t.sm), D = fsub(rsm, bn2);
+  t.degen = lt_pos(fabs(D), fmul(kHlldDegenEps, rsm));
   if (t.degen) {
     t.vs = W.v; t.ws = W.w; t.b1s = W.b1; t.b2s = W.b2;
     t.iD = t.cv = t.cb = 0.0;
   } else {
     t.iD = rcp(D);
-    t.cv = (bn * (SM - W.u)) * t.iD;
+    t.cv = fmul((fmul(bn, (fsub(SM, W.u)))), t.iD);
     t.vs = fma(-W.b1, t.cv, W.v);
     t.ws = fma(-W.b2, t.cv, W.w);
-    t.cb = fma(t.rs, t.sd, -bn2) * t.iD;
-    t.b1s = W.b1 * t.cb;
-    t.b2s = W.b2 * t.cb;
+    t.cb = fmul(fma(t.rs, t.sd, -bn2), t.iD);
+    t.b1s = fmul(W.b1, t.cb);
+    t.b2s = fmul(W.b2, t.cb);
   }
 }
 // Cotangents of one side's star quantities, accumulated by the reverse.
@@ -261,54 +261,54 @@ __device__ __forceinline__ void star_side_vjp(const W7& W, double SM, double bn,
                                               W7b& Wb, double& Sb, double& SMb, double& bnb, double& bn2b) {
   double smb = 0.0;
   if (t.degen) {
-    Wb.v += b.vs;
-    Wb.w += b.ws;
-    Wb.b1 += b.b1s;
-    Wb.b2 += b.b2s;
+    Wb.v = fadd(Wb.v, b.vs);
+    Wb.w = fadd(Wb.w, b.ws);
+    Wb.b1 = fadd(Wb.b1, b.b1s);
+    Wb.b2 = fadd(Wb.b2, b.b2s);
   } else {
     Wb.b1 = fma(b.b1s, t.cb, fma(-b.vs, t.cv, Wb.b1));
     Wb.b2 = fma(b.b2s, t.cb, fma(-b.ws, t.cv, Wb.b2));
-    Wb.v += b.vs;
-    Wb.w += b.ws;
-    const double cbb = fma(b.b1s, W.b1, b.b2s * W.b2);
-    const double cvb = fma(-b.vs, W.b1, -(b.ws * W.b2));
+    Wb.v = fadd(Wb.v, b.vs);
+    Wb.w = fadd(Wb.w, b.ws);
+    const double cbb = fma(b.b1s, W.b1, fmul(b.b2s, W.b2));
+    const double cvb = fma(-b.vs, W.b1, -(fmul(b.ws, W.b2)));
     // cb = (rs sd - bn2) iD
-    const double Nbb = cbb * t.iD;
-    double iDb = cbb * fma(t.rs, t.sd, -bn2);
+    const double Nbb = fmul(cbb, t.iD);
+    double iDb = fmul(cbb, fma(t.rs, t.sd, -bn2));
     b.rs = fma(Nbb, t.sd, b.rs);
     b.sd = fma(Nbb, t.rs, b.sd);
-    bn2b -= Nbb;
+    bn2b = fsub(bn2b, Nbb);
     // cv = bn (SM - u) iD
-    const double du = SM - W.u;
-    const double Nvb = cvb * t.iD;
-    iDb = fma(cvb, (bn * du), iDb);
+    const double du = fsub(SM, W.u);
+    const double Nvb = fmul(cvb, t.iD);
+    iDb = fma(cvb, (fmul(bn, du)), iDb);
     bnb = fma(Nvb, du, bnb);
     SMb = fma(Nvb, bn, SMb);
     Wb.u = fma(-Nvb, bn, Wb.u);
     // iD = 1/D, D = rs sm - bn2
-    const double Db = iDb * (-(t.iD * t.iD));
-    bn2b -= Db;
+    const double Db = fmul(iDb, (-(fmul(t.iD, t.iD))));
+    bn2b = fsub(bn2b, Db);
     b.rs = fma(Db, t.sm, b.rs);
     smb = fma(Db, t.rs, smb);
   }
   // rhos = rs ism, ism = 1/sm, sm = S - SM
   b.rs = fma(b.rhos, t.ism, b.rs);
   b.ism = fma(b.rhos, t.rs, b.ism);
-  smb = fma(b.ism, (-(t.ism * t.ism)), smb);
-  Sb += smb;
-  SMb -= smb;
+  smb = fma(b.ism, (-(fmul(t.ism, t.ism))), smb);
+  Sb = fadd(Sb, smb);
+  SMb = fsub(SMb, smb);
 }
 
 __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, double bn, double gamma, double igm1,
                                                  const double Fb[7], const double Ib[5], W7b& Lb, W7b& Rb,
                                                  double& bnb) {
-  const double bn2 = bn * bn;
+  const double bn2 = fmul(bn, bn);
   SideNumT<double> ll, lr;
   side_num(L, bn2, gamma, ll);
   side_num(R, bn2, gamma, lr);
   const bool c_right = cmax_right(ll.n, L.rho, lr.n, R.rho);
   const double cmax = fast_speed_max(ll.n, L.rho, lr.n, R.rho);
-  const double SL = imin(L.u, R.u) - cmax, SR = imax(L.u, R.u) + cmax;
+  const double SL = fsub(imin(L.u, R.u), cmax), SR = fadd(imax(L.u, R.u), cmax);
   double SLb = 0.0, SRb = 0.0, bn2b = 0.0;
   double B2bL = 0.0, pTbL = 0.0, B2bR = 0.0, pTbR = 0.0;
   if (gt0(SL) || lt0(SR)) {  // supersonic: the upwind physical flux
@@ -318,14 +318,14 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     else side_full_vjp(R, bn, igm1, lr.B2, lr.pT, Ub, Fb, 0.0, Rb, bnb, bn2b, B2bR, pTbR);
   } else {
     // ---- primal, as in riemann_hlld ----
-    const double sdL = SL - L.u, sdR = SR - R.u;
-    const double rsL = sdL * L.rho, rsR = sdR * R.rho;
-    const double iden = rcp(rsR - rsL);
-    const double NM = (fma(rsR, R.u, -rsL * L.u) - lr.pT) + ll.pT;
-    const double SM = NM * iden;
-    const double a1 = (L.rho * rsR) * sdL;
-    const double Np = fma(a1, R.u - L.u, fma(rsR, ll.pT, -rsL * lr.pT));
-    const double pTs = Np * iden;
+    const double sdL = fsub(SL, L.u), sdR = fsub(SR, R.u);
+    const double rsL = fmul(sdL, L.rho), rsR = fmul(sdR, R.rho);
+    const double iden = rcp(fsub(rsR, rsL));
+    const double NM = fadd((fsub(fma(rsR, R.u, fmul(-rsL, L.u)), lr.pT)), ll.pT);
+    const double SM = fmul(NM, iden);
+    const double a1 = fmul((fmul(L.rho, rsR)), sdL);
+    const double Np = fma(a1, fsub(R.u, L.u), fma(rsR, ll.pT, fmul(-rsL, lr.pT)));
+    const double pTs = fmul(Np, iden);
     StarT tL, tR;
     star_side(L, SL, SM, bn, bn2, tL);
     star_side(R, SR, SM, bn, bn2, tR);
@@ -336,53 +336,53 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     const double S = left ? SL : SR;
     double Ua[7], Fa[7], vBa;
     side_full(A, bn, bn2, igm1, left ? ll : lr, Ua, Fa, vBa);
-    const double vBs = fma(SM, bn, fma(ta.vs, ta.b1s, ta.ws * ta.b2s));
-    const double NE = fma(ta.sd, Ua[6], -pTa * A.u) + fma(pTs, SM, bn * (vBa - vBs));
-    const double Es = NE * ta.ism;
-    const double Us[7] = {ta.rhos, ta.rhos * SM, ta.rhos * ta.vs, ta.rhos * ta.ws, ta.b1s, ta.b2s, Es};
+    const double vBs = fma(SM, bn, fma(ta.vs, ta.b1s, fmul(ta.ws, ta.b2s)));
+    const double NE = fadd(fma(ta.sd, Ua[6], fmul(-pTa, A.u)), fma(pTs, SM, fmul(bn, (fsub(vBa, vBs)))));
+    const double Es = fmul(NE, ta.ism);
+    const double Us[7] = {ta.rhos, fmul(ta.rhos, SM), fmul(ta.rhos, ta.vs), fmul(ta.rhos, ta.ws), ta.b1s, ta.b2s, Es};
     StarB bL, bR;
     StarB& ba = left ? bL : bR;
     double SMb = 0.0, pTsb = 0.0, Sb = 0.0, Esb = 0.0, vBsb = 0.0;
     double Usb[7] = {0, 0, 0, 0, 0, 0, 0};
     // ---- rotational waves ----
-    if (!lt_pos(0.5 * bn2, kHlldBnEps * pTs)) {
+    if (!lt_pos(kmul(RK_HALF, bn2), fmul(kHlldBnEps, pTs))) {
       const double iqL = frsqrt(tL.rhos), iqR = frsqrt(tR.rhos);
-      const double sqL = tL.rhos * iqL, sqR = tR.rhos * iqR;
+      const double sqL = fmul(tL.rhos, iqL), sqR = fmul(tR.rhos, iqR);
       const double abn = fabs(bn);
       const double Ss = left ? fma(-abn, iqL, SM) : fma(abn, iqR, SM);
       const bool beyond = left ? lt0(Ss) : ge0(Ss);
       if (beyond) {
         const double sg = gt0(bn) ? 1.0 : -1.0;
-        const double isum = rcp(sqL + sqR);
-        const double Nv = fma(sqL, tL.vs, fma(sqR, tR.vs, times_sign(tR.b1s - tL.b1s, bn)));
-        const double Nw = fma(sqL, tL.ws, fma(sqR, tR.ws, times_sign(tR.b2s - tL.b2s, bn)));
-        const double vss = Nv * isum, wss = Nw * isum;
-        const double sq2 = sqL * sqR;
-        const double N1 = fma(sqL, tR.b1s, fma(sqR, tL.b1s, times_sign(sq2 * (tR.vs - tL.vs), bn)));
-        const double N2 = fma(sqL, tR.b2s, fma(sqR, tL.b2s, times_sign(sq2 * (tR.ws - tL.ws), bn)));
-        const double b1ss = N1 * isum, b2ss = N2 * isum;
-        const double vBss = fma(SM, bn, fma(vss, b1ss, wss * b2ss));
+        const double isum = rcp(fadd(sqL, sqR));
+        const double Nv = fma(sqL, tL.vs, fma(sqR, tR.vs, times_sign(fsub(tR.b1s, tL.b1s), bn)));
+        const double Nw = fma(sqL, tL.ws, fma(sqR, tR.ws, times_sign(fsub(tR.b2s, tL.b2s), bn)));
+        const double vss = fmul(Nv, isum), wss = fmul(Nw, isum);
+        const double sq2 = fmul(sqL, sqR);
+        const double N1 = fma(sqL, tR.b1s, fma(sqR, tL.b1s, times_sign(fmul(sq2, (fsub(tR.vs, tL.vs))), bn)));
+        const double N2 = fma(sqL, tR.b2s, fma(sqR, tL.b2s, times_sign(fmul(sq2, (fsub(tR.ws, tL.ws))), bn)));
+        const double b1ss = fmul(N1, isum), b2ss = fmul(N2, isum);
+        const double vBss = fma(SM, bn, fma(vss, b1ss, fmul(wss, b2ss)));
         const double sqa = left ? -sqL : sqR;
-        const double dvB = vBs - vBss;
+        const double dvB = fsub(vBs, vBss);
         const double Ess = fma(sqa, times_sign(dvB, bn), Es);
         // F2..F6 += S*_a (U** - U*)
         double Ssb = fma(Fb[2], fma(ta.rhos, vss, -Us[2]),
                          fma(Fb[3], fma(ta.rhos, wss, -Us[3]),
-                             fma(Fb[4], b1ss - ta.b1s, fma(Fb[5], b2ss - ta.b2s, Fb[6] * (Ess - Es)))));
-        ba.rhos = fma(Ss, fma(Fb[2], vss, Fb[3] * wss), ba.rhos);
-        double vssb = Fb[2] * Ss * ta.rhos, wssb = Fb[3] * Ss * ta.rhos;
+                             fma(Fb[4], fsub(b1ss, ta.b1s), fma(Fb[5], fsub(b2ss, ta.b2s), fmul(Fb[6], fsub(Ess, Es))))));
+        ba.rhos = fma(Ss, fma(Fb[2], vss, fmul(Fb[3], wss)), ba.rhos);
+        double vssb = fmul(fmul(Fb[2], Ss), ta.rhos), wssb = fmul(fmul(Fb[3], Ss), ta.rhos);
         Usb[2] = fma(-Fb[2], Ss, Usb[2]);
         Usb[3] = fma(-Fb[3], Ss, Usb[3]);
-        double b1ssb = Fb[4] * Ss, b2ssb = Fb[5] * Ss;
+        double b1ssb = fmul(Fb[4], Ss), b2ssb = fmul(Fb[5], Ss);
         ba.b1s = fma(-Fb[4], Ss, ba.b1s);
         ba.b2s = fma(-Fb[5], Ss, ba.b2s);
-        const double Essb = Fb[6] * Ss;
+        const double Essb = fmul(Fb[6], Ss);
         Esb = fma(-Fb[6], Ss, Esb);
         // Ess = Es + sqa sg (vBs - vBss)
-        Esb += Essb;
-        const double sqab = Essb * sg * dvB;
-        vBsb = fma((Essb * sqa), sg, vBsb);
-        const double vBssb = -Essb * sqa * sg;
+        Esb = fadd(Esb, Essb);
+        const double sqab = fmul(fmul(Essb, sg), dvB);
+        vBsb = fma((fmul(Essb, sqa)), sg, vBsb);
+        const double vBssb = fmul(fmul(-Essb, sqa), sg);
         double sqLb = left ? -sqab : 0.0, sqRb = left ? 0.0 : sqab;
         // vBss = SM bn + vss b1ss + wss b2ss
         SMb = fma(vBssb, bn, SMb);
@@ -392,16 +392,16 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
         wssb = fma(vBssb, b2ss, wssb);
         b2ssb = fma(vBssb, wss, b2ssb);
         // b1ss, b2ss
-        double isumb = fma(b1ssb, N1, fma(b2ssb, N2, fma(vssb, Nv, wssb * Nw)));
-        const double N1b = b1ssb * isum, N2b = b2ssb * isum, Nvb = vssb * isum, Nwb = wssb * isum;
+        double isumb = fma(b1ssb, N1, fma(b2ssb, N2, fma(vssb, Nv, fmul(wssb, Nw))));
+        const double N1b = fmul(b1ssb, isum), N2b = fmul(b2ssb, isum), Nvb = fmul(vssb, isum), Nwb = fmul(wssb, isum);
         sqLb = fma(N1b, tR.b1s, fma(N2b, tR.b2s, fma(Nvb, tL.vs, fma(Nwb, tL.ws, sqLb))));
         sqRb = fma(N1b, tL.b1s, fma(N2b, tL.b2s, fma(Nvb, tR.vs, fma(Nwb, tR.ws, sqRb))));
         bR.b1s = fma(N1b, sqL, fma(Nvb, sg, bR.b1s));
         bL.b1s = fma(N1b, sqR, fma(-Nvb, sg, bL.b1s));
         bR.b2s = fma(N2b, sqL, fma(Nwb, sg, bR.b2s));
         bL.b2s = fma(N2b, sqR, fma(-Nwb, sg, bL.b2s));
-        const double t1 = N1b * sg, t2 = N2b * sg;
-        const double sq2b = fma(t1, (tR.vs - tL.vs), t2 * (tR.ws - tL.ws));
+        const double t1 = fmul(N1b, sg), t2 = fmul(N2b, sg);
+        const double sq2b = fma(t1, (fsub(tR.vs, tL.vs)), fmul(t2, (fsub(tR.ws, tL.ws))));
         bR.vs = fma(t1, sq2, fma(Nvb, sqR, bR.vs));
         bL.vs = fma(-t1, sq2, fma(Nvb, sqL, bL.vs));
         bR.ws = fma(t2, sq2, fma(Nwb, sqR, bR.ws));
@@ -409,56 +409,56 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
         sqLb = fma(sq2b, sqR, sqLb);
         sqRb = fma(sq2b, sqL, sqRb);
         // isum = 1/(sqL + sqR)
-        const double db = isumb * (-(isum * isum));
-        sqLb += db;
-        sqRb += db;
+        const double db = fmul(isumb, (-(fmul(isum, isum))));
+        sqLb = fadd(sqLb, db);
+        sqRb = fadd(sqRb, db);
         // Ss
-        SMb += Ssb;
+        SMb = fadd(SMb, Ssb);
         double iqLb = 0.0, iqRb = 0.0, abnb;
         if (left) {
-          abnb = -Ssb * iqL;
+          abnb = fmul(-Ssb, iqL);
           iqLb = fma(-Ssb, abn, iqLb);
         } else {
-          abnb = Ssb * iqR;
+          abnb = fmul(Ssb, iqR);
           iqRb = fma(Ssb, abn, iqRb);
         }
-        bnb += lt0(bn) ? -abnb : abnb;
+        bnb = fadd(bnb, lt0(bn) ? -abnb : abnb);
         // sq = rhos iq, iq = rhos^(-1/2)
         bL.rhos = fma(sqLb, iqL, bL.rhos);
         iqLb = fma(sqLb, tL.rhos, iqLb);
         bR.rhos = fma(sqRb, iqR, bR.rhos);
         iqRb = fma(sqRb, tR.rhos, iqRb);
-        bL.rhos = fma(iqLb, (-0.5 * (iqL * iqL) * iqL), bL.rhos);
-        bR.rhos = fma(iqRb, (-0.5 * (iqR * iqR) * iqR), bR.rhos);
+        bL.rhos = fma(iqLb, (fmul(kmul(RK_MHALF, (fmul(iqL, iqL))), iqL)), bL.rhos);
+        bR.rhos = fma(iqRb, (fmul(kmul(RK_MHALF, (fmul(iqR, iqR))), iqR)), bR.rhos);
       }
     }
     // ---- F = F_a + S_a (U*_a - U_a) ----
     double Uab[7];
 #pragma unroll
     for (int q = 0; q < 7; q++) {
-      Sb = fma(Fb[q], (Us[q] - Ua[q]), Sb);
+      Sb = fma(Fb[q], (fsub(Us[q], Ua[q])), Sb);
       Usb[q] = fma(Fb[q], S, Usb[q]);
-      Uab[q] = -Fb[q] * S;
+      Uab[q] = fmul(-Fb[q], S);
     }
     // U*_a = (rhos, rhos SM, rhos vs, rhos ws, b1s, b2s, Es)
-    ba.rhos = fma(Usb[1], SM, fma(Usb[2], ta.vs, fma(Usb[3], ta.ws, ba.rhos + Usb[0])));
+    ba.rhos = fma(Usb[1], SM, fma(Usb[2], ta.vs, fma(Usb[3], ta.ws, fadd(ba.rhos, Usb[0]))));
     SMb = fma(Usb[1], ta.rhos, SMb);
     ba.vs = fma(Usb[2], ta.rhos, ba.vs);
     ba.ws = fma(Usb[3], ta.rhos, ba.ws);
-    ba.b1s += Usb[4];
-    ba.b2s += Usb[5];
-    Esb += Usb[6];
+    ba.b1s = fadd(ba.b1s, Usb[4]);
+    ba.b2s = fadd(ba.b2s, Usb[5]);
+    Esb = fadd(Esb, Usb[6]);
     // Es = [(sd E_a - pT_a u_a) + (pT* SM + bn (vB_a - vB*))] ism
-    const double NEb = Esb * ta.ism;
+    const double NEb = fmul(Esb, ta.ism);
     ba.ism = fma(Esb, NE, ba.ism);
     ba.sd = fma(NEb, Ua[6], ba.sd);
     Uab[6] = fma(NEb, ta.sd, Uab[6]);
-    double pTab = -NEb * A.u;
-    const double uab = -NEb * pTa;
+    double pTab = fmul(-NEb, A.u);
+    const double uab = fmul(-NEb, pTa);
     pTsb = fma(NEb, SM, pTsb);
     SMb = fma(NEb, pTs, SMb);
-    bnb = fma(NEb, (vBa - vBs), bnb);
-    const double vBab = NEb * bn;
+    bnb = fma(NEb, (fsub(vBa, vBs)), bnb);
+    const double vBab = fmul(NEb, bn);
     vBsb = fma(-NEb, bn, vBsb);
     // vB* = SM bn + vs b1s + ws b2s
     SMb = fma(vBsb, bn, SMb);
@@ -469,7 +469,7 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     ba.b2s = fma(vBsb, ta.ws, ba.b2s);
     // side a: conserved state, flux, v.B
     W7b& Wab = left ? Lb : Rb;
-    Wab.u += uab;
+    Wab.u = fadd(Wab.u, uab);
     double B2ab = 0.0;
     side_full_vjp(A, bn, igm1, B2a, pTa, Uab, Fb, vBab, Wab, bnb, bn2b, B2ab, pTab);
     if (left) { B2bL += B2ab; pTbL += pTab; }
@@ -480,51 +480,51 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     star_side_vjp(L, SM, bn, bn2, tL, bL, Lb, SLb, SMb, bnb, bn2b);
     star_side_vjp(R, SM, bn, bn2, tR, bR, Rb, SRb, SMb, bnb, bn2b);
     // pT* = a1 (uR - uL) + (rsR pTL - rsL pTR), times iden; a1 = (rhoL rsR) sdL
-    const double Npb = pTsb * iden;
-    double idenb = pTsb * Np;
-    const double a1b = Npb * (R.u - L.u);
+    const double Npb = fmul(pTsb, iden);
+    double idenb = fmul(pTsb, Np);
+    const double a1b = fmul(Npb, (fsub(R.u, L.u)));
     Rb.u = fma(Npb, a1, Rb.u);
     Lb.u = fma(-Npb, a1, Lb.u);
     bR.rs = fma(Npb, ll.pT, bR.rs);
     pTbL = fma(Npb, rsR, pTbL);
     bL.rs = fma(-Npb, lr.pT, bL.rs);
     pTbR = fma(-Npb, rsL, pTbR);
-    const double rr = L.rho * rsR;
+    const double rr = fmul(L.rho, rsR);
     bL.sd = fma(a1b, rr, bL.sd);
-    const double rrb = a1b * sdL;
+    const double rrb = fmul(a1b, sdL);
     Lb.rho = fma(rrb, rsR, Lb.rho);
     bR.rs = fma(rrb, L.rho, bR.rs);
     // SM = [(rsR uR - rsL uL) - pTR + pTL] iden
-    const double NMb = SMb * iden;
+    const double NMb = fmul(SMb, iden);
     idenb = fma(SMb, NM, idenb);
     bR.rs = fma(NMb, R.u, bR.rs);
     Rb.u = fma(NMb, rsR, Rb.u);
     bL.rs = fma(-NMb, L.u, bL.rs);
     Lb.u = fma(-NMb, rsL, Lb.u);
-    pTbR -= NMb;
-    pTbL += NMb;
+    pTbR = fsub(pTbR, NMb);
+    pTbL = fadd(pTbL, NMb);
     // iden = 1/(rsR - rsL)
-    const double d = idenb * (-(iden * iden));
-    bR.rs += d;
-    bL.rs -= d;
+    const double d = fmul(idenb, (-(fmul(iden, iden))));
+    bR.rs = fadd(bR.rs, d);
+    bL.rs = fsub(bL.rs, d);
     // rs = sd rho, sd = S - u
     bL.sd = fma(bL.rs, L.rho, bL.sd);
     Lb.rho = fma(bL.rs, sdL, Lb.rho);
     bR.sd = fma(bR.rs, R.rho, bR.sd);
     Rb.rho = fma(bR.rs, sdR, Rb.rho);
-    SLb += bL.sd;
-    Lb.u -= bL.sd;
-    SRb += bR.sd;
-    Rb.u -= bR.sd;
+    SLb = fadd(SLb, bL.sd);
+    Lb.u = fsub(Lb.u, bL.sd);
+    SRb = fadd(SRb, bR.sd);
+    Rb.u = fsub(Rb.u, bR.sd);
   }
   double uLb = 0.0, uRb = 0.0, cmaxb = 0.0;
   speeds_vjp(L.u, R.u, cmax, Ib, SLb, SRb, uLb, uRb, cmaxb);
-  Lb.u += uLb;
-  Rb.u += uRb;
+  Lb.u = fadd(Lb.u, uLb);
+  Rb.u = fadd(Rb.u, uRb);
   cmax_vjp(L, R, c_right, ll.B2, lr.B2, bn2, gamma, cmaxb, Lb, Rb, B2bL, B2bR, bn2b);
   side_num_vjp(L, B2bL, pTbL, Lb, bn2b);
   side_num_vjp(R, B2bR, pTbR, Rb, bn2b);
-  bnb = fma((2.0 * bn), bn2b, bnb);
+  bnb = fma((kmul(RK_2, bn)), bn2b, bnb);
 }
 
 }  // namespace mhd
