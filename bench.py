@@ -52,6 +52,8 @@ WORKLOADS = {
                     "3D magnetised blast 128^3 (profiling size), same setup and scheme as blast3d-512"),
     "blast3d-512-ppm": (lambda: W.blast_3d(512, recon="ppm"), "blast3d_ppm_hlld_rk3",
                         "3D magnetised blast 512^3 outflow; PPM + HLLD + SSP-RK3 + UCT-HLL CT, CFL 0.4"),
+    "blast3d-128-ppm": (lambda: W.blast_3d(128, recon="ppm"), "blast3d_ppm_hlld_rk3",
+                        "3D magnetised blast 128^3 (profiling size), same setup and scheme as blast3d-512-ppm"),
     "orszag-tang3d-704": (lambda: W.orszag_tang_3d((704, 704, 352), recon="wenoz", rk=3, emf="uct_hlld"),
                           "orszag_tang3d_wenoz_hlld_rk3_ucthlld",
                           "3D Orszag-Tang of paper §4.1 at its per-node resolution 704x704x352 on the unit periodic cube, "
@@ -77,6 +79,10 @@ WORKLOADS = {
                               "orszag_tang3d_wenoz_hlld_rk3_glm",
                               "3D Orszag-Tang of paper §4.1 at 704x704x352 with GLM divergence cleaning (the "
                               "paper's strong-scaling configuration); WENO-Z + HLLD + SSP-RK3, alpha = 0.1, CFL 0.4"),
+    "orszag-tang3d-128-glm": (lambda: W.to_glm(*W.orszag_tang_3d(128, recon="wenoz", rk=3)),
+                              "orszag_tang3d_wenoz_hlld_rk3_glm",
+                              "3D Orszag-Tang 128^3 with GLM (profiling size), same setup and scheme as "
+                              "orszag-tang3d-704-glm"),
     "orszag-tang2d-128": (lambda: W.orszag_tang_2d(128), "orszag_tang2d_plm_hlld_rk2",
                           "2D Orszag-Tang 128^2 periodic; PLM-minmod + HLLD + SSP-RK2 + UCT-HLL CT, CFL 0.4"),
     "ensemble2d-256": (None, "orszag_tang2d_plm_hlld_rk2",
@@ -103,6 +109,9 @@ SAMPLES = {
     "blast3d-512": (lambda: W.blast_3d(32), "blast 3D 32^3 (same scheme and setup)"),
     "blast3d-128": (lambda: W.blast_3d(32), "blast 3D 32^3 (same scheme and setup)"),
     "blast3d-512-ppm": (lambda: W.blast_3d(32, recon="ppm"), "blast 3D 32^3 PPM (same scheme and setup)"),
+    "blast3d-128-ppm": (lambda: W.blast_3d(32, recon="ppm"), "blast 3D 32^3 PPM (same scheme and setup)"),
+    "orszag-tang3d-128-glm": (lambda: W.to_glm(*W.orszag_tang_3d(32, recon="wenoz", rk=3)),
+                              "3D Orszag-Tang 32^3 with GLM (same scheme)"),
     "orszag-tang3d-704": (lambda: W.orszag_tang_3d(32, recon="wenoz", rk=3, emf="uct_hlld"),
                           "3D Orszag-Tang 32^3 (same scheme)"),
     "orszag-tang3d-704-ucthll": (lambda: W.orszag_tang_3d(32, recon="wenoz", rk=3), "3D Orszag-Tang 32^3 (same scheme)"),
