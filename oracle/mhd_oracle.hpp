@@ -11,7 +11,7 @@
 //
 // Every function is written in the order of the formula it follows; nothing is
 // fused, blocked or reordered for speed.  Where the paper is silent the reading
-// taken is stated at the function (and listed in the design doc).
+// taken is stated at the function.
 //
 // Parity pins (tests/test_oracle_*.py): closed forms, exact Riemann solutions,
 // conservation, div B, symmetries, convergence orders.  No paper-printed values
