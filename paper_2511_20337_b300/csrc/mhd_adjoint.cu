@@ -35,7 +35,6 @@ struct AdjointState {
   size_t ing_count = 0;
   F8 A[4];                    // cotangent accumulators of the stage inputs (A[3]: incoming)
   L6 Lb;                      // cotangent of the stage increment (cells)
-  L3 LB;                      // cotangent of the CT face increment
   E3 Eb;                      // cotangent of the edge fields
   GE18 GE;                    // edge-local cotangents
   F8 WbL[3], WbR[3];          // per direction: cotangents of the face states (7 used; WbL.q[7] holds the PLM codes)
@@ -63,7 +62,7 @@ void adjoint_free(mhd_ctx* c) {
 
 namespace {
 
-constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 + 3 * 18 + 3 * (8 + 8) + 8 + 6;
+constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 * 18 + 3 * (8 + 8) + 8 + 6;
 
 // The per-cell PLM decisions of the current direction (adj_riemann_kernel ->
 // adj_recon_kernel) live in the face-state cotangent fields' spare slot 7.
@@ -101,7 +100,6 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
     for (int r = 0; r < 4; r++)
       for (int q = 0; q < 8; q++) a->A[r].q[q] = next();
     for (int q = 0; q < 6; q++) a->Lb.q[q] = next();
-    for (int d = 0; d < 3; d++) a->LB.q[d] = next();
     for (int d = 0; d < 3; d++) a->Eb.e[d] = next();
     for (int C = 0; C < 3; C++)
       for (int m = 0; m < 18; m++) a->GE.q[C][m] = next();
@@ -204,15 +202,14 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const FaceIngr& ING, const F8& 
   stage_coeffs(c->cfg.rk, s, c0, c1, cL);
   const long long edges = edge_work<NDIM>(g);
   const int nbe = blocks_for(edges, 256);
-  adj_combine_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->LB, c0, c1, cL);
-  adj_curl_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, a->LB, a->Eb, dt);
+  adj_combine_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->Eb, c0, c1, cL, dt);
   prof_mark(c, MHD_AKCLASS_COMBINE);
   adj_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Xs, ING, a->Eb, a->GE);
   long long box = (long long)(g.n[0] + 4) * (g.n[1] + 4) * (NDIM == 3 ? g.n[2] + 4 : 1);
   adj_edge_faces_kernel<NDIM><<<blocks_for(box, 256), 256, 0, c->stream>>>(g, a->GE, As);
   prof_mark(c, MHD_AKCLASS_EDGE);
   CK(cudaMemsetAsync(a->Pb.q[0], 0, 8 * a->fe * sizeof(double), c->stream));
-  c->launches += 4;
+  c->launches += 3;
   if (split_now(c)) {  // the directions' Riemann transposes side by side (small grids)
     cudaEventRecord(c->ev_fork, c->stream);
     cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0);
@@ -243,10 +240,9 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const FaceIngr& ING, const F8& 
   long long pad = (long long)g.ext[0] * g.ext[1] * g.ext[2];
   adj_c2p_faces_kernel<NDIM><<<blocks_for(pad, 256), 256, 0, c->stream>>>(g, a->Pb, As);
   prof_mark(c, MHD_AKCLASS_C2P);
-  for (int d = g.ndim - 1; d >= 0; d--)
-    adj_ghost_periodic_kernel<<<blocks_for(ghost_layers_work(g, d), 256), 256, 0, c->stream>>>(g, As, d);
+  adj_ghost_shell_kernel<NDIM><<<blocks_for((long long)g.n[0] * g.n[1] * g.n[2], 256), 256, 0, c->stream>>>(g, As);
   prof_mark(c, MHD_AKCLASS_GHOST);
-  c->launches += 2 + g.ndim;
+  c->launches += 3;
   CK(cudaGetLastError());
   return MHD_OK;
 }
@@ -272,9 +268,11 @@ int seed(mhd_ctx* c, int functional) {
   else adj_seed_kernel<3><<<nb, 256, 0, c->stream>>>(g, c->U[0], a->A[3], functional, a->T, dV, a->Jcell);
   long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
   adj_sum_kernel<<<1, 1024, 0, c->stream>>>(a->Jcell, ncell, 0.5 * dV, a->scal);
-  for (int d = g.ndim - 1; d >= 0; d--)
-    adj_ghost_periodic_kernel<<<blocks_for(ghost_layers_work(g, d), 256), 256, 0, c->stream>>>(g, a->A[3], d);
-  c->launches += 2 + g.ndim;
+  if (g.ndim == 2)
+    adj_ghost_shell_kernel<2><<<blocks_for((long long)g.n[0] * g.n[1], 256), 256, 0, c->stream>>>(g, a->A[3]);
+  else
+    adj_ghost_shell_kernel<3><<<blocks_for((long long)g.n[0] * g.n[1] * g.n[2], 256), 256, 0, c->stream>>>(g, a->A[3]);
+  c->launches += 3;
   CK(cudaGetLastError());
   return MHD_OK;
 }

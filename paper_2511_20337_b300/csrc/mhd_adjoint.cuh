@@ -132,34 +132,62 @@ static __global__ void adj_sum_kernel(const double* __restrict__ v, long long n,
 }
 
 // ---------------------------------------------------------------------------
-// Transpose of the periodic ghost fill along axis d: every ghost slot's
-// cotangent is added to the interior slot it was copied from, then cleared.
-// The forward fills x, y, z in turn; the transposes run z, y, x.  Distinct
-// ghost slots of one pass have distinct sources when n_d >= 2G + 1.
+// Transpose of the periodic ghost fill: every ghost slot's cotangent is added
+// to the interior slot it was copied from, then cleared.  The forward fills
+// x, y, z in turn (each pass over the full padded transverse range), so the
+// transposes run z, y, x.
 // ---------------------------------------------------------------------------
-static __global__ void adj_ghost_periodic_kernel(Grid g, F8 A, int d) {
-  const long long total = ghost_layers_work(g, d);
+
+// All axes' transposes in one pass: every ghost slot of a periodic axis wraps
+// to exactly one interior cell, so the thread of that cell gathers its images
+// and clears them.  The sums keep the order of the axis-by-axis passes (z, y,
+// x): with Z = A + A(z image), Y = Z + Z(y image), the cell gets
+// Y + Y(x image), each term present only where the image exists (for
+// n_d >= 2G + 1 a cell has at most one image per axis).
+template <int NDIM>
+static __global__ void adj_ghost_shell_kernel(Grid g, F8 A) {
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
-    int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-    int e1 = g.hi(t1) - g.lo(t1) + 1;
-    int nl = 2 * g.G + 1;
-    int l = (int)(id % nl);
-    long long r = id / nl;
-    int a = (int)(r % e1) + g.lo(t1);
-    int b = (int)(r / e1) + g.lo(t2);
-    int gi = l < g.G ? l - g.G : g.n[d] + (l - g.G);
-    int x[3];
-    x[d] = gi;
-    x[t1] = a;
-    x[t2] = b;
-    int dst = g.at(x[0], x[1], x[2]);
-    x[d] = wrap(gi, g.n[d]);
-    int src = g.at(x[0], x[1], x[2]);
+    const int i = (int)(id % g.n[0]);
+    const long long r = id / g.n[0];
+    const int j = (int)(r % g.n[1]);
+    const int k = (int)(r / g.n[1]);
+    // the image along axis d of interior index x (or the index itself when there is none)
+    auto image = [&](int d, int x) {
+      if (d >= NDIM) return x;
+      if (x <= g.G) return x + g.n[d];            // upper ghost layer n_d + x (up to the extra slot n_d + G)
+      if (x >= g.n[d] - g.G) return x - g.n[d];   // lower ghost layer
+      return x;
+    };
+    const int ix = image(0, i), jy = image(1, j), kz = image(2, k);
+    const bool hx = ix != i, hy = jy != j, hz = kz != k;
+    if (!hx && !hy && !hz) continue;
+    const int ci[2] = {i, ix}, cj[2] = {j, jy}, ck[2] = {k, kz};
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-      A.q[q][src] += A.q[q][dst];
-      A.q[q][dst] = 0.0;
+      double* a = A.q[q];
+      double xs[2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {  // the cell's column and its x image
+        if (u == 1 && !hx) continue;
+        double ys[2];
+#pragma unroll
+        for (int v = 0; v < 2; v++) {  // the row and its y image
+          if (v == 1 && !hy) continue;
+          const int c0 = g.at(ci[u], cj[v], k);
+          double z = a[c0];
+          if (hz) {
+            const int c1 = g.at(ci[u], cj[v], ck[1]);
+            z += a[c1];
+            a[c1] = 0.0;
+          }
+          if (u == 1 || v == 1) a[c0] = 0.0;
+          ys[v] = z;
+        }
+        xs[u] = hy ? ys[0] + ys[1] : ys[0];
+      }
+      a[g.at(i, j, k)] = hx ? xs[0] + xs[1] : xs[0];
     }
   }
 }
@@ -169,9 +197,26 @@ static __global__ void adj_ghost_periodic_kernel(Grid g, F8 A, int d) {
 // out_B = c0 B0 + c1 Bs + cL L_B (evolved faces): the cotangents of the stage
 // increment (Lb on cells, LB on faces) and the accumulation into U0 and Us.
 // ---------------------------------------------------------------------------
+// Face (normal d) at index x evolved by the CT update on a periodic grid: the
+// faces the combine transpose writes LB on (every other LB is zero).
 template <int NDIM>
-static __global__ void adj_combine_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, L3 LB, double c0, double c1,
-                                          double cL) {
+__device__ __forceinline__ bool face_evolved(const Grid& g, int d, const int x[3]) {
+  bool ok = NDIM == 3 || x[2] == 0;
+#pragma unroll
+  for (int e = 0; e < NDIM; e++) {
+    ok = ok && x[e] >= 0;
+    if (e == d) ok = ok && (x[e] < g.n[e] || !g.periodic[e]);
+    else ok = ok && x[e] < g.n[e];
+  }
+  return ok;
+}
+
+// The combine transpose fused with that of the CT curl: Eb is formed
+// from LB = cL Aout on the evolved faces (zero elsewhere), read from Aout,
+// which no thread of this kernel writes.
+template <int NDIM>
+static __global__ void adj_combine_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, E3 Eb, double c0, double c1,
+                                          double cL, double dt) {
   const long long total = edge_work<NDIM>(g);
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
@@ -204,43 +249,32 @@ static __global__ void adj_combine_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, 
       if (NDIM == 2) ok = ok && k == 0;
       if (!ok) continue;
       double x = Aout.q[5 + d][c];
-      LB.q[d][c] = cL * x;
       A0.q[5 + d][c] += c0 * x;
       As.q[5 + d][c] += c1 * x;
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Transpose of the CT face increment L_B,d = -dt (curl E)_d: the cotangent of
-// each edge field from the face cotangents LB (zero on faces that are not
-// evolved).  E_C enters the faces of normal (C+1)%3 through their
-// (C+2)-difference and the faces of normal (C+2)%3 through their
-// (C+1)-difference.
-// ---------------------------------------------------------------------------
-template <int NDIM>
-static __global__ void adj_curl_kernel(Grid g, L3 LB, E3 Eb, double dt) {
-  const long long total = edge_work<NDIM>(g);
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int ex = g.n[0] + 1, ey = g.n[1] + 1;
-    int i = (int)(id % ex);
-    long long r = id / ex;
-    int j = (int)(r % ey);
-    int k = (int)(r / ey);
-    int c = g.at(i, j, k);
+    // transpose of the CT face increment L_B,d = -dt (curl E)_d at the edges
+    // (i, j, k): E_C enters the faces of normal (C+1)%3 through their
+    // (C+2)-difference and the faces of normal (C+2)%3 through their
+    // (C+1)-difference
+    auto lb = [&](int d, int di, int dj, int dk) {
+      const int x[3] = {i + di, j + dj, k + dk};
+      return face_evolved<NDIM>(g, d, x) ? cL * Aout.q[5 + d][g.at(x[0], x[1], x[2])] : 0.0;
+    };
 #pragma unroll
     for (int C = 0; C < 3; C++) {
       if (!edge_valid<NDIM>(g, C, i, j, k)) continue;
       double acc = 0.0;
-      const int d = (C + 1) % 3, d1 = (C + 2) % 3;  // L_B,d = -(E_C[+d1] - E_C) dt/dx_d1 (+ ...)
-      if (d < NDIM && d1 < NDIM) acc += (dt * g.idx[d1]) * (LB.q[d][c] - LB.q[d][c - g.stride(d1)]);
-      const int e = (C + 2) % 3, e2 = (C + 1) % 3;  // L_B,e = (E_C[+e2] - E_C) dt/dx_e2 (+ ...)
-      if (e < NDIM && e2 < NDIM) acc += (dt * g.idx[e2]) * (LB.q[e][c - g.stride(e2)] - LB.q[e][c]);
+      const int d = (C + 1) % 3, d1 = (C + 2) % 3;
+      if (d < NDIM && d1 < NDIM)
+        acc += (dt * g.idx[d1]) * (lb(d, 0, 0, 0) - lb(d, -(d1 == 0), -(d1 == 1), -(d1 == 2)));
+      const int e = (C + 2) % 3, e2 = (C + 1) % 3;
+      if (e < NDIM && e2 < NDIM)
+        acc += (dt * g.idx[e2]) * (lb(e, -(e2 == 0), -(e2 == 1), -(e2 == 2)) - lb(e, 0, 0, 0));
       Eb.e[C][c] = acc;
     }
   }
 }
+
 
 // ---------------------------------------------------------------------------
 // Transpose of one UCT edge field (uct_edge<C>): the 18 edge-local cotangents
