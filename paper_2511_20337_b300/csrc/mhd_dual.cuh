@@ -117,6 +117,7 @@ __device__ __forceinline__ D3 frsqrt(const D3& x) {
   return r;
 }
 __device__ __forceinline__ D3 fabs(const D3& x) { return lt0(x.v) ? -x : x; }
+__device__ __forceinline__ D3 dabs(const D3& x) { return fabs(x); }
 __device__ __forceinline__ bool gt0(const D3& x) { return gt0(x.v); }
 __device__ __forceinline__ bool lt0(const D3& x) { return lt0(x.v); }
 __device__ __forceinline__ bool ge0(const D3& x) { return ge0(x.v); }

@@ -87,9 +87,9 @@ static __global__ void __launch_bounds__(256) glm_prim_kernel(Grid g, F9 S, F9 P
       }
       if (CFL) {
         double B2 = a_(a_(m_(V.bx, V.bx), m_(V.by, V.by)), m_(V.bz, V.bz));
-        double lam = m_(a_(fabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
-        lam = a_(lam, m_(a_(fabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
-        if (NDIM == 3) lam = a_(lam, m_(a_(fabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
+        double lam = m_(a_(dabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
+        lam = a_(lam, m_(a_(dabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
+        if (NDIM == 3) lam = a_(lam, m_(a_(dabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
         lam_max = (lam > lam_max) ? lam : lam_max;
       }
     }

@@ -281,9 +281,9 @@ __device__ __forceinline__ double prim_item(const Grid& g, const F8& S, const F8
     }
     if (CFL) {
       double B2 = a_(a_(m_(V.bx, V.bx), m_(V.by, V.by)), m_(V.bz, V.bz));
-      lam = m_(a_(fabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
-      lam = a_(lam, m_(a_(fabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
-      if (NDIM == 3) lam = a_(lam, m_(a_(fabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
+      lam = m_(a_(dabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
+      lam = a_(lam, m_(a_(dabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
+      if (NDIM == 3) lam = a_(lam, m_(a_(dabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
     }
   }
   return lam;
@@ -340,17 +340,17 @@ __device__ __forceinline__ void cfl_block_finish(double lam_max, DevScalars* sc,
 template <int NDIM>
 __device__ __forceinline__ double cfl_rate_near_ieee(const Grid& g, const Prim8& V) {
   double B2 = a_(a_(m_(V.bx, V.bx), m_(V.by, V.by)), m_(V.bz, V.bz));
-  double lam = m_(a_(fabs(V.vx), fast_speed_near_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
-  lam = a_(lam, m_(a_(fabs(V.vy), fast_speed_near_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
-  if (NDIM == 3) lam = a_(lam, m_(a_(fabs(V.vz), fast_speed_near_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
+  double lam = m_(a_(dabs(V.vx), fast_speed_near_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
+  lam = a_(lam, m_(a_(dabs(V.vy), fast_speed_near_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
+  if (NDIM == 3) lam = a_(lam, m_(a_(dabs(V.vz), fast_speed_near_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
   return lam;
 }
 template <int NDIM>
 __device__ __forceinline__ double cfl_rate_ieee(const Grid& g, const Prim8& V) {
   double B2 = a_(a_(m_(V.bx, V.bx), m_(V.by, V.by)), m_(V.bz, V.bz));
-  double lam = m_(a_(fabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
-  lam = a_(lam, m_(a_(fabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
-  if (NDIM == 3) lam = a_(lam, m_(a_(fabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
+  double lam = m_(a_(dabs(V.vx), fast_speed_ieee(V.rho, V.p, B2, V.bx, g.gamma)), g.idx[0]);
+  lam = a_(lam, m_(a_(dabs(V.vy), fast_speed_ieee(V.rho, V.p, B2, V.by, g.gamma)), g.idx[1]));
+  if (NDIM == 3) lam = a_(lam, m_(a_(dabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
   return lam;
 }
 // Primitive pass of the single grid; with CFL, the near-IEEE rate of every
@@ -820,12 +820,14 @@ static __global__ void __launch_bounds__(256) emf_kernel(Grid g, F8 S, FaceIngr 
 // ---------------------------------------------------------------------------
 enum { COMB_FIRST = 0, COMB_RK2_FINAL = 1, COMB_RK3_SECOND = 2, COMB_RK3_FINAL = 3 };
 
+// Plain arithmetic here: the CT + RK kernel is bound by memory, where loading
+// the register constants of the DFMA forms would cost more than it saves.
 __device__ __forceinline__ double combine(int mode, double u0, double us, double l) {
   switch (mode) {
-    case COMB_FIRST: return fadd(us, l);
-    case COMB_RK2_FINAL: return kmul(RK_HALF, fadd(fadd(u0, us), l));
-    case COMB_RK3_SECOND: return kmul(RK_QUARTER, fadd(fma(rk(RK_3), u0, us), l));
-    default: return fmul(fma(rk(RK_2), l, fma(rk(RK_2), us, u0)), rk(RK_THIRD));
+    case COMB_FIRST: return us + l;
+    case COMB_RK2_FINAL: return 0.5 * ((u0 + us) + l);
+    case COMB_RK3_SECOND: return 0.25 * (fma(3.0, u0, us) + l);
+    default: return fma(2.0, l, fma(2.0, us, u0)) * (1.0 / 3.0);
   }
 }
 
@@ -850,8 +852,8 @@ __device__ __forceinline__ void ct_rk_item(const Grid& g, const F8& U0, const F8
       int slot = q < 5 ? q : 7;
       double l = L.q[q][c];
       if (SPLIT) {
-        l = fma(-fmul(dt, g.idx[1]), Dy->q[q][c], l);
-        if (NDIM == 3) l = fma(-fmul(dt, g.idx[2]), Dz->q[q][c], l);
+        l = fma(-(dt * g.idx[1]), Dy->q[q][c], l);
+        if (NDIM == 3) l = fma(-(dt * g.idx[2]), Dz->q[q][c], l);
       }
       Out.q[slot][c] = combine(mode, U0.q[slot][c], Us.q[slot][c], l);
     }
@@ -871,9 +873,9 @@ __device__ __forceinline__ void ct_rk_item(const Grid& g, const F8& U0, const F8
     if (!ok) continue;
     const bool has1 = d1 < NDIM, has2 = d2 < NDIM;
     double t1 = 0.0, t2 = 0.0;
-    if (has1) t1 = fmul(fsub(E.e[d2][c + g.stride(d1)], E.e[d2][c]), fmul(dt, g.idx[d1]));
-    if (has2) t2 = fmul(fsub(E.e[d1][c + g.stride(d2)], E.e[d1][c]), fmul(dt, g.idx[d2]));
-    double lb = (has1 && has2) ? fsub(t2, t1) : (has1 ? -t1 : t2);
+    if (has1) t1 = __dmul_rn(E.e[d2][c + g.stride(d1)] - E.e[d2][c], dt * g.idx[d1]);
+    if (has2) t2 = __dmul_rn(E.e[d1][c + g.stride(d2)] - E.e[d1][c], dt * g.idx[d2]);
+    double lb = (has1 && has2) ? t2 - t1 : (has1 ? -t1 : t2);
     Out.q[5 + d][c] = combine(mode, U0.q[5 + d][c], Us.q[5 + d][c], lb);
   }
 }

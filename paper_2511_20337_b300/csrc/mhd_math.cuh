@@ -140,6 +140,8 @@ __device__ __forceinline__ double imax(double a, double b) { return order_key(a)
 // both arguments non-negative
 __device__ __forceinline__ double imax_pos(double a, double b) { return bits(a) < bits(b) ? b : a; }
 __device__ __forceinline__ bool lt_pos(double a, double b) { return bits(a) < bits(b); }   // a < b, b >= 0
+// |x| by clearing the sign bit on the integer pipes (the same value as fabs)
+__device__ __forceinline__ double dabs(double x) { return from_bits(bits(x) & kMag); }
 // x * (s > 0 ? 1 : -1) by flipping the sign bit
 __device__ __forceinline__ double times_sign(double x, double s) {
   return from_bits(bits(x) ^ (gt0(s) ? 0LL : kSign));
@@ -410,7 +412,7 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
   T eL(1.0), eR(1.0);  // star ratios B*_t / B_t (UCT weights)
   {
     T rsm = mul_rn(rsL, smL), D = fsub(rsm, bn2);
-    if (lt_pos(fabs(D), kmul(RK_EPS, rsm))) {
+    if (lt_pos(dabs(D), kmul(RK_EPS, rsm))) {
       vsL = L.v; wsL = L.w; b1sL = L.b1; b2sL = L.b2;
     } else {
       T iD = rcp(D);
@@ -425,7 +427,7 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
   }
   {
     T rsm = mul_rn(rsR, smR), D = fsub(rsm, bn2);
-    if (lt_pos(fabs(D), kmul(RK_EPS, rsm))) {
+    if (lt_pos(dabs(D), kmul(RK_EPS, rsm))) {
       vsR = R.v; wsR = R.w; b1sR = R.b1; b2sR = R.b2;
     } else {
       T iD = rcp(D);
@@ -463,7 +465,7 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
   if (!lt_pos(bn2, kmul(RK_2EPS, pTs))) {  // 0.5 bn2 >= eps pTs, scaled by 2 exactly
     T iqL = frsqrt(rhosL), iqR = frsqrt(rhosR);  // 1/sqrt(rho*)
     T sqL = fmul(rhosL, iqL), sqR = fmul(rhosR, iqR);  // sqrt(rho*)
-    T abn = fabs(bn);
+    T abn = dabs(bn);
     T Ss = left ? fma(-abn, iqL, SM) : fma(abn, iqR, SM);
     bool beyond = left ? lt0(Ss) : ge0(Ss);      // x/t = 0 lies between S*_a and S_M
     if (UCT && beyond) {                         // S*_L < 0 <= S*_R
@@ -549,7 +551,7 @@ __device__ __forceinline__ void recon_wenoz_c(double a0, double a1, double a2, d
   c2 = curv(a2, a3, a4);
   u = fma(rk(RK_3), a2, fma(rk(RK_M4), a3, a4));
   double b2 = fma(c2.k, c2.t, fmul(kmul(RK_QUARTER, u), u));
-  double tau = fabs(fsub(b0, b2));
+  double tau = dabs(fsub(b0, b2));
   const double weps = rk(RK_WEPS);
   double r0 = fmul(tau, rcp(fadd(b0, weps))), r1 = fmul(tau, rcp(fadd(b1, weps))), r2 = fmul(tau, rcp(fadd(b2, weps)));
   double g0 = fma(r0, r0, rk(RK_ONE)), g1 = fma(r1, r1, rk(RK_ONE)), g2 = fma(r2, r2, rk(RK_ONE));

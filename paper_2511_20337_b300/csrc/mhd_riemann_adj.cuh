@@ -237,7 +237,7 @@ __device__ __forceinline__ void star_side(const W7& W, double S, double SM, doub
   t.ism = rcp(t.sm);
   t.rhos = fmul(t.rs, t.ism);
   const double rsm = mul_rn(t.rs, t.sm), D = fsub(rsm, bn2);
-  t.degen = lt_pos(fabs(D), fmul(kHlldDegenEps, rsm));
+  t.degen = lt_pos(dabs(D), fmul(kHlldDegenEps, rsm));
   if (t.degen) {
     t.vs = W.v; t.ws = W.w; t.b1s = W.b1; t.b2s = W.b2;
     t.iD = t.cv = t.cb = 0.0;
@@ -348,7 +348,7 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     if (!lt_pos(kmul(RK_HALF, bn2), fmul(kHlldBnEps, pTs))) {
       const double iqL = frsqrt(tL.rhos), iqR = frsqrt(tR.rhos);
       const double sqL = fmul(tL.rhos, iqL), sqR = fmul(tR.rhos, iqR);
-      const double abn = fabs(bn);
+      const double abn = dabs(bn);
       const double Ss = left ? fma(-abn, iqL, SM) : fma(abn, iqR, SM);
       const bool beyond = left ? lt0(Ss) : ge0(Ss);
       if (beyond) {
