@@ -245,8 +245,16 @@ GLM_SWEEP_SOURCES = SWEEP_SOURCES + ("mhd_glm.cuh",)
 
 
 def sweep_source_hash(files=SWEEP_SOURCES):
-    src = [os.path.join(ROOT, "paper_2511_20337_b300", "csrc", f) for f in files]
-    return hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
+    """Hash of the sweep kernels' code: the sources with comments and
+    whitespace removed, so that an edit of a comment keeps the captures."""
+    import re
+    text = ""
+    for f in files:
+        s = open(os.path.join(ROOT, "paper_2511_20337_b300", "csrc", f)).read()
+        s = re.sub(r"/\*.*?\*/", " ", s, flags=re.S)
+        s = re.sub(r"//[^\n]*", " ", s)
+        text += " ".join(s.split()) + "\n"
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 def fp64_peak(dev):

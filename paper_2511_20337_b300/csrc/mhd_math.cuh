@@ -3,14 +3,17 @@
 // solvers, and the PLM / WENO-Z / PPM reconstructions (paper §2.2).
 //
 // Two flavours of arithmetic:
-//   *_ieee : fixed-order IEEE operations (__dadd_rn & co.) for the primitive
-//            recovery and the CFL speed, so that those values match the
-//            oracle to the bit;
+//   *_ieee : fixed-order IEEE operations (correctly rounded sums, products,
+//            quotients and square roots, each rounded once) for the
+//            primitive recovery and the CFL speed, so that those values match
+//            the oracle to the bit;
 //   the rest: fused multiply-adds written out as fma(), reciprocals formed
 //            once per quantity.  The library is compiled without implicit
 //            contraction, so every kernel that inlines these functions rounds
 //            them identically (the batched and single-grid paths agree to the
 //            bit).
+// Both write single products, sums and differences in the exact DFMA forms
+// below (fmul, fadd, fsub), which the FP64 pipe issues faster.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
