@@ -20,7 +20,7 @@ struct mhd_ctx {
   mhd::F8 U[3];        // RK registers (U[0] = U^n); each register's 8 fields are contiguous
   mhd::F8 P;           // primitives of the stage input
   mhd::L6 L;           // stage increment of the cell variables
-  mhd::FaceIngr ING;    // UCT face ingredients
+  mhd::FaceIngr ING;   // UCT face ingredients
   mhd::E3 E;           // edge fields
   double* lam;         // near-IEEE CFL rate of every cell (the candidate pass of the CFL step)
   mhd::DevScalars* sc;
