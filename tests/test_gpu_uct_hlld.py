@@ -1,7 +1,7 @@
 """The UCT-HLLD edge field (emf="uct_hlld") on the GPU against the oracle:
 the sweeps' HLLD weights face by face over every region of the wave fan, one
-step to 1e-12 and twenty steps to 1e-10 (normwise per array), the CFL step
-bitwise; plus properties that hold at any size (the plane-parallel CT B_y =
+step to 1e-12, twenty steps and 100 CFL steps to 1e-10 (normwise per array),
+the CFL step bitwise; plus properties that hold at any size (the plane-parallel CT B_y =
 finite-volume B_z identity, conservation, div B, segment-length invariance),
 the batched and allocation-free entry points equal to the context API
 bitwise, and the configurations that must be refused."""
@@ -122,6 +122,19 @@ def test_twenty_steps_match_oracle(mhd, case):
     for dt in dts:
         h.step(dt)
     assert relerr(h.get_conserved()["b0"], g.get_conserved()["b0"]) > 1e-9
+
+
+def test_orszag_tang_2d_128_100_steps(mhd):
+    """The 2D Orszag-Tang workload (128^2, PLM + HLLD + RK2, CFL 0.4) with the
+    HLLD edge weights: 100 CFL steps each side with its own dt, state within
+    1e-10, time to round-off."""
+    cfg, st = W.orszag_tang_2d(128, emf="uct_hlld")
+    o = oracle.OracleSim(cfg, st)
+    o.advance(100)
+    g = mhd.Sim(cfg, st)
+    g.advance(100)
+    compare(g.get_conserved(), o.get_state(), 1e-10, "OT 100 steps")
+    assert abs(g.time - o.time) <= 1e-13 * o.time
 
 
 @pytest.mark.parametrize("rk", [2, 3])
