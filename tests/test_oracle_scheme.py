@@ -455,10 +455,10 @@ def wave_state_2d(n, wave, amp, t=0.0, recon="plm", rk=2):
     return cfg, st, period
 
 
-def wave_error(n, wave, recon="plm", rk=2):
+def wave_error(n, wave, recon="plm", rk=2, emf="uct_hll"):
     amp = 1e-6
     cfg, st, T = wave_state_2d(n, wave, amp, recon=recon, rk=rk)
-    s = oracle.OracleSim(cfg, st)
+    s = oracle.OracleSim(dict(cfg, emf=emf), st)
     t = 0.0
     while t < T - 1e-14:
         dt = min(s.cfl_dt(), T - t)

@@ -275,3 +275,18 @@ def test_cpa_2d_converges_to_exact_translation():
     e = [err(n, "uct_hlld") for n in (16, 32, 64)]
     assert e[0] / e[1] > 2.4 and e[1] / e[2] > 2.3, e
     assert e[2] <= 1.05 * cpa_error(64, 2, T)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("wave", ["fast", "alfven"])
+def test_linear_wave_second_order(wave):
+    """Oblique linear fast and Alfven waves over one period with the HLLD edge
+    weights: about second order (a first-order defect would give a ratio near
+    2), and on the Alfven wave, the mode the HLLD fan resolves, a smaller error
+    than with the HLL weights at every resolution."""
+    from test_oracle_scheme import wave_error
+    e = [wave_error(n, wave, emf="uct_hlld") for n in (16, 32, 64)]
+    assert e[0] / e[1] > 2.5 and e[1] / e[2] > 2.4, e
+    if wave == "alfven":
+        h = [wave_error(n, wave) for n in (16, 32, 64)]
+        assert all(a < 0.95 * b for a, b in zip(e, h)), (e, h)
