@@ -1,6 +1,6 @@
 """The scheme with GLM divergence cleaning on the GPU against the oracle's
-(oracle/glm_oracle.hpp), element by element: one step to 1e-12 and 20 steps
-to 1e-10 (normwise per array), the CFL step bitwise; plus properties that hold
+(oracle/glm_oracle.hpp), element by element: one step to 1e-12, 20 steps and
+100 CFL steps to 1e-10 (normwise per array), the CFL step bitwise; plus properties that hold
 at any size (segment-length invariance, steady uniform states, conservation)
 and the CT-only entry points rejecting GLM."""
 import numpy as np
@@ -81,6 +81,20 @@ def test_twenty_steps_match_oracle(name):
     for dt in dts:
         g.step(dt)
     compare(g.get_conserved(), o.get_state(), 1e-10, name)
+
+
+def test_orszag_tang_2d_128_100_steps():
+    """The 2D Orszag-Tang workload (128^2, PLM + HLLD + RK2) with GLM
+    cleaning: 100 CFL steps each side with its own dt, state within 1e-10,
+    time to round-off."""
+    cfg, st = W.orszag_tang_2d(128)
+    cfg, st = glm_cfg(cfg), glm_state(cfg, st)
+    o = oracle.OracleGlm(cfg, st, alpha=cfg["glm_alpha"])
+    t = sum(o.advance(100, record_dt=True))
+    g = mhd.Sim(cfg, st)
+    g.advance(100)
+    compare(g.get_conserved(), o.get_state(), 1e-10, "OT GLM 100 steps")
+    assert abs(g.time - t) <= 1e-13 * t
 
 
 def test_device_cfl_steps_equal_host_steps_bitwise():
