@@ -14,6 +14,22 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
 
 
+_CUDA = None
+
+
+def pytest_runtest_setup(item):
+    """A test marked gpu is skipped, before its fixtures, where no CUDA device
+    is present (it would otherwise fail at the library's first device call)."""
+    global _CUDA
+    if item.get_closest_marker("gpu") is None:
+        return
+    if _CUDA is None:
+        import torch
+        _CUDA = torch.cuda.is_available()
+    if not _CUDA:
+        pytest.skip("no CUDA device")
+
+
 def relerr(a, b):
     """Normwise relative difference max|a-b| / max|b| (0 if both vanish)."""
     a = np.asarray(a, dtype=np.float64)
