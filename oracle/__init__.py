@@ -92,6 +92,9 @@ def lib():
         L.orc_glm_fallbacks.argtypes = [P]
         L.orc_count_tape.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
                                      ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
+        L.orc_count_wenoz_shared.restype = ctypes.c_ulonglong
+        L.orc_count_wenoz_shared.argtypes = [DP]
+        L.orc_state_from_prims.argtypes = [ctypes.POINTER(OrcConfig), PP, PP, ctypes.POINTER(DP)]
         _lib = L
     return _lib
 
@@ -329,6 +332,14 @@ def cfl_dt_state(cfg, state):
     return lib().orc_cfl_dt_state(ctypes.byref(c), _ptrs(arrs))
 
 
+def count_wenoz_shared(stencil=(0.3, -1.2, 0.7, 2.1, -0.4)):
+    """Counted flops of the face-independent part of one WENO-Z face value
+    (indicators, tau5, ratios, 1 + ratio^2), which is the same for both faces
+    of a cell; the count does not depend on the stencil's values."""
+    a = np.ascontiguousarray(stencil, dtype=np.float64)
+    return int(lib().orc_count_wenoz_shared(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
 def count_flops(cfg, state, nsteps, dt):
     """Counted-scalar run: dict phase -> dict op -> count (one CFL + nsteps steps)."""
     c = make_config(cfg)
@@ -376,6 +387,15 @@ def _prim_args(cfg, prim, B, dts, target):
         T = [np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(shapes[0])) for t in target]
     keep = (P, Bs, d, T)
     return keep, _parr(P), _parr(Bs), _dp(d), (_parr(T) if T is not None else None)
+
+
+def state_from_prims(cfg, prim, B):
+    """The conserved state (dict of KEYS) that the functional's initial map
+    builds from primitives rho, vx, vy, vz, p and the field B (Eq. Energy)."""
+    keep, P, Bp, d, T = _prim_args(cfg, prim, B, [], None)
+    arrs = [np.zeros(s) for s in state_shapes(cfg)]
+    lib().orc_state_from_prims(ctypes.byref(make_config(cfg)), P, Bp, _ptrs(arrs))
+    return dict(zip(KEYS, arrs))
 
 
 def functional_prim(cfg, prim, B, dts, which="magnetic_energy", target=None, signature=False):

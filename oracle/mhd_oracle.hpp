@@ -394,10 +394,14 @@ template <class R> inline void recon_plm(const R s[5], R& plus, R& minus) {
 // values q_k, Jiang-Shu smoothness indicators beta_k, tau5 = |beta_0 - beta_2|,
 // alpha_k = d_k (1 + (tau5 / (beta_k + eps))^2), d = (1/10, 6/10, 3/10).
 // Readings: eps = 1e-40, exponent 2, applied componentwise to primitives.
-template <class R> inline R wenoz_face(R a0, R a1, R a2, R a3, R a4) {
-  R q0 = ((R(2.0) * a0 - R(7.0) * a1) + R(11.0) * a2) / R(6.0);
-  R q1 = ((-a1 + R(5.0) * a2) + R(2.0) * a3) / R(6.0);
-  R q2 = ((R(2.0) * a2 + R(5.0) * a3) - a4) / R(6.0);
+//
+// The indicators, tau5, the ratios tau5 / (beta_k + eps) and the factors
+// 1 + ratio^2 depend only on the five cell values, not on the face: the
+// mirrored stencil of the cell's left face has the same ones with beta_0 and
+// beta_2 exchanged.  wenoz_shared forms them (one face's worth, as the formula
+// states them); wenoz_face calls it for each face.  The flop count of
+// wenoz_shared is what an implementation that forms them once per cell saves.
+template <class R> inline void wenoz_shared(R a0, R a1, R a2, R a3, R a4, R& h0, R& h1, R& h2) {
   R t;
   t = (a0 - R(2.0) * a1) + a2;
   R u = (a0 - R(4.0) * a1) + R(3.0) * a2;
@@ -412,9 +416,19 @@ template <class R> inline R wenoz_face(R a0, R a1, R a2, R a3, R a4) {
   R r0 = tau / (b0 + R(WENOZ_EPS));
   R r1 = tau / (b1 + R(WENOZ_EPS));
   R r2 = tau / (b2 + R(WENOZ_EPS));
-  R al0 = R(0.1) * (R(1.0) + r0 * r0);
-  R al1 = R(0.6) * (R(1.0) + r1 * r1);
-  R al2 = R(0.3) * (R(1.0) + r2 * r2);
+  h0 = R(1.0) + r0 * r0;
+  h1 = R(1.0) + r1 * r1;
+  h2 = R(1.0) + r2 * r2;
+}
+template <class R> inline R wenoz_face(R a0, R a1, R a2, R a3, R a4) {
+  R q0 = ((R(2.0) * a0 - R(7.0) * a1) + R(11.0) * a2) / R(6.0);
+  R q1 = ((-a1 + R(5.0) * a2) + R(2.0) * a3) / R(6.0);
+  R q2 = ((R(2.0) * a2 + R(5.0) * a3) - a4) / R(6.0);
+  R h0, h1, h2;
+  wenoz_shared(a0, a1, a2, a3, a4, h0, h1, h2);
+  R al0 = R(0.1) * h0;
+  R al1 = R(0.6) * h1;
+  R al2 = R(0.3) * h2;
   R sum = (al0 + al1) + al2;
   return ((al0 * q0 + al1 * q1) + al2 * q2) / sum;
 }

@@ -272,6 +272,21 @@ int orc_count_flops(const OrcConfig* c, const double* const* arrays, int nsteps,
   return 0;
 }
 
+// Flops of the face-independent part of one WENO-Z face value (wenoz_shared:
+// the three indicators, tau5, the ratios and 1 + ratio^2) on the stencil a[5],
+// counted with the Counted scalar: the part a per-cell implementation forms
+// once for both faces of a cell.
+unsigned long long orc_count_wenoz_shared(const double* a) {
+  g_flops.reset();
+  g_flops.phase = PH_RECON;
+  Counted h0, h1, h2;
+  wenoz_shared<Counted>(Counted(a[0]), Counted(a[1]), Counted(a[2]), Counted(a[3]), Counted(a[4]), h0, h1, h2);
+  unsigned long long n = 0;
+  for (int op = 0; op < OP_N; op++) n += g_flops.n[PH_RECON][op];
+  g_flops.reset();
+  return n;
+}
+
 // Reverse-mode work of nsteps steps of size dt from the given state, every
 // state element (cells and faces) a tape variable: out_links[PH_N] flops of
 // the backward sweep and out_pflops[PH_N] partial-derivative flops per phase.
@@ -302,6 +317,16 @@ int orc_count_tape(const OrcConfig* c, const double* const* arrays, int nsteps, 
 // dts[nsteps] the frozen step sizes; which = 0 magnetic energy, 1 misfit to
 // target[0..4 (2D: 5)] (cell arrays of rho, mx, my, mz, E (, Bz)).
 static size_t ncells(const Config& c) { return (size_t)c.nx * c.ny * (c.ndim == 3 ? c.nz : 1); }
+
+// The initial conserved state set_from_prims builds from prim[0..4] = rho, vx,
+// vy, vz, p and the fields B[0..2], written to out[0..7] in the state layout.
+int orc_state_from_prims(const OrcConfig* oc, const double* const* prim, const double* const* B,
+                         double* const* out) {
+  Sim<double> s(to_cfg(oc));
+  set_from_prims(s, prim[0], prim[1], prim[2], prim[3], prim[4], B);
+  store(s, out);
+  return 0;
+}
 
 int orc_functional_prim(const OrcConfig* oc, const double* const* prim, const double* const* B, const double* dts,
                         int nsteps, int which, const double* const* target, double* J, unsigned long long* sig) {

@@ -16,6 +16,10 @@ the oracle's own loop ranges:
   ct        per evolved face and stage
   rk        per evolved element and stage
   cfl       per interior cell
+WENO-Z recon counts the face-independent part of each face value (the
+smoothness indicators, tau5, the ratios and 1 + ratio^2) once per cell and
+variable, as the method needs it; the oracle's per-face count is kept beside
+it (recon_per_face_count).
 Each variant also gets the reverse-mode (adjoint) work per unit of the same
 phases, from the oracle's tape on one step: the forward flops, plus the flops
 that form the partial derivatives, plus the backward sweep over the tape
@@ -116,6 +120,23 @@ def glm_counts(cfg, st):
     return o.count_flops(1, dt)
 
 
+def wenoz_once_per_cell(cfg, per, nvar):
+    """WENO-Z: the oracle forms each face value as the formula states it, so
+    the indicators, tau5, the ratios and 1 + ratio^2 -- the same for the two
+    faces of a cell -- are counted twice per cell and variable.  The method's
+    work forms them once: per["recon"] becomes that count (the oracle's count
+    less one Counted run of those sub-expressions per reconstructed variable),
+    and the oracle's own count is kept as per["recon_per_face_count"].
+    nvar reconstructed variables per cell: 7 (rho, v, the two transverse B, p)
+    for CT, 9 (all of B and psi) for GLM."""
+    if cfg["recon"] != "wenoz":
+        return
+    shared = oracle.count_wenoz_shared()
+    per["recon_per_face_count"] = per["recon"]
+    per["wenoz_shared_per_variable"] = shared
+    per["recon"] = per["recon"] - nvar * shared
+
+
 def main():
     out = {"convention": "flops per unit: +,-,*,/,sqrt = 1; a*b+c = 2; compare/abs/min/max = 0",
            "variants": {}}
@@ -129,6 +150,7 @@ def main():
             tot = sum(counts[ph].values())
             per[ph] = tot / u[ph]
         per["div_sqrt_per_face"] = (counts["riemann"]["div"] + counts["riemann"]["sqrt"]) / u["riemann"]
+        wenoz_once_per_cell(cfg, per, nvar=7)
         tape = oracle.count_tape(cfg, st, 1, dt)
         adj = {}
         for ph in ("c2p", "recon", "riemann", "fluxdiff", "emf", "ct", "rk"):
@@ -144,6 +166,7 @@ def main():
         counts = glm_counts(cfg, st)
         u = units_glm(cfg)
         per = {ph: sum(counts[ph].values()) / u[ph] for ph in ("c2p", "recon", "riemann", "fluxdiff", "rk", "cfl")}
+        wenoz_once_per_cell(cfg, per, nvar=9)
         out["variants"][name] = {"config": {k: cfg[k] for k in ("ndim", "n", "recon", "riemann", "rk", "bc")},
                                  "divb": "glm", "per_unit": per}
     path = os.path.join(HERE, "flops_per_unit.json")
