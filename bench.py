@@ -11,6 +11,13 @@ host memory before, and read back after, every step.  Under torchrun each rank
 runs its own replica (the step is not sharded across GPUs): value = all ranks'
 cell-updates / max rank time.
 
+The default workload is the 512^3 magnetised blast (WENO-Z + HLLD + SSP-RK3 +
+UCT CT, outflow).  After its plain step, the same run measures the batched
+ensemble (256 2D runs in one graph per step) and the adjoint (a 400-step
+gradient of a 256^2 run) on the same GPU and adds them to the one JSON line as
+batched_vs_plain and adjoint_vs_plain, each with its own cell-updates/s, its
+roofline fraction and its ratio to the plain step (--no-companions skips them).
+
 --impl reference times the FP64 CPU oracle on the host cores, on a bounded
 sample of the same workload (a smaller grid of the same kind), same metric.
 """
@@ -167,6 +174,18 @@ def cells_of(cfg):
 # ---------------------------------------------------------------------------
 # algorithmic flops (per-unit counts of the oracle, stored by tests/golden/make_flops.py)
 # ---------------------------------------------------------------------------
+def per_unit_counts(variant, per_face=False):
+    """The oracle's per-unit flop counts of a variant.  per_face=True takes
+    the WENO-Z reconstruction as the oracle counts it, face by face (the
+    face-independent indicators and ratios twice per cell); the default counts
+    them once per cell, as the method needs them."""
+    path = os.path.join(ROOT, "tests", "golden", "flops_per_unit.json")
+    per = dict(json.load(open(path))["variants"][variant]["per_unit"])
+    if per_face and "recon_per_face_count" in per:
+        per["recon"] = per["recon_per_face_count"]
+    return per
+
+
 def glm_flop_model(cfg, per):
     """Algorithmic flops of the GLM scheme (its own loop ranges: interior pencils, 9 variables)."""
     nd = cfg["ndim"]
@@ -183,9 +202,8 @@ def glm_flop_model(cfg, per):
     return {"sweep_per_launch": sweep, "step": step, "per_cell_update": step / cells}
 
 
-def flop_model(cfg, variant):
-    path = os.path.join(ROOT, "tests", "golden", "flops_per_unit.json")
-    per = json.load(open(path))["variants"][variant]["per_unit"]
+def flop_model(cfg, variant, per_face=False):
+    per = per_unit_counts(variant, per_face)
     if cfg.get("divb", "ct") == "glm":
         return glm_flop_model(cfg, per)
     nd = cfg["ndim"]
@@ -480,11 +498,13 @@ def run_ours(args):
     value = job_rate(ncell * args.steps, world, t_max)
 
     # ---- per-kernel device times (events after each launch) for the roofline ----
-    prof_steps = max(1, min(args.steps, 10))
+    big = ncell > 256 ** 3   # a 512^3 step takes seconds: shorter profile and e2e legs
+    prof_steps = max(1, min(args.steps, 5 if big else 10))
     kms, kcnt = sim.profile_steps(prof_steps)
     peak, peak_src, rates = fp64_peak(dev)
     probe = rates["dfma"]
     fm = flop_model(cfg, variant)
+    fm_face = flop_model(cfg, variant, per_face=True)
     nd = cfg["ndim"]
     sweep_ms = sum(kms[f"sweep_{a}"] for a in "xyz"[:nd])
     sweep_launches = sum(kcnt[f"sweep_{a}"] for a in "xyz"[:nd])
@@ -492,6 +512,8 @@ def run_ours(args):
     achieved = sweep_flops / (sweep_ms * 1e-3) / 1e9
     step_ms_prof = sum(kms.values()) / prof_steps
     step_achieved = fm["step"] / (step_ms_prof * 1e-3) / 1e9
+    face_frac = sum(fm_face["sweep_per_launch"].values()) * cfg["rk"] * prof_steps / (sweep_ms * 1e-3) / 1e9 / peak
+    face_step_frac = fm_face["step"] / (step_ms_prof * 1e-3) / 1e9 / peak
     n = list(cfg["n"][:nd])
     faces_per_launch = sum((n[d] + 1) * int(np.prod([n[t] + 2 for t in range(nd) if t != d])) for d in range(nd)) / nd
     sweep_name = ("glm_sweep_kernel (fused reconstruct + (B_n, psi) solve + HLLD + flux difference)"
@@ -508,6 +530,12 @@ def run_ours(args):
                 "step_achieved": step_achieved, "step_frac": step_achieved / peak,
                 "flops_per_cell_update": fm["per_cell_update"],
                 "kernel_ms_per_step": {k: v / prof_steps for k, v in kms.items()}}
+    if cfg["recon"] == "wenoz":
+        roofline["frac_per_face_count"] = face_frac
+        roofline["step_frac_per_face_count"] = face_step_frac
+        roofline["count_note"] = ("frac and step_frac count the WENO-Z indicators, tau5 and ratios once per cell, as the "
+                                  "method needs them; the *_per_face_count fractions take the oracle's face-by-face "
+                                  "count (those terms twice per cell)")
 
     # ---- end to end through the C-ABI with host buffers ----
     # Two contexts on two streams take the steps in turn: a step's host-to-device
@@ -527,7 +555,7 @@ def run_ours(args):
         c.get_conserved(out_host)
     torch.cuda.synchronize(dev)
     barrier()
-    e2e_steps = max(2, min(args.steps, 20))
+    e2e_steps = max(2, min(args.steps, 8 if big else 20))
     t0 = time.perf_counter()
     prev, done = None, None
     for s in range(e2e_steps):
@@ -567,6 +595,11 @@ def run_ours(args):
                            "dt": "CFL dt computed on the device every step", "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary()}
+        if world == 1 and not args.no_companions:
+            sim.close()
+            sim = None
+            line["batched_vs_plain"], line["adjoint_vs_plain"] = companions(
+                dev, stream, value, roofline["frac"], roofline["step_frac"], args.steps)
         if args.workload in PAPER_PER_GPU:
             line["paper_context"] = {"per_gpu_cell_updates_per_s": PAPER_PER_GPU[args.workload],
                                      "this_gpu_over_paper_gpu": {k: value / world / v
@@ -574,50 +607,44 @@ def run_ours(args):
                                      "note": "the paper's single-node 3D Orszag-Tang runs (704x704x352 per node of 4 "
                                              "GPUs, UCT-HLLD edge fields); context, not the target"}
         print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def run_ensemble(args):
+def measure_ensemble(dev, stream, steps, warmup, loop=True, clocks=None, barrier=lambda: None):
+    """The batched ensemble (256 2D Orszag-Tang runs of 64^2..512^2 in one
+    graph per step, autotuned segment lengths): `steps` timed steps after
+    `warmup`, the batched sweep on the FP64 roofline, and (loop=True) the same
+    runs as a loop of single-grid steps on the same stream, the plain step of
+    those grids.  Returns the measurements and the live batch."""
     import torch
     from paper_2511_20337_b300 import mhd
-
-    rank, world, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    _, variant, desc = WORKLOADS[args.workload]
+    _, variant, desc = WORKLOADS["ensemble2d-256"]
     cases = ensemble_cases(256)
     cfgs = [c for c, _ in cases]
     ncell = sum(cells_of(c) for c in cfgs)
-    stream = torch.cuda.Stream(device=dev)
     host = [{k: torch.from_numpy(v).pin_memory() for k, v in st.items()} for _, st in cases]
     h2d = sum(v.numel() * 8 for h in host for v in h.values())
     del cases
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
     bt = mhd.Batch(cfgs, stream=stream.cuda_stream)
     for r, h in enumerate(host):
         bt.set_conserved(r, h)
     seg = bt.autotune()
-    bt.step(args.warmup)
+    bt.step(warmup)
     torch.cuda.synchronize(dev)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     launches0 = bt.launches
-    with ClockSampler(local) as clk:
+    clk = clocks if clocks is not None else _NullClocks()
+    with clk:
         torch.cuda.synchronize(dev)
         barrier()
         e0.record(stream)
-        bt.step(args.steps)
+        bt.step(steps)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
@@ -626,11 +653,9 @@ def run_ensemble(args):
     rc, bad_run, bad = bt.status()
     if rc != 0:
         raise RuntimeError(f"device reported {rc} in run {bad_run} at cell {bad}")
-    t_max = job_time_ms(ms, world, dev)
-    value = job_rate(ncell * args.steps, world, t_max)
 
     # roofline of the batched sweep (events after each launch)
-    prof_steps = max(1, min(args.steps, 5))
+    prof_steps = max(1, min(steps, 5))
     kms, kcnt = bt.profile_steps(prof_steps)
     peak, peak_src, rates = fp64_peak(dev)
     probe = rates["dfma"]
@@ -652,20 +677,57 @@ def run_ensemble(args):
                 "step_frac": step_flops / (step_ms_prof * 1e-3) / 1e9 / peak,
                 "kernel_ms_per_step": {k: v / prof_steps for k, v in kms.items()}}
 
-    # the same runs as a loop of single-grid steps on the same stream
-    sims = [mhd.Sim(c, h, stream=stream.cuda_stream) for c, h in zip(cfgs, host)]
-    for sm in sims:
-        sm.advance(args.warmup)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for sm in sims:
-        sm.advance(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    loop_ms = e0.elapsed_time(e1)
-    for sm in sims:
-        sm.close()
-    del sims
+    loop_ms = None
+    if loop:   # the same runs as a loop of single-grid steps on the same stream
+        sims = [mhd.Sim(c, h, stream=stream.cuda_stream) for c, h in zip(cfgs, host)]
+        for sm in sims:
+            sm.advance(warmup)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for sm in sims:
+            sm.advance(steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        loop_ms = e0.elapsed_time(e1)
+        for sm in sims:
+            sm.close()
+        del sims
+    return {"bt": bt, "cfgs": cfgs, "host": host, "ncell": ncell, "h2d": h2d, "seg": seg, "ms": ms,
+            "launches": launches, "roofline": roofline, "loop_ms": loop_ms, "desc": desc, "clk": clk}
+
+
+class _NullClocks:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def summary(self):
+        return None
+
+
+def run_ensemble(args):
+    import torch
+    from paper_2511_20337_b300 import mhd
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    m = measure_ensemble(dev, stream, args.steps, args.warmup, clocks=ClockSampler(local), barrier=barrier)
+    bt, cfgs, host, ncell, h2d, seg, ms = m["bt"], m["cfgs"], m["host"], m["ncell"], m["h2d"], m["seg"], m["ms"]
+    t_max = job_time_ms(ms, world, dev)
+    value = job_rate(ncell * args.steps, world, t_max)
+    loop_ms = m["loop_ms"]
 
     # end to end: every run's state in from pinned host memory, one step, every
     # state out, all runs as one packed array (one copy and one scatter or
@@ -731,7 +793,7 @@ def run_ensemble(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": desc, "runs": len(cfgs), "cells": ncell,
+                "config": {"workload": m["desc"], "runs": len(cfgs), "cells": ncell,
                            "sizes": sorted(set(c["n"][0] for c in cfgs)),
                            "autotuned_seglen": {"small_runs": seg[0], "large_runs": seg[1]},
                            "l2": f"inputs larger than L2 (states {h2d / 1e9:.2f} GB)",
@@ -740,8 +802,8 @@ def run_ensemble(args):
                 "loop_of_single_grid_steps": {"value": ncell * args.steps / (loop_ms * 1e-3), "unit": UNIT,
                                               "ms_per_step": loop_ms / args.steps,
                                               "batched_speedup": loop_ms / ms},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary()}
+                "roofline": m["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": m["launches"],
+                "clocks": m["clk"].summary()}
         print(json.dumps(line), flush=True)
     bt.close()
     if world > 1:
@@ -773,43 +835,29 @@ def oracle_gradient_rate(cfg, st, nsteps, which="magnetic_energy", seconds_budge
     return 3 * cells_of(cfg) * nsteps * reps / el, el, reps
 
 
-def run_adjoint(args):
-    """A step is one gradient evaluation: ADJOINT_STEPS forward steps from the
+def measure_adjoint(dev, stream, workload, gradients, warmup, seglen=0, clocks=None, barrier=lambda: None):
+    """One gradient evaluation per step: ADJOINT_STEPS forward steps from the
     initial state with checkpoints, the block recomputes and the reverse pass.
-    Cell-updates count 3 per cell and time step (forward, recompute, reverse);
-    the phases are also reported separately."""
+    Times `gradients` evaluations after `warmup`, profiles the phases and the
+    reverse kernel classes, places the Riemann transpose and the gradient on
+    the FP64 roofline, and times the plain forward run of the same grid and
+    steps on the same GPU.  Returns the measurements and the live context."""
     import torch
     from paper_2511_20337_b300 import mhd
-
-    rank, world, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    gen, variant, desc = WORKLOADS[args.workload]
+    gen, variant, desc = WORKLOADS[workload]
     cfg, st = gen()
     ncell = cells_of(cfg)
     N, K = ADJOINT_STEPS, ADJOINT_CKPT
-    stream = torch.cuda.Stream(device=dev)
     host = {k: torch.from_numpy(v).pin_memory() for k, v in st.items()}
     devs = {k: v.to(dev) for k, v in host.items()}
-    h2d = sum(v.numel() * 8 for v in host.values())
-    grad_host = {k: torch.empty_like(host["rho"]).pin_memory() for k in ("rho", "vx", "vy", "vz")}
-    d2h = sum(v.numel() * 8 for v in grad_host.values())
     sim = mhd.Sim(cfg, devs, stream=stream.cuda_stream)
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    if args.seglen:
-        sim.set_seglen(args.seglen)
-        seg = args.seglen
+    if seglen:
+        sim.set_seglen(seglen)
+        seg = seglen
     else:
         seg = sim.autotune()
     _, dts = sim.adjoint(N, None, K)  # records the CFL steps, then frozen
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         sim.set_conserved(devs)
         sim.adjoint(N, dts, K)
     torch.cuda.synchronize(dev)
@@ -817,11 +865,12 @@ def run_adjoint(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     launches0 = sim.launches
-    with ClockSampler(local) as clk:
+    clk = clocks if clocks is not None else _NullClocks()
+    with clk:
         torch.cuda.synchronize(dev)
         barrier()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(gradients):
             sim.set_conserved(devs)
             J, _ = sim.adjoint(N, dts, K)
         e1.record(stream)
@@ -829,8 +878,6 @@ def run_adjoint(args):
         barrier()
     ms = e0.elapsed_time(e1)
     launches = sim.launches - launches0
-    t_max = job_time_ms(ms, world, dev)
-    value = job_rate(3 * ncell * N * args.steps, world, t_max)
 
     # phases and kernel classes (events on the library stream; syncs every reverse step)
     sim.set_conserved(devs)
@@ -842,7 +889,7 @@ def run_adjoint(args):
     riemann_launches = N * cfg["rk"] * nd
     riemann_ms = classes["adj_riemann"]
     achieved = am["riemann_per_launch"] * riemann_launches / (riemann_ms * 1e-3) / 1e9
-    eval_ms = t_max / args.steps
+    eval_ms = ms / gradients
     roofline = {"bound": "alu", "kernel": "adj_riemann_kernel (Riemann solver + flux difference transpose, per face)",
                 "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
                 "peak_source": peak_src, "probe_gflops": probe, "frac_of_probe": achieved / probe,
@@ -871,13 +918,45 @@ def run_adjoint(args):
     torch.cuda.synchronize(dev)
     plain_ms = e0.elapsed_time(e1)
     ref.close()
+    return {"sim": sim, "cfg": cfg, "host": host, "devs": devs, "dts": dts, "ncell": ncell, "seg": seg, "ms": ms,
+            "eval_ms": eval_ms, "J": J, "launches": launches, "roofline": roofline, "phases": phase_rates,
+            "plain_ms": plain_ms, "desc": desc, "clk": clk}
+
+
+def run_adjoint(args):
+    """A step is one gradient evaluation (measure_adjoint).  Cell-updates count
+    3 per cell and time step (forward, recompute, reverse); the phases are also
+    reported separately."""
+    import torch
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    m = measure_adjoint(dev, stream, args.workload, args.steps, args.warmup, args.seglen,
+                        clocks=ClockSampler(local), barrier=barrier)
+    sim, cfg, host, ncell, N, K = m["sim"], m["cfg"], m["host"], m["ncell"], ADJOINT_STEPS, ADJOINT_CKPT
+    t_max = job_time_ms(m["ms"], world, dev)
+    value = job_rate(3 * ncell * N * args.steps, world, t_max)
+    eval_ms = t_max / args.steps
+    h2d = sum(v.numel() * 8 for v in host.values())
+    grad_host = {k: torch.empty_like(host["rho"]).pin_memory() for k in ("rho", "vx", "vy", "vz")}
+    d2h = sum(v.numel() * 8 for v in grad_host.values())
 
     # end to end: state in from pinned host memory, gradient out to pinned host memory
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         sim.set_conserved(host)
-        sim.adjoint(N, dts, K)
+        sim.adjoint(N, m["dts"], K)
         sim.grad_prim(grad_host)
     el = time.perf_counter() - t0
     e2e = {"value": 3 * ncell * N * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -890,26 +969,69 @@ def run_adjoint(args):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{SAMPLES[args.workload][1]}: {reps} tape gradients in {sec:.1f} s, single thread"}
     if rank == 0:
+        plain_ms = m["plain_ms"]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": eval_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": desc, "grid": list(cfg["n"]), "cells": ncell, "time_steps": N,
-                           "checkpoint_every": K, "J": J, "autotuned_seglen": seg,
+                "config": {"workload": m["desc"], "grid": list(cfg["n"]), "cells": ncell, "time_steps": N,
+                           "checkpoint_every": K, "J": m["J"], "autotuned_seglen": m["seg"],
                            "step": "one gradient evaluation; 3 cell-updates per cell and time step "
                                    "(forward, recompute, reverse)",
                            "l2": "each gradient evaluation streams its checkpoints and stage states "
                                  f"({(N // K + K * cfg['rk'] + 1) * h2d / 1e6:.0f} MB) through HBM, larger than L2",
                            "dt": "CFL steps of the first run, then frozen", "parallelism": f"replicas x{world}"},
-                "phases": phase_rates,
+                "phases": m["phases"],
                 "plain_step": {"value": ncell * N / (plain_ms * 1e-3), "unit": UNIT, "ms_per_step": plain_ms / N,
                                "gradient_vs_plain_time": eval_ms / plain_ms},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary()}
+                "roofline": m["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": m["launches"],
+                "clocks": m["clk"].summary()}
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def companions(dev, stream, plain_value, plain_frac, plain_step_frac, steps):
+    """The batched and adjoint forms measured on the same GPU after the plain
+    step, compactly (no e2e, no CPU baseline), each with its own cell-updates/s
+    and roofline fraction and its ratio to the plain step: to the headline's
+    plain step, and to the plain step of its own grids (the loop of
+    single-grid steps of the same runs; the plain forward run of the same grid
+    and time steps)."""
+    import torch
+    e = measure_ensemble(dev, stream, max(3, min(steps, 20)), 3)
+    ens_value = e["ncell"] * max(3, min(steps, 20)) / (e["ms"] * 1e-3)
+    loop_value = e["ncell"] * max(3, min(steps, 20)) / (e["loop_ms"] * 1e-3)
+    batched = {"workload": e["desc"], "value": ens_value, "unit": UNIT, "steps": max(3, min(steps, 20)),
+               "ms_per_step": e["ms"] / max(3, min(steps, 20)), "cells": e["ncell"], "gpu_launches": e["launches"],
+               "frac": e["roofline"]["frac"], "step_frac": e["roofline"]["step_frac"],
+               "roofline_kernel": e["roofline"]["kernel"],
+               "plain_step_same_runs": {"value": loop_value, "unit": UNIT,
+                                        "what": "the same 256 runs as a loop of single-grid steps, same stream"},
+               "batched_over_plain_same_runs": ens_value / loop_value,
+               "value_over_headline": ens_value / plain_value, "frac_over_headline": e["roofline"]["frac"] / plain_frac,
+               "step_frac_over_headline": e["roofline"]["step_frac"] / plain_step_frac}
+    e["bt"].close()
+    del e
+    torch.cuda.synchronize(dev)
+    a = measure_adjoint(dev, stream, "adjoint2d-256", 2, 1)
+    N = ADJOINT_STEPS
+    adj_value = 3 * a["ncell"] * N / (a["eval_ms"] * 1e-3)
+    plain_grid = a["ncell"] * N / (a["plain_ms"] * 1e-3)
+    adjoint = {"workload": a["desc"], "value": adj_value, "unit": UNIT, "gradients": 2,
+               "ms_per_gradient": a["eval_ms"], "cell_updates_counted": "3 per cell and time step (forward, "
+                                                                        "recompute, reverse)",
+               "frac": a["roofline"]["frac"], "gradient_frac": a["roofline"]["gradient_frac"],
+               "roofline_kernel": a["roofline"]["kernel"], "gpu_launches": a["launches"],
+               "phases": a["phases"],
+               "plain_step_same_grid": {"value": plain_grid, "unit": UNIT, "ms_per_step": a["plain_ms"] / N,
+                                        "what": "the plain forward run of the same 256^2 grid and 400 steps"},
+               "gradient_over_plain_time": a["eval_ms"] / a["plain_ms"],
+               "value_over_headline": adj_value / plain_value,
+               "gradient_frac_over_headline_step_frac": a["roofline"]["gradient_frac"] / plain_step_frac}
+    a["sim"].close()
+    return batched, adjoint
 
 
 def ctypes_stream(stream):
@@ -922,7 +1044,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="turbulent3d-256", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="blast3d-512", choices=list(WORKLOADS))
+    ap.add_argument("--no-companions", action="store_true",
+                    help="single-grid workloads: skip the batched-ensemble and adjoint measurements that follow "
+                         "the plain step (batched_vs_plain, adjoint_vs_plain)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seglen", type=int, default=0,
