@@ -595,6 +595,11 @@ def run_ours(args):
                            "dt": "CFL dt computed on the device every step", "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary()}
+        if args.bricks:
+            parts = [int(x) for x in args.bricks.split("x")]
+            dom = measure_domain(cfg, devs, parts, args.steps, args.warmup, stream, seg)
+            dom["value_over_undivided"] = dom["value"] / value
+            line["decomposed"] = dom
         if world == 1 and not args.no_companions:
             sim.close()
             sim = None
@@ -612,6 +617,37 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def measure_domain(cfg, devs, parts, steps, warmup, stream, seglen=None):
+    """The same workload split into bricks (mhd_domain_*: a halo exchange per
+    RK stage, all bricks on this GPU): cell-updates/s over `steps` CFL steps
+    after `warmup`, and the bytes one exchange moves."""
+    import torch
+    from paper_2511_20337_b300 import mhd
+    d = mhd.Domain(cfg, parts, devs, stream=stream.cuda_stream)
+    if seglen:
+        d.set_seglen(seglen)
+    d.advance(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = d.launches
+    e0.record(stream)
+    d.advance(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rc, bad = d.status()
+    if rc != 0:
+        raise RuntimeError(f"device reported {rc} at cell {bad}")
+    out = {"bricks": list(parts), "value": cells_of(cfg) * steps / (ms * 1e-3), "unit": UNIT,
+           "ms_per_step": ms / steps, "steps": steps, "gpu_launches": d.launches - l0,
+           "halo_bytes_per_exchange": d.halo_bytes, "exchanges_per_step": cfg["rk"],
+           "what": "the same grid as bricks with a pack / device-copy / unpack halo exchange per RK stage, "
+                   "all bricks on this GPU; state, dt and time equal the undivided run's to the bit"}
+    d.close()
+    return out
 
 
 def measure_ensemble(dev, stream, steps, warmup, loop=True, clocks=None, barrier=lambda: None):
@@ -1048,6 +1084,9 @@ def main():
     ap.add_argument("--no-companions", action="store_true",
                     help="single-grid workloads: skip the batched-ensemble and adjoint measurements that follow "
                          "the plain step (batched_vs_plain, adjoint_vs_plain)")
+    ap.add_argument("--bricks", default="",
+                    help="single-grid workloads: also time the grid split into bricks, e.g. 2x2x2 (the halo "
+                         "exchange of the domain decomposition, all bricks on this GPU)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seglen", type=int, default=0,

@@ -44,6 +44,8 @@ extern "C" {
 #define MHD_ERR_TIMEOUT    -5   /* a bounded device-side wait gave up */
 #define MHD_ERR_STATE      -6   /* no state has been set on this context */
 #define MHD_ERR_TOO_LARGE  -7   /* grid needs more scratch than mhd_step_noalloc's fixed array */
+#define MHD_ERR_DIVB       -8   /* the div B monitor (mhd_set_divb_check) found max |div B| h / max |B_c|
+                                   above its tolerance */
 
 /* ---- options ---- */
 #define MHD_RECON_PLM     0     /* piecewise linear, minmod limiter */
@@ -93,6 +95,11 @@ typedef struct mhd_ctx mhd_ctx;   /* opaque; owns all device state of one grid *
 /* Create a context on the current CUDA device: validates cfg, allocates the
  * device state (three RK registers, primitives, stage increment, face
  * ingredients and edge fields; about 55 doubles per padded cell in 3D).
+ * The grid is the uniform Cartesian mesh of the finite-volume method of
+ * paper §2.2: cell averages of rho, m, E at cell centres x0 + (i + 1/2) dx
+ * and the staggered face field of constrained transport at the cell faces,
+ * with the ghost layers a stencil of cfg->recon needs (2, or 3 for
+ * WENO-Z / PPM).
  * *out receives the handle.  MHD_ERR_ARG on a bad configuration,
  * MHD_ERR_OOM if the device allocation fails.  Sync. */
 int mhd_create(const mhd_config* cfg, mhd_ctx** out);
@@ -132,13 +139,20 @@ int mhd_set_boundaries(mhd_ctx* ctx, const int bc[6]);
  * Computed on the device with IEEE operations in a fixed order.  Sync. */
 int mhd_cfl_dt(mhd_ctx* ctx, double* dt_out);
 
-/* Advance one time step of size dt (all RK stages).  Async; a non-positive
+/* Advance one time step of size dt: the RK stages of Eq. RK3 (SSP-RK3, or
+ * the two-stage SSP-RK2), each stage U' = combine(U^n, U^s, L(U^s)) with L the
+ * Delta t-scaled finite-volume increment of Eq. FV built from the
+ * reconstruction of Eq. reconstruct and the Riemann flux of §2.2, and the face
+ * field advanced by constrained transport with the UCT edge fields (§2.2, the
+ * paragraph before §3; §4.1 "UCT HLLD average").  Async; a non-positive
  * density or pressure is reported by the next sync call. */
 int mhd_step(mhd_ctx* ctx, double dt);
 
-/* Advance nsteps steps, each with its own CFL dt computed on the device from
- * the state at the start of that step (no host round trip).  The launch
- * sequence of a step is captured once in a CUDA graph and replayed.  Async. */
+/* Advance nsteps steps as mhd_step does, each with its own CFL dt (the
+ * reading of mhd_cfl_dt; the paper states no CFL condition) computed on the
+ * device from the state at the start of that step, with no host round trip.
+ * The launch sequence of a step is captured once in a CUDA graph and
+ * replayed.  Async. */
 int mhd_advance(mhd_ctx* ctx, int nsteps);
 
 /* Simulation time (sum of the dt of all steps since the last set).  Sync. */
@@ -158,6 +172,23 @@ int mhd_last_dt(mhd_ctx* ctx, double* dt_out);
  * (may be NULL) = the smallest flat interior index k*ny*nx + j*nx + i of a
  * cell whose recovered density or pressure was not positive.  Clears it. */
 int mhd_status(mhd_ctx* ctx, long long* bad_cell);
+
+/* div B monitor (CT only; MHD_ERR_ARG with GLM).  Constrained transport keeps
+ * the discrete divergence of the staggered face field at round-off (paper
+ * §2.2, the paragraph on the induction equation before §3):
+ *   div_c = sum_d (B_d at the upper face - B_d at the lower face) / dx_d
+ * per interior cell.  The monitor forms
+ *   rel = max_c |div_c| h / max_c |B_c|,   h = min_d dx_d,
+ * B_c the cell-centred field (mean of the two faces; 2D B_z the cell value).
+ * mhd_set_divb_check(ctx, tol): tol > 0 checks rel at the end of every later
+ * step (a few microseconds of device work per step, captured with the step);
+ * a step with rel > tol sets the status MHD_ERR_DIVB, reported by the next
+ * sync call with *bad_cell the flat index of the cell of largest |div| h
+ * (compared in single precision; ties go to the larger index).  tol = 0
+ * turns it off (the default).  Sync.
+ * mhd_divb(ctx, &rel): rel of the current state, without setting a status.  Sync. */
+int mhd_set_divb_check(mhd_ctx* ctx, double tol);
+int mhd_divb(mhd_ctx* ctx, double* rel_out);
 
 /* Event counters since the last state set (sync):
  *   *recon_fallbacks: cell reconstructions (per cell, direction and stage)
@@ -332,6 +363,116 @@ int mhd_adjoint_grad_conserved(mhd_ctx* ctx, int mem, double* const* gU, double*
  * arrays: grad_rho, grad_v[3]).  MHD_ERR_STATE before a successful run.  Sync. */
 int mhd_adjoint_grad_prim(mhd_ctx* ctx, int mem, double* grad_rho, double* const* grad_v);
 
+/* ---- domain decomposition ----
+ *
+ * One grid split into px x py x pz bricks (paper §3.4 "Multi GPU
+ * communication", Fig. par_ex: the domain is split between processes and, at
+ * every stage, the data each neighbour needs -- 8 neighbours in 2D, 26 in 3D,
+ * diagonal ones included -- is packed into device buffers, exchanged and
+ * unpacked into the ghost zones).  Each brick is a single-grid context on the
+ * current device; its ghost fill is replaced by
+ *   pack     (one kernel per brick: the boxes of its interior its neighbours
+ *             need, into its send buffer),
+ *   exchange (one device-to-device copy per brick and neighbour, from the
+ *             sender's send buffer into the receiver's receive buffer),
+ *   unpack   (one kernel per brick: its receive buffer into its ghost shell),
+ * followed by the outflow fill on the sides that lie on an outflow boundary
+ * of the whole grid.  Every ghost slot then holds the undivided grid's value,
+ * so the bricks advance exactly as the undivided grid does: the state after
+ * any number of steps, the CFL step (the least of the bricks' steps) and the
+ * time equal the undivided grid's to the bit.  All bricks run on the one
+ * device and on cfg->stream; this is the decomposition and the exchange of a
+ * multi-GPU run with the transfers made by local device copies.
+ *
+ * Brick layout: bricks are numbered x fastest over the brick grid; axis d of
+ * N cells splits into parts[d] spans, the first N % parts[d] of them one cell
+ * longer.  Constraints (MHD_ERR_ARG otherwise): constrained transport
+ * (divb = MHD_DIVB_CT), parts[d] >= 1 (1 on inactive axes), at least G + 1
+ * cells per brick on every active axis (G = 2 for PLM, 3 otherwise), at most
+ * 4096 bricks. */
+typedef struct mhd_domain mhd_domain;
+
+/* One box of a brick's halo exchange, in the brick's padded coordinates
+ * (cell index -G .. n+G per active axis, 0 on inactive ones):
+ *   peer    the neighbouring brick;
+ *   dir     its direction (-1, 0 or +1 per axis);
+ *   lo, ext first slot and slots per axis (ext = 1 on inactive axes);
+ *   offset  first slot of the box in the brick's send (receive) buffer; the
+ *           buffer holds, box after box, the 8 state fields of the box
+ *           field-major (field q of slot k at 8 offset + q slots_of_box + k),
+ *           slots x fastest.
+ * A send box (dir o) is the part of the brick's interior the neighbour in
+ * direction o needs: per axis o = +1: [n-G, n-1]; o = -1: [0, G]; o = 0:
+ * [0, n-1].  A receive box (dir o) is the ghost region in direction o:
+ * o = -1: [-G, -1]; o = +1: [n, n+G]; o = 0: [0, n-1] (the slot n+G of the
+ * upper layers is the last face of a face array).  The box a brick sends in
+ * direction o lands in the box its peer receives from direction -o; the two
+ * have the same extents.  Periodic axes wrap around the brick grid; across an
+ * outflow boundary of the whole grid there is no neighbour and no box. */
+typedef struct {
+  int peer;
+  int dir[3];
+  int lo[3];
+  int ext[3];
+  long long offset;
+} mhd_halo_box;
+
+/* Host-only index maps (no device work; usable without a GPU):
+ * mhd_domain_brick: the first global cell lo[3] and the cells n[3] of brick
+ *   `brick` (inactive axes: lo 0, n 1);
+ * mhd_domain_halo: the brick's send boxes (send != 0) or receive boxes
+ *   (send == 0) in direction order (x fastest over dir, all-zero skipped),
+ *   at most max_boxes of them (26 suffice), *nboxes their number. */
+int mhd_domain_brick(const mhd_config* cfg, const int parts[3], int brick, int lo[3], int n[3]);
+int mhd_domain_halo(const mhd_config* cfg, const int parts[3], int brick, int send, mhd_halo_box* boxes,
+                    int max_boxes, int* nboxes);
+
+/* Create the bricks (one context each, with the whole grid's dx) and the
+ * exchange buffers on the current device.  Sync. */
+int mhd_domain_create(const mhd_config* cfg, const int parts[3], mhd_domain** out);
+int mhd_domain_destroy(mhd_domain* d);
+
+/* The whole grid's state in the boundary layout of this file (host or device
+ * per mem), scattered to the bricks; resets the time and counters.  Async as
+ * mhd_set_conserved. */
+int mhd_domain_set_conserved(mhd_domain* d, int mem, const double* const* U, const double* const* B);
+
+/* Gather the whole grid's state (after an exchange, so a periodic axis's last
+ * face is a copy of the first).  Sync; returns the device status as
+ * mhd_domain_status. */
+int mhd_domain_get_conserved(mhd_domain* d, int mem, double* const* U, double* const* B);
+
+/* The CFL step of the whole grid (as mhd_cfl_dt), without advancing the time.  Sync. */
+int mhd_domain_cfl_dt(mhd_domain* d, double* dt_out);
+
+/* One step of size dt (async), or nsteps CFL steps with dt on the device,
+ * captured once in a CUDA graph and replayed (async). */
+int mhd_domain_step(mhd_domain* d, double dt);
+int mhd_domain_advance(mhd_domain* d, int nsteps);
+
+/* Simulation time of the whole grid.  Sync. */
+int mhd_domain_get_time(mhd_domain* d, double* t_out);
+
+/* First device-side error of any brick since the last call (as mhd_status),
+ * *bad_cell (may be NULL) the smallest flat index of the whole grid,
+ * k*ny*nx + j*nx + i, among the bricks' first bad cells.  Sync; clears. */
+int mhd_domain_status(mhd_domain* d, long long* bad_cell);
+
+/* Sums of the bricks' counters (as mhd_counters).  The pressure floors count
+ * interior cells, as on the undivided grid; the reconstruction fallbacks count
+ * every reconstruction a brick's sweeps made, and a brick also reconstructs
+ * the cells next to it in its halo, so that count can exceed the undivided
+ * grid's.  Sync. */
+int mhd_domain_counters(mhd_domain* d, long long* recon_fallbacks, long long* pressure_floors);
+
+/* Sweep segment length of every brick (as mhd_set_seglen).  Sync. */
+int mhd_domain_set_seglen(mhd_domain* d, int seglen);
+
+/* Kernel launches so far (graph replays count their kernels); bytes moved by
+ * one exchange (all bricks, all boxes). */
+long long mhd_domain_launch_count(const mhd_domain* d);
+long long mhd_domain_halo_bytes(const mhd_domain* d);
+
 /* ---- allocation-free variant ----
  *
  * For callers that must not allocate device memory: for example code whose
@@ -349,19 +490,27 @@ int mhd_adjoint_grad_prim(mhd_ctx* ctx, int mem, double* grad_rho, double* const
  * GPU loading the library holds until the process exits.  The call allocates
  * nothing (no cudaMalloc, no cudaFree, no allocating library routine).
  *
- * Limit: grids whose padded scratch (57 float64 fields over the padded box,
- * (nx+2G+1)(ny+2G+1)(nz+2G+1) cells with G = 2 for PLM and 3 otherwise; 2D:
- * no z padding) exceeds the array are rejected with MHD_ERR_TOO_LARGE before
- * any device work (about 266 x 266 in 2D or 36^3 in 3D with PLM).
+ * Limit: the padded scratch -- 57 float64 fields with the UCT-HLL edge fields,
+ * 60 with UCT-HLLD, each over the padded box (nx+2G+1)(ny+2G+1)(nz+2G+1)
+ * rounded up to 32 elements (G = 2 for PLM, 3 otherwise; 2D: no z padding),
+ * plus 256 bytes of device scalars -- must fit in the array.  Largest square
+ * and cubic grids that fit:
+ *                  2D PLM   2D WENO-Z/PPM   3D PLM   3D WENO-Z/PPM
+ *     UCT-HLL       266^2       264^2        36^3        34^3
+ *     UCT-HLLD      259^2       257^2        36^3        34^3
+ * Larger grids are rejected with MHD_ERR_TOO_LARGE before any device work.
  *
  * The array is shared by every call and keeps the last call's contents: the
  * call clears the part it uses before the step.  Calls that overlap on the GPU
  * (from several host threads or streams at once) race on it and must not be
  * made.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Work runs on cfg->stream (NULL = legacy default
- * stream); the call waits for it and returns MHD_ERR_UNPHYSICAL if a
- * non-positive density or pressure was met.  Sync. */
+ * (cudaGetSymbolAddress) with that device current; that may load the
+ * library's device code on that device, which is when the driver reserves the
+ * array -- make that first call before any stream capture and before any
+ * phase that must not see device memory change.  Work runs on cfg->stream
+ * (NULL = legacy default stream) and the call waits for it.  A step that met
+ * a non-positive density or pressure returns MHD_ERR_UNPHYSICAL and leaves the
+ * caller's arrays as they were.  Sync. */
 #define MHD_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double* const* B, double dt);
 

@@ -8,8 +8,17 @@
 //   reverse   for each block of k steps, last block first: recompute its
 //             steps from the checkpoint, keeping every stage input, then run
 //             the stage transposes backwards through the block.
-// Memory: ceil(n/k) + k*S + 1 states (S = RK stages) plus the scratch of the
-// transposes; work: two forward passes and one reverse pass.
+// The recompute of block b-1 runs on a second stream, with a context of its
+// own for the scratch of the forward kernels, while the transposes of block b
+// run on the context's stream: the block storage is double-buffered, and
+// events order each block's transposes after its recompute and each
+// recompute after the transposes that last read its buffers.  At a 256^2 grid
+// both are latency-bound chains of small kernels, so the device runs them
+// side by side.  (The profiling run keeps them in sequence, so that each
+// phase's events time only its own kernels.)
+// Memory: ceil(n/k) + 2(k*S + 1) states (S = RK stages), 2 k*S ingredient
+// sets, a second context's scratch, plus the scratch of the transposes; work:
+// two forward passes and one reverse pass.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -45,10 +54,17 @@ struct AdjointState {
   std::vector<double> dts;
   double J = 0.0;
   bool has_grad = false;
+  mhd_ctx* shadow = nullptr;    // the block recomputes' context (own stream and scratch)
+  cudaEvent_t ev_fwd = nullptr;           // forward pass done
+  cudaEvent_t ev_rec[2] = {nullptr, nullptr};  // recompute into buffer set i done
+  cudaEvent_t ev_rev[2] = {nullptr, nullptr};  // transposes reading buffer set i done
 };
 
 void adjoint_free(mhd_ctx* c) {
   if (!c || !c->adj) return;
+  if (c->adj->shadow) mhd_destroy(c->adj->shadow);
+  for (cudaEvent_t e : {c->adj->ev_fwd, c->adj->ev_rec[0], c->adj->ev_rec[1], c->adj->ev_rev[0], c->adj->ev_rev[1]})
+    if (e) cudaEventDestroy(e);
   cudaFree(c->adj->pool);
   cudaFree(c->adj->states);
   cudaFree(c->adj->ings);
@@ -85,7 +101,7 @@ FaceIngr ing_at(const AdjointState* a, int ndim, size_t idx) {
 int ensure_state(mhd_ctx* c, int nsteps, int k) {
   const int S = c->cfg.rk;
   const int nck = (nsteps + k - 1) / k;
-  const size_t need_states = (size_t)nck + (size_t)k * S + 1;
+  const size_t need_states = (size_t)nck + 2 * ((size_t)k * S + 1);  // checkpoints, two block buffer sets
   AdjointState* a = c->adj;
   if (!a) {
     a = new (std::nothrow) AdjointState();
@@ -112,6 +128,17 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
     for (int q = 0; q < 6; q++) a->T.q[q] = next();
     long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
     if (cudaMalloc(&a->Jcell, sizeof(double) * ncell) != cudaSuccess) { cudaGetLastError(); adjoint_free(c); return MHD_ERR_OOM; }
+    // the block recomputes' own context, on its own stream, and the events between the two streams
+    mhd_config sc = c->cfg;
+    sc.stream = nullptr;
+    int rc = mhd_create(&sc, &a->shadow);
+    if (rc) { adjoint_free(c); return rc; }
+    a->shadow->g = c->g;
+    a->shadow->seglen = c->seglen;
+    bool ok = true;
+    for (cudaEvent_t* e : {&a->ev_fwd, &a->ev_rec[0], &a->ev_rec[1], &a->ev_rev[0], &a->ev_rev[1]})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { adjoint_free(c); return MHD_ERR_CUDA; }
   }
   if (a->state_count < need_states) {
     cudaFree(a->states);
@@ -123,7 +150,7 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
     }
     a->state_count = need_states;
   }
-  const size_t need_ings = (size_t)k * S;
+  const size_t need_ings = 2 * (size_t)k * S;
   if (a->ing_count < need_ings) {
     cudaFree(a->ings);
     a->ings = nullptr;
@@ -197,7 +224,7 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const FaceIngr& ING, const F8& 
   // ghost cells need no fill: the block recompute ran the forward stage on
   // Xs, whose ghost fill wrote them in place (periodic, so idempotent), and
   // its UCT ingredients ING were kept then too.
-  prim(c, Xs, false);
+  prim(c, Xs, false, s > 0);  // the primitives the forward stage s used
   double c0, c1, cL;
   stage_coeffs(c->cfg.rk, s, c0, c1, cL);
   const long long edges = edge_work<NDIM>(g);
@@ -353,32 +380,39 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
   rc = seed(c, functional);
   if (rc) return rc;
 
-  // reverse pass, one checkpoint block at a time
+  // reverse pass, one checkpoint block at a time, last block first
   F8 Ain = a->A[3];
-  for (int b = a->nck - 1; b >= 0; b--) {
+  const size_t base = (size_t)a->nck;  // the two block buffer sets follow the checkpoints
+  const size_t set_states = (size_t)k * S + 1, set_ings = (size_t)k * S;
+  auto X = [&](int set, int n0, int n, int st) {
+    return state_at(a, base + set * set_states + (size_t)(n - n0) * S + st);
+  };
+  auto ING = [&](int set, int n0, int n, int st) {
+    return ing_at(a, g.ndim, set * set_ings + (size_t)(n - n0) * S + st);
+  };
+  // block b's stage inputs and UCT ingredients into buffer set `set`,
+  // recomputed from its checkpoint by context r on r's stream
+  auto recompute = [&](mhd_ctx* r, int b, int set) -> int {
     const int n0 = b * k, n1 = (n0 + k < nsteps) ? n0 + k : nsteps;
-    const size_t base = (size_t)a->nck;  // block stage inputs follow the checkpoints
-    auto X = [&](int n, int s) { return state_at(a, base + (size_t)(n - n0) * S + s); };
-    if (prof) CK(cudaEventRecord(prof->e0, c->stream));
-    rc = copy_state(c, X(n0, 0), state_at(a, b));
-    if (rc) return rc;
+    CK(cudaMemcpyAsync(X(set, n0, n0, 0).q[0], state_at(a, b).q[0], 8 * a->fe * sizeof(double),
+                       cudaMemcpyDeviceToDevice, r->stream));
     for (int n = n0; n < n1; n++) {
-      set_dt_only_kernel<<<1, 1, 0, c->stream>>>(c->sc, a->dts[n]);
-      c->launches++;
-      for (int s = 0; s < S; s++) {
-        F8 out = s + 1 < S ? X(n, s + 1) : X(n + 1, 0);
-        run_stage_regs(c, s, X(n, 0), X(n, s), out, false);
+      set_dt_only_kernel<<<1, 1, 0, r->stream>>>(r->sc, a->dts[n]);
+      r->launches++;
+      for (int st = 0; st < S; st++) {
+        F8 out = st + 1 < S ? X(set, n0, n, st + 1) : X(set, n0, n + 1, 0);
+        run_stage_regs(r, st, X(set, n0, n, 0), X(set, n0, n, st), out, false);
         // keep the stage's UCT ingredients (the context's are contiguous, direction-major)
-        const FaceIngr keep = ing_at(a, g.ndim, (size_t)(n - n0) * S + s);
-        CK(cudaMemcpyAsync(keep.a[0][0], c->ING.a[0][0], (size_t)5 * g.ndim * a->fe * sizeof(double),
-                           cudaMemcpyDeviceToDevice, c->stream));
+        const FaceIngr keep = ING(set, n0, n, st);
+        CK(cudaMemcpyAsync(keep.a[0][0], r->ING.a[0][0], (size_t)5 * g.ndim * a->fe * sizeof(double),
+                           cudaMemcpyDeviceToDevice, r->stream));
       }
     }
-    if (prof) {
-      CK(cudaEventRecord(prof->e1, c->stream));
-      CK(cudaEventSynchronize(prof->e1));
-      prof->phase_ms[1] += elapsed(prof->e0, prof->e1);
-    }
+    return MHD_OK;
+  };
+  // the stage transposes of block b, backwards, reading buffer set `set`
+  auto reverse = [&](int b, int set) -> int {
+    const int n0 = b * k, n1 = (n0 + k < nsteps) ? n0 + k : nsteps;
     for (int n = n1 - 1; n >= n0; n--) {
       const double dt = a->dts[n];
       if (prof) {
@@ -386,13 +420,13 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
         c->prof_n = 0;
         prof_mark(c, -1);
       }
-      for (int s = 0; s < S; s++) CK(cudaMemsetAsync(a->A[s].q[0], 0, 8 * a->fe * sizeof(double), c->stream));
-      for (int s = S - 1; s >= 0; s--) {
-        const F8& Aout = s == S - 1 ? Ain : a->A[s + 1];
-        rc = adj_stage(c, s, X(n, s), ing_at(a, g.ndim, (size_t)(n - n0) * S + s), Aout, a->A[0], a->A[s], dt);
-        if (rc) {
+      for (int st = 0; st < S; st++) CK(cudaMemsetAsync(a->A[st].q[0], 0, 8 * a->fe * sizeof(double), c->stream));
+      for (int st = S - 1; st >= 0; st--) {
+        const F8& Aout = st == S - 1 ? Ain : a->A[st + 1];
+        int rc2 = adj_stage(c, st, X(set, n0, n, st), ING(set, n0, n, st), Aout, a->A[0], a->A[st], dt);
+        if (rc2) {
           c->prof_on = false;
-          return rc;
+          return rc2;
         }
       }
       if (prof) {
@@ -409,6 +443,45 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
       Ain = a->A[0];
       a->A[0] = t;
     }
+    return MHD_OK;
+  };
+  if (prof) {  // in sequence on the context, each phase timed on its own
+    for (int b = a->nck - 1; b >= 0; b--) {
+      CK(cudaEventRecord(prof->e0, c->stream));
+      rc = recompute(c, b, 0);
+      if (rc) return rc;
+      CK(cudaEventRecord(prof->e1, c->stream));
+      CK(cudaEventSynchronize(prof->e1));
+      prof->phase_ms[1] += elapsed(prof->e0, prof->e1);
+      rc = reverse(b, 0);
+      if (rc) return rc;
+    }
+  } else {  // block b - 1 recomputed on the second context while block b is transposed
+    mhd_ctx* r = a->shadow;
+    const long long l0 = r->launches;
+    CK(cudaEventRecord(a->ev_fwd, c->stream));
+    CK(cudaStreamWaitEvent(r->stream, a->ev_fwd, 0));
+    const int last = a->nck - 1;
+    rc = recompute(r, last, last & 1);
+    if (rc) return rc;
+    CK(cudaEventRecord(a->ev_rec[last & 1], r->stream));
+    for (int b = last; b >= 0; b--) {
+      const int set = b & 1;
+      if (b > 0) {
+        const int other = (b - 1) & 1;
+        // its buffers were last read by the transposes of block b + 1
+        if (b < last) CK(cudaStreamWaitEvent(r->stream, a->ev_rev[other], 0));
+        rc = recompute(r, b - 1, other);
+        if (rc) return rc;
+        CK(cudaEventRecord(a->ev_rec[other], r->stream));
+      }
+      CK(cudaStreamWaitEvent(c->stream, a->ev_rec[set], 0));
+      rc = reverse(b, set);
+      if (rc) return rc;
+      CK(cudaEventRecord(a->ev_rev[set], c->stream));
+    }
+    CK(cudaStreamSynchronize(r->stream));
+    c->launches += r->launches - l0;
   }
   a->A[3] = Ain;  // holds dJ/dU^0
   CK(cudaGetLastError());

@@ -57,16 +57,18 @@ void ghost_fill(mhd_ctx* c, const F8& S) {
     }
 }
 
-void prim(mhd_ctx* c, const F8& S, bool cfl) {
+void prim(mhd_ctx* c, const F8& S, bool cfl, bool fast) {
   const Grid& g = c->g;
   long long work = (long long)(g.n[0] + 2 * g.G) * (g.n[1] + 2 * g.G) * (g.ndim == 3 ? g.n[2] + 2 * g.G : 1);
   int nb = blocks_for(work, 256);
   if (g.ndim == 2) {
-    if (cfl) prim_kernel<2, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
-    else prim_kernel<2, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
+    if (cfl) prim_kernel<2, true, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
+    else if (fast) prim_kernel<2, false, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
+    else prim_kernel<2, false, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
   } else {
-    if (cfl) prim_kernel<3, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
-    else prim_kernel<3, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
+    if (cfl) prim_kernel<3, true, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
+    else if (fast) prim_kernel<3, false, true><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
+    else prim_kernel<3, false, false><<<nb, 256, 0, c->stream>>>(g, S, c->P, c->sc, c->lam);
   }
   c->launches++;
   prof_mark(c, MHD_KCLASS_PRIM);
@@ -210,7 +212,7 @@ int stage_mode(int rk, int s) {
 
 void run_stage_regs(mhd_ctx* c, int s, const F8& U0, const F8& Us, const F8& Out, bool cfl) {
   ghost_fill(c, Us);
-  prim(c, Us, cfl);
+  prim(c, Us, cfl, s > 0);
   sweeps(c, Us);
   emf(c, Us);
   ct_rk(c, U0, Us, Out, stage_mode(c->cfg.rk, s));
@@ -302,15 +304,26 @@ void run_stage(mhd_ctx* c, int s, bool cfl) {
   run_stage_regs(c, s, c->U[0], Us, Out, cfl);
 }
 
+void divb_check(mhd_ctx* c, double tol) {
+  const Grid& g = c->g;
+  const long long cells = (long long)g.n[0] * g.n[1] * g.n[2];
+  if (g.ndim == 2) divb_kernel<2><<<blocks_for(cells, 256), 256, 0, c->stream>>>(g, c->U[0], c->sc);
+  else divb_kernel<3><<<blocks_for(cells, 256), 256, 0, c->stream>>>(g, c->U[0], c->sc);
+  divb_finish_kernel<<<1, 1, 0, c->stream>>>(c->sc, tol);
+  c->launches += 2;
+  prof_mark(c, MHD_KCLASS_OTHER);
+}
+
 void run_step(mhd_ctx* c, bool device_dt) {
   for (int s = 0; s < c->cfg.rk; s++) run_stage(c, s, device_dt && s == 0);
+  if (c->divb_tol > 0.0) divb_check(c, c->divb_tol);
 }
 
 }  // namespace mhd
 
 // Default sweep segment length: each segment repeats one face and one
 // reconstruction at its end, so long segments waste less, while short ones
-// give more threads.  Take the longest (2..64) that still leaves about eight
+// give more threads.  Take the longest (2..128) that still leaves about eight
 // waves of 384-thread SM loads in the sweep with the fewest faces.
 static long long faces_per_thread_target(const Grid& g) {
   int dev = 0, sms = 148;
@@ -327,7 +340,7 @@ static long long faces_per_thread_target(const Grid& g) {
 }
 static int default_seglen(const Grid& g) {
   const long long per_thread = faces_per_thread_target(g);
-  return (int)(per_thread < 2 ? 2 : (per_thread > 64 ? 64 : per_thread));
+  return (int)(per_thread < 2 ? 2 : (per_thread > 128 ? 128 : per_thread));
 }
 // Sweeps side by side when even segments of 2 faces leave fewer than about
 // eight waves of threads in one sweep (CT only).
@@ -345,6 +358,7 @@ const char* mhd_strerror(int code) {
     case MHD_ERR_TIMEOUT: return "device-side wait timed out";
     case MHD_ERR_STATE: return "no state set";
     case MHD_ERR_TOO_LARGE: return "grid exceeds the fixed scratch of mhd_step_noalloc";
+    case MHD_ERR_DIVB: return "discrete div B above the monitor's tolerance";
     default: return "unknown error";
   }
 }
@@ -640,6 +654,33 @@ static __global__ void set_time_kernel(DevScalars* sc, double t) { sc->time = t;
 
 extern "C" {
 
+int mhd_set_divb_check(mhd_ctx* c, double tol) {
+  if (!c || !(tol >= 0.0) || !std::isfinite(tol) || c->g.glm) return MHD_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  c->divb_tol = tol;
+  if (c->graph_ready) {  // the captured step changes
+    cudaGraphExecDestroy(c->graph);
+    c->graph_ready = false;
+  }
+  return MHD_OK;
+}
+
+int mhd_divb(mhd_ctx* c, double* rel_out) {
+  if (!c || !rel_out || c->g.glm) return MHD_ERR_ARG;
+  if (!c->has_state) return MHD_ERR_STATE;
+  ghost_fill(c, c->U[0]);
+  divb_check(c, 0.0);
+  CK(cudaGetLastError());
+  DevScalars h;
+  CK(copy_sync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  *rel_out = h.divb_rel;
+  return MHD_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
 int mhd_set_time(mhd_ctx* c, double t) {
   if (!c || !(t == t)) return MHD_ERR_ARG;
   set_time_kernel<<<1, 1, 0, c->stream>>>(c->sc, t);
@@ -718,7 +759,7 @@ int mhd_autotune(mhd_ctx* c, int* seglen_out) {
   // longest pencil into 4..12 equal segments: the segment count sets how many
   // waves of blocks a sweep takes and how short its last segment is
   int cand[32], ncand = 0;
-  for (int s : {2, 4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 64}) cand[ncand++] = s;
+  for (int s : {2, 4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 64, 96, 128}) cand[ncand++] = s;
   for (int k = 4; k <= 12; k++) cand[ncand++] = (longest + k - 1) / k;
   std::sort(cand, cand + ncand);
   ncand = (int)(std::unique(cand, cand + ncand) - cand);
@@ -988,7 +1029,7 @@ int mhd_probe_cfl_rate(int ndim, double gamma, const double* dx, int n, const do
 namespace {
 
 constexpr size_t kNoAllocDoubles = MHD_NOALLOC_SCRATCH_BYTES / sizeof(double);
-constexpr int kNoAllocFields = 3 * 8 + 8 + 6 + 15 + 3 + 1;  // same carve-up as mhd_create (CT, UCT-HLL)
+constexpr int kNoAllocFields = 3 * 8 + 8 + 6 + 15 + 3 + 1;  // mhd_create's carve-up (CT, UCT-HLL); +3 for UCT-HLLD
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
@@ -1069,15 +1110,18 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   set_dt_kernel<<<1, 1, 0, c.stream>>>(c.sc, dt);
   run_step(&c, false);
   ghost_fill(&c, c.U[0]);  // the duplicate last face of periodic axes
+  CK(cudaGetLastError());
+  // a step that met a non-positive density or pressure leaves the caller's
+  // arrays as they were: the status is read before anything is copied back
+  DevScalars h;
+  CK(copy_sync(&h, c.sc, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
+  if (h.status) return h.status;
   for (int q = 0; q < 8; q++) {
     int e[3];
     slot_extents(g, q, e);
     rc = copy_field(c.g, c.stream, c.U[0].q[q], nullptr, q < 5 ? U[q] : B[q - 5], e, false);
     if (rc) return rc;
   }
-  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c.stream));
-  DevScalars h;
-  CK(copy_sync(&h, c.sc, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
-  return h.status ? h.status : MHD_OK;
+  return MHD_OK;
 }

@@ -48,13 +48,18 @@ struct mhd_ctx {
   cudaStream_t aux[2];
   cudaEvent_t ev_fork, ev_join[2];
   mhd::L6 D[2];
+  // div B monitor at the end of every step (CT): 0 = off, else the tolerance
+  // on max |div B| h / max |B_c| above which a step reports MHD_ERR_DIVB
+  double divb_tol;
 };
 
 namespace mhd {
 
 void prof_mark(mhd_ctx* c, int cls);
 void ghost_fill(mhd_ctx* c, const F8& S);
-void prim(mhd_ctx* c, const F8& S, bool cfl);        // primitives of S into c->P (+ CFL dt)
+// primitives of S into c->P (+ CFL dt); fast: c2p_fast (the stages after the
+// first, whose primitives decide nothing that must match the oracle bitwise)
+void prim(mhd_ctx* c, const F8& S, bool cfl, bool fast = false);
 void sweeps(mhd_ctx* c, const F8& S);                // all directions: c->L and c->ING
 void emf(mhd_ctx* c, const F8& S);                   // edge fields into c->E
 void ct_rk(mhd_ctx* c, const F8& U0, const F8& Us, const F8& Out, int mode);
@@ -63,6 +68,7 @@ int stage_mode(int rk, int s);                       // COMB_* of stage s
 void run_stage_regs(mhd_ctx* c, int s, const F8& U0, const F8& Us, const F8& Out, bool cfl);
 void run_stage(mhd_ctx* c, int s, bool cfl);         // on the context's registers
 void run_step(mhd_ctx* c, bool device_dt);
+void divb_check(mhd_ctx* c, double tol);            // the div B monitor on U[0] (tol 0: measure only)
 void adjoint_free(mhd_ctx* c);                       // defined in mhd_adjoint.cu
 bool split_now(const mhd_ctx* c);                    // sweeps side by side in this launch sequence
 

@@ -106,7 +106,7 @@ __device__ __forceinline__ D3 fsqrt(const D3& x) {
   for (int k = 0; k < KT; k++) r.d[k] = h * x.d[k];
   return r;
 }
-__device__ __forceinline__ D3 fsqrt0(const D3& x) { return gt0(x.v) ? fsqrt(x) : D3(0.0); }
+__device__ __forceinline__ D3 fsqrt0(const D3& x) { return bits(x.v) >= kMinNormalBits ? fsqrt(x) : D3(0.0); }
 __device__ __forceinline__ D3 frsqrt(const D3& x) {
   D3 r;
   double y = frsqrt(x.v);

@@ -58,6 +58,9 @@ struct DevScalars {                     // small device-side scalars of one cont
   unsigned long long fallbacks;         // first-order reconstruction fallbacks
   unsigned long long floors;            // interior pressures raised to the floor
   unsigned long long lapx_bits;         // max of the near-IEEE CFL rates (candidate search)
+  unsigned long long divb_key;          // div B check: float bits of max |div B| h (high) and its cell (low)
+  unsigned long long bmax_bits;         // div B check: max |B_c|^2 over interior cells (bits)
+  double divb_rel;                      // div B check: the last max |div B| h / max |B_c|
 };
 
 // ---------------------------------------------------------------------------
@@ -151,8 +154,11 @@ static __global__ void ghost_shell_kernel(Grid g, F8 S) {
 }
 
 // Outflow pass along axis d, part 1: zero-gradient copies of every slot except
-// the normal face field (d-index -1..-G from 0; n..n+G from n-1).
-__device__ __forceinline__ void ghost_outflow_copy_item(const Grid& g, const F8& S, int d, long long id) {
+// the normal face field (d-index -1..-G from 0; n..n+G from n-1).  sides
+// selects the low (bit 0) and high (bit 1) side; a brick of a decomposed grid
+// has an outflow boundary on one side of an axis only.
+__device__ __forceinline__ void ghost_outflow_copy_item(const Grid& g, const F8& S, int d, long long id,
+                                                        int sides = 3) {
   int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   int e1 = g.hi(t1) - g.lo(t1) + 1;
   int nl = 2 * g.G + 1;
@@ -162,6 +168,7 @@ __device__ __forceinline__ void ghost_outflow_copy_item(const Grid& g, const F8&
   int a = (int)(r % e1) + g.lo(t1);
   int b = (int)(r / e1) + g.lo(t2);
   int gi = l < g.G ? l - g.G : g.n[d] + (l - g.G);
+  if (!(sides & (gi < 0 ? 1 : 2))) return;
   int x[3];
   x[d] = gi;
   x[t1] = a;
@@ -188,7 +195,8 @@ __host__ __device__ __forceinline__ long long ghost_rows_work(const Grid& g, int
   int e2 = g.hi(t2) - g.lo(t2) + (t2 < g.ndim ? 0 : 1);
   return (long long)e1 * e2;
 }
-__device__ __forceinline__ void ghost_outflow_normal_item(const Grid& g, const F8& S, int d, long long id) {
+__device__ __forceinline__ void ghost_outflow_normal_item(const Grid& g, const F8& S, int d, long long id,
+                                                          int sides = 3) {
   int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   int e1 = g.hi(t1) - g.lo(t1) + (t1 < g.ndim ? 0 : 1);
   double* Bn = S.q[5 + d];
@@ -216,12 +224,12 @@ __device__ __forceinline__ void ghost_outflow_normal_item(const Grid& g, const F
   int x[3];
   x[t1] = a;
   x[t2] = b;
-  for (int m = 1; m <= g.G; m++) {
+  for (int m = 1; m <= g.G && (sides & 1); m++) {
     x[d] = -m;
     int c = g.at(x[0], x[1], x[2]);
     Bn[c] = a_(Bn[c + g.stride(d)], m_(g.dx[d], divT(-m)));
   }
-  for (int m = 0; m < g.G; m++) {
+  for (int m = 0; m < g.G && (sides & 2); m++) {
     int cell = g.n[d] + m;
     x[d] = cell;
     int c = g.at(x[0], x[1], x[2]);
@@ -246,8 +254,11 @@ __host__ __device__ __forceinline__ long long prim_work(const Grid& g) {
   return (long long)(g.n[0] + 2 * g.G) * (g.n[1] + 2 * g.G) * (NDIM == 3 ? g.n[2] + 2 * g.G : 1);
 }
 // One padded cell: primitives, floor, status; returns its CFL rate (interior
-// cells, CFL pass) or 0.
-template <int NDIM, bool CFL>
+// cells, CFL pass) or 0.  FAST: c2p_fast, with c2p_ieee's pressure wherever
+// the floor or positivity test is within c2p_fast's error bound (the passes
+// after the CFL pass; the CFL pass keeps c2p_ieee, whose primitives the exact
+// CFL decision reads).
+template <int NDIM, bool CFL, bool FAST = false>
 __device__ __forceinline__ double prim_item(const Grid& g, const F8& S, const F8& P, DevScalars* sc, long long id) {
   const int nxp = g.n[0] + 2 * g.G, nyp = g.n[1] + 2 * g.G;
   int i = (int)(id % nxp) - g.G;
@@ -258,7 +269,15 @@ __device__ __forceinline__ double prim_item(const Grid& g, const F8& S, const F8
   double bx = m_(0.5, a_(S.q[5][c], S.q[5][c + 1]));
   double by = m_(0.5, a_(S.q[6][c], S.q[6][c + g.sy]));
   double bz = NDIM == 3 ? m_(0.5, a_(S.q[7][c], S.q[7][c + g.sz])) : S.q[7][c];
-  Prim8 V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1);
+  Prim8 V;
+  if (FAST) {
+    double pb;
+    V = c2p_fast(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1, pb);
+    if (lt_pos(dabs(fsub(V.p, g.p_floor)), pb) || lt_pos(dabs(V.p), pb))
+      V.p = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1).p;
+  } else {
+    V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1);
+  }
   bool interior = i >= 0 && i < g.n[0] && j >= 0 && j < g.n[1] && k >= 0 && k < g.n[2];
   if (V.p < g.p_floor) {  // primitives only; the conserved energy is not changed
     V.p = g.p_floor;
@@ -353,16 +372,17 @@ __device__ __forceinline__ double cfl_rate_ieee(const Grid& g, const Prim8& V) {
   if (NDIM == 3) lam = a_(lam, m_(a_(dabs(V.vz), fast_speed_ieee(V.rho, V.p, B2, V.bz, g.gamma)), g.idx[2]));
   return lam;
 }
-// Primitive pass of the single grid; with CFL, the near-IEEE rate of every
+// Primitive pass of the single grid (FAST: c2p_fast, for the stages after the
+// first); with CFL, the near-IEEE rate of every
 // interior cell goes to lam_near and its maximum to sc->lapx_bits (the
 // IEEE decision follows in cfl_exact_kernel).
-template <int NDIM, bool CFL>
+template <int NDIM, bool CFL, bool FAST>
 static __global__ void __launch_bounds__(256) prim_kernel(Grid g, F8 S, F8 P, DevScalars* sc, double* lam_near) {
   const long long total = prim_work<NDIM>(g);
   double lam_max = 0.0;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
-    prim_item<NDIM, false>(g, S, P, sc, id);
+    prim_item<NDIM, false, FAST>(g, S, P, sc, id);
     if (CFL) {
       const int nxp = g.n[0] + 2 * g.G, nyp = g.n[1] + 2 * g.G;
       int i = (int)(id % nxp) - g.G;
@@ -412,6 +432,75 @@ static __global__ void __launch_bounds__(256) cfl_exact_kernel(Grid g, F8 P, con
     }
   }
   cfl_block_finish(lam_max, sc, g.cfl, gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// div B monitor (constrained transport keeps the discrete divergence of the
+// face field at round-off, paper §2.2): per interior cell
+//   div = sum_d (B_d(face +) - B_d(face -)) / dx_d,
+// the largest |div| h (h = min dx) with its cell, and the largest |B_c|^2 of
+// the cell-centred field (2D: B_z the cell value).  divb_finish_kernel forms
+// rel = max |div| h / max |B_c| and, when rel > tol (tol > 0), reports
+// MHD_ERR_DIVB with the cell of the largest |div| h (its value taken in
+// single precision for the key; ties go to the larger index).
+// ---------------------------------------------------------------------------
+template <int NDIM>
+static __global__ void __launch_bounds__(256) divb_kernel(Grid g, F8 S, DevScalars* sc) {
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  const double h = NDIM == 3 ? fmin(g.dx[0], fmin(g.dx[1], g.dx[2])) : fmin(g.dx[0], g.dx[1]);
+  unsigned long long key = 0ull, b2max = 0ull;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % g.n[0]);
+    const long long r = id / g.n[0];
+    const int j = (int)(r % g.n[1]);
+    const int k = (int)(r / g.n[1]);
+    const int c = g.at(i, j, k);
+    // the upper face of the last cell of a periodic axis is face 0 (its ghost
+    // copy is refreshed only by the next stage's fill)
+    const int ux = (i + 1 == g.n[0] && g.periodic[0]) ? c - i : c + 1;
+    const int uy = (j + 1 == g.n[1] && g.periodic[1]) ? c - j * g.sy : c + g.sy;
+    const double bxl = S.q[5][c], bxr = S.q[5][ux], byl = S.q[6][c], byr = S.q[6][uy];
+    double div = (bxr - bxl) * g.idx[0] + (byr - byl) * g.idx[1];
+    double bz = S.q[7][c];
+    if (NDIM == 3) {
+      const int uz = (k + 1 == g.n[2] && g.periodic[2]) ? c - k * g.sz : c + g.sz;
+      const double bzr = S.q[7][uz];
+      div += (bzr - bz) * g.idx[2];
+      bz = 0.5 * (bz + bzr);
+    }
+    const double bx = 0.5 * (bxl + bxr), by = 0.5 * (byl + byr);
+    const double b2 = bx * bx + by * by + bz * bz;
+    const float v = (float)(fabs(div) * h);
+    const unsigned long long kk = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)id;
+    key = kk > key ? kk : key;
+    const unsigned long long bb = (unsigned long long)__double_as_longlong(b2);
+    b2max = bb > b2max ? bb : b2max;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, b2max, o);
+    key = k2 > key ? k2 : key;
+    b2max = b2 > b2max ? b2 : b2max;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&sc->divb_key, key);
+    atomicMax(&sc->bmax_bits, b2max);
+  }
+}
+static __global__ void divb_finish_kernel(DevScalars* sc, double tol) {
+  const unsigned long long key = sc->divb_key;
+  const double b2 = __longlong_as_double((long long)sc->bmax_bits);
+  const double v = (double)__uint_as_float((unsigned int)(key >> 32));
+  const double rel = b2 > 0.0 ? v / sqrt(b2) : v;
+  sc->divb_rel = rel;
+  if (tol > 0.0 && rel > tol && sc->status == 0) {
+    sc->status = -8;  // MHD_ERR_DIVB
+    sc->bad_cell = (long long)(key & 0xffffffffull);
+  }
+  sc->divb_key = 0ull;
+  sc->bmax_bits = 0ull;
 }
 
 // Set the step size from the host value (mhd_step) and add it to the time.
@@ -511,14 +600,11 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
 #pragma unroll
     for (int v = 0; v < 7; v++) dl[v] = fsub(win[v][1], win[v][0]);
   }
-  // WENO-Z: the curvatures of the stencils centred on the window's cells 1 and 2
-  Curv cv[7][2];
+  // WENO-Z: what consecutive cells share of the indicators (WzCarry)
+  WzCarry cv[7];
   if (RECON == RECON_WENOZ) {
 #pragma unroll
-    for (int v = 0; v < 7; v++) {
-      cv[v][0] = curv(win[v][0], win[v][1], win[v][2]);
-      cv[v][1] = curv(win[v][1], win[v][2], win[v][3]);
-    }
+    for (int v = 0; v < 7; v++) cv[v] = wenoz_start(win[v][0], win[v][1], win[v][2], win[v][3]);
   }
   auto reconstruct = [&](double plus[7], double minus[7], bool count) {
 #pragma unroll
@@ -529,10 +615,7 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
         dl[v] = dr;
       }
       else if (RECON == RECON_WENOZ) {
-        Curv c2;
-        recon_wenoz_c(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], cv[v][0], cv[v][1], c2, plus[v], minus[v]);
-        cv[v][0] = cv[v][1];
-        cv[v][1] = c2;
+        recon_wenoz_m(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], cv[v], plus[v], minus[v]);
       }
       else recon_ppm(win[v][0], win[v][1], win[v][2], win[v][3], win[v][4], plus[v], minus[v]);
     }
@@ -988,7 +1071,7 @@ static __global__ void __launch_bounds__(256) batch_prim_kernel(const RunDev* __
   const RunDev& R = runs[r];
   const long long id = block_local_id(blk0, r);
   double lam = 0.0;
-  if (id < prim_work<NDIM>(R.g)) lam = prim_item<NDIM, CFL>(R.g, R.U[reg], R.P, R.sc, id);
+  if (id < prim_work<NDIM>(R.g)) lam = prim_item<NDIM, CFL, !CFL>(R.g, R.U[reg], R.P, R.sc, id);
   if (CFL) cfl_block_finish(lam, R.sc, R.g.cfl, (unsigned int)(__ldg(blk0 + r + 1) - __ldg(blk0 + r)));
 }
 // Batched sweeps load directly (the ensemble's grids are small); a run whose

@@ -43,11 +43,16 @@ enum {
   RK_13_12, RK_M2, RK_3, RK_M4, RK_WEPS, RK_2, RK_M7, RK_11, RK_5, RK_0_1, RK_0_6, RK_0_3, RK_6,
   // PPM, RK3
   RK_7_12, RK_1_12, RK_THIRD,
+  // WENO-Z candidates times 6 d_k, and 6 d_k (d = 1/10, 6/10, 3/10)
+  RK_0_2, RK_M0_7, RK_1_1, RK_M0_6, RK_1_2, RK_M0_3, RK_1_5, RK_3_6, RK_1_8,
+  // bound factor of c2p_fast's pressure
+  RK_PB,
   RK_NK
 };
 __device__ double kRegK[RK_NK] = {-0.0, 1.0, -1.0, 0.5, -0.5, 0.375, 0.25, 4.0, kHlldDegenEps, 2.0 * kHlldBnEps,
                                   13.0 / 12.0, -2.0, 3.0, -4.0, kWenozEps, 2.0, -7.0, 11.0, 5.0, 0.1, 0.6, 0.3, 6.0,
-                                  7.0 / 12.0, 1.0 / 12.0, 1.0 / 3.0};
+                                  7.0 / 12.0, 1.0 / 12.0, 1.0 / 3.0,
+                                  0.2, -0.7, 1.1, -0.6, 1.2, -0.3, 1.5, 3.6, 1.8, 1e-14};
 __device__ __forceinline__ double rk(int i) { return __ldg(&kRegK[i]); }
 __device__ __forceinline__ double fmul(double a, double b) { return fma(a, b, rk(RK_NZ)); }
 __device__ __forceinline__ double fadd(double a, double b) { return fma(a, rk(RK_ONE), b); }
@@ -65,7 +70,12 @@ __device__ __forceinline__ double kmul(int i, double x) { return fma(rk(i), x, r
 // rcp.approx.ftz.f64) refined by one cubic Newton-Raphson step
 //   e = 1 - x r,  r' = r + r (e + e^2),
 // whose relative error is e^3 (< 2^-59 from a 2^-20 seed) plus rounding, i.e.
-// within about one ulp of the correctly rounded 1/x for normal, nonzero x.
+// within about one ulp of the correctly rounded 1/x.
+// Valid range: normal x with |x| < 2^1022 (so that 1/x is normal too).  The
+// seed flushes subnormals: a subnormal or zero x gives an infinite seed and a
+// NaN result, and |x| >= 2^1022 a zero seed and result 0.  The solvers call it
+// on densities, wave-speed differences and denominators that the degenerate
+// branches keep away from zero, all normal for physical states.
 __device__ __forceinline__ double rcp(double x) {
 #if MHD_FAST_RCP
   double r;
@@ -100,6 +110,31 @@ __device__ __forceinline__ Prim8 c2p_ieee(double rho, double mx, double my, doub
   double kin = m_(rk(RK_HALF), a_(a_(m_(mx, o.vx), m_(my, o.vy)), m_(mz, o.vz)));
   double B2 = a_(a_(m_(bx, bx), m_(by, by)), m_(bz, bz));
   o.p = m_(gm1, s_(s_(en, kin), m_(rk(RK_HALF), B2)));
+  o.rho = rho;
+  o.bx = bx;
+  o.by = by;
+  o.bz = bz;
+  return o;
+}
+
+// The same recovery with one refined reciprocal and fused sums, within a few
+// ulps of c2p_ieee, for the passes whose primitives decide nothing the oracle
+// must reproduce bit for bit (every pass but the CFL one).  pbound receives
+// 1e-14 (G-1)(|E| + (m.v + B^2)/2), far above the difference from c2p_ieee's
+// pressure (about ten roundings of those magnitudes): where the pressure lies
+// that close to a threshold the caller takes c2p_ieee's instead, so the floor
+// and positivity decisions are the IEEE ones.
+__device__ __forceinline__ Prim8 c2p_fast(double rho, double mx, double my, double mz, double en, double bx,
+                                          double by, double bz, double gm1, double& pbound) {
+  Prim8 o;
+  const double inv = rcp(rho);
+  o.vx = fmul(mx, inv);
+  o.vy = fmul(my, inv);
+  o.vz = fmul(mz, inv);
+  const double kin2 = fma(mx, o.vx, fma(my, o.vy, fmul(mz, o.vz)));  // m.v = 2 x kinetic energy
+  const double B2 = fma(bx, bx, fma(by, by, fmul(bz, bz)));
+  o.p = fmul(gm1, fma(rk(RK_MHALF), kin2, fma(rk(RK_MHALF), B2, en)));
+  pbound = fmul(gm1, kmul(RK_PB, fma(rk(RK_HALF), fadd(kin2, B2), fabs(en))));
   o.rho = rho;
   o.bx = bx;
   o.by = by;
@@ -154,6 +189,10 @@ __device__ __forceinline__ double times_sign(double x, double s) {
 // square-root seed (PTX rsqrt.approx.ftz.f64), refined by one third-order
 // step of the binomial series  (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + ...,
 // e = 1 - x y^2: relative error O(e^3) plus rounding, about one ulp.
+// Valid range: positive normal x.  The seed flushes subnormals, so a
+// subnormal or zero x gives NaN; fsqrt0 returns 0 for x below the smallest
+// normal double (negative, zero or subnormal), and the CFL rate's fast speed
+// sends a discriminant below 1e-290 to 0 before taking its root.
 __device__ __forceinline__ double rsqrt_seed(double x) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -172,8 +211,10 @@ __device__ __forceinline__ double frsqrt(double x) {
   double t = fmul(fma(rk(RK_3_8), e, rk(RK_HALF)), e);
   return fma(y, t, y);
 }
-// sqrt(x) for x >= 0 (the seed of 0 is infinite)
-__device__ __forceinline__ double fsqrt0(double x) { return gt0(x) ? fsqrt(x) : 0.0; }
+// sqrt(x) for any x, 0 below the smallest normal double (the seed of 0 or of a
+// subnormal is infinite; sqrt of a subnormal is below 1.5e-154 anyway)
+constexpr long long kMinNormalBits = 0x0010000000000000LL;
+__device__ __forceinline__ double fsqrt0(double x) { return bits(x) >= kMinNormalBits ? fsqrt(x) : 0.0; }
 
 // fast_speed_ieee with its square roots and division replaced by the refined
 // seeds (about one ulp each), everything else in the same IEEE operations:
@@ -524,17 +565,91 @@ __device__ __forceinline__ void recon_plm(double s1, double s2, double s3, doubl
 }
 
 // WENO-Z (Borges et al. 2008) values at both faces of the middle cell of
-// a0..a4 = V_{i-2..i+2}.  Candidate values q_k, Jiang-Shu indicators beta_k,
+// a0..a4 = V_{i-2..i+2}: candidate values q_k, Jiang-Shu indicators beta_k,
 // tau5 = |beta_0 - beta_2|, alpha_k = d_k (1 + (tau5 / (beta_k + eps))^2),
-// d = (1/10, 6/10, 3/10).  The mirrored (minus-face) stencil has the same
-// indicators with beta_0 and beta_2 exchanged, so the ratios
-// r_k = tau5 / (beta_k + eps) are formed once for both faces; the factor 1/6
-// of the candidate values is folded into the normalisation.
-//
-// beta_k's curvature term (13/12) (a_{j-1} - 2 a_j + a_{j+1})^2 belongs to the
-// three-cell stencil centred at j = i-1, i, i+1; a sweep marching along a
-// pencil passes those of i-1 and i in (c0, c1) and gets that of i+1 back in c2
-// for the next cell (the same operations on the same values as forming them here).
+// d = (1/10, 6/10, 3/10), value = sum alpha_k q_k / sum alpha_k.  The
+// mirrored (minus-face) stencil has the same indicators with beta_0 and
+// beta_2 exchanged, so the ratios r_k = tau5 / (beta_k + eps) and the factors
+// g_k = 1 + r_k^2 are formed once for both faces, and so is the middle
+// weight d_1 g_1.  The candidates are formed as 6 q_k and the normalisation
+// as 6 sum_k alpha_k = sum_k (6 d_k) g_k.
+__device__ __forceinline__ void wenoz_from_indicators(double a0, double a1, double a2, double a3, double a4,
+                                                      double b0, double b1, double b2, double& plus,
+                                                      double& minus) {
+  const double tau = dabs(fsub(b0, b2));
+  const double weps = rk(RK_WEPS);
+  const double r0 = fmul(tau, rcp(fadd(b0, weps)));
+  const double r1 = fmul(tau, rcp(fadd(b1, weps)));
+  const double r2 = fmul(tau, rcp(fadd(b2, weps)));
+  const double g0 = fma(r0, r0, rk(RK_ONE)), g1 = fma(r1, r1, rk(RK_ONE)), g2 = fma(r2, r2, rk(RK_ONE));
+  // alpha_k = d_k g_k: the plus face weighs (g0, g1, g2), the minus face (g2, g1, g0)
+  const double w1 = kmul(RK_0_6, g1);
+  const double K1 = kmul(RK_3_6, g1);  // 6 d_1 g_1
+  {  // plus face: stencils (a0 a1 a2), (a1 a2 a3), (a2 a3 a4); 6 q_k
+    const double q0 = fma(rk(RK_2), a0, fma(rk(RK_M7), a1, kmul(RK_11, a2)));
+    const double q1 = fma(rk(RK_5), a2, fma(rk(RK_2), a3, -a1));
+    const double q2 = fma(rk(RK_2), a2, fma(rk(RK_5), a3, -a4));
+    const double num = fma(kmul(RK_0_1, g0), q0, fma(w1, q1, fmul(kmul(RK_0_3, g2), q2)));
+    const double den = fma(rk(RK_0_6), g0, fma(rk(RK_1_8), g2, K1));  // 6 sum alpha_k
+    plus = fmul(num, rcp(den));
+  }
+  {  // minus face: the mirrored stencils with g2, g1, g0
+    const double q0 = fma(rk(RK_2), a4, fma(rk(RK_M7), a3, kmul(RK_11, a2)));
+    const double q1 = fma(rk(RK_5), a2, fma(rk(RK_2), a1, -a3));
+    const double q2 = fma(rk(RK_2), a2, fma(rk(RK_5), a1, -a0));
+    const double num = fma(kmul(RK_0_1, g2), q0, fma(w1, q1, fmul(kmul(RK_0_3, g0), q2)));
+    const double den = fma(rk(RK_0_6), g2, fma(rk(RK_1_8), g0, K1));
+    minus = fmul(num, rcp(den));
+  }
+}
+
+// beta_k = (13/12) (a_{j-1} - 2 a_j + a_{j+1})^2 + (1/4) u_k^2, the curvature
+// term belonging to the three-cell stencil centred at j = i-1, i, i+1 and u_k
+// the stencil's one-sided combination.  A sweep marching along a pencil
+// carries, per variable, what consecutive cells share (WzCarry for the window
+// of cell i):
+//   P0, P1 = the curvature terms of the stencils centred at a1 and a2,
+//   h      = u_0 / 2 = (a0 - 4 a1 + 3 a2) / 2,
+//   d      = a3 - a2.
+// With t2 = (a4 - a3) - d the curvature at a3, u_2 / 2 = t2 / 2 - d and
+// u_1 / 2 = (a1 - a3) / 2; the next cell's u_0 / 2 = u_1 / 2 + 2 d.
+// wenoz_start forms the carry of a segment's first window with the very
+// operations the march would have used (differences of neighbours, their
+// difference, (a0 - a2)/2 + 2 (a2 - a1)), so every cell's result is the same
+// to the bit wherever a segment starts.
+struct WzCarry {
+  double P0, P1, h, d;
+};
+__device__ __forceinline__ WzCarry wenoz_start(double a0, double a1, double a2, double a3) {
+  WzCarry c;
+  const double d01 = fsub(a1, a0), d12 = fsub(a2, a1);
+  c.d = fsub(a3, a2);
+  const double t0 = fsub(d12, d01), t1 = fsub(c.d, d12);
+  c.P0 = fmul(kmul(RK_13_12, t0), t0);
+  c.P1 = fmul(kmul(RK_13_12, t1), t1);
+  c.h = fma(rk(RK_2), d12, fma(rk(RK_HALF), a0, kmul(RK_MHALF, a2)));
+  return c;
+}
+__device__ __forceinline__ void recon_wenoz_m(double a0, double a1, double a2, double a3, double a4, WzCarry& c,
+                                              double& plus, double& minus) {
+  const double d34 = fsub(a4, a3);
+  const double t2 = fsub(d34, c.d);
+  const double P2 = fmul(kmul(RK_13_12, t2), t2);
+  const double h2 = fma(rk(RK_HALF), t2, -c.d);                  // (3 a2 - 4 a3 + a4) / 2
+  const double h1 = fma(rk(RK_HALF), a1, kmul(RK_MHALF, a3));    // (a1 - a3) / 2
+  const double b0 = fma(c.h, c.h, c.P0);
+  const double b1 = fma(h1, h1, c.P1);
+  const double b2 = fma(h2, h2, P2);
+  c.h = fma(rk(RK_2), c.d, h1);                                  // (a1 - 4 a2 + 3 a3) / 2, for cell i+1
+  c.P0 = c.P1;
+  c.P1 = P2;
+  c.d = d34;
+  wenoz_from_indicators(a0, a1, a2, a3, a4, b0, b1, b2, plus, minus);
+}
+
+// The same reconstruction from the curvatures alone (the GLM sweep carries
+// two per variable): c0, c1 of the stencils centred at a1, a2 in, that of a3
+// out in c2.
 struct Curv {
   double t, k;  // a_{j-1} - 2 a_j + a_{j+1} and 13/12 of it
 };
@@ -554,31 +669,12 @@ __device__ __forceinline__ void recon_wenoz_c(double a0, double a1, double a2, d
   c2 = curv(a2, a3, a4);
   u = fma(rk(RK_3), a2, fma(rk(RK_M4), a3, a4));
   double b2 = fma(c2.k, c2.t, fmul(kmul(RK_QUARTER, u), u));
-  double tau = dabs(fsub(b0, b2));
-  const double weps = rk(RK_WEPS);
-  double r0 = fmul(tau, rcp(fadd(b0, weps))), r1 = fmul(tau, rcp(fadd(b1, weps))), r2 = fmul(tau, rcp(fadd(b2, weps)));
-  double g0 = fma(r0, r0, rk(RK_ONE)), g1 = fma(r1, r1, rk(RK_ONE)), g2 = fma(r2, r2, rk(RK_ONE));
-  // plus face: stencils (a0 a1 a2), (a1 a2 a3), (a2 a3 a4); 6 q_k
-  {
-    double q0 = fma(rk(RK_2), a0, fma(rk(RK_M7), a1, kmul(RK_11, a2)));
-    double q1 = fma(rk(RK_5), a2, fma(rk(RK_2), a3, -a1));
-    double q2 = fma(rk(RK_2), a2, fma(rk(RK_5), a3, -a4));
-    double al0 = kmul(RK_0_1, g0), al1 = kmul(RK_0_6, g1), al2 = kmul(RK_0_3, g2);
-    plus = fmul(fma(al0, q0, fma(al1, q1, fmul(al2, q2))), rcp(kmul(RK_6, fadd(fadd(al0, al1), al2))));
-  }
-  // minus face: the mirrored stencils, indicators beta_2, beta_1, beta_0
-  {
-    double q0 = fma(rk(RK_2), a4, fma(rk(RK_M7), a3, kmul(RK_11, a2)));
-    double q1 = fma(rk(RK_5), a2, fma(rk(RK_2), a1, -a3));
-    double q2 = fma(rk(RK_2), a2, fma(rk(RK_5), a1, -a0));
-    double al0 = kmul(RK_0_1, g2), al1 = kmul(RK_0_6, g1), al2 = kmul(RK_0_3, g0);
-    minus = fmul(fma(al0, q0, fma(al1, q1, fmul(al2, q2))), rcp(kmul(RK_6, fadd(fadd(al0, al1), al2))));
-  }
+  wenoz_from_indicators(a0, a1, a2, a3, a4, b0, b1, b2, plus, minus);
 }
 __device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, double a3, double a4, double& plus,
                                             double& minus) {
-  Curv c2;
-  recon_wenoz_c(a0, a1, a2, a3, a4, curv(a0, a1, a2), curv(a1, a2, a3), c2, plus, minus);
+  WzCarry c = wenoz_start(a0, a1, a2, a3);
+  recon_wenoz_m(a0, a1, a2, a3, a4, c, plus, minus);
 }
 
 __device__ __forceinline__ double ppm_face(double a, double b, double c, double d) {

@@ -18,7 +18,7 @@ SO = os.path.join(HERE, "libmhd.so")
 
 MHD_OK = 0
 ERRORS = {-1: "MHD_ERR_ARG", -2: "MHD_ERR_CUDA", -3: "MHD_ERR_OOM", -4: "MHD_ERR_UNPHYSICAL",
-          -5: "MHD_ERR_TIMEOUT", -6: "MHD_ERR_STATE", -7: "MHD_ERR_TOO_LARGE"}
+          -5: "MHD_ERR_TIMEOUT", -6: "MHD_ERR_STATE", -7: "MHD_ERR_TOO_LARGE", -8: "MHD_ERR_DIVB"}
 RECON = {"plm": 0, "wenoz": 1, "ppm": 2}
 RIEMANN = {"hll": 0, "hlld": 1}
 BC = {"periodic": 0, "outflow": 1}
@@ -37,10 +37,15 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
+           "mhd_set_divb_check", "mhd_divb",
            "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen",
            "mhd_batch_get_conserved_async", "mhd_batch_synchronize", "mhd_batch_packed_size",
            "mhd_batch_set_conserved_packed", "mhd_batch_get_conserved_packed", "mhd_set_time",
-           "mhd_probe_riemann", "mhd_probe_fp64_forms")
+           "mhd_probe_riemann", "mhd_probe_fp64_forms",
+           "mhd_domain_brick", "mhd_domain_halo", "mhd_domain_create", "mhd_domain_destroy",
+           "mhd_domain_set_conserved", "mhd_domain_get_conserved", "mhd_domain_cfl_dt", "mhd_domain_step",
+           "mhd_domain_advance", "mhd_domain_get_time", "mhd_domain_status", "mhd_domain_counters",
+           "mhd_domain_set_seglen", "mhd_domain_launch_count", "mhd_domain_halo_bytes")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -50,6 +55,11 @@ class MhdError(RuntimeError):
     def __init__(self, code, what):
         super().__init__(f"{what}: {ERRORS.get(code, code)} ({lib().mhd_strerror(code).decode()})")
         self.code = code
+
+
+class mhd_halo_box(ctypes.Structure):
+    _fields_ = [("peer", ctypes.c_int), ("dir", ctypes.c_int * 3), ("lo", ctypes.c_int * 3),
+                ("ext", ctypes.c_int * 3), ("offset", ctypes.c_longlong)]
 
 
 class mhd_config(ctypes.Structure):
@@ -123,6 +133,25 @@ def lib():
             "mhd_probe_cfl_rate": (I, [I, D, P, I, P, P, P]),
             "mhd_probe_riemann": (I, [I, I, I, D, P, P, P]),
             "mhd_get_seglen": (I, [P, ctypes.POINTER(I)]),
+            "mhd_set_divb_check": (I, [P, D]),
+            "mhd_divb": (I, [P, ctypes.POINTER(D)]),
+            "mhd_domain_brick": (I, [ctypes.POINTER(mhd_config), ctypes.POINTER(I), I, ctypes.POINTER(I),
+                                     ctypes.POINTER(I)]),
+            "mhd_domain_halo": (I, [ctypes.POINTER(mhd_config), ctypes.POINTER(I), I, I,
+                                    ctypes.POINTER(mhd_halo_box), I, ctypes.POINTER(I)]),
+            "mhd_domain_create": (I, [ctypes.POINTER(mhd_config), ctypes.POINTER(I), ctypes.POINTER(P)]),
+            "mhd_domain_destroy": (I, [P]),
+            "mhd_domain_set_conserved": (I, [P, I, DPP, DPP]),
+            "mhd_domain_get_conserved": (I, [P, I, DPP, DPP]),
+            "mhd_domain_cfl_dt": (I, [P, ctypes.POINTER(D)]),
+            "mhd_domain_step": (I, [P, D]),
+            "mhd_domain_advance": (I, [P, I]),
+            "mhd_domain_get_time": (I, [P, ctypes.POINTER(D)]),
+            "mhd_domain_status": (I, [P, ctypes.POINTER(ctypes.c_longlong)]),
+            "mhd_domain_counters": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+            "mhd_domain_set_seglen": (I, [P, I]),
+            "mhd_domain_launch_count": (ctypes.c_longlong, [P]),
+            "mhd_domain_halo_bytes": (ctypes.c_longlong, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -323,6 +352,16 @@ class Sim:
         s = ctypes.c_int()
         _check(lib().mhd_autotune(self.h, ctypes.byref(s)), "mhd_autotune")
         return s.value
+
+    def set_divb_check(self, tol):
+        """Check max |div B| h / max |B_c| at the end of every step (tol > 0; 0 = off)."""
+        _check(lib().mhd_set_divb_check(self.h, float(tol)), "mhd_set_divb_check")
+
+    def divb(self):
+        """max |div B| h / max |B_c| of the current state."""
+        r = ctypes.c_double()
+        _check(lib().mhd_divb(self.h, ctypes.byref(r)), "mhd_divb")
+        return r.value
 
     def set_boundaries(self, bc):
         arr = (ctypes.c_int * 6)(*[BC[b] for b in bc])
@@ -677,3 +716,114 @@ def final_functional(cfg, rho, vx, vy, vz, p, B, nsteps, dts=None, ckpt_every=20
             return tuple(gJ * t for t in ctx.saved_tensors)
 
     return _Final.apply(rho, vx, vy, vz)
+
+
+# ---------------------------------------------------------------------------
+# domain decomposition: bricks with a halo exchange per stage
+# ---------------------------------------------------------------------------
+def _parts(parts):
+    parts = list(parts) + [1] * (3 - len(parts))
+    return (ctypes.c_int * 3)(*parts)
+
+
+def domain_brick(cfg, parts, brick):
+    """(lo, n): first global cell and cells per axis (3 each) of a brick."""
+    lo, n = (ctypes.c_int * 3)(), (ctypes.c_int * 3)()
+    _check(lib().mhd_domain_brick(ctypes.byref(make_config(cfg)), _parts(parts), int(brick), lo, n),
+           "mhd_domain_brick")
+    return tuple(lo), tuple(n)
+
+
+def domain_halo(cfg, parts, brick, send):
+    """The brick's send (send=True) or receive boxes: list of dicts peer, dir,
+    lo, ext, offset (see mhd_halo_box in include/mhd.h)."""
+    boxes = (mhd_halo_box * 26)()
+    nb = ctypes.c_int()
+    _check(lib().mhd_domain_halo(ctypes.byref(make_config(cfg)), _parts(parts), int(brick), int(bool(send)), boxes,
+                                 26, ctypes.byref(nb)), "mhd_domain_halo")
+    return [{"peer": b.peer, "dir": tuple(b.dir), "lo": tuple(b.lo), "ext": tuple(b.ext), "offset": b.offset}
+            for b in boxes[:nb.value]]
+
+
+class Domain:
+    """One grid split into bricks (parts = bricks per axis), advanced together
+    with a halo exchange per RK stage on one GPU; the state, dt and time are
+    the undivided grid's to the bit."""
+
+    def __init__(self, cfg, parts, state=None, stream=None):
+        self.cfg = dict(cfg)
+        self.parts = tuple(list(parts) + [1] * (3 - len(parts)))
+        self.shapes = state_shapes(cfg)
+        self._c = make_config(cfg, stream)
+        h = ctypes.c_void_p()
+        _check(lib().mhd_domain_create(ctypes.byref(self._c), _parts(parts), ctypes.byref(h)), "mhd_domain_create")
+        self.h = h
+        if state is not None:
+            self.set_conserved(state)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mhd_domain_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_conserved(self, state):
+        arrs = [state[k] for k in KEYS]
+        dev = _is_device(arrs[0])
+        if not dev:
+            arrs = _host_arrays(arrs, self.shapes)
+        self._keep = arrs
+        _check(lib().mhd_domain_set_conserved(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
+                                              _ptr_array(arrs[5:])), "mhd_domain_set_conserved")
+
+    def get_conserved(self, out=None):
+        if out is None:
+            out = {k: np.zeros(s) for k, s in zip(KEYS, self.shapes)}
+        arrs = [out[k] for k in KEYS]
+        dev = _is_device(arrs[0])
+        _check(lib().mhd_domain_get_conserved(self.h, MEM_DEVICE if dev else MEM_HOST, _ptr_array(arrs[:5]),
+                                              _ptr_array(arrs[5:])), "mhd_domain_get_conserved")
+        return out
+
+    def cfl_dt(self):
+        dt = ctypes.c_double()
+        _check(lib().mhd_domain_cfl_dt(self.h, ctypes.byref(dt)), "mhd_domain_cfl_dt")
+        return dt.value
+
+    def step(self, dt):
+        _check(lib().mhd_domain_step(self.h, float(dt)), "mhd_domain_step")
+
+    def advance(self, nsteps):
+        _check(lib().mhd_domain_advance(self.h, int(nsteps)), "mhd_domain_advance")
+
+    @property
+    def time(self):
+        t = ctypes.c_double()
+        _check(lib().mhd_domain_get_time(self.h, ctypes.byref(t)), "mhd_domain_get_time")
+        return t.value
+
+    def status(self):
+        bad = ctypes.c_longlong()
+        rc = lib().mhd_domain_status(self.h, ctypes.byref(bad))
+        return rc, bad.value
+
+    def counters(self):
+        f, p = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().mhd_domain_counters(self.h, ctypes.byref(f), ctypes.byref(p)), "mhd_domain_counters")
+        return f.value, p.value
+
+    def set_seglen(self, seglen):
+        _check(lib().mhd_domain_set_seglen(self.h, int(seglen)), "mhd_domain_set_seglen")
+
+    @property
+    def launches(self):
+        return lib().mhd_domain_launch_count(self.h)
+
+    @property
+    def halo_bytes(self):
+        return lib().mhd_domain_halo_bytes(self.h)

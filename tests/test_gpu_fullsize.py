@@ -138,6 +138,17 @@ def test_orszag_tang3d_704():
     compare_boxes(cfg, st, out, dt, boxes, 4)
 
 
+def test_cpa3d_704():
+    """The paper's circularly polarised Alfven wave (§4.2) at 704 x 704 x 352 with WENO-Z + HLLD +
+    SSP-RK3 and UCT-HLLD edge fields: the wave travels along the cube's diagonal, so every box
+    sees the double-star region of the fan."""
+    cfg, st = W.cpa_3d((704, 704, 352), recon="wenoz", rk=3, emf="uct_hlld")
+    dt, out = bench_step(cfg, st)
+    assert dt == oracle.cfl_dt_state(cfg, st)
+    boxes = [[0, 0, 0], [703, 703, 351], [351, 351, 175], [100, 600, 20]] + random_boxes(cfg, 4, 3, 7)
+    compare_boxes(cfg, st, out, dt, boxes, 4)
+
+
 def test_ensemble_256_runs():
     """256 Orszag-Tang runs of 64^2 .. 512^2 cells in one batched, graph-captured step."""
     members = W.ensemble_members(256, seed=4)

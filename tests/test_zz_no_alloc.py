@@ -4,8 +4,11 @@ Some callers cannot allocate device memory (their memory belongs to another
 allocator or budget, or they may not pay the synchronisation an allocation can
 imply); mhd_step_noalloc serves them from a fixed file-scope scratch array.
 Its result must equal mhd_step's on the same state and dt, on two calls in a
-row, and it must refuse grids larger than its array.  Collected last, so a
-failure here comes after every other test has run; it also passes alone.
+row; it must accept the grids the header's table lists and refuse one cell
+more; a step that meets a non-positive pressure leaves the caller's arrays as
+they were; and calls after the first leave the device's free memory
+unchanged.  Collected last, so a failure here comes after every other test
+has run; it also passes alone.
 """
 import numpy as np
 import pytest
@@ -89,3 +92,65 @@ def test_noalloc_rejects_grids_beyond_its_scratch(mhd):
     assert e.value.code == -7
     for k in KEYS:
         assert torch.equal(dev[k], before[k])   # nothing was touched
+
+
+def _uniform(cfg, shapes):
+    """A uniform state (steady under the step): rho = 1, v = 0, p = 1, B = (0.3, -0.2, 0.1)."""
+    B = (0.3, -0.2, 0.1)
+    E = 1.0 / (cfg["gamma"] - 1.0) + 0.5 * sum(b * b for b in B)
+    return {k: np.full(s, v) for k, s, v in zip(KEYS, shapes, (1.0, 0.0, 0.0, 0.0, E) + B)}
+
+
+# largest square / cubic grids that fit the scratch array (the table in include/mhd.h)
+LIMITS = [(2, "plm", "uct_hll", 266), (2, "plm", "uct_hlld", 259), (2, "wenoz", "uct_hll", 264),
+          (2, "ppm", "uct_hlld", 257), (3, "plm", "uct_hll", 36), (3, "plm", "uct_hlld", 36),
+          (3, "wenoz", "uct_hll", 34), (3, "ppm", "uct_hlld", 34)]
+
+
+@pytest.mark.parametrize("ndim,recon,emf,n", LIMITS, ids=[f"{a}d-{b}-{c}-{d}" for a, b, c, d in LIMITS])
+def test_noalloc_documented_limits(mhd, ndim, recon, emf, n):
+    import torch
+    for m, ok in ((n, True), (n + 1, False)):
+        cfg = W.base_cfg(ndim, (m,) * ndim, (0,) * ndim, (1,) * ndim, recon=recon, emf=emf)
+        st = _uniform(cfg, mhd.state_shapes(cfg))
+        dev = {k: torch.from_numpy(st[k]).cuda() for k in KEYS}
+        if ok:
+            mhd.step_noalloc(cfg, dev, 1e-3)
+            for k in KEYS:   # a uniform state stays uniform
+                assert relerr(dev[k].cpu().numpy(), st[k]) <= 1e-14, (m, k)
+        else:
+            with pytest.raises(mhd.MhdError) as e:
+                mhd.step_noalloc(cfg, dev, 1e-3)
+            assert e.value.code == -7
+
+
+def test_noalloc_leaves_the_arrays_alone_on_an_unphysical_step(mhd):
+    import torch
+    cfg, st = CASES["orszag-tang2d-64-plm-hlld-rk2"]()
+    st = {k: np.ascontiguousarray(v).copy() for k, v in st.items()}
+    st["E"][0, 20, 30] = -5.0          # a negative pressure, made on the host
+    dev = {k: torch.from_numpy(st[k]).cuda() for k in KEYS}
+    with pytest.raises(mhd.MhdError) as e:
+        mhd.step_noalloc(cfg, dev, 1e-3)
+    assert e.value.code == -4
+    for k in KEYS:
+        np.testing.assert_array_equal(dev[k].cpu().numpy(), st[k], err_msg=k)
+
+
+def test_noalloc_allocates_no_device_memory(mhd):
+    """After a first call (which may load the library's device code on this
+    device, and with it the scratch array), further calls leave the device's
+    free memory unchanged."""
+    import torch
+    cfg, st = CASES["turbulent3d-12x10x8-wenoz-hlld-rk3"]()
+    dev = {k: torch.from_numpy(np.ascontiguousarray(st[k])).cuda() for k in KEYS}
+    mhd.step_noalloc(cfg, dev, 1e-4)
+    b_cfg, b_st = CASES["orszag-tang2d-64-plm-hlld-rk2"]()
+    b_dev = {k: torch.from_numpy(np.ascontiguousarray(b_st[k])).cuda() for k in KEYS}
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        mhd.step_noalloc(cfg, dev, 1e-4)
+        mhd.step_noalloc(b_cfg, b_dev, 1e-4)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
