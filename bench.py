@@ -1060,7 +1060,9 @@ def companions(dev, stream, plain_value, plain_frac, plain_step_frac, steps):
                                                                         "recompute, reverse)",
                "frac": a["roofline"]["frac"], "gradient_frac": a["roofline"]["gradient_frac"],
                "roofline_kernel": a["roofline"]["kernel"], "gpu_launches": a["launches"],
-               "phases": a["phases"],
+               "phases": a["phases"], "reverse_ms_by_class": a["roofline"]["reverse_ms_by_class"],
+               "phases_note": "the phases are timed in sequence by the profiling run; the timed gradients overlap "
+                              "the block recomputes with the reverse pass",
                "plain_step_same_grid": {"value": plain_grid, "unit": UNIT, "ms_per_step": a["plain_ms"] / N,
                                         "what": "the plain forward run of the same 256^2 grid and 400 steps"},
                "gradient_over_plain_time": a["eval_ms"] / a["plain_ms"],

@@ -8,17 +8,22 @@
 //   reverse   for each block of k steps, last block first: recompute its
 //             steps from the checkpoint, keeping every stage input, then run
 //             the stage transposes backwards through the block.
-// The recompute of block b-1 runs on a second stream, with a context of its
-// own for the scratch of the forward kernels, while the transposes of block b
-// run on the context's stream: the block storage is double-buffered, and
-// events order each block's transposes after its recompute and each
-// recompute after the transposes that last read its buffers.  At a 256^2 grid
-// both are latency-bound chains of small kernels, so the device runs them
-// side by side.  (The profiling run keeps them in sequence, so that each
+// The recomputes run on a second stream, with a context of their own for the
+// scratch of the forward kernels, while the transposes run on the context's
+// stream.  The block storage is double-buffered, and the recompute context
+// stays two blocks ahead: it rebuilds the last two blocks first (with the
+// step sizes given, beside the forward pass's last block, as soon as that
+// block's checkpoint is saved), then block b - 2 once the transposes of block
+// b have read their buffers.  Events order each block's transposes after its
+// recompute.  At a 256^2 grid both are latency-bound chains of small kernels,
+// so the device runs them side by side.  The recompute also keeps each
+// stage's primitives (its primitive pass writes them into the block
+// storage), so the transposes need no primitive pass of their own.  (The
+// profiling run keeps everything in sequence on the context, so that each
 // phase's events time only its own kernels.)
 // Memory: ceil(n/k) + 2(k*S + 1) states (S = RK stages), 2 k*S ingredient
-// sets, a second context's scratch, plus the scratch of the transposes; work:
-// two forward passes and one reverse pass.
+// and primitive sets, a second context's scratch, plus the scratch of the
+// transposes; work: two forward passes and one reverse pass.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -42,6 +47,7 @@ struct AdjointState {
   size_t state_count = 0;
   double* ings = nullptr;     // UCT ingredients of every stage of the block (5 ndim fields each)
   size_t ing_count = 0;
+  double* prims = nullptr;    // primitives of every stage of the block (8 fields each)
   F8 A[4];                    // cotangent accumulators of the stage inputs (A[3]: incoming)
   L6 Lb;                      // cotangent of the stage increment (cells)
   E3 Eb;                      // cotangent of the edge fields
@@ -68,6 +74,7 @@ void adjoint_free(mhd_ctx* c) {
   cudaFree(c->adj->pool);
   cudaFree(c->adj->states);
   cudaFree(c->adj->ings);
+  cudaFree(c->adj->prims);
   cudaFree(c->adj->Jcell);
   cudaFree(c->adj->scal);
   delete c->adj;
@@ -87,6 +94,13 @@ unsigned* plm_codes(const AdjointState* a, int d) { return reinterpret_cast<unsi
 F8 state_at(const AdjointState* a, size_t idx) {
   F8 s;
   for (int q = 0; q < 8; q++) s.q[q] = a->states + (idx * 8 + q) * a->fe;
+  return s;
+}
+
+// The stored primitives of stage idx, laid out like the context's.
+F8 prim_at(const AdjointState* a, size_t idx) {
+  F8 s;
+  for (int q = 0; q < 8; q++) s.q[q] = a->prims + (idx * 8 + q) * a->fe;
   return s;
 }
 
@@ -153,9 +167,11 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
   const size_t need_ings = 2 * (size_t)k * S;
   if (a->ing_count < need_ings) {
     cudaFree(a->ings);
-    a->ings = nullptr;
+    cudaFree(a->prims);
+    a->ings = a->prims = nullptr;
     a->ing_count = 0;
-    if (cudaMalloc(&a->ings, need_ings * 5 * c->g.ndim * a->fe * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&a->ings, need_ings * 5 * c->g.ndim * a->fe * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&a->prims, need_ings * 8 * a->fe * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return MHD_ERR_OOM;
     }
@@ -191,13 +207,13 @@ void stage_coeffs(int rk, int s, double& c0, double& c1, double& cL) {
 // cotangents and PLM codes), then, separately, its reconstruction transpose,
 // which adds into Pb and so runs on the context stream in direction order.
 template <int NDIM, int RS, int DIR>
-void adj_riemann_dir(mhd_ctx* c, const F8& Xs, const F8& As, double dt, cudaStream_t st) {
+void adj_riemann_dir(mhd_ctx* c, const F8& Xs, const F8& Ps, const F8& As, double dt, cudaStream_t st) {
   AdjointState* a = c->adj;
   const Grid& g = c->g;
   long long faces = 1;
   for (int d = 0; d < 3; d++) faces *= d == DIR ? g.n[d] + 1 : (d < NDIM ? g.n[d] + 2 : 1);
   adj_riemann_kernel<DIR, NDIM, RS><<<(int)((faces + 127) / 128), 128, 0, st>>>(
-      g, c->P, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL[DIR], a->WbR[DIR], As.q[5 + DIR], plm_codes(a, DIR));
+      g, Ps, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL[DIR], a->WbR[DIR], As.q[5 + DIR], plm_codes(a, DIR));
   prof_mark(c, MHD_AKCLASS_RIEMANN);
   c->launches++;
 }
@@ -216,15 +232,13 @@ void adj_recon_dir(mhd_ctx* c) {
 // Transpose of stage s at the stage input Xs: the cotangent Aout of the
 // stage output is distributed to A0 (U^n) and As (the stage input).
 template <int NDIM, int RS>
-int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const FaceIngr& ING, const F8& Aout, const F8& A0, const F8& As,
-                double dt) {
+int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& ING, const F8& Aout, const F8& A0,
+                const F8& As, double dt) {
   AdjointState* a = c->adj;
   const Grid& g = c->g;
-  // forward recompute of what the transposes read: the primitives of Xs.  Its
-  // ghost cells need no fill: the block recompute ran the forward stage on
-  // Xs, whose ghost fill wrote them in place (periodic, so idempotent), and
-  // its UCT ingredients ING were kept then too.
-  prim(c, Xs, false, s > 0);  // the primitives the forward stage s used
+  // what the transposes read of the forward stage -- its input Xs with the
+  // ghost cells its fill wrote, its primitives Ps and its UCT ingredients ING
+  // -- was kept when the block recompute ran that stage
   double c0, c1, cL;
   stage_coeffs(c->cfg.rk, s, c0, c1, cL);
   const long long edges = edge_work<NDIM>(g);
@@ -240,30 +254,30 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const FaceIngr& ING, const F8& 
   if (split_now(c)) {  // the directions' Riemann transposes side by side (small grids)
     cudaEventRecord(c->ev_fork, c->stream);
     cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0);
-    adj_riemann_dir<NDIM, RS, 1>(c, Xs, As, dt, c->aux[0]);
+    adj_riemann_dir<NDIM, RS, 1>(c, Xs, Ps, As, dt, c->aux[0]);
     cudaEventRecord(c->ev_join[0], c->aux[0]);
     if constexpr (NDIM == 3) {
       cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0);
-      adj_riemann_dir<NDIM, RS, 2>(c, Xs, As, dt, c->aux[1]);
+      adj_riemann_dir<NDIM, RS, 2>(c, Xs, Ps, As, dt, c->aux[1]);
       cudaEventRecord(c->ev_join[1], c->aux[1]);
     }
-    adj_riemann_dir<NDIM, RS, 0>(c, Xs, As, dt, c->stream);
+    adj_riemann_dir<NDIM, RS, 0>(c, Xs, Ps, As, dt, c->stream);
     cudaStreamWaitEvent(c->stream, c->ev_join[0], 0);
     if constexpr (NDIM == 3) cudaStreamWaitEvent(c->stream, c->ev_join[1], 0);
     adj_recon_dir<NDIM, 0>(c);
     adj_recon_dir<NDIM, 1>(c);
     if constexpr (NDIM == 3) adj_recon_dir<NDIM, 2>(c);
   } else {
-    adj_riemann_dir<NDIM, RS, 0>(c, Xs, As, dt, c->stream);
+    adj_riemann_dir<NDIM, RS, 0>(c, Xs, Ps, As, dt, c->stream);
     adj_recon_dir<NDIM, 0>(c);
-    adj_riemann_dir<NDIM, RS, 1>(c, Xs, As, dt, c->stream);
+    adj_riemann_dir<NDIM, RS, 1>(c, Xs, Ps, As, dt, c->stream);
     adj_recon_dir<NDIM, 1>(c);
     if constexpr (NDIM == 3) {
-      adj_riemann_dir<NDIM, RS, 2>(c, Xs, As, dt, c->stream);
+      adj_riemann_dir<NDIM, RS, 2>(c, Xs, Ps, As, dt, c->stream);
       adj_recon_dir<NDIM, 2>(c);
     }
   }
-  adj_c2p_cells_kernel<NDIM><<<blocks_for(prim_work<NDIM>(g), 256), 256, 0, c->stream>>>(g, Xs, c->P, a->Pb, As);
+  adj_c2p_cells_kernel<NDIM><<<blocks_for(prim_work<NDIM>(g), 256), 256, 0, c->stream>>>(g, Xs, Ps, a->Pb, As);
   long long pad = (long long)g.ext[0] * g.ext[1] * g.ext[2];
   adj_c2p_faces_kernel<NDIM><<<blocks_for(pad, 256), 256, 0, c->stream>>>(g, a->Pb, As);
   prof_mark(c, MHD_AKCLASS_C2P);
@@ -274,14 +288,14 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const FaceIngr& ING, const F8& 
   return MHD_OK;
 }
 
-int adj_stage(mhd_ctx* c, int s, const F8& Xs, const FaceIngr& ING, const F8& Aout, const F8& A0, const F8& As,
-              double dt) {
+int adj_stage(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& ING, const F8& Aout, const F8& A0,
+              const F8& As, double dt) {
   const bool hlld = c->cfg.riemann == MHD_RIEMANN_HLLD;
   if (c->g.ndim == 2)
-    return hlld ? adj_stage_t<2, RS_HLLD>(c, s, Xs, ING, Aout, A0, As, dt)
-                : adj_stage_t<2, RS_HLL>(c, s, Xs, ING, Aout, A0, As, dt);
-  return hlld ? adj_stage_t<3, RS_HLLD>(c, s, Xs, ING, Aout, A0, As, dt)
-              : adj_stage_t<3, RS_HLL>(c, s, Xs, ING, Aout, A0, As, dt);
+    return hlld ? adj_stage_t<2, RS_HLLD>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
+                : adj_stage_t<2, RS_HLL>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+  return hlld ? adj_stage_t<3, RS_HLLD>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
+              : adj_stage_t<3, RS_HLL>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
 }
 
 int seed(mhd_ctx* c, int functional) {
@@ -347,12 +361,71 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
     }
   }
 
+  const size_t base = (size_t)a->nck;  // the two block buffer sets follow the checkpoints
+  const size_t set_states = (size_t)k * S + 1, set_ings = (size_t)k * S;
+  auto X = [&](int set, int n0, int n, int st) {
+    return state_at(a, base + set * set_states + (size_t)(n - n0) * S + st);
+  };
+  auto ING = [&](int set, int n0, int n, int st) {
+    return ing_at(a, g.ndim, set * set_ings + (size_t)(n - n0) * S + st);
+  };
+  auto PRIM = [&](int set, int n0, int n, int st) { return prim_at(a, set * set_ings + (size_t)(n - n0) * S + st); };
+  // block b's stage inputs and UCT ingredients into buffer set `set`,
+  // recomputed from its checkpoint by context r on r's stream
+  auto recompute = [&](mhd_ctx* r, int b, int set) -> int {
+    const int n0 = b * k, n1 = (n0 + k < nsteps) ? n0 + k : nsteps;
+    CK(cudaMemcpyAsync(X(set, n0, n0, 0).q[0], state_at(a, b).q[0], 8 * a->fe * sizeof(double),
+                       cudaMemcpyDeviceToDevice, r->stream));
+    for (int n = n0; n < n1; n++) {
+      set_dt_only_kernel<<<1, 1, 0, r->stream>>>(r->sc, a->dts[n]);
+      r->launches++;
+      for (int st = 0; st < S; st++) {
+        F8 out = st + 1 < S ? X(set, n0, n, st + 1) : X(set, n0, n + 1, 0);
+        const F8 own = r->P;
+        r->P = PRIM(set, n0, n, st);  // the stage's primitive pass writes them where the transposes read them
+        run_stage_regs(r, st, X(set, n0, n, 0), X(set, n0, n, st), out, false);
+        r->P = own;
+        // keep the stage's UCT ingredients (the context's are contiguous, direction-major)
+        const FaceIngr keep = ING(set, n0, n, st);
+        CK(cudaMemcpyAsync(keep.a[0][0], r->ING.a[0][0], (size_t)5 * g.ndim * a->fe * sizeof(double),
+                           cudaMemcpyDeviceToDevice, r->stream));
+      }
+    }
+    return MHD_OK;
+  };
   // forward pass with checkpoints; dt frozen (given) or from the CFL condition
   if (prof) CK(cudaEventRecord(prof->e0, c->stream));
+  // The recompute context rebuilds the last two blocks ahead of the reverse
+  // pass, from their checkpoints: with the step sizes given, as soon as the
+  // forward pass has saved the last block's checkpoint (beside the forward
+  // pass's remaining steps); otherwise after the forward pass, which records
+  // the steps.  It then stays two blocks ahead of the transposes.
+  mhd_ctx* r = prof ? c : a->shadow;
+  const int last = a->nck - 1;
+  const long long l0 = r == c ? 0 : r->launches;
+  auto start_recomputes = [&]() -> int {
+    if (r != c) {
+      CK(cudaEventRecord(a->ev_fwd, c->stream));
+      CK(cudaStreamWaitEvent(r->stream, a->ev_fwd, 0));
+    }
+    for (int b = last; b >= 0 && b >= last - 1; b--) {
+      int rc2 = recompute(r, b, b & 1);
+      if (rc2) return rc2;
+      CK(cudaEventRecord(a->ev_rec[b & 1], r->stream));
+    }
+    return MHD_OK;
+  };
+  bool started = false;
+  if (dts) a->dts.assign(dts, dts + nsteps);
   for (int n = 0; n < nsteps; n++) {
     if (n % k == 0) {
       rc = copy_state(c, state_at(a, n / k), c->U[0]);
       if (rc) return rc;
+      if (dts && !prof && n / k == last) {
+        rc = start_recomputes();
+        if (rc) return rc;
+        started = true;
+      }
     }
     if (dts) {
       set_dt_kernel<<<1, 1, 0, c->stream>>>(c->sc, dts[n]);
@@ -380,37 +453,8 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
   rc = seed(c, functional);
   if (rc) return rc;
 
-  // reverse pass, one checkpoint block at a time, last block first
-  F8 Ain = a->A[3];
-  const size_t base = (size_t)a->nck;  // the two block buffer sets follow the checkpoints
-  const size_t set_states = (size_t)k * S + 1, set_ings = (size_t)k * S;
-  auto X = [&](int set, int n0, int n, int st) {
-    return state_at(a, base + set * set_states + (size_t)(n - n0) * S + st);
-  };
-  auto ING = [&](int set, int n0, int n, int st) {
-    return ing_at(a, g.ndim, set * set_ings + (size_t)(n - n0) * S + st);
-  };
-  // block b's stage inputs and UCT ingredients into buffer set `set`,
-  // recomputed from its checkpoint by context r on r's stream
-  auto recompute = [&](mhd_ctx* r, int b, int set) -> int {
-    const int n0 = b * k, n1 = (n0 + k < nsteps) ? n0 + k : nsteps;
-    CK(cudaMemcpyAsync(X(set, n0, n0, 0).q[0], state_at(a, b).q[0], 8 * a->fe * sizeof(double),
-                       cudaMemcpyDeviceToDevice, r->stream));
-    for (int n = n0; n < n1; n++) {
-      set_dt_only_kernel<<<1, 1, 0, r->stream>>>(r->sc, a->dts[n]);
-      r->launches++;
-      for (int st = 0; st < S; st++) {
-        F8 out = st + 1 < S ? X(set, n0, n, st + 1) : X(set, n0, n + 1, 0);
-        run_stage_regs(r, st, X(set, n0, n, 0), X(set, n0, n, st), out, false);
-        // keep the stage's UCT ingredients (the context's are contiguous, direction-major)
-        const FaceIngr keep = ING(set, n0, n, st);
-        CK(cudaMemcpyAsync(keep.a[0][0], r->ING.a[0][0], (size_t)5 * g.ndim * a->fe * sizeof(double),
-                           cudaMemcpyDeviceToDevice, r->stream));
-      }
-    }
-    return MHD_OK;
-  };
   // the stage transposes of block b, backwards, reading buffer set `set`
+  F8 Ain = a->A[3];
   auto reverse = [&](int b, int set) -> int {
     const int n0 = b * k, n1 = (n0 + k < nsteps) ? n0 + k : nsteps;
     for (int n = n1 - 1; n >= n0; n--) {
@@ -423,7 +467,8 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
       for (int st = 0; st < S; st++) CK(cudaMemsetAsync(a->A[st].q[0], 0, 8 * a->fe * sizeof(double), c->stream));
       for (int st = S - 1; st >= 0; st--) {
         const F8& Aout = st == S - 1 ? Ain : a->A[st + 1];
-        int rc2 = adj_stage(c, st, X(set, n0, n, st), ING(set, n0, n, st), Aout, a->A[0], a->A[st], dt);
+        int rc2 = adj_stage(c, st, X(set, n0, n, st), PRIM(set, n0, n, st), ING(set, n0, n, st), Aout, a->A[0],
+                            a->A[st], dt);
         if (rc2) {
           c->prof_on = false;
           return rc2;
@@ -446,7 +491,7 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
     return MHD_OK;
   };
   if (prof) {  // in sequence on the context, each phase timed on its own
-    for (int b = a->nck - 1; b >= 0; b--) {
+    for (int b = last; b >= 0; b--) {
       CK(cudaEventRecord(prof->e0, c->stream));
       rc = recompute(c, b, 0);
       if (rc) return rc;
@@ -456,29 +501,23 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
       rc = reverse(b, 0);
       if (rc) return rc;
     }
-  } else {  // block b - 1 recomputed on the second context while block b is transposed
-    mhd_ctx* r = a->shadow;
-    const long long l0 = r->launches;
-    CK(cudaEventRecord(a->ev_fwd, c->stream));
-    CK(cudaStreamWaitEvent(r->stream, a->ev_fwd, 0));
-    const int last = a->nck - 1;
-    rc = recompute(r, last, last & 1);
-    if (rc) return rc;
-    CK(cudaEventRecord(a->ev_rec[last & 1], r->stream));
+  } else {  // the recompute context two blocks ahead of the transposes
+    if (!started) {
+      rc = start_recomputes();
+      if (rc) return rc;
+    }
     for (int b = last; b >= 0; b--) {
       const int set = b & 1;
-      if (b > 0) {
-        const int other = (b - 1) & 1;
-        // its buffers were last read by the transposes of block b + 1
-        if (b < last) CK(cudaStreamWaitEvent(r->stream, a->ev_rev[other], 0));
-        rc = recompute(r, b - 1, other);
-        if (rc) return rc;
-        CK(cudaEventRecord(a->ev_rec[other], r->stream));
-      }
       CK(cudaStreamWaitEvent(c->stream, a->ev_rec[set], 0));
       rc = reverse(b, set);
       if (rc) return rc;
       CK(cudaEventRecord(a->ev_rev[set], c->stream));
+      if (b >= 2) {  // block b - 2 reuses the buffers the transposes of block b just read
+        CK(cudaStreamWaitEvent(r->stream, a->ev_rev[set], 0));
+        rc = recompute(r, b - 2, set);
+        if (rc) return rc;
+        CK(cudaEventRecord(a->ev_rec[set], r->stream));
+      }
     }
     CK(cudaStreamSynchronize(r->stream));
     c->launches += r->launches - l0;
