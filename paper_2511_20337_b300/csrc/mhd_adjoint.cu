@@ -88,7 +88,7 @@ namespace {
 constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 * 18 + 3 * (8 + 8) + 8 + 6;
 
 // The per-cell PLM decisions of the current direction (adj_riemann_kernel ->
-// adj_recon_kernel) live in the face-state cotangent fields' spare slot 7.
+// adj_recon_all_kernel) live in the face-state cotangent fields' spare slot 7.
 unsigned* plm_codes(const AdjointState* a, int d) { return reinterpret_cast<unsigned*>(a->WbL[d].q[7]); }
 
 F8 state_at(const AdjointState* a, size_t idx) {
@@ -204,8 +204,9 @@ void stage_coeffs(int rk, int s, double& c0, double& c1, double& cL) {
 }
 
 // Riemann transpose of direction DIR on stream st (its own face-state
-// cotangents and PLM codes), then, separately, its reconstruction transpose,
-// which adds into Pb and so runs on the context stream in direction order.
+// cotangents and PLM codes); the reconstruction transposes of all directions
+// follow in one launch (adj_recon_all_kernel), which adds into Pb in
+// direction order.
 template <int NDIM, int RS, int DIR>
 void adj_riemann_dir(mhd_ctx* c, const F8& Xs, const F8& Ps, const F8& As, double dt, cudaStream_t st) {
   AdjointState* a = c->adj;
@@ -217,18 +218,6 @@ void adj_riemann_dir(mhd_ctx* c, const F8& Xs, const F8& Ps, const F8& As, doubl
   prof_mark(c, MHD_AKCLASS_RIEMANN);
   c->launches++;
 }
-template <int NDIM, int DIR>
-void adj_recon_dir(mhd_ctx* c) {
-  AdjointState* a = c->adj;
-  const Grid& g = c->g;
-  long long cells = 1;
-  for (int d = 0; d < 3; d++) cells *= d == DIR ? g.n[d] + 4 : (d < NDIM ? g.n[d] + 2 : 1);
-  adj_recon_kernel<DIR, NDIM><<<(int)((cells + 127) / 128), 128, 0, c->stream>>>(g, plm_codes(a, DIR), a->WbL[DIR],
-                                                                                   a->WbR[DIR], a->Pb);
-  prof_mark(c, MHD_AKCLASS_RECON);
-  c->launches++;
-}
-
 // Transpose of stage s at the stage input Xs: the cotangent Aout of the
 // stage output is distributed to A0 (U^n) and As (the stage input).
 template <int NDIM, int RS>
@@ -264,26 +253,27 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& I
     adj_riemann_dir<NDIM, RS, 0>(c, Xs, Ps, As, dt, c->stream);
     cudaStreamWaitEvent(c->stream, c->ev_join[0], 0);
     if constexpr (NDIM == 3) cudaStreamWaitEvent(c->stream, c->ev_join[1], 0);
-    adj_recon_dir<NDIM, 0>(c);
-    adj_recon_dir<NDIM, 1>(c);
-    if constexpr (NDIM == 3) adj_recon_dir<NDIM, 2>(c);
   } else {
     adj_riemann_dir<NDIM, RS, 0>(c, Xs, Ps, As, dt, c->stream);
-    adj_recon_dir<NDIM, 0>(c);
     adj_riemann_dir<NDIM, RS, 1>(c, Xs, Ps, As, dt, c->stream);
-    adj_recon_dir<NDIM, 1>(c);
-    if constexpr (NDIM == 3) {
-      adj_riemann_dir<NDIM, RS, 2>(c, Xs, Ps, As, dt, c->stream);
-      adj_recon_dir<NDIM, 2>(c);
-    }
+    if constexpr (NDIM == 3) adj_riemann_dir<NDIM, RS, 2>(c, Xs, Ps, As, dt, c->stream);
   }
-  adj_c2p_cells_kernel<NDIM><<<blocks_for(prim_work<NDIM>(g), 256), 256, 0, c->stream>>>(g, Xs, Ps, a->Pb, As);
+  // the reconstruction transposes of every direction (they read only what
+  // the Riemann transposes wrote) in one launch, adding in direction order
+  {
+    long long box = (long long)(g.n[0] + 4) * (g.n[1] + 4) * (NDIM == 3 ? g.n[2] + 4 : 1);
+    adj_recon_all_kernel<NDIM><<<(int)((box + 127) / 128), 128, 0, c->stream>>>(
+        g, plm_codes(a, 0), plm_codes(a, 1), plm_codes(a, NDIM == 3 ? 2 : 0), a->WbL[0], a->WbR[0], a->WbL[1],
+        a->WbR[1], a->WbL[NDIM == 3 ? 2 : 0], a->WbR[NDIM == 3 ? 2 : 0], a->Pb);
+    prof_mark(c, MHD_AKCLASS_RECON);
+    c->launches++;
+  }
   long long pad = (long long)g.ext[0] * g.ext[1] * g.ext[2];
-  adj_c2p_faces_kernel<NDIM><<<blocks_for(pad, 256), 256, 0, c->stream>>>(g, a->Pb, As);
+  adj_c2p_kernel<NDIM><<<blocks_for(pad, 256), 256, 0, c->stream>>>(g, Xs, Ps, a->Pb, As);
   prof_mark(c, MHD_AKCLASS_C2P);
   adj_ghost_shell_kernel<NDIM><<<blocks_for((long long)g.n[0] * g.n[1] * g.n[2], 256), 256, 0, c->stream>>>(g, As);
   prof_mark(c, MHD_AKCLASS_GHOST);
-  c->launches += 3;
+  c->launches += 2;
   CK(cudaGetLastError());
   return MHD_OK;
 }

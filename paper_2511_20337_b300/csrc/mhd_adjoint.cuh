@@ -608,16 +608,9 @@ static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, c
 // PLM decisions adj_riemann_kernel recorded for those cells.
 // ---------------------------------------------------------------------------
 template <int DIR, int NDIM>
-static __global__ void __launch_bounds__(128) adj_recon_kernel(Grid g, const unsigned* __restrict__ plm_codes, F8 WbL,
-                                                               F8 WbR, F8 Pb) {
+__device__ __forceinline__ void adj_recon_item(const Grid& g, const unsigned* __restrict__ plm_codes, const F8& WbL,
+                                               const F8& WbR, const F8& Pb, const int x[3]) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
-  int lo[3], ext[3];
-  sweep_box<DIR, NDIM>(g, lo, ext, -2, g.n[DIR] + 1);
-  const long long total = (long long)ext[0] * ext[1] * ext[2];
-  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (id >= total) return;
-  int x[3];
-  box_index(id, lo, ext, x);
   const int c = g.at(x[0], x[1], x[2]);
   const int st = g.stride(DIR);
   const int n = g.n[DIR];
@@ -650,51 +643,54 @@ static __global__ void __launch_bounds__(128) adj_recon_kernel(Grid g, const uns
 #pragma unroll
   for (int v = 0; v < 7; v++) Pb.q[slot[v]][c] += acc[v];
 }
-
-// ---------------------------------------------------------------------------
-// Primitive recovery, cells: v = m/rho, p = (G-1)(E - m.v/2 - B^2/2) with the
-// cell field B; a pressure raised to the floor passes no cotangent.  The
-// total cotangent of the cell field replaces Pb.q[4..6] for the face pass.
-// ---------------------------------------------------------------------------
+// Every direction's reconstruction transpose in one launch, over the union of
+// the directions' sweep boxes ([-2, n + 1] along the direction, the sweep's
+// pencils [-1, n] across it): each cell adds the directions' contributions to
+// its primitive cotangents in direction order, the same additions in the
+// same order as one launch per direction.
 template <int NDIM>
-static __global__ void adj_c2p_cells_kernel(Grid g, F8 S, F8 P, F8 Pb, F8 A) {
-  const long long total = prim_work<NDIM>(g);
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int nxp = g.n[0] + 2 * g.G, nyp = g.n[1] + 2 * g.G;
-    int i = (int)(id % nxp) - g.G;
-    long long r = id / nxp;
-    int j = (int)(r % nyp) - g.G;
-    int k = NDIM == 3 ? (int)(r / nyp) - g.G : 0;
-    int c = g.at(i, j, k);
-    const double rho = P.q[0][c], vx = P.q[1][c], vy = P.q[2][c], vz = P.q[3][c];
-    const double bx = P.q[4][c], by = P.q[5][c], bz = P.q[6][c];
-    double pb = Pb.q[7][c];
-    if (g.p_floor > 0.0) {
-      Prim8 V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1);
-      if (V.p < g.p_floor) pb = 0.0;
-    }
-    const double gp = g.gm1 * pb;
-    const double ir = 1.0 / rho;
-    const double vbx = Pb.q[1][c], vby = Pb.q[2][c], vbz = Pb.q[3][c];
-    const double v2 = (vx * vx + vy * vy) + vz * vz;
-    A.q[0][c] += (Pb.q[0][c] - ((vbx * vx + vby * vy) + vbz * vz) * ir) + 0.5 * gp * v2;
-    A.q[1][c] += vbx * ir - gp * vx;
-    A.q[2][c] += vby * ir - gp * vy;
-    A.q[3][c] += vbz * ir - gp * vz;
-    A.q[4][c] += gp;
-    const double bbx = Pb.q[4][c] - gp * bx, bby = Pb.q[5][c] - gp * by, bbz = Pb.q[6][c] - gp * bz;
-    Pb.q[4][c] = bbx;
-    Pb.q[5][c] = bby;
-    if (NDIM == 2) A.q[7][c] += bbz;
-    else Pb.q[6][c] = bbz;
-  }
+static __global__ void __launch_bounds__(128) adj_recon_all_kernel(Grid g, const unsigned* __restrict__ codes0,
+                                                                   const unsigned* __restrict__ codes1,
+                                                                   const unsigned* __restrict__ codes2, F8 WbL0,
+                                                                   F8 WbR0, F8 WbL1, F8 WbR1, F8 WbL2, F8 WbR2,
+                                                                   F8 Pb) {
+  int lo[3] = {-2, -2, NDIM == 3 ? -2 : 0};
+  int ext[3] = {g.n[0] + 4, g.n[1] + 4, NDIM == 3 ? g.n[2] + 4 : 1};
+  const long long total = (long long)ext[0] * ext[1] * ext[2];
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= total) return;
+  int x[3];
+  box_index(id, lo, ext, x);
+  // in the DIR box: [-2, n + 1] along DIR, [-1, n] along the other active axes
+  auto in_box = [&](int dir) {
+    for (int e = 0; e < NDIM; e++)
+      if (e != dir && (x[e] < -1 || x[e] > g.n[e])) return false;
+    return true;
+  };
+  if (in_box(0)) adj_recon_item<0, NDIM>(g, codes0, WbL0, WbR0, Pb, x);
+  if (in_box(1)) adj_recon_item<1, NDIM>(g, codes1, WbL1, WbR1, Pb, x);
+  if (NDIM == 3 && in_box(2)) adj_recon_item<NDIM == 3 ? 2 : 0, NDIM>(g, codes2, WbL2, WbR2, Pb, x);
 }
 
-// Primitive recovery, faces: each face field gets half the cell-field
-// cotangent of the padded cells on either side.
+// ---------------------------------------------------------------------------
+// Primitive recovery, v = m/rho, p = (G-1)(E - m.v/2 - B^2/2) with the cell
+// field B = the mean of its two faces, transposed in one launch: thread id
+// serves the padded cell and the faces with the same index.
+//   cell: the cotangents of rho, m, E (2D: and of the cell B_z) from the
+//         primitive cotangents Pb; a pressure raised to the floor passes none;
+//   face: half of each adjacent padded cell's field cotangent
+//         Pb.q[4 + d] - (G-1) pb B_d, formed by the face itself.
 template <int NDIM>
-static __global__ void adj_c2p_faces_kernel(Grid g, F8 Pb, F8 A) {
+__device__ __forceinline__ double adj_c2p_gp(const Grid& g, const F8& S, const F8& P, const F8& Pb, int c) {
+  double pb = Pb.q[7][c];
+  if (g.p_floor > 0.0) {
+    Prim8 V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], P.q[4][c], P.q[5][c], P.q[6][c], g.gm1);
+    if (V.p < g.p_floor) pb = 0.0;
+  }
+  return g.gm1 * pb;
+}
+template <int NDIM>
+static __global__ void adj_c2p_kernel(Grid g, F8 S, F8 P, F8 Pb, F8 A) {
   int lo[3] = {-g.G, -g.G, NDIM == 3 ? -g.G : 0};
   int ext[3] = {g.n[0] + 2 * g.G + 1, g.n[1] + 2 * g.G + 1, NDIM == 3 ? g.n[2] + 2 * g.G + 1 : 1};
   const long long total = (long long)ext[0] * ext[1] * ext[2];
@@ -702,7 +698,24 @@ static __global__ void adj_c2p_faces_kernel(Grid g, F8 Pb, F8 A) {
        id += (long long)gridDim.x * blockDim.x) {
     int x[3];
     box_index(id, lo, ext, x);
-    const int f = g.at(x[0], x[1], x[2]);
+    const int c = g.at(x[0], x[1], x[2]);
+    bool cell = true;  // a padded cell: every index within [-G, n + G - 1]
+#pragma unroll
+    for (int e = 0; e < NDIM; e++)
+      if (x[e] > g.n[e] + g.G - 1) cell = false;
+    if (cell) {
+      const double rho = P.q[0][c], vx = P.q[1][c], vy = P.q[2][c], vz = P.q[3][c];
+      const double gp = adj_c2p_gp<NDIM>(g, S, P, Pb, c);
+      const double ir = 1.0 / rho;
+      const double vbx = Pb.q[1][c], vby = Pb.q[2][c], vbz = Pb.q[3][c];
+      const double v2 = (vx * vx + vy * vy) + vz * vz;
+      A.q[0][c] += (Pb.q[0][c] - ((vbx * vx + vby * vy) + vbz * vz) * ir) + 0.5 * gp * v2;
+      A.q[1][c] += vbx * ir - gp * vx;
+      A.q[2][c] += vby * ir - gp * vy;
+      A.q[3][c] += vbz * ir - gp * vz;
+      A.q[4][c] += gp;
+      if (NDIM == 2) A.q[7][c] += Pb.q[6][c] - gp * P.q[6][c];
+    }
 #pragma unroll
     for (int d = 0; d < NDIM; d++) {
       bool ok = true;  // the transverse indices must be those of padded cells
@@ -711,12 +724,16 @@ static __global__ void adj_c2p_faces_kernel(Grid g, F8 Pb, F8 A) {
         if (e != d && x[e] > g.n[e] + g.G - 1) ok = false;
       if (!ok) continue;
       double acc = 0.0;
-      if (x[d] <= g.n[d] + g.G - 1) acc += Pb.q[4 + d][f];
-      if (x[d] - 1 >= -g.G) acc += Pb.q[4 + d][f - g.stride(d)];
-      A.q[5 + d][f] += 0.5 * acc;
+      if (x[d] <= g.n[d] + g.G - 1) acc += Pb.q[4 + d][c] - adj_c2p_gp<NDIM>(g, S, P, Pb, c) * P.q[4 + d][c];
+      if (x[d] - 1 >= -g.G) {
+        const int cm = c - g.stride(d);
+        acc += Pb.q[4 + d][cm] - adj_c2p_gp<NDIM>(g, S, P, Pb, cm) * P.q[4 + d][cm];
+      }
+      A.q[5 + d][c] += 0.5 * acc;
     }
   }
 }
+
 
 // Chain of the initial conserved cotangent to the initial primitives with p
 // and B held: m = rho v, E = p/(G-1) + rho v^2/2 + B^2/2.
