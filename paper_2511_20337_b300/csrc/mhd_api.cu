@@ -323,7 +323,7 @@ void run_step(mhd_ctx* c, bool device_dt) {
 
 // Default sweep segment length: each segment repeats one face and one
 // reconstruction at its end, so long segments waste less, while short ones
-// give more threads.  Take the longest (2..128) that still leaves about eight
+// give more threads.  Take the longest (2..256) that still leaves about eight
 // waves of 384-thread SM loads in the sweep with the fewest faces.
 static long long faces_per_thread_target(const Grid& g) {
   int dev = 0, sms = 148;
@@ -340,7 +340,7 @@ static long long faces_per_thread_target(const Grid& g) {
 }
 static int default_seglen(const Grid& g) {
   const long long per_thread = faces_per_thread_target(g);
-  return (int)(per_thread < 2 ? 2 : (per_thread > 128 ? 128 : per_thread));
+  return (int)(per_thread < 2 ? 2 : (per_thread > 256 ? 256 : per_thread));
 }
 // Sweeps side by side when even segments of 2 faces leave fewer than about
 // eight waves of threads in one sweep (CT only).
