@@ -170,7 +170,9 @@ int mhd_last_dt(mhd_ctx* ctx, double* dt_out);
 /* Wait for the context's stream and report the first device-side error of the
  * steps since the last call: MHD_OK, or MHD_ERR_UNPHYSICAL with *bad_cell
  * (may be NULL) = the smallest flat interior index k*ny*nx + j*nx + i of a
- * cell whose recovered density or pressure was not positive.  Clears it. */
+ * cell whose recovered density or pressure was not positive, or
+ * MHD_ERR_TIMEOUT (a grid barrier of the fused stage gave up; *bad_cell = -1;
+ * see mhd_set_fused), or MHD_ERR_DIVB.  Clears it. */
 int mhd_status(mhd_ctx* ctx, long long* bad_cell);
 
 /* div B monitor (CT only; MHD_ERR_ARG with GLM).  Constrained transport keeps
@@ -204,7 +206,7 @@ int mhd_counters(mhd_ctx* ctx, long long* recon_fallbacks, long long* pressure_f
 long long mhd_launch_count(const mhd_ctx* ctx);
 
 /* Sweep segment length: the number of faces one thread of a sweep marches
- * (default: the longest of 2..64 that leaves about eight waves of threads
+ * (default: the longest of 2..256 that leaves about eight waves of threads
  * on the device in the sweep with the fewest faces).  Shorter segments give
  * more threads, longer ones fewer repeated Riemann solves and reconstructions
  * at segment ends (one each per segment); the result does not depend on it.
@@ -216,12 +218,54 @@ int mhd_set_seglen(mhd_ctx* ctx, int seglen);
 int mhd_get_seglen(const mhd_ctx* ctx, int* seglen_out);
 
 /* Choose the segment length by timing two CFL steps for each of 2, 4, 8, 12,
- * 16, 20, 24, 28, 32, 40, 48, 64 and the lengths that split the longest
+ * 16, 20, 24, 28, 32, 40, 48, 64, 96, 128 and the lengths that split the longest
  * pencil's faces into 4..12 equal segments (up to twice the longest axis) on
  * the current state, which is restored
  * afterwards together with the time and counters; *seglen_out (may be NULL)
  * receives the choice.  Sync; allocates a temporary copy of the state. */
 int mhd_autotune(mhd_ctx* ctx, int* seglen_out);
+
+/* ---- fused stage (2D, CT) ----
+ *
+ * On 2D constrained-transport grids small enough that the y sweep runs beside
+ * the x sweep (below about 670^2 cells), each RK stage (Eq. RK3, or the
+ * two-stage SSP-RK2) is one cooperative kernel launch instead of one launch
+ * per phase.  Its phases -- ghost fill, primitive recovery with the CFL step
+ * of mhd_cfl_dt, the two sweeps (Eq. FV), the UCT edge fields and the CT + RK
+ * combine (§2.2) -- execute the same item arithmetic in the same order, separated by
+ * grid-wide barriers, so the state equals the per-phase launches' to the bit.
+ * It is on by default where the device supports cooperative launches.
+ * Profiling (mhd_profile_steps) and the adjoint's recompute context use the
+ * per-phase launches.
+ *
+ * Every barrier wait is bounded (default 1 s).  A wait that runs out sets
+ * MHD_ERR_TIMEOUT in the device status; every block of the launch returns at
+ * its next barrier, later stage launches return at once, and the next sync
+ * call (mhd_status, mhd_get_conserved) reports it and re-arms the barrier.
+ * The conserved state is then that of the last completed step (a stage writes
+ * its output only after its last barrier); the time and counters may include
+ * the failed step's.
+ *
+ * mhd_set_fused(ctx, on): 1 = fused stages (MHD_ERR_ARG where the context does
+ *   not qualify: 3D, GLM, larger 2D grids, no cooperative launch), 0 = one
+ *   launch per phase.  Sync.
+ * mhd_get_fused(ctx, &on, &blocks): whether the fused stage is on, and the
+ *   blocks of its launch (0 where the context does not qualify; blocks may be
+ *   NULL).
+ * mhd_set_wait_limit(ctx, seconds): the bound of every wait, 0 < seconds <= 60.
+ *   Sync.
+ * mhd_inject_skip_arrive(ctx, block, barrier): fault injection for tests:
+ *   from the next launch on, block `block` does not arrive at barrier
+ *   `barrier` (counted from 0 within each stage launch) of every stage, so
+ *   that barrier's wait runs out; block = -1 turns it off.  A timeout report
+ *   by mhd_status also turns it off.  Sync.
+ * mhd_fused_waits(ctx, &n): the barriers of the last fused stage launch
+ *   that completed its edge fields.  Sync. */
+int mhd_set_fused(mhd_ctx* ctx, int on);
+int mhd_get_fused(const mhd_ctx* ctx, int* on_out, int* blocks_out);
+int mhd_set_wait_limit(mhd_ctx* ctx, double seconds);
+int mhd_inject_skip_arrive(mhd_ctx* ctx, int block, int barrier);
+int mhd_fused_waits(mhd_ctx* ctx, int* waits_out);
 
 /* Static text for a return code. */
 const char* mhd_strerror(int code);

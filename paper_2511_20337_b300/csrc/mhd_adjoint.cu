@@ -149,6 +149,9 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
     if (rc) { adjoint_free(c); return rc; }
     a->shadow->g = c->g;
     a->shadow->seglen = c->seglen;
+    // the recomputes run beside the forward and reverse passes: one
+    // cooperative grid at a time on the device, the forward's
+    a->shadow->fused = false;
     bool ok = true;
     for (cudaEvent_t* e : {&a->ev_fwd, &a->ev_rec[0], &a->ev_rec[1], &a->ev_rev[0], &a->ev_rev[1]})
       ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;

@@ -211,6 +211,10 @@ int stage_mode(int rk, int s) {
 }
 
 void run_stage_regs(mhd_ctx* c, int s, const F8& U0, const F8& Us, const F8& Out, bool cfl) {
+  if (fused_now(c)) {
+    coop_stage(c, s, U0, Us, Out, cfl);
+    return;
+  }
   ghost_fill(c, Us);
   prim(c, Us, cfl, s > 0);
   sweeps(c, Us);
@@ -453,6 +457,11 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
       return MHD_ERR_CUDA;
     }
   }
+  rc = coop_init(c);
+  if (rc) {
+    mhd_destroy(c);
+    return rc;
+  }
   c->launches_per_step = -1;
   *out = c;
   return MHD_OK;
@@ -463,6 +472,7 @@ int mhd_destroy(mhd_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->graph_ready) cudaGraphExecDestroy(c->graph);
   adjoint_free(c);
+  coop_free(c);
   cudaFree(c->pool);
   cudaFree(c->sc);
   for (int d = 0; d < 2; d++) {
@@ -543,12 +553,16 @@ int mhd_status(mhd_ctx* c, long long* bad_cell) {
   CK(cudaStreamSynchronize(c->stream));
   DevScalars h;
   CK(copy_sync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  if (bad_cell) *bad_cell = h.status ? h.bad_cell : -1;
+  if (bad_cell) *bad_cell = h.status && h.status != MHD_ERR_TIMEOUT ? h.bad_cell : -1;
   if (h.status) {
     int st = h.status;
     h.status = 0;
     h.bad_cell = LLONG_MAX;
     CK(copy_sync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    if (st == MHD_ERR_TIMEOUT) {
+      int rc = coop_clear(c);
+      if (rc) return rc;
+    }
     return st;
   }
   return MHD_OK;

@@ -8,6 +8,7 @@
 
 namespace mhd {
 struct AdjointState;
+struct CoopBar;
 }
 
 struct mhd_ctx {
@@ -51,6 +52,13 @@ struct mhd_ctx {
   // div B monitor at the end of every step (CT): 0 = off, else the tolerance
   // on max |div B| h / max |B_c| above which a step reports MHD_ERR_DIVB
   double divb_tol;
+  // fused stage (2D CT grids with the side-by-side sweep buffers): each RK
+  // stage is one cooperative launch of coop_blocks blocks whose phases are
+  // separated by grid barriers in *bar, every wait bounded by coop_limit_ns
+  bool fused;
+  int coop_blocks;
+  unsigned long long coop_limit_ns;
+  mhd::CoopBar* bar;
 };
 
 namespace mhd {
@@ -71,5 +79,12 @@ void run_step(mhd_ctx* c, bool device_dt);
 void divb_check(mhd_ctx* c, double tol);            // the div B monitor on U[0] (tol 0: measure only)
 void adjoint_free(mhd_ctx* c);                       // defined in mhd_adjoint.cu
 bool split_now(const mhd_ctx* c);                    // sweeps side by side in this launch sequence
+int sweep_rs(const mhd_config* cfg);                 // the sweeps' Riemann-solver template value
+// fused stage (mhd_coop.cu)
+int coop_init(mhd_ctx* c);                           // eligibility, barrier, blocks; fused on where eligible
+void coop_free(mhd_ctx* c);
+bool fused_now(const mhd_ctx* c);                    // fused stages in this launch sequence
+void coop_stage(mhd_ctx* c, int s, const F8& U0, const F8& Us, const F8& Out, bool cfl);
+int coop_clear(mhd_ctx* c);                          // the barrier's initial state after a timeout
 
 }  // namespace mhd

@@ -45,7 +45,8 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_domain_brick", "mhd_domain_halo", "mhd_domain_create", "mhd_domain_destroy",
            "mhd_domain_set_conserved", "mhd_domain_get_conserved", "mhd_domain_cfl_dt", "mhd_domain_step",
            "mhd_domain_advance", "mhd_domain_get_time", "mhd_domain_status", "mhd_domain_counters",
-           "mhd_domain_set_seglen", "mhd_domain_launch_count", "mhd_domain_halo_bytes")
+           "mhd_domain_set_seglen", "mhd_domain_launch_count", "mhd_domain_halo_bytes",
+           "mhd_set_fused", "mhd_get_fused", "mhd_set_wait_limit", "mhd_inject_skip_arrive", "mhd_fused_waits")
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -152,6 +153,11 @@ def lib():
             "mhd_domain_set_seglen": (I, [P, I]),
             "mhd_domain_launch_count": (ctypes.c_longlong, [P]),
             "mhd_domain_halo_bytes": (ctypes.c_longlong, [P]),
+            "mhd_set_fused": (I, [P, I]),
+            "mhd_get_fused": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "mhd_set_wait_limit": (I, [P, D]),
+            "mhd_inject_skip_arrive": (I, [P, I, I]),
+            "mhd_fused_waits": (I, [P, ctypes.POINTER(I)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -352,6 +358,31 @@ class Sim:
         s = ctypes.c_int()
         _check(lib().mhd_autotune(self.h, ctypes.byref(s)), "mhd_autotune")
         return s.value
+
+    def set_fused(self, on):
+        """One cooperative launch per RK stage (2D CT grids that qualify) or one per phase."""
+        _check(lib().mhd_set_fused(self.h, 1 if on else 0), "mhd_set_fused")
+
+    @property
+    def fused(self):
+        """(on, blocks): whether the fused stage is on and its launch's block count (0: not eligible)."""
+        on, blocks = ctypes.c_int(), ctypes.c_int()
+        _check(lib().mhd_get_fused(self.h, ctypes.byref(on), ctypes.byref(blocks)), "mhd_get_fused")
+        return bool(on.value), blocks.value
+
+    def set_wait_limit(self, seconds):
+        """Bound of every grid-barrier wait of the fused stage."""
+        _check(lib().mhd_set_wait_limit(self.h, float(seconds)), "mhd_set_wait_limit")
+
+    def inject_skip_arrive(self, block, barrier):
+        """Fault injection: block `block` skips its arrival at barrier `barrier` of each stage (-1: off)."""
+        _check(lib().mhd_inject_skip_arrive(self.h, int(block), int(barrier)), "mhd_inject_skip_arrive")
+
+    def fused_waits(self):
+        """Barriers per stage of the last fused launch."""
+        n = ctypes.c_int()
+        _check(lib().mhd_fused_waits(self.h, ctypes.byref(n)), "mhd_fused_waits")
+        return n.value
 
     def set_divb_check(self, tol):
         """Check max |div B| h / max |B_c| at the end of every step (tol > 0; 0 = off)."""
