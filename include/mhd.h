@@ -222,7 +222,9 @@ int mhd_get_seglen(const mhd_ctx* ctx, int* seglen_out);
  * pencil's faces into 4..12 equal segments (up to twice the longest axis) on
  * the current state, which is restored
  * afterwards together with the time and counters; *seglen_out (may be NULL)
- * receives the choice.  Sync; allocates a temporary copy of the state. */
+ * receives the choice.  Where the fused stage is available (see below) both
+ * launch forms are timed and the faster is kept (mhd_get_fused reports it).
+ * Sync; allocates a temporary copy of the state. */
 int mhd_autotune(mhd_ctx* ctx, int* seglen_out);
 
 /* ---- fused stage (2D, CT) ----
@@ -234,7 +236,10 @@ int mhd_autotune(mhd_ctx* ctx, int* seglen_out);
  * of mhd_cfl_dt, the two sweeps (Eq. FV), the UCT edge fields and the CT + RK
  * combine (§2.2) -- execute the same item arithmetic in the same order, separated by
  * grid-wide barriers, so the state equals the per-phase launches' to the bit.
- * It is on by default where the device supports cooperative launches.
+ * It is on by default for grids of up to 256^2 cells (where it was measured
+ * level with or faster than the per-phase launches) on devices with
+ * cooperative launches; mhd_autotune picks the faster form for any eligible
+ * grid.
  * Profiling (mhd_profile_steps) and the adjoint's recompute context use the
  * per-phase launches.
  *

@@ -782,20 +782,26 @@ int mhd_autotune(mhd_ctx* c, int* seglen_out) {
   cudaEventCreate(&e1);
   float best = 1e30f;
   int pick = c->seglen, rc = MHD_OK;
-  for (int i = 0; i < ncand && rc == MHD_OK; i++) {
-    if (cand[i] > 2 * longest) break;
-    c->seglen = cand[i];
-    run_step(c, true);  // warm
-    cudaEventRecord(e0, c->stream);
-    run_step(c, true);
-    run_step(c, true);
-    cudaEventRecord(e1, c->stream);
-    cudaError_t e = cudaEventSynchronize(e1);
-    if (e != cudaSuccess) { rc = cuda_err(e); break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; pick = cand[i]; }
-    cudaMemcpyAsync(c->U[0].q[0], backup, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  bool pick_fused = c->fused;
+  // both launch forms where the fused stage is available (2D CT grids)
+  const int nforms = c->bar ? 2 : 1;
+  for (int f = 0; f < nforms && rc == MHD_OK; f++) {
+    if (c->bar) c->fused = f == 1;
+    for (int i = 0; i < ncand && rc == MHD_OK; i++) {
+      if (cand[i] > 2 * longest) break;
+      c->seglen = cand[i];
+      run_step(c, true);  // warm
+      cudaEventRecord(e0, c->stream);
+      run_step(c, true);
+      run_step(c, true);
+      cudaEventRecord(e1, c->stream);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) { rc = cuda_err(e); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; pick = cand[i]; pick_fused = c->fused; }
+      cudaMemcpyAsync(c->U[0].q[0], backup, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -803,6 +809,7 @@ int mhd_autotune(mhd_ctx* c, int* seglen_out) {
   cudaFree(backup);
   CK(copy_sync(c->sc, &sc_h, sizeof(sc_h), cudaMemcpyHostToDevice, c->stream));
   c->seglen = pick;
+  c->fused = pick_fused;
   if (c->graph_ready) {
     cudaGraphExecDestroy(c->graph);
     c->graph_ready = false;

@@ -13,6 +13,11 @@ using namespace mhd;
 namespace mhd {
 
 constexpr unsigned long long kDefaultWaitNs = 1000000000ull;  // 1 s
+// Fused by default up to 256^2 cells: measured (PLM + HLLD + RK2, each form
+// at its best segment length) level with or faster than the per-phase
+// launches from 64^2 to 256^2 and within +-7 % above; mhd_autotune decides
+// for any eligible grid.
+constexpr long long kFusedDefaultCells = 256LL * 256;
 
 template <int RECON, int RS>
 void* coop_fn() {
@@ -43,7 +48,8 @@ static CoopBar bar_reset(unsigned long long limit_ns) {
 }
 
 // 2D CT grids with the side-by-side sweeps' buffers qualify; the launch takes
-// every block the device can hold at once (the cooperative limit).
+// every block the device can hold at once (the cooperative limit).  On by
+// default for grids up to kFusedDefaultCells.
 int coop_init(mhd_ctx* c) {
   c->fused = false;
   c->coop_blocks = 0;
@@ -63,7 +69,7 @@ int coop_init(mhd_ctx* c) {
   const CoopBar h = bar_reset(c->coop_limit_ns);
   CK(copy_sync(c->bar, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
   c->coop_blocks = per_sm * sms;
-  c->fused = true;
+  c->fused = (long long)c->g.n[0] * c->g.n[1] <= kFusedDefaultCells;
   return MHD_OK;
 }
 
@@ -93,6 +99,12 @@ void coop_stage(mhd_ctx* c, int s, const F8& U0, const F8& Us, const F8& Out, bo
   a.mode = stage_mode(c->cfg.rk, s);
   a.cfl = cfl ? 1 : 0;
   a.fast = s > 0 ? 1 : 0;
+  // all axes periodic: each stage leaves the periodic images of its output,
+  // which is the next stage's input, so the stages after the first skip
+  // their ghost phase (the first keeps it: the host may have set U^n)
+  const bool periodic = c->g.periodic[0] && c->g.periodic[1];
+  a.ghost_out = periodic && s + 1 < c->cfg.rk ? 1 : 0;
+  a.ghost_in = periodic && s > 0 ? 1 : 0;
   void* args[] = {&a};
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)c->coop_blocks);

@@ -109,6 +109,8 @@ struct CoopStage {
   double* lam;      // near-IEEE CFL rates (cfl)
   CoopBar* bar;
   int seglen, mode, cfl, fast;
+  int ghost_in;     // Us's ghost zones are already filled (the previous fused stage's images)
+  int ghost_out;    // write the periodic images of Out (all axes periodic)
 };
 
 template <int RECON, int RS>
@@ -131,7 +133,9 @@ static __global__ void __launch_bounds__(kCoopThreads, 1) coop_stage_kernel(Coop
   const long long t0 = ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
   int k = 0;
   // ghost zones of Us: periodic axes, then outflow axes (copy, then the normal field)
-  if (g.periodic[0] && g.periodic[1]) {
+  if (a.ghost_in) {
+    // the previous stage of this step wrote them with its output
+  } else if (g.periodic[0] && g.periodic[1]) {
     const long long w = ghost_shell_work<2>(g);
     for (long long id = t0; id < w; id += T) ghost_shell_item<2>(g, a.Us, id);
     if (!coop_sync(a.bar, a.sc, k++, skip_at)) return;
@@ -239,6 +243,21 @@ static __global__ void __launch_bounds__(kCoopThreads, 1) coop_stage_kernel(Coop
         for (int q = 0; q < 6; q++) a.L.q[q][c] = -fmul(dtdx, a.L.q[q][c]);
       }
       ct_rk_item<2, true>(g, a.U0, a.Us, a.Out, a.L, a.E, dt, a.mode, id, &a.D, &a.D);
+      if (a.ghost_out && i < g.n[0] && j < g.n[1]) {
+        // every ghost slot whose wrapped position is (i, j) takes its values
+        // (the copies ghost_shell_item makes in the next stage's ghost phase)
+        const int c = g.at(i, j, 0);
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) v[q] = a.Out.q[q][c];
+        for (int jj = j - g.n[1] * ((j + g.G) / g.n[1]); jj <= g.n[1] + g.G; jj += g.n[1])
+          for (int ii = i - g.n[0] * ((i + g.G) / g.n[0]); ii <= g.n[0] + g.G; ii += g.n[0]) {
+            if (ii == i && jj == j) continue;
+            const int d = g.at(ii, jj, 0);
+#pragma unroll
+            for (int q = 0; q < 8; q++) a.Out.q[q][d] = v[q];
+          }
+      }
     }
   }
   coop_exit(a.bar);

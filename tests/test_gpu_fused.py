@@ -97,15 +97,45 @@ def test_fused_eligibility(mhd):
             s.set_wait_limit(bad)
     with pytest.raises(mhd.MhdError):
         s.inject_skip_arrive(s.fused[1], 0)   # no such block
+    # above 256^2 cells: eligible, off by default, on when asked
+    big_cfg, big_st = W.orszag_tang_2d(300)
+    b = mhd.Sim(big_cfg, big_st)
+    on, blocks = b.fused
+    assert not on and blocks >= 148
+    b.set_fused(True)
+    assert b.fused == (True, blocks)
+
+
+def test_autotune_picks_a_form_and_restores_the_state(mhd):
+    cfg, st = W.orszag_tang_2d(96)
+    g = mhd.Sim(cfg, st)
+    g.advance(3)
+    before, t = g.get_conserved(), g.time
+    seglen = g.autotune()
+    assert seglen >= 2 and g.seglen == seglen
+    on, blocks = g.fused
+    assert blocks >= 148
+    after = g.get_conserved()
+    for k in before:
+        np.testing.assert_array_equal(after[k], before[k], err_msg=k)
+    assert g.time == t
+    g.advance(2)
+    ref = mhd.Sim(cfg, st)
+    ref.advance(5)
+    want, got = ref.get_conserved(), g.get_conserved()
+    for k in want:
+        np.testing.assert_array_equal(got[k], want[k], err_msg=k)
 
 
 def test_barrier_count_per_stage(mhd):
     cfg, st = W.orszag_tang_2d(32)
     g = mhd.Sim(cfg, st)
     g.advance(1)
-    assert g.fused_waits() == 4            # last stage: ghost, primitives, sweeps, edge fields
+    # last stage: primitives, sweeps, edge fields (its ghost zones came with
+    # the first stage's output)
+    assert g.fused_waits() == 3
     g.step(1e-3)
-    assert g.fused_waits() == 4
+    assert g.fused_waits() == 3
     ocfg, ost = rand2d((20, 24), 2, bc="outflow")
     h = mhd.Sim(ocfg, ost)
     h.advance(1)
