@@ -41,7 +41,7 @@ __device__ __forceinline__ bool edge_valid(const Grid& g, int C, int i, int j, i
 // 0 = neither (opposite signs or a zero argument, where the value is 0).
 __device__ __forceinline__ int minmod_pick(double a, double b) {
   if (!((gt0(a) && gt0(b)) || (lt0(a) && lt0(b)))) return 0;
-  return (bits(b) & kMag) < (bits(a) & kMag) ? 2 : 1;
+  return bits(b) < bits(a) ? 2 : 1;  // same signs: the bits order like the magnitudes (see minmod)
 }
 
 __device__ __forceinline__ void box_index(long long id, const int lo[3], const int ext[3], int x[3]) {

@@ -227,7 +227,7 @@ static __global__ void __launch_bounds__(kCoopThreads, 1) coop_stage_kernel(Coop
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) a.bar->waits = k;
   // CT + RK combine (the stage's only write of its output register).  The x
-  // increment -fmul(dt/dx, D_x) is the value the x sweep stores when it
+  // increment fmul(-dt/dx, D_x) is the value the x sweep stores when it
   // scales its own differences (accumulate mode 0), formed in the same two
   // roundings, so the combine is that of the side-by-side sweeps to the bit.
   {
@@ -240,7 +240,7 @@ static __global__ void __launch_bounds__(kCoopThreads, 1) coop_stage_kernel(Coop
       if (i < g.n[0] && j < g.n[1]) {
         const int c = g.at(i, j, 0);
 #pragma unroll
-        for (int q = 0; q < 6; q++) a.L.q[q][c] = -fmul(dtdx, a.L.q[q][c]);
+        for (int q = 0; q < 6; q++) a.L.q[q][c] = fmul(-dtdx, a.L.q[q][c]);
       }
       ct_rk_item<2, true>(g, a.U0, a.Us, a.Out, a.L, a.E, dt, a.mode, id, &a.D, &a.D);
       if (a.ghost_out && i < g.n[0] && j < g.n[1]) {

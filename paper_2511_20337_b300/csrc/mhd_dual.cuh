@@ -126,5 +126,7 @@ __device__ __forceinline__ D3 imax(const D3& a, const D3& b) { return order_key(
 __device__ __forceinline__ D3 imax_pos(const D3& a, const D3& b) { return bits(a.v) < bits(b.v) ? b : a; }
 __device__ __forceinline__ bool lt_pos(const D3& a, const D3& b) { return bits(a.v) < bits(b.v); }
 __device__ __forceinline__ D3 times_sign(const D3& x, const D3& s) { return gt0(s.v) ? x : -x; }
+__device__ __forceinline__ D3 neg_if(const D3& x, bool c) { return c ? -x : x; }
+__device__ __forceinline__ bool lt_abs(const D3& x, const D3& y) { return lt_abs(x.v, y.v); }
 
 }  // namespace mhd

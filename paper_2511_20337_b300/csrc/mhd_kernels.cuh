@@ -273,7 +273,7 @@ __device__ __forceinline__ double prim_item(const Grid& g, const F8& S, const F8
   if (FAST) {
     double pb;
     V = c2p_fast(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1, pb);
-    if (lt_pos(dabs(fsub(V.p, g.p_floor)), pb) || lt_pos(dabs(V.p), pb))
+    if (lt_abs(fsub(V.p, g.p_floor), pb) || lt_abs(V.p, pb))
       V.p = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1).p;
   } else {
     V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], bx, by, bz, g.gm1);
@@ -678,7 +678,7 @@ __device__ __forceinline__ void sweep_body(const Grid& g, const double* __restri
       if (NDIM == 2) dv[5] = (DIR == 0) ? fsub(F.f[5], Fprev[5]) : fsub(F.f[4], Fprev[4]);
 #pragma unroll
       for (int q = 0; q < NV; q++)  // explicit roundings: the same in every kernel that inlines this
-        L.q[q][cc] = accumulate == 2 ? dv[q] : (accumulate ? fma(-dtdx, dv[q], L.q[q][cc]) : -fmul(dtdx, dv[q]));
+        L.q[q][cc] = accumulate == 2 ? dv[q] : (accumulate ? fma(-dtdx, dv[q], L.q[q][cc]) : fmul(-dtdx, dv[q]));
     }
 #pragma unroll
     for (int v = 0; v < 7; v++) {

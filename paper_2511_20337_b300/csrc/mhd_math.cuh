@@ -184,6 +184,16 @@ __device__ __forceinline__ double dabs(double x) { return from_bits(bits(x) & kM
 __device__ __forceinline__ double times_sign(double x, double s) {
   return from_bits(bits(x) ^ (gt0(s) ? 0LL : kSign));
 }
+// -x when c, else x (the sign bit, on the integer pipes: a negated value that
+// is selected or stored would otherwise be formed by an FP64 add)
+__device__ __forceinline__ double neg_if(double x, bool c) { return from_bits(bits(x) ^ (c ? kSign : 0LL)); }
+// lt_pos(|x|, y): false for y < 0, else |x| < y, with the bit patterns
+// shifted left by one (dropping the sign), which compare like the
+// magnitudes.  Clearing the sign bit with a mask instead is turned by the
+// compiler into an FP64 absolute value.
+__device__ __forceinline__ bool lt_abs(double x, double y) {
+  return bits(y) >= 0 && ((unsigned long long)bits(x) << 1) < ((unsigned long long)bits(y) << 1);
+}
 
 // sqrt(x) and 1/sqrt(x) for x > 0 from the hardware's ~20-bit reciprocal
 // square-root seed (PTX rsqrt.approx.ftz.f64), refined by one third-order
@@ -456,7 +466,7 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
   T eL(1.0), eR(1.0);  // star ratios B*_t / B_t (UCT weights)
   {
     T rsm = mul_rn(rsL, smL), D = fsub(rsm, bn2);
-    if (lt_pos(dabs(D), kmul(RK_EPS, rsm))) {
+    if (lt_abs(D, kmul(RK_EPS, rsm))) {
       vsL = L.v; wsL = L.w; b1sL = L.b1; b2sL = L.b2;
     } else {
       T iD = rcp(D);
@@ -471,7 +481,7 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
   }
   {
     T rsm = mul_rn(rsR, smR), D = fsub(rsm, bn2);
-    if (lt_pos(dabs(D), kmul(RK_EPS, rsm))) {
+    if (lt_abs(D, kmul(RK_EPS, rsm))) {
       vsR = R.v; wsR = R.w; b1sR = R.b1; b2sR = R.b2;
     } else {
       T iD = rcp(D);
@@ -529,8 +539,9 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
       T b1ss = fmul(fma(sqL, b1sR, fma(sqR, b1sL, times_sign(fmul(sq2, fsub(vsR, vsL)), bn))), isum);
       T b2ss = fmul(fma(sqL, b2sR, fma(sqR, b2sL, times_sign(fmul(sq2, fsub(wsR, wsL)), bn))), isum);
       T vBss = fma(SM, bn, fma(vss, b1ss, fmul(wss, b2ss)));
-      T sqa = left ? -sqL : sqR;
-      T Ess = fma(sqa, times_sign(fsub(vBs, vBss), bn), Es);
+      // Es + s_a sign(B_n) (vB* - vB**) with s_a = -sqrt(rho*_L) on the left, sqrt(rho*_R) on the
+      // right: both signs go into one flip of the difference
+      T Ess = fma(left ? sqL : sqR, neg_if(fsub(vBs, vBss), gt0(bn) == left), Es);
       // F += S*_a (U** - U*): the density and normal momentum are continuous
       F.f[2] = fma(Ss, fma(rhos, vss, -Us[2]), F.f[2]);
       F.f[3] = fma(Ss, fma(rhos, wss, -Us[3]), F.f[3]);
@@ -546,11 +557,15 @@ __device__ __forceinline__ void riemann_hlld(const W7T<T>& L, const W7T<T>& R, T
 // minus = V^R_{i-1/2}.
 // ---------------------------------------------------------------------------
 // minmod(a, b): 0 when the signs differ (or either is 0), else the argument of
-// smaller magnitude, on integer pipes.
+// smaller magnitude, on integer pipes.  For two doubles of the same sign the
+// bit patterns, read as signed integers, order like the magnitudes (the
+// magnitude bits sit below the sign bit), so no mask is needed; a masked
+// compare (bits & 0x7fff...) is turned by the compiler into two FP64 absolute
+// values, 2 of the FP64 pipe's instructions per call.
 __device__ __forceinline__ double minmod(double a, double b) {
   long long ia = bits(a), ib = bits(b);
   if ((ia ^ ib) < 0) return 0.0;
-  return (ib & kMag) < (ia & kMag) ? b : a;
+  return ib < ia ? b : a;
 }
 
 // PLM from the two one-sided differences of cell value s2 (a marching sweep
@@ -576,7 +591,7 @@ __device__ __forceinline__ void recon_plm(double s1, double s2, double s3, doubl
 __device__ __forceinline__ void wenoz_from_indicators(double a0, double a1, double a2, double a3, double a4,
                                                       double b0, double b1, double b2, double& plus,
                                                       double& minus) {
-  const double tau = dabs(fsub(b0, b2));
+  const double tau = fsub(b0, b2);  // tau5 up to its sign, which the squares of r_k drop
   const double weps = rk(RK_WEPS);
   const double r0 = fmul(tau, rcp(fadd(b0, weps)));
   const double r1 = fmul(tau, rcp(fadd(b1, weps)));
@@ -697,7 +712,7 @@ __device__ __forceinline__ void recon_ppm(double s0, double s1, double s2, doubl
     double v6 = kmul(RK_6, fma(rk(RK_MHALF), fadd(vm, vp), s2));
     double x = fmul(dv, v6), y = fmul(dv, dv);
     if (order_key(y) < order_key(x)) vm = fma(rk(RK_3), s2, -kmul(RK_2, vp));
-    else if (order_key(x) < order_key(-y)) vp = fma(rk(RK_3), s2, -kmul(RK_2, vm));
+    else if (order_key(x) < ~bits(y)) vp = fma(rk(RK_3), s2, -kmul(RK_2, vm));  // x < -y: y >= 0, key(-y) = ~bits(y)
   }
   plus = vp;
   minus = vm;

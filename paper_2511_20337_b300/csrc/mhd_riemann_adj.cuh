@@ -237,7 +237,7 @@ __device__ __forceinline__ void star_side(const W7& W, double S, double SM, doub
   t.ism = rcp(t.sm);
   t.rhos = fmul(t.rs, t.ism);
   const double rsm = mul_rn(t.rs, t.sm), D = fsub(rsm, bn2);
-  t.degen = lt_pos(dabs(D), fmul(kHlldDegenEps, rsm));
+  t.degen = lt_abs(D, fmul(kHlldDegenEps, rsm));
   if (t.degen) {
     t.vs = W.v; t.ws = W.w; t.b1s = W.b1; t.b2s = W.b2;
     t.iD = t.cv = t.cb = 0.0;
@@ -362,7 +362,7 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
         const double N2 = fma(sqL, tR.b2s, fma(sqR, tL.b2s, times_sign(fmul(sq2, (fsub(tR.ws, tL.ws))), bn)));
         const double b1ss = fmul(N1, isum), b2ss = fmul(N2, isum);
         const double vBss = fma(SM, bn, fma(vss, b1ss, fmul(wss, b2ss)));
-        const double sqa = left ? -sqL : sqR;
+        const double sqa = neg_if(left ? sqL : sqR, left);  // -sqrt(rho*_L) on the left
         const double dvB = fsub(vBs, vBss);
         const double Ess = fma(sqa, times_sign(dvB, bn), Es);
         // F2..F6 += S*_a (U** - U*)
@@ -383,7 +383,7 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
         const double sqab = fmul(fmul(Essb, sg), dvB);
         vBsb = fma((fmul(Essb, sqa)), sg, vBsb);
         const double vBssb = fmul(fmul(-Essb, sqa), sg);
-        double sqLb = left ? -sqab : 0.0, sqRb = left ? 0.0 : sqab;
+        double sqLb = left ? neg_if(sqab, true) : 0.0, sqRb = left ? 0.0 : sqab;
         // vBss = SM bn + vss b1ss + wss b2ss
         SMb = fma(vBssb, bn, SMb);
         bnb = fma(vBssb, SM, bnb);
