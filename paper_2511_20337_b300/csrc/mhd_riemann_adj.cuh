@@ -422,7 +422,7 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
           abnb = fmul(Ssb, iqR);
           iqRb = fma(Ssb, abn, iqRb);
         }
-        bnb = fadd(bnb, lt0(bn) ? -abnb : abnb);
+        bnb = fadd(bnb, neg_if(abnb, lt0(bn)));
         // sq = rhos iq, iq = rhos^(-1/2)
         bL.rhos = fma(sqLb, iqL, bL.rhos);
         iqLb = fma(sqLb, tL.rhos, iqLb);
