@@ -589,13 +589,15 @@ __device__ __forceinline__ void recon_plm(double s1, double s2, double s3, doubl
 // weight d_1 g_1.  The candidates are formed as 6 q_k and the normalisation
 // as 6 sum_k alpha_k = sum_k (6 d_k) g_k.
 __device__ __forceinline__ void wenoz_from_indicators(double a0, double a1, double a2, double a3, double a4,
-                                                      double b0, double b1, double b2, double& plus,
+                                                      double be0, double be1, double be2, double& plus,
                                                       double& minus) {
-  const double tau = fsub(b0, b2);  // tau5 up to its sign, which the squares of r_k drop
-  const double weps = rk(RK_WEPS);
-  const double r0 = fmul(tau, rcp(fadd(b0, weps)));
-  const double r1 = fmul(tau, rcp(fadd(b1, weps)));
-  const double r2 = fmul(tau, rcp(fadd(b2, weps)));
+  // be_k = beta_k + eps, the epsilon already added in a free addend slot of
+  // the indicators' FMAs; tau5 = |be_0 - be_2| up to its sign, which the
+  // squares of r_k drop
+  const double tau = fsub(be0, be2);
+  const double r0 = fmul(tau, rcp(be0));
+  const double r1 = fmul(tau, rcp(be1));
+  const double r2 = fmul(tau, rcp(be2));
   const double g0 = fma(r0, r0, rk(RK_ONE)), g1 = fma(r1, r1, rk(RK_ONE)), g2 = fma(r2, r2, rk(RK_ONE));
   // alpha_k = d_k g_k: the plus face weighs (g0, g1, g2), the minus face (g2, g1, g0)
   const double w1 = kmul(RK_0_6, g1);
@@ -623,7 +625,8 @@ __device__ __forceinline__ void wenoz_from_indicators(double a0, double a1, doub
 // the stencil's one-sided combination.  A sweep marching along a pencil
 // carries, per variable, what consecutive cells share (WzCarry for the window
 // of cell i):
-//   P0, P1 = the curvature terms of the stencils centred at a1 and a2,
+//   P0, P1 = the curvature terms of the stencils centred at a1 and a2, each
+//            plus the WENO-Z epsilon (so every indicator arrives as beta + eps),
 //   h      = u_0 / 2 = (a0 - 4 a1 + 3 a2) / 2,
 //   d      = a3 - a2.
 // With t2 = (a4 - a3) - d the curvature at a3, u_2 / 2 = t2 / 2 - d and
@@ -640,8 +643,8 @@ __device__ __forceinline__ WzCarry wenoz_start(double a0, double a1, double a2, 
   const double d01 = fsub(a1, a0), d12 = fsub(a2, a1);
   c.d = fsub(a3, a2);
   const double t0 = fsub(d12, d01), t1 = fsub(c.d, d12);
-  c.P0 = fmul(kmul(RK_13_12, t0), t0);
-  c.P1 = fmul(kmul(RK_13_12, t1), t1);
+  c.P0 = fma(kmul(RK_13_12, t0), t0, rk(RK_WEPS));
+  c.P1 = fma(kmul(RK_13_12, t1), t1, rk(RK_WEPS));
   c.h = fma(rk(RK_2), d12, fma(rk(RK_HALF), a0, kmul(RK_MHALF, a2)));
   return c;
 }
@@ -649,7 +652,7 @@ __device__ __forceinline__ void recon_wenoz_m(double a0, double a1, double a2, d
                                               double& plus, double& minus) {
   const double d34 = fsub(a4, a3);
   const double t2 = fsub(d34, c.d);
-  const double P2 = fmul(kmul(RK_13_12, t2), t2);
+  const double P2 = fma(kmul(RK_13_12, t2), t2, rk(RK_WEPS));
   const double h2 = fma(rk(RK_HALF), t2, -c.d);                  // (3 a2 - 4 a3 + a4) / 2
   const double h1 = fma(rk(RK_HALF), a1, kmul(RK_MHALF, a3));    // (a1 - a3) / 2
   const double b0 = fma(c.h, c.h, c.P0);
@@ -677,13 +680,14 @@ __device__ __forceinline__ Curv curv_of(double t) {
 __device__ __forceinline__ Curv curv(double l, double m, double r) { return curv_of(fadd(fma(rk(RK_M2), m, l), r)); }
 __device__ __forceinline__ void recon_wenoz_c(double a0, double a1, double a2, double a3, double a4, const Curv& c0,
                                               const Curv& c1, Curv& c2, double& plus, double& minus) {
+  // beta_k + eps, the epsilon in the one-sided term's addend slot
   double u = fma(rk(RK_3), a2, fma(rk(RK_M4), a1, a0));
-  double b0 = fma(c0.k, c0.t, fmul(kmul(RK_QUARTER, u), u));
+  double b0 = fma(c0.k, c0.t, fma(kmul(RK_QUARTER, u), u, rk(RK_WEPS)));
   u = fsub(a1, a3);
-  double b1 = fma(c1.k, c1.t, fmul(kmul(RK_QUARTER, u), u));
+  double b1 = fma(c1.k, c1.t, fma(kmul(RK_QUARTER, u), u, rk(RK_WEPS)));
   c2 = curv(a2, a3, a4);
   u = fma(rk(RK_3), a2, fma(rk(RK_M4), a3, a4));
-  double b2 = fma(c2.k, c2.t, fmul(kmul(RK_QUARTER, u), u));
+  double b2 = fma(c2.k, c2.t, fma(kmul(RK_QUARTER, u), u, rk(RK_WEPS)));
   wenoz_from_indicators(a0, a1, a2, a3, a4, b0, b1, b2, plus, minus);
 }
 __device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, double a3, double a4, double& plus,
