@@ -145,10 +145,8 @@ static __global__ void adj_sum_kernel(const double* __restrict__ v, long long n,
 // Y + Y(x image), each term present only where the image exists (for
 // n_d >= 2G + 1 a cell has at most one image per axis).
 template <int NDIM>
-static __global__ void adj_ghost_shell_kernel(Grid g, F8 A) {
-  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void adj_ghost_shell_item(const Grid& g, const F8& A, long long id) {
+  {
     const int i = (int)(id % g.n[0]);
     const long long r = id / g.n[0];
     const int j = (int)(r % g.n[1]);
@@ -162,7 +160,7 @@ static __global__ void adj_ghost_shell_kernel(Grid g, F8 A) {
     };
     const int ix = image(0, i), jy = image(1, j), kz = image(2, k);
     const bool hx = ix != i, hy = jy != j, hz = kz != k;
-    if (!hx && !hy && !hz) continue;
+    if (!hx && !hy && !hz) return;
     const int ci[2] = {i, ix}, cj[2] = {j, jy}, ck[2] = {k, kz};
 #pragma unroll
     for (int q = 0; q < 8; q++) {
@@ -191,6 +189,13 @@ static __global__ void adj_ghost_shell_kernel(Grid g, F8 A) {
     }
   }
 }
+template <int NDIM>
+static __global__ void adj_ghost_shell_kernel(Grid g, F8 A) {
+  const long long total = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    adj_ghost_shell_item<NDIM>(g, A, id);
+}
 
 // ---------------------------------------------------------------------------
 // Transpose of the stage combine  out = c0 U0 + c1 Us + cL L  (cells), and
@@ -215,11 +220,10 @@ __device__ __forceinline__ bool face_evolved(const Grid& g, int d, const int x[3
 // from LB = cL Aout on the evolved faces (zero elsewhere), read from Aout,
 // which no thread of this kernel writes.
 template <int NDIM>
-static __global__ void adj_combine_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, E3 Eb, double c0, double c1,
-                                          double cL, double dt) {
-  const long long total = edge_work<NDIM>(g);
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void adj_combine_item(const Grid& g, const F8& Aout, const F8& A0, const F8& As,
+                                                 const L6& Lb, const E3& Eb, double c0, double c1, double cL,
+                                                 double dt, long long id) {
+  {
     const int ex = g.n[0] + 1, ey = g.n[1] + 1;
     int i = (int)(id % ex);
     long long r = id / ex;
@@ -273,6 +277,14 @@ static __global__ void adj_combine_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, 
       Eb.e[C][c] = acc;
     }
   }
+}
+template <int NDIM>
+static __global__ void adj_combine_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, E3 Eb, double c0, double c1,
+                                          double cL, double dt) {
+  const long long total = edge_work<NDIM>(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    adj_combine_item<NDIM>(g, Aout, A0, As, Lb, Eb, c0, c1, cL, dt, id);
 }
 
 
@@ -349,35 +361,42 @@ __device__ __forceinline__ void uct_edge_vjp(const Grid& g, const F8& S, const F
 }
 
 template <int NDIM>
+__device__ __forceinline__ void adj_edge_item(const Grid& g, const F8& S, const FaceIngr& ING, const E3& Eb,
+                                              const GE18& GE, long long id) {
+  const int ex = g.n[0] + 1, ey = g.n[1] + 1;
+  int i = (int)(id % ex);
+  long long r = id / ex;
+  int j = (int)(r % ey);
+  int k = (int)(r / ey);
+  int c = g.at(i, j, k);
+  if (edge_valid<NDIM>(g, 2, i, j, k)) uct_edge_vjp<2>(g, S, ING, c, Eb.e[2][c], GE.q[2]);
+  if (NDIM == 3) {
+    if (edge_valid<NDIM>(g, 0, i, j, k)) uct_edge_vjp<0>(g, S, ING, c, Eb.e[0][c], GE.q[0]);
+    if (edge_valid<NDIM>(g, 1, i, j, k)) uct_edge_vjp<1>(g, S, ING, c, Eb.e[1][c], GE.q[1]);
+  }
+}
+template <int NDIM>
 static __global__ void adj_edge_kernel(Grid g, F8 S, FaceIngr ING, E3 Eb, GE18 GE) {
   const long long total = edge_work<NDIM>(g);
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int ex = g.n[0] + 1, ey = g.n[1] + 1;
-    int i = (int)(id % ex);
-    long long r = id / ex;
-    int j = (int)(r % ey);
-    int k = (int)(r / ey);
-    int c = g.at(i, j, k);
-    if (edge_valid<NDIM>(g, 2, i, j, k)) uct_edge_vjp<2>(g, S, ING, c, Eb.e[2][c], GE.q[2]);
-    if (NDIM == 3) {
-      if (edge_valid<NDIM>(g, 0, i, j, k)) uct_edge_vjp<0>(g, S, ING, c, Eb.e[0][c], GE.q[0]);
-      if (edge_valid<NDIM>(g, 1, i, j, k)) uct_edge_vjp<1>(g, S, ING, c, Eb.e[1][c], GE.q[1]);
-    }
-  }
+       id += (long long)gridDim.x * blockDim.x)
+    adj_edge_item<NDIM>(g, S, ING, Eb, GE, id);
 }
 
 // Face-field cotangents from the edge reconstructions: the face field of
 // normal D is B_b of E_C for C = (D+1)%3 (reconstructed along a = (D+2)%3)
 // and B_a of E_C for C = (D+2)%3 (along b = (D+1)%3).  Box: [-2, n+1] on
 // every active axis.
+// The cells and faces of the box [-2, n + 1] on every active axis.
 template <int NDIM>
-static __global__ void adj_edge_faces_kernel(Grid g, GE18 GE, F8 A) {
+__host__ __device__ __forceinline__ long long adj_box_work(const Grid& g) {
+  return (long long)(g.n[0] + 4) * (g.n[1] + 4) * (NDIM == 3 ? g.n[2] + 4 : 1);
+}
+template <int NDIM>
+__device__ __forceinline__ void adj_edge_faces_item(const Grid& g, const GE18& GE, const F8& A, long long id) {
   int lo[3] = {-2, -2, NDIM == 3 ? -2 : 0};
   int ext[3] = {g.n[0] + 4, g.n[1] + 4, NDIM == 3 ? g.n[2] + 4 : 1};
-  const long long total = (long long)ext[0] * ext[1] * ext[2];
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
+  {
     int x[3];
     box_index(id, lo, ext, x);
     const int f = g.at(x[0], x[1], x[2]);
@@ -403,6 +422,13 @@ static __global__ void adj_edge_faces_kernel(Grid g, GE18 GE, F8 A) {
       if (any) A.q[5 + D][f] += acc;
     }
   }
+}
+template <int NDIM>
+static __global__ void adj_edge_faces_kernel(Grid g, GE18 GE, F8 A) {
+  const long long total = adj_box_work<NDIM>(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    adj_edge_faces_item<NDIM>(g, GE, A, id);
 }
 
 // ---------------------------------------------------------------------------
@@ -521,16 +547,19 @@ static __global__ void riemann_vjp_probe_kernel(int n, double gamma, const doubl
   for (int i = 0; i < 15; i++) hand[15 * f + i] = xb[i];
 }
 
+template <int DIR, int NDIM>
+__host__ __device__ __forceinline__ long long adj_riemann_work(const Grid& g) {
+  long long faces = 1;
+  for (int d = 0; d < 3; d++) faces *= d == DIR ? g.n[d] + 1 : (d < NDIM ? g.n[d] + 2 : 1);
+  return faces;
+}
 template <int DIR, int NDIM, int RS>
-static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, const double* __restrict__ Bn,
-                                                                 L6 Lb, GE18 GE, double dt, F8 WbL, F8 WbR,
-                                                                 double* Bnb, unsigned* plm_codes) {
+__device__ __forceinline__ void adj_riemann_item(const Grid& g, const F8& P, const double* Bn, const L6& Lb,
+                                                 const GE18& GE, double dt, const F8& WbL, const F8& WbR,
+                                                 double* Bnb, unsigned* plm_codes, long long id) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   int lo[3], ext[3];
   sweep_box<DIR, NDIM>(g, lo, ext, 0, g.n[DIR]);
-  const long long total = (long long)ext[0] * ext[1] * ext[2];
-  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (id >= total) return;
   int x[3];
   box_index(id, lo, ext, x);
   const int cf = g.at(x[0], x[1], x[2]);
@@ -600,6 +629,14 @@ static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, c
   }
   Bnb[cf] += xb[14];
 }
+template <int DIR, int NDIM, int RS>
+static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, const double* __restrict__ Bn,
+                                                                 L6 Lb, GE18 GE, double dt, F8 WbL, F8 WbR,
+                                                                 double* Bnb, unsigned* plm_codes) {
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= adj_riemann_work<DIR, NDIM>(g)) return;
+  adj_riemann_item<DIR, NDIM, RS>(g, P, Bn, Lb, GE, dt, WbL, WbR, Bnb, plm_codes, id);
+}
 
 // ---------------------------------------------------------------------------
 // PLM reconstruction, per cell of the sweep box along DIR ([-2, n_DIR + 1]):
@@ -608,7 +645,7 @@ static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, c
 // PLM decisions adj_riemann_kernel recorded for those cells.
 // ---------------------------------------------------------------------------
 template <int DIR, int NDIM>
-__device__ __forceinline__ void adj_recon_item(const Grid& g, const unsigned* __restrict__ plm_codes, const F8& WbL,
+__device__ __forceinline__ void adj_recon_item(const Grid& g, const unsigned* plm_codes, const F8& WbL,
                                                const F8& WbR, const F8& Pb, const int x[3]) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   const int c = g.at(x[0], x[1], x[2]);
@@ -649,16 +686,12 @@ __device__ __forceinline__ void adj_recon_item(const Grid& g, const unsigned* __
 // its primitive cotangents in direction order, the same additions in the
 // same order as one launch per direction.
 template <int NDIM>
-static __global__ void __launch_bounds__(128) adj_recon_all_kernel(Grid g, const unsigned* __restrict__ codes0,
-                                                                   const unsigned* __restrict__ codes1,
-                                                                   const unsigned* __restrict__ codes2, F8 WbL0,
-                                                                   F8 WbR0, F8 WbL1, F8 WbR1, F8 WbL2, F8 WbR2,
-                                                                   F8 Pb) {
+__device__ __forceinline__ void adj_recon_all_item(const Grid& g, const unsigned* codes0, const unsigned* codes1,
+                                                   const unsigned* codes2, const F8& WbL0, const F8& WbR0,
+                                                   const F8& WbL1, const F8& WbR1, const F8& WbL2, const F8& WbR2,
+                                                   const F8& Pb, long long id) {
   int lo[3] = {-2, -2, NDIM == 3 ? -2 : 0};
   int ext[3] = {g.n[0] + 4, g.n[1] + 4, NDIM == 3 ? g.n[2] + 4 : 1};
-  const long long total = (long long)ext[0] * ext[1] * ext[2];
-  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (id >= total) return;
   int x[3];
   box_index(id, lo, ext, x);
   // in the DIR box: [-2, n + 1] along DIR, [-1, n] along the other active axes
@@ -670,6 +703,16 @@ static __global__ void __launch_bounds__(128) adj_recon_all_kernel(Grid g, const
   if (in_box(0)) adj_recon_item<0, NDIM>(g, codes0, WbL0, WbR0, Pb, x);
   if (in_box(1)) adj_recon_item<1, NDIM>(g, codes1, WbL1, WbR1, Pb, x);
   if (NDIM == 3 && in_box(2)) adj_recon_item<NDIM == 3 ? 2 : 0, NDIM>(g, codes2, WbL2, WbR2, Pb, x);
+}
+template <int NDIM>
+static __global__ void __launch_bounds__(128) adj_recon_all_kernel(Grid g, const unsigned* __restrict__ codes0,
+                                                                   const unsigned* __restrict__ codes1,
+                                                                   const unsigned* __restrict__ codes2, F8 WbL0,
+                                                                   F8 WbR0, F8 WbL1, F8 WbR1, F8 WbL2, F8 WbR2,
+                                                                   F8 Pb) {
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= adj_box_work<NDIM>(g)) return;
+  adj_recon_all_item<NDIM>(g, codes0, codes1, codes2, WbL0, WbR0, WbL1, WbR1, WbL2, WbR2, Pb, id);
 }
 
 // ---------------------------------------------------------------------------
@@ -690,12 +733,11 @@ __device__ __forceinline__ double adj_c2p_gp(const Grid& g, const F8& S, const F
   return g.gm1 * pb;
 }
 template <int NDIM>
-static __global__ void adj_c2p_kernel(Grid g, F8 S, F8 P, F8 Pb, F8 A) {
+__device__ __forceinline__ void adj_c2p_item(const Grid& g, const F8& S, const F8& P, const F8& Pb, const F8& A,
+                                             long long id) {
   int lo[3] = {-g.G, -g.G, NDIM == 3 ? -g.G : 0};
   int ext[3] = {g.n[0] + 2 * g.G + 1, g.n[1] + 2 * g.G + 1, NDIM == 3 ? g.n[2] + 2 * g.G + 1 : 1};
-  const long long total = (long long)ext[0] * ext[1] * ext[2];
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
+  {
     int x[3];
     box_index(id, lo, ext, x);
     const int c = g.at(x[0], x[1], x[2]);
@@ -732,6 +774,13 @@ static __global__ void adj_c2p_kernel(Grid g, F8 S, F8 P, F8 Pb, F8 A) {
       A.q[5 + d][c] += 0.5 * acc;
     }
   }
+}
+template <int NDIM>
+static __global__ void adj_c2p_kernel(Grid g, F8 S, F8 P, F8 Pb, F8 A) {
+  const long long total = (long long)g.ext[0] * g.ext[1] * g.ext[2];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x)
+    adj_c2p_item<NDIM>(g, S, P, Pb, A, id);
 }
 
 

@@ -209,3 +209,59 @@ def test_two_fused_contexts_side_by_side(mhd):
         got, want = x.get_conserved(), y.get_conserved()
         for k in want:
             np.testing.assert_array_equal(got[k], want[k], err_msg=k)
+
+
+ADJ_CASES = {
+    "adjoint-48-hlld-rk2": lambda: W.adjoint_2d(48),
+    "random-40x36-hll-rk3": lambda: rand2d((40, 36), 9, riemann="hll", rk=3),
+    "random-37x29-hlld-rk3-misfit": lambda: rand2d((37, 29), 10, rk=3),
+}
+
+
+def adjoint_of(M, cfg, st, fused, nsteps=10, functional="magnetic_energy"):
+    g = M.Sim(cfg, st)
+    g.set_fused(fused)
+    target = None
+    if functional == "misfit":
+        target = [np.full(s, 0.5) for s in g.shapes[:5]] + [np.full(g.shapes[0], 0.1)]
+    J, dts = g.adjoint(nsteps, None, ckpt_every=4, functional=functional, target=target)
+    return J, dts, g.grad_conserved()
+
+
+@pytest.mark.parametrize("case", list(ADJ_CASES))
+def test_adjoint_of_a_fused_context_equals_the_per_launch_one(mhd, case):
+    """The adjoint of a fused context (its forward pass one cooperative launch
+    per stage) equals that of a per-launch context to the bit."""
+    cfg, st = ADJ_CASES[case]()
+    functional = "misfit" if "misfit" in case else "magnetic_energy"
+    Jf, dtf, gf = adjoint_of(mhd, cfg, st, True, functional=functional)
+    Ju, dtu, gu = adjoint_of(mhd, cfg, st, False, functional=functional)
+    assert Jf == Ju
+    assert np.array_equal(dtf, dtu)
+    for k in gu:
+        np.testing.assert_array_equal(gf[k], gu[k], err_msg=k)
+
+
+def test_forward_pass_timeout_in_an_adjoint_run(mhd):
+    """A barrier of the adjoint's fused forward pass that runs out: the run
+    reports MHD_ERR_TIMEOUT, mhd_status re-arms the barrier, and the next run
+    gives the per-launch context's gradient."""
+    cfg, st = W.adjoint_2d(32)
+    g = mhd.Sim(cfg, st)
+    g.set_wait_limit(0.05)
+    g.inject_skip_arrive(7, 1)
+    with pytest.raises(mhd.MhdError) as err:
+        g.adjoint(6, None, ckpt_every=3)
+    assert err.value.code == -5
+    assert g.status() == (-5, -1)
+    assert g.status() == (0, -1)
+    g.set_conserved(st)
+    J, dts = g.adjoint(6, None, ckpt_every=3)
+    got = g.grad_conserved()
+    ref = mhd.Sim(cfg, st)
+    ref.set_fused(False)
+    J2, dts2 = ref.adjoint(6, None, ckpt_every=3)
+    want = ref.grad_conserved()
+    assert J == J2
+    for k in want:
+        np.testing.assert_array_equal(got[k], want[k], err_msg=k)
