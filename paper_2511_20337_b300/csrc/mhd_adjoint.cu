@@ -235,14 +235,21 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& I
   stage_coeffs(c->cfg.rk, s, c0, c1, cL);
   const long long edges = edge_work<NDIM>(g);
   const int nbe = blocks_for(edges, 256);
-  adj_combine_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->Eb, c0, c1, cL, dt);
-  prof_mark(c, MHD_AKCLASS_COMBINE);
-  adj_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Xs, ING, a->Eb, a->GE);
+  if (c->prof_on) {  // one launch per kernel class, each timed on its own
+    adj_combine_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->Eb, c0, c1, cL, dt);
+    prof_mark(c, MHD_AKCLASS_COMBINE);
+    adj_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Xs, ING, a->Eb, a->GE);
+    CK(cudaMemsetAsync(a->Pb.q[0], 0, 8 * a->fe * sizeof(double), c->stream));
+    c->launches += 2;
+  } else {  // the same in one launch
+    adj_combine_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->Eb, c0, c1, cL, dt, Xs,
+                                                              ING, a->GE, a->Pb.q[0], 8 * (long long)a->fe);
+    c->launches++;
+  }
   long long box = (long long)(g.n[0] + 4) * (g.n[1] + 4) * (NDIM == 3 ? g.n[2] + 4 : 1);
   adj_edge_faces_kernel<NDIM><<<blocks_for(box, 256), 256, 0, c->stream>>>(g, a->GE, As);
   prof_mark(c, MHD_AKCLASS_EDGE);
-  CK(cudaMemsetAsync(a->Pb.q[0], 0, 8 * a->fe * sizeof(double), c->stream));
-  c->launches += 3;
+  c->launches++;
   if (split_now(c)) {  // the directions' Riemann transposes side by side (small grids)
     cudaEventRecord(c->ev_fork, c->stream);
     cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0);

@@ -382,6 +382,25 @@ static __global__ void adj_edge_kernel(Grid g, F8 S, FaceIngr ING, E3 Eb, GE18 G
        id += (long long)gridDim.x * blockDim.x)
     adj_edge_item<NDIM>(g, S, ING, Eb, GE, id);
 }
+// The combine / CT-curl transpose and the UCT edge transpose of the same
+// edge index in one thread (the edge item reads only the edge cotangents the
+// combine item of its own index wrote), with the primitive cotangents of the
+// reconstruction transposes cleared in the same launch: one launch for what
+// adj_combine_kernel, adj_edge_kernel and a memset do, the same operations on
+// every element.
+template <int NDIM>
+static __global__ void adj_combine_edge_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, E3 Eb, double c0, double c1,
+                                               double cL, double dt, F8 S, FaceIngr ING, GE18 GE, double* pb,
+                                               long long pb_count) {
+  const long long total = edge_work<NDIM>(g);
+  const long long T = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (long long id = t0; id < total; id += T) {
+    adj_combine_item<NDIM>(g, Aout, A0, As, Lb, Eb, c0, c1, cL, dt, id);
+    adj_edge_item<NDIM>(g, S, ING, Eb, GE, id);
+  }
+  for (long long id = t0; id < pb_count; id += T) pb[id] = 0.0;
+}
 
 // Face-field cotangents from the edge reconstructions: the face field of
 // normal D is B_b of E_C for C = (D+1)%3 (reconstructed along a = (D+2)%3)

@@ -265,3 +265,20 @@ def test_forward_pass_timeout_in_an_adjoint_run(mhd):
     assert J == J2
     for k in want:
         np.testing.assert_array_equal(got[k], want[k], err_msg=k)
+
+
+def test_profiled_adjoint_equals_the_timed_one(mhd):
+    """The profiling run keeps one launch per reverse kernel class (and runs the
+    recomputes in sequence on the context); the timed run fuses the combine and
+    edge transposes into one launch and recomputes beside the reverse pass.
+    Both give the same gradient to the bit."""
+    cfg, st = W.adjoint_2d(40)
+    g = mhd.Sim(cfg, st)
+    J, dts = g.adjoint(8, None, ckpt_every=3)
+    want = g.grad_conserved()
+    h = mhd.Sim(cfg, st)
+    phases, classes = h.adjoint_profile(8, dts, ckpt_every=3)
+    assert phases["reverse"] > 0.0
+    got = h.grad_conserved()
+    for k in want:
+        np.testing.assert_array_equal(got[k], want[k], err_msg=k)
