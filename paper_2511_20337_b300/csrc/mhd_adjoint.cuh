@@ -162,6 +162,20 @@ __device__ __forceinline__ void adj_ghost_shell_item(const Grid& g, const F8& A,
     const bool hx = ix != i, hy = jy != j, hz = kz != k;
     if (!hx && !hy && !hz) return;
     const int ci[2] = {i, ix}, cj[2] = {j, jy}, ck[2] = {k, kz};
+    // every value first, then the sums and stores: each slot is read once and
+    // written after all reads, so the loads of all fields are in flight
+    // together instead of one field's chain after another's
+    double val[8][4][2];
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+#pragma unroll
+      for (int u = 0; u < 2; u++)
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+          if ((u == 1 && !hx) || (v == 1 && !hy)) continue;
+          val[q][2 * u + v][0] = A.q[q][g.at(ci[u], cj[v], k)];
+          if (hz) val[q][2 * u + v][1] = A.q[q][g.at(ci[u], cj[v], ck[1])];
+        }
 #pragma unroll
     for (int q = 0; q < 8; q++) {
       double* a = A.q[q];
@@ -173,14 +187,12 @@ __device__ __forceinline__ void adj_ghost_shell_item(const Grid& g, const F8& A,
 #pragma unroll
         for (int v = 0; v < 2; v++) {  // the row and its y image
           if (v == 1 && !hy) continue;
-          const int c0 = g.at(ci[u], cj[v], k);
-          double z = a[c0];
+          double z = val[q][2 * u + v][0];
           if (hz) {
-            const int c1 = g.at(ci[u], cj[v], ck[1]);
-            z += a[c1];
-            a[c1] = 0.0;
+            z += val[q][2 * u + v][1];
+            a[g.at(ci[u], cj[v], ck[1])] = 0.0;
           }
-          if (u == 1 || v == 1) a[c0] = 0.0;
+          if (u == 1 || v == 1) a[g.at(ci[u], cj[v], k)] = 0.0;
           ys[v] = z;
         }
         xs[u] = hy ? ys[0] + ys[1] : ys[0];
