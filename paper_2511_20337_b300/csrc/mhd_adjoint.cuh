@@ -675,15 +675,19 @@ static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, c
 // this cell and add their contribution to the primitive cotangents, with the
 // PLM decisions adj_riemann_kernel recorded for those cells.
 // ---------------------------------------------------------------------------
+// Primitive slot of the v-th sweep-order variable of direction d.
+__device__ __forceinline__ int recon_slot(int d, int v) {
+  return v == 0 ? 0 : (v < 4 ? 1 + (d + v - 1) % 3 : (v < 6 ? 4 + (d + v - 3) % 3 : 7));
+}
 template <int DIR, int NDIM>
 __device__ __forceinline__ void adj_recon_item(const Grid& g, const unsigned* plm_codes, const F8& WbL,
-                                               const F8& WbR, const F8& Pb, const int x[3]) {
-  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+                                               const F8& WbR, const int x[3], double acc[7]) {
+  // acc[v]: the cotangent this cell's primitive recon_slot(DIR, v) receives
   const int c = g.at(x[0], x[1], x[2]);
   const int st = g.stride(DIR);
   const int n = g.n[DIR];
-  const int slot[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4 + T1, 4 + T2, 7};
-  double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int v = 0; v < 7; v++) acc[v] = 0.0;
 #pragma unroll
   for (int o = -1; o <= 1; o++) {  // reconstruction of cell x + o reads this cell at window slot 1 - o
     const int xo = x[DIR] + o;
@@ -708,8 +712,6 @@ __device__ __forceinline__ void adj_recon_item(const Grid& g, const unsigned* pl
       acc[v] += ws[1 - o];
     }
   }
-#pragma unroll
-  for (int v = 0; v < 7; v++) Pb.q[slot[v]][c] += acc[v];
 }
 // Every direction's reconstruction transpose in one launch, over the union of
 // the directions' sweep boxes ([-2, n + 1] along the direction, the sweep's
@@ -731,9 +733,33 @@ __device__ __forceinline__ void adj_recon_all_item(const Grid& g, const unsigned
       if (e != dir && (x[e] < -1 || x[e] > g.n[e])) return false;
     return true;
   };
-  if (in_box(0)) adj_recon_item<0, NDIM>(g, codes0, WbL0, WbR0, Pb, x);
-  if (in_box(1)) adj_recon_item<1, NDIM>(g, codes1, WbL1, WbR1, Pb, x);
-  if (NDIM == 3 && in_box(2)) adj_recon_item<NDIM == 3 ? 2 : 0, NDIM>(g, codes2, WbL2, WbR2, Pb, x);
+  const bool in[3] = {in_box(0), in_box(1), NDIM == 3 && in_box(2)};
+  double acc[3][7];
+  if (in[0]) adj_recon_item<0, NDIM>(g, codes0, WbL0, WbR0, x, acc[0]);
+  if (in[1]) adj_recon_item<1, NDIM>(g, codes1, WbL1, WbR1, x, acc[1]);
+  if (in[2]) adj_recon_item<NDIM == 3 ? 2 : 0, NDIM>(g, codes2, WbL2, WbR2, x, acc[2]);
+  // the primitive cotangents the directions add to, all loaded before any
+  // store; then each direction's terms in direction order, as separate
+  // launches per direction would add them
+  const int c = g.at(x[0], x[1], x[2]);
+  bool t[8] = {false, false, false, false, false, false, false, false};
+#pragma unroll
+  for (int d = 0; d < NDIM; d++)
+    if (in[d])
+#pragma unroll
+      for (int v = 0; v < 7; v++) t[recon_slot(d, v)] = true;
+  double pv[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++)
+    if (t[q]) pv[q] = Pb.q[q][c];
+#pragma unroll
+  for (int d = 0; d < NDIM; d++)
+    if (in[d])
+#pragma unroll
+      for (int v = 0; v < 7; v++) pv[recon_slot(d, v)] += acc[d][v];
+#pragma unroll
+  for (int q = 0; q < 8; q++)
+    if (t[q]) Pb.q[q][c] = pv[q];
 }
 template <int NDIM>
 static __global__ void __launch_bounds__(128) adj_recon_all_kernel(Grid g, const unsigned* __restrict__ codes0,
@@ -776,19 +802,24 @@ __device__ __forceinline__ void adj_c2p_item(const Grid& g, const F8& S, const F
 #pragma unroll
     for (int e = 0; e < NDIM; e++)
       if (x[e] > g.n[e] + g.G - 1) cell = false;
+    // the increments first, then the cotangents they add to, then the stores,
+    // so that all loads are in flight together
+    double cv[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (cell) {
       const double rho = P.q[0][c], vx = P.q[1][c], vy = P.q[2][c], vz = P.q[3][c];
       const double gp = adj_c2p_gp<NDIM>(g, S, P, Pb, c);
       const double ir = 1.0 / rho;
       const double vbx = Pb.q[1][c], vby = Pb.q[2][c], vbz = Pb.q[3][c];
       const double v2 = (vx * vx + vy * vy) + vz * vz;
-      A.q[0][c] += (Pb.q[0][c] - ((vbx * vx + vby * vy) + vbz * vz) * ir) + 0.5 * gp * v2;
-      A.q[1][c] += vbx * ir - gp * vx;
-      A.q[2][c] += vby * ir - gp * vy;
-      A.q[3][c] += vbz * ir - gp * vz;
-      A.q[4][c] += gp;
-      if (NDIM == 2) A.q[7][c] += Pb.q[6][c] - gp * P.q[6][c];
+      cv[0] = (Pb.q[0][c] - ((vbx * vx + vby * vy) + vbz * vz) * ir) + 0.5 * gp * v2;
+      cv[1] = vbx * ir - gp * vx;
+      cv[2] = vby * ir - gp * vy;
+      cv[3] = vbz * ir - gp * vz;
+      cv[4] = gp;
+      if (NDIM == 2) cv[5] = Pb.q[6][c] - gp * P.q[6][c];
     }
+    bool fok[3] = {false, false, false};
+    double fv[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int d = 0; d < NDIM; d++) {
       bool ok = true;  // the transverse indices must be those of padded cells
@@ -802,8 +833,24 @@ __device__ __forceinline__ void adj_c2p_item(const Grid& g, const F8& S, const F
         const int cm = c - g.stride(d);
         acc += Pb.q[4 + d][cm] - adj_c2p_gp<NDIM>(g, S, P, Pb, cm) * P.q[4 + d][cm];
       }
-      A.q[5 + d][c] += 0.5 * acc;
+      fok[d] = true;
+      fv[d] = 0.5 * acc;
     }
+    constexpr int kCellSlot[6] = {0, 1, 2, 3, 4, 7};
+    constexpr int NC = NDIM == 2 ? 6 : 5;
+    double ao[6], fo[3];
+    if (cell)
+#pragma unroll
+      for (int k = 0; k < NC; k++) ao[k] = A.q[kCellSlot[k]][c];
+#pragma unroll
+    for (int d = 0; d < NDIM; d++)
+      if (fok[d]) fo[d] = A.q[5 + d][c];
+    if (cell)
+#pragma unroll
+      for (int k = 0; k < NC; k++) A.q[kCellSlot[k]][c] = ao[k] + cv[k];
+#pragma unroll
+    for (int d = 0; d < NDIM; d++)
+      if (fok[d]) A.q[5 + d][c] = fo[d] + fv[d];
   }
 }
 template <int NDIM>
