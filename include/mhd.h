@@ -46,6 +46,7 @@ extern "C" {
 #define MHD_ERR_TOO_LARGE  -7   /* grid needs more scratch than mhd_step_noalloc's fixed array */
 #define MHD_ERR_DIVB       -8   /* the div B monitor (mhd_set_divb_check) found max |div B| h / max |B_c|
                                    above its tolerance */
+#define MHD_ERR_GUARD      -9   /* a guard word after (or before) a device array was overwritten */
 
 /* ---- options ---- */
 #define MHD_RECON_PLM     0     /* piecewise linear, minmod limiter */
@@ -275,6 +276,39 @@ int mhd_fused_waits(mhd_ctx* ctx, int* waits_out);
 /* Static text for a return code. */
 const char* mhd_strerror(int code);
 
+/* ---- guard words ----
+ *
+ * Not an operation of the paper: a check of the library's own memory.  Every
+ * device array of a context (each field of its pool: RK registers,
+ * primitives, increments, face ingredients, edge fields, CFL rates) is
+ * followed by at least 32 guard words, and the pool starts with 32 of them.
+ * The words hold a signalling-NaN bit pattern that no arithmetic produces and
+ * no memset writes.  They are written once, when the context is made; no
+ * launch of a step reads or writes them, so they cost nothing per step (256
+ * bytes per field).  A changed word means that some launch wrote outside the
+ * array it was given.
+ *
+ * mhd_check_guards(ctx, &field, &word): sync; scans every guard word of the
+ *   context's pool.  MHD_OK (field = -1, word = -1) when all are intact, else
+ *   MHD_ERR_GUARD with the first damaged word in pool order: `field` is the
+ *   array's index in the pool (0 .. nfields-1) and `word` counts from the
+ *   array's end (0 = the first word past its last element), or is negative
+ *   for the words before field 0 (-1 = the word just before it).  The guard
+ *   stays damaged; later checks report it again.
+ * mhd_guard_layout(ctx, &nfields, &used, &words_after): the pool's field
+ *   count, the elements each field uses (the cells of the grid with its ghost
+ *   zones), and the guard words after each field (>= 32).
+ * mhd_inject_guard_write(ctx, field, word): for tests: writes 0.0 into guard
+ *   word (field, word) from the host, as an out-of-bounds store would;
+ *   MHD_ERR_ARG where (field, word) is not a guard word.  Sync.
+ * The batched ensemble and the domain have the same check over every run's
+ * block and every brick (mhd_batch_check_guards, mhd_domain_check_guards). */
+#define MHD_GUARD_SEND -2   /* mhd_domain_check_guards: a brick's region of the halo send buffer */
+#define MHD_GUARD_RECV -3   /* ... of the halo receive buffer */
+int mhd_check_guards(mhd_ctx* ctx, int* field, long long* word);
+int mhd_guard_layout(const mhd_ctx* ctx, int* nfields, long long* used, long long* words_after);
+int mhd_inject_guard_write(mhd_ctx* ctx, int field, long long word);
+
 /* ---- divergence cleaning (divb = MHD_DIVB_GLM) ----
  *
  * The div B control the paper uses for its strong-scaling runs (§2.1, citing
@@ -360,6 +394,10 @@ int mhd_batch_get_times(mhd_batch* b, double* t_out);
 /* First device-side error of any run (as mhd_status, with *bad_run the run's
  * index, -1 if none).  Sync; does not clear. */
 int mhd_batch_status(mhd_batch* b, int* bad_run, long long* bad_cell);
+/* Guard words of every run's block of fields (see "guard words"): MHD_OK, or
+ * MHD_ERR_GUARD with the run, field and word of the first damaged word
+ * (lowest run first).  Sync. */
+int mhd_batch_check_guards(mhd_batch* b, int* run, int* field, long long* word);
 
 /* Kernel launches issued by the batch so far (graph replays count their kernels). */
 long long mhd_batch_launch_count(const mhd_batch* b);
@@ -521,6 +559,12 @@ int mhd_domain_set_seglen(mhd_domain* d, int seglen);
  * one exchange (all bricks, all boxes). */
 long long mhd_domain_launch_count(const mhd_domain* d);
 long long mhd_domain_halo_bytes(const mhd_domain* d);
+/* Guard words of every brick's context and of every brick's region of the
+ * halo send and receive buffers (each region has 32 guard words before it and
+ * at least 32 after it): MHD_OK, or MHD_ERR_GUARD with the brick and either
+ * the field of its pool or MHD_GUARD_SEND / MHD_GUARD_RECV, and the word as
+ * in mhd_check_guards.  Bricks' pools are scanned first.  Sync. */
+int mhd_domain_check_guards(mhd_domain* d, int* brick, int* field, long long* word);
 
 /* ---- allocation-free variant ----
  *

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 SO = os.path.join(HERE, "libmhd.so")
-SOURCES = ["mhd_api.cu", "mhd_batch.cu", "mhd_adjoint.cu", "mhd_domain.cu", "mhd_coop.cu"]
+SOURCES = ["mhd_api.cu", "mhd_batch.cu", "mhd_adjoint.cu", "mhd_domain.cu", "mhd_coop.cu", "mhd_guard.cu"]
 DEPS = ["mhd_math.cuh", "mhd_kernels.cuh", "mhd_host.cuh", "mhd_ctx.cuh", "mhd_dual.cuh", "mhd_adjoint.cuh", "mhd_riemann_adj.cuh", "mhd_glm.cuh", "mhd_coop.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -363,6 +363,7 @@ const char* mhd_strerror(int code) {
     case MHD_ERR_STATE: return "no state set";
     case MHD_ERR_TOO_LARGE: return "grid exceeds the fixed scratch of mhd_step_noalloc";
     case MHD_ERR_DIVB: return "discrete div B above the monitor's tolerance";
+    case MHD_ERR_GUARD: return "a guard word beside a device array was overwritten";
     default: return "unknown error";
   }
 }
@@ -381,7 +382,8 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
   c->g = g;
   c->seglen = default_seglen(g);
   c->split = split_sweeps(g);
-  c->field_elems = (size_t)((elems + 31) / 32 * 32);
+  c->field_used = elems;
+  c->field_elems = (size_t)guard_stride(elems);
   if (cfg->stream) {
     c->stream = (cudaStream_t)cfg->stream;
     c->own_stream = false;
@@ -396,7 +398,8 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
   // and z sweeps)
   const int ningr = cfg->emf == MHD_EMF_UCT_HLLD ? 6 : 5;
   const int nfields = (g.glm ? 3 * 9 + 9 + 9 : 3 * 8 + 8 + 6 + 3 * ningr + 3) + 1 + (c->split ? 6 * (g.ndim - 1) : 0);
-  size_t bytes = c->field_elems * sizeof(double) * nfields;
+  c->pool_fields = nfields;
+  size_t bytes = (size_t)guard_block_words(nfields, (long long)c->field_elems) * sizeof(double);
   if (cudaMalloc(&c->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -404,7 +407,8 @@ int mhd_create(const mhd_config* cfg, mhd_ctx** out) {
     return MHD_ERR_OOM;
   }
   cudaMemsetAsync(c->pool, 0, bytes, c->stream);
-  double* p = c->pool;
+  guard_fill(c->stream, c->pool, nfields, (long long)c->field_elems, elems);
+  double* p = c->pool + kGuardWords;
   auto next = [&]() { double* r = p; p += c->field_elems; return r; };
   if (g.glm) {
     c->reg_fields = 9;
@@ -514,7 +518,7 @@ int mhd_set_conserved(mhd_ctx* c, int mem, const double* const* U, const double*
   }
   int rc = set_common_faces(c, B);
   if (rc) return rc;
-  if (c->g.glm) CK(cudaMemsetAsync(c->GU[0].q[8], 0, c->field_elems * sizeof(double), c->stream));
+  if (c->g.glm) CK(cudaMemsetAsync(c->GU[0].q[8], 0, c->field_used * sizeof(double), c->stream));
   c->has_state = true;
   return reset_time(c);
 }
@@ -534,7 +538,7 @@ int mhd_set_prim(mhd_ctx* c, int mem, const double* rho, const double* const* v,
   if (rc) return rc;
   long long work = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
   if (c->g.glm) {
-    CK(cudaMemsetAsync(c->GU[0].q[8], 0, c->field_elems * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->GU[0].q[8], 0, c->field_used * sizeof(double), c->stream));
     if (c->g.ndim == 2) glm_prim_to_cons_kernel<2><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->GU[0]);
     else glm_prim_to_cons_kernel<3><<<blocks_for(work, 256), 256, 0, c->stream>>>(c->g, c->GU[0]);
   } else if (c->g.ndim == 2) {
@@ -1103,6 +1107,7 @@ extern "C" int mhd_step_noalloc(const mhd_config* cfg, double* const* U, double*
   c.stream = (cudaStream_t)cfg->stream;
   c.own_stream = false;
   c.field_elems = (size_t)field;
+  c.field_used = elems;
   c.pool = base;
   c.seglen = 16;
   double* p = base;

@@ -55,6 +55,10 @@ struct mhd_batch {
   int prof_n = 0;
   cudaEvent_t prof_ev[128];
   int prof_cls[128];
+  // guard words: run r's fields form one guarded block at guard_base[r]
+  int guard_fields = 0;
+  std::vector<const double*> guard_base;
+  std::vector<long long> guard_stride_w, guard_used;
 };
 
 namespace {
@@ -322,9 +326,12 @@ int mhd_batch_create(int nruns, const mhd_config* cfgs, mhd_batch** out) {
     const Grid& g = b->runs[r].g;
     long long elems = (long long)g.ext[0] * g.ext[1] * g.ext[2];
     if (elems > (long long)INT_MAX - 1) { mhd_batch_destroy(b); return MHD_ERR_ARG; }
-    field[r] = (size_t)((elems + 31) / 32 * 32);
-    total += field[r] * nfields;
+    field[r] = (size_t)guard_stride(elems);
+    total += (size_t)guard_block_words(nfields, (long long)field[r]);
+    b->guard_used.push_back(elems);
+    b->guard_stride_w.push_back((long long)field[r]);
   }
+  b->guard_fields = nfields;
   if (cudaMalloc(&b->pool, total * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&b->sc, sizeof(DevScalars) * nruns) != cudaSuccess ||
       cudaMalloc(&b->runs_d, sizeof(RunDev) * nruns) != cudaSuccess) {
@@ -336,6 +343,9 @@ int mhd_batch_create(int nruns, const mhd_config* cfgs, mhd_batch** out) {
   double* p = b->pool;
   for (int r = 0; r < nruns; r++) {
     RunDev& run = b->runs[r];
+    guard_fill(b->stream, p, nfields, (long long)field[r], b->guard_used[r]);
+    b->guard_base.push_back(p);
+    p += kGuardWords;
     auto next = [&]() { double* q = p; p += field[r]; return q; };
     for (int k = 0; k < 3; k++)
       for (int q = 0; q < 8; q++) run.U[k].q[q] = next();
@@ -666,3 +676,10 @@ int mhd_batch_profile_steps(mhd_batch* b, int nsteps, double* ms_out, int* launc
 }
 
 }  // extern "C"
+
+int mhd_batch_check_guards(mhd_batch* b, int* run, int* field, long long* word) {
+  if (!b || !run || !field || !word) return MHD_ERR_ARG;
+  std::vector<int> nf(b->nruns, b->guard_fields);
+  return guard_check_blocks(b->stream, b->nruns, b->guard_base.data(), nf.data(), b->guard_stride_w.data(),
+                            b->guard_used.data(), run, field, word);
+}

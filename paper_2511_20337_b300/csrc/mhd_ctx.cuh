@@ -16,8 +16,10 @@ struct mhd_ctx {
   mhd::Grid g;
   cudaStream_t stream;
   bool own_stream;
-  size_t field_elems;  // padded elements per field (rounded up)
-  double* pool;        // every field lives in this one allocation
+  size_t field_elems;  // words from one field's start to the next's: the used words, rounded up, + guard
+  long long field_used;  // words a field uses (the grid's cells with ghost zones)
+  int pool_fields;     // fields in the pool
+  double* pool;        // every field lives in this one allocation, after kGuardWords guard words
   mhd::F8 U[3];        // RK registers (U[0] = U^n); each register's 8 fields are contiguous
   mhd::F8 P;           // primitives of the stage input
   mhd::L6 L;           // stage increment of the cell variables

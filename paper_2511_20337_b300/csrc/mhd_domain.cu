@@ -289,6 +289,7 @@ struct mhd_domain {
   std::vector<HaloTable> send, recv;
   std::vector<std::vector<Copy>> copies;  // per sending brick
   std::vector<long long> send_base, recv_base;
+  std::vector<long long> send_used, recv_used;  // doubles of each brick's region
   std::vector<int> outflow_sides;         // per brick and axis: bit 0 low, bit 1 high
   double* sendbuf = nullptr;
   double* recvbuf = nullptr;
@@ -471,6 +472,8 @@ int mhd_domain_create(const mhd_config* cfg, const int parts[3], mhd_domain** ou
   long long send_total = 0, recv_total = 0;
   D->send_base.resize(D->nb);
   D->recv_base.resize(D->nb);
+  D->send_used.resize(D->nb);
+  D->recv_used.resize(D->nb);
   for (int b = 0; b < D->nb; b++) {
     int* lo = &D->lo[3 * b];
     int* n = &D->n[3 * b];
@@ -509,10 +512,13 @@ int mhd_domain_create(const mhd_config* cfg, const int parts[3], mhd_domain** ou
     rb[b].resize(nr);
     D->send.push_back(make_table(sb[b].data(), ns));
     D->recv.push_back(make_table(rb[b].data(), nr));
-    D->send_base[b] = send_total;
-    D->recv_base[b] = recv_total;
-    send_total += 8 * ss;
-    recv_total += 8 * rs;
+    // each brick's region of a buffer is a guarded block of one field
+    D->send_base[b] = send_total + kGuardWords;
+    D->recv_base[b] = recv_total + kGuardWords;
+    D->send_used[b] = 8 * ss;
+    D->recv_used[b] = 8 * rs;
+    send_total += guard_block_words(1, guard_stride(8 * ss));
+    recv_total += guard_block_words(1, guard_stride(8 * rs));
   }
   // each box sent in direction o lands in the peer's box received from direction -o
   D->copies.resize(D->nb);
@@ -537,6 +543,15 @@ int mhd_domain_create(const mhd_config* cfg, const int parts[3], mhd_domain** ou
     cudaGetLastError();
     free_domain(D);
     return MHD_ERR_OOM;
+  }
+  for (int b = 0; b < D->nb && ok; b++)
+    ok = guard_fill(D->stream, D->sendbuf + D->send_base[b] - kGuardWords, 1, guard_stride(D->send_used[b]),
+                    D->send_used[b]) == MHD_OK &&
+         guard_fill(D->stream, D->recvbuf + D->recv_base[b] - kGuardWords, 1, guard_stride(D->recv_used[b]),
+                    D->recv_used[b]) == MHD_OK;
+  if (!ok) {
+    free_domain(D);
+    return MHD_ERR_CUDA;
   }
   std::vector<DevScalars*> ptrs(D->nb);
   for (int b = 0; b < D->nb; b++) ptrs[b] = D->bricks[b]->sc;
@@ -735,3 +750,30 @@ long long mhd_domain_launch_count(const mhd_domain* D) { return D ? total_launch
 long long mhd_domain_halo_bytes(const mhd_domain* D) { return D ? D->halo_doubles * (long long)sizeof(double) : 0; }
 
 }  // extern "C"
+
+int mhd_domain_check_guards(mhd_domain* D, int* brick, int* field, long long* word) {
+  if (!D || !brick || !field || !word) return MHD_ERR_ARG;
+  for (int b = 0; b < D->nb; b++) {
+    int rc = mhd_check_guards(D->bricks[b], field, word);
+    if (rc == MHD_ERR_GUARD) *brick = b;
+    if (rc) return rc;
+  }
+  // the bricks' regions of the send buffer, then of the receive buffer
+  for (int which = 0; which < 2; which++) {
+    std::vector<const double*> base(D->nb);
+    std::vector<int> nf(D->nb, 1);
+    std::vector<long long> stride(D->nb);
+    const std::vector<long long>& used = which ? D->recv_used : D->send_used;
+    for (int b = 0; b < D->nb; b++) {
+      base[b] = (which ? D->recvbuf + D->recv_base[b] : D->sendbuf + D->send_base[b]) - kGuardWords;
+      stride[b] = guard_stride(used[b]);
+    }
+    int rc = guard_check_blocks(D->stream, D->nb, base.data(), nf.data(), stride.data(), used.data(), brick, field,
+                                word);
+    if (rc == MHD_ERR_GUARD) *field = which ? MHD_GUARD_RECV : MHD_GUARD_SEND;
+    if (rc) return rc;
+  }
+  *brick = *field = -1;
+  *word = -1;
+  return MHD_OK;
+}

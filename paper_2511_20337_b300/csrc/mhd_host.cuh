@@ -85,6 +85,20 @@ inline void reset_scalars_host(DevScalars* h) {
   memset(h, 0, sizeof(*h));
   h->bad_cell = LLONG_MAX;
 }
+
+// guard words (mhd_guard.cu): kGuardWords before a pool's first field and at
+// least that many after every field, each holding the canary, a signalling NaN
+// that no arithmetic produces and no memset writes
+constexpr int kGuardWords = 32;
+constexpr unsigned long long kGuardCanary = 0x7ff0dead5afe5afeull;
+long long guard_stride(long long used);              // field stride with room for the guard after it
+long long guard_block_words(int nfields, long long stride);  // a block's words, leading guard included
+int guard_fill(cudaStream_t s, double* base, int nfields, long long stride, long long used);
+// Scan nblocks blocks (sync): MHD_OK, or MHD_ERR_GUARD with the first damaged
+// word (block, field, word: < 0 before field 0, >= 0 past the field's end).
+int guard_check_blocks(cudaStream_t s, int nblocks, const double* const* bases, const int* nfields,
+                       const long long* strides, const long long* used, int* block, int* field, long long* word);
+
 // A small host<->device copy in a stream's order, waited for.  Unlike
 // cudaMemcpy it does not go through the legacy default stream, so it never
 // waits for the work of other contexts.

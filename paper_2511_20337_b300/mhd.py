@@ -18,7 +18,8 @@ SO = os.path.join(HERE, "libmhd.so")
 
 MHD_OK = 0
 ERRORS = {-1: "MHD_ERR_ARG", -2: "MHD_ERR_CUDA", -3: "MHD_ERR_OOM", -4: "MHD_ERR_UNPHYSICAL",
-          -5: "MHD_ERR_TIMEOUT", -6: "MHD_ERR_STATE", -7: "MHD_ERR_TOO_LARGE", -8: "MHD_ERR_DIVB"}
+          -5: "MHD_ERR_TIMEOUT", -6: "MHD_ERR_STATE", -7: "MHD_ERR_TOO_LARGE", -8: "MHD_ERR_DIVB",
+          -9: "MHD_ERR_GUARD"}
 RECON = {"plm": 0, "wenoz": 1, "ppm": 2}
 RIEMANN = {"hll": 0, "hlld": 1}
 BC = {"periodic": 0, "outflow": 1}
@@ -46,7 +47,11 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_domain_set_conserved", "mhd_domain_get_conserved", "mhd_domain_cfl_dt", "mhd_domain_step",
            "mhd_domain_advance", "mhd_domain_get_time", "mhd_domain_status", "mhd_domain_counters",
            "mhd_domain_set_seglen", "mhd_domain_launch_count", "mhd_domain_halo_bytes",
-           "mhd_set_fused", "mhd_get_fused", "mhd_set_wait_limit", "mhd_inject_skip_arrive", "mhd_fused_waits")
+           "mhd_set_fused", "mhd_get_fused", "mhd_set_wait_limit", "mhd_inject_skip_arrive", "mhd_fused_waits",
+           "mhd_check_guards", "mhd_guard_layout", "mhd_inject_guard_write", "mhd_batch_check_guards",
+           "mhd_domain_check_guards")
+# field of mhd_domain_check_guards: a brick's region of the halo send / receive buffer
+GUARD_SEND, GUARD_RECV = -2, -3
 FUNCTIONALS = {"magnetic_energy": 0, "misfit": 1}
 KCLASSES = ("ghost", "prim", "sweep_x", "sweep_y", "sweep_z", "emf", "ct_rk", "other")
 AKCLASSES = KCLASSES + ("adj_combine", "adj_edge", "adj_riemann", "adj_recon", "adj_c2p", "adj_ghost")
@@ -158,6 +163,14 @@ def lib():
             "mhd_set_wait_limit": (I, [P, D]),
             "mhd_inject_skip_arrive": (I, [P, I, I]),
             "mhd_fused_waits": (I, [P, ctypes.POINTER(I)]),
+            "mhd_check_guards": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)]),
+            "mhd_guard_layout": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_longlong)]),
+            "mhd_inject_guard_write": (I, [P, I, ctypes.c_longlong]),
+            "mhd_batch_check_guards": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I),
+                                           ctypes.POINTER(ctypes.c_longlong)]),
+            "mhd_domain_check_guards": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I),
+                                            ctypes.POINTER(ctypes.c_longlong)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -383,6 +396,27 @@ class Sim:
         n = ctypes.c_int()
         _check(lib().mhd_fused_waits(self.h, ctypes.byref(n)), "mhd_fused_waits")
         return n.value
+
+    def check_guards(self):
+        """None when every guard word of the pool is intact, else (field, word) of the
+        first damaged one (word < 0: before field 0; word >= 0: past the field's end)."""
+        f, w = ctypes.c_int(), ctypes.c_longlong()
+        rc = lib().mhd_check_guards(self.h, ctypes.byref(f), ctypes.byref(w))
+        if rc == -9:
+            return f.value, w.value
+        _check(rc, "mhd_check_guards")
+        return None
+
+    @property
+    def guard_layout(self):
+        """(fields in the pool, elements each uses, guard words after each)."""
+        n, u, a = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().mhd_guard_layout(self.h, ctypes.byref(n), ctypes.byref(u), ctypes.byref(a)), "mhd_guard_layout")
+        return n.value, u.value, a.value
+
+    def inject_guard_write(self, field, word):
+        """For tests: write 0.0 into a guard word from the host, as an out-of-bounds store would."""
+        _check(lib().mhd_inject_guard_write(self.h, int(field), int(word)), "mhd_inject_guard_write")
 
     def set_divb_check(self, tol):
         """Check max |div B| h / max |B_c| at the end of every step (tol > 0; 0 = off)."""
@@ -705,6 +739,15 @@ class Batch:
         rc = lib().mhd_batch_status(self.h, ctypes.byref(r), ctypes.byref(c))
         return rc, r.value, c.value
 
+    def check_guards(self):
+        """None when every run's guard words are intact, else (run, field, word) of the first damaged one."""
+        r, f, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        rc = lib().mhd_batch_check_guards(self.h, ctypes.byref(r), ctypes.byref(f), ctypes.byref(w))
+        if rc == -9:
+            return r.value, f.value, w.value
+        _check(rc, "mhd_batch_check_guards")
+        return None
+
     @property
     def launches(self):
         return lib().mhd_batch_launch_count(self.h)
@@ -842,6 +885,16 @@ class Domain:
         bad = ctypes.c_longlong()
         rc = lib().mhd_domain_status(self.h, ctypes.byref(bad))
         return rc, bad.value
+
+    def check_guards(self):
+        """None when the bricks' pools and halo buffer regions are intact, else (brick, field, word):
+        field >= 0 is a field of the brick's pool, GUARD_SEND / GUARD_RECV its halo buffer region."""
+        b, f, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        rc = lib().mhd_domain_check_guards(self.h, ctypes.byref(b), ctypes.byref(f), ctypes.byref(w))
+        if rc == -9:
+            return b.value, f.value, w.value
+        _check(rc, "mhd_domain_check_guards")
+        return None
 
     def counters(self):
         f, p = ctypes.c_longlong(), ctypes.c_longlong()
