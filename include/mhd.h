@@ -414,8 +414,11 @@ long long mhd_batch_launch_count(const mhd_batch* b);
  *                             the cell's two faces (2D B_z: the cell value);
  *   MHD_FUNC_MISFIT           J = 1/2 sum_cells sum_q (U_q - T_q)^2 dV over
  *                             rho, m_x, m_y, m_z, E (2D: and the cell B_z).
- * Supported: PLM reconstruction, HLL or HLLD, RK2 or RK3, periodic on every
- * axis with at least 2G+1 = 5 cells (MHD_ERR_ARG otherwise). */
+ * Supported: PLM, WENO-Z or PPM reconstruction (for WENO-Z the derivative of
+ * the weights is taken, so the gradient is that of the nonlinear scheme; for
+ * PPM the clip and steepening choices the forward values take), HLL or HLLD,
+ * RK2 or RK3, UCT-HLL edge fields, periodic on every axis with at least
+ * 2G+1 cells (5 for PLM, 7 for WENO-Z and PPM; MHD_ERR_ARG otherwise). */
 #define MHD_FUNC_MAGNETIC_ENERGY 0
 #define MHD_FUNC_MISFIT          1
 

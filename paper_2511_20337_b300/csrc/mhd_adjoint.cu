@@ -210,20 +210,33 @@ void stage_coeffs(int rk, int s, double& c0, double& c1, double& cL) {
 // cotangents and PLM codes); the reconstruction transposes of all directions
 // follow in one launch (adj_recon_all_kernel), which adds into Pb in
 // direction order.
-template <int NDIM, int RS, int DIR>
+template <int NDIM, int RS, int RECON, int DIR>
 void adj_riemann_dir(mhd_ctx* c, const F8& Xs, const F8& Ps, const F8& As, double dt, cudaStream_t st) {
   AdjointState* a = c->adj;
   const Grid& g = c->g;
   long long faces = 1;
   for (int d = 0; d < 3; d++) faces *= d == DIR ? g.n[d] + 1 : (d < NDIM ? g.n[d] + 2 : 1);
-  adj_riemann_kernel<DIR, NDIM, RS><<<(int)((faces + 127) / 128), 128, 0, st>>>(
+  adj_riemann_kernel<DIR, NDIM, RS, RECON><<<(int)((faces + 127) / 128), 128, 0, st>>>(
       g, Ps, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL[DIR], a->WbR[DIR], As.q[5 + DIR], plm_codes(a, DIR));
   prof_mark(c, MHD_AKCLASS_RIEMANN);
   c->launches++;
 }
 // Transpose of stage s at the stage input Xs: the cotangent Aout of the
 // stage output is distributed to A0 (U^n) and As (the stage input).
-template <int NDIM, int RS>
+// The WENO-Z / PPM reconstruction transpose of direction DIR: the owner-cell
+// pass into the window-slot fields T, then the gather into Pb.
+template <int NDIM, int RECON, int DIR>
+void adj_recon5_dir(mhd_ctx* c, const F8& Ps, const T35& T) {
+  AdjointState* a = c->adj;
+  const Grid& g = c->g;
+  const long long cells = adj_recon5_cells<DIR, NDIM>(g, g.n[DIR] + 2);
+  adj_recon5_cell_kernel<DIR, NDIM, RECON><<<blocks_for(cells, 128), 128, 0, c->stream>>>(g, Ps, a->WbL[DIR],
+                                                                                          a->WbR[DIR], T);
+  const long long reach = adj_recon5_cells<DIR, NDIM>(g, g.n[DIR] + 6);
+  adj_recon5_gather_kernel<DIR, NDIM><<<blocks_for(reach, 128), 128, 0, c->stream>>>(g, T, a->Pb);
+  c->launches += 2;
+}
+template <int NDIM, int RS, int RECON>
 int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& ING, const F8& Aout, const F8& A0,
                 const F8& As, double dt) {
   AdjointState* a = c->adj;
@@ -253,24 +266,32 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& I
   if (split_now(c)) {  // the directions' Riemann transposes side by side (small grids)
     cudaEventRecord(c->ev_fork, c->stream);
     cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0);
-    adj_riemann_dir<NDIM, RS, 1>(c, Xs, Ps, As, dt, c->aux[0]);
+    adj_riemann_dir<NDIM, RS, RECON, 1>(c, Xs, Ps, As, dt, c->aux[0]);
     cudaEventRecord(c->ev_join[0], c->aux[0]);
     if constexpr (NDIM == 3) {
       cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0);
-      adj_riemann_dir<NDIM, RS, 2>(c, Xs, Ps, As, dt, c->aux[1]);
+      adj_riemann_dir<NDIM, RS, RECON, 2>(c, Xs, Ps, As, dt, c->aux[1]);
       cudaEventRecord(c->ev_join[1], c->aux[1]);
     }
-    adj_riemann_dir<NDIM, RS, 0>(c, Xs, Ps, As, dt, c->stream);
+    adj_riemann_dir<NDIM, RS, RECON, 0>(c, Xs, Ps, As, dt, c->stream);
     cudaStreamWaitEvent(c->stream, c->ev_join[0], 0);
     if constexpr (NDIM == 3) cudaStreamWaitEvent(c->stream, c->ev_join[1], 0);
   } else {
-    adj_riemann_dir<NDIM, RS, 0>(c, Xs, Ps, As, dt, c->stream);
-    adj_riemann_dir<NDIM, RS, 1>(c, Xs, Ps, As, dt, c->stream);
-    if constexpr (NDIM == 3) adj_riemann_dir<NDIM, RS, 2>(c, Xs, Ps, As, dt, c->stream);
+    adj_riemann_dir<NDIM, RS, RECON, 0>(c, Xs, Ps, As, dt, c->stream);
+    adj_riemann_dir<NDIM, RS, RECON, 1>(c, Xs, Ps, As, dt, c->stream);
+    if constexpr (NDIM == 3) adj_riemann_dir<NDIM, RS, RECON, 2>(c, Xs, Ps, As, dt, c->stream);
   }
   // the reconstruction transposes of every direction (they read only what
-  // the Riemann transposes wrote) in one launch, adding in direction order
-  {
+  // the Riemann transposes wrote), adding in direction order: PLM in one
+  // launch, the five-cell reconstructions in two per direction
+  if constexpr (RECON != RECON_PLM) {
+    T35 T;
+    for (int i = 0; i < 35; i++) T.q[i] = a->GE.q[i / 18][i % 18];
+    adj_recon5_dir<NDIM, RECON, 0>(c, Ps, T);
+    adj_recon5_dir<NDIM, RECON, 1>(c, Ps, T);
+    if constexpr (NDIM == 3) adj_recon5_dir<NDIM, RECON, 2>(c, Ps, T);
+    prof_mark(c, MHD_AKCLASS_RECON);
+  } else {
     long long box = (long long)(g.n[0] + 4) * (g.n[1] + 4) * (NDIM == 3 ? g.n[2] + 4 : 1);
     adj_recon_all_kernel<NDIM><<<(int)((box + 127) / 128), 128, 0, c->stream>>>(
         g, plm_codes(a, 0), plm_codes(a, 1), plm_codes(a, NDIM == 3 ? 2 : 0), a->WbL[0], a->WbR[0], a->WbL[1],
@@ -288,14 +309,23 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& I
   return MHD_OK;
 }
 
-int adj_stage(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& ING, const F8& Aout, const F8& A0,
-              const F8& As, double dt) {
+template <int RECON>
+int adj_stage_r(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& ING, const F8& Aout, const F8& A0,
+                const F8& As, double dt) {
   const bool hlld = c->cfg.riemann == MHD_RIEMANN_HLLD;
   if (c->g.ndim == 2)
-    return hlld ? adj_stage_t<2, RS_HLLD>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
-                : adj_stage_t<2, RS_HLL>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
-  return hlld ? adj_stage_t<3, RS_HLLD>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
-              : adj_stage_t<3, RS_HLL>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+    return hlld ? adj_stage_t<2, RS_HLLD, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
+                : adj_stage_t<2, RS_HLL, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+  return hlld ? adj_stage_t<3, RS_HLLD, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
+              : adj_stage_t<3, RS_HLL, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+}
+int adj_stage(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& ING, const F8& Aout, const F8& A0,
+              const F8& As, double dt) {
+  switch (c->cfg.recon) {
+    case MHD_RECON_WENOZ: return adj_stage_r<RECON_WENOZ>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+    case MHD_RECON_PPM: return adj_stage_r<RECON_PPM>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+    default: return adj_stage_r<RECON_PLM>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+  }
 }
 
 int seed(mhd_ctx* c, int functional) {
@@ -339,7 +369,7 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
   if (functional == MHD_FUNC_MISFIT && (!target || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE))) return MHD_ERR_ARG;
   if (!c->has_state) return MHD_ERR_STATE;
   const Grid& g = c->g;
-  if (c->cfg.recon != MHD_RECON_PLM || c->g.glm || c->cfg.emf != MHD_EMF_UCT_HLL) return MHD_ERR_ARG;
+  if (c->g.glm || c->cfg.emf != MHD_EMF_UCT_HLL) return MHD_ERR_ARG;
   for (int d = 0; d < g.ndim; d++)
     if (!g.periodic[d] || g.n[d] < 2 * g.G + 1) return MHD_ERR_ARG;
   if (dts)

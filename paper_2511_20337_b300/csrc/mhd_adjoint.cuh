@@ -495,6 +495,25 @@ __device__ __forceinline__ unsigned plm_code(const double w[7][3], bool fallback
   return code;
 }
 
+// WENO-Z or PPM states of one cell from its 5-cell window, with the positivity
+// fallback of the forward sweep (recon_wenoz gives the marching sweep's bits).
+template <int RECON>
+__device__ __forceinline__ void recon_one5(const double w[5], double& plus, double& minus) {
+  if constexpr (RECON == RECON_WENOZ) recon_wenoz(w[0], w[1], w[2], w[3], w[4], plus, minus);
+  else recon_ppm(w[0], w[1], w[2], w[3], w[4], plus, minus);
+}
+template <int RECON>
+__device__ __forceinline__ bool recon_cell5(const double w[7][5], double plus[7], double minus[7]) {
+#pragma unroll
+  for (int v = 0; v < 7; v++) recon_one5<RECON>(w[v], plus[v], minus[v]);
+  if (!gt0(plus[0]) || !gt0(minus[0]) || !gt0(plus[6]) || !gt0(minus[6])) {
+#pragma unroll
+    for (int v = 0; v < 7; v++) plus[v] = minus[v] = w[v][2];
+    return true;
+  }
+  return false;
+}
+
 template <int DIR, int NDIM>
 __device__ __forceinline__ void sweep_box(const Grid& g, int lo[3], int ext[3], int dir_lo, int dir_hi) {
 #pragma unroll
@@ -584,7 +603,7 @@ __host__ __device__ __forceinline__ long long adj_riemann_work(const Grid& g) {
   for (int d = 0; d < 3; d++) faces *= d == DIR ? g.n[d] + 1 : (d < NDIM ? g.n[d] + 2 : 1);
   return faces;
 }
-template <int DIR, int NDIM, int RS>
+template <int DIR, int NDIM, int RS, int RECON = RECON_PLM>
 __device__ __forceinline__ void adj_riemann_item(const Grid& g, const F8& P, const double* Bn, const L6& Lb,
                                                  const GE18& GE, double dt, const F8& WbL, const F8& WbR,
                                                  double* Bnb, unsigned* plm_codes, long long id) {
@@ -598,7 +617,23 @@ __device__ __forceinline__ void adj_riemann_item(const Grid& g, const F8& P, con
   const double* pr[7] = {P.q[0], P.q[1 + DIR], P.q[1 + T1], P.q[1 + T2], P.q[4 + T1], P.q[4 + T2], P.q[7]};
   // the face's states: plus of cell f-1 and minus of cell f
   double xin[15];
-  {
+  if constexpr (RECON != RECON_PLM) {  // five-cell windows; no decisions recorded (the transpose re-derives them)
+    double w[7][5], plus[7], minus[7];
+#pragma unroll
+    for (int v = 0; v < 7; v++)
+#pragma unroll
+      for (int m = 0; m < 5; m++) w[v][m] = pr[v][cf + (m - 3) * st];
+    recon_cell5<RECON>(w, plus, minus);  // cell f-1
+#pragma unroll
+    for (int v = 0; v < 7; v++) xin[v] = plus[v];
+#pragma unroll
+    for (int v = 0; v < 7; v++)
+#pragma unroll
+      for (int m = 0; m < 5; m++) w[v][m] = pr[v][cf + (m - 2) * st];
+    recon_cell5<RECON>(w, plus, minus);  // cell f
+#pragma unroll
+    for (int v = 0; v < 7; v++) xin[7 + v] = minus[v];
+  } else {
     double w[7][3], plus[7], minus[7];
 #pragma unroll
     for (int v = 0; v < 7; v++)
@@ -660,13 +695,13 @@ __device__ __forceinline__ void adj_riemann_item(const Grid& g, const F8& P, con
   }
   Bnb[cf] += xb[14];
 }
-template <int DIR, int NDIM, int RS>
+template <int DIR, int NDIM, int RS, int RECON = RECON_PLM>
 static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, const double* __restrict__ Bn,
                                                                  L6 Lb, GE18 GE, double dt, F8 WbL, F8 WbR,
                                                                  double* Bnb, unsigned* plm_codes) {
   const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= adj_riemann_work<DIR, NDIM>(g)) return;
-  adj_riemann_item<DIR, NDIM, RS>(g, P, Bn, Lb, GE, dt, WbL, WbR, Bnb, plm_codes, id);
+  adj_riemann_item<DIR, NDIM, RS, RECON>(g, P, Bn, Lb, GE, dt, WbL, WbR, Bnb, plm_codes, id);
 }
 
 // ---------------------------------------------------------------------------
@@ -770,6 +805,211 @@ static __global__ void __launch_bounds__(128) adj_recon_all_kernel(Grid g, const
   const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= adj_box_work<NDIM>(g)) return;
   adj_recon_all_item<NDIM>(g, codes0, codes1, codes2, WbL0, WbR0, WbL1, WbR1, WbL2, WbR2, Pb, id);
+}
+
+// ---------------------------------------------------------------------------
+// WENO-Z and PPM reconstruction transposes.  A cell's reconstruction reads
+// five cells, so a cell's cotangent gathers from the reconstructions of five
+// cells; re-deriving each of them in every reader would cost five times the
+// work.  Instead two launches per direction:
+//   cell pass    per owner cell x ([-1, n] along DIR, [-1, n] across): redo
+//                its reconstruction and form the cotangents of its five
+//                window cells from those of its plus state (left state of
+//                face x+1) and minus state (right state of face x);
+//                window slot m of variable v goes to T.q[7 m + v];
+//   gather pass  per cell ([-3, n + 2] along DIR): add the slots the five
+//                owners x-2..x+2 left for it (slot 2 - o of owner x+o), in
+//                owner order, to its primitive cotangents.
+// T lives in the edge-local cotangent fields, free once the Riemann
+// transposes of every direction have read them.
+// ---------------------------------------------------------------------------
+struct T35 { double* q[35]; };
+
+// Reverse of recon_wenoz for one variable: the window cotangents ab[0..4]
+// from those of the plus and minus face values.  With the curvatures t_k,
+// the one-sided terms u_k, be_k = 13/12 t_k^2 + 1/4 u_k^2 + eps,
+// tau = be_0 - be_2 (its sign drops out of the squares), r_k = tau / be_k,
+// g_k = 1 + r_k^2, weights w+ = (g0/10, 6 g1/10, 3 g2/10) for the plus face
+// and w- = (g2/10, 6 g1/10, 3 g0/10) for the minus face, and the candidates
+// q+_k, q-_k, value = sum w_k q_k / sum w_k:
+//   d value / d q_k = w_k / W,   d value / d w_k = (q_k - value) / W,
+// then back through g_k, r_k, tau, be_k to t_k, u_k and the window.
+__device__ __forceinline__ void wenoz_vjp(const double a[5], double pb, double mb, double ab[5]) {
+  const double t0 = (a[0] - 2.0 * a[1]) + a[2], t1 = (a[1] - 2.0 * a[2]) + a[3], t2 = (a[2] - 2.0 * a[3]) + a[4];
+  const double u0 = (a[0] - 4.0 * a[1]) + 3.0 * a[2], u1 = a[1] - a[3], u2 = (3.0 * a[2] - 4.0 * a[3]) + a[4];
+  const double be[3] = {fma(13.0 / 12.0 * t0, t0, fma(0.25 * u0, u0, kWenozEps)),
+                        fma(13.0 / 12.0 * t1, t1, fma(0.25 * u1, u1, kWenozEps)),
+                        fma(13.0 / 12.0 * t2, t2, fma(0.25 * u2, u2, kWenozEps))};
+  const double tau = be[0] - be[2];
+  double ib[3], r[3], gk[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    ib[k] = 1.0 / be[k];
+    r[k] = tau * ib[k];
+    gk[k] = fma(r[k], r[k], 1.0);
+  }
+  const double qp[3] = {((2.0 * a[0] - 7.0 * a[1]) + 11.0 * a[2]) / 6.0, ((-a[1] + 5.0 * a[2]) + 2.0 * a[3]) / 6.0,
+                        ((2.0 * a[2] + 5.0 * a[3]) - a[4]) / 6.0};
+  const double qm[3] = {((2.0 * a[4] - 7.0 * a[3]) + 11.0 * a[2]) / 6.0, ((-a[3] + 5.0 * a[2]) + 2.0 * a[1]) / 6.0,
+                        ((2.0 * a[2] + 5.0 * a[1]) - a[0]) / 6.0};
+  const double wp[3] = {0.1 * gk[0], 0.6 * gk[1], 0.3 * gk[2]};
+  const double wm[3] = {0.1 * gk[2], 0.6 * gk[1], 0.3 * gk[0]};
+  const double Wp = (wp[0] + wp[1]) + wp[2], Wm = (wm[0] + wm[1]) + wm[2];
+  const double vp = ((wp[0] * qp[0] + wp[1] * qp[1]) + wp[2] * qp[2]) / Wp;
+  const double vm = ((wm[0] * qm[0] + wm[1] * qm[1]) + wm[2] * qm[2]) / Wm;
+  // reverse
+  const double sp = pb / Wp, sm = mb / Wm;
+  double qbp[3], qbm[3], wbp[3], wbm[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    qbp[k] = sp * wp[k];
+    qbm[k] = sm * wm[k];
+    wbp[k] = sp * (qp[k] - vp);
+    wbm[k] = sm * (qm[k] - vm);
+  }
+  const double gb[3] = {0.1 * wbp[0] + 0.3 * wbm[2], 0.6 * (wbp[1] + wbm[1]), 0.3 * wbp[2] + 0.1 * wbm[0]};
+  double taub = 0.0, beb[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const double rb = 2.0 * r[k] * gb[k];
+    taub += rb * ib[k];
+    beb[k] = -rb * r[k] * ib[k];
+  }
+  beb[0] += taub;
+  beb[2] -= taub;
+  const double tb0 = 13.0 / 6.0 * t0 * beb[0], tb1 = 13.0 / 6.0 * t1 * beb[1], tb2 = 13.0 / 6.0 * t2 * beb[2];
+  const double ub0 = 0.5 * u0 * beb[0], ub1 = 0.5 * u1 * beb[1], ub2 = 0.5 * u2 * beb[2];
+  ab[0] = (tb0 + ub0) + (2.0 * qbp[0] - qbm[2]) / 6.0;
+  ab[1] = ((-2.0 * tb0 + tb1) + (-4.0 * ub0 + ub1)) + (((-7.0 * qbp[0] - qbp[1]) + 2.0 * qbm[1]) + 5.0 * qbm[2]) / 6.0;
+  ab[2] = ((tb0 - 2.0 * tb1) + tb2) + 3.0 * (ub0 + ub2) +
+          ((11.0 * (qbp[0] + qbm[0]) + 5.0 * (qbp[1] + qbm[1])) + 2.0 * (qbp[2] + qbm[2])) / 6.0;
+  ab[3] = ((tb1 - 2.0 * tb2) + (-ub1 - 4.0 * ub2)) + (((2.0 * qbp[1] + 5.0 * qbp[2]) - 7.0 * qbm[0]) - qbm[1]) / 6.0;
+  ab[4] = (tb2 + ub2) + (2.0 * qbm[0] - qbp[2]) / 6.0;
+}
+
+// Reverse of ppm_face(a, b, c, d): the clipped fourth-order value passes its
+// cotangent fb to (a, b, c, d) with weights (-1/12, 7/12, 7/12, -1/12), or all
+// of it to the neighbour it was clipped to (the choices ppm_face takes).
+__device__ __forceinline__ void ppm_face_vjp(double a, double b, double c, double d, double fb, double ab[4]) {
+  const double f = fma(rk(RK_7_12), fadd(b, c), -kmul(RK_1_12, fadd(a, d)));
+  const double lo = imin(b, c), hi = imax(b, c);
+  const bool lo_wins = order_key(f) < order_key(lo);  // imax(f, lo) took lo
+  const bool hi_wins = order_key(hi) < order_key(lo_wins ? lo : f);  // imin(., hi) took hi
+  ab[0] = ab[1] = ab[2] = ab[3] = 0.0;
+  if (hi_wins) {
+    if (order_key(b) < order_key(c)) ab[2] = fb;  // imax(b, c) = c
+    else ab[1] = fb;
+  } else if (lo_wins) {
+    if (order_key(c) < order_key(b)) ab[2] = fb;  // imin(b, c) = c
+    else ab[1] = fb;
+  } else {
+    ab[0] = -fb / 12.0;
+    ab[1] = 7.0 * fb / 12.0;
+    ab[2] = 7.0 * fb / 12.0;
+    ab[3] = -fb / 12.0;
+  }
+}
+// Reverse of recon_ppm: the branch the forward values take (flattened,
+// minus side steepened, plus side steepened, or neither), then the two face
+// values' transposes.
+__device__ __forceinline__ void ppm_vjp(const double s[5], double pb, double mb, double ab[5]) {
+  const double vp = ppm_face(s[1], s[2], s[3], s[4]);
+  const double vm = ppm_face(s[0], s[1], s[2], s[3]);
+  double vpb = 0.0, vmb = 0.0;
+  ab[0] = ab[1] = ab[2] = ab[3] = ab[4] = 0.0;
+  if (!gt0(fmul(fsub(vp, s[2]), fsub(s[2], vm)))) {
+    ab[2] = pb + mb;
+  } else {
+    const double dv = fsub(vp, vm);
+    const double v6 = kmul(RK_6, fma(rk(RK_MHALF), fadd(vm, vp), s[2]));
+    const double x = fmul(dv, v6), y = fmul(dv, dv);
+    if (order_key(y) < order_key(x)) {         // vm = 3 s2 - 2 vp
+      ab[2] = 3.0 * mb;
+      vpb = pb - 2.0 * mb;
+    } else if (order_key(x) < ~bits(y)) {      // vp = 3 s2 - 2 vm
+      ab[2] = 3.0 * pb;
+      vmb = mb - 2.0 * pb;
+    } else {
+      vpb = pb;
+      vmb = mb;
+    }
+  }
+  double fbv[4];
+  ppm_face_vjp(s[1], s[2], s[3], s[4], vpb, fbv);
+#pragma unroll
+  for (int m = 0; m < 4; m++) ab[1 + m] += fbv[m];
+  ppm_face_vjp(s[0], s[1], s[2], s[3], vmb, fbv);
+#pragma unroll
+  for (int m = 0; m < 4; m++) ab[m] += fbv[m];
+}
+
+template <int DIR, int NDIM>
+__host__ __device__ __forceinline__ long long adj_recon5_cells(const Grid& g, int along) {
+  long long w = 1;
+  for (int d = 0; d < 3; d++) w *= d == DIR ? along : (d < NDIM ? g.n[d] + 2 : 1);
+  return w;
+}
+template <int DIR, int NDIM, int RECON>
+__device__ __forceinline__ void adj_recon5_cell_item(const Grid& g, const F8& P, const F8& WbL, const F8& WbR,
+                                                     const T35& T, long long id) {
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  int lo[3], ext[3];
+  sweep_box<DIR, NDIM>(g, lo, ext, -1, g.n[DIR]);
+  int x[3];
+  box_index(id, lo, ext, x);
+  const int co = g.at(x[0], x[1], x[2]);
+  const int st = g.stride(DIR);
+  const int n = g.n[DIR];
+  const double* pr[7] = {P.q[0], P.q[1 + DIR], P.q[1 + T1], P.q[1 + T2], P.q[4 + T1], P.q[4 + T2], P.q[7]};
+  double w[7][5];
+#pragma unroll
+  for (int v = 0; v < 7; v++)
+#pragma unroll
+    for (int m = 0; m < 5; m++) w[v][m] = pr[v][co + (m - 2) * st];
+  // the positivity fallback, decided as the forward decides it
+  double p0, m0, p6, m6;
+  recon_one5<RECON>(w[0], p0, m0);
+  recon_one5<RECON>(w[6], p6, m6);
+  const bool fb = !gt0(p0) || !gt0(m0) || !gt0(p6) || !gt0(m6);
+#pragma unroll
+  for (int v = 0; v < 7; v++) {
+    const double pb = x[DIR] + 1 <= n ? WbL.q[v][co + st] : 0.0;
+    const double mb = x[DIR] >= 0 ? WbR.q[v][co] : 0.0;
+    double ab[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (fb) ab[2] = pb + mb;
+    else if constexpr (RECON == RECON_WENOZ) wenoz_vjp(w[v], pb, mb, ab);
+    else ppm_vjp(w[v], pb, mb, ab);
+#pragma unroll
+    for (int m = 0; m < 5; m++) T.q[7 * m + v][co] = ab[m];
+  }
+}
+template <int DIR, int NDIM, int RECON>
+static __global__ void __launch_bounds__(128) adj_recon5_cell_kernel(Grid g, F8 P, F8 WbL, F8 WbR, T35 T) {
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= adj_recon5_cells<DIR, NDIM>(g, g.n[DIR] + 2)) return;
+  adj_recon5_cell_item<DIR, NDIM, RECON>(g, P, WbL, WbR, T, id);
+}
+template <int DIR, int NDIM>
+static __global__ void __launch_bounds__(128) adj_recon5_gather_kernel(Grid g, T35 T, F8 Pb) {
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= adj_recon5_cells<DIR, NDIM>(g, g.n[DIR] + 6)) return;
+  int lo[3], ext[3];
+  sweep_box<DIR, NDIM>(g, lo, ext, -3, g.n[DIR] + 2);
+  int x[3];
+  box_index(id, lo, ext, x);
+  const int c = g.at(x[0], x[1], x[2]);
+  const int st = g.stride(DIR);
+  const int n = g.n[DIR];
+  double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int o = -2; o <= 2; o++) {  // owner x + o reads this cell at window slot 2 - o
+    const int xo = x[DIR] + o;
+    if (xo < -1 || xo > n) continue;
+#pragma unroll
+    for (int v = 0; v < 7; v++) acc[v] += T.q[7 * (2 - o) + v][c + o * st];
+  }
+#pragma unroll
+  for (int v = 0; v < 7; v++) Pb.q[recon_slot(DIR, v)][c] += acc[v];
 }
 
 // ---------------------------------------------------------------------------

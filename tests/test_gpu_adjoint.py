@@ -40,6 +40,17 @@ CASES = {
         W.base_cfg(3, (6, 5, 5), (0, 0, 0), (1.2, 1.0, 1.0))),
     "3d-5x6x5-hll-rk3": lambda: (lambda c: (c, W.random_state(c, 64, v=0.2, bamp=0.2)))(
         W.base_cfg(3, (5, 6, 5), (0, 0, 0), (1.0, 1.2, 1.0), riemann="hll", rk=3)),
+    # the five-cell reconstructions (at least 2G+1 = 7 cells per axis)
+    "2d-12-wenoz-hlld-rk3": lambda: W.adjoint_2d(12, recon="wenoz", rk=3),
+    "2d-9x8-wenoz-hll-rk2-random": lambda: (lambda c: (c, W.random_state(c, 65, v=0.3, bamp=0.3)))(
+        W.base_cfg(2, (9, 8), (0, 0), (0.9, 0.8), recon="wenoz", riemann="hll")),
+    "2d-11x7-ppm-hlld-rk2-random": lambda: (lambda c: (c, W.random_state(c, 66, v=0.3, bamp=0.3)))(
+        W.base_cfg(2, (11, 7), (0, 0), (1.1, 0.7), recon="ppm")),
+    "2d-10-ppm-hll-rk3": lambda: W.adjoint_2d(10, recon="ppm", riemann="hll", rk=3, seed=7),
+    "3d-7x8x7-wenoz-hlld-rk2": lambda: (lambda c: (c, W.random_state(c, 67, v=0.2, bamp=0.2)))(
+        W.base_cfg(3, (7, 8, 7), (0, 0, 0), (1.0, 1.1, 1.0), recon="wenoz")),
+    "3d-7x7x8-ppm-hlld-rk3": lambda: (lambda c: (c, W.random_state(c, 68, v=0.2, bamp=0.2)))(
+        W.base_cfg(3, (7, 7, 8), (0, 0, 0), (1.0, 1.0, 1.1), recon="ppm", rk=3)),
 }
 
 
@@ -69,10 +80,11 @@ def test_gradient_matches_oracle_tape(case, which):
         assert err <= 1e-10 * scale, (k, err, scale)
 
 
-def test_checkpoint_interval_does_not_change_the_gradient():
+@pytest.mark.parametrize("recon", ["plm", "wenoz", "ppm"])
+def test_checkpoint_interval_does_not_change_the_gradient(recon):
     """Recomputation from checkpoints reproduces the forward bit for bit, so
     any interval gives the same gradient, bitwise."""
-    cfg, st = W.adjoint_2d(16)
+    cfg, st = W.adjoint_2d(16, recon=recon)
     nsteps = 7
     grads = []
     for k in (1, 3, 7, 100):
@@ -117,13 +129,17 @@ def _gpu_J(cfg, st, dts, which="magnetic_energy", target=None):
     return J
 
 
-def test_conserved_gradient_matches_central_differences():
+@pytest.mark.parametrize("recon", ["plm", "wenoz"])
+def test_conserved_gradient_matches_central_differences(recon):
     """<dJ/dU0, d> against (J(U0 + h d) - J(U0 - h d)) / 2h of the GPU forward,
     along smooth directions d of every conserved cell variable and face field
     (face perturbations from a potential, so div B stays zero).  The initial
     face field is non-uniform: on a uniform one the edge reconstruction sits
-    at minmod(0, 0), where J is only directionally differentiable in B."""
+    at minmod(0, 0), where J is only directionally differentiable in B.
+    WENO-Z's weights are smooth functions of the window, so its gradient
+    meets the same bound."""
     cfg, st, _ = W.smooth_2d(32, bpert=0.1)
+    cfg = dict(cfg, recon=recon)
     nsteps = 8
     sim = mhd.Sim(cfg, st)
     _, dts = sim.adjoint(nsteps, None, ckpt_every=3)
@@ -177,15 +193,16 @@ def test_autograd_function_gives_the_library_gradient():
 
 def test_unsupported_schemes_are_rejected():
     cfg, st = W.adjoint_2d(12)
-    for bad in (dict(cfg, recon="wenoz"), dict(cfg, bc=["outflow"] * 6)):
+    for bad in (dict(cfg, emf="uct_hlld"), dict(cfg, bc=["outflow"] * 6)):
         sim = mhd.Sim(bad, st)
         with pytest.raises(mhd.MhdError) as e:
             sim.adjoint(2, None)
         assert e.value.code == -1
-    small_cfg, small_st = W.adjoint_2d(4)
-    sim = mhd.Sim(small_cfg, small_st)
-    with pytest.raises(mhd.MhdError):
-        sim.adjoint(2, None)
+    # fewer than 2G + 1 cells on an axis: 4 for PLM, 6 for WENO-Z (G = 3)
+    for small_cfg, small_st in (W.adjoint_2d(4), W.adjoint_2d(6, recon="wenoz")):
+        sim = mhd.Sim(small_cfg, small_st)
+        with pytest.raises(mhd.MhdError):
+            sim.adjoint(2, None)
     sim = mhd.Sim(cfg, st)
     with pytest.raises(mhd.MhdError) as e:
         sim.grad_prim()

@@ -215,6 +215,8 @@ ADJ_CASES = {
     "adjoint-48-hlld-rk2": lambda: W.adjoint_2d(48),
     "random-40x36-hll-rk3": lambda: rand2d((40, 36), 9, riemann="hll", rk=3),
     "random-37x29-hlld-rk3-misfit": lambda: rand2d((37, 29), 10, rk=3),
+    "random-33x30-wenoz-hlld-rk3": lambda: rand2d((33, 30), 11, recon="wenoz", rk=3),
+    "random-31x27-ppm-hll-rk2-misfit": lambda: rand2d((31, 27), 12, recon="ppm", riemann="hll"),
 }
 
 

@@ -31,6 +31,10 @@ CASES = {
         W.base_cfg(2, (10, 8), (0, 0), (1.0, 0.8), riemann="hll")),
     "random3d-5x4x3-hlld": lambda: (lambda c: (c, W.random_state(c, 52, v=0.2, bamp=0.2)))(
         W.base_cfg(3, (5, 4, 3), (0, 0, 0), (1, 1, 1))),
+    "wenoz2d-8x7-hlld-rk3": lambda: (lambda c: (c, W.random_state(c, 54, v=0.2, bamp=0.2)))(
+        W.base_cfg(2, (8, 7), (0, 0), (1.0, 0.9), recon="wenoz", rk=3)),
+    "ppm2d-7x8-hll": lambda: (lambda c: (c, W.random_state(c, 55, v=0.2, bamp=0.2)))(
+        W.base_cfg(2, (7, 8), (0, 0), (0.9, 1.0), recon="ppm", riemann="hll")),
 }
 
 
@@ -77,13 +81,15 @@ def smooth_state(n=16, seed=5):
     return cfg, st, prim, (st["b0"], st["b1"], st["b2"])
 
 
-def test_gradient_matches_central_differences_on_smooth_run():
+@pytest.mark.parametrize("recon", ["plm", "wenoz", "ppm"])
+def test_gradient_matches_central_differences_on_smooth_run(recon):
     """Smooth 16^2 state, 4 steps, misfit to a shifted target so that dJ is of
     the order of J.  Central differences along random directions agree with
     the gradient to 1e-5.  A step size counts only if the branch signature
     (every limiter, min/max and wave-fan decision) is the same at x - h, x and
     x + h; samples that switch a branch are excluded, not passed."""
     cfg, st, prim, B = smooth_state()
+    cfg = dict(cfg, recon=recon)
     dts = frozen_dts(cfg, st, 4)
     keys = ["rho", "mx", "my", "mz", "E", "b2"]
     target = [np.roll(st[k], 3, axis=2) * 1.05 for k in keys]
