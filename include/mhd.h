@@ -417,7 +417,8 @@ long long mhd_batch_launch_count(const mhd_batch* b);
  * Supported: PLM, WENO-Z or PPM reconstruction (for WENO-Z the derivative of
  * the weights is taken, so the gradient is that of the nonlinear scheme; for
  * PPM the clip and steepening choices the forward values take), HLL or HLLD,
- * RK2 or RK3, UCT-HLL edge fields, periodic on every axis with at least
+ * RK2 or RK3, UCT-HLL or UCT-HLLD edge fields (UCT-HLLD: through the
+ * solver's fan-region weights and star ratios), periodic on every axis with at least
  * 2G+1 cells (5 for PLM, 7 for WENO-Z and PPM; MHD_ERR_ARG otherwise). */
 #define MHD_FUNC_MAGNETIC_ENERGY 0
 #define MHD_FUNC_MISFIT          1

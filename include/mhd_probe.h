@@ -67,6 +67,15 @@ int mhd_adjoint_profile(mhd_ctx* ctx, int nsteps, const double* dts, int ckpt_ev
 int mhd_probe_riemann_vjp(int riemann, int n, double gamma, const double* in, const double* cot, double* dual,
                           double* hand);
 
+/* The same with the edge-field form: emf = MHD_EMF_UCT_HLL, or
+ * MHD_EMF_UCT_HLLD with riemann = MHD_RIEMANN_HLLD (the solver's own weights,
+ * whose reverse runs through the fan regions' star ratios and speeds).
+ * cot[13 n] = (7 flux cotangents, 6 ingredient cotangents in the order of
+ * mhd_probe_riemann's ing: a^L, a^R, d^L, u_L, u_R, d^R; for UCT-HLL a+, a-,
+ * d, u_L, u_R and a sixth that is ignored).  Sync. */
+int mhd_probe_riemann_vjp_emf(int riemann, int emf, int n, double gamma, const double* in, const double* cot,
+                              double* dual, double* hand);
+
 /* The sweeps' Riemann solver (MHD_RIEMANN_HLL / _HLLD) on n faces, with the
  * UCT-HLL or (emf = MHD_EMF_UCT_HLLD, HLLD only) UCT-HLLD face weights.
  * Host arrays: in[15 n] as for mhd_probe_riemann_vjp; F[7 n] receives the

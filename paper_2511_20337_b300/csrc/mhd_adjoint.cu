@@ -45,13 +45,14 @@ struct AdjointState {
   double* pool = nullptr;     // scratch of the transposes
   double* states = nullptr;   // checkpoints, then the block's stage inputs
   size_t state_count = 0;
-  double* ings = nullptr;     // UCT ingredients of every stage of the block (5 ndim fields each)
+  double* ings = nullptr;     // UCT ingredients of every stage of the block (ningr ndim fields each)
+  int ningr = 5;              // face ingredients per direction: 5, or 6 with the UCT-HLLD d^R
   size_t ing_count = 0;
   double* prims = nullptr;    // primitives of every stage of the block (8 fields each)
   F8 A[4];                    // cotangent accumulators of the stage inputs (A[3]: incoming)
   L6 Lb;                      // cotangent of the stage increment (cells)
   E3 Eb;                      // cotangent of the edge fields
-  GE18 GE;                    // edge-local cotangents
+  GE20 GE;                    // edge-local cotangents
   F8 WbL[3], WbR[3];          // per direction: cotangents of the face states (7 used; WbL.q[7] holds the PLM codes)
   F8 Pb;                      // cotangent of the primitives
   L6 T;                       // misfit target (padded cells)
@@ -85,7 +86,7 @@ void adjoint_free(mhd_ctx* c) {
 
 namespace {
 
-constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 * 18 + 3 * (8 + 8) + 8 + 6;
+constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 * 20 + 3 * (8 + 8) + 8 + 6;
 
 // The per-cell PLM decisions of the current direction (adj_riemann_kernel ->
 // adj_recon_all_kernel) live in the face-state cotangent fields' spare slot 7.
@@ -107,8 +108,9 @@ F8 prim_at(const AdjointState* a, size_t idx) {
 // The stored ingredients of stage idx, laid out like the context's (direction-major).
 FaceIngr ing_at(const AdjointState* a, int ndim, size_t idx) {
   FaceIngr g{};
+  const size_t ni = (size_t)a->ningr;
   for (int d = 0; d < ndim; d++)
-    for (int q = 0; q < 5; q++) g.a[d][q] = a->ings + (idx * 5 * ndim + (size_t)d * 5 + q) * a->fe;
+    for (int q = 0; q < a->ningr; q++) g.a[d][q] = a->ings + (idx * ni * ndim + (size_t)d * ni + q) * a->fe;
   return g;
 }
 
@@ -122,6 +124,7 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
     if (!a) return MHD_ERR_OOM;
     c->adj = a;
     a->fe = c->field_elems;
+    a->ningr = c->cfg.emf == MHD_EMF_UCT_HLLD ? 6 : 5;
     size_t bytes = a->fe * sizeof(double) * kScratchFields;
     if (cudaMalloc(&a->pool, bytes) != cudaSuccess) { cudaGetLastError(); adjoint_free(c); return MHD_ERR_OOM; }
     CK(cudaMemsetAsync(a->pool, 0, bytes, c->stream));
@@ -132,7 +135,7 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
     for (int q = 0; q < 6; q++) a->Lb.q[q] = next();
     for (int d = 0; d < 3; d++) a->Eb.e[d] = next();
     for (int C = 0; C < 3; C++)
-      for (int m = 0; m < 18; m++) a->GE.q[C][m] = next();
+      for (int m = 0; m < 20; m++) a->GE.q[C][m] = next();
     for (int d = 0; d < 3; d++)
       for (int q = 0; q < 8; q++) {
         a->WbL[d].q[q] = next();
@@ -173,7 +176,7 @@ int ensure_state(mhd_ctx* c, int nsteps, int k) {
     cudaFree(a->prims);
     a->ings = a->prims = nullptr;
     a->ing_count = 0;
-    if (cudaMalloc(&a->ings, need_ings * 5 * c->g.ndim * a->fe * sizeof(double)) != cudaSuccess ||
+    if (cudaMalloc(&a->ings, need_ings * a->ningr * c->g.ndim * a->fe * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&a->prims, need_ings * 8 * a->fe * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return MHD_ERR_OOM;
@@ -251,11 +254,11 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& I
   if (c->prof_on) {  // one launch per kernel class, each timed on its own
     adj_combine_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->Eb, c0, c1, cL, dt);
     prof_mark(c, MHD_AKCLASS_COMBINE);
-    adj_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Xs, ING, a->Eb, a->GE);
+    adj_edge_kernel<NDIM, RS == RS_HLLD_UCT><<<nbe, 256, 0, c->stream>>>(g, Xs, ING, a->Eb, a->GE);
     CK(cudaMemsetAsync(a->Pb.q[0], 0, 8 * a->fe * sizeof(double), c->stream));
     c->launches += 2;
   } else {  // the same in one launch
-    adj_combine_edge_kernel<NDIM><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->Eb, c0, c1, cL, dt, Xs,
+    adj_combine_edge_kernel<NDIM, RS == RS_HLLD_UCT><<<nbe, 256, 0, c->stream>>>(g, Aout, A0, As, a->Lb, a->Eb, c0, c1, cL, dt, Xs,
                                                               ING, a->GE, a->Pb.q[0], 8 * (long long)a->fe);
     c->launches++;
   }
@@ -286,7 +289,7 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& I
   // launch, the five-cell reconstructions in two per direction
   if constexpr (RECON != RECON_PLM) {
     T35 T;
-    for (int i = 0; i < 35; i++) T.q[i] = a->GE.q[i / 18][i % 18];
+    for (int i = 0; i < 35; i++) T.q[i] = a->GE.q[i / 20][i % 20];
     adj_recon5_dir<NDIM, RECON, 0>(c, Ps, T);
     adj_recon5_dir<NDIM, RECON, 1>(c, Ps, T);
     if constexpr (NDIM == 3) adj_recon5_dir<NDIM, RECON, 2>(c, Ps, T);
@@ -312,12 +315,15 @@ int adj_stage_t(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& I
 template <int RECON>
 int adj_stage_r(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& ING, const F8& Aout, const F8& A0,
                 const F8& As, double dt) {
-  const bool hlld = c->cfg.riemann == MHD_RIEMANN_HLLD;
-  if (c->g.ndim == 2)
-    return hlld ? adj_stage_t<2, RS_HLLD, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
-                : adj_stage_t<2, RS_HLL, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
-  return hlld ? adj_stage_t<3, RS_HLLD, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
-              : adj_stage_t<3, RS_HLL, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+  const int rs = sweep_rs(&c->cfg);
+  if (c->g.ndim == 2) {
+    if (rs == RS_HLLD_UCT) return adj_stage_t<2, RS_HLLD_UCT, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+    return rs == RS_HLLD ? adj_stage_t<2, RS_HLLD, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
+                         : adj_stage_t<2, RS_HLL, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+  }
+  if (rs == RS_HLLD_UCT) return adj_stage_t<3, RS_HLLD_UCT, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
+  return rs == RS_HLLD ? adj_stage_t<3, RS_HLLD, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt)
+                       : adj_stage_t<3, RS_HLL, RECON>(c, s, Xs, Ps, ING, Aout, A0, As, dt);
 }
 int adj_stage(mhd_ctx* c, int s, const F8& Xs, const F8& Ps, const FaceIngr& ING, const F8& Aout, const F8& A0,
               const F8& As, double dt) {
@@ -369,7 +375,7 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
   if (functional == MHD_FUNC_MISFIT && (!target || (mem != MHD_MEM_HOST && mem != MHD_MEM_DEVICE))) return MHD_ERR_ARG;
   if (!c->has_state) return MHD_ERR_STATE;
   const Grid& g = c->g;
-  if (c->g.glm || c->cfg.emf != MHD_EMF_UCT_HLL) return MHD_ERR_ARG;
+  if (c->g.glm) return MHD_ERR_ARG;
   for (int d = 0; d < g.ndim; d++)
     if (!g.periodic[d] || g.n[d] < 2 * g.G + 1) return MHD_ERR_ARG;
   if (dts)
@@ -417,7 +423,7 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
         r->P = own;
         // keep the stage's UCT ingredients (the context's are contiguous, direction-major)
         const FaceIngr keep = ING(set, n0, n, st);
-        CK(cudaMemcpyAsync(keep.a[0][0], r->ING.a[0][0], (size_t)5 * g.ndim * a->fe * sizeof(double),
+        CK(cudaMemcpyAsync(keep.a[0][0], r->ING.a[0][0], (size_t)a->ningr * g.ndim * a->fe * sizeof(double),
                            cudaMemcpyDeviceToDevice, r->stream));
       }
     }
@@ -568,6 +574,37 @@ int adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int f
 
 }  // namespace
 
+namespace {
+// The probe of both products, with NC cotangents per face.
+template <int NC>
+int probe_vjp(int rs, int n, double gamma, const double* in, const double* cot, double* dual, double* hand) {
+  double *d_in = nullptr, *d_cot = nullptr, *d_dual = nullptr, *d_hand = nullptr;
+  const size_t nin = (size_t)15 * n, ncot = (size_t)NC * n;
+  cudaError_t e = cudaMalloc(&d_in, nin * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_cot, ncot * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_dual, nin * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_hand, nin * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, in, nin * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_cot, cot, ncot * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int nb = (n + 127) / 128;
+    if (rs == RS_HLLD_UCT)
+      riemann_vjp_probe_kernel<RS_HLLD_UCT, NC><<<nb, 128>>>(n, gamma, d_in, d_cot, d_dual, d_hand);
+    else if (rs == RS_HLLD)
+      riemann_vjp_probe_kernel<RS_HLLD, NC><<<nb, 128>>>(n, gamma, d_in, d_cot, d_dual, d_hand);
+    else riemann_vjp_probe_kernel<RS_HLL, NC><<<nb, 128>>>(n, gamma, d_in, d_cot, d_dual, d_hand);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(dual, d_dual, nin * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(hand, d_hand, nin * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d_in);
+  cudaFree(d_cot);
+  cudaFree(d_dual);
+  cudaFree(d_hand);
+  return cuda_err(e);
+}
+}  // namespace
+
 extern "C" {
 
 int mhd_adjoint_run(mhd_ctx* c, int nsteps, const double* dts, int ckpt_every, int functional, int mem,
@@ -593,31 +630,23 @@ int mhd_adjoint_profile(mhd_ctx* c, int nsteps, const double* dts, int ckpt_ever
   return rc;
 }
 
+
 int mhd_probe_riemann_vjp(int riemann, int n, double gamma, const double* in, const double* cot, double* dual,
                           double* hand) {
   if (n < 1 || !in || !cot || !dual || !hand || !(gamma > 1.0)) return MHD_ERR_ARG;
   if (riemann != MHD_RIEMANN_HLL && riemann != MHD_RIEMANN_HLLD) return MHD_ERR_ARG;
-  double *d_in = nullptr, *d_cot = nullptr, *d_dual = nullptr, *d_hand = nullptr;
-  const size_t nin = (size_t)15 * n, ncot = (size_t)12 * n;
-  cudaError_t e = cudaMalloc(&d_in, nin * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&d_cot, ncot * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&d_dual, nin * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&d_hand, nin * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemcpy(d_in, in, nin * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_cot, cot, ncot * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    const int nb = (n + 127) / 128;
-    if (riemann == MHD_RIEMANN_HLLD) riemann_vjp_probe_kernel<RS_HLLD><<<nb, 128>>>(n, gamma, d_in, d_cot, d_dual, d_hand);
-    else riemann_vjp_probe_kernel<RS_HLL><<<nb, 128>>>(n, gamma, d_in, d_cot, d_dual, d_hand);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaMemcpy(dual, d_dual, nin * sizeof(double), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(hand, d_hand, nin * sizeof(double), cudaMemcpyDeviceToHost);
-  cudaFree(d_in);
-  cudaFree(d_cot);
-  cudaFree(d_dual);
-  cudaFree(d_hand);
-  return cuda_err(e);
+  return probe_vjp<12>(riemann == MHD_RIEMANN_HLLD ? RS_HLLD : RS_HLL, n, gamma, in, cot, dual, hand);
+}
+
+int mhd_probe_riemann_vjp_emf(int riemann, int emf, int n, double gamma, const double* in, const double* cot,
+                              double* dual, double* hand) {
+  if (n < 1 || !in || !cot || !dual || !hand || !(gamma > 1.0)) return MHD_ERR_ARG;
+  if (riemann != MHD_RIEMANN_HLL && riemann != MHD_RIEMANN_HLLD) return MHD_ERR_ARG;
+  if (emf != MHD_EMF_UCT_HLL && !(emf == MHD_EMF_UCT_HLLD && riemann == MHD_RIEMANN_HLLD)) return MHD_ERR_ARG;
+  mhd_config cfg{};
+  cfg.riemann = riemann;
+  cfg.emf = emf;
+  return probe_vjp<13>(sweep_rs(&cfg), n, gamma, in, cot, dual, hand);
 }
 
 int mhd_adjoint_grad_conserved(mhd_ctx* c, int mem, double* const* gU, double* const* gB) {

@@ -23,7 +23,7 @@
 namespace mhd {
 
 struct L3 { double* q[3]; };              // face arrays, one per normal direction
-struct GE18 { double* q[3][18]; };        // per edge component: 18 edge-local cotangents
+struct GE20 { double* q[3][20]; };        // per edge component: 20 edge-local cotangents
 
 // Edge component C exists in the forward step: all three in 3D, E_z in 2D.
 template <int NDIM> __device__ __forceinline__ bool has_edge(int C) { return NDIM == 3 || C == 2; }
@@ -301,12 +301,14 @@ static __global__ void adj_combine_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, 
 
 
 // ---------------------------------------------------------------------------
-// Transpose of one UCT edge field (uct_edge<C>): the 18 edge-local cotangents
-//   0-4   a-face ingredient sums (a+, a-, d, u^W, u^E), each shared by the two
-//         a-faces touching the edge,
+// Transpose of one UCT edge field (uct_edge<C, HLLD>): the edge-local
+// cotangents
+//   0-4   a-face ingredient sums (a+, a-, d, u^W, u^E; UCT-HLLD: a^L, a^R,
+//         d^L, u^W, u^E), each shared by the two a-faces touching the edge,
 //   5-9   the same for the b-faces,
 //   10-13 the face field B_b at a-offsets -2, -1, 0, +1,
-//   14-17 the face field B_a at b-offsets -2, -1, 0, +1.
+//   14-17 the face field B_a at b-offsets -2, -1, 0, +1,
+//   18-19 UCT-HLLD only: d^R of the a-faces and of the b-faces.
 // ---------------------------------------------------------------------------
 // Cotangents of (v_-2, v_-1, v_0, v_+1) from the cotangents gw, ge of the two
 // minmod-limited edge values  w = v_-1 + m(v_-1 - v_-2, v_0 - v_-1)/2  and
@@ -324,7 +326,7 @@ __device__ __forceinline__ void edge_recon_vjp(double vm2, double vm1, double v0
   else w[2] = fadd(w[2], gev);
 }
 
-template <int C>
+template <int C, bool HLLD = false>
 __device__ __forceinline__ void uct_edge_vjp(const Grid& g, const F8& S, const FaceIngr& ING, int c, double eb,
                                              double* const* ge) {
   constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
@@ -346,53 +348,64 @@ __device__ __forceinline__ void uct_edge_vjp(const Grid& g, const F8& S, const F
   double BaN = fma(rk(RK_MHALF), minmod(fsub(a0, am1), fsub(ap1, a0)), a0);
   // E = (1/4) [(apb vS BaS + amb vN BaN) - (apa uW BbW + ama uE BbE)]
   //   + (1/2) [dda (BbE - BbW) - ddb (BaN - BaS)]
+  // UCT-HLLD: the dissipation (1/2) [(dra BbE - dda BbW) - (drb BaN - ddb BaS)]
+  // with the d^R sums dra, drb
   const double gu = kmul(RK_QUARTER, eb), gd = kmul(RK_HALF, eb);
+  double dra = dda, drb = ddb;
+  if (HLLD) {
+    dra = fadd(ING.a[A][5][cb], ING.a[A][5][c]);
+    drb = fadd(ING.a[B][5][ca], ING.a[B][5][c]);
+  }
   ge[0][c] = fmul(fmul(-gu, uW), BbW);
   ge[1][c] = fmul(fmul(-gu, uE), BbE);
-  ge[2][c] = fmul(gd, (fsub(BbE, BbW)));
+  ge[2][c] = HLLD ? fmul(-gd, BbW) : fmul(gd, (fsub(BbE, BbW)));
   ge[3][c] = fmul(fmul(-gu, apa), BbW);
   ge[4][c] = fmul(fmul(-gu, ama), BbE);
   ge[5][c] = fmul(fmul(gu, vS), BaS);
   ge[6][c] = fmul(fmul(gu, vN), BaN);
-  ge[7][c] = fmul(-gd, (fsub(BaN, BaS)));
+  ge[7][c] = HLLD ? fmul(gd, BaS) : fmul(-gd, (fsub(BaN, BaS)));
   ge[8][c] = fmul(fmul(gu, apb), BaS);
   ge[9][c] = fmul(fmul(gu, amb), BaN);
+  if (HLLD) {
+    ge[18][c] = fmul(gd, BbE);
+    ge[19][c] = fmul(-gd, BaN);
+  }
   double w[4];
   edge_recon_vjp(bm2, bm1, b0, bp1, fsub(fmul(fmul(-gu, apa), uW), fmul(gd, dda)),
-                 fadd(fmul(fmul(-gu, ama), uE), fmul(gd, dda)), w);
+                 fadd(fmul(fmul(-gu, ama), uE), fmul(gd, dra)), w);
   ge[10][c] = w[0];
   ge[11][c] = w[1];
   ge[12][c] = w[2];
   ge[13][c] = w[3];
   edge_recon_vjp(am2, am1, a0, ap1, fadd(fmul(fmul(gu, apb), vS), fmul(gd, ddb)),
-                 fsub(fmul(fmul(gu, amb), vN), fmul(gd, ddb)), w);
+                 fsub(fmul(fmul(gu, amb), vN), fmul(gd, drb)), w);
   ge[14][c] = w[0];
   ge[15][c] = w[1];
   ge[16][c] = w[2];
   ge[17][c] = w[3];
 }
 
-template <int NDIM>
+template <int NDIM, bool HLLD = false>
 __device__ __forceinline__ void adj_edge_item(const Grid& g, const F8& S, const FaceIngr& ING, const E3& Eb,
-                                              const GE18& GE, long long id) {
+                                              const GE20& GE, long long id) {
   const int ex = g.n[0] + 1, ey = g.n[1] + 1;
   int i = (int)(id % ex);
   long long r = id / ex;
   int j = (int)(r % ey);
   int k = (int)(r / ey);
   int c = g.at(i, j, k);
-  if (edge_valid<NDIM>(g, 2, i, j, k)) uct_edge_vjp<2>(g, S, ING, c, Eb.e[2][c], GE.q[2]);
+  if (edge_valid<NDIM>(g, 2, i, j, k)) uct_edge_vjp<2, HLLD>(g, S, ING, c, Eb.e[2][c], GE.q[2]);
   if (NDIM == 3) {
-    if (edge_valid<NDIM>(g, 0, i, j, k)) uct_edge_vjp<0>(g, S, ING, c, Eb.e[0][c], GE.q[0]);
-    if (edge_valid<NDIM>(g, 1, i, j, k)) uct_edge_vjp<1>(g, S, ING, c, Eb.e[1][c], GE.q[1]);
+    if (edge_valid<NDIM>(g, 0, i, j, k)) uct_edge_vjp<0, HLLD>(g, S, ING, c, Eb.e[0][c], GE.q[0]);
+    if (edge_valid<NDIM>(g, 1, i, j, k)) uct_edge_vjp<1, HLLD>(g, S, ING, c, Eb.e[1][c], GE.q[1]);
   }
 }
-template <int NDIM>
-static __global__ void adj_edge_kernel(Grid g, F8 S, FaceIngr ING, E3 Eb, GE18 GE) {
+template <int NDIM, bool HLLD = false>
+static __global__ void adj_edge_kernel(Grid g, F8 S, FaceIngr ING, E3 Eb, GE20 GE) {
   const long long total = edge_work<NDIM>(g);
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x)
-    adj_edge_item<NDIM>(g, S, ING, Eb, GE, id);
+    adj_edge_item<NDIM, HLLD>(g, S, ING, Eb, GE, id);
 }
 // The combine / CT-curl transpose and the UCT edge transpose of the same
 // edge index in one thread (the edge item reads only the edge cotangents the
@@ -400,16 +413,16 @@ static __global__ void adj_edge_kernel(Grid g, F8 S, FaceIngr ING, E3 Eb, GE18 G
 // reconstruction transposes cleared in the same launch: one launch for what
 // adj_combine_kernel, adj_edge_kernel and a memset do, the same operations on
 // every element.
-template <int NDIM>
+template <int NDIM, bool HLLD = false>
 static __global__ void adj_combine_edge_kernel(Grid g, F8 Aout, F8 A0, F8 As, L6 Lb, E3 Eb, double c0, double c1,
-                                               double cL, double dt, F8 S, FaceIngr ING, GE18 GE, double* pb,
+                                               double cL, double dt, F8 S, FaceIngr ING, GE20 GE, double* pb,
                                                long long pb_count) {
   const long long total = edge_work<NDIM>(g);
   const long long T = (long long)gridDim.x * blockDim.x;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   for (long long id = t0; id < total; id += T) {
     adj_combine_item<NDIM>(g, Aout, A0, As, Lb, Eb, c0, c1, cL, dt, id);
-    adj_edge_item<NDIM>(g, S, ING, Eb, GE, id);
+    adj_edge_item<NDIM, HLLD>(g, S, ING, Eb, GE, id);
   }
   for (long long id = t0; id < pb_count; id += T) pb[id] = 0.0;
 }
@@ -424,7 +437,7 @@ __host__ __device__ __forceinline__ long long adj_box_work(const Grid& g) {
   return (long long)(g.n[0] + 4) * (g.n[1] + 4) * (NDIM == 3 ? g.n[2] + 4 : 1);
 }
 template <int NDIM>
-__device__ __forceinline__ void adj_edge_faces_item(const Grid& g, const GE18& GE, const F8& A, long long id) {
+__device__ __forceinline__ void adj_edge_faces_item(const Grid& g, const GE20& GE, const F8& A, long long id) {
   int lo[3] = {-2, -2, NDIM == 3 ? -2 : 0};
   int ext[3] = {g.n[0] + 4, g.n[1] + 4, NDIM == 3 ? g.n[2] + 4 : 1};
   {
@@ -455,7 +468,7 @@ __device__ __forceinline__ void adj_edge_faces_item(const Grid& g, const GE18& G
   }
 }
 template <int NDIM>
-static __global__ void adj_edge_faces_kernel(Grid g, GE18 GE, F8 A) {
+static __global__ void adj_edge_faces_kernel(Grid g, GE20 GE, F8 A) {
   const long long total = adj_box_work<NDIM>(g);
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x)
@@ -529,7 +542,7 @@ __device__ __forceinline__ void sweep_box(const Grid& g, int lo[3], int ext[3], 
 // cross-check of the hand-written reverse below.
 template <int RS>
 __device__ __forceinline__ void riemann_vjp_dual(const double xin[15], double gamma, double igm1, const double Fb[7],
-                                                 const double Ib[5], double xb[15]) {
+                                                 const double Ib[6], double xb[15]) {
 #pragma unroll
   for (int p = 0; p < 5; p++) {
     D3 in[15];
@@ -542,11 +555,13 @@ __device__ __forceinline__ void riemann_vjp_dual(const double xin[15], double ga
     W7T<D3> R = {in[7], in[8], in[9], in[10], in[11], in[12], in[13]};
     Flux7T<D3> F;
     IngrT<D3> ing;
-    if (RS == RS_HLLD) riemann_hlld(L, R, in[14], gamma, igm1, F, ing);
+    if (RS == RS_HLLD_UCT) riemann_hlld<D3, true>(L, R, in[14], gamma, igm1, F, ing);
+    else if (RS == RS_HLLD) riemann_hlld(L, R, in[14], gamma, igm1, F, ing);
     else riemann_hll(L, R, in[14], gamma, igm1, F, ing);
 #pragma unroll
     for (int t = 0; t < 3; t++) {
       double acc = Ib[0] * ing.ap.d[t];
+      if (RS == RS_HLLD_UCT) acc = fma(Ib[5], ing.dr.d[t], acc);
       acc = fma(Ib[1], ing.am.d[t], acc);
       acc = fma(Ib[2], ing.dd.d[t], acc);
       acc = fma(Ib[3], ing.uL.d[t], acc);
@@ -559,14 +574,17 @@ __device__ __forceinline__ void riemann_vjp_dual(const double xin[15], double ga
 }
 
 // Vector-Jacobian product of the Riemann solver by its hand-written reverse.
+// Ib: the ingredient cotangents (a+, a-, d, u_L, u_R; RS_HLLD_UCT: a^L, a^R,
+// d^L, u_L, u_R, d^R).
 template <int RS>
 __device__ __forceinline__ void riemann_vjp(const double xin[15], double gamma, double igm1, const double Fb[7],
-                                            const double Ib[5], double xb[15]) {
+                                            const double Ib[6], double xb[15]) {
   const W7 L = {xin[0], xin[1], xin[2], xin[3], xin[4], xin[5], xin[6]};
   const W7 R = {xin[7], xin[8], xin[9], xin[10], xin[11], xin[12], xin[13]};
   W7b Lb, Rb;
   double bnb = 0.0;
-  if (RS == RS_HLLD) riemann_hlld_vjp(L, R, xin[14], gamma, igm1, Fb, Ib, Lb, Rb, bnb);
+  if (RS == RS_HLLD_UCT) riemann_hlld_vjp<true>(L, R, xin[14], gamma, igm1, Fb, Ib, Lb, Rb, bnb);
+  else if (RS == RS_HLLD) riemann_hlld_vjp(L, R, xin[14], gamma, igm1, Fb, Ib, Lb, Rb, bnb);
   else riemann_hll_vjp(L, R, xin[14], gamma, igm1, Fb, Ib, Lb, Rb, bnb);
   const double out[15] = {Lb.rho, Lb.u, Lb.v, Lb.w, Lb.b1, Lb.b2, Lb.p,
                           Rb.rho, Rb.u, Rb.v, Rb.w, Rb.b1, Rb.b2, Rb.p, bnb};
@@ -574,20 +592,21 @@ __device__ __forceinline__ void riemann_vjp(const double xin[15], double gamma, 
   for (int i = 0; i < 15; i++) xb[i] = out[i];
 }
 
-// Both products on n faces: in[15 n] = (W_L, W_R, b_n) per face, cot[12 n] =
-// (flux cotangent 7, ingredient cotangent 5); dual / hand [15 n].
-template <int RS>
+// Both products on n faces: in[15 n] = (W_L, W_R, b_n) per face, cot[NC n] =
+// (flux cotangent 7, ingredient cotangents NC - 7: 5, or 6 with d^R);
+// dual / hand [15 n].
+template <int RS, int NC = 12>
 static __global__ void riemann_vjp_probe_kernel(int n, double gamma, const double* __restrict__ in,
                                                 const double* __restrict__ cot, double* dual, double* hand) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= n) return;
-  double x[15], Fb[7], Ib[5], xb[15];
+  double x[15], Fb[7], Ib[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, xb[15];
 #pragma unroll
   for (int i = 0; i < 15; i++) x[i] = in[15 * f + i];
 #pragma unroll
-  for (int i = 0; i < 7; i++) Fb[i] = cot[12 * f + i];
+  for (int i = 0; i < 7; i++) Fb[i] = cot[NC * f + i];
 #pragma unroll
-  for (int i = 0; i < 5; i++) Ib[i] = cot[12 * f + 7 + i];
+  for (int i = 0; i < NC - 7; i++) Ib[i] = cot[NC * f + 7 + i];
   const double igm1 = 1.0 / (gamma - 1.0);
   riemann_vjp_dual<RS>(x, gamma, igm1, Fb, Ib, xb);
 #pragma unroll
@@ -605,7 +624,7 @@ __host__ __device__ __forceinline__ long long adj_riemann_work(const Grid& g) {
 }
 template <int DIR, int NDIM, int RS, int RECON = RECON_PLM>
 __device__ __forceinline__ void adj_riemann_item(const Grid& g, const F8& P, const double* Bn, const L6& Lb,
-                                                 const GE18& GE, double dt, const F8& WbL, const F8& WbR,
+                                                 const GE20& GE, double dt, const F8& WbL, const F8& WbR,
                                                  double* Bnb, unsigned* plm_codes, long long id) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   int lo[3], ext[3];
@@ -669,7 +688,7 @@ __device__ __forceinline__ void adj_riemann_item(const Grid& g, const F8& P, con
     else Fb[4] = lbar(5);
   }
   // UCT-ingredient cotangent from the edges that use this face
-  double Ib[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double Ib[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int role = 0; role < 2; role++) {
     const int C = role == 0 ? (DIR + 2) % 3 : (DIR + 1) % 3;  // this face is an a-face / a b-face of E_C
@@ -684,6 +703,7 @@ __device__ __forceinline__ void adj_riemann_item(const Grid& g, const F8& P, con
       const int e = g.at(y[0], y[1], y[2]);
 #pragma unroll
       for (int q = 0; q < 5; q++) Ib[q] += GE.q[C][base + q][e];
+      if (RS == RS_HLLD_UCT) Ib[5] += GE.q[C][18 + role][e];
     }
   }
   double xb[15];
@@ -697,7 +717,7 @@ __device__ __forceinline__ void adj_riemann_item(const Grid& g, const F8& P, con
 }
 template <int DIR, int NDIM, int RS, int RECON = RECON_PLM>
 static __global__ void __launch_bounds__(128) adj_riemann_kernel(Grid g, F8 P, const double* __restrict__ Bn,
-                                                                 L6 Lb, GE18 GE, double dt, F8 WbL, F8 WbR,
+                                                                 L6 Lb, GE20 GE, double dt, F8 WbL, F8 WbR,
                                                                  double* Bnb, unsigned* plm_codes) {
   const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= adj_riemann_work<DIR, NDIM>(g)) return;

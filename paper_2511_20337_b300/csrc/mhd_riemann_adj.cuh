@@ -254,9 +254,11 @@ __device__ __forceinline__ void star_side(const W7& W, double S, double SM, doub
 // Cotangents of one side's star quantities, accumulated by the reverse.
 struct StarB {
   double rhos = 0.0, vs = 0.0, ws = 0.0, b1s = 0.0, b2s = 0.0, ism = 0.0, sd = 0.0, rs = 0.0;
+  double cb = 0.0;  // the star ratio e = B*_t / B_t itself (UCT-HLLD weights)
 };
 // Reverse of star_side down to rs and sd (their own reverse, rs = sd rho and
 // sd = S - u, runs after the contact-speed reverse has added to them).
+template <bool UCT = false>
 __device__ __forceinline__ void star_side_vjp(const W7& W, double SM, double bn, double bn2, const StarT& t, StarB& b,
                                               W7b& Wb, double& Sb, double& SMb, double& bnb, double& bn2b) {
   double smb = 0.0;
@@ -270,7 +272,7 @@ __device__ __forceinline__ void star_side_vjp(const W7& W, double SM, double bn,
     Wb.b2 = fma(b.b2s, t.cb, fma(-b.ws, t.cv, Wb.b2));
     Wb.v = fadd(Wb.v, b.vs);
     Wb.w = fadd(Wb.w, b.ws);
-    const double cbb = fma(b.b1s, W.b1, fmul(b.b2s, W.b2));
+    const double cbb = UCT ? fma(b.b1s, W.b1, fma(b.b2s, W.b2, b.cb)) : fma(b.b1s, W.b1, fmul(b.b2s, W.b2));
     const double cvb = fma(-b.vs, W.b1, -(fmul(b.ws, W.b2)));
     // cb = (rs sd - bn2) iD
     const double Nbb = fmul(cbb, t.iD);
@@ -299,9 +301,14 @@ __device__ __forceinline__ void star_side_vjp(const W7& W, double SM, double bn,
   SMb = fsub(SMb, smb);
 }
 
+// UCT: the solver's own edge-field weights (riemann_hlld<T, true>); Ib[6]
+// holds the cotangents of (a^L, a^R, d^L, u_L, u_R, d^R).  They replace the
+// outer-speed weights in every branch, so those pass no cotangent.
+template <bool UCT = false>
 __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, double bn, double gamma, double igm1,
-                                                 const double Fb[7], const double Ib[5], W7b& Lb, W7b& Rb,
+                                                 const double Fb[7], const double* Ib, W7b& Lb, W7b& Rb,
                                                  double& bnb) {
+  const double Ih[5] = {UCT ? 0.0 : Ib[0], UCT ? 0.0 : Ib[1], UCT ? 0.0 : Ib[2], Ib[3], Ib[4]};
   const double bn2 = fmul(bn, bn);
   SideNumT<double> ll, lr;
   side_num(L, bn2, gamma, ll);
@@ -344,6 +351,9 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     StarB& ba = left ? bL : bR;
     double SMb = 0.0, pTsb = 0.0, Sb = 0.0, Esb = 0.0, vBsb = 0.0;
     double Usb[7] = {0, 0, 0, 0, 0, 0, 0};
+    // star ratios of the UCT-HLLD weights (1 on a degenerate side)
+    const double eL = tL.degen ? 1.0 : tL.cb, eR = tR.degen ? 1.0 : tR.cb;
+    bool dstar = false;  // the double-star weights replaced the single-star ones
     // ---- rotational waves ----
     if (!lt_pos(kmul(RK_HALF, bn2), fmul(kHlldBnEps, pTs))) {
       const double iqL = frsqrt(tL.rhos), iqR = frsqrt(tR.rhos);
@@ -423,6 +433,32 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
           iqRb = fma(Ssb, abn, iqRb);
         }
         bnb = fadd(bnb, neg_if(abnb, lt0(bn)));
+        if (UCT) {  // a^L = S*_R w, a^R = -S*_L w, w = 1/(S*_R - S*_L); d^L = a^L kL, d^R = a^R kR
+          dstar = true;
+          const double SsL = fma(-abn, iqL, SM), SsR = fma(abn, iqR, SM);
+          const double iw = rcp(fsub(SsR, SsL));
+          const double aL = fmul(SsR, iw), aR = fmul(-SsL, iw);
+          const double kL = fma(fsub(SL, SsL), eL, -SL), kR = fma(fsub(SsR, SR), eR, SR);
+          const double aLb = fma(Ib[2], kL, Ib[0]), aRb = fma(Ib[5], kR, Ib[1]);
+          const double kLb = fmul(Ib[2], aL), kRb = fmul(Ib[5], aR);
+          // kL = (S_L - S*_L) e_L - S_L, kR = (S*_R - S_R) e_R + S_R
+          SLb = fma(kLb, fsub(eL, 1.0), SLb);
+          SRb = fma(kRb, fsub(1.0, eR), SRb);
+          double SsLb = fmul(-kLb, eL), SsRb = fmul(kRb, eR);
+          if (!tL.degen) bL.cb = fma(kLb, fsub(SL, SsL), bL.cb);
+          if (!tR.degen) bR.cb = fma(kRb, fsub(SsR, SR), bR.cb);
+          SsRb = fma(aLb, iw, SsRb);
+          SsLb = fma(-aRb, iw, SsLb);
+          const double iwb = fma(aLb, SsR, fmul(-aRb, SsL));
+          const double dwb = fmul(iwb, -(fmul(iw, iw)));
+          SsRb = fadd(SsRb, dwb);
+          SsLb = fsub(SsLb, dwb);
+          // S*_L = S_M - |b_n| iqL, S*_R = S_M + |b_n| iqR
+          SMb = fadd(SMb, fadd(SsLb, SsRb));
+          iqLb = fma(-SsLb, abn, iqLb);
+          iqRb = fma(SsRb, abn, iqRb);
+          bnb = fadd(bnb, neg_if(fma(SsRb, iqR, fmul(-SsLb, iqL)), lt0(bn)));
+        }
         // sq = rhos iq, iq = rhos^(-1/2)
         bL.rhos = fma(sqLb, iqL, bL.rhos);
         iqLb = fma(sqLb, tL.rhos, iqLb);
@@ -430,6 +466,15 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
         iqRb = fma(sqRb, tR.rhos, iqRb);
         bL.rhos = fma(iqLb, (fmul(kmul(RK_MHALF, (fmul(iqL, iqL))), iqL)), bL.rhos);
         bR.rhos = fma(iqRb, (fmul(kmul(RK_MHALF, (fmul(iqR, iqR))), iqR)), bR.rhos);
+      }
+    }
+    if (UCT && !dstar) {  // single-star weights: d^L = S_L (e_L - 1) left of the contact, d^R = S_R (1 - e_R) right
+      if (left) {
+        SLb = fma(Ib[2], fsub(eL, 1.0), SLb);
+        if (!tL.degen) bL.cb = fma(Ib[2], SL, bL.cb);
+      } else {
+        SRb = fma(Ib[5], fsub(1.0, eR), SRb);
+        if (!tR.degen) bR.cb = fma(-Ib[5], SR, bR.cb);
       }
     }
     // ---- F = F_a + S_a (U*_a - U_a) ----
@@ -477,8 +522,8 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     if (left) SLb += Sb;
     else SRb += Sb;
     // star states of both sides
-    star_side_vjp(L, SM, bn, bn2, tL, bL, Lb, SLb, SMb, bnb, bn2b);
-    star_side_vjp(R, SM, bn, bn2, tR, bR, Rb, SRb, SMb, bnb, bn2b);
+    star_side_vjp<UCT>(L, SM, bn, bn2, tL, bL, Lb, SLb, SMb, bnb, bn2b);
+    star_side_vjp<UCT>(R, SM, bn, bn2, tR, bR, Rb, SRb, SMb, bnb, bn2b);
     // pT* = a1 (uR - uL) + (rsR pTL - rsL pTR), times iden; a1 = (rhoL rsR) sdL
     const double Npb = fmul(pTsb, iden);
     double idenb = fmul(pTsb, Np);
@@ -518,7 +563,7 @@ __device__ __forceinline__ void riemann_hlld_vjp(const W7& L, const W7& R, doubl
     Rb.u = fsub(Rb.u, bR.sd);
   }
   double uLb = 0.0, uRb = 0.0, cmaxb = 0.0;
-  speeds_vjp(L.u, R.u, cmax, Ib, SLb, SRb, uLb, uRb, cmaxb);
+  speeds_vjp(L.u, R.u, cmax, Ih, SLb, SRb, uLb, uRb, cmaxb);
   Lb.u = fadd(Lb.u, uLb);
   Rb.u = fadd(Rb.u, uRb);
   cmax_vjp(L, R, c_right, ll.B2, lr.B2, bn2, gamma, cmaxb, Lb, Rb, B2bL, B2bR, bn2b);

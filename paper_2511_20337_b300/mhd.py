@@ -38,6 +38,7 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
+           "mhd_probe_riemann_vjp_emf",
            "mhd_set_divb_check", "mhd_divb",
            "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen",
            "mhd_batch_get_conserved_async", "mhd_batch_synchronize", "mhd_batch_packed_size",
@@ -132,6 +133,7 @@ def lib():
             "mhd_adjoint_grad_prim": (I, [P, I, P, DPP]),
             "mhd_adjoint_profile": (I, [P, I, ctypes.POINTER(D), I, ctypes.POINTER(D), ctypes.POINTER(D)]),
             "mhd_probe_riemann_vjp": (I, [I, I, D, P, P, P, P]),
+            "mhd_probe_riemann_vjp_emf": (I, [I, I, I, D, P, P, P, P]),
             "mhd_set_seglen": (I, [P, I]),
             "mhd_autotune": (I, [P, ctypes.POINTER(I)]),
             "mhd_set_psi": (I, [P, I, P]),
@@ -533,16 +535,21 @@ class Sim:
         return out
 
 
-def probe_riemann_vjp(solver, inputs, cotangents, gamma):
+def probe_riemann_vjp(solver, inputs, cotangents, gamma, emf=None):
     """The Riemann solver's vector-Jacobian product on the GPU by forward-mode
     numbers and by the hand-written reverse: inputs (n, 15), cotangents (n, 12)
-    -> (dual, hand), each (n, 15)."""
+    -> (dual, hand), each (n, 15).  With emf ("uct_hll" or "uct_hlld") the
+    cotangents are (n, 13): 7 flux and 6 ingredient (a^L, a^R, d^L, u_L, u_R, d^R)."""
     x = np.ascontiguousarray(np.asarray(inputs, dtype=np.float64))
     c = np.ascontiguousarray(np.asarray(cotangents, dtype=np.float64))
     n = x.shape[0]
     dual, hand = np.zeros((n, 15)), np.zeros((n, 15))
-    _check(lib().mhd_probe_riemann_vjp(RIEMANN[solver], n, float(gamma), _ptr(x), _ptr(c), _ptr(dual), _ptr(hand)),
-           "mhd_probe_riemann_vjp")
+    if emf is None:
+        _check(lib().mhd_probe_riemann_vjp(RIEMANN[solver], n, float(gamma), _ptr(x), _ptr(c), _ptr(dual),
+                                           _ptr(hand)), "mhd_probe_riemann_vjp")
+    else:
+        _check(lib().mhd_probe_riemann_vjp_emf(RIEMANN[solver], EMF[emf], n, float(gamma), _ptr(x), _ptr(c),
+                                               _ptr(dual), _ptr(hand)), "mhd_probe_riemann_vjp_emf")
     return dual, hand
 
 

@@ -51,6 +51,12 @@ CASES = {
         W.base_cfg(3, (7, 8, 7), (0, 0, 0), (1.0, 1.1, 1.0), recon="wenoz")),
     "3d-7x7x8-ppm-hlld-rk3": lambda: (lambda c: (c, W.random_state(c, 68, v=0.2, bamp=0.2)))(
         W.base_cfg(3, (7, 7, 8), (0, 0, 0), (1.0, 1.0, 1.1), recon="ppm", rk=3)),
+    # UCT-HLLD edge fields, and the paper's scheme (WENO-Z + HLLD + RK3 + UCT-HLLD)
+    "2d-10x9-plm-hlld-rk2-ucthlld": lambda: (lambda c: (c, W.random_state(c, 69, v=0.3, bamp=0.3)))(
+        W.base_cfg(2, (10, 9), (0, 0), (1.0, 0.9), emf="uct_hlld")),
+    "2d-12-wenoz-hlld-rk3-ucthlld": lambda: W.adjoint_2d(12, recon="wenoz", rk=3, emf="uct_hlld"),
+    "3d-7x8x7-wenoz-hlld-rk3-ucthlld": lambda: (lambda c: (c, W.random_state(c, 70, v=0.2, bamp=0.2)))(
+        W.base_cfg(3, (7, 8, 7), (0, 0, 0), (1.0, 1.1, 1.0), recon="wenoz", rk=3, emf="uct_hlld")),
 }
 
 
@@ -193,7 +199,7 @@ def test_autograd_function_gives_the_library_gradient():
 
 def test_unsupported_schemes_are_rejected():
     cfg, st = W.adjoint_2d(12)
-    for bad in (dict(cfg, emf="uct_hlld"), dict(cfg, bc=["outflow"] * 6)):
+    for bad in (dict(cfg, bc=["outflow"] * 6), dict(cfg, bc=["periodic"] * 2 + ["outflow"] * 4)):
         sim = mhd.Sim(bad, st)
         with pytest.raises(mhd.MhdError) as e:
             sim.adjoint(2, None)

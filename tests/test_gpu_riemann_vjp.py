@@ -110,3 +110,48 @@ def test_reverse_matches_oracle_directional_derivatives(solver):
         lhs = float(np.dot(hand[f], t))
         rhs = float(np.dot(cot[f], jt))
         assert abs(lhs - rhs) <= 1e-6 * max(1.0, abs(rhs)), (f, lhs, rhs)
+
+
+def test_uct_hlld_weights_reverse_equals_forward_mode():
+    """The UCT-HLLD weights (a^L, a^R, d^L, d^R of the fan region that holds
+    x/t = 0) through the hand-written reverse and through forward-mode
+    numbers: the same agreement as the flux's, on faces in every region."""
+    n = 4096
+    x = faces(n, 76)
+    cot = np.random.default_rng(77).standard_normal((n, 13))
+    dual, hand = mhd.probe_riemann_vjp("hlld", x, cot, GAMMA, emf="uct_hlld")
+    assert np.all(np.isfinite(hand))
+    scale = np.maximum(np.max(np.abs(dual), axis=1), 1e-300)
+    err = np.max(np.abs(hand - dual), axis=1) / scale
+    tol = 1e-13 / star_conditioning(x) ** 2
+    bad = np.nonzero(err > tol)[0]
+    assert bad.size == 0, [(int(f), float(err[f]), float(tol[f])) for f in bad[:5]]
+    assert np.median(err) <= 1e-15
+    # with the d^R cotangent zero and UCT-HLL's the same as the old 12-column probe
+    c12 = cot[:, :12]
+    d_old, h_old = mhd.probe_riemann_vjp("hlld", x, c12, GAMMA)
+    c13 = np.concatenate([c12, np.zeros((n, 1))], axis=1)
+    d_new, h_new = mhd.probe_riemann_vjp("hlld", x, c13, GAMMA, emf="uct_hll")
+    assert np.array_equal(h_old, h_new) and np.array_equal(d_old, d_new)
+
+
+def test_uct_hlld_reverse_matches_oracle_directional_derivatives():
+    """<xbar, t> = <ybar, J t> with J t from central differences of the
+    oracle's HLLD solver and its UCT-HLLD weights, on subsonic faces."""
+    n = 64
+    x = faces(8 * n, 78)[5 * n:6 * n]
+    rng = np.random.default_rng(79)
+    cot = rng.standard_normal((n, 13))
+    _, hand = mhd.probe_riemann_vjp("hlld", x, cot, GAMMA, emf="uct_hlld")
+    for f in range(n):
+        t = rng.standard_normal(15)
+        h = 1e-6
+
+        def out(z):
+            F, ing = oracle.riemann("hlld", z[0:7], z[7:14], z[14], GAMMA, emf="uct_hlld")
+            return np.concatenate([F, ing])
+
+        jt = (out(x[f] + h * t) - out(x[f] - h * t)) / (2 * h)
+        lhs = float(np.dot(hand[f], t))
+        rhs = float(np.dot(cot[f], jt))
+        assert abs(lhs - rhs) <= 1e-6 * max(1.0, abs(rhs)), (f, lhs, rhs)

@@ -35,6 +35,8 @@ CASES = {
         W.base_cfg(2, (8, 7), (0, 0), (1.0, 0.9), recon="wenoz", rk=3)),
     "ppm2d-7x8-hll": lambda: (lambda c: (c, W.random_state(c, 55, v=0.2, bamp=0.2)))(
         W.base_cfg(2, (7, 8), (0, 0), (0.9, 1.0), recon="ppm", riemann="hll")),
+    "wenoz2d-8x8-hlld-rk3-ucthlld": lambda: (lambda c: (c, W.random_state(c, 56, v=0.2, bamp=0.2)))(
+        W.base_cfg(2, (8, 8), (0, 0), (1.0, 1.0), recon="wenoz", rk=3, emf="uct_hlld")),
 }
 
 
@@ -81,15 +83,16 @@ def smooth_state(n=16, seed=5):
     return cfg, st, prim, (st["b0"], st["b1"], st["b2"])
 
 
-@pytest.mark.parametrize("recon", ["plm", "wenoz", "ppm"])
-def test_gradient_matches_central_differences_on_smooth_run(recon):
+@pytest.mark.parametrize("recon,emf", [("plm", "uct_hll"), ("wenoz", "uct_hll"), ("ppm", "uct_hll"),
+                                       ("wenoz", "uct_hlld")])
+def test_gradient_matches_central_differences_on_smooth_run(recon, emf):
     """Smooth 16^2 state, 4 steps, misfit to a shifted target so that dJ is of
     the order of J.  Central differences along random directions agree with
     the gradient to 1e-5.  A step size counts only if the branch signature
     (every limiter, min/max and wave-fan decision) is the same at x - h, x and
     x + h; samples that switch a branch are excluded, not passed."""
     cfg, st, prim, B = smooth_state()
-    cfg = dict(cfg, recon=recon)
+    cfg = dict(cfg, recon=recon, emf=emf)
     dts = frozen_dts(cfg, st, 4)
     keys = ["rho", "mx", "my", "mz", "E", "b2"]
     target = [np.roll(st[k], 3, axis=2) * 1.05 for k in keys]
