@@ -418,8 +418,12 @@ long long mhd_batch_launch_count(const mhd_batch* b);
  * the weights is taken, so the gradient is that of the nonlinear scheme; for
  * PPM the clip and steepening choices the forward values take), HLL or HLLD,
  * RK2 or RK3, UCT-HLL or UCT-HLLD edge fields (UCT-HLLD: through the
- * solver's fan-region weights and star ratios), periodic on every axis with at least
- * 2G+1 cells (5 for PLM, 7 for WENO-Z and PPM; MHD_ERR_ARG otherwise). */
+ * solver's fan-region weights and star ratios), periodic or outflow axes
+ * (outflow: the transposes of the zero-gradient copies and of the ghost normal
+ * field's div B = 0 march), at least 2G+1 cells per axis (5 for PLM, 7 for
+ * WENO-Z and PPM; MHD_ERR_ARG otherwise).  On a periodic axis the face at n is
+ * the ghost copy of face 0 and its gradient entry is 0; on an outflow axis it
+ * is a face of its own. */
 #define MHD_FUNC_MAGNETIC_ENERGY 0
 #define MHD_FUNC_MISFIT          1
 

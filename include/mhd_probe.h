@@ -76,6 +76,27 @@ int mhd_probe_riemann_vjp(int riemann, int n, double gamma, const double* in, co
 int mhd_probe_riemann_vjp_emf(int riemann, int emf, int n, double gamma, const double* in, const double* cot,
                               double* dual, double* hand);
 
+/* The ghost fill of a CT context and its transpose, for the dot-product check
+ * <fill(x), abar> = <x, fill^T(abar)>.  x, abar: host arrays [8][E] of whole
+ * padded fields (E = ext_x ext_y ext_z, ext_d = n_d + 2G + 1 on active axes,
+ * 1 otherwise, G = 2 for PLM and 3 for WENO-Z / PPM, x fastest), in the slot
+ * order of the state (rho, m_x, m_y, m_z, E, B_x, B_y, B_z faces; 2D: cell
+ * B_z in slot 7).  fx receives the filled x, xbar the transpose applied to
+ * abar (what the adjoint does at the end of every stage).  MHD_ERR_ARG on a
+ * GLM context.  Sync. */
+int mhd_probe_ghost_vjp(mhd_ctx* ctx, const double* x, const double* abar, double* fx, double* xbar);
+
+/* One first RK stage of a CT context, U* = U + L(U) with step dt, and its
+ * transpose: grad = J^T w, J the Jacobian of U* with respect to U and w a
+ * cotangent of U* on the evolved cells and faces (the combine transpose
+ * reads w there only).  U, w, grad:
+ * host arrays in the layout of mhd_set_conserved (rho, m_x, m_y, m_z, E, then
+ * the three face fields; 2D: cell B_z in slot 7).  Allocates the adjoint's
+ * buffers on first use and leaves the context's step size at dt (its state and
+ * time are not changed).  MHD_ERR_ARG on a GLM context.  Sync. */
+int mhd_probe_stage_vjp(mhd_ctx* ctx, const double* const* U, double dt, const double* const* w,
+                        double* const* grad);
+
 /* The sweeps' Riemann solver (MHD_RIEMANN_HLL / _HLLD) on n faces, with the
  * UCT-HLL or (emf = MHD_EMF_UCT_HLLD, HLLD only) UCT-HLLD face weights.
  * Host arrays: in[15 n] as for mhd_probe_riemann_vjp; F[7 n] receives the

@@ -74,6 +74,8 @@ def lib():
                                           ctypes.POINTER(ctypes.c_ulonglong)]
         L.orc_jvp_prim.argtypes = [ctypes.POINTER(OrcConfig), PP, PP, DP, ctypes.c_int, ctypes.c_int, PP, PP, DP, DP]
         L.orc_grad_prim.argtypes = [ctypes.POINTER(OrcConfig), PP, PP, DP, ctypes.c_int, ctypes.c_int, PP, DP, PP]
+        L.orc_grad_conserved.argtypes = [ctypes.POINTER(OrcConfig), PP, DP, ctypes.c_int, ctypes.c_int, PP, DP, PP]
+        L.orc_stage_vjp.argtypes = [ctypes.POINTER(OrcConfig), PP, D, PP, DP, PP]
         L.orc_count_flops.argtypes = [ctypes.POINTER(OrcConfig), ctypes.POINTER(DP), ctypes.c_int, D,
                                       ctypes.POINTER(ctypes.c_ulonglong)]
         L.orc_glm_create.restype = P
@@ -434,3 +436,38 @@ def grad_prim(cfg, prim, B, dts, which="magnetic_energy", target=None):
     if rc:
         raise FloatingPointError("non-positive density or pressure")
     return J.value, dict(zip(("rho", "vx", "vy", "vz"), g))
+
+
+def grad_conserved(cfg, state, dts, which="magnetic_energy", target=None):
+    """(J, grad): reverse-mode gradient of J w.r.t. every element of the initial
+    conserved state (dict of KEYS; on a periodic axis the face at n is the
+    ghost copy of face 0 and its entry is 0)."""
+    shapes = state_shapes(cfg)
+    arrs = [np.ascontiguousarray(np.asarray(state[k], dtype=np.float64).reshape(sh)) for k, sh in zip(KEYS, shapes)]
+    d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+    T = None
+    if target is not None:
+        T = [np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(shapes[0])) for t in target]
+    g = [np.zeros(sh) for sh in shapes]
+    J = ctypes.c_double()
+    rc = lib().orc_grad_conserved(ctypes.byref(make_config(cfg)), _ptrs(arrs), _dp(d), len(dts), FUNCTIONALS[which],
+                                  _parr(T) if T is not None else None, ctypes.byref(J), _parr(g))
+    if rc:
+        raise FloatingPointError("non-positive density or pressure")
+    return J.value, dict(zip(KEYS, g))
+
+
+def stage_vjp(cfg, state, dt, w):
+    """(J, grad): J = <w, U + L(U)> over the evolved cells and faces after one
+    first RK stage of size dt from state U, and its reverse-mode gradient
+    with respect to every element of U (dicts of KEYS)."""
+    shapes = state_shapes(cfg)
+    arrs = [np.ascontiguousarray(np.asarray(state[k], dtype=np.float64).reshape(sh)) for k, sh in zip(KEYS, shapes)]
+    ws = [np.ascontiguousarray(np.asarray(w[k], dtype=np.float64).reshape(sh)) for k, sh in zip(KEYS, shapes)]
+    g = [np.zeros(sh) for sh in shapes]
+    J = ctypes.c_double()
+    rc = lib().orc_stage_vjp(ctypes.byref(make_config(cfg)), _ptrs(arrs), float(dt), _ptrs(ws), ctypes.byref(J),
+                             _parr(g))
+    if rc:
+        raise FloatingPointError("non-positive density or pressure")
+    return J.value, dict(zip(KEYS, g))

@@ -378,4 +378,73 @@ int orc_grad_prim(const OrcConfig* oc, const double* const* prim, const double* 
   return bad ? -4 : 0;
 }
 
+// The same functional's reverse-mode gradient with respect to every element
+// of the initial state in the layout of orc_state_from_prims (cells rho, mx,
+// my, mz, E and the face fields): state[8] in, grad[8] out.  On a periodic
+// axis the face at n is the ghost copy of face 0, so its entry is 0.
+int orc_grad_conserved(const OrcConfig* oc, const double* const* state, const double* dts, int nsteps, int which,
+                       const double* const* target, double* J, double* const* grad) {
+  Config c = to_cfg(oc);
+  g_tape.clear();
+  Sim<Tape> s(c);
+  std::vector<std::vector<int>> ids(NQ);
+  for (int q = 0; q < NQ; q++) {
+    int e[3];
+    Ext<Tape>::extents(s, q, e);
+    const double* p = state[q];
+    for (int k = 0; k < e[2]; k++)
+      for (int j = 0; j < e[1]; j++)
+        for (int i = 0; i < e[0]; i++) {
+          Tape v = Tape::variable(*p++);
+          ids[q].push_back(v.i);
+          s.U0[q](i, j, k) = v;
+        }
+  }
+  for (int t = 0; t < nsteps; t++) s.step(Tape(dts[t]));
+  Tape r = functional(s, which, target);
+  *J = r.v;
+  std::vector<double> adj = tape_backprop(r);
+  for (int q = 0; q < NQ; q++)
+    for (size_t m = 0; m < ids[q].size(); m++) grad[q][m] = adj[ids[q][m]];
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return s.bad ? -4 : 0;
+}
+
+// One first RK stage, U* = U + L(U) with step dt: J = <w, U*> over the
+// evolved cells and faces (w in the state layout, its other entries unused),
+// and its reverse-mode gradient with respect to every element of U.
+int orc_stage_vjp(const OrcConfig* oc, const double* const* state, double dt, const double* const* w, double* J,
+                  double* const* grad) {
+  Config c = to_cfg(oc);
+  g_tape.clear();
+  Sim<Tape> s(c);
+  std::vector<std::vector<int>> ids(NQ);
+  int ext[NQ][3];
+  for (int q = 0; q < NQ; q++) {
+    Ext<Tape>::extents(s, q, ext[q]);
+    const double* p = state[q];
+    for (int k = 0; k < ext[q][2]; k++)
+      for (int j = 0; j < ext[q][1]; j++)
+        for (int i = 0; i < ext[q][0]; i++) {
+          Tape v = Tape::variable(*p++);
+          ids[q].push_back(v.i);
+          s.U0[q](i, j, k) = v;
+        }
+  }
+  s.stage_increment(s.U0, Tape(dt));
+  Tape r(0.0);
+  s.each_updated([&](int q, int i, int j, int k) {
+    const double wq = w[q][((size_t)k * ext[q][1] + j) * ext[q][0] + i];
+    r = r + Tape(wq) * (s.U0[q](i, j, k) + s.Lq[q](i, j, k));
+  });
+  *J = r.v;
+  std::vector<double> adj = tape_backprop(r);
+  for (int q = 0; q < NQ; q++)
+    for (size_t m = 0; m < ids[q].size(); m++) grad[q][m] = adj[ids[q][m]];
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return s.bad ? -4 : 0;
+}
+
 }  // extern "C"

@@ -210,6 +210,170 @@ static __global__ void adj_ghost_shell_kernel(Grid g, F8 A) {
 }
 
 // ---------------------------------------------------------------------------
+// Transposes of the per-axis ghost passes (grids with an outflow axis).  The
+// forward fills the periodic axes first, then each outflow axis with its copy
+// pass and its normal-field pass, every pass over the full padded transverse
+// range; the transposes run in the reverse order.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ long long pass_rows(const Grid& g, int d) {
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  return (long long)(g.hi(t1) - g.lo(t1) + 1) * (g.hi(t2) - g.lo(t2) + 1);
+}
+__device__ __forceinline__ void pass_row(const Grid& g, int d, long long r, int x[3]) {
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  const int e1 = g.hi(t1) - g.lo(t1) + 1;
+  x[t1] = (int)(r % e1) + g.lo(t1);
+  x[t2] = (int)(r / e1) + g.lo(t2);
+}
+
+// Periodic pass along d: each interior slot x gathers its image x - n
+// (x >= n - G) or x + n (x <= G) and clears it (n >= 2G + 1: one image at most).
+static __global__ void adj_ghost_periodic_kernel(Grid g, F8 A, int d) {
+  const int n = g.n[d];
+  const long long total = pass_rows(g, d) * n;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int y[3];
+    y[d] = (int)(id % n);
+    pass_row(g, d, id / n, y);
+    const int x = y[d];
+    int img;
+    if (x >= n - g.G) img = x - n;
+    else if (x <= g.G) img = x + n;
+    else continue;
+    const int c = g.at(y[0], y[1], y[2]);
+    y[d] = img;
+    const int ci = g.at(y[0], y[1], y[2]);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      A.q[q][c] += A.q[q][ci];
+      A.q[q][ci] = 0.0;
+    }
+  }
+}
+
+// Outflow copy pass along d: the boundary cell gathers the G copies on its
+// side (G + 1 slots on the high side, the last one the extra face slot) of
+// every slot but the normal face field, and clears them.
+static __global__ void adj_ghost_outflow_copy_kernel(Grid g, F8 A, int d) {
+  const int n = g.n[d];
+  const long long total = pass_rows(g, d);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int y[3];
+    pass_row(g, d, id, y);
+    auto at = [&](int x) {
+      y[d] = x;
+      return g.at(y[0], y[1], y[2]);
+    };
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      if (q == 5 + d) continue;
+      double* a = A.q[q];
+      double s = a[at(0)];
+      for (int x = -g.G; x < 0; x++) {
+        s += a[at(x)];
+        a[at(x)] = 0.0;
+      }
+      a[at(0)] = s;
+      s = a[at(n - 1)];
+      for (int x = n; x <= n + g.G; x++) {
+        s += a[at(x)];
+        a[at(x)] = 0.0;
+      }
+      a[at(n - 1)] = s;
+    }
+  }
+}
+
+// Outflow normal-field pass along d, part 1, per row of the pass: the forward
+// marches B_n[-m] = B_n[-m + 1] + dx_d divT(-m) (m = 1..G) and
+// B_n[n + m + 1] = B_n[n + m] - dx_d divT(n + m) (m = 0..G-1), divT the
+// tangential divergence of the ghost cell.  Walking each march back, the
+// cotangent of a ghost face, with those of the faces beyond it, passes to the
+// face inside it; H keeps each ghost face's total (the factor of its divT)
+// and the ghost faces' own cotangents are cleared.
+static __global__ void adj_ghost_outflow_chain_kernel(Grid g, F8 A, int d, double* H) {
+  const int n = g.n[d];
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  const int e1 = g.hi(t1) - g.lo(t1) + (t1 < g.ndim ? 0 : 1);
+  const long long total = ghost_rows_work(g, d);
+  double* An = A.q[5 + d];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    int y[3];
+    y[t1] = (int)(id % e1) + g.lo(t1);
+    y[t2] = (int)(id / e1) + g.lo(t2);
+    auto at = [&](int x) {
+      y[d] = x;
+      return g.at(y[0], y[1], y[2]);
+    };
+    double s = 0.0;
+    for (int m = g.G; m >= 1; m--) {
+      const int f = at(-m);
+      s += An[f];
+      An[f] = 0.0;
+      H[f] = s;
+    }
+    An[at(0)] += s;
+    s = 0.0;
+    for (int m = g.G - 1; m >= 0; m--) {
+      const int f = at(n + m + 1);
+      s += An[f];
+      An[f] = 0.0;
+      H[f] = s;
+    }
+    An[at(n)] += s;
+  }
+}
+
+// Part 2, per tangential face of the ghost cells (layer l: cells -1..-G, then
+// n..n+G-1): divT(cell) of row r holds (B_t[r + 1] - B_t[r]) / dx_t, so face f
+// of axis t gets +k H from row f - 1 and -k H from row f, k = +-dx_d / dx_t
+// (minus on the high side), H the row's factor from part 1.
+__host__ __device__ __forceinline__ long long adj_outflow_faces_work(const Grid& g, int d) {
+  return 2LL * g.G * pass_rows(g, d);
+}
+static __global__ void adj_ghost_outflow_faces_kernel(Grid g, F8 A, int d, const double* __restrict__ H) {
+  const int n = g.n[d];
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  const long long total = adj_outflow_faces_work(g, d);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(id % (2 * g.G));
+    int p[3];
+    pass_row(g, d, id / (2 * g.G), p);
+    const bool low = l < g.G;
+    const int cell = low ? -(l + 1) : n + (l - g.G);
+    const int hslot = low ? cell : cell + 1;  // the row's ghost face: B_n[-m] or B_n[n + m + 1]
+    const int ts[2] = {t1, t2};
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const int t = ts[k], u = ts[1 - k];
+      if (t >= g.ndim) continue;
+      if (u < g.ndim && p[u] > g.hi(u) - 1) continue;  // not a row of the pass across u
+      const int f = p[t];
+      const double coef = (low ? g.dx[d] : -g.dx[d]) / g.dx[t];
+      int y[3];
+      y[d] = hslot;
+      y[u] = p[u];
+      double acc = 0.0;
+      if (f - 1 >= g.lo(t)) {
+        y[t] = f - 1;
+        acc += coef * H[g.at(y[0], y[1], y[2])];
+      }
+      if (f <= g.hi(t) - 1) {
+        y[t] = f;
+        acc -= coef * H[g.at(y[0], y[1], y[2])];
+      }
+      y[d] = cell;
+      y[t] = f;
+      A.q[5 + t][g.at(y[0], y[1], y[2])] += acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Transpose of the stage combine  out = c0 U0 + c1 Us + cL L  (cells), and
 // out_B = c0 B0 + c1 Bs + cL L_B (evolved faces): the cotangents of the stage
 // increment (Lb on cells, LB on faces) and the accumulation into U0 and Us.
@@ -1042,8 +1206,14 @@ static __global__ void __launch_bounds__(128) adj_recon5_gather_kernel(Grid g, T
 //         Pb.q[4 + d] - (G-1) pb B_d, formed by the face itself.
 template <int NDIM>
 __device__ __forceinline__ double adj_c2p_gp(const Grid& g, const F8& S, const F8& P, const F8& Pb, int c) {
+  // The forward raises a recovered pressure below the floor to it in every
+  // padded cell, a floor of 0 included (outflow ghost cells can recover a
+  // negative pressure: their normal field is extrapolated, their energy
+  // copied); such a cell passes no pressure cotangent.  A stored pressure
+  // above the floor was not raised; one at the floor is decided as the
+  // forward decided it, on the IEEE pressure.
   double pb = Pb.q[7][c];
-  if (g.p_floor > 0.0) {
+  if (!(P.q[7][c] > g.p_floor)) {
     Prim8 V = c2p_ieee(S.q[0][c], S.q[1][c], S.q[2][c], S.q[3][c], S.q[4][c], P.q[4][c], P.q[5][c], P.q[6][c], g.gm1);
     if (V.p < g.p_floor) pb = 0.0;
   }

@@ -38,7 +38,8 @@ EXPORTS = ("mhd_create", "mhd_destroy", "mhd_set_conserved", "mhd_set_prim", "mh
            "mhd_batch_get_conserved", "mhd_batch_step", "mhd_batch_autotune", "mhd_batch_set_seglen",
            "mhd_batch_get_times", "mhd_batch_status", "mhd_batch_launch_count", "mhd_batch_profile_steps",
            "mhd_adjoint_run", "mhd_adjoint_grad_conserved", "mhd_adjoint_grad_prim", "mhd_adjoint_profile", "mhd_probe_riemann_vjp",
-           "mhd_probe_riemann_vjp_emf",
+           "mhd_probe_riemann_vjp_emf", "mhd_probe_ghost_vjp",
+           "mhd_probe_stage_vjp",
            "mhd_set_divb_check", "mhd_divb",
            "mhd_set_seglen", "mhd_autotune", "mhd_set_psi", "mhd_get_psi", "mhd_probe_cfl_rate", "mhd_get_seglen",
            "mhd_batch_get_conserved_async", "mhd_batch_synchronize", "mhd_batch_packed_size",
@@ -134,6 +135,8 @@ def lib():
             "mhd_adjoint_profile": (I, [P, I, ctypes.POINTER(D), I, ctypes.POINTER(D), ctypes.POINTER(D)]),
             "mhd_probe_riemann_vjp": (I, [I, I, D, P, P, P, P]),
             "mhd_probe_riemann_vjp_emf": (I, [I, I, I, D, P, P, P, P]),
+            "mhd_probe_ghost_vjp": (I, [P, P, P, P, P]),
+            "mhd_probe_stage_vjp": (I, [P, DPP, D, DPP, DPP]),
             "mhd_set_seglen": (I, [P, I]),
             "mhd_autotune": (I, [P, ctypes.POINTER(I)]),
             "mhd_set_psi": (I, [P, I, P]),
@@ -551,6 +554,29 @@ def probe_riemann_vjp(solver, inputs, cotangents, gamma, emf=None):
         _check(lib().mhd_probe_riemann_vjp_emf(RIEMANN[solver], EMF[emf], n, float(gamma), _ptr(x), _ptr(c),
                                                _ptr(dual), _ptr(hand)), "mhd_probe_riemann_vjp_emf")
     return dual, hand
+
+
+def probe_ghost_vjp(sim, x, abar):
+    """The ghost fill of sim's grid on whole padded fields x (8, E) and its
+    transpose on abar (8, E): returns (fill(x), fill^T(abar))."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    a = np.ascontiguousarray(np.asarray(abar, dtype=np.float64))
+    fx, xb = np.zeros_like(x), np.zeros_like(a)
+    _check(lib().mhd_probe_ghost_vjp(sim.h, _ptr(x), _ptr(a), _ptr(fx), _ptr(xb)), "mhd_probe_ghost_vjp")
+    return fx, xb
+
+
+def probe_stage_vjp(sim, state, dt, w):
+    """One first RK stage U* = U + L(U) of sim's scheme from state (dict of
+    KEYS) with step dt, transposed: returns J^T w (J the Jacobian of U* with
+    respect to U) as a dict of KEYS."""
+    shapes = sim.shapes
+    arrs = [np.ascontiguousarray(np.asarray(state[k], dtype=np.float64).reshape(s)) for k, s in zip(KEYS, shapes)]
+    ws = [np.ascontiguousarray(np.asarray(w[k], dtype=np.float64).reshape(s)) for k, s in zip(KEYS, shapes)]
+    out = [np.zeros(s) for s in shapes]
+    _check(lib().mhd_probe_stage_vjp(sim.h, _ptr_array(arrs), float(dt), _ptr_array(ws), _ptr_array(out)),
+           "mhd_probe_stage_vjp")
+    return dict(zip(KEYS, out))
 
 
 def probe_riemann(solver, inputs, gamma, emf="uct_hll"):
