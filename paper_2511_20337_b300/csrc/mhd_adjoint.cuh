@@ -1019,30 +1019,33 @@ struct T35 { double* q[35]; };
 //   d value / d q_k = w_k / W,   d value / d w_k = (q_k - value) / W,
 // then back through g_k, r_k, tau, be_k to t_k, u_k and the window.
 __device__ __forceinline__ void wenoz_vjp(const double a[5], double pb, double mb, double ab[5]) {
+  // the values to linearise at, formed without divisions (the reciprocal of
+  // the library, constants 1/6, 13/12): within a few ulps of the forward's
+  constexpr double k6 = 1.0 / 6.0, k13_12 = 13.0 / 12.0, k13_6 = 13.0 / 6.0;
   const double t0 = (a[0] - 2.0 * a[1]) + a[2], t1 = (a[1] - 2.0 * a[2]) + a[3], t2 = (a[2] - 2.0 * a[3]) + a[4];
   const double u0 = (a[0] - 4.0 * a[1]) + 3.0 * a[2], u1 = a[1] - a[3], u2 = (3.0 * a[2] - 4.0 * a[3]) + a[4];
-  const double be[3] = {fma(13.0 / 12.0 * t0, t0, fma(0.25 * u0, u0, kWenozEps)),
-                        fma(13.0 / 12.0 * t1, t1, fma(0.25 * u1, u1, kWenozEps)),
-                        fma(13.0 / 12.0 * t2, t2, fma(0.25 * u2, u2, kWenozEps))};
+  const double be[3] = {fma(k13_12 * t0, t0, fma(0.25 * u0, u0, kWenozEps)),
+                        fma(k13_12 * t1, t1, fma(0.25 * u1, u1, kWenozEps)),
+                        fma(k13_12 * t2, t2, fma(0.25 * u2, u2, kWenozEps))};
   const double tau = be[0] - be[2];
   double ib[3], r[3], gk[3];
 #pragma unroll
   for (int k = 0; k < 3; k++) {
-    ib[k] = 1.0 / be[k];
+    ib[k] = rcp(be[k]);
     r[k] = tau * ib[k];
     gk[k] = fma(r[k], r[k], 1.0);
   }
-  const double qp[3] = {((2.0 * a[0] - 7.0 * a[1]) + 11.0 * a[2]) / 6.0, ((-a[1] + 5.0 * a[2]) + 2.0 * a[3]) / 6.0,
-                        ((2.0 * a[2] + 5.0 * a[3]) - a[4]) / 6.0};
-  const double qm[3] = {((2.0 * a[4] - 7.0 * a[3]) + 11.0 * a[2]) / 6.0, ((-a[3] + 5.0 * a[2]) + 2.0 * a[1]) / 6.0,
-                        ((2.0 * a[2] + 5.0 * a[1]) - a[0]) / 6.0};
+  const double qp[3] = {k6 * ((2.0 * a[0] - 7.0 * a[1]) + 11.0 * a[2]), k6 * ((-a[1] + 5.0 * a[2]) + 2.0 * a[3]),
+                        k6 * ((2.0 * a[2] + 5.0 * a[3]) - a[4])};
+  const double qm[3] = {k6 * ((2.0 * a[4] - 7.0 * a[3]) + 11.0 * a[2]), k6 * ((-a[3] + 5.0 * a[2]) + 2.0 * a[1]),
+                        k6 * ((2.0 * a[2] + 5.0 * a[1]) - a[0])};
   const double wp[3] = {0.1 * gk[0], 0.6 * gk[1], 0.3 * gk[2]};
   const double wm[3] = {0.1 * gk[2], 0.6 * gk[1], 0.3 * gk[0]};
-  const double Wp = (wp[0] + wp[1]) + wp[2], Wm = (wm[0] + wm[1]) + wm[2];
-  const double vp = ((wp[0] * qp[0] + wp[1] * qp[1]) + wp[2] * qp[2]) / Wp;
-  const double vm = ((wm[0] * qm[0] + wm[1] * qm[1]) + wm[2] * qm[2]) / Wm;
+  const double iWp = rcp((wp[0] + wp[1]) + wp[2]), iWm = rcp((wm[0] + wm[1]) + wm[2]);
+  const double vp = fma(wp[0], qp[0], fma(wp[1], qp[1], wp[2] * qp[2])) * iWp;
+  const double vm = fma(wm[0], qm[0], fma(wm[1], qm[1], wm[2] * qm[2])) * iWm;
   // reverse
-  const double sp = pb / Wp, sm = mb / Wm;
+  const double sp = pb * iWp, sm = mb * iWm;
   double qbp[3], qbm[3], wbp[3], wbm[3];
 #pragma unroll
   for (int k = 0; k < 3; k++) {
@@ -1051,24 +1054,24 @@ __device__ __forceinline__ void wenoz_vjp(const double a[5], double pb, double m
     wbp[k] = sp * (qp[k] - vp);
     wbm[k] = sm * (qm[k] - vm);
   }
-  const double gb[3] = {0.1 * wbp[0] + 0.3 * wbm[2], 0.6 * (wbp[1] + wbm[1]), 0.3 * wbp[2] + 0.1 * wbm[0]};
+  const double gb[3] = {fma(0.1, wbp[0], 0.3 * wbm[2]), 0.6 * (wbp[1] + wbm[1]), fma(0.3, wbp[2], 0.1 * wbm[0])};
   double taub = 0.0, beb[3];
 #pragma unroll
   for (int k = 0; k < 3; k++) {
     const double rb = 2.0 * r[k] * gb[k];
-    taub += rb * ib[k];
+    taub = fma(rb, ib[k], taub);
     beb[k] = -rb * r[k] * ib[k];
   }
   beb[0] += taub;
   beb[2] -= taub;
-  const double tb0 = 13.0 / 6.0 * t0 * beb[0], tb1 = 13.0 / 6.0 * t1 * beb[1], tb2 = 13.0 / 6.0 * t2 * beb[2];
+  const double tb0 = k13_6 * t0 * beb[0], tb1 = k13_6 * t1 * beb[1], tb2 = k13_6 * t2 * beb[2];
   const double ub0 = 0.5 * u0 * beb[0], ub1 = 0.5 * u1 * beb[1], ub2 = 0.5 * u2 * beb[2];
-  ab[0] = (tb0 + ub0) + (2.0 * qbp[0] - qbm[2]) / 6.0;
-  ab[1] = ((-2.0 * tb0 + tb1) + (-4.0 * ub0 + ub1)) + (((-7.0 * qbp[0] - qbp[1]) + 2.0 * qbm[1]) + 5.0 * qbm[2]) / 6.0;
-  ab[2] = ((tb0 - 2.0 * tb1) + tb2) + 3.0 * (ub0 + ub2) +
-          ((11.0 * (qbp[0] + qbm[0]) + 5.0 * (qbp[1] + qbm[1])) + 2.0 * (qbp[2] + qbm[2])) / 6.0;
-  ab[3] = ((tb1 - 2.0 * tb2) + (-ub1 - 4.0 * ub2)) + (((2.0 * qbp[1] + 5.0 * qbp[2]) - 7.0 * qbm[0]) - qbm[1]) / 6.0;
-  ab[4] = (tb2 + ub2) + (2.0 * qbm[0] - qbp[2]) / 6.0;
+  ab[0] = fma(k6, 2.0 * qbp[0] - qbm[2], tb0 + ub0);
+  ab[1] = fma(k6, ((-7.0 * qbp[0] - qbp[1]) + 2.0 * qbm[1]) + 5.0 * qbm[2], (-2.0 * tb0 + tb1) + (-4.0 * ub0 + ub1));
+  ab[2] = fma(k6, (11.0 * (qbp[0] + qbm[0]) + 5.0 * (qbp[1] + qbm[1])) + 2.0 * (qbp[2] + qbm[2]),
+              ((tb0 - 2.0 * tb1) + tb2) + 3.0 * (ub0 + ub2));
+  ab[3] = fma(k6, ((2.0 * qbp[1] + 5.0 * qbp[2]) - 7.0 * qbm[0]) - qbm[1], (tb1 - 2.0 * tb2) + (-ub1 - 4.0 * ub2));
+  ab[4] = fma(k6, 2.0 * qbm[0] - qbp[2], tb2 + ub2);
 }
 
 // Reverse of ppm_face(a, b, c, d): the clipped fourth-order value passes its
@@ -1087,10 +1090,10 @@ __device__ __forceinline__ void ppm_face_vjp(double a, double b, double c, doubl
     if (order_key(c) < order_key(b)) ab[2] = fb;  // imin(b, c) = c
     else ab[1] = fb;
   } else {
-    ab[0] = -fb / 12.0;
-    ab[1] = 7.0 * fb / 12.0;
-    ab[2] = 7.0 * fb / 12.0;
-    ab[3] = -fb / 12.0;
+    ab[0] = (-1.0 / 12.0) * fb;
+    ab[1] = (7.0 / 12.0) * fb;
+    ab[2] = ab[1];
+    ab[3] = ab[0];
   }
 }
 // Reverse of recon_ppm: the branch the forward values take (flattened,
