@@ -103,6 +103,9 @@ WORKLOADS = {
                       "gradient of the final magnetic energy w.r.t. the initial rho and v, checkpoints every 20 steps"),
     "adjoint2d-256-hll": (lambda: W.adjoint_2d(256, riemann="hll"), "adjoint2d_plm_hll_rk2",
                           "adjoint2d-256 with the HLL Riemann solver"),
+    "adjoint2d-256-paper": (lambda: W.adjoint_2d(256, recon="wenoz", rk=3, emf="uct_hlld"),
+                            "adjoint2d_wenoz_hlld_rk3_ucthlld",
+                            "adjoint2d-256 with the paper's scheme: WENO-Z + HLLD + SSP-RK3 + UCT-HLLD"),
 }
 ADJOINT_STEPS, ADJOINT_CKPT = 400, 20
 # The paper's single-node FP64 3D Orszag-Tang throughput per GPU (its per-node figures over 4 GPUs), quoted
@@ -134,6 +137,8 @@ SAMPLES = {
                        "the first 16 ensemble members of at most 128^2 cells"),
     "adjoint2d-256": (lambda: W.adjoint_2d(32), "the same recipe on 32^2, 8 steps"),
     "adjoint2d-256-hll": (lambda: W.adjoint_2d(32, riemann="hll"), "the same recipe on 32^2, 8 steps (HLL)"),
+    "adjoint2d-256-paper": (lambda: W.adjoint_2d(32, recon="wenoz", rk=3, emf="uct_hlld"),
+                            "the same recipe on 32^2, 8 steps (WENO-Z + HLLD + RK3 + UCT-HLLD)"),
 }
 ADJOINT_SAMPLE_STEPS = 8
 

@@ -58,6 +58,7 @@ VARIANTS = {
     "cpa3d_wenoz_hlld_rk3_ucthlld": lambda: W.cpa_3d(16, recon="wenoz", rk=3, emf="uct_hlld"),
     "adjoint2d_plm_hlld_rk2": lambda: W.adjoint_2d(32),
     "adjoint2d_plm_hll_rk2": lambda: W.adjoint_2d(32, riemann="hll"),
+    "adjoint2d_wenoz_hlld_rk3_ucthlld": lambda: W.adjoint_2d(32, recon="wenoz", rk=3, emf="uct_hlld"),
 }
 
 
