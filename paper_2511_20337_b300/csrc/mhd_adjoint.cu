@@ -250,6 +250,11 @@ void adj_riemann_dir(mhd_ctx* c, const F8& Xs, const F8& Ps, const F8& As, doubl
   const Grid& g = c->g;
   long long faces = 1;
   for (int d = 0; d < 3; d++) faces *= d == DIR ? g.n[d] + 1 : (d < NDIM ? g.n[d] + 2 : 1);
+  if constexpr (RECON != RECON_PLM) {
+    adj_face_states_kernel<DIR, NDIM, RECON><<<blocks_for(adj_face_states_work<DIR, NDIM>(g), 128), 128, 0, st>>>(
+        g, Ps, a->WbL[DIR], a->WbR[DIR]);
+    c->launches++;
+  }
   adj_riemann_kernel<DIR, NDIM, RS, RECON><<<(int)((faces + 127) / 128), 128, 0, st>>>(
       g, Ps, Xs.q[5 + DIR], a->Lb, a->GE, dt, a->WbL[DIR], a->WbR[DIR], As.q[5 + DIR], plm_codes(a, DIR));
   prof_mark(c, MHD_AKCLASS_RIEMANN);

@@ -780,6 +780,42 @@ static __global__ void riemann_vjp_probe_kernel(int n, double gamma, const doubl
   for (int i = 0; i < 15; i++) hand[15 * f + i] = xb[i];
 }
 
+// WENO-Z / PPM: the face states of direction DIR, each cell's reconstruction
+// formed once (cells [-1, n] along DIR, [-1, n] across): its plus state into
+// WbL at face x+1, its minus state into WbR at face x -- the slots where the
+// Riemann transpose of that face reads them and then stores their cotangents.
+template <int DIR, int NDIM>
+__host__ __device__ __forceinline__ long long adj_face_states_work(const Grid& g) {
+  long long w = 1;
+  for (int d = 0; d < 3; d++) w *= d == DIR ? g.n[d] + 2 : (d < NDIM ? g.n[d] + 2 : 1);
+  return w;
+}
+template <int DIR, int NDIM, int RECON>
+static __global__ void __launch_bounds__(128) adj_face_states_kernel(Grid g, F8 P, F8 WbL, F8 WbR) {
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= adj_face_states_work<DIR, NDIM>(g)) return;
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  int lo[3], ext[3];
+  sweep_box<DIR, NDIM>(g, lo, ext, -1, g.n[DIR]);
+  int x[3];
+  box_index(id, lo, ext, x);
+  const int co = g.at(x[0], x[1], x[2]);
+  const int st = g.stride(DIR);
+  const double* pr[7] = {P.q[0], P.q[1 + DIR], P.q[1 + T1], P.q[1 + T2], P.q[4 + T1], P.q[4 + T2], P.q[7]};
+  double w[7][5], plus[7], minus[7];
+#pragma unroll
+  for (int v = 0; v < 7; v++)
+#pragma unroll
+    for (int m = 0; m < 5; m++) w[v][m] = pr[v][co + (m - 2) * st];
+  recon_cell5<RECON>(w, plus, minus);
+  const bool up = x[DIR] + 1 <= g.n[DIR], down = x[DIR] >= 0;
+#pragma unroll
+  for (int v = 0; v < 7; v++) {
+    if (up) WbL.q[v][co + st] = plus[v];
+    if (down) WbR.q[v][co] = minus[v];
+  }
+}
+
 template <int DIR, int NDIM>
 __host__ __device__ __forceinline__ long long adj_riemann_work(const Grid& g) {
   long long faces = 1;
@@ -800,22 +836,12 @@ __device__ __forceinline__ void adj_riemann_item(const Grid& g, const F8& P, con
   const double* pr[7] = {P.q[0], P.q[1 + DIR], P.q[1 + T1], P.q[1 + T2], P.q[4 + T1], P.q[4 + T2], P.q[7]};
   // the face's states: plus of cell f-1 and minus of cell f
   double xin[15];
-  if constexpr (RECON != RECON_PLM) {  // five-cell windows; no decisions recorded (the transpose re-derives them)
-    double w[7][5], plus[7], minus[7];
+  if constexpr (RECON != RECON_PLM) {  // the states adj_face_states_kernel left in the cotangent slots
 #pragma unroll
-    for (int v = 0; v < 7; v++)
-#pragma unroll
-      for (int m = 0; m < 5; m++) w[v][m] = pr[v][cf + (m - 3) * st];
-    recon_cell5<RECON>(w, plus, minus);  // cell f-1
-#pragma unroll
-    for (int v = 0; v < 7; v++) xin[v] = plus[v];
-#pragma unroll
-    for (int v = 0; v < 7; v++)
-#pragma unroll
-      for (int m = 0; m < 5; m++) w[v][m] = pr[v][cf + (m - 2) * st];
-    recon_cell5<RECON>(w, plus, minus);  // cell f
-#pragma unroll
-    for (int v = 0; v < 7; v++) xin[7 + v] = minus[v];
+    for (int v = 0; v < 7; v++) {
+      xin[v] = WbL.q[v][cf];
+      xin[7 + v] = WbR.q[v][cf];
+    }
   } else {
     double w[7][3], plus[7], minus[7];
 #pragma unroll
