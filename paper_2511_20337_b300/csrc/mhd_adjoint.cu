@@ -89,7 +89,9 @@ namespace {
 constexpr int kScratchFields = 4 * 8 + 6 + 3 + 3 * 20 + 3 * (8 + 8) + 8 + 6;
 
 // The per-cell PLM decisions of the current direction (adj_riemann_kernel ->
-// adj_recon_all_kernel) live in the face-state cotangent fields' spare slot 7.
+// adj_recon_all_kernel), or the WENO-Z / PPM positivity fallbacks
+// (adj_face_states_kernel -> adj_recon5_cell_kernel), live in the face-state
+// cotangent fields' spare slot 7.
 unsigned* plm_codes(const AdjointState* a, int d) { return reinterpret_cast<unsigned*>(a->WbL[d].q[7]); }
 
 F8 state_at(const AdjointState* a, size_t idx) {
@@ -252,7 +254,7 @@ void adj_riemann_dir(mhd_ctx* c, const F8& Xs, const F8& Ps, const F8& As, doubl
   for (int d = 0; d < 3; d++) faces *= d == DIR ? g.n[d] + 1 : (d < NDIM ? g.n[d] + 2 : 1);
   if constexpr (RECON != RECON_PLM) {
     adj_face_states_kernel<DIR, NDIM, RECON><<<blocks_for(adj_face_states_work<DIR, NDIM>(g), 128), 128, 0, st>>>(
-        g, Ps, a->WbL[DIR], a->WbR[DIR]);
+        g, Ps, a->WbL[DIR], a->WbR[DIR], plm_codes(a, DIR));
     c->launches++;
   }
   adj_riemann_kernel<DIR, NDIM, RS, RECON><<<(int)((faces + 127) / 128), 128, 0, st>>>(
@@ -269,8 +271,8 @@ void adj_recon5_dir(mhd_ctx* c, const F8& Ps, const T35& T) {
   AdjointState* a = c->adj;
   const Grid& g = c->g;
   const long long cells = adj_recon5_cells<DIR, NDIM>(g, g.n[DIR] + 2);
-  adj_recon5_cell_kernel<DIR, NDIM, RECON><<<blocks_for(cells, 128), 128, 0, c->stream>>>(g, Ps, a->WbL[DIR],
-                                                                                          a->WbR[DIR], T);
+  adj_recon5_cell_kernel<DIR, NDIM, RECON><<<blocks_for(cells, 128), 128, 0, c->stream>>>(
+      g, Ps, a->WbL[DIR], a->WbR[DIR], plm_codes(a, DIR), T);
   const long long reach = adj_recon5_cells<DIR, NDIM>(g, g.n[DIR] + 6);
   adj_recon5_gather_kernel<DIR, NDIM><<<blocks_for(reach, 128), 128, 0, c->stream>>>(g, T, a->Pb);
   c->launches += 2;

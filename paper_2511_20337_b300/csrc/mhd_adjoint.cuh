@@ -791,7 +791,8 @@ __host__ __device__ __forceinline__ long long adj_face_states_work(const Grid& g
   return w;
 }
 template <int DIR, int NDIM, int RECON>
-static __global__ void __launch_bounds__(128) adj_face_states_kernel(Grid g, F8 P, F8 WbL, F8 WbR) {
+static __global__ void __launch_bounds__(128) adj_face_states_kernel(Grid g, F8 P, F8 WbL, F8 WbR,
+                                                                     unsigned* fallback) {
   const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= adj_face_states_work<DIR, NDIM>(g)) return;
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
@@ -807,7 +808,7 @@ static __global__ void __launch_bounds__(128) adj_face_states_kernel(Grid g, F8 
   for (int v = 0; v < 7; v++)
 #pragma unroll
     for (int m = 0; m < 5; m++) w[v][m] = pr[v][co + (m - 2) * st];
-  recon_cell5<RECON>(w, plus, minus);
+  fallback[co] = recon_cell5<RECON>(w, plus, minus) ? 1u : 0u;  // for the reconstruction transpose
   const bool up = x[DIR] + 1 <= g.n[DIR], down = x[DIR] >= 0;
 #pragma unroll
   for (int v = 0; v < 7; v++) {
@@ -1164,7 +1165,7 @@ __host__ __device__ __forceinline__ long long adj_recon5_cells(const Grid& g, in
 }
 template <int DIR, int NDIM, int RECON>
 __device__ __forceinline__ void adj_recon5_cell_item(const Grid& g, const F8& P, const F8& WbL, const F8& WbR,
-                                                     const T35& T, long long id) {
+                                                     const unsigned* fallback, const T35& T, long long id) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   int lo[3], ext[3];
   sweep_box<DIR, NDIM>(g, lo, ext, -1, g.n[DIR]);
@@ -1179,11 +1180,7 @@ __device__ __forceinline__ void adj_recon5_cell_item(const Grid& g, const F8& P,
   for (int v = 0; v < 7; v++)
 #pragma unroll
     for (int m = 0; m < 5; m++) w[v][m] = pr[v][co + (m - 2) * st];
-  // the positivity fallback, decided as the forward decides it
-  double p0, m0, p6, m6;
-  recon_one5<RECON>(w[0], p0, m0);
-  recon_one5<RECON>(w[6], p6, m6);
-  const bool fb = !gt0(p0) || !gt0(m0) || !gt0(p6) || !gt0(m6);
+  const bool fb = fallback[co] != 0u;  // the positivity fallback adj_face_states_kernel recorded
 #pragma unroll
   for (int v = 0; v < 7; v++) {
     const double pb = x[DIR] + 1 <= n ? WbL.q[v][co + st] : 0.0;
@@ -1197,10 +1194,11 @@ __device__ __forceinline__ void adj_recon5_cell_item(const Grid& g, const F8& P,
   }
 }
 template <int DIR, int NDIM, int RECON>
-static __global__ void __launch_bounds__(128) adj_recon5_cell_kernel(Grid g, F8 P, F8 WbL, F8 WbR, T35 T) {
+static __global__ void __launch_bounds__(128) adj_recon5_cell_kernel(Grid g, F8 P, F8 WbL, F8 WbR,
+                                                                     const unsigned* __restrict__ fallback, T35 T) {
   const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= adj_recon5_cells<DIR, NDIM>(g, g.n[DIR] + 2)) return;
-  adj_recon5_cell_item<DIR, NDIM, RECON>(g, P, WbL, WbR, T, id);
+  adj_recon5_cell_item<DIR, NDIM, RECON>(g, P, WbL, WbR, fallback, T, id);
 }
 template <int DIR, int NDIM>
 static __global__ void __launch_bounds__(128) adj_recon5_gather_kernel(Grid g, T35 T, F8 Pb) {
