@@ -588,9 +588,14 @@ __device__ __forceinline__ void recon_plm(double s1, double s2, double s3, doubl
 // g_k = 1 + r_k^2 are formed once for both faces, and so is the middle
 // weight d_1 g_1.  The candidates are formed as 6 q_k and the normalisation
 // as 6 sum_k alpha_k = sum_k (6 d_k) g_k.
+// Two of the minus face's candidates are the plus-face candidates of the
+// cell before: both faces meet at x_{i-1/2}, where the stencils of cells
+// i-2..i and i-1..i+1 give one value whichever cell they are seen from.  So
+// qm1, qm2 (6 q_1, 6 q_2 of the minus face) come in, and the plus face's
+// 6 q_2, 6 q_1 -- the next cell's qm1, qm2 -- go out in the same variables.
 __device__ __forceinline__ void wenoz_from_indicators(double a0, double a1, double a2, double a3, double a4,
-                                                      double be0, double be1, double be2, double& plus,
-                                                      double& minus) {
+                                                      double be0, double be1, double be2, double& qm1,
+                                                      double& qm2, double& plus, double& minus) {
   // be_k = beta_k + eps, the epsilon already added in a free addend slot of
   // the indicators' FMAs; tau5 = |be_0 - be_2| up to its sign, which the
   // squares of r_k drop
@@ -602,22 +607,31 @@ __device__ __forceinline__ void wenoz_from_indicators(double a0, double a1, doub
   // alpha_k = d_k g_k: the plus face weighs (g0, g1, g2), the minus face (g2, g1, g0)
   const double w1 = kmul(RK_0_6, g1);
   const double K1 = kmul(RK_3_6, g1);  // 6 d_1 g_1
-  {  // plus face: stencils (a0 a1 a2), (a1 a2 a3), (a2 a3 a4); 6 q_k
-    const double q0 = fma(rk(RK_2), a0, fma(rk(RK_M7), a1, kmul(RK_11, a2)));
+  {  // plus face: stencils (a0 a1 a2), (a1 a2 a3), (a2 a3 a4); 6 q_k, and 6 d_0 q_0 with d_0
+     // folded into the stencil's coefficients (q_0 is used by one face only)
+    const double q0 = fma(rk(RK_0_2), a0, fma(rk(RK_M0_7), a1, kmul(RK_1_1, a2)));
     const double q1 = fma(rk(RK_5), a2, fma(rk(RK_2), a3, -a1));
     const double q2 = fma(rk(RK_2), a2, fma(rk(RK_5), a3, -a4));
-    const double num = fma(kmul(RK_0_1, g0), q0, fma(w1, q1, fmul(kmul(RK_0_3, g2), q2)));
+    const double num = fma(g0, q0, fma(w1, q1, fmul(kmul(RK_0_3, g2), q2)));
     const double den = fma(rk(RK_0_6), g0, fma(rk(RK_1_8), g2, K1));  // 6 sum alpha_k
     plus = fmul(num, rcp(den));
+    // minus face: the mirrored stencils with g2, g1, g0; q1, q2 from the cell before
+    const double q0m = fma(rk(RK_0_2), a4, fma(rk(RK_M0_7), a3, kmul(RK_1_1, a2)));
+    const double numm = fma(g2, q0m, fma(w1, qm1, fmul(kmul(RK_0_3, g0), qm2)));
+    const double denm = fma(rk(RK_0_6), g2, fma(rk(RK_1_8), g0, K1));
+    minus = fmul(numm, rcp(denm));
+    qm1 = q2;
+    qm2 = q1;
   }
-  {  // minus face: the mirrored stencils with g2, g1, g0
-    const double q0 = fma(rk(RK_2), a4, fma(rk(RK_M7), a3, kmul(RK_11, a2)));
-    const double q1 = fma(rk(RK_5), a2, fma(rk(RK_2), a1, -a3));
-    const double q2 = fma(rk(RK_2), a2, fma(rk(RK_5), a1, -a0));
-    const double num = fma(kmul(RK_0_1, g2), q0, fma(w1, q1, fmul(kmul(RK_0_3, g0), q2)));
-    const double den = fma(rk(RK_0_6), g2, fma(rk(RK_1_8), g0, K1));
-    minus = fmul(num, rcp(den));
-  }
+}
+
+// The minus face's 6 q_1 and 6 q_2 of the cell whose window starts with
+// a0..a3, formed as the plus face of the cell before forms them (its q_2 and
+// q_1), so that a march gives the same bits wherever it starts.
+__device__ __forceinline__ void wenoz_minus_q12(double a0, double a1, double a2, double a3, double& qm1,
+                                                double& qm2) {
+  qm1 = fma(rk(RK_2), a1, fma(rk(RK_5), a2, -a3));
+  qm2 = fma(rk(RK_5), a1, fma(rk(RK_2), a2, -a0));
 }
 
 // beta_k = (13/12) (a_{j-1} - 2 a_j + a_{j+1})^2 + (1/4) u_k^2, the curvature
@@ -628,7 +642,8 @@ __device__ __forceinline__ void wenoz_from_indicators(double a0, double a1, doub
 //   P0, P1 = the curvature terms of the stencils centred at a1 and a2, each
 //            plus the WENO-Z epsilon (so every indicator arrives as beta + eps),
 //   h      = u_0 / 2 = (a0 - 4 a1 + 3 a2) / 2,
-//   d      = a3 - a2.
+//   d      = a3 - a2,
+//   m1, m2 = 6 q_1, 6 q_2 of the minus face (wenoz_from_indicators).
 // With t2 = (a4 - a3) - d the curvature at a3, u_2 / 2 = t2 / 2 - d and
 // u_1 / 2 = (a1 - a3) / 2; the next cell's u_0 / 2 = u_1 / 2 + 2 d.
 // wenoz_start forms the carry of a segment's first window with the very
@@ -636,7 +651,7 @@ __device__ __forceinline__ void wenoz_from_indicators(double a0, double a1, doub
 // difference, (a0 - a2)/2 + 2 (a2 - a1)), so every cell's result is the same
 // to the bit wherever a segment starts.
 struct WzCarry {
-  double P0, P1, h, d;
+  double P0, P1, h, d, m1, m2;
 };
 __device__ __forceinline__ WzCarry wenoz_start(double a0, double a1, double a2, double a3) {
   WzCarry c;
@@ -646,6 +661,7 @@ __device__ __forceinline__ WzCarry wenoz_start(double a0, double a1, double a2, 
   c.P0 = fma(kmul(RK_13_12, t0), t0, rk(RK_WEPS));
   c.P1 = fma(kmul(RK_13_12, t1), t1, rk(RK_WEPS));
   c.h = fma(rk(RK_2), d12, fma(rk(RK_HALF), a0, kmul(RK_MHALF, a2)));
+  wenoz_minus_q12(a0, a1, a2, a3, c.m1, c.m2);
   return c;
 }
 __device__ __forceinline__ void recon_wenoz_m(double a0, double a1, double a2, double a3, double a4, WzCarry& c,
@@ -662,7 +678,7 @@ __device__ __forceinline__ void recon_wenoz_m(double a0, double a1, double a2, d
   c.P0 = c.P1;
   c.P1 = P2;
   c.d = d34;
-  wenoz_from_indicators(a0, a1, a2, a3, a4, b0, b1, b2, plus, minus);
+  wenoz_from_indicators(a0, a1, a2, a3, a4, b0, b1, b2, c.m1, c.m2, plus, minus);
 }
 
 // The same reconstruction from the curvatures alone (the GLM sweep carries
@@ -688,7 +704,9 @@ __device__ __forceinline__ void recon_wenoz_c(double a0, double a1, double a2, d
   c2 = curv(a2, a3, a4);
   u = fma(rk(RK_3), a2, fma(rk(RK_M4), a3, a4));
   double b2 = fma(c2.k, c2.t, fma(kmul(RK_QUARTER, u), u, rk(RK_WEPS)));
-  wenoz_from_indicators(a0, a1, a2, a3, a4, b0, b1, b2, plus, minus);
+  double qm1, qm2;
+  wenoz_minus_q12(a0, a1, a2, a3, qm1, qm2);
+  wenoz_from_indicators(a0, a1, a2, a3, a4, b0, b1, b2, qm1, qm2, plus, minus);
 }
 __device__ __forceinline__ void recon_wenoz(double a0, double a1, double a2, double a3, double a4, double& plus,
                                             double& minus) {
