@@ -1036,69 +1036,85 @@ static __global__ void __launch_bounds__(128) adj_recon_all_kernel(Grid g, const
 // ---------------------------------------------------------------------------
 struct T35 { double* q[35]; };
 
-// Reverse of recon_wenoz for one variable: the window cotangents ab[0..4]
-// from those of the plus and minus face values.  With the curvatures t_k,
-// the one-sided terms u_k, be_k = 13/12 t_k^2 + 1/4 u_k^2 + eps,
-// tau = be_0 - be_2 (its sign drops out of the squares), r_k = tau / be_k,
-// g_k = 1 + r_k^2, weights w+ = (g0/10, 6 g1/10, 3 g2/10) for the plus face
-// and w- = (g2/10, 6 g1/10, 3 g0/10) for the minus face, and the candidates
-// q+_k, q-_k, value = sum w_k q_k / sum w_k:
-//   d value / d q_k = w_k / W,   d value / d w_k = (q_k - value) / W,
-// then back through g_k, r_k, tau, be_k to t_k, u_k and the window.
+// Constants of the WENO-Z reverse that the shared register table lacks, read
+// into registers the same way (a DFMA with a register operand issues faster
+// than one with a constant-bank operand).
+__device__ double kWzAdjK[2] = {-0.6, -6.0};
+__device__ __forceinline__ double wk(int i) { return __ldg(&kWzAdjK[i]); }
+
+// Reverse of recon_wenoz (both faces of the middle cell of a[0..4]): ab[]
+// receives the window cotangents for pb = dJ/d(plus), mb = dJ/d(minus).  The
+// values to linearise at are formed without divisions, within a few ulps of
+// the forward's, in scaled forms that the FMAs take for free: the indicators
+// as BE_k = 4 (beta_k + eps) = (13/3) t_k^2 + u_k^2 + 4 eps (the factor
+// cancels in r_k = tau5 / (beta_k + eps)), the candidates as Q_k = 6 q_k with
+// d_0 folded into Q_0' = 6 d_0 q_0, so that with g_k = 1 + r_k^2
+//   plus = num / den,  num = g_0 Q_0' + 0.6 g_1 Q_1 + 0.3 g_2 Q_2,
+//   den = 0.6 g_0 + 3.6 g_1 + 1.8 g_2  (= 6 sum_k d_k g_k),
+// and the mirrored weights for minus.  Reverse, with P = pb / den:
+//   dJ/dQ_0' = P g_0, dJ/dQ_1 = 0.6 P g_1, dJ/dQ_2 = 0.3 P g_2,
+//   dJ/dg_0 = P (Q_0' - 0.6 plus), dJ/dg_1 = 0.6 P (Q_1 - 6 plus),
+//   dJ/dg_2 = 0.3 P (Q_2 - 6 plus)  (and the mirror for minus);
+//   g_k = 1 + r_k^2, r_k = tau ib_k, ib_k = 1 / BE_k: with S_k = r_k gb_k ib_k,
+//   dJ/dtau = 2 sum_k S_k, dJ/dBE_k = -2 S_k r_k, plus dJ/dtau for k = 0 and
+//   minus it for k = 2; E_k = 2 dJ/dBE_k carries the factor 2 of
+//   dBE_k/dt_k = 2 (13/3) t_k and dBE_k/du_k = 2 u_k;
+// then the transposes of the linear stencils t_k, u_k and Q.
 __device__ __forceinline__ void wenoz_vjp(const double a[5], double pb, double mb, double ab[5]) {
-  // the values to linearise at, formed without divisions (the reciprocal of
-  // the library, constants 1/6, 13/12): within a few ulps of the forward's
-  constexpr double k6 = 1.0 / 6.0, k13_12 = 13.0 / 12.0, k13_6 = 13.0 / 6.0;
-  const double t0 = (a[0] - 2.0 * a[1]) + a[2], t1 = (a[1] - 2.0 * a[2]) + a[3], t2 = (a[2] - 2.0 * a[3]) + a[4];
-  const double u0 = (a[0] - 4.0 * a[1]) + 3.0 * a[2], u1 = a[1] - a[3], u2 = (3.0 * a[2] - 4.0 * a[3]) + a[4];
-  const double be[3] = {fma(k13_12 * t0, t0, fma(0.25 * u0, u0, kWenozEps)),
-                        fma(k13_12 * t1, t1, fma(0.25 * u1, u1, kWenozEps)),
-                        fma(k13_12 * t2, t2, fma(0.25 * u2, u2, kWenozEps))};
-  const double tau = be[0] - be[2];
-  double ib[3], r[3], gk[3];
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    ib[k] = rcp(be[k]);
-    r[k] = tau * ib[k];
-    gk[k] = fma(r[k], r[k], 1.0);
-  }
-  const double qp[3] = {k6 * ((2.0 * a[0] - 7.0 * a[1]) + 11.0 * a[2]), k6 * ((-a[1] + 5.0 * a[2]) + 2.0 * a[3]),
-                        k6 * ((2.0 * a[2] + 5.0 * a[3]) - a[4])};
-  const double qm[3] = {k6 * ((2.0 * a[4] - 7.0 * a[3]) + 11.0 * a[2]), k6 * ((-a[3] + 5.0 * a[2]) + 2.0 * a[1]),
-                        k6 * ((2.0 * a[2] + 5.0 * a[1]) - a[0])};
-  const double wp[3] = {0.1 * gk[0], 0.6 * gk[1], 0.3 * gk[2]};
-  const double wm[3] = {0.1 * gk[2], 0.6 * gk[1], 0.3 * gk[0]};
-  const double iWp = rcp((wp[0] + wp[1]) + wp[2]), iWm = rcp((wm[0] + wm[1]) + wm[2]);
-  const double vp = fma(wp[0], qp[0], fma(wp[1], qp[1], wp[2] * qp[2])) * iWp;
-  const double vm = fma(wm[0], qm[0], fma(wm[1], qm[1], wm[2] * qm[2])) * iWm;
+  // forward
+  const double t0 = fadd(fma(rk(RK_M2), a[1], a[0]), a[2]);
+  const double t1 = fadd(fma(rk(RK_M2), a[2], a[1]), a[3]);
+  const double t2 = fadd(fma(rk(RK_M2), a[3], a[2]), a[4]);
+  const double u0 = fma(rk(RK_3), a[2], fma(rk(RK_M4), a[1], a[0]));
+  const double u1 = fsub(a[1], a[3]);
+  const double u2 = fma(rk(RK_3), a[2], fma(rk(RK_M4), a[3], a[4]));
+  const double K0 = kmul(RK_13_3, t0), K1 = kmul(RK_13_3, t1), K2 = kmul(RK_13_3, t2);
+  const double be0 = fma(K0, t0, fma(u0, u0, rk(RK_4WEPS)));
+  const double be1 = fma(K1, t1, fma(u1, u1, rk(RK_4WEPS)));
+  const double be2 = fma(K2, t2, fma(u2, u2, rk(RK_4WEPS)));
+  const double tau = fsub(be0, be2);
+  const double ib0 = rcp(be0), ib1 = rcp(be1), ib2 = rcp(be2);
+  const double r0 = fmul(tau, ib0), r1 = fmul(tau, ib1), r2 = fmul(tau, ib2);
+  const double g0 = fma(r0, r0, rk(RK_ONE)), g1 = fma(r1, r1, rk(RK_ONE)), g2 = fma(r2, r2, rk(RK_ONE));
+  const double c11 = kmul(RK_1_1, a[2]);
+  const double Qp0 = fma(rk(RK_0_2), a[0], fma(rk(RK_M0_7), a[1], c11));
+  const double Qp1 = fma(rk(RK_5), a[2], fma(rk(RK_2), a[3], -a[1]));
+  const double Qp2 = fma(rk(RK_2), a[2], fma(rk(RK_5), a[3], -a[4]));
+  const double Qm0 = fma(rk(RK_0_2), a[4], fma(rk(RK_M0_7), a[3], c11));
+  const double Qm1 = fma(rk(RK_5), a[2], fma(rk(RK_2), a[1], -a[3]));
+  const double Qm2 = fma(rk(RK_2), a[2], fma(rk(RK_5), a[1], -a[0]));
+  const double w1 = kmul(RK_0_6, g1), K61 = kmul(RK_3_6, g1);
+  const double w2p = kmul(RK_0_3, g2), w0m = kmul(RK_0_3, g0);
+  const double ip = rcp(fma(rk(RK_0_6), g0, fma(rk(RK_1_8), g2, K61)));
+  const double im = rcp(fma(rk(RK_0_6), g2, fma(rk(RK_1_8), g0, K61)));
+  const double vp = fmul(fma(g0, Qp0, fma(w1, Qp1, fmul(w2p, Qp2))), ip);
+  const double vm = fmul(fma(g2, Qm0, fma(w1, Qm1, fmul(w0m, Qm2))), im);
   // reverse
-  const double sp = pb * iWp, sm = mb * iWm;
-  double qbp[3], qbm[3], wbp[3], wbm[3];
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    qbp[k] = sp * wp[k];
-    qbm[k] = sm * wm[k];
-    wbp[k] = sp * (qp[k] - vp);
-    wbm[k] = sm * (qm[k] - vm);
-  }
-  const double gb[3] = {fma(0.1, wbp[0], 0.3 * wbm[2]), 0.6 * (wbp[1] + wbm[1]), fma(0.3, wbp[2], 0.1 * wbm[0])};
-  double taub = 0.0, beb[3];
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    const double rb = 2.0 * r[k] * gb[k];
-    taub = fma(rb, ib[k], taub);
-    beb[k] = -rb * r[k] * ib[k];
-  }
-  beb[0] += taub;
-  beb[2] -= taub;
-  const double tb0 = k13_6 * t0 * beb[0], tb1 = k13_6 * t1 * beb[1], tb2 = k13_6 * t2 * beb[2];
-  const double ub0 = 0.5 * u0 * beb[0], ub1 = 0.5 * u1 * beb[1], ub2 = 0.5 * u2 * beb[2];
-  ab[0] = fma(k6, 2.0 * qbp[0] - qbm[2], tb0 + ub0);
-  ab[1] = fma(k6, ((-7.0 * qbp[0] - qbp[1]) + 2.0 * qbm[1]) + 5.0 * qbm[2], (-2.0 * tb0 + tb1) + (-4.0 * ub0 + ub1));
-  ab[2] = fma(k6, (11.0 * (qbp[0] + qbm[0]) + 5.0 * (qbp[1] + qbm[1])) + 2.0 * (qbp[2] + qbm[2]),
-              ((tb0 - 2.0 * tb1) + tb2) + 3.0 * (ub0 + ub2));
-  ab[3] = fma(k6, ((2.0 * qbp[1] + 5.0 * qbp[2]) - 7.0 * qbm[0]) - qbm[1], (tb1 - 2.0 * tb2) + (-ub1 - 4.0 * ub2));
-  ab[4] = fma(k6, 2.0 * qbm[0] - qbp[2], tb2 + ub2);
+  const double P = fmul(pb, ip), M = fmul(mb, im);
+  const double QBp0 = fmul(P, g0), QBp1 = fmul(P, w1), QBp2 = fmul(P, w2p);
+  const double QBm0 = fmul(M, g2), QBm1 = fmul(M, w1), QBm2 = fmul(M, w0m);
+  const double P3 = kmul(RK_0_3, P), M3 = kmul(RK_0_3, M);
+  const double gb0 = fma(P, fma(wk(0), vp, Qp0), fmul(M3, fma(wk(1), vm, Qm2)));
+  const double gb1 = kmul(RK_0_6, fma(P, fma(wk(1), vp, Qp1), fmul(M, fma(wk(1), vm, Qm1))));
+  const double gb2 = fma(M, fma(wk(0), vm, Qm0), fmul(P3, fma(wk(1), vp, Qp2)));
+  const double S0 = fmul(fmul(r0, gb0), ib0), S1 = fmul(fmul(r1, gb1), ib1), S2 = fmul(fmul(r2, gb2), ib2);
+  const double T4 = kmul(RK_FOUR, fadd(fadd(S0, S1), S2));  // 2 dJ/dtau
+  const double E0 = fma(S0, kmul(RK_M4, r0), T4);
+  const double E1 = fmul(S1, kmul(RK_M4, r1));
+  const double E2 = fma(S2, kmul(RK_M4, r2), -T4);
+  const double tb0 = fmul(E0, K0), tb1 = fmul(E1, K1), tb2 = fmul(E2, K2);
+  const double ub0 = fmul(E0, u0), ub1 = fmul(E1, u1), ub2 = fmul(E2, u2);
+  ab[0] = fma(rk(RK_0_2), QBp0, fsub(fadd(tb0, ub0), QBm2));
+  ab[1] = fma(rk(RK_M0_7), QBp0,
+              fma(rk(RK_2), QBm1,
+                  fma(rk(RK_5), QBm2, fma(rk(RK_M2), tb0, fma(rk(RK_M4), ub0, fsub(fadd(tb1, ub1), QBp1))))));
+  ab[2] = fma(rk(RK_1_1), fadd(QBp0, QBm0),
+              fma(rk(RK_5), fadd(QBp1, QBm1),
+                  fma(rk(RK_2), fadd(QBp2, QBm2), fma(rk(RK_3), fadd(ub0, ub2), fma(rk(RK_M2), tb1, fadd(tb0, tb2))))));
+  ab[3] = fma(rk(RK_2), QBp1,
+              fma(rk(RK_5), QBp2,
+                  fma(rk(RK_M0_7), QBm0, fma(rk(RK_M2), tb2, fma(rk(RK_M4), ub2, fsub(fsub(tb1, ub1), QBm1))))));
+  ab[4] = fma(rk(RK_0_2), QBm0, fsub(fadd(tb2, ub2), QBp2));
 }
 
 // Reverse of ppm_face(a, b, c, d): the clipped fourth-order value passes its
